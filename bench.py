@@ -1,0 +1,329 @@
+"""Benchmark of the NSFR-EC residual hot path on GB300.
+
+Workload (default): the inviscid Taylor-Green vortex on the warped periodic
+cube [-pi, pi]^3, 64^3 hexahedra at p = 4 (32,768,000 GL nodes, 5 variables),
+Chandrashekar EC volume and face flux, positive FR parameter c (c_HU, see
+tests/golden/c_values.json: the paper does not print c_+), classic RK4 at
+CFL 0.1.  One bench "step" is one RK4 step = four RK stages; every stage is
+the whole hot path (entropy-projected face states, volume/hybrid/surface flux
+differencing, weight-adjusted mass inverse, stage update), and the step also
+computes its CFL time step from the maximum wave speed.
+
+Metric: GDOF/s per RK stage = (nodes x stages) / time / 1e9, DOF = one
+solution node (the paper's count); x5 per conserved component is printed
+separately.  The state (1.3 GB) is larger than L2 (129 MB), so no L2 flush is
+needed between steps.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                        [--precision fp64|fp32_bulk] [--n-el E] [--p P]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+# algorithmic FP64 work (add/mul/fma/div/sqrt/log/exp each counted once) of the
+# volume kernel per two-point flux and per hybrid-term accumulation; see the
+# roofline section of the design notes for the breakdown
+OPS_PER_FLUX = 48
+OPS_PER_PAIR_ACC = 10
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
+    ap.add_argument("--n-el", type=int, default=64)
+    ap.add_argument("--p", type=int, default=4)
+    ap.add_argument("--cfl", type=float, default=0.1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def c_value(p):
+    with open(os.path.join(ROOT, "tests", "golden", "c_values.json")) as f:
+        return float(json.load(f)["c_hu"][str(p)])
+
+
+def workload_config(args):
+    n = args.p + 1
+    nodes = args.n_el ** 3 * n ** 3
+    return {
+        "workload": f"tgv_warped_{args.n_el}^3_p{args.p}",
+        "elements": args.n_el ** 3, "p": args.p, "nodes": nodes, "variables": 5,
+        "c": c_value(args.p), "c_kind": "c_HU (stand-in for c_+)", "volume_flux": "chandrashekar",
+        "face_flux": "ec", "quadrature": "GL collocated", "cfl": args.cfl, "step": "RK4 step = 4 stages",
+        "l2_flush": "not needed: state 40 B/node x nodes > 129 MB L2",
+    }
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing: each rank runs an independent replica (weak scaling)
+# --------------------------------------------------------------------------
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# --------------------------------------------------------------------------
+def oracle_sample_rate(p, n_sample=8, budget_s=20.0):
+    """GDOF/s of the oracle (one RK stage = residual + WA inverse + stage update)
+    on an n_sample^3-element periodic sample of the warped Taylor-Green cube."""
+    from oracle.problem import Problem
+    ctrl = wl.tgv_mesh(n_sample, p)
+    P = Problem(ctrl, (n_sample,) * 3, p, c=c_value(p))
+    U = P.to_internal(wl.tgv_state(P.node_coords()))
+    nodes = n_sample ** 3 * (p + 1) ** 3
+    stages = 0
+    t0 = time.perf_counter()
+    while True:
+        k = P.dudt(U)
+        U = U + 1e-4 * k  # stage update
+        stages += 1
+        if time.perf_counter() - t0 > budget_s or stages >= 40:
+            break
+    dt = time.perf_counter() - t0
+    cores = 1
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        cores = max([1] + [i.get("num_threads", 1) for i in info])
+    except Exception:
+        pass
+    return nodes * stages / dt / 1e9, cores, f"{n_sample}^3 elements at p={p} ({nodes} nodes), {stages} stages, {dt:.1f} s"
+
+
+def run_reference(args, rank, ws, dist):
+    if rank != 0:
+        return
+    cfg = workload_config(args)
+    val, cores, sample = oracle_sample_rate(args.p)
+    line = {"impl": "reference", "metric": "NSFR-EC residual GDOF/s per RK stage", "value": val,
+            "unit": "GDOF/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": val, "unit": "GDOF/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our implementation
+# --------------------------------------------------------------------------
+def volume_kernel_ops(n_el, p):
+    n = p + 1
+    fluxes_vol = 3 * n * n * n * (n - 1) // 2
+    fluxes_hyb = 6 * n ** 3
+    fluxes_face = 6 * n * n
+    per_el = (fluxes_vol + fluxes_hyb + fluxes_face) * OPS_PER_FLUX + (fluxes_vol + fluxes_hyb) * OPS_PER_PAIR_ACC
+    return per_el * n_el, {"volume_pairs": fluxes_vol, "hybrid": fluxes_hyb, "face": fluxes_face}
+
+
+def run_ours(args, rank, ws, dist):
+    import torch
+    from paper_2312_07725_gb300 import Solver
+
+    dev = torch.cuda.current_device()
+    cfg = workload_config(args)
+    p, N = args.p, args.n_el
+    ctrl = wl.tgv_mesh(N, p)
+    S = Solver(ctrl, (N, N, N), p, c=cfg["c"], face_flux="ec", precision=args.precision)
+    del ctrl
+    xyz = S.node_coords()
+    u0 = np.ascontiguousarray(wl.tgv_state(xyz))
+    del xyz
+    u = torch.from_numpy(u0).cuda()
+    stream = torch.cuda.current_stream()
+    nodes = cfg["nodes"]
+
+    for _ in range(args.warmup):
+        S.rk_step(u, cfl=args.cfl)
+    torch.cuda.synchronize()
+    barrier(dist)
+    launches0 = S.kernel_launches()
+    S.profile(True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        S.rk_step(u, cfl=args.cfl)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    S.profile(False)
+    prof = S.profile_read()
+    launches = S.kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(dist, ms)
+    stages = 4 * args.steps
+    value = nodes * stages * ws / (ms / 1e3) / 1e9
+
+    # e2e: the same RK4 step through the C ABI with pinned host buffers
+    uh = torch.from_numpy(u0).pin_memory()
+    S.rk_step(uh.numpy(), cfl=args.cfl)  # warm the staging buffers
+    barrier(dist)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        S.rk_step(uh.numpy(), cfl=args.cfl)
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
+    e2e_value = nodes * 4 * args.e2e_steps * ws / e2e_s / 1e9
+    state_bytes = u0.nbytes
+
+    # roofline of the dominant kernel (the volume/hybrid/surface kernel)
+    vol_ms, vol_n = prof.get("volume", (0.0, 0))
+    ops, counts = volume_kernel_ops(N ** 3, p)
+    achieved = ops / (vol_ms / vol_n / 1e3) / 1e12 if vol_n else None
+    peak, peak_src = fp64_peak(clk)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
+            "kernel": "volume_kernel (FP64 pipe)", "peak_source": peak_src,
+            "ops_per_launch": ops, "flux_evals_per_element": counts}
+    kern = {k: {"ms_total": v[0], "launches": v[1], "ms_avg": v[0] / v[1]} for k, v in prof.items()}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        val, cores, sample = oracle_sample_rate(p)
+        cpu = {"value": val, "unit": "GDOF/s", "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        line = {"metric": "NSFR-EC residual GDOF/s per RK stage", "value": value, "unit": "GDOF/s",
+                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+                "precision_mode": args.precision, "data": "synthetic", "config": cfg,
+                "gdof_per_s_x5_components": 5 * value,
+                "e2e": {"value": e2e_value, "unit": "GDOF/s", "h2d_bytes_per_step": state_bytes,
+                        "d2h_bytes_per_step": state_bytes},
+                "gpu_launches": launches, "kernels": kern, "roofline": roof, "clocks": clk,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+
+
+def fp64_peak(clk):
+    """FP64 FMA peak in TFLOP/s: SMs x FP64 FMA lanes per SM per clock x 2 x clock.
+
+    The lane count comes from the design notes' measurement of this part; the
+    clock is the median SM clock sampled during the timed region (max clock if
+    the sampler was unavailable)."""
+    lanes = FP64_LANES_PER_SM
+    mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    return 152 * lanes * 2 * mhz * 1e6 / 1e12, f"152 SMs x {lanes} FP64 FMA/clk/SM x 2 x {mhz:.0f} MHz"
+
+
+FP64_LANES_PER_SM = 2.0  # nominal 1.25 TFLOP/s at 2070 MHz over 152 SMs
+
+
+def main():
+    args = parse()
+    rank, ws, dist = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, ws, dist)
+    else:
+        run_ours(args, rank, ws, dist)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,225 @@
+/*
+ * nsfr.h -- C ABI of the GB300 (sm_103a) NSFR-EC residual library.
+ *
+ * Method: weight-adjusted, entropy-conserving nonlinearly stable flux
+ * reconstruction (NSFR-EC) for the 3D compressible Euler equations on
+ * curvilinear hexahedra (Cicchino & Nadarajah, arXiv 2312.07725).  The
+ * library evaluates, once per Runge-Kutta stage,
+ *   (M_m + K_m) du/dt = -R(u),           Eq. NSFR (Sec. "Nonlinearly Stable
+ *                                        Flux Reconstruction")
+ *   du/dt = -Pi~ (W J_m)^{-1} Pi~^T R,   Eq. weight-adj ESFR mass
+ *                                        (Sec. "Weight-Adjusted Inverse ...")
+ * with the solution and volume quadrature collocated on Gauss-Legendre (GL)
+ * nodes, Chandrashekar's two-point flux in the volume and on faces,
+ * entropy-projected face states u~_f = u(chi_f v^) (Sec. "Nonlinearly Stable
+ * Flux Reconstruction", entropy projected variables), conservative-curl
+ * metric terms (Sec. "Computational Space", Eq. GCL) and classic RK4
+ * (Sec. "Results").
+ *
+ * Conventions shared by every entry point
+ *   - Mesh: a structured, fully periodic block of nx*ny*nz hexahedra, element
+ *     e = ex + nx*(ey + ny*ez); element-local xi, eta, zeta follow +x, +y, +z.
+ *   - n = p+1 GL nodes per direction, n^3 per element, node index
+ *     i + n*(j + n*k) (xi fastest).  1 <= p <= 7.
+ *   - State u: conserved variables (rho, rho u, rho v, rho w, rho e) at the
+ *     GL nodes, layout [N_e][5][n^3], FP64.  With the collocated basis these
+ *     nodal values are the solution coefficients.
+ *   - Pointers marked "host or device" may point to either; the library
+ *     detects which.  Device pointers must be in the memory of the device
+ *     that was current at nsfr_setup.
+ *   - Every call that takes a stream is asynchronous on that stream
+ *     (cudaStream_t passed as void*; NULL = legacy default stream) when all
+ *     its buffers are device buffers; with a host buffer the call
+ *     synchronises the stream before returning.
+ *   - The caller owns every buffer it passes.  The library owns the metric
+ *     terms, face buffers and its workspace, freed by nsfr_destroy.
+ *   - No call aborts, traps or throws.  Errors are returned as nsfr_status;
+ *     a message is kept per context (nsfr_last_error).  Non-physical states
+ *     (rho <= 0, p <= 0 or NaN at a node) detected on the device set a
+ *     device flag; it is reported as NSFR_ERR_NONPHYSICAL by the next call
+ *     that synchronises (nsfr_rk_step with cfl > 0, nsfr_entropy,
+ *     nsfr_check) and then cleared.
+ */
+#ifndef NSFR_H
+#define NSFR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nsfr_ctx nsfr_ctx;
+
+typedef enum {
+  NSFR_OK = 0,
+  NSFR_ERR_ARG = -1,         /* invalid argument (sizes, NULL, unsupported p) */
+  NSFR_ERR_MESH = -2,        /* J <= 0 at some GL node of the mesh */
+  NSFR_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  NSFR_ERR_NONPHYSICAL = -4, /* rho <= 0, p <= 0 or NaN met on the device */
+  NSFR_ERR_OOM = -5,         /* device allocation failed */
+  NSFR_ERR_STATE = -6        /* call not valid for this context */
+} nsfr_status;
+
+typedef enum { NSFR_FLUX_CHANDRASHEKAR = 0 } nsfr_vol_flux;
+typedef enum { NSFR_FACE_EC = 0, NSFR_FACE_EC_ROE = 1 } nsfr_face_flux;
+typedef enum { NSFR_FP64 = 0, NSFR_FP32_BULK = 1 } nsfr_precision;
+
+/*
+ * nsfr_setup -- build a context: 1D operators, metric terms, workspace.
+ *   grid_nodes  host or device, [N_e][(p_geo+1)^3][3] FP64: control points
+ *               of each element's degree-p_geo tensor-product Lagrange map
+ *               x = sum_i Theta_i(xi) x_i (Sec. "Computational Space"),
+ *               placed at equispaced reference nodes xi_k = -1 + 2k/p_geo,
+ *               xi fastest.  Control points on shared faces must coincide
+ *               (up to a constant shift across the periodic boundary).
+ *   nx, ny, nz  elements per direction (each >= 1).
+ *   p_geo       map degree, 1 <= p_geo <= p.
+ *   p           solution degree, 1 <= p <= 7.
+ *   c           ESFR parameter (c = 0: DG; Sec. "Energy Stable Flux
+ *               Reconstruction", Eq. Km with c_(s,v,w) = c^{(s+v+w)/p}).
+ *   vol_flux    NSFR_FLUX_CHANDRASHEKAR (the paper's EC two-point flux).
+ *   face_flux   NSFR_FACE_EC (entropy conserving) or NSFR_FACE_EC_ROE (EC
+ *               flux plus Roe dissipation, Sec. "Nonlinear Stability").
+ *   gamma       ratio of specific heats (> 1).
+ *   precision   NSFR_FP64, or NSFR_FP32_BULK: flux differencing and operator
+ *               contractions in FP32 with FP32 accumulation; log means,
+ *               entropy variables, the entropy projection and all
+ *               reductions stay FP64 (the state itself is always FP64).
+ *   out         receives the context (NULL on failure).
+ * Metric terms are built on the device in conservative-curl form on the
+ * degree-p Lobatto nodes and interpolated to the GL nodes (Eq. GCL); the
+ * face normal of each face is shared by both neighbours.  Returns
+ * NSFR_ERR_MESH if J <= 0 anywhere.  Synchronises the current device.
+ */
+nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_geo, int p,
+                       double c, int vol_flux, int face_flux, double gamma, int precision,
+                       nsfr_ctx** out);
+
+/*
+ * nsfr_residual -- du/dt = -Pi~ (W J)^{-1} Pi~^T R(u)  (Eq. NSFR with the
+ * weight-adjusted inverse, Eq. weight-adj ESFR mass).
+ *   u     host or device, [N_e][5][n^3] FP64, read only.
+ *   dudt  host or device, [N_e][5][n^3] FP64, overwritten.
+ *   stream  cudaStream_t or NULL.
+ */
+nsfr_status nsfr_residual(nsfr_ctx* ctx, const double* u, double* dudt, void* stream);
+
+/*
+ * nsfr_residual_raw -- R(u) of Eq. NSFR, i.e. the volume flux differencing,
+ * hybrid volume-face terms and face fluxes before the mass inverse, so that
+ * (M_m + K_m) du/dt = -R.  Same arguments as nsfr_residual.
+ */
+nsfr_status nsfr_residual_raw(nsfr_ctx* ctx, const double* u, double* R, void* stream);
+
+/*
+ * nsfr_rk_step -- one classic 4-stage, 4th-order Runge-Kutta step (Sec.
+ * "Results"), u <- u + dt/6 (k1 + 2 k2 + 2 k3 + k4), each stage a fused
+ * residual + stage update.
+ *   u         host or device, [N_e][5][n^3] FP64, updated in place.
+ *   cfl       if dt_fixed <= 0: dt = cfl * dx / max_i(|u_i| + a_i) with
+ *             dx = min_d L_d/(N_d (p+1)) from the node coordinates' extent;
+ *             needs one device->host read of the max (synchronises).
+ *   dt_fixed  > 0: use this step and do not read anything back.
+ *   dt_used   host, receives dt (may be NULL).
+ */
+nsfr_status nsfr_rk_step(nsfr_ctx* ctx, double* u, double cfl, double dt_fixed, double* dt_used,
+                         void* stream);
+
+/*
+ * nsfr_entropy -- diagnostics of a state (synchronises; FP64 compensated sums).
+ *   u    host or device, [N_e][5][n^3].
+ *   out  host, 14 doubles:
+ *        [0] S       = sum W J U(u), U = -rho s/(gamma-1), s = ln p - gamma ln rho
+ *        [1] dS/dt   = -sum_i v(u_i) . R_i  (semi-discrete entropy rate,
+ *                      Sec. "Nonlinear Stability"; 0 to round-off for EC)
+ *        [2] sum_i |v(u_i) . R_i|  (scale of [1])
+ *        [3..7]  Q_k = sum W J (Pi~^{-1} u)_k, conserved by the WA scheme
+ *                      (Sec. "Global Conservation")
+ *        [8] KE      = sum W J rho |u|^2 / 2
+ *        [9..13] sum_i R_{i,k}  (0 to round-off on a periodic mesh)
+ */
+nsfr_status nsfr_entropy(nsfr_ctx* ctx, const double* u, double* out, void* stream);
+
+/*
+ * nsfr_vjp -- vector-Jacobian product of du/dt(u; x) (reverse mode, hand
+ * written; the paper has no adjoint):
+ *   u_bar += (d dudt/du)^T dudt_bar,
+ *   x_bar += (d dudt/dx)^T dudt_bar  (through the metric terms and 1/J to the
+ *            control points; skipped when x_bar is NULL).
+ *   u, dudt_bar, u_bar  device, [N_e][5][n^3] FP64.
+ *   x_bar               device or NULL, [N_e][(p_geo+1)^3][3] FP64.
+ * FP64 contexts only (NSFR_ERR_STATE otherwise).
+ */
+nsfr_status nsfr_vjp(nsfr_ctx* ctx, const double* u, const double* dudt_bar, double* u_bar,
+                     double* x_bar, void* stream);
+
+/*
+ * nsfr_node_coords -- physical coordinates of the GL nodes, [N_e][3][n^3]
+ * (host or device), for sampling initial states.
+ */
+nsfr_status nsfr_node_coords(nsfr_ctx* ctx, double* xyz, void* stream);
+
+/*
+ * nsfr_get_metrics -- copies of the metric data (host or device buffers,
+ * any may be NULL):
+ *   C    [N_e][9][n^3]  C[3d+c] = (J a^d)_c at GL volume nodes (row d of C^T)
+ *   J    [N_e][n^3]     Jacobian determinant at GL nodes
+ *   Cf   [N_e][3][3][n^2] face row (J a^d)_c on the element's xi_d = +1 face,
+ *        shared with the neighbour across that face.
+ */
+nsfr_status nsfr_get_metrics(nsfr_ctx* ctx, double* C, double* J, double* Cf, void* stream);
+
+/*
+ * nsfr_set_metrics -- replace the context's metric terms with caller-supplied
+ * ones (host or device buffers, layouts as nsfr_get_metrics; none may be
+ * NULL): C [N_e][9][n^3], J [N_e][n^3], Cf [N_e][3][3][n^2].  1/(w J) and
+ * w J are recomputed.  The face rows must be the ones both neighbours share
+ * (row of the element's xi_d = +1 face).  Returns NSFR_ERR_MESH if some
+ * J <= 0; synchronises the stream.  The control points kept for nsfr_vjp's
+ * x_bar are not changed.
+ */
+nsfr_status nsfr_set_metrics(nsfr_ctx* ctx, const double* C, const double* J, const double* Cf, void* stream);
+
+/* nsfr_info -- sizes: out[0]=N_e, [1]=p, [2]=n^3, [3]=p_geo, [4]=precision. */
+nsfr_status nsfr_info(const nsfr_ctx* ctx, long long* out);
+
+/*
+ * nsfr_check -- synchronise the context's last stream and report (then
+ * clear) a device-side non-physical-state flag.
+ */
+nsfr_status nsfr_check(nsfr_ctx* ctx);
+
+/*
+ * Kernel ids for nsfr_profile_read: 0 metric set-up, 1 face states (entropy
+ * projection), 2 volume/hybrid/surface + WA inverse (+ RK stage), 3 maximum
+ * wave speed, 4 diagnostics, 5 VJP face pass, 6 VJP volume pass, 7 VJP metric
+ * pass.
+ */
+#define NSFR_NKERNELS 8
+
+/*
+ * nsfr_profile -- on != 0: from now on record a CUDA event pair around every
+ * kernel launch, on the launch's stream, and reset the totals; on == 0: stop.
+ * Up to 65536 launches are recorded; later launches are not timed.
+ */
+nsfr_status nsfr_profile(nsfr_ctx* ctx, int on);
+
+/*
+ * nsfr_profile_read -- synchronise, then add the recorded launches' device
+ * time (ms, host double[NSFR_NKERNELS]) and counts (host long long
+ * [NSFR_NKERNELS]) per kernel id; either pointer may be NULL.
+ */
+nsfr_status nsfr_profile_read(nsfr_ctx* ctx, double* ms, long long* count);
+
+/* nsfr_kernel_launches -- kernels this context has launched so far. */
+long long nsfr_kernel_launches(const nsfr_ctx* ctx);
+
+/* nsfr_last_error -- message of the last failure on ctx ("" if none). */
+const char* nsfr_last_error(const nsfr_ctx* ctx);
+
+/* nsfr_destroy -- free everything the context owns (NULL is a no-op). */
+void nsfr_destroy(nsfr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NSFR_H */

@@ -13,7 +13,10 @@ Construction (the readings listed in the design notes):
      exact for degree <= q);
   3. (J a^i)_n = -[curl_xi (X_l grad_xi X_m)]_i, (n, m, l) cyclic, where the
      products X_l d_k X_m are interpolated on the LGL nodes and the curl is
-     the exact derivative of that interpolant;
+     the exact derivative of that interpolant; X_l is taken relative to the
+     element's first control point: curl(c grad X_m) = 0 for a constant c
+     (the discrete derivatives along different directions commute), so the
+     shift changes only rounding, which would otherwise grow like |X|/h;
   4. the resulting degree-<=q polynomials are interpolated to the GL volume
      nodes; face values are the LGL face layer interpolated tangentially to
      the face GL nodes;
@@ -86,12 +89,13 @@ def metric_terms(ctrl, p_geo, ops, dtype=None):
     # 2. exact derivatives on LGL nodes: dX[k][m] = d X_m / d xi^k
     Dl = ops.D_lgl
     dX = [[apply_1d(Dl, X[m], k) for m in range(3)] for k in range(3)]
-    # 3. conservative curl
+    # 3. conservative curl, coordinates relative to the first control point
+    Xr = X - X_eq[(slice(None), slice(None), 0, 0, 0)][..., None, None, None]
     Cl = [[None] * 3 for _ in range(3)]
     for nn in range(3):
         m = (nn + 1) % 3
         l = (nn + 2) % 3
-        V = [X[l] * dX[k][m] for k in range(3)]  # V_k = X_l d_k X_m
+        V = [Xr[l] * dX[k][m] for k in range(3)]  # V_k = (X_l - c_l) d_k X_m
         curl = [
             apply_1d(Dl, V[2], 1) - apply_1d(Dl, V[1], 2),  # d_eta V_3 - d_zeta V_2
             apply_1d(Dl, V[0], 2) - apply_1d(Dl, V[2], 0),  # d_zeta V_1 - d_xi V_3
@@ -137,6 +141,17 @@ def metric_terms(ctrl, p_geo, ops, dtype=None):
         xyz = apply_1d(Eg, xyz, d)
     return {"C": C, "J": J, "Cf": Cf, "Cf_m": Cf_m, "xyz": xyz, "C_lgl": C_lgl,
             "a_gl": a_gl}
+
+
+def node_coordinates(ctrl, p_geo, ops):
+    """Physical coordinates of the GL nodes only, (3, N_e, n, n, n): the map
+    evaluated at the GL nodes (step 1 of ``metric_terms`` without the metric)."""
+    q = p_geo + 1
+    X = _to_nodal(np.asarray(ctrl), q)
+    Eg = lagrange_eval(quadrature.equispaced(q), ops.xi)
+    for d in range(3):
+        X = apply_1d(Eg, X, d)
+    return X
 
 
 def shared_face_normals(geo, mesh):

@@ -1,0 +1,423 @@
+// C ABI of the library: context set-up, residual, RK4 step, diagnostics.
+// See include/nsfr.h for the contract of every entry point.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "nsfr_internal.h"
+
+size_t nsfr_metric_smem();
+
+namespace {
+
+nsfr_status fail(nsfr_ctx* ctx, nsfr_status st, const char* msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+nsfr_status cuda_fail(nsfr_ctx* ctx, cudaError_t e, const char* where) {
+  if (ctx) {
+    ctx->err = std::string(where) + ": " + cudaGetErrorString(e);
+  }
+  return NSFR_ERR_CUDA;
+}
+
+#define CK(call, where)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, count * sizeof(T) + 16);
+}
+
+void prof_free(nsfr_ctx* c) {
+  if (c->prof_ev) {
+    for (int i = 0; i < 2 * NSFR_PROF_CAP; ++i) cudaEventDestroy(c->prof_ev[i]);
+    delete[] c->prof_ev;
+    delete[] c->prof_kind;
+    c->prof_ev = nullptr;
+    c->prof_kind = nullptr;
+  }
+}
+
+void free_all(nsfr_ctx* c) {
+  double* dbl[] = {c->ctrl, c->metric, c->J, c->invwj, c->wj, c->nfp_plus, c->xyz, c->face,
+                   c->ustage, c->acc, c->rtmp, c->hbuf_in, c->hbuf_out, c->red};
+  for (double* p : dbl)
+    if (p) cudaFree(p);
+  if (c->metric32) cudaFree(c->metric32);
+  if (c->nfp_plus32) cudaFree(c->nfp_plus32);
+  if (c->flag) cudaFree(c->flag);
+  if (c->umax) cudaFree(c->umax);
+  if (c->red_host) cudaFreeHost(c->red_host);
+  if (c->flag_host) cudaFreeHost(c->flag_host);
+  if (c->umax_host) cudaFreeHost(c->umax_host);
+  prof_free(c);
+}
+
+size_t state_count(const nsfr_ctx* c) { return (size_t)c->ne * 5 * c->nv; }
+
+nsfr_status ensure_host_buffers(nsfr_ctx* ctx) {
+  if (!ctx->hbuf_in) CK(dalloc(&ctx->hbuf_in, state_count(ctx)), "cudaMalloc(staging)");
+  if (!ctx->hbuf_out) CK(dalloc(&ctx->hbuf_out, state_count(ctx)), "cudaMalloc(staging)");
+  return NSFR_OK;
+}
+
+// read (and clear) the device error word; synchronises the stream
+nsfr_status read_flag(nsfr_ctx* ctx, cudaStream_t s) {
+  CK(cudaMemcpyAsync(ctx->flag_host, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(flag)");
+  CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  const int f = *ctx->flag_host;
+  if (f) {
+    CK(cudaMemsetAsync(ctx->flag, 0, sizeof(int), s), "cudaMemsetAsync(flag)");
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (f & 2) return fail(ctx, NSFR_ERR_MESH, "non-positive Jacobian at a GL node");
+    return fail(ctx, NSFR_ERR_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or NaN) met on the device");
+  }
+  return NSFR_OK;
+}
+
+nsfr_status residual_device(nsfr_ctx* ctx, const double* u, double* out, int epi, cudaStream_t s) {
+  CK(nsfr_launch_face_states(ctx, u, s), "face_state_kernel");
+  CK(nsfr_launch_volume(ctx, u, out, epi, nullptr, s), "volume_kernel");
+  return NSFR_OK;
+}
+
+nsfr_status residual_any(nsfr_ctx* ctx, const double* u, double* out, int epi, void* stream) {
+  if (!ctx) return NSFR_ERR_ARG;
+  if (!u || !out) return fail(ctx, NSFR_ERR_ARG, "NULL buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  const bool du = is_device_ptr(u), dout = is_device_ptr(out);
+  if (du && dout) return residual_device(ctx, u, out, epi, s);
+  nsfr_status st = ensure_host_buffers(ctx);
+  if (st != NSFR_OK) return st;
+  const size_t bytes = state_count(ctx) * sizeof(double);
+  const double* ud = u;
+  if (!du) {
+    CK(cudaMemcpyAsync(ctx->hbuf_in, u, bytes, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(H2D)");
+    ud = ctx->hbuf_in;
+  }
+  double* od = dout ? out : ctx->hbuf_out;
+  st = residual_device(ctx, ud, od, epi, s);
+  if (st != NSFR_OK) return st;
+  if (!dout) CK(cudaMemcpyAsync(out, od, bytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(D2H)");
+  CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  return NSFR_OK;
+}
+
+nsfr_status rk_step_device(nsfr_ctx* ctx, double* u, double cfl, double dt_fixed, double* dt_used,
+                           cudaStream_t s) {
+  double dt = dt_fixed;
+  if (!(dt_fixed > 0.0)) {
+    if (!(cfl > 0.0)) return fail(ctx, NSFR_ERR_ARG, "need cfl > 0 or dt_fixed > 0");
+    CK(nsfr_launch_max_wavespeed(ctx, u, s), "max_wavespeed_kernel");
+    CK(cudaMemcpyAsync(ctx->umax_host, ctx->umax, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s),
+       "cudaMemcpyAsync(max)");
+    nsfr_status st = read_flag(ctx, s);  // synchronises
+    if (st != NSFR_OK) return st;
+    double lam;
+    std::memcpy(&lam, ctx->umax_host, sizeof(double));
+    if (!(lam > 0.0)) return fail(ctx, NSFR_ERR_NONPHYSICAL, "zero or invalid wave speed");
+    dt = cfl * ctx->dx / lam;
+  }
+  if (dt_used) *dt_used = dt;
+  // classic RK4: u_{s+1} = u^n + a_s dt k_s, acc = u^n + sum b_s dt k_s
+  const double a[3] = {0.5, 0.5, 1.0};
+  const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  for (int st = 0; st < 4; ++st) {
+    const double* in = (st == 0) ? u : ctx->ustage;
+    RkArgs rk;
+    rk.u0 = u;
+    rk.acc = ctx->acc;
+    rk.dt = dt;
+    rk.b = b[st];
+    rk.first = (st == 0);
+    rk.last = (st == 3);
+    rk.a_next = (st < 3) ? a[st] : 0.0;
+    rk.unext = (st == 3) ? u : ctx->ustage;
+    CK(nsfr_launch_face_states(ctx, in, s), "face_state_kernel");
+    CK(nsfr_launch_volume(ctx, in, nullptr, EPI_RK, &rk, s), "volume_kernel(rk)");
+  }
+  return NSFR_OK;
+}
+
+}  // namespace
+
+void nsfr_prof_begin(nsfr_ctx* ctx, int kind, cudaStream_t s) {
+  if (!ctx->prof_on || ctx->prof_n >= NSFR_PROF_CAP) return;
+  ctx->prof_kind[ctx->prof_n] = kind;
+  cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], s);
+}
+
+void nsfr_prof_end(nsfr_ctx* ctx, cudaStream_t s) {
+  if (!ctx->prof_on || ctx->prof_n >= NSFR_PROF_CAP) return;
+  cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], s);
+  ctx->prof_n++;
+}
+
+extern "C" {
+
+nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_geo, int p, double c,
+                       int vol_flux, int face_flux, double gamma, int precision, nsfr_ctx** out) {
+  if (!out) return NSFR_ERR_ARG;
+  *out = nullptr;
+  if (!grid_nodes || nx < 1 || ny < 1 || nz < 1 || p < 1 || p > 7 || p_geo < 1 || p_geo > p || !(gamma > 1.0) ||
+      vol_flux != NSFR_FLUX_CHANDRASHEKAR || (face_flux != NSFR_FACE_EC && face_flux != NSFR_FACE_EC_ROE) ||
+      (precision != NSFR_FP64 && precision != NSFR_FP32_BULK) || !std::isfinite(c) || c < 0.0)
+    return NSFR_ERR_ARG;
+  if (precision == NSFR_FP32_BULK) return NSFR_ERR_ARG;  // FP32-bulk kernels not built yet
+  nsfr_ctx* ctx = new (std::nothrow) nsfr_ctx();
+  if (!ctx) return NSFR_ERR_OOM;
+  ctx->nx = nx;
+  ctx->ny = ny;
+  ctx->nz = nz;
+  ctx->ne = nx * ny * nz;
+  ctx->p = p;
+  ctx->n = p + 1;
+  ctx->pg = p_geo;
+  ctx->q = p_geo + 1;
+  ctx->nv = ctx->n * ctx->n * ctx->n;
+  ctx->nfp = ctx->n * ctx->n;
+  ctx->c = c;
+  ctx->gamma = gamma;
+  ctx->vol_flux = vol_flux;
+  ctx->face_flux = face_flux;
+  ctx->precision = precision;
+  cudaGetDevice(&ctx->device);
+  nsfr_build_ops(p, p_geo, c, gamma, &ctx->ops, &ctx->gops);
+
+  auto bail = [&](nsfr_status st) {
+    free_all(ctx);
+    delete ctx;
+    return st;
+  };
+  const size_t ne = ctx->ne, nv = ctx->nv, nfp = ctx->nfp, q3 = (size_t)ctx->q * ctx->q * ctx->q;
+  bool ok = dalloc(&ctx->ctrl, ne * q3 * 3) == cudaSuccess && dalloc(&ctx->metric, ne * 9 * nv) == cudaSuccess &&
+            dalloc(&ctx->J, ne * nv) == cudaSuccess && dalloc(&ctx->invwj, ne * nv) == cudaSuccess &&
+            dalloc(&ctx->wj, ne * nv) == cudaSuccess && dalloc(&ctx->nfp_plus, ne * 9 * nfp) == cudaSuccess &&
+            dalloc(&ctx->xyz, ne * 3 * nv) == cudaSuccess &&
+            dalloc(&ctx->face, ne * 6 * NSFR_NFIELD * nfp) == cudaSuccess &&
+            dalloc(&ctx->ustage, ne * 5 * nv) == cudaSuccess && dalloc(&ctx->acc, ne * 5 * nv) == cudaSuccess &&
+            dalloc(&ctx->flag, 1) == cudaSuccess && dalloc(&ctx->umax, 1) == cudaSuccess &&
+            cudaMallocHost((void**)&ctx->flag_host, sizeof(int)) == cudaSuccess &&
+            cudaMallocHost((void**)&ctx->umax_host, sizeof(unsigned long long)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return bail(NSFR_ERR_OOM);
+  }
+  if (cudaMemset(ctx->flag, 0, sizeof(int)) != cudaSuccess) return bail(NSFR_ERR_CUDA);
+  const size_t cbytes = ne * q3 * 3 * sizeof(double);
+  if (cudaMemcpy(ctx->ctrl, grid_nodes, cbytes, cudaMemcpyDefault) != cudaSuccess) return bail(NSFR_ERR_CUDA);
+  // node spacing for the CFL step: domain extent of the control points
+  {
+    std::vector<double> h(ne * q3 * 3);
+    if (cudaMemcpy(h.data(), ctx->ctrl, cbytes, cudaMemcpyDeviceToHost) != cudaSuccess) return bail(NSFR_ERR_CUDA);
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (size_t i = 0; i < h.size(); ++i) {
+      const int cc = (int)(i % 3);
+      lo[cc] = std::fmin(lo[cc], h[i]);
+      hi[cc] = std::fmax(hi[cc], h[i]);
+    }
+    const int N[3] = {nx, ny, nz};
+    double dx = 1e300;
+    for (int d = 0; d < 3; ++d) dx = std::fmin(dx, (hi[d] - lo[d]) / (N[d] * (p + 1.0)));
+    ctx->dx = dx;
+  }
+  if (nsfr_launch_metrics(ctx, 0) != cudaSuccess) return bail(NSFR_ERR_CUDA);
+  if (cudaDeviceSynchronize() != cudaSuccess) return bail(NSFR_ERR_CUDA);
+  int f = 0;
+  if (cudaMemcpy(&f, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return bail(NSFR_ERR_CUDA);
+  if (f & 2) return bail(NSFR_ERR_MESH);
+  *out = ctx;
+  return NSFR_OK;
+}
+
+nsfr_status nsfr_residual(nsfr_ctx* ctx, const double* u, double* dudt, void* stream) {
+  return residual_any(ctx, u, dudt, EPI_DUDT, stream);
+}
+
+nsfr_status nsfr_residual_raw(nsfr_ctx* ctx, const double* u, double* R, void* stream) {
+  return residual_any(ctx, u, R, EPI_RAW, stream);
+}
+
+nsfr_status nsfr_rk_step(nsfr_ctx* ctx, double* u, double cfl, double dt_fixed, double* dt_used, void* stream) {
+  if (!ctx) return NSFR_ERR_ARG;
+  if (!u) return fail(ctx, NSFR_ERR_ARG, "NULL state");
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  if (is_device_ptr(u)) return rk_step_device(ctx, u, cfl, dt_fixed, dt_used, s);
+  nsfr_status st = ensure_host_buffers(ctx);
+  if (st != NSFR_OK) return st;
+  const size_t bytes = state_count(ctx) * sizeof(double);
+  CK(cudaMemcpyAsync(ctx->hbuf_in, u, bytes, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(H2D)");
+  st = rk_step_device(ctx, ctx->hbuf_in, cfl, dt_fixed, dt_used, s);
+  if (st != NSFR_OK) return st;
+  CK(cudaMemcpyAsync(u, ctx->hbuf_in, bytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(D2H)");
+  CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  return NSFR_OK;
+}
+
+nsfr_status nsfr_entropy(nsfr_ctx* ctx, const double* u, double* out, void* stream) {
+  if (!ctx) return NSFR_ERR_ARG;
+  if (!u || !out) return fail(ctx, NSFR_ERR_ARG, "NULL buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  if (!ctx->rtmp) CK(dalloc(&ctx->rtmp, state_count(ctx)), "cudaMalloc(rtmp)");
+  const int nb = nsfr_diag_blocks(ctx);
+  if (!ctx->red || ctx->red_cap < nb) {
+    if (ctx->red) cudaFree(ctx->red);
+    if (ctx->red_host) cudaFreeHost(ctx->red_host);
+    ctx->red = nullptr;
+    ctx->red_host = nullptr;
+    CK(dalloc(&ctx->red, (size_t)nb * 28), "cudaMalloc(red)");
+    CK(cudaMallocHost((void**)&ctx->red_host, (size_t)nb * 28 * sizeof(double)), "cudaMallocHost(red)");
+    ctx->red_cap = nb;
+  }
+  const double* ud = u;
+  if (!is_device_ptr(u)) {
+    nsfr_status st = ensure_host_buffers(ctx);
+    if (st != NSFR_OK) return st;
+    CK(cudaMemcpyAsync(ctx->hbuf_in, u, state_count(ctx) * sizeof(double), cudaMemcpyHostToDevice, s),
+       "cudaMemcpyAsync(H2D)");
+    ud = ctx->hbuf_in;
+  }
+  nsfr_status st = residual_device(ctx, ud, ctx->rtmp, EPI_RAW, s);
+  if (st != NSFR_OK) return st;
+  CK(nsfr_launch_diagnostics(ctx, ud, ctx->rtmp, ctx->red, nb, s), "diagnostics_kernel");
+  CK(cudaMemcpyAsync(ctx->red_host, ctx->red, (size_t)nb * 28 * sizeof(double), cudaMemcpyDeviceToHost, s),
+     "cudaMemcpyAsync(partials)");
+  st = read_flag(ctx, s);
+  if (st != NSFR_OK) return st;
+  // finish the compensated sums over blocks (Neumaier on the leading parts)
+  for (int k = 0; k < 14; ++k) {
+    double sum = 0.0, comp = 0.0;
+    for (int b = 0; b < nb; ++b) {
+      const double x = ctx->red_host[((size_t)b * 14 + k) * 2];
+      comp += ctx->red_host[((size_t)b * 14 + k) * 2 + 1];
+      const double t = sum + x;
+      if (std::fabs(sum) >= std::fabs(x)) comp += (sum - t) + x;
+      else comp += (x - t) + sum;
+      sum = t;
+    }
+    out[k] = sum + comp;
+  }
+  return NSFR_OK;
+}
+
+nsfr_status nsfr_vjp(nsfr_ctx* ctx, const double* u, const double* dudt_bar, double* u_bar, double* x_bar,
+                     void* stream) {
+  if (!ctx) return NSFR_ERR_ARG;
+  if (ctx->precision != NSFR_FP64) return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp needs an FP64 context");
+  if (!u || !dudt_bar || !u_bar) return fail(ctx, NSFR_ERR_ARG, "NULL buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  CK(nsfr_launch_vjp(ctx, u, dudt_bar, u_bar, x_bar, s), "vjp kernels");
+  return NSFR_OK;
+}
+
+nsfr_status nsfr_node_coords(nsfr_ctx* ctx, double* xyz, void* stream) {
+  if (!ctx) return NSFR_ERR_ARG;
+  if (!xyz) return fail(ctx, NSFR_ERR_ARG, "NULL buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(xyz, ctx->xyz, (size_t)ctx->ne * 3 * ctx->nv * sizeof(double), cudaMemcpyDefault, s),
+     "cudaMemcpyAsync(xyz)");
+  CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  return NSFR_OK;
+}
+
+nsfr_status nsfr_get_metrics(nsfr_ctx* ctx, double* C, double* J, double* Cf, void* stream) {
+  if (!ctx) return NSFR_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ne = ctx->ne, nv = ctx->nv, nfp = ctx->nfp;
+  if (C) CK(cudaMemcpyAsync(C, ctx->metric, ne * 9 * nv * sizeof(double), cudaMemcpyDefault, s), "copy C");
+  if (J) CK(cudaMemcpyAsync(J, ctx->J, ne * nv * sizeof(double), cudaMemcpyDefault, s), "copy J");
+  if (Cf) CK(cudaMemcpyAsync(Cf, ctx->nfp_plus, ne * 9 * nfp * sizeof(double), cudaMemcpyDefault, s), "copy Cf");
+  CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  return NSFR_OK;
+}
+
+nsfr_status nsfr_set_metrics(nsfr_ctx* ctx, const double* C, const double* J, const double* Cf, void* stream) {
+  if (!ctx) return NSFR_ERR_ARG;
+  if (!C || !J || !Cf) return fail(ctx, NSFR_ERR_ARG, "NULL buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ne = ctx->ne, nv = ctx->nv, nfp = ctx->nfp;
+  CK(cudaMemcpyAsync(ctx->metric, C, ne * 9 * nv * sizeof(double), cudaMemcpyDefault, s), "copy C");
+  CK(cudaMemcpyAsync(ctx->J, J, ne * nv * sizeof(double), cudaMemcpyDefault, s), "copy J");
+  CK(cudaMemcpyAsync(ctx->nfp_plus, Cf, ne * 9 * nfp * sizeof(double), cudaMemcpyDefault, s), "copy Cf");
+  CK(nsfr_launch_jacobian_derived(ctx, s), "jacobian_derived_kernel");
+  return read_flag(ctx, s);
+}
+
+nsfr_status nsfr_info(const nsfr_ctx* ctx, long long* out) {
+  if (!ctx || !out) return NSFR_ERR_ARG;
+  out[0] = ctx->ne;
+  out[1] = ctx->p;
+  out[2] = ctx->nv;
+  out[3] = ctx->pg;
+  out[4] = ctx->precision;
+  return NSFR_OK;
+}
+
+nsfr_status nsfr_check(nsfr_ctx* ctx) {
+  if (!ctx) return NSFR_ERR_ARG;
+  return read_flag(ctx, ctx->last_stream);
+}
+
+nsfr_status nsfr_profile(nsfr_ctx* ctx, int on) {
+  if (!ctx) return NSFR_ERR_ARG;
+  if (on && !ctx->prof_ev) {
+    ctx->prof_ev = new (std::nothrow) cudaEvent_t[2 * NSFR_PROF_CAP];
+    ctx->prof_kind = new (std::nothrow) int[NSFR_PROF_CAP];
+    if (!ctx->prof_ev || !ctx->prof_kind) return fail(ctx, NSFR_ERR_OOM, "profile buffers");
+    for (int i = 0; i < 2 * NSFR_PROF_CAP; ++i) CK(cudaEventCreate(&ctx->prof_ev[i]), "cudaEventCreate");
+  }
+  ctx->prof_on = on ? 1 : 0;
+  if (on) ctx->prof_n = 0;
+  return NSFR_OK;
+}
+
+nsfr_status nsfr_profile_read(nsfr_ctx* ctx, double* ms, long long* count) {
+  if (!ctx) return NSFR_ERR_ARG;
+  double t[NSFR_NKERNELS] = {0};
+  long long c[NSFR_NKERNELS] = {0};
+  for (int i = 0; i < ctx->prof_n; ++i) {
+    CK(cudaEventSynchronize(ctx->prof_ev[2 * i + 1]), "cudaEventSynchronize");
+    float el = 0.f;
+    CK(cudaEventElapsedTime(&el, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]), "cudaEventElapsedTime");
+    t[ctx->prof_kind[i]] += el;
+    c[ctx->prof_kind[i]] += 1;
+  }
+  for (int k = 0; k < NSFR_NKERNELS; ++k) {
+    if (ms) ms[k] = t[k];
+    if (count) count[k] = c[k];
+  }
+  return NSFR_OK;
+}
+
+long long nsfr_kernel_launches(const nsfr_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+const char* nsfr_last_error(const nsfr_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+void nsfr_destroy(nsfr_ctx* ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  free_all(ctx);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "nsfr.h"
+
+#define NSFR_MAXN 8   // n = p+1 <= 8
+#define NSFR_NFIELD 8 // per-node primitive record, see Prim below
+
+// 1D operators of the collocated GL basis, passed to kernels by value (they
+// land in the constant bank).  Row-major n x n matrices.
+struct OpsGL {
+  int n;
+  int has_K;             // c != 0: the FR projection is not the identity
+  double gamma;
+  double w[NSFR_MAXN];   // GL weights
+  double tm[NSFR_MAXN];  // l_j(-1)
+  double tp[NSFR_MAXN];  // l_j(+1)
+  double S1[NSFR_MAXN * NSFR_MAXN];   // W D - D^T W
+  double Pi1[NSFR_MAXN * NSFR_MAXN];  // (W + K1)^{-1} W
+  double Pinv1[NSFR_MAXN * NSFR_MAXN];  // Pi1^{-1} = I + W^{-1} K1
+  float S1f[NSFR_MAXN * NSFR_MAXN];
+  float Pi1f[NSFR_MAXN * NSFR_MAXN];
+  float wf[NSFR_MAXN];
+  float tmf[NSFR_MAXN];
+  float tpf[NSFR_MAXN];
+};
+
+// Operators of the metric construction (Lobatto nodes of degree p).
+struct OpsGeo {
+  int n;   // GL/LGL nodes per direction
+  int q;   // control points per direction (p_geo + 1)
+  double E[NSFR_MAXN * NSFR_MAXN];   // equispaced(q) -> LGL(n), n x q
+  double Eg[NSFR_MAXN * NSFR_MAXN];  // equispaced(q) -> GL(n),  n x q
+  double Dl[NSFR_MAXN * NSFR_MAXN];  // LGL differentiation, n x n
+  double I[NSFR_MAXN * NSFR_MAXN];   // LGL -> GL interpolation, n x n
+  double w[NSFR_MAXN];               // GL weights
+};
+
+// Host construction of the operators (ops1d.cpp).
+void nsfr_build_ops(int p, int p_geo, double c, double gamma, OpsGL* gl, OpsGeo* geo);
+void nsfr_gauss_legendre(int n, double* x, double* w);
+void nsfr_gauss_lobatto(int n, double* x, double* w);
+
+struct nsfr_ctx {
+  int nx, ny, nz, ne, p, n, pg, q, nv, nfp;
+  double c, gamma;
+  int vol_flux, face_flux, precision;
+  OpsGL ops;
+  OpsGeo gops;
+  int device;
+  double dx;  // min_d L_d / (N_d (p+1))
+  // device buffers owned by the context
+  double* ctrl = nullptr;     // [ne][q^3][3]
+  double* metric = nullptr;   // [ne][9][nv]
+  float* metric32 = nullptr;  // [ne][9][nv] (FP32-bulk contexts)
+  double* J = nullptr;        // [ne][nv]
+  double* invwj = nullptr;    // [ne][nv] 1/(w_i w_j w_k J)
+  double* wj = nullptr;       // [ne][nv] w_i w_j w_k J
+  double* nfp_plus = nullptr; // [ne][3][3][nfp]
+  float* nfp_plus32 = nullptr;
+  double* xyz = nullptr;      // [ne][3][nv]
+  double* face = nullptr;     // [ne][6][NSFR_NFIELD][nfp] face-state scratch
+  double* ustage = nullptr;   // [ne][5][nv]
+  double* acc = nullptr;      // [ne][5][nv]
+  double* rtmp = nullptr;     // [ne][5][nv] (diagnostics / VJP scratch)
+  double* hbuf_in = nullptr;  // staging for host pointers [ne][5][nv]
+  double* hbuf_out = nullptr;
+  double* red = nullptr;      // reduction scratch
+  int red_cap = 0;
+  double* red_host = nullptr; // pinned
+  int* flag = nullptr;        // device error word
+  int* flag_host = nullptr;   // pinned
+  unsigned long long* umax = nullptr;  // max wave speed (bit pattern)
+  unsigned long long* umax_host = nullptr;
+  long long launches = 0;
+  // per-launch event pairs (nsfr_profile)
+  int prof_on = 0;
+  int prof_n = 0;
+  cudaEvent_t* prof_ev = nullptr;  // 2 * NSFR_PROF_CAP events
+  int* prof_kind = nullptr;
+  cudaStream_t last_stream = nullptr;
+  std::string err;
+};
+
+#define NSFR_PROF_CAP 65536
+// bracket a launch with profiling events (no-op unless nsfr_profile is on)
+void nsfr_prof_begin(nsfr_ctx* ctx, int kind, cudaStream_t s);
+void nsfr_prof_end(nsfr_ctx* ctx, cudaStream_t s);
+
+// Per-node primitive record used by the flux kernels (NSFR_NFIELD doubles).
+enum { P_RHO = 0, P_U = 1, P_V = 2, P_W = 3, P_BETA = 4, P_LRHO = 5, P_LBETA = 6, P_Q2 = 7 };
+
+// Launchers (residual.cu)
+enum { EPI_RAW = 0, EPI_DUDT = 1, EPI_RK = 2 };
+struct RkArgs {
+  const double* u0;   // u^n
+  double* unext;      // where the next stage state goes
+  double* acc;        // RK accumulator
+  double a_next;      // u_next = u0 + a_next dt k
+  double b;           // acc (+)= b dt k
+  double dt;
+  int first;          // acc = u0 + b dt k
+  int last;           // unext = acc + b dt k (final update)
+};
+cudaError_t nsfr_launch_face_states(nsfr_ctx* ctx, const double* u, cudaStream_t s);
+cudaError_t nsfr_launch_volume(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk,
+                               cudaStream_t s);
+// geometry.cu
+cudaError_t nsfr_launch_metrics(nsfr_ctx* ctx, cudaStream_t s);
+cudaError_t nsfr_launch_jacobian_derived(nsfr_ctx* ctx, cudaStream_t s);
+// reduce.cu
+cudaError_t nsfr_launch_max_wavespeed(nsfr_ctx* ctx, const double* u, cudaStream_t s);
+cudaError_t nsfr_launch_diagnostics(nsfr_ctx* ctx, const double* u, const double* R, double* partial,
+                                    int nblocks, cudaStream_t s);
+int nsfr_diag_blocks(nsfr_ctx* ctx);
+// vjp.cu
+cudaError_t nsfr_launch_vjp(nsfr_ctx* ctx, const double* u, const double* dbar, double* ubar,
+                            double* xbar, cudaStream_t s);

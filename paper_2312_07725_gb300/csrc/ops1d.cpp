@@ -1,0 +1,175 @@
+// Host construction of the 1D operators (run once per context).
+//
+// GL and Lobatto rules by Newton iteration on the Legendre recurrence;
+// Lagrange interpolation and differentiation in barycentric form (Berrut &
+// Trefethen's formulas); SBP skew operator S1 = W D - D^T W (Sec.
+// "Computational Space", SBP property); ESFR K1 = c (D^p)^T W D^p = 2c g g^T,
+// g_j the p-th derivative of the j-th Lagrange polynomial (Eq. Km in 1D with
+// J = 1); FR projection Pi~1 = (W + K1)^{-1} W (Eq. Fr projection with
+// chi = I) written in Sherman-Morrison form, and its inverse I + W^{-1} K1.
+#include <cmath>
+#include <cstring>
+
+#include "nsfr_internal.h"
+
+static void legendre(int N, double x, double* P, double* dP) {
+  double p0 = 1.0, p1 = x;
+  if (N == 0) {
+    *P = 1.0;
+    *dP = 0.0;
+    return;
+  }
+  for (int k = 2; k <= N; ++k) {
+    double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+    p0 = p1;
+    p1 = p2;
+  }
+  *P = p1;
+  *dP = (std::fabs(x * x - 1.0) > 0.0) ? N * (x * p1 - p0) / (x * x - 1.0) : 0.0;
+}
+
+void nsfr_gauss_legendre(int n, double* x, double* w) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double xi = -std::cos(pi * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre(n, xi, &P, &dP);
+      double dx = P / dP;
+      xi -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    double P, dP;
+    legendre(n, xi, &P, &dP);
+    x[i] = xi;
+    w[i] = 2.0 / ((1.0 - xi * xi) * dP * dP);
+  }
+}
+
+void nsfr_gauss_lobatto(int n, double* x, double* w) {
+  const double pi = 3.14159265358979323846;
+  const int N = n - 1;
+  x[0] = -1.0;
+  x[N] = 1.0;
+  for (int i = 1; i < N; ++i) {
+    double xi = -std::cos(pi * i / N);
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre(N, xi, &P, &dP);
+      double d2P = (2.0 * xi * dP - N * (N + 1.0) * P) / (1.0 - xi * xi);
+      double dx = dP / d2P;
+      xi -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    x[i] = xi;
+  }
+  for (int i = 0; i < n; ++i) {
+    double P, dP;
+    legendre(N, x[i], &P, &dP);
+    w[i] = 2.0 / (N * (N + 1.0) * P * P);
+  }
+}
+
+// barycentric weights lambda_j = 1 / prod_{k != j} (x_j - x_k)
+static void bary_weights(int n, const double* x, double* lam) {
+  for (int j = 0; j < n; ++j) {
+    double prod = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != j) prod *= (x[j] - x[k]);
+    lam[j] = 1.0 / prod;
+  }
+}
+
+// L[r][j] = l_j(y_r), r < m: barycentric interpolation matrix (m x n)
+static void interp_matrix(int n, const double* x, int m, const double* y, double* L) {
+  double lam[NSFR_MAXN];
+  bary_weights(n, x, lam);
+  for (int r = 0; r < m; ++r) {
+    int hit = -1;
+    for (int j = 0; j < n; ++j)
+      if (y[r] == x[j]) hit = j;
+    if (hit >= 0) {
+      for (int j = 0; j < n; ++j) L[r * n + j] = (j == hit) ? 1.0 : 0.0;
+      continue;
+    }
+    double den = 0.0;
+    for (int j = 0; j < n; ++j) den += lam[j] / (y[r] - x[j]);
+    for (int j = 0; j < n; ++j) L[r * n + j] = (lam[j] / (y[r] - x[j])) / den;
+  }
+}
+
+// D[i][j] = l_j'(x_i) on the nodes themselves (barycentric, negative-sum diagonal)
+static void diff_matrix(int n, const double* x, double* D) {
+  double lam[NSFR_MAXN];
+  bary_weights(n, x, lam);
+  for (int i = 0; i < n; ++i) {
+    double diag = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double v = (lam[j] / lam[i]) / (x[i] - x[j]);
+      D[i * n + j] = v;
+      diag -= v;
+    }
+    D[i * n + i] = diag;
+  }
+}
+
+void nsfr_build_ops(int p, int p_geo, double c, double gamma, OpsGL* gl, OpsGeo* geo) {
+  const int n = p + 1;
+  const int q = p_geo + 1;
+  std::memset(gl, 0, sizeof(*gl));
+  std::memset(geo, 0, sizeof(*geo));
+  double xg[NSFR_MAXN], wg[NSFR_MAXN], xl[NSFR_MAXN], wl[NSFR_MAXN], xe[NSFR_MAXN];
+  nsfr_gauss_legendre(n, xg, wg);
+  nsfr_gauss_lobatto(n, xl, wl);
+  for (int k = 0; k < q; ++k) xe[k] = (q == 1) ? 0.0 : -1.0 + 2.0 * k / (q - 1);
+
+  gl->n = n;
+  gl->gamma = gamma;
+  gl->has_K = (c != 0.0);
+  double D[NSFR_MAXN * NSFR_MAXN];
+  diff_matrix(n, xg, D);
+  double ends[2] = {-1.0, 1.0};
+  double T[2 * NSFR_MAXN];
+  interp_matrix(n, xg, 2, ends, T);
+  for (int j = 0; j < n; ++j) {
+    gl->w[j] = wg[j];
+    gl->tm[j] = T[j];
+    gl->tp[j] = T[n + j];
+  }
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) gl->S1[a * n + b] = wg[a] * D[a * n + b] - D[b * n + a] * wg[b];
+  // g_j = p! lambda_j (p-th derivative of l_j)
+  double lam[NSFR_MAXN], g[NSFR_MAXN];
+  bary_weights(n, xg, lam);
+  double fact = 1.0;
+  for (int k = 2; k <= p; ++k) fact *= k;
+  for (int j = 0; j < n; ++j) g[j] = fact * lam[j];
+  // K1 = 2 c g g^T ; (W + K1)^{-1} W = I - 2c W^{-1} g g^T / (1 + 2c g^T W^{-1} g)
+  double gWg = 0.0;
+  for (int j = 0; j < n; ++j) gWg += g[j] * g[j] / wg[j];
+  const double denom = 1.0 + 2.0 * c * gWg;
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      double id = (a == b) ? 1.0 : 0.0;
+      gl->Pi1[a * n + b] = id - 2.0 * c * (g[a] / wg[a]) * g[b] / denom;
+      gl->Pinv1[a * n + b] = id + 2.0 * c * (g[a] / wg[a]) * g[b];
+    }
+  for (int k = 0; k < n * n; ++k) {
+    gl->S1f[k] = (float)gl->S1[k];
+    gl->Pi1f[k] = (float)gl->Pi1[k];
+  }
+  for (int j = 0; j < n; ++j) {
+    gl->wf[j] = (float)gl->w[j];
+    gl->tmf[j] = (float)gl->tm[j];
+    gl->tpf[j] = (float)gl->tp[j];
+  }
+
+  geo->n = n;
+  geo->q = q;
+  interp_matrix(q, xe, n, xl, geo->E);
+  interp_matrix(q, xe, n, xg, geo->Eg);
+  diff_matrix(n, xl, geo->Dl);
+  interp_matrix(n, xl, n, xg, geo->I);
+  for (int j = 0; j < n; ++j) geo->w[j] = wg[j];
+}

@@ -1,0 +1,214 @@
+"""Thin ctypes binding of the C ABI declared in include/nsfr.h.
+
+Argument marshalling only: every computation runs in the CUDA library
+``libnsfr.so`` built in-tree for sm_103a.  Tensors are passed by
+``data_ptr()``, numpy arrays by their buffer address (host pointers, which the
+library stages through device memory), streams as the raw cudaStream_t of
+``torch.cuda.current_stream()``.  A missing library raises at import: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnsfr.so")
+
+NSFR_OK = 0
+STATUS = {0: "NSFR_OK", -1: "NSFR_ERR_ARG", -2: "NSFR_ERR_MESH", -3: "NSFR_ERR_CUDA",
+          -4: "NSFR_ERR_NONPHYSICAL", -5: "NSFR_ERR_OOM", -6: "NSFR_ERR_STATE"}
+FACE_FLUX = {"ec": 0, "ec_roe": 1}
+PRECISION = {"fp64": 0, "fp32_bulk": 1}
+
+# every symbol include/nsfr.h declares
+EXPORTS = ["nsfr_setup", "nsfr_residual", "nsfr_residual_raw", "nsfr_rk_step", "nsfr_entropy",
+           "nsfr_vjp", "nsfr_node_coords", "nsfr_get_metrics", "nsfr_set_metrics", "nsfr_info", "nsfr_check",
+           "nsfr_profile", "nsfr_profile_read", "nsfr_kernel_launches", "nsfr_last_error", "nsfr_destroy"]
+KERNELS = ["metrics", "face_states", "volume", "max_wavespeed", "diagnostics", "vjp_face", "vjp_volume",
+           "vjp_metrics"]
+
+
+class NSFRError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load_library(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2312_07725_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.nsfr_setup.argtypes = [vp, i, i, i, i, i, d, i, i, d, i, ctypes.POINTER(vp)]
+    lib.nsfr_setup.restype = i
+    for name in ("nsfr_residual", "nsfr_residual_raw"):
+        getattr(lib, name).argtypes = [vp, vp, vp, vp]
+        getattr(lib, name).restype = i
+    lib.nsfr_rk_step.argtypes = [vp, vp, d, d, ctypes.POINTER(d), vp]
+    lib.nsfr_rk_step.restype = i
+    lib.nsfr_entropy.argtypes = [vp, vp, vp, vp]
+    lib.nsfr_entropy.restype = i
+    lib.nsfr_vjp.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.nsfr_vjp.restype = i
+    lib.nsfr_node_coords.argtypes = [vp, vp, vp]
+    lib.nsfr_node_coords.restype = i
+    lib.nsfr_get_metrics.argtypes = [vp, vp, vp, vp, vp]
+    lib.nsfr_get_metrics.restype = i
+    lib.nsfr_set_metrics.argtypes = [vp, vp, vp, vp, vp]
+    lib.nsfr_set_metrics.restype = i
+    lib.nsfr_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    lib.nsfr_info.restype = i
+    lib.nsfr_check.argtypes = [vp]
+    lib.nsfr_check.restype = i
+    lib.nsfr_profile.argtypes = [vp, i]
+    lib.nsfr_profile.restype = i
+    lib.nsfr_profile_read.argtypes = [vp, vp, vp]
+    lib.nsfr_profile_read.restype = i
+    lib.nsfr_kernel_launches.argtypes = [vp]
+    lib.nsfr_kernel_launches.restype = ctypes.c_longlong
+    lib.nsfr_last_error.argtypes = [vp]
+    lib.nsfr_last_error.restype = ctypes.c_char_p
+    lib.nsfr_destroy.argtypes = [vp]
+    lib.nsfr_destroy.restype = None
+    return lib
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = load_library()
+    return _LIB
+
+
+def _ptr(x):
+    """Address of a torch tensor (device or host) or a C-contiguous numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"] or x.dtype != np.float64:
+            raise ValueError("numpy buffers must be C-contiguous float64")
+        return x.ctypes.data
+    if not x.is_contiguous() or str(x.dtype) != "torch.float64":
+        raise ValueError("tensors must be contiguous float64")
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # pragma: no cover
+        pass
+    return None
+
+
+class Solver:
+    """One NSFR-EC discretisation (mesh, p, c, fluxes, precision) on the current device."""
+
+    def __init__(self, grid_nodes, shape, p, p_geo=None, c=0.0, face_flux="ec", gamma=1.4,
+                 precision="fp64"):
+        self._lib = lib()
+        nx, ny, nz = shape
+        pg = p if p_geo is None else p_geo
+        self.shape, self.p, self.p_geo, self.n = tuple(shape), p, pg, p + 1
+        self.nv = self.n ** 3
+        self.n_el = nx * ny * nz
+        self.c, self.gamma, self.face_flux, self.precision = c, gamma, face_flux, precision
+        self._keep = grid_nodes
+        h = ctypes.c_void_p()
+        st = self._lib.nsfr_setup(_ptr(grid_nodes), nx, ny, nz, pg, p, float(c), 0, FACE_FLUX[face_flux],
+                                  float(gamma), PRECISION[precision], ctypes.byref(h))
+        if st != NSFR_OK:
+            raise NSFRError(st, "nsfr_setup failed")
+        self._h = h
+
+    # -- helpers -----------------------------------------------------------
+    def _check(self, st, what):
+        if st != NSFR_OK:
+            msg = self._lib.nsfr_last_error(self._h).decode()
+            raise NSFRError(st, f"{what}: {msg}")
+
+    @property
+    def state_shape(self):
+        return (self.n_el, 5, self.nv)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.nsfr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- the ABI calls --------------------------------------------------------
+    def residual(self, u, dudt, stream=None):
+        self._check(self._lib.nsfr_residual(self._h, _ptr(u), _ptr(dudt), _stream(stream)), "nsfr_residual")
+        return dudt
+
+    def residual_raw(self, u, R, stream=None):
+        self._check(self._lib.nsfr_residual_raw(self._h, _ptr(u), _ptr(R), _stream(stream)), "nsfr_residual_raw")
+        return R
+
+    def rk_step(self, u, cfl=0.1, dt=0.0, stream=None):
+        used = ctypes.c_double(0.0)
+        self._check(self._lib.nsfr_rk_step(self._h, _ptr(u), float(cfl), float(dt), ctypes.byref(used),
+                                           _stream(stream)), "nsfr_rk_step")
+        return used.value
+
+    def entropy(self, u, stream=None):
+        out = np.zeros(14)
+        self._check(self._lib.nsfr_entropy(self._h, _ptr(u), out.ctypes.data, _stream(stream)), "nsfr_entropy")
+        return {"entropy": out[0], "entropy_rate": out[1], "entropy_rate_scale": out[2],
+                "Q": out[3:8].copy(), "kinetic_energy": out[8], "sum_R": out[9:14].copy()}
+
+    def vjp(self, u, dudt_bar, u_bar, x_bar=None, stream=None):
+        self._check(self._lib.nsfr_vjp(self._h, _ptr(u), _ptr(dudt_bar), _ptr(u_bar), _ptr(x_bar),
+                                       _stream(stream)), "nsfr_vjp")
+
+    def node_coords(self, out=None, stream=None):
+        if out is None:
+            out = np.zeros((self.n_el, 3, self.nv))
+        self._check(self._lib.nsfr_node_coords(self._h, _ptr(out), _stream(stream)), "nsfr_node_coords")
+        return out
+
+    def metrics(self, stream=None):
+        C = np.zeros((self.n_el, 9, self.nv))
+        J = np.zeros((self.n_el, self.nv))
+        Cf = np.zeros((self.n_el, 3, 3, self.n ** 2))
+        self._check(self._lib.nsfr_get_metrics(self._h, _ptr(C), _ptr(J), _ptr(Cf), _stream(stream)),
+                    "nsfr_get_metrics")
+        return C, J, Cf
+
+    def set_metrics(self, C, J, Cf, stream=None):
+        """Use caller-supplied metric terms (layouts as ``metrics``)."""
+        C, J, Cf = (np.ascontiguousarray(x, dtype=np.float64) if isinstance(x, np.ndarray) else x
+                    for x in (C, J, Cf))
+        self._check(self._lib.nsfr_set_metrics(self._h, _ptr(C), _ptr(J), _ptr(Cf), _stream(stream)),
+                    "nsfr_set_metrics")
+
+    def check(self):
+        self._check(self._lib.nsfr_check(self._h), "nsfr_check")
+
+    def profile(self, on=True):
+        self._check(self._lib.nsfr_profile(self._h, 1 if on else 0), "nsfr_profile")
+
+    def profile_read(self):
+        ms = np.zeros(len(KERNELS))
+        cnt = np.zeros(len(KERNELS), dtype=np.int64)
+        self._check(self._lib.nsfr_profile_read(self._h, ms.ctypes.data, cnt.ctypes.data), "nsfr_profile_read")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNELS) if cnt[i]}
+
+    def kernel_launches(self):
+        return int(self._lib.nsfr_kernel_launches(self._h))

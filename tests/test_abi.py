@@ -1,0 +1,53 @@
+"""CPU-side checks of the C ABI: the library loads and exports every declared symbol,
+and argument validation needs no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "nsfr.h")).read()
+    return sorted(set(re.findall(r"\b(nsfr_[a-z_]+)\s*\(", text)))
+
+
+def test_header_and_binding_agree():
+    from paper_2312_07725_gb300 import nsfr
+    assert declared_symbols() == sorted(nsfr.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2312_07725_gb300 import nsfr
+    if not os.path.exists(nsfr.LIB_PATH):
+        from paper_2312_07725_gb300 import build
+        build.build()
+    lib = ctypes.CDLL(nsfr.LIB_PATH)
+    for s in declared_symbols():
+        assert hasattr(lib, s), s
+
+
+def test_setup_rejects_bad_arguments_without_touching_a_gpu():
+    from paper_2312_07725_gb300 import nsfr
+    lib = nsfr.lib()
+    h = ctypes.c_void_p()
+    buf = (ctypes.c_double * 24)()
+    # p out of range, zero elements, p_geo > p, gamma <= 1, negative c, unknown flux
+    bad = [(1, 1, 1, 1, 9, 0.0, 0, 1.4, 0), (0, 1, 1, 1, 1, 0.0, 0, 1.4, 0), (1, 1, 1, 3, 2, 0.0, 0, 1.4, 0),
+           (1, 1, 1, 1, 1, 0.0, 0, 1.0, 0), (1, 1, 1, 1, 1, -1.0, 0, 1.4, 0), (1, 1, 1, 1, 1, 0.0, 7, 1.4, 0)]
+    for nx, ny, nz, pg, p, c, ff, g, prec in bad:
+        st = lib.nsfr_setup(ctypes.cast(buf, ctypes.c_void_p), nx, ny, nz, pg, p, c, 0, ff, g, prec, ctypes.byref(h))
+        assert st == -1
+        assert not h.value
+    assert lib.nsfr_setup(None, 1, 1, 1, 1, 1, 0.0, 0, 0, 1.4, 0, ctypes.byref(h)) == -1
+    assert lib.nsfr_residual(None, None, None, None) == -1
+    assert lib.nsfr_last_error(None) == b"NULL context"
+    lib.nsfr_destroy(None)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_2312_07725_gb300 import nsfr
+    with pytest.raises(ImportError):
+        nsfr.load_library(str(tmp_path / "libnsfr.so"))

@@ -1,0 +1,173 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+Bar (FP64 path): relative L2 error over all five variables <= 1e-12 for the
+residual R, for du/dt and for one RK4 step, and for the metric terms.
+
+The residual is ill-conditioned: the fluxes are O(p |J a|) while R is their
+small divergence, so a 1 ulp change of the state moves du/dt by up to ~4e-13
+and a 1e-14 relative change of the metric by up to ~3e-12 (measured with the
+oracle alone).  The residual comparisons therefore give the library the
+oracle's own metric terms (``nsfr_set_metrics``), and the library's metric
+construction is compared with the oracle's separately.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from tests._pairs import oracle_metrics_abi, oracle_problem, rel_l2, state_for  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def solver_for(ctrl, shape, P, precision="fp64"):
+    from paper_2312_07725_gb300 import Solver
+    return Solver(np.ascontiguousarray(ctrl), shape, P.p, p_geo=P.p_geo, c=P.ops.c, face_flux=P.face_flux,
+                  gamma=P.gamma, precision=precision)
+
+
+def to_dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 7])
+def test_metrics_match_oracle(p):
+    shape = (3, 2, 2)
+    ctrl, P = oracle_problem(shape, p)
+    S = solver_for(ctrl, shape, P)
+    C, J, Cf = S.metrics()
+    ne, n = P.mesh.n_el, P.n
+    Co = np.moveaxis(P.C.reshape(3, 3, ne, n ** 3), 2, 0).reshape(ne, 9, n ** 3)
+    Jo = P.J.reshape(ne, n ** 3)
+    Cfo = np.moveaxis(P.geo["Cf"].reshape(3, 3, ne, n * n), 2, 0)
+    assert rel_l2(C, Co) < TOL
+    assert rel_l2(J, Jo) < TOL
+    assert rel_l2(Cf, Cfo) < TOL
+    xyz = S.node_coords()
+    assert np.abs(xyz - P.node_coords()).max() < 1e-13 * np.pi
+
+
+CASES = [
+    # p, shape, c, face flux, mesh
+    (1, (2, 3, 2), "dg", "ec", "tgv"),
+    (2, (3, 2, 5), "hu", "ec", "tgv"),      # 30 elements: ragged last CTA
+    (3, (4, 4, 4), "dg", "ec", "tgv"),      # the small TGV configuration
+    (3, (3, 3, 2), "hu", "ec_roe", "unit"),
+    (4, (3, 2, 3), "hu", "ec", "tgv"),
+    (4, (2, 3, 2), "dg", "ec_roe", "paper"),
+    (5, (2, 2, 3), "hu", "ec", "tgv"),
+    (6, (2, 2, 2), "dg", "ec_roe", "unit"),
+    (7, (2, 1, 2), "hu", "ec", "tgv"),
+    (3, (1, 1, 1), "hu", "ec", "tgv"),      # a single periodic element
+]
+
+
+@pytest.mark.parametrize("p,shape,c_kind,face_flux,kind", CASES)
+def test_residual_and_dudt_match_oracle(p, shape, c_kind, face_flux, kind):
+    ctrl, P = oracle_problem(shape, p, c_kind, face_flux, kind)
+    S = solver_for(ctrl, shape, P)
+    S.set_metrics(*oracle_metrics_abi(P))
+    u = state_for(P, kind)
+    U = P.to_internal(u)
+    R_ref = P.to_abi(P.residual(U))
+    D_ref = P.to_abi(P.dudt(U))
+    ud = to_dev(u)
+    R = torch.empty_like(ud)
+    D = torch.empty_like(ud)
+    S.residual_raw(ud, R)
+    S.residual(ud, D)
+    torch.cuda.synchronize()
+    assert rel_l2(R.cpu().numpy(), R_ref) < TOL
+    assert rel_l2(D.cpu().numpy(), D_ref) < TOL
+    # host buffers through the same entry point give the same numbers
+    Dh = np.zeros_like(u)
+    S.residual(u, Dh)
+    assert np.array_equal(Dh, D.cpu().numpy())
+
+
+@pytest.mark.parametrize("p,c_kind,face_flux", [(3, "dg", "ec"), (4, "hu", "ec_roe")])
+def test_rk4_step_matches_oracle(p, c_kind, face_flux):
+    shape = (3, 2, 2)
+    ctrl, P = oracle_problem(shape, p, c_kind, face_flux)
+    S = solver_for(ctrl, shape, P)
+    S.set_metrics(*oracle_metrics_abi(P))
+    u = state_for(P)
+    dt = 2e-3
+    u1_ref = P.rk4_step_abi(u, dt)
+    ud = to_dev(u)
+    S.rk_step(ud, dt=dt)
+    torch.cuda.synchronize()
+    du_ref = u1_ref - u
+    # u1 - u is formed from rounded u1 (|u| ~ 180 in energy): add that rounding to the bar
+    eps = np.finfo(np.float64).eps
+    bar = TOL + 4 * eps * np.linalg.norm(u1_ref) / np.linalg.norm(du_ref)
+    assert rel_l2(ud.cpu().numpy() - u, du_ref) < bar
+    # CFL step: dt from the maximum wave speed
+    ud = to_dev(u)
+    dt_used = S.rk_step(ud, cfl=0.1)
+    dx = 2 * np.pi / (3 * (p + 1))
+    assert abs(dt_used - P.cfl_dt(P.to_internal(u), 0.1, dx)) < 1e-14 * dt_used
+
+
+@pytest.mark.parametrize("N", [8, 16])
+def test_metrics_and_free_stream_floor_on_finer_meshes(N):
+    """Metric terms agree with the oracle's on a finer mesh, and the free-stream
+    residual of the library stays at the oracle's own round-off level."""
+    import workloads as wl
+    from oracle.operators1d import c_hu
+    from oracle.problem import Problem
+    p = 4
+    ctrl = wl.tgv_mesh(N, p)
+    P = Problem(ctrl, (N,) * 3, p, c=c_hu(p))
+    S = solver_for(ctrl, (N,) * 3, P)
+    C, J, Cf = S.metrics()
+    Co, Jo, Cfo = oracle_metrics_abi(P)
+    assert rel_l2(C, Co) < TOL and rel_l2(J, Jo) < TOL and rel_l2(Cf, Cfo) < TOL
+    fs = np.ascontiguousarray(wl.free_stream_state(P.node_coords()))
+    R = np.zeros_like(fs)
+    S.residual_raw(fs, R)
+    R_or = P.residual_abi(fs)
+    f_scale = np.abs(wl.free_stream_state(P.node_coords())).max() * np.abs(Co).max()
+    assert np.abs(R).max() < 1e-13 * f_scale
+    assert np.abs(R).max() < 10 * max(np.abs(R_or).max(), 1e-18)
+
+
+def test_diagnostics_match_oracle():
+    p, shape = 4, (3, 2, 2)
+    ctrl, P = oracle_problem(shape, p, "hu", "ec")
+    S = solver_for(ctrl, shape, P)
+    S.set_metrics(*oracle_metrics_abi(P))
+    u = state_for(P)
+    g = S.entropy(to_dev(u))
+    o = P.diagnostics(P.to_internal(u))
+    assert abs(g["entropy"] - o["entropy"]) < 1e-13 * abs(o["entropy"])
+    assert abs(g["kinetic_energy"] - o["kinetic_energy"]) < 1e-13 * abs(o["kinetic_energy"])
+    for k in range(5):
+        assert abs(g["Q"][k] - o["Q"][k]) < 1e-13 * o["Q_abs"][k]
+    # EC: the semi-discrete entropy rate vanishes (paper: O(1e-13))
+    assert abs(g["entropy_rate"]) < 1e-13 * g["entropy_rate_scale"]
+    assert abs(g["entropy_rate_scale"] - o["entropy_rate_scale"]) < 1e-10 * o["entropy_rate_scale"]
+
+
+def test_errors_are_reported_not_raised():
+    from paper_2312_07725_gb300 import NSFRError
+    shape = (2, 2, 2)
+    ctrl, P = oracle_problem(shape, 3)
+    S = solver_for(ctrl, shape, P)
+    u = state_for(P)
+    bad = u.copy()
+    bad[3, 4, 7] = -1.0  # negative total energy: p < 0
+    D = torch.empty(u.shape, dtype=torch.float64, device="cuda")
+    S.residual(to_dev(bad), D)
+    with pytest.raises(NSFRError) as ei:
+        S.check()
+    assert "NONPHYSICAL" in str(ei.value)
+    S.check()  # the flag was cleared
+    # a tangled mesh is rejected at set-up
+    from paper_2312_07725_gb300 import Solver
+    tangled = ctrl.copy()
+    tangled[0, :, 0] *= -1.0
+    with pytest.raises(NSFRError) as ei:
+        Solver(np.ascontiguousarray(tangled), shape, 3)
+    assert "MESH" in str(ei.value)
