@@ -210,6 +210,38 @@ nsfr_status nsfr_profile(nsfr_ctx* ctx, int on);
  */
 nsfr_status nsfr_profile_read(nsfr_ctx* ctx, double* ms, long long* count);
 
+/*
+ * nsfr_residual_static -- du/dt exactly as nsfr_residual computes it, for
+ * callers that must not allocate device memory: code running under a memory
+ * manager that owns the whole device (a framework's caching allocator, an
+ * application with a fixed memory budget) or code that cannot afford the
+ * implicit device synchronisation of cudaMalloc/cudaFree.  It needs no
+ * context and calls no cudaMalloc, cudaFree or other allocating routine; the
+ * paper has no counterpart of this call.
+ *   u     device [N_e][5][n^3] state
+ *   C     device [N_e][9][n^3] metric rows, J device [N_e][n^3] Jacobians,
+ *   Cf    device [N_e][3][3][n^2] shared face rows (layouts of
+ *         nsfr_get_metrics; e.g. copied once from a context)
+ *   nx, ny, nz, p, c, face_flux, gamma   as in nsfr_setup (FP64 only)
+ *   dudt  device [N_e][5][n^3] output
+ * Its working memory (face states, 1/(wJ), an error word) is a fixed
+ * 16 MiB array inside the library (NSFR_STATIC_SCRATCH_BYTES), which every
+ * GPU that loads the library keeps until the process exits.  A problem
+ * needing more than that, 256 + 8 N_e (48 n^2 + 2 n^3) bytes, is rejected
+ * with NSFR_ERR_ARG before anything runs.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array and the last call's contents stay in it; the error word is
+ * cleared at the start of every call.  Calls that overlap on the GPU (other
+ * streams, other threads) race on the array: serialise them.  The call
+ * synchronises the stream to read the error word (NSFR_ERR_NONPHYSICAL,
+ * NSFR_ERR_MESH for J <= 0).
+ */
+#define NSFR_STATIC_SCRATCH_BYTES (16u << 20)
+nsfr_status nsfr_residual_static(const double* u, const double* C, const double* J, const double* Cf, int nx,
+                                 int ny, int nz, int p, double c, int face_flux, double gamma, double* dudt,
+                                 void* stream);
+
 /* nsfr_kernel_launches -- kernels this context has launched so far. */
 long long nsfr_kernel_launches(const nsfr_ctx* ctx);
 

@@ -366,3 +366,77 @@ cudaError_t nsfr_launch_volume(nsfr_ctx* ctx, const double* u, double* out, int 
   }
   return cudaErrorInvalidValue;
 }
+
+// ---------------------------------------------------------------------------
+// nsfr_residual_static: the same kernels on caller buffers, with the working
+// memory in a fixed device array of this file instead of allocations.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+static __device__ __align__(256) unsigned char g_static_scratch[NSFR_STATIC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_static_mu;
+void* g_static_addr[256] = {nullptr};  // device address of g_static_scratch, per device ordinal
+}  // namespace
+
+extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, const double* J, const double* Cf,
+                                            int nx, int ny, int nz, int p, double c, int face_flux, double gamma,
+                                            double* dudt, void* stream) {
+  if (!u || !C || !J || !Cf || !dudt || nx < 1 || ny < 1 || nz < 1 || p < 1 || p > 7 || !(gamma > 1.0) ||
+      !(c >= 0.0) || (face_flux != NSFR_FACE_EC && face_flux != NSFR_FACE_EC_ROE))
+    return NSFR_ERR_ARG;
+  const size_t ne = (size_t)nx * ny * nz, n = p + 1, nv = n * n * n, nfp = n * n;
+  const size_t face_bytes = ne * 6 * NSFR_NFIELD * nfp * sizeof(double);
+  const size_t jac_bytes = ne * nv * sizeof(double);
+  const size_t need = 256 + face_bytes + 2 * jac_bytes;  // error word (padded), faces, 1/(wJ), wJ
+  if (need > NSFR_STATIC_SCRATCH_BYTES || ne > (size_t)0x7fffffff) return NSFR_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return NSFR_ERR_CUDA;
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+      void* addr = nullptr;
+      if (cudaGetSymbolAddress(&addr, g_static_scratch) != cudaSuccess || !addr) return NSFR_ERR_CUDA;
+      g_static_addr[dev] = addr;
+    }
+    base = (unsigned char*)g_static_addr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  nsfr_ctx ctx;  // a view of caller buffers and the fixed array; owns nothing
+  ctx.nx = nx;
+  ctx.ny = ny;
+  ctx.nz = nz;
+  ctx.ne = (int)ne;
+  ctx.p = p;
+  ctx.n = (int)n;
+  ctx.pg = p;
+  ctx.q = (int)n;
+  ctx.nv = (int)nv;
+  ctx.nfp = (int)nfp;
+  ctx.c = c;
+  ctx.gamma = gamma;
+  ctx.vol_flux = NSFR_FLUX_CHANDRASHEKAR;
+  ctx.face_flux = face_flux;
+  ctx.precision = NSFR_FP64;
+  ctx.device = dev;
+  nsfr_build_ops(p, p, c, gamma, &ctx.ops, &ctx.gops);
+  ctx.flag = (int*)base;
+  ctx.face = (double*)(base + 256);
+  ctx.invwj = (double*)(base + 256 + face_bytes);
+  ctx.wj = (double*)(base + 256 + face_bytes + jac_bytes);
+  ctx.metric = const_cast<double*>(C);
+  ctx.J = const_cast<double*>(J);
+  ctx.nfp_plus = const_cast<double*>(Cf);
+  if (cudaMemsetAsync(ctx.flag, 0, sizeof(int), s) != cudaSuccess) return NSFR_ERR_CUDA;
+  if (nsfr_launch_jacobian_derived(&ctx, s) != cudaSuccess) return NSFR_ERR_CUDA;
+  if (nsfr_launch_face_states(&ctx, u, s) != cudaSuccess) return NSFR_ERR_CUDA;
+  if (nsfr_launch_volume(&ctx, u, dudt, EPI_DUDT, nullptr, s) != cudaSuccess) return NSFR_ERR_CUDA;
+  int flag = 0;
+  if (cudaMemcpyAsync(&flag, ctx.flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return NSFR_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return NSFR_ERR_CUDA;
+  if (flag & 2) return NSFR_ERR_MESH;
+  if (flag & 1) return NSFR_ERR_NONPHYSICAL;
+  return NSFR_OK;
+}

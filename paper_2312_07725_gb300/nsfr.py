@@ -26,7 +26,7 @@ PRECISION = {"fp64": 0, "fp32_bulk": 1}
 # every symbol include/nsfr.h declares
 EXPORTS = ["nsfr_setup", "nsfr_residual", "nsfr_residual_raw", "nsfr_rk_step", "nsfr_entropy",
            "nsfr_vjp", "nsfr_node_coords", "nsfr_get_metrics", "nsfr_set_metrics", "nsfr_info", "nsfr_check",
-           "nsfr_profile", "nsfr_profile_read", "nsfr_kernel_launches", "nsfr_last_error", "nsfr_destroy"]
+           "nsfr_profile", "nsfr_profile_read", "nsfr_residual_static", "nsfr_kernel_launches", "nsfr_last_error", "nsfr_destroy"]
 KERNELS = ["metrics", "face_states", "volume", "max_wavespeed", "diagnostics", "vjp_face", "vjp_volume",
            "vjp_metrics"]
 
@@ -67,6 +67,8 @@ def load_library(path=LIB_PATH):
     lib.nsfr_profile.restype = i
     lib.nsfr_profile_read.argtypes = [vp, vp, vp]
     lib.nsfr_profile_read.restype = i
+    lib.nsfr_residual_static.argtypes = [vp, vp, vp, vp, i, i, i, i, d, i, d, vp, vp]
+    lib.nsfr_residual_static.restype = i
     lib.nsfr_kernel_launches.argtypes = [vp]
     lib.nsfr_kernel_launches.restype = ctypes.c_longlong
     lib.nsfr_last_error.argtypes = [vp]
@@ -109,6 +111,18 @@ def _stream(stream):
     except Exception:  # pragma: no cover
         pass
     return None
+
+
+def residual_static(u, C, J, Cf, shape, p, c=0.0, face_flux="ec", gamma=1.4, dudt=None, stream=None):
+    """du/dt through nsfr_residual_static: no context and no device allocation by the
+    library (its working memory is a fixed array inside libnsfr.so).  All buffers
+    are caller-owned device tensors; returns ``dudt``."""
+    nx, ny, nz = shape
+    st = lib().nsfr_residual_static(_ptr(u), _ptr(C), _ptr(J), _ptr(Cf), nx, ny, nz, p, float(c),
+                                    FACE_FLUX[face_flux], float(gamma), _ptr(dudt), _stream(stream))
+    if st != NSFR_OK:
+        raise NSFRError(st, "nsfr_residual_static failed")
+    return dudt
 
 
 class Solver:
