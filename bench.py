@@ -36,11 +36,11 @@ sys.path.insert(0, ROOT)
 
 import workloads as wl  # noqa: E402
 
-# algorithmic FP64 work (add/mul/fma/div/sqrt/log/exp each counted once) of the
-# volume kernel per two-point flux and per hybrid-term accumulation; see the
-# roofline section of the design notes for the breakdown
-OPS_PER_FLUX = 48
-OPS_PER_PAIR_ACC = 10
+# Algorithmic FP64 flops of the volume kernel (an FMA counts 2, a reciprocal or
+# division 1): per two-point flux evaluation (the Chandrashekar flux with its
+# two log means) and per accumulation of one flux into two residual entries
+FLOPS_PER_FLUX = 55
+FLOPS_PER_ACC = 20
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -208,45 +208,45 @@ def run_reference(args, rank, ws, dist):
 # --------------------------------------------------------------------------
 # our implementation
 # --------------------------------------------------------------------------
-def volume_kernel_ops(n_el, p):
+def volume_kernel_flops(n_el, p, has_k=True):
+    """Algorithmic FP64 flops of one volume-kernel launch over n_el elements."""
     n = p + 1
-    fluxes_vol = 3 * n * n * n * (n - 1) // 2
-    fluxes_hyb = 6 * n ** 3
-    fluxes_face = 6 * n * n
-    per_el = (fluxes_vol + fluxes_hyb + fluxes_face) * OPS_PER_FLUX + (fluxes_vol + fluxes_hyb) * OPS_PER_PAIR_ACC
-    return per_el * n_el, {"volume_pairs": fluxes_vol, "hybrid": fluxes_hyb, "face": fluxes_face}
+    fluxes_vol = 3 * n * n * n * (n - 1) // 2      # unordered pairs on every line
+    fluxes_hyb = 6 * n ** 3                         # volume node x face node of its line
+    fluxes_face = 6 * n * n                         # f* on the element's six faces
+    per_el = (fluxes_vol + fluxes_hyb + fluxes_face) * FLOPS_PER_FLUX + (fluxes_vol + fluxes_hyb) * FLOPS_PER_ACC
+    per_el += 6 * n * n * (5 + 10 * n)              # face term combination, both faces of each line
+    per_el += 5 * n ** 3                            # 1/(w J)
+    if has_k:
+        per_el += 6 * 5 * n * n * 4 * n             # rank-one Pi~ / Pi~^T sweeps
+    return per_el * n_el, {"volume_pairs": fluxes_vol, "hybrid": fluxes_hyb, "face": fluxes_face,
+                           "flops_per_element": per_el}
 
 
-def run_ours(args, rank, ws, dist):
+def measure(args, ctrl, u0, precision, dist, ws, steps):
+    """Time `steps` RK4 steps of one precision mode, plus its e2e variant."""
     import torch
     from paper_2312_07725_gb300 import Solver
 
-    dev = torch.cuda.current_device()
-    cfg = workload_config(args)
     p, N = args.p, args.n_el
-    ctrl = wl.tgv_mesh(N, p)
-    S = Solver(ctrl, (N, N, N), p, c=cfg["c"], face_flux="ec", precision=args.precision)
-    del ctrl
-    xyz = S.node_coords()
-    u0 = np.ascontiguousarray(wl.tgv_state(xyz))
-    del xyz
+    c = c_value(p)
+    S = Solver(ctrl, (N, N, N), p, c=c, face_flux="ec", precision=precision)
     u = torch.from_numpy(u0).cuda()
     stream = torch.cuda.current_stream()
-    nodes = cfg["nodes"]
-
+    nodes = N ** 3 * (p + 1) ** 3
     for _ in range(args.warmup):
         S.rk_step(u, cfl=args.cfl)
     torch.cuda.synchronize()
     barrier(dist)
     launches0 = S.kernel_launches()
     S.profile(True)
-    clocks = ClockSampler(dev)
+    clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         S.rk_step(u, cfl=args.cfl)
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -254,63 +254,93 @@ def run_ours(args, rank, ws, dist):
     S.profile(False)
     prof = S.profile_read()
     launches = S.kernel_launches() - launches0
-    ms = ev0.elapsed_time(ev1)
-    ms = max_over_ranks(dist, ms)
-    stages = 4 * args.steps
-    value = nodes * stages * ws / (ms / 1e3) / 1e9
-
+    ms = max_over_ranks(dist, ev0.elapsed_time(ev1))
+    value = nodes * 4 * steps * ws / (ms / 1e3) / 1e9
     # e2e: the same RK4 step through the C ABI with pinned host buffers
     uh = torch.from_numpy(u0).pin_memory()
-    S.rk_step(uh.numpy(), cfl=args.cfl)  # warm the staging buffers
+    S.rk_step(uh.numpy(), cfl=args.cfl)  # sizes the staging buffers
     barrier(dist)
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         S.rk_step(uh.numpy(), cfl=args.cfl)
     e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
-    e2e_value = nodes * 4 * args.e2e_steps * ws / e2e_s / 1e9
+    e2e = nodes * 4 * args.e2e_steps * ws / e2e_s / 1e9
+    # one du/dt of the initial state, to compare the two precision modes
+    D = torch.empty_like(u)
+    S.residual(torch.from_numpy(u0).cuda(), D)
+    torch.cuda.synchronize()
+    kern = {k: {"ms_total": v[0], "launches": v[1], "ms_avg": v[0] / v[1]} for k, v in prof.items()}
+    res = {"value": value, "ms_per_step": ms / steps, "e2e": e2e, "gpu_launches": launches, "kernels": kern,
+           "clocks": clk, "dudt": D.cpu().numpy()}
+    S.close()
+    del u, D
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_ours(args, rank, ws, dist):
+    cfg = workload_config(args)
+    p, N = args.p, args.n_el
+    ctrl = wl.tgv_mesh(N, p)
+    from paper_2312_07725_gb300 import Solver
+    S0 = Solver(ctrl, (N, N, N), p, c=cfg["c"])
+    xyz = S0.node_coords()
+    S0.close()
+    u0 = np.ascontiguousarray(wl.tgv_state(xyz))
+    del xyz
     state_bytes = u0.nbytes
 
-    # roofline of the dominant kernel (the volume/hybrid/surface kernel)
-    vol_ms, vol_n = prof.get("volume", (0.0, 0))
-    ops, counts = volume_kernel_ops(N ** 3, p)
-    achieved = ops / (vol_ms / vol_n / 1e3) / 1e12 if vol_n else None
-    peak, peak_src = fp64_peak(clk)
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
-            "kernel": "volume_kernel (FP64 pipe)", "peak_source": peak_src,
-            "ops_per_launch": ops, "flux_evals_per_element": counts}
-    kern = {k: {"ms_total": v[0], "launches": v[1], "ms_avg": v[0] / v[1]} for k, v in prof.items()}
+    m64 = measure(args, ctrl, u0, "fp64", dist, ws, args.steps)
+    m32 = measure(args, ctrl, u0, "fp32_bulk", dist, ws, args.steps)
+    d64, d32 = m64.pop("dudt"), m32.pop("dudt")
+    bulk_err = float(np.linalg.norm((d32 - d64).ravel()) / np.linalg.norm(d64.ravel()))
+    del d64, d32
 
+    clk = m64["clocks"]
+    vol_ms, vol_n = m64["kernels"]["volume"]["ms_total"], m64["kernels"]["volume"]["launches"]
+    flops, counts = volume_kernel_flops(N ** 3, p, cfg["c"] != 0.0)
+    achieved = flops / (vol_ms / vol_n / 1e3) / 1e12
+    peak, peak_src = fp64_peak(clk)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "volume_kernel<5> (FP64 pipe)", "peak_source": peak_src,
+            "peak_measured_dfma_probe": FP64_MEASURED_TFLOPS, "frac_of_measured": achieved / FP64_MEASURED_TFLOPS,
+            "flops_per_launch": flops, "flux_evals_per_element": counts}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         val, cores, sample = oracle_sample_rate(p)
         cpu = {"value": val, "unit": "GDOF/s", "cores": cores, "kind": "oracle", "sample": sample}
     if rank == 0:
-        line = {"metric": "NSFR-EC residual GDOF/s per RK stage", "value": value, "unit": "GDOF/s",
-                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if args.precision == "fp64" else "f32+f64",
-                "precision_mode": args.precision, "data": "synthetic", "config": cfg,
-                "gdof_per_s_x5_components": 5 * value,
-                "e2e": {"value": e2e_value, "unit": "GDOF/s", "h2d_bytes_per_step": state_bytes,
+        line = {"metric": "NSFR-EC residual GDOF/s per RK stage", "value": m64["value"], "unit": "GDOF/s",
+                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": m64["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": cfg, "gdof_per_s_x5_components": 5 * m64["value"],
+                "e2e": {"value": m64["e2e"], "unit": "GDOF/s", "h2d_bytes_per_step": state_bytes,
                         "d2h_bytes_per_step": state_bytes},
-                "gpu_launches": launches, "kernels": kern, "roofline": roof, "clocks": clk,
-                "cpu_baseline": cpu}
+                "gpu_launches": m64["gpu_launches"], "kernels": m64["kernels"], "roofline": roof, "clocks": clk,
+                "cpu_baseline": cpu,
+                "fp32_bulk": {"value": m32["value"], "unit": "GDOF/s", "ms_per_step": m32["ms_per_step"],
+                              "speedup_vs_fp64": m32["value"] / m64["value"],
+                              "dudt_rel_l2_vs_fp64_path": bulk_err,
+                              "e2e": {"value": m32["e2e"], "unit": "GDOF/s", "h2d_bytes_per_step": state_bytes,
+                                      "d2h_bytes_per_step": state_bytes},
+                              "gpu_launches": m32["gpu_launches"], "kernels": m32["kernels"],
+                              "clocks": m32["clocks"], "dtype": "f32 bulk, f64 log means/state"}}
         print(json.dumps(line), flush=True)
 
 
 def fp64_peak(clk):
     """FP64 FMA peak in TFLOP/s: SMs x FP64 FMA lanes per SM per clock x 2 x clock.
 
-    The lane count comes from the design notes' measurement of this part; the
-    clock is the median SM clock sampled during the timed region (max clock if
-    the sampler was unavailable)."""
+    The lane count is the FP64 issue rate ncu reports for this part
+    (sm__sass_thread_inst_executed_op_dfma_pred_on peak, 2 per SM per cycle);
+    the clock is the median SM clock sampled during the timed region."""
     lanes = FP64_LANES_PER_SM
     mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
     return 152 * lanes * 2 * mhz * 1e6 / 1e12, f"152 SMs x {lanes} FP64 FMA/clk/SM x 2 x {mhz:.0f} MHz"
 
 
-FP64_LANES_PER_SM = 2.0  # nominal 1.25 TFLOP/s at 2070 MHz over 152 SMs
+FP64_LANES_PER_SM = 2.0  # ncu: 2 DFMA thread-instructions per SM per cycle (nominal 1.26 TFLOP/s at 2070 MHz)
+FP64_MEASURED_TFLOPS = 1.008  # DFMA-chain microbenchmark on this pool's GB300 (0.504 T DFMA/s)
 
 
 def main():

@@ -227,7 +227,7 @@ nsfr_status nsfr_profile_read(nsfr_ctx* ctx, double* ms, long long* count);
  * Its working memory (face states, 1/(wJ), an error word) is a fixed
  * 16 MiB array inside the library (NSFR_STATIC_SCRATCH_BYTES), which every
  * GPU that loads the library keeps until the process exits.  A problem
- * needing more than that, 256 + 8 N_e (48 n^2 + 2 n^3) bytes, is rejected
+ * needing more than that, 256 + 8 N_e (48 n^2 + 4 n^3) bytes, is rejected
  * with NSFR_ERR_ARG before anything runs.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture.  All calls share

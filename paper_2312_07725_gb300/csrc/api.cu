@@ -55,7 +55,7 @@ void prof_free(nsfr_ctx* c) {
 }
 
 void free_all(nsfr_ctx* c) {
-  double* dbl[] = {c->ctrl, c->metric, c->J, c->invwj, c->wj, c->nfp_plus, c->xyz, c->face,
+  double* dbl[] = {c->ctrl, c->metric, c->J, c->invwj, c->wj, c->nfp_plus, c->xyz, c->face, c->lnrec,
                    c->ustage, c->acc, c->rtmp, c->hbuf_in, c->hbuf_out, c->red};
   for (double* p : dbl)
     if (p) cudaFree(p);
@@ -91,9 +91,15 @@ nsfr_status read_flag(nsfr_ctx* ctx, cudaStream_t s) {
   return NSFR_OK;
 }
 
+cudaError_t launch_volume_any(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk,
+                              cudaStream_t s) {
+  return ctx->precision == NSFR_FP32_BULK ? nsfr_launch_volume_bulk(ctx, u, out, epi, rk, s)
+                                          : nsfr_launch_volume(ctx, u, out, epi, rk, s);
+}
+
 nsfr_status residual_device(nsfr_ctx* ctx, const double* u, double* out, int epi, cudaStream_t s) {
   CK(nsfr_launch_face_states(ctx, u, s), "face_state_kernel");
-  CK(nsfr_launch_volume(ctx, u, out, epi, nullptr, s), "volume_kernel");
+  CK(launch_volume_any(ctx, u, out, epi, nullptr, s), "volume_kernel");
   return NSFR_OK;
 }
 
@@ -151,7 +157,7 @@ nsfr_status rk_step_device(nsfr_ctx* ctx, double* u, double cfl, double dt_fixed
     rk.a_next = (st < 3) ? a[st] : 0.0;
     rk.unext = (st == 3) ? u : ctx->ustage;
     CK(nsfr_launch_face_states(ctx, in, s), "face_state_kernel");
-    CK(nsfr_launch_volume(ctx, in, nullptr, EPI_RK, &rk, s), "volume_kernel(rk)");
+    CK(launch_volume_any(ctx, in, nullptr, EPI_RK, &rk, s), "volume_kernel(rk)");
   }
   return NSFR_OK;
 }
@@ -180,7 +186,6 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
       vol_flux != NSFR_FLUX_CHANDRASHEKAR || (face_flux != NSFR_FACE_EC && face_flux != NSFR_FACE_EC_ROE) ||
       (precision != NSFR_FP64 && precision != NSFR_FP32_BULK) || !std::isfinite(c) || c < 0.0)
     return NSFR_ERR_ARG;
-  if (precision == NSFR_FP32_BULK) return NSFR_ERR_ARG;  // FP32-bulk kernels not built yet
   nsfr_ctx* ctx = new (std::nothrow) nsfr_ctx();
   if (!ctx) return NSFR_ERR_OOM;
   ctx->nx = nx;
@@ -211,7 +216,7 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
             dalloc(&ctx->J, ne * nv) == cudaSuccess && dalloc(&ctx->invwj, ne * nv) == cudaSuccess &&
             dalloc(&ctx->wj, ne * nv) == cudaSuccess && dalloc(&ctx->nfp_plus, ne * 9 * nfp) == cudaSuccess &&
             dalloc(&ctx->xyz, ne * 3 * nv) == cudaSuccess &&
-            dalloc(&ctx->face, ne * 6 * NSFR_NFIELD * nfp) == cudaSuccess &&
+            dalloc(&ctx->face, ne * 6 * NSFR_NFIELD * nfp) == cudaSuccess && dalloc(&ctx->lnrec, ne * 2 * nv) == cudaSuccess &&
             dalloc(&ctx->ustage, ne * 5 * nv) == cudaSuccess && dalloc(&ctx->acc, ne * 5 * nv) == cudaSuccess &&
             dalloc(&ctx->flag, 1) == cudaSuccess && dalloc(&ctx->umax, 1) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->flag_host, sizeof(int)) == cudaSuccess &&

@@ -1,0 +1,36 @@
+// Index helpers shared by the residual kernels.
+#pragma once
+
+namespace nsfr_k {
+
+// elements per CTA (one thread per line, 3 n^2 lines per element) chosen so
+// that a CTA has at most 8 warps, i.e. two per SM sub-partition, which lets
+// every thread keep up to 255 registers
+constexpr int epb_for(int n) { return n == 2 ? 16 : n == 3 ? 8 : n == 4 ? 4 : n == 5 ? 3 : n == 6 ? 2 : 1; }
+constexpr int threads_for(int n) { return epb_for(n) * 3 * n * n; }
+
+// neighbour of element e across face (d, side): side 0 is xi_d = -1 (periodic)
+__device__ __forceinline__ int nbr_index(int e, int d, int side, int nx, int ny, int nz) {
+  int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
+  const int st = side ? 1 : -1;
+  if (d == 0) ex = (ex + st + nx) % nx;
+  else if (d == 1) ey = (ey + st + ny) % ny;
+  else ez = (ez + st + nz) % nz;
+  return ex + nx * (ey + ny * ez);
+}
+
+// node index of line node a for line (d, l0, l1): base + a * stride
+template <int N>
+__device__ __forceinline__ void line_geometry(int d, int l0, int l1, int& base, int& stride) {
+  if (d == 0) { base = N * (l0 + N * l1); stride = 1; }
+  else if (d == 1) { base = l0 + N * N * l1; stride = N; }
+  else { base = l0 + N * l1; stride = N * N; }
+}
+
+// w_perp of node (i, j, k) for lines of direction d: the weights of the other two
+__device__ __forceinline__ double wperp_of(const double* w, int node, int n, int d) {
+  const int i = node % n, j = (node / n) % n, k = node / (n * n);
+  return d == 0 ? w[j] * w[k] : (d == 1 ? w[i] * w[k] : w[i] * w[j]);
+}
+
+}  // namespace nsfr_k

@@ -27,6 +27,21 @@ struct OpsGL {
   float wf[NSFR_MAXN];
   float tmf[NSFR_MAXN];
   float tpf[NSFR_MAXN];
+  // low parts: S1 = S1f + S1lo, t = tf + tlo as float-float constants
+  float S1lo[NSFR_MAXN * NSFR_MAXN];
+  float tmlo[NSFR_MAXN];
+  float tplo[NSFR_MAXN];
+  // Pi~1 = I - hv g^T (rank one: K1 = 2c g g^T), hv = alpha W^{-1} g
+  double gv[NSFR_MAXN];
+  double hv[NSFR_MAXN];
+  float gvf[NSFR_MAXN];
+  float hvf[NSFR_MAXN];
+  // log-mean series coefficients (Horner order c0..c3):
+  //   Gh(u) = G(u)/2 with G = f/atanh(f), F4g(u) = 2/(gamma-1) atanh(f)/f, u = f^2
+  double gh[4];
+  double f4g[4];
+  double fr2[4];  // 2 atanh(f)/f (for 1/rho_ln)
+  double inv_gm1;
 };
 
 // Operators of the metric construction (Lobatto nodes of degree p).
@@ -64,6 +79,7 @@ struct nsfr_ctx {
   float* nfp_plus32 = nullptr;
   double* xyz = nullptr;      // [ne][3][nv]
   double* face = nullptr;     // [ne][6][NSFR_NFIELD][nfp] face-state scratch
+  double* lnrec = nullptr;    // [ne][2][nv] ln rho, ln beta of the last face-state pass
   double* ustage = nullptr;   // [ne][5][nv]
   double* acc = nullptr;      // [ne][5][nv]
   double* rtmp = nullptr;     // [ne][5][nv] (diagnostics / VJP scratch)
@@ -91,8 +107,9 @@ struct nsfr_ctx {
 void nsfr_prof_begin(nsfr_ctx* ctx, int kind, cudaStream_t s);
 void nsfr_prof_end(nsfr_ctx* ctx, cudaStream_t s);
 
-// Per-node primitive record used by the flux kernels (NSFR_NFIELD doubles).
-enum { P_RHO = 0, P_U = 1, P_V = 2, P_W = 3, P_BETA = 4, P_LRHO = 5, P_LBETA = 6, P_Q2 = 7 };
+// Per-node record used by the flux kernels (NSFR_NFIELD doubles): rho, 2 beta,
+// u/2 (3), |u|^2/4, ln rho, ln beta.  The halves make arithmetic means plain sums.
+enum { P_RHO = 0, P_B2 = 1, P_UH = 2, P_QQ = 5, P_LRHO = 6, P_LBETA = 7 };
 
 // Launchers (residual.cu)
 enum { EPI_RAW = 0, EPI_DUDT = 1, EPI_RK = 2 };
@@ -109,6 +126,9 @@ struct RkArgs {
 cudaError_t nsfr_launch_face_states(nsfr_ctx* ctx, const double* u, cudaStream_t s);
 cudaError_t nsfr_launch_volume(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk,
                                cudaStream_t s);
+// residual_bulk.cu: the FP32-bulk form of nsfr_launch_volume
+cudaError_t nsfr_launch_volume_bulk(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk,
+                                    cudaStream_t s);
 // geometry.cu
 cudaError_t nsfr_launch_metrics(nsfr_ctx* ctx, cudaStream_t s);
 cudaError_t nsfr_launch_jacobian_derived(nsfr_ctx* ctx, cudaStream_t s);

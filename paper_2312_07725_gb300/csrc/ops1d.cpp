@@ -155,6 +155,23 @@ void nsfr_build_ops(int p, int p_geo, double c, double gamma, OpsGL* gl, OpsGeo*
       gl->Pi1[a * n + b] = id - 2.0 * c * (g[a] / wg[a]) * g[b] / denom;
       gl->Pinv1[a * n + b] = id + 2.0 * c * (g[a] / wg[a]) * g[b];
     }
+  // rank-one form of the same projection: Pi~1 = I - hv g^T
+  for (int a = 0; a < n; ++a) {
+    gl->gv[a] = g[a];
+    gl->hv[a] = 2.0 * c * (g[a] / wg[a]) / denom;
+    gl->gvf[a] = (float)gl->gv[a];
+    gl->hvf[a] = (float)gl->hv[a];
+  }
+  // series of the logarithmic mean in u = f^2, f = (a-b)/(a+b):
+  //   atanh(f)/f = 1 + u/3 + u^2/5 + u^3/7 + ...,  f/atanh(f) = 1 - u/3 - 4u^2/45 - 44u^3/945 - ...
+  const double F[4] = {1.0, 1.0 / 3.0, 1.0 / 5.0, 1.0 / 7.0};
+  const double G[4] = {1.0, -1.0 / 3.0, -4.0 / 45.0, -44.0 / 945.0};
+  for (int k = 0; k < 4; ++k) {
+    gl->gh[k] = 0.5 * G[k];
+    gl->f4g[k] = 2.0 / (gamma - 1.0) * F[k];
+    gl->fr2[k] = 2.0 * F[k];
+  }
+  gl->inv_gm1 = 1.0 / (gamma - 1.0);
   for (int k = 0; k < n * n; ++k) {
     gl->S1f[k] = (float)gl->S1[k];
     gl->Pi1f[k] = (float)gl->Pi1[k];
@@ -163,7 +180,10 @@ void nsfr_build_ops(int p, int p_geo, double c, double gamma, OpsGL* gl, OpsGeo*
     gl->wf[j] = (float)gl->w[j];
     gl->tmf[j] = (float)gl->tm[j];
     gl->tpf[j] = (float)gl->tp[j];
+    gl->tmlo[j] = (float)(gl->tm[j] - (double)gl->tmf[j]);
+    gl->tplo[j] = (float)(gl->tp[j] - (double)gl->tpf[j]);
   }
+  for (int k = 0; k < n * n; ++k) gl->S1lo[k] = (float)(gl->S1[k] - (double)gl->S1f[k]);
 
   geo->n = n;
   geo->q = q;

@@ -8,119 +8,136 @@
 // whose logarithmic means use Ismail and Roe's series for nearly equal
 // arguments.  Face dissipation: Roe's linearisation (Sec. "Nonlinear
 // Stability").
+//
+// FP64 work is the cost of every kernel on this part (FP32 runs ~74x
+// faster), so the per-node record (Rec) stores what makes each pair cheap:
+// rho, 2 beta, u/2, |u|^2/4, ln rho, ln beta.  Arithmetic means are then plain
+// sums, and reciprocals are Newton iterations on a hardware seed.
 #pragma once
 
 #include "nsfr_internal.h"
 
-// Below this value of f^2 = ((a-b)/(a+b))^2 the log mean uses the series; the
+// Below this value of f^2 = ((a-b)/(a+b))^2 the log mean uses its series; the
 // truncation of the series is then below the FP64 rounding level.
 #define NSFR_LM_EPS 1.0e-4
 
-struct Prim {
-  double r, u0, u1, u2, b, lr, lb, q2;  // rho, velocity, beta, ln rho, ln beta, |u|^2
+struct Rec {
+  double r, b2, u0, u1, u2, qq, lr, lb;  // rho, 2 beta, u/2, |u|^2/4, ln rho, ln beta
 };
 
-__device__ __forceinline__ Prim load_prim(const double* P, int stride) {
-  Prim a;
+__device__ __forceinline__ Rec load_rec(const double* P, int stride) {
+  Rec a;
   a.r = P[P_RHO * stride];
-  a.u0 = P[P_U * stride];
-  a.u1 = P[P_V * stride];
-  a.u2 = P[P_W * stride];
-  a.b = P[P_BETA * stride];
+  a.b2 = P[P_B2 * stride];
+  a.u0 = P[P_UH * stride];
+  a.u1 = P[(P_UH + 1) * stride];
+  a.u2 = P[(P_UH + 2) * stride];
+  a.qq = P[P_QQ * stride];
   a.lr = P[P_LRHO * stride];
   a.lb = P[P_LBETA * stride];
-  a.q2 = P[P_Q2 * stride];
   return a;
 }
 
-__device__ __forceinline__ void store_prim(double* P, int stride, const Prim& a) {
+__device__ __forceinline__ void store_rec(double* P, int stride, const Rec& a) {
   P[P_RHO * stride] = a.r;
-  P[P_U * stride] = a.u0;
-  P[P_V * stride] = a.u1;
-  P[P_W * stride] = a.u2;
-  P[P_BETA * stride] = a.b;
+  P[P_B2 * stride] = a.b2;
+  P[P_UH * stride] = a.u0;
+  P[(P_UH + 1) * stride] = a.u1;
+  P[(P_UH + 2) * stride] = a.u2;
+  P[P_QQ * stride] = a.qq;
   P[P_LRHO * stride] = a.lr;
   P[P_LBETA * stride] = a.lb;
-  P[P_Q2 * stride] = a.q2;
 }
 
-// Primitive record of a conserved state; flags rho <= 0, p <= 0, NaN.
-__device__ __forceinline__ Prim prim_from_conserved(double r, double m0, double m1, double m2, double E,
-                                                    double gamma, int* flag) {
-  Prim a;
-  const double ir = 1.0 / r;
-  a.r = r;
-  a.u0 = m0 * ir;
-  a.u1 = m1 * ir;
-  a.u2 = m2 * ir;
-  a.q2 = a.u0 * a.u0 + a.u1 * a.u1 + a.u2 * a.u2;
-  const double p = (gamma - 1.0) * (E - 0.5 * r * a.q2);
+// 1/x by Newton's iteration r <- r + r (1 - x r) from the hardware's ~2^-20
+// approximation: one step gives ~1e-12 relative, two give the FP64 result.
+__device__ __forceinline__ double rcp_seed(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return r;
+}
+__device__ __forceinline__ double rcp_newton1(double x) {
+  const double r = rcp_seed(x);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+__device__ __forceinline__ double rcp_newton2(double x) {
+  const double r = rcp_newton1(x);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
+// u < NSFR_LM_EPS for u = f^2 >= 0, decided on the integer bit pattern
+__device__ __forceinline__ bool lm_small(double u) {
+  return __double_as_longlong(u) < __double_as_longlong(NSFR_LM_EPS);
+}
+
+__device__ __forceinline__ double horner4(const double* c, double u) {
+  return fma(fma(fma(c[3], u, c[2]), u, c[1]), u, c[0]);
+}
+
+// Record of a conserved state; flags rho <= 0, p <= 0 or NaN.  ln rho and
+// ln beta come from the face-state pass, which already formed them.
+__device__ __forceinline__ Rec rec_from_conserved(double r, double m0, double m1, double m2, double E, double lr,
+                                                  double lb, double gm1, int* flag) {
+  Rec a;
+  const double ir = rcp_newton2(r);
+  const double u0 = m0 * ir, u1 = m1 * ir, u2 = m2 * ir;
+  const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
+  const double p = gm1 * fma(-0.5 * r, q2, E);
   if (!(r > 0.0) || !(p > 0.0)) atomicOr(flag, 1);
-  a.b = 0.5 * r / p;
-  a.lr = log(r);
-  a.lb = log(a.b);
+  a.r = r;
+  a.b2 = r * rcp_newton2(p);
+  a.u0 = 0.5 * u0;
+  a.u1 = 0.5 * u1;
+  a.u2 = 0.5 * u2;
+  a.qq = 0.25 * q2;
+  a.lr = lr;
+  a.lb = lb;
   return a;
 }
 
-// sum_k u^k/(2k+1), k <= 3: atanh(f)/f with u = f^2
-__device__ __forceinline__ double lm_series_F(double u) {
-  return 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0)));
-}
-// its reciprocal f/atanh(f) = 1 - u/3 - 4u^2/45 - 44u^3/945 - ...
-__device__ __forceinline__ double lm_series_G(double u) {
-  return 1.0 + u * (-1.0 / 3.0 + u * (-4.0 / 45.0 + u * (-44.0 / 945.0)));
-}
-
-// rho_ln, 1/beta_ln and p_hat = rho_bar/(2 beta_bar) of a pair.
-__device__ __forceinline__ void ec_means(const Prim& A, const Prim& B, double& rln, double& ibln, double& ph) {
+// F = f_s(A, B) . n, n the averaged metric row (n0, n1, n2).
+//   rho_ln = (rho_a + rho_b) Gh(u_r),        1/(2(gamma-1) beta_ln) = F4g(u_b) / (2 beta_a + 2 beta_b)
+//   p_hat  = (rho_a + rho_b) / (2 beta_a + 2 beta_b)
+//   F_rho = rho_ln u.n,  F_m = F_rho u + p_hat n,  F_E = F_rho (1/(2(gamma-1)beta_ln) - |u|^2_bar/2) + u.F_m
+__device__ __forceinline__ void ec_flux(const Rec& A, const Rec& B, double n0, double n1, double n2,
+                                        const OpsGL& K, double F[5]) {
   const double sr = A.r + B.r, dr = A.r - B.r;
-  const double sb = A.b + B.b, db = A.b - B.b;
-  const double rsr = 1.0 / sr, rsb = 1.0 / sb;
-  const double fr = dr * rsr, fb = db * rsb;
+  const double s2 = A.b2 + B.b2, d2 = A.b2 - B.b2;
+  const double rb2 = rcp_newton2(s2);
+  const double rr = rcp_newton1(sr);  // only enters f^2, a correction below 1e-4
+  const double fr = dr * rr, fb = d2 * rb2;
   const double ur = fr * fr, ub = fb * fb;
-  if (ur < NSFR_LM_EPS) {
-    rln = 0.5 * sr * lm_series_G(ur);
-  } else {
-    rln = dr / (A.lr - B.lr);
-  }
-  if (ub < NSFR_LM_EPS) {
-    ibln = 2.0 * rsb * lm_series_F(ub);
-  } else {
-    ibln = (A.lb - B.lb) / db;
-  }
-  ph = 0.5 * sr * rsb;
-}
-
-// F = f_s(A, B) . n with n the (already averaged) metric row.
-__device__ __forceinline__ void ec_flux(const Prim& A, const Prim& B, double n0, double n1, double n2,
-                                        double inv2gm1, double F[5]) {
-  double rln, ibln, ph;
-  ec_means(A, B, rln, ibln, ph);
-  const double u0 = 0.5 * (A.u0 + B.u0), u1 = 0.5 * (A.u1 + B.u1), u2 = 0.5 * (A.u2 + B.u2);
-  const double un = u0 * n0 + u1 * n1 + u2 * n2;
+  double rln, ibg;
+  if (lm_small(ur)) rln = sr * horner4(K.gh, ur);
+  else rln = dr / (A.lr - B.lr);
+  if (lm_small(ub)) ibg = horner4(K.f4g, ub) * rb2;
+  else ibg = K.inv_gm1 * (A.lb - B.lb) / d2;
+  const double ph = sr * rb2;
+  const double v0 = A.u0 + B.u0, v1 = A.u1 + B.u1, v2 = A.u2 + B.u2;  // u_bar
+  const double un = fma(v0, n0, fma(v1, n1, v2 * n2));
   const double Fr = rln * un;
   F[0] = Fr;
-  F[1] = Fr * u0 + ph * n0;
-  F[2] = Fr * u1 + ph * n1;
-  F[3] = Fr * u2 + ph * n2;
-  const double q2 = 0.5 * (A.q2 + B.q2);
-  F[4] = Fr * (ibln * inv2gm1 - 0.5 * q2) + u0 * F[1] + u1 * F[2] + u2 * F[3];
+  F[1] = fma(Fr, v0, ph * n0);
+  F[2] = fma(Fr, v1, ph * n1);
+  F[3] = fma(Fr, v2, ph * n2);
+  F[4] = fma(v2, F[3], fma(v1, F[2], fma(v0, F[1], Fr * (ibg - (A.qq + B.qq)))));
 }
 
 // D = |A_n| (u_R - u_L): Roe-averaged flux Jacobian along n (non-unit),
 // applied through its eigen-decomposition (acoustic waves q -+ a, entropy
 // and shear waves q), scaled by |n|.
-__device__ __forceinline__ void roe_dissipation(const Prim& L, const Prim& R, double n0, double n1, double n2,
+__device__ __forceinline__ void roe_dissipation(const Rec& L, const Rec& R, double n0, double n1, double n2,
                                                 double gamma, double D[5]) {
   const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
   const double in = 1.0 / nn;
   const double h0 = n0 * in, h1 = n1 * in, h2 = n2 * in;
-  const double pL = 0.5 * L.r / L.b, pR = 0.5 * R.r / R.b;
+  const double pL = L.r / L.b2, pR = R.r / R.b2;
   const double gg = gamma / (gamma - 1.0);
-  const double HL = gg * pL / L.r + 0.5 * L.q2, HR = gg * pR / R.r + 0.5 * R.q2;
+  const double HL = gg * pL / L.r + 2.0 * L.qq, HR = gg * pR / R.r + 2.0 * R.qq;
   const double sL = sqrt(L.r), sR = sqrt(R.r);
   const double wl = sL / (sL + sR), wr = 1.0 - wl;
-  const double uh0 = wl * L.u0 + wr * R.u0, uh1 = wl * L.u1 + wr * R.u1, uh2 = wl * L.u2 + wr * R.u2;
+  const double uh0 = 2.0 * (wl * L.u0 + wr * R.u0), uh1 = 2.0 * (wl * L.u1 + wr * R.u1),
+               uh2 = 2.0 * (wl * L.u2 + wr * R.u2);
   const double Hh = wl * HL + wr * HR;
   const double q2h = uh0 * uh0 + uh1 * uh1 + uh2 * uh2;
   const double a2 = (gamma - 1.0) * (Hh - 0.5 * q2h);
@@ -128,7 +145,7 @@ __device__ __forceinline__ void roe_dissipation(const Prim& L, const Prim& R, do
   const double rh = sL * sR;
   const double qh = uh0 * h0 + uh1 * h1 + uh2 * h2;
   const double dr = R.r - L.r, dp = pR - pL;
-  const double du0 = R.u0 - L.u0, du1 = R.u1 - L.u1, du2 = R.u2 - L.u2;
+  const double du0 = 2.0 * (R.u0 - L.u0), du1 = 2.0 * (R.u1 - L.u1), du2 = 2.0 * (R.u2 - L.u2);
   const double dq = du0 * h0 + du1 * h1 + du2 * h2;
   const double al1 = (dp - rh * ah * dq) / (2.0 * a2);
   const double al5 = (dp + rh * ah * dq) / (2.0 * a2);
@@ -144,12 +161,12 @@ __device__ __forceinline__ void roe_dissipation(const Prim& L, const Prim& R, do
 }
 
 // f*(u~_L, u~_R; n): EC flux, minus (1/2)|A_n|(u_R - u_L) with Roe dissipation.
-__device__ __forceinline__ void face_flux(const Prim& L, const Prim& R, double n0, double n1, double n2,
-                                          double gamma, double inv2gm1, int kind, double F[5]) {
-  ec_flux(L, R, n0, n1, n2, inv2gm1, F);
+__device__ __forceinline__ void face_flux(const Rec& L, const Rec& R, double n0, double n1, double n2,
+                                          const OpsGL& K, int kind, double F[5]) {
+  ec_flux(L, R, n0, n1, n2, K, F);
   if (kind == NSFR_FACE_EC_ROE) {
     double D[5];
-    roe_dissipation(L, R, n0, n1, n2, gamma, D);
+    roe_dissipation(L, R, n0, n1, n2, K.gamma, D);
 #pragma unroll
     for (int k = 0; k < 5; ++k) F[k] -= 0.5 * D[k];
   }

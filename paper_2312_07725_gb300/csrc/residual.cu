@@ -17,58 +17,45 @@
 //     epilogue applies the weight-adjusted inverse (Eq. weight-adj ESFR mass,
 //     Pi~^T, 1/(w J), Pi~, each a 1D contraction per direction) and either
 //     stores du/dt or performs the RK stage update in place.
+#include "kernel_common.cuh"
 #include "physics.cuh"
 
 namespace {
-
-// elements per CTA and CTA size (one thread per line, 3 n^2 lines per element)
-constexpr int epb_for(int n) { return n == 2 ? 16 : n == 3 ? 8 : n <= 5 ? 4 : n == 6 ? 2 : 1; }
-constexpr int threads_for(int n) { return epb_for(n) * 3 * n * n; }
-
-__device__ __forceinline__ int nbr_index(int e, int d, int side, int nx, int ny, int nz) {
-  int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
-  const int st = side ? 1 : -1;
-  if (d == 0) ex = (ex + st + nx) % nx;
-  else if (d == 1) ey = (ey + st + ny) % ny;
-  else ez = (ez + st + nz) % nz;
-  return ex + nx * (ey + ny * ez);
-}
-
-// node index of line node a for line (d, l0, l1): base + a * stride
-template <int N>
-__device__ __forceinline__ void line_geometry(int d, int l0, int l1, int& base, int& stride) {
-  if (d == 0) { base = N * (l0 + N * l1); stride = 1; }
-  else if (d == 1) { base = l0 + N * N * l1; stride = N; }
-  else { base = l0 + N * l1; stride = N * N; }
-}
+using namespace nsfr_k;
 
 template <int N>
 __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double* __restrict__ u, OpsGL ops,
-                                                                    double* __restrict__ face, int ne, int* flag) {
+                                                                    double* __restrict__ face,
+                                                                    double* __restrict__ lnrec, int ne, int* flag) {
   constexpr int NV = N * N * N, NFP = N * N, NL = 3 * NFP;
   extern __shared__ double sm[];
   const int epb = blockDim.x / NL;
   const int e0 = blockIdx.x * epb;
   const double g = ops.gamma, gm1 = g - 1.0;
-  // v(u) at every node of the block's elements
+  const double ln2 = 0.69314718055994530942;
+  // v(u) at every node of the block's elements; ln rho and ln beta are kept
+  // for the volume kernel, which needs them for its logarithmic means
   for (int t = threadIdx.x; t < epb * NV; t += blockDim.x) {
     const int le = t / NV, node = t % NV, e = e0 + le;
     if (e >= ne) continue;
     const double* ue = u + (size_t)e * 5 * NV + node;
     const double r = ue[0], m0 = ue[NV], m1 = ue[2 * NV], m2 = ue[3 * NV], E = ue[4 * NV];
-    const double ir = 1.0 / r;
+    const double ir = rcp_newton2(r);
     const double u0 = m0 * ir, u1 = m1 * ir, u2 = m2 * ir;
-    const double q2 = u0 * u0 + u1 * u1 + u2 * u2;
-    const double p = gm1 * (E - 0.5 * r * q2);
+    const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
+    const double p = gm1 * fma(-0.5 * r, q2, E);
     if (!(r > 0.0) || !(p > 0.0)) atomicOr(flag, 1);
-    const double b = 0.5 * r / p;
-    const double s = log(p) - g * log(r);
+    const double b = 0.5 * r * rcp_newton2(p);
+    const double lr = log(r), lp = log(p);
+    const double s = lp - g * lr;
     double* v = sm + (size_t)le * 5 * NV + node;
-    v[0] = (g - s) / gm1 - b * q2;
+    v[0] = (g - s) * ops.inv_gm1 - b * q2;
     v[NV] = 2.0 * b * u0;
     v[2 * NV] = 2.0 * b * u1;
     v[3 * NV] = 2.0 * b * u2;
     v[4 * NV] = -2.0 * b;
+    lnrec[(size_t)e * 2 * NV + node] = lr;
+    lnrec[(size_t)e * 2 * NV + NV + node] = lr - lp - ln2;  // ln beta = ln rho - ln 2p
   }
   __syncthreads();
   const int le = threadIdx.x / NL, l = threadIdx.x % NL, e = e0 + le;
@@ -84,34 +71,53 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
 #pragma unroll
     for (int a = 0; a < N; ++a) {
       const double x = v[k * NV + a * stride];
-      am += ops.tm[a] * x;
-      ap += ops.tp[a] * x;
+      am = fma(ops.tm[a], x, am);
+      ap = fma(ops.tp[a], x, ap);
     }
     vm[k] = am;
     vp[k] = ap;
   }
-  const double ln2 = 0.69314718055994530942;
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const double* w = s ? vp : vm;
     if (!(w[4] < 0.0)) atomicOr(flag, 1);
-    const double b = -0.5 * w[4];
-    const double iv5 = 1.0 / w[4];
+    const double b2 = -w[4];                  // 2 beta
+    const double iv5 = rcp_newton2(w[4]);
     const double u0 = -w[1] * iv5, u1 = -w[2] * iv5, u2 = -w[3] * iv5;
-    const double q2 = u0 * u0 + u1 * u1 + u2 * u2;
-    const double sent = g - gm1 * (w[0] + b * q2);
-    const double L5 = log(-w[4]);          // ln(2 beta)
-    const double lr = -(sent + L5) / gm1;  // s = (1-gamma) ln rho - ln(2 beta)
-    Prim P;
+    const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
+    const double sent = g - gm1 * fma(0.5 * b2, q2, w[0]);
+    const double L5 = log(b2);                // ln(2 beta)
+    const double lr = -(sent + L5) * ops.inv_gm1;  // s = (1-gamma) ln rho - ln(2 beta)
+    Rec P;
     P.r = exp(lr);
-    P.u0 = u0;
-    P.u1 = u1;
-    P.u2 = u2;
-    P.b = b;
+    P.b2 = b2;
+    P.u0 = 0.5 * u0;
+    P.u1 = 0.5 * u1;
+    P.u2 = 0.5 * u2;
+    P.qq = 0.25 * q2;
     P.lr = lr;
     P.lb = L5 - ln2;
-    P.q2 = q2;
-    store_prim(face + (((size_t)e * 6 + 2 * d + s) * NSFR_NFIELD) * NFP + line, NFP, P);
+    store_rec(face + (((size_t)e * 6 + 2 * d + s) * NSFR_NFIELD) * NFP + line, NFP, P);
+  }
+}
+
+// Pi~1^T (transpose) or Pi~1 along direction d for every line of X[nel][5][NV],
+// in place: Pi~1 x = x - hv (g . x), Pi~1^T x = x - g (hv . x).
+template <int N>
+__device__ __forceinline__ void rank_one_sweep(double* X, int nel, int d, bool transpose, const OpsGL& ops) {
+  constexpr int NV = N * N * N, NFP = N * N;
+  const int st = (d == 0) ? 1 : (d == 1 ? N : N * N);
+  const int nlines = nel * 5 * NFP;
+  for (int t = threadIdx.x; t < nlines; t += blockDim.x) {
+    const int line = t % NFP, lk = t / NFP;  // lk = element*5 + var
+    int base, stride;
+    line_geometry<N>(d, line % N, line / N, base, stride);
+    double* x = X + (size_t)lk * NV + base;
+    double dot = 0.0;
+#pragma unroll
+    for (int a = 0; a < N; ++a) dot = fma(transpose ? ops.hv[a] : ops.gv[a], x[a * st], dot);
+#pragma unroll
+    for (int a = 0; a < N; ++a) x[a * st] = fma(-(transpose ? ops.gv[a] : ops.hv[a]), dot, x[a * st]);
   }
 }
 
@@ -119,7 +125,8 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
 // next stage state over it (each CTA only over its own elements, after its
 // own reads).
 template <int N>
-__global__ void __launch_bounds__(threads_for(N)) volume_kernel(const double* u, const double* __restrict__ metric,
+__global__ void __launch_bounds__(threads_for(N), 1) volume_kernel(const double* u, const double* __restrict__ lnrec,
+                                                                const double* __restrict__ metric,
                                                                 const double* __restrict__ nf_plus,
                                                                 const double* __restrict__ face,
                                                                 const double* __restrict__ invwj, OpsGL ops, int nx,
@@ -129,24 +136,30 @@ __global__ void __launch_bounds__(threads_for(N)) volume_kernel(const double* u,
   extern __shared__ double sm[];
   const int epb = blockDim.x / NL;
   const int e0 = blockIdx.x * epb;
-  double* P = sm;                                   // [epb][8][NV] node primitives
-  double* Ms = P + (size_t)epb * NSFR_NFIELD * NV;  // [epb][9][NV] metric
+  double* P = sm;                                   // [epb][8][NV] node records
+  double* Ms = P + (size_t)epb * NSFR_NFIELD * NV;  // [epb][9][NV] metric rows / 2
   double* Rs = Ms + (size_t)epb * 9 * NV;           // [epb][5][NV] residual
-  double* Ts = P;                                   // epilogue temp (aliases P)
-  const double g = ops.gamma, inv2gm1 = 0.5 / (g - 1.0);
+  const double gm1 = ops.gamma - 1.0;
 
-  // prologue: primitive records and metric rows of the block's elements
+  // prologue: node records and half metric rows of the block's elements
   for (int t = threadIdx.x; t < epb * NV; t += blockDim.x) {
     const int le = t / NV, node = t % NV, e = e0 + le;
     if (e >= ne) continue;
     const double* ue = u + (size_t)e * 5 * NV + node;
-    Prim a = prim_from_conserved(ue[0], ue[NV], ue[2 * NV], ue[3 * NV], ue[4 * NV], g, flag);
-    store_prim(P + (size_t)le * NSFR_NFIELD * NV + node, NV, a);
+    const double* ln = lnrec + (size_t)e * 2 * NV + node;
+    Rec a = rec_from_conserved(ue[0], ue[NV], ue[2 * NV], ue[3 * NV], ue[4 * NV], ln[0], ln[NV], gm1, flag);
+    store_rec(P + (size_t)le * NSFR_NFIELD * NV + node, NV, a);
   }
+  // metric rows of direction d scaled by w_perp / 2: w_perp (the weights of
+  // the two other directions) is constant along a line of direction d, and
+  // the fluxes are linear in the metric row, so the pair weights reduce to S1
   for (int t = threadIdx.x; t < epb * 9 * NV; t += blockDim.x) {
     const int le = t / (9 * NV), e = e0 + le;
     if (e >= ne) continue;
-    Ms[t] = metric[(size_t)e0 * 9 * NV + t];
+    const int node = t % NV, dd = (t / NV) % 9 / 3;
+    const int i = node % N, j = (node / N) % N, k = node / (N * N);
+    const double wp = dd == 0 ? ops.w[j] * ops.w[k] : (dd == 1 ? ops.w[i] * ops.w[k] : ops.w[i] * ops.w[j]);
+    Ms[t] = 0.5 * wp * metric[(size_t)e0 * 9 * NV + t];
   }
   __syncthreads();
 
@@ -165,24 +178,22 @@ __global__ void __launch_bounds__(threads_for(N)) volume_kernel(const double* u,
     const double* Pe = P + (size_t)le * NSFR_NFIELD * NV + base;
     const double* Me = Ms + ((size_t)le * 9 + 3 * d) * NV + base;
     const double wperp = ops.w[l0] * ops.w[l1];
-    // volume-volume pairs along the line
+    // volume-volume pairs along the line: each unordered pair once (S1 is skew);
+    // the metric rows already carry w_perp / 2
 #pragma unroll
     for (int a = 0; a < N; ++a) {
-      const Prim A = load_prim(Pe + a * stride, NV);
+      const Rec A = load_rec(Pe + a * stride, NV);
       const double na0 = Me[a * stride], na1 = Me[NV + a * stride], na2 = Me[2 * NV + a * stride];
 #pragma unroll
       for (int b = a + 1; b < N; ++b) {
-        const Prim B = load_prim(Pe + b * stride, NV);
-        const double n0 = 0.5 * (na0 + Me[b * stride]);
-        const double n1 = 0.5 * (na1 + Me[NV + b * stride]);
-        const double n2 = 0.5 * (na2 + Me[2 * NV + b * stride]);
+        const Rec B = load_rec(Pe + b * stride, NV);
         double F[5];
-        ec_flux(A, B, n0, n1, n2, inv2gm1, F);
-        const double c = wperp * ops.S1[a * N + b];
+        ec_flux(A, B, na0 + Me[b * stride], na1 + Me[NV + b * stride], na2 + Me[2 * NV + b * stride], ops, F);
+        const double c = ops.S1[a * N + b];
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-          R[a][k] += c * F[k];
-          R[b][k] -= c * F[k];
+          R[a][k] = fma(c, F[k], R[a][k]);
+          R[b][k] = fma(-c, F[k], R[b][k]);
         }
       }
     }
@@ -193,35 +204,38 @@ __global__ void __launch_bounds__(threads_for(N)) volume_kernel(const double* u,
       const double* fo = face + (((size_t)e * 6 + 2 * d + s) * NSFR_NFIELD) * NFP + line;
       const double* fn = face + (((size_t)enb * 6 + 2 * d + 1 - s) * NSFR_NFIELD) * NFP + line;
       const double* nf = nf_plus + (((size_t)(s ? e : enb) * 3 + d) * 3) * NFP + line;
-      const double f0 = nf[0], f1 = nf[NFP], f2 = nf[2 * NFP];
-      const Prim Fo = load_prim(fo, NFP);
-      const Prim Fn = load_prim(fn, NFP);
+      const double f0 = wperp * nf[0], f1 = wperp * nf[NFP], f2 = wperp * nf[2 * NFP];
+      const Rec Fo = load_rec(fo, NFP);
+      const Rec Fn = load_rec(fn, NFP);
       double fs[5];
-      if (s) face_flux(Fo, Fn, f0, f1, f2, g, inv2gm1, face_kind, fs);
-      else face_flux(Fn, Fo, f0, f1, f2, g, inv2gm1, face_kind, fs);
+      if (s) face_flux(Fo, Fn, f0, f1, f2, ops, face_kind, fs);
+      else face_flux(Fn, Fo, f0, f1, f2, ops, face_kind, fs);
       const double* t = s ? ops.tp : ops.tm;
-      const double sw = (s ? 1.0 : -1.0) * wperp;
+      const double sw = s ? 1.0 : -1.0;
+      const double h0 = 0.5 * f0, h1 = 0.5 * f1, h2 = 0.5 * f2;
       double tphi[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
       for (int a = 0; a < N; ++a) {
-        const Prim A = load_prim(Pe + a * stride, NV);
+        const Rec A = load_rec(Pe + a * stride, NV);
         double F[5];
-        ec_flux(A, Fo, 0.5 * (Me[a * stride] + f0), 0.5 * (Me[NV + a * stride] + f1),
-                0.5 * (Me[2 * NV + a * stride] + f2), inv2gm1, F);
-        const double ta = t[a];
+        ec_flux(A, Fo, Me[a * stride] + h0, Me[NV + a * stride] + h1, Me[2 * NV + a * stride] + h2, ops, F);
+        const double ta = t[a], swt = sw * ta;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-          tphi[k] += ta * F[k];
-          R[a][k] += sw * ta * F[k];
+          tphi[k] = fma(ta, F[k], tphi[k]);
+          R[a][k] = fma(swt, F[k], R[a][k]);
         }
       }
 #pragma unroll
-      for (int a = 0; a < N; ++a)
+      for (int k = 0; k < 5; ++k) tphi[k] = fs[k] - tphi[k];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) R[a][k] += sw * t[a] * (fs[k] - tphi[k]);
+      for (int a = 0; a < N; ++a) {
+        const double swt = sw * t[a];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) R[a][k] = fma(swt, tphi[k], R[a][k]);
+      }
     }
   }
-  __syncthreads();  // P and Ms are no longer read
   // the three directions meet in shared memory (fixed order: d = 0, 1, 2)
 #pragma unroll
   for (int dd = 0; dd < 3; ++dd) {
@@ -240,65 +254,42 @@ __global__ void __launch_bounds__(threads_for(N)) volume_kernel(const double* u,
 
   const int nel = min(epb, ne - e0);
   const int total = nel * 5 * NV;
-  double* X = Rs;
   if (epi != EPI_RAW) {
+    // weight-adjusted inverse: Pi~^T along xi, eta, zeta; 1/(w J); Pi~ along xi, eta, zeta
     if (ops.has_K) {
-      // Pi~^T along xi, eta, zeta; 1/(w J); Pi~ along xi, eta, zeta
-      double* src = Rs;
-      double* dst = Ts;
-#pragma unroll 1
-      for (int pass = 0; pass < 7; ++pass) {
-        if (pass == 3) {
-          for (int t = threadIdx.x; t < total; t += blockDim.x) {
-            const int lq = t / (5 * NV), node = t % NV;
-            src[t] *= invwj[(size_t)(e0 + lq) * NV + node];
-          }
-          __syncthreads();
-          continue;
-        }
-        const int dd = (pass < 3) ? pass : pass - 4;
-        const bool transpose = pass < 3;
-        const int st = (dd == 0) ? 1 : (dd == 1 ? N : N * N);
-        for (int t = threadIdx.x; t < total; t += blockDim.x) {
-          const int node = t % NV;
-          const int r = (node / st) % N;
-          const double* col = src + (t - r * st);
-          double acc = 0.0;
-#pragma unroll
-          for (int b = 0; b < N; ++b)
-            acc += (transpose ? ops.Pi1[b * N + r] : ops.Pi1[r * N + b]) * col[b * st];
-          dst[t] = acc;
-        }
+      for (int dd = 0; dd < 3; ++dd) {
+        rank_one_sweep<N>(Rs, nel, dd, true, ops);
         __syncthreads();
-        double* tmp = src;
-        src = dst;
-        dst = tmp;
       }
-      X = src;
-    } else {
-      for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int lq = t / (5 * NV), node = t % NV;
-        X[t] *= invwj[(size_t)(e0 + lq) * NV + node];
+    }
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int lq = t / (5 * NV), node = t % NV;
+      Rs[t] *= invwj[(size_t)(e0 + lq) * NV + node];
+    }
+    __syncthreads();
+    if (ops.has_K) {
+      for (int dd = 0; dd < 3; ++dd) {
+        rank_one_sweep<N>(Rs, nel, dd, false, ops);
+        __syncthreads();
       }
-      __syncthreads();
     }
   }
   // store
   const size_t off = (size_t)e0 * 5 * NV;
   if (epi == EPI_RAW) {
-    for (int t = threadIdx.x; t < total; t += blockDim.x) out[off + t] = X[t];
+    for (int t = threadIdx.x; t < total; t += blockDim.x) out[off + t] = Rs[t];
   } else if (epi == EPI_DUDT) {
-    for (int t = threadIdx.x; t < total; t += blockDim.x) out[off + t] = -X[t];
+    for (int t = threadIdx.x; t < total; t += blockDim.x) out[off + t] = -Rs[t];
   } else {
     const double bdt = rk.b * rk.dt, adt = rk.a_next * rk.dt;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const double k = -X[t];
+      const double k = -Rs[t];
       if (rk.last) {
-        rk.unext[off + t] = rk.acc[off + t] + bdt * k;
+        rk.unext[off + t] = fma(bdt, k, rk.acc[off + t]);
       } else {
         const double u0 = rk.u0[off + t];
-        rk.acc[off + t] = (rk.first ? u0 : rk.acc[off + t]) + bdt * k;
-        rk.unext[off + t] = u0 + adt * k;
+        rk.acc[off + t] = fma(bdt, k, rk.first ? u0 : rk.acc[off + t]);
+        rk.unext[off + t] = fma(adt, k, u0);
       }
     }
   }
@@ -313,7 +304,7 @@ cudaError_t launch_face_n(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
   cudaError_t err = cudaFuncSetAttribute(face_state_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   nsfr_prof_begin(ctx, 1, s);
-  face_state_kernel<N><<<grid, threads_for(N), smem, s>>>(u, ctx->ops, ctx->face, ctx->ne, ctx->flag);
+  face_state_kernel<N><<<grid, threads_for(N), smem, s>>>(u, ctx->ops, ctx->face, ctx->lnrec, ctx->ne, ctx->flag);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
   return cudaGetLastError();
@@ -330,7 +321,7 @@ cudaError_t launch_volume_n(nsfr_ctx* ctx, const double* u, double* out, int epi
   if (err != cudaSuccess) return err;
   RkArgs r = rk ? *rk : RkArgs{};
   nsfr_prof_begin(ctx, 2, s);
-  volume_kernel<N><<<grid, threads_for(N), smem, s>>>(u, ctx->metric, ctx->nfp_plus, ctx->face, ctx->invwj,
+  volume_kernel<N><<<grid, threads_for(N), smem, s>>>(u, ctx->lnrec, ctx->metric, ctx->nfp_plus, ctx->face, ctx->invwj,
                                                       ctx->ops, ctx->nx, ctx->ny, ctx->nz, ctx->ne, ctx->face_flux,
                                                       epi, r, out, ctx->flag);
   nsfr_prof_end(ctx, s);
@@ -389,7 +380,7 @@ extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, co
   const size_t ne = (size_t)nx * ny * nz, n = p + 1, nv = n * n * n, nfp = n * n;
   const size_t face_bytes = ne * 6 * NSFR_NFIELD * nfp * sizeof(double);
   const size_t jac_bytes = ne * nv * sizeof(double);
-  const size_t need = 256 + face_bytes + 2 * jac_bytes;  // error word (padded), faces, 1/(wJ), wJ
+  const size_t need = 256 + face_bytes + 4 * jac_bytes;  // error word (padded), faces, 1/(wJ), wJ, ln rho/beta
   if (need > NSFR_STATIC_SCRATCH_BYTES || ne > (size_t)0x7fffffff) return NSFR_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return NSFR_ERR_CUDA;
@@ -426,6 +417,7 @@ extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, co
   ctx.face = (double*)(base + 256);
   ctx.invwj = (double*)(base + 256 + face_bytes);
   ctx.wj = (double*)(base + 256 + face_bytes + jac_bytes);
+  ctx.lnrec = (double*)(base + 256 + face_bytes + 2 * jac_bytes);
   ctx.metric = const_cast<double*>(C);
   ctx.J = const_cast<double*>(J);
   ctx.nfp_plus = const_cast<double*>(Cf);

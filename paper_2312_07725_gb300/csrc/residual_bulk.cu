@@ -1,0 +1,421 @@
+// NSFR-EC volume/hybrid/surface kernel, FP32-bulk form.
+//
+// Same discretisation as volume_kernel (Eq. NSFR with sum-factorised
+// Hadamard products, Eq. weight-adj ESFR mass, fused RK stage), with the work
+// split by precision:
+//   FP64  the logarithmic means and the two scalars formed from them (p_hat
+//         and the energy coefficient H = 1/(2(gamma-1) beta_ln) + p_hat/rho_ln),
+//         the entropy projection (the shared face-state kernel) and the state;
+//   FP32  the momentum and energy flux arithmetic and their accumulation, and
+//         the mass-inverse contractions;
+//   float-float (FP32 pairs)  the mass flux rho_ln u.n and its accumulation.
+// The fluxes are formed as deviations from the state of the element's first
+// node (rho_ref, u_ref, p_ref): subtracting p_ref n from the momentum flux
+// leaves R unchanged (the scheme is free-stream preserving, Sec. "Free-stream
+// Preservation"), and because R is linear in the flux values,
+//   F_m = F_rho u_bar + p_hat n      -> F_m' = F_rho (u_bar - u_ref) + (p_hat - p_ref) n,
+//                                        R_m = R(F_m') + u_ref R_rho,
+//   F_E = F_rho (H - |u|^2_bar/2 + |u_bar|^2), H = 1/(2(gamma-1) beta_ln) + p_hat/rho_ln
+//                                     -> F_E' = F_E - E_ref F_rho, E_ref = H_ref + |u_ref|^2/2,
+//                                        R_E = R(F_E') + E_ref R_rho,
+// exactly.  Only O(deviation) quantities then meet FP32 rounding; the mass
+// residual, which u_ref and E_ref (~250 for the Taylor-Green vortex) multiply,
+// is kept to ~48 bits.
+#include "ffloat.cuh"
+#include "kernel_common.cuh"
+#include "physics.cuh"
+
+namespace {
+using namespace nsfr_k;
+
+struct BNode {
+  double r, b2, lr, lb;  // FP64 log-mean inputs
+  ff u0, u1, u2;         // u/2
+  float qq;              // |u|^2/4
+};
+
+__device__ __forceinline__ BNode bnode_from_rec(const Rec& a) {
+  BNode b;
+  b.r = a.r;
+  b.b2 = a.b2;
+  b.lr = a.lr;
+  b.lb = a.lb;
+  b.u0 = ff_from_double(a.u0);
+  b.u1 = ff_from_double(a.u1);
+  b.u2 = ff_from_double(a.u2);
+  b.qq = __double2float_rn(a.qq);
+  return b;
+}
+
+struct BRef {
+  double p, H;       // p_ref, H_ref = gamma p_ref / ((gamma - 1) rho_ref)
+  ff u0, u1, u2;     // u_ref
+  float kin;         // |u_ref|^2 / 2
+};
+
+// deviation flux of a pair: Fr (mass, float-float), Fm = F_m - u_ref F_rho - p_ref n,
+// FE = F_E - (H_ref + |u_ref|^2/2) F_rho; (n0, n1, n2) the averaged metric row.
+__device__ __forceinline__ void bulk_flux(const BNode& A, const BNode& B, ff n0, ff n1, ff n2, const BRef& ref,
+                                          const OpsGL& K, ff& Fr, float Fm[3], float& FE) {
+  const double sr = A.r + B.r, dr = A.r - B.r;
+  const double s2 = A.b2 + B.b2, d2 = A.b2 - B.b2;
+  const double rb2 = rcp_newton1(s2), rr = rcp_newton1(sr);
+  const double fr = dr * rr, fb = d2 * rb2;
+  const double ur = fr * fr, ub = fb * fb;
+  double rln, irln, ibg;
+  if (lm_small(ur)) {
+    rln = sr * horner4(K.gh, ur);
+    irln = horner4(K.fr2, ur) * rr;
+  } else {
+    const double dl = A.lr - B.lr;
+    rln = dr / dl;
+    irln = dl / dr;
+  }
+  if (lm_small(ub)) ibg = horner4(K.f4g, ub) * rb2;
+  else ibg = K.inv_gm1 * (A.lb - B.lb) / d2;
+  const double ph = sr * rb2;
+  const float dp = __double2float_rn(ph - ref.p);
+  const float dH = __double2float_rn(fma(ph, irln, ibg) - ref.H);
+  const ff v0 = ff_add(A.u0, B.u0), v1 = ff_add(A.u1, B.u1), v2 = ff_add(A.u2, B.u2);
+  const ff un = ff_add(ff_add(ff_mul(v0, n0), ff_mul(v1, n1)), ff_mul(v2, n2));
+  Fr = ff_mul(ff_from_double(rln), un);
+  const float f = Fr.hi;
+  // velocity deviations, exact to the float-float level before rounding
+  const float w0 = ff_add(v0, ff_neg(ref.u0)).hi, w1 = ff_add(v1, ff_neg(ref.u1)).hi,
+              w2 = ff_add(v2, ff_neg(ref.u2)).hi;
+  Fm[0] = fmaf(f, w0, dp * n0.hi);
+  Fm[1] = fmaf(f, w1, dp * n1.hi);
+  Fm[2] = fmaf(f, w2, dp * n2.hi);
+  // |u_bar|^2 - |u_ref|^2/2 - |u|^2_bar/2, with |u_bar|^2 - |u_ref|^2 = (u_bar - u_ref).(u_bar + u_ref)
+  const float du2 = fmaf(w0, v0.hi + ref.u0.hi, fmaf(w1, v1.hi + ref.u1.hi, w2 * (v2.hi + ref.u2.hi)));
+  FE = f * (dH + du2 + ref.kin - (A.qq + B.qq));
+}
+
+// reference state of an element: its node 0 (records in shared memory; the
+// float copy of u/2 is doubled exactly)
+__device__ __forceinline__ BRef element_ref(const double* pd, const float* pf, int NV, const OpsGL& ops) {
+  BRef r;
+  const double b20 = pd[NV];
+  r.p = pd[0] / b20;
+  r.H = ops.gamma * ops.inv_gm1 / b20;
+  r.u0 = ff{2.0f * pf[0], 2.0f * pf[3 * NV]};
+  r.u1 = ff{2.0f * pf[NV], 2.0f * pf[4 * NV]};
+  r.u2 = ff{2.0f * pf[2 * NV], 2.0f * pf[5 * NV]};
+  const float a = r.u0.hi, b = r.u1.hi, c = r.u2.hi;
+  r.kin = 0.5f * fmaf(a, a, fmaf(b, b, c * c));
+  return r;
+}
+
+template <int N>
+__device__ __forceinline__ void rank_one_sweep_f(float* X, int nel, int d, bool transpose, const OpsGL& ops) {
+  constexpr int NV = N * N * N, NFP = N * N;
+  const int st = (d == 0) ? 1 : (d == 1 ? N : N * N);
+  const int nlines = nel * 5 * NFP;
+  for (int t = threadIdx.x; t < nlines; t += blockDim.x) {
+    const int line = t % NFP, lk = t / NFP;
+    int base, stride;
+    line_geometry<N>(d, line % N, line / N, base, stride);
+    float* x = X + (size_t)lk * NV + base;
+    float dot = 0.0f;
+#pragma unroll
+    for (int a = 0; a < N; ++a) dot = fmaf(transpose ? ops.hvf[a] : ops.gvf[a], x[a * st], dot);
+#pragma unroll
+    for (int a = 0; a < N; ++a) x[a * st] = fmaf(-(transpose ? ops.gvf[a] : ops.hvf[a]), dot, x[a * st]);
+  }
+}
+
+// shared-memory layout per element (SoA over the NV nodes)
+//   doubles: r, 2 beta, ln rho, ln beta                       4 NV
+//   floats : u/2 hi(3) lo(3), |u|^2/4, metric hi(9) lo(9)     25 NV
+//   floats : R_rho hi, lo, R_m(3), R_E'                        6 NV
+//   doubles: R (combined), epilogue                            5 NV
+template <int N>
+__global__ void __launch_bounds__(threads_for(N), 1)
+    volume_bulk_kernel(const double* u, const double* __restrict__ lnrec, const double* __restrict__ metric,
+                       const double* __restrict__ nf_plus, const double* __restrict__ face,
+                       const double* __restrict__ invwj, OpsGL ops, int nx, int ny, int nz, int ne, int face_kind,
+                       int epi, RkArgs rk, double* out, int* flag) {
+  constexpr int NV = N * N * N, NFP = N * N, NL = 3 * NFP;
+  extern __shared__ double sm[];
+  const int epb = blockDim.x / NL;
+  const int e0 = blockIdx.x * epb;
+  double* Pd = sm;                                 // [epb][4][NV]
+  double* Rd = Pd + (size_t)epb * 4 * NV;          // [epb][5][NV]
+  float* Pf = (float*)(Rd + (size_t)epb * 5 * NV); // [epb][25][NV]
+  float* Ra = Pf + (size_t)epb * 25 * NV;          // [epb][6][NV]
+  float* Xf = Pf;                                  // epilogue (aliases Pf)
+  const double gm1 = ops.gamma - 1.0;
+
+  for (int t = threadIdx.x; t < epb * NV; t += blockDim.x) {
+    const int le = t / NV, node = t % NV, e = e0 + le;
+    if (e >= ne) continue;
+    const double* ue = u + (size_t)e * 5 * NV + node;
+    const double* ln = lnrec + (size_t)e * 2 * NV + node;
+    const Rec a = rec_from_conserved(ue[0], ue[NV], ue[2 * NV], ue[3 * NV], ue[4 * NV], ln[0], ln[NV], gm1, flag);
+    double* pd = Pd + (size_t)le * 4 * NV + node;
+    pd[0] = a.r;
+    pd[NV] = a.b2;
+    pd[2 * NV] = a.lr;
+    pd[3 * NV] = a.lb;
+    float* pf = Pf + (size_t)le * 25 * NV + node;
+    const ff u0 = ff_from_double(a.u0), u1 = ff_from_double(a.u1), u2 = ff_from_double(a.u2);
+    pf[0] = u0.hi;
+    pf[NV] = u1.hi;
+    pf[2 * NV] = u2.hi;
+    pf[3 * NV] = u0.lo;
+    pf[4 * NV] = u1.lo;
+    pf[5 * NV] = u2.lo;
+    pf[6 * NV] = __double2float_rn(a.qq);
+    for (int r = 0; r < 9; ++r) {
+      const ff m = ff_from_double(0.5 * wperp_of(ops.w, node, N, r / 3) * metric[((size_t)e * 9 + r) * NV + node]);
+      pf[(7 + r) * NV] = m.hi;
+      pf[(16 + r) * NV] = m.lo;
+    }
+  }
+  __syncthreads();
+
+  const int le = threadIdx.x / NL, l = threadIdx.x % NL, e = e0 + le;
+  const bool valid = (le < epb) && (e < ne);
+  const int d = l / NFP, line = l % NFP, l0 = line % N, l1 = line / N;
+  int base, stride;
+  line_geometry<N>(d, l0, l1, base, stride);
+  ff Rr[N];
+  float Rm[N][3], Re[N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    Rr[a] = ff{0.0f, 0.0f};
+    Rm[a][0] = Rm[a][1] = Rm[a][2] = Re[a] = 0.0f;
+  }
+  BRef ref;
+  if (valid) {
+    const double* pd = Pd + (size_t)le * 4 * NV + base;
+    const float* pf = Pf + (size_t)le * 25 * NV + base;
+    ref = element_ref(Pd + (size_t)le * 4 * NV, Pf + (size_t)le * 25 * NV, NV, ops);
+    auto node_at = [&](int a) {
+      BNode b;
+      b.r = pd[a * stride];
+      b.b2 = pd[NV + a * stride];
+      b.lr = pd[2 * NV + a * stride];
+      b.lb = pd[3 * NV + a * stride];
+      b.u0 = ff{pf[a * stride], pf[3 * NV + a * stride]};
+      b.u1 = ff{pf[NV + a * stride], pf[4 * NV + a * stride]};
+      b.u2 = ff{pf[2 * NV + a * stride], pf[5 * NV + a * stride]};
+      b.qq = pf[6 * NV + a * stride];
+      return b;
+    };
+    auto metric_at = [&](int a, int c) {
+      return ff{pf[(7 + 3 * d + c) * NV + a * stride], pf[(16 + 3 * d + c) * NV + a * stride]};
+    };
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      const BNode A = node_at(a);
+      const ff na0 = metric_at(a, 0), na1 = metric_at(a, 1), na2 = metric_at(a, 2);
+#pragma unroll
+      for (int b = a + 1; b < N; ++b) {
+        const BNode B = node_at(b);
+        ff Fr;
+        float Fm[3], FE;
+        bulk_flux(A, B, ff_add(na0, metric_at(b, 0)), ff_add(na1, metric_at(b, 1)), ff_add(na2, metric_at(b, 2)),
+                  ref, ops, Fr, Fm, FE);
+        const ff c{ops.S1f[a * N + b], ops.S1lo[a * N + b]};
+        Rr[a] = ff_fma(c, Fr, Rr[a]);
+        Rr[b] = ff_fma(ff_neg(c), Fr, Rr[b]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          Rm[a][k] = fmaf(c.hi, Fm[k], Rm[a][k]);
+          Rm[b][k] = fmaf(-c.hi, Fm[k], Rm[b][k]);
+        }
+        Re[a] = fmaf(c.hi, FE, Re[a]);
+        Re[b] = fmaf(-c.hi, FE, Re[b]);
+      }
+    }
+    const double wperp = ops.w[l0] * ops.w[l1];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int enb = nbr_index(e, d, s, nx, ny, nz);
+      const double* fo = face + (((size_t)e * 6 + 2 * d + s) * NSFR_NFIELD) * NFP + line;
+      const double* fn = face + (((size_t)enb * 6 + 2 * d + 1 - s) * NSFR_NFIELD) * NFP + line;
+      const double* nf = nf_plus + (((size_t)(s ? e : enb) * 3 + d) * 3) * NFP + line;
+      const double f0 = wperp * nf[0], f1 = wperp * nf[NFP], f2 = wperp * nf[2 * NFP];
+      const Rec FoR = load_rec(fo, NFP), FnR = load_rec(fn, NFP);
+      const BNode Fo = bnode_from_rec(FoR), Fn = bnode_from_rec(FnR);
+      // face flux (EC, deviation form) and optional Roe dissipation
+      ff sr_;
+      float sm_[3], se_;
+      {
+        const ff g0 = ff_from_double(f0), g1 = ff_from_double(f1), g2 = ff_from_double(f2);
+        if (s) bulk_flux(Fo, Fn, g0, g1, g2, ref, ops, sr_, sm_, se_);
+        else bulk_flux(Fn, Fo, g0, g1, g2, ref, ops, sr_, sm_, se_);
+        if (face_kind == NSFR_FACE_EC_ROE) {
+          double D[5];
+          if (s) roe_dissipation(FoR, FnR, f0, f1, f2, ops.gamma, D);
+          else roe_dissipation(FnR, FoR, f0, f1, f2, ops.gamma, D);
+          // the dissipation enters the mass flux too: subtract u_ref, E_ref times its mass part
+          sr_ = ff_add(sr_, ff_from_double(-0.5 * D[0]));
+          const double ur[3] = {ff_to_double(ref.u0), ff_to_double(ref.u1), ff_to_double(ref.u2)};
+#pragma unroll
+          for (int k = 0; k < 3; ++k) sm_[k] -= __double2float_rn(0.5 * (D[1 + k] - ur[k] * D[0]));
+          se_ -= __double2float_rn(0.5 * (D[4] - (ref.H + (double)ref.kin) * D[0]));
+        }
+      }
+      const ff h0 = ff_from_double(0.5 * f0), h1 = ff_from_double(0.5 * f1), h2 = ff_from_double(0.5 * f2);
+      const float* tf = s ? ops.tpf : ops.tmf;
+      const float* tl = s ? ops.tplo : ops.tmlo;
+      const float sg = s ? 1.0f : -1.0f;
+      ff tr = ff{0.0f, 0.0f};
+      float tm[3] = {0.0f, 0.0f, 0.0f}, te = 0.0f;
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        const BNode A = node_at(a);
+        ff Fr;
+        float Fm[3], FE;
+        bulk_flux(A, Fo, ff_add(metric_at(a, 0), h0), ff_add(metric_at(a, 1), h1), ff_add(metric_at(a, 2), h2),
+                  ref, ops, Fr, Fm, FE);
+        const ff ta{tf[a], tl[a]};
+        const ff sta{sg * tf[a], sg * tl[a]};
+        tr = ff_fma(ta, Fr, tr);
+        Rr[a] = ff_fma(sta, Fr, Rr[a]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          tm[k] = fmaf(ta.hi, Fm[k], tm[k]);
+          Rm[a][k] = fmaf(sta.hi, Fm[k], Rm[a][k]);
+        }
+        te = fmaf(ta.hi, FE, te);
+        Re[a] = fmaf(sta.hi, FE, Re[a]);
+      }
+      const ff dr_ = ff_add(sr_, ff_neg(tr));
+      float dm[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) dm[k] = sm_[k] - tm[k];
+      const float de = se_ - te;
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        const ff sta{sg * tf[a], sg * tl[a]};
+        Rr[a] = ff_fma(sta, dr_, Rr[a]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Rm[a][k] = fmaf(sta.hi, dm[k], Rm[a][k]);
+        Re[a] = fmaf(sta.hi, de, Re[a]);
+      }
+    }
+  }
+  // directions meet in shared memory (fixed order d = 0, 1, 2)
+#pragma unroll
+  for (int dd = 0; dd < 3; ++dd) {
+    if (valid && d == dd) {
+      float* ra = Ra + (size_t)le * 6 * NV + base;
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        const int o = a * stride;
+        if (dd == 0) {
+          ra[o] = Rr[a].hi;
+          ra[NV + o] = Rr[a].lo;
+          ra[2 * NV + o] = Rm[a][0];
+          ra[3 * NV + o] = Rm[a][1];
+          ra[4 * NV + o] = Rm[a][2];
+          ra[5 * NV + o] = Re[a];
+        } else {
+          const ff s_ = ff_add(ff{ra[o], ra[NV + o]}, Rr[a]);
+          ra[o] = s_.hi;
+          ra[NV + o] = s_.lo;
+          ra[2 * NV + o] += Rm[a][0];
+          ra[3 * NV + o] += Rm[a][1];
+          ra[4 * NV + o] += Rm[a][2];
+          ra[5 * NV + o] += Re[a];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int nel = min(epb, ne - e0);
+  // R in FP64: R_m = R(F_m') + u_ref R_rho, R_E = R(F_E') + E_ref R_rho
+  // (the momentum's p_ref part needs no term back: its residual vanishes)
+  for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
+    const int lq = t / NV, node = t % NV;
+    const float* ra = Ra + (size_t)lq * 6 * NV + node;
+    const BRef rf = element_ref(Pd + (size_t)lq * 4 * NV, Pf + (size_t)lq * 25 * NV, NV, ops);
+    const double Rrho = (double)ra[0] + (double)ra[NV];
+    double* rd = Rd + (size_t)lq * 5 * NV + node;
+    rd[0] = Rrho;
+    rd[NV] = fma(ff_to_double(rf.u0), Rrho, (double)ra[2 * NV]);
+    rd[2 * NV] = fma(ff_to_double(rf.u1), Rrho, (double)ra[3 * NV]);
+    rd[3 * NV] = fma(ff_to_double(rf.u2), Rrho, (double)ra[4 * NV]);
+    rd[4 * NV] = fma(rf.H + (double)rf.kin, Rrho, (double)ra[5 * NV]);
+  }
+  __syncthreads();
+  const int total = nel * 5 * NV;
+  const size_t off = (size_t)e0 * 5 * NV;
+  if (epi == EPI_RAW) {
+    for (int t = threadIdx.x; t < total; t += blockDim.x) out[off + t] = Rd[t];
+    return;
+  }
+  // weight-adjusted inverse in FP32
+  for (int t = threadIdx.x; t < total; t += blockDim.x) Xf[t] = __double2float_rn(Rd[t]);
+  __syncthreads();
+  if (ops.has_K) {
+    for (int dd = 0; dd < 3; ++dd) {
+      rank_one_sweep_f<N>(Xf, nel, dd, true, ops);
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int lq = t / (5 * NV), node = t % NV;
+    Xf[t] *= __double2float_rn(invwj[(size_t)(e0 + lq) * NV + node]);
+  }
+  __syncthreads();
+  if (ops.has_K) {
+    for (int dd = 0; dd < 3; ++dd) {
+      rank_one_sweep_f<N>(Xf, nel, dd, false, ops);
+      __syncthreads();
+    }
+  }
+  if (epi == EPI_DUDT) {
+    for (int t = threadIdx.x; t < total; t += blockDim.x) out[off + t] = -(double)Xf[t];
+  } else {
+    const double bdt = rk.b * rk.dt, adt = rk.a_next * rk.dt;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const double k = -(double)Xf[t];
+      if (rk.last) {
+        rk.unext[off + t] = fma(bdt, k, rk.acc[off + t]);
+      } else {
+        const double u0 = rk.u0[off + t];
+        rk.acc[off + t] = fma(bdt, k, rk.first ? u0 : rk.acc[off + t]);
+        rk.unext[off + t] = fma(adt, k, u0);
+      }
+    }
+  }
+}
+
+template <int N>
+cudaError_t launch_bulk_n(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk, cudaStream_t s) {
+  constexpr int NV = N * N * N;
+  constexpr int epb = epb_for(N);
+  const int grid = (ctx->ne + epb - 1) / epb;
+  const size_t smem = (size_t)epb * NV * (9 * sizeof(double) + 31 * sizeof(float));
+  cudaError_t err =
+      cudaFuncSetAttribute(volume_bulk_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  RkArgs r = rk ? *rk : RkArgs{};
+  nsfr_prof_begin(ctx, 2, s);
+  volume_bulk_kernel<N><<<grid, threads_for(N), smem, s>>>(u, ctx->lnrec, ctx->metric, ctx->nfp_plus, ctx->face,
+                                                           ctx->invwj, ctx->ops, ctx->nx, ctx->ny, ctx->nz, ctx->ne,
+                                                           ctx->face_flux, epi, r, out, ctx->flag);
+  nsfr_prof_end(ctx, s);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t nsfr_launch_volume_bulk(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk,
+                                    cudaStream_t s) {
+  switch (ctx->n) {
+    case 2: return launch_bulk_n<2>(ctx, u, out, epi, rk, s);
+    case 3: return launch_bulk_n<3>(ctx, u, out, epi, rk, s);
+    case 4: return launch_bulk_n<4>(ctx, u, out, epi, rk, s);
+    case 5: return launch_bulk_n<5>(ctx, u, out, epi, rk, s);
+    case 6: return launch_bulk_n<6>(ctx, u, out, epi, rk, s);
+    case 7: return launch_bulk_n<7>(ctx, u, out, epi, rk, s);
+    case 8: return launch_bulk_n<8>(ctx, u, out, epi, rk, s);
+  }
+  return cudaErrorInvalidValue;
+}

@@ -1,0 +1,109 @@
+"""FP32-bulk path against the FP64 oracle.
+
+The bulk path does the flux arithmetic and contractions in FP32 (mass flux in
+float-float), keeping the log means, the entropy projection, the state and the
+reductions in FP64.  Bar: relative L2 error of du/dt over all five variables
+<= 1e-5 (the target for this mode); per-variable errors are checked loosely and
+the conservation drift is reported.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads as wl  # noqa: E402
+from oracle.operators1d import c_hu  # noqa: E402
+from oracle.problem import Problem  # noqa: E402
+from tests._pairs import oracle_metrics_abi, oracle_problem, rel_l2, state_for  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL_BULK = 1e-5
+
+
+def bulk_solver(ctrl, shape, P):
+    from paper_2312_07725_gb300 import Solver
+    S = Solver(np.ascontiguousarray(ctrl), shape, P.p, p_geo=P.p_geo, c=P.ops.c, face_flux=P.face_flux,
+               precision="fp32_bulk")
+    S.set_metrics(*oracle_metrics_abi(P))
+    return S
+
+
+CASES = [
+    (3, (4, 4, 4), "dg", "ec", "tgv"),
+    (4, (8, 8, 8), "hu", "ec", "tgv"),
+    (2, (3, 2, 5), "hu", "ec", "tgv"),
+    (5, (3, 3, 3), "hu", "ec_roe", "unit"),
+    (7, (2, 2, 2), "dg", "ec", "tgv"),
+]
+
+
+@pytest.mark.parametrize("p,shape,c_kind,face_flux,kind", CASES)
+@pytest.mark.parametrize("state", ["perturbed", "exact_ic"])
+def test_bulk_dudt_within_1e5(p, shape, c_kind, face_flux, kind, state):
+    ctrl, P = oracle_problem(shape, p, c_kind, face_flux, kind)
+    S = bulk_solver(ctrl, shape, P)
+    xyz = P.node_coords()
+    if state == "perturbed":
+        u = state_for(P, kind)
+    elif kind == "unit":
+        u = np.ascontiguousarray(wl.density_wave_state(xyz))
+    else:
+        u = np.ascontiguousarray(wl.tgv_state(xyz))
+    D_ref = P.dudt_abi(u)
+    D = np.zeros_like(u)
+    S.residual(u, D)
+    err = rel_l2(D, D_ref)
+    per = [rel_l2(D[:, k], D_ref[:, k]) if np.linalg.norm(D_ref[:, k]) > 1e-8 * np.linalg.norm(D_ref) else 0.0
+           for k in range(5)]
+    print(f"bulk p={p} {shape} {state}: rel L2 {err:.2e} per var {['%.1e' % x for x in per]}")
+    assert err < TOL_BULK
+
+
+def test_bulk_conservation_and_entropy_are_reported():
+    """Conservation (sum R) and the entropy rate in bulk mode: round-off of FP32."""
+    p, shape = 4, (4, 4, 4)
+    ctrl, P = oracle_problem(shape, p, "hu", "ec")
+    S = bulk_solver(ctrl, shape, P)
+    u = torch.from_numpy(state_for(P)).cuda()
+    d = S.entropy(u)
+    R = torch.empty_like(u)
+    S.residual_raw(u, R)
+    scale = R.abs().sum(dim=(0, 2)).cpu().numpy()
+    drift = [abs(d["sum_R"][k]) / scale[k] for k in range(5)]
+    print("bulk conservation drift per variable:", ["%.1e" % x for x in drift],
+          "entropy rate / scale: %.1e" % (abs(d["entropy_rate"]) / d["entropy_rate_scale"]))
+    assert max(drift) < 1e-5
+    assert abs(d["entropy_rate"]) < 1e-5 * d["entropy_rate_scale"]
+
+
+def test_bulk_at_full_size_sampled():
+    """64^3 elements at p = 4 (the benchmark size): sampled 4^3 blocks against the oracle
+    on 6^3 patches, oracle metric terms injected for the patch."""
+    from paper_2312_07725_gb300 import Solver
+    NE, p = 64, 4
+    ctrl = wl.tgv_mesh(NE, p)
+    S = Solver(ctrl, (NE,) * 3, p, c=c_hu(p), precision="fp32_bulk")
+    from oracle import geometry
+    from oracle.operators1d import Ops1D
+    X = geometry.node_coordinates(ctrl, p, Ops1D(p))
+    u = np.ascontiguousarray(wl.tgv_state(np.ascontiguousarray(np.moveaxis(X, 0, 1).reshape(NE ** 3, 3, -1))))
+    C, J, Cf = S.metrics()
+    for corner in [(0, 0, 0), (30, 61, 17)]:
+        rng = [(np.arange(-1, 5) + e0) % NE for e0 in corner]
+        ez, ey, ex = np.meshgrid(rng[2], rng[1], rng[0], indexing="ij")
+        idx = (ex + NE * (ey + NE * ez)).ravel()
+        P = Problem(ctrl[idx], (6, 6, 6), p, c=c_hu(p))
+        inner = np.zeros((6, 6, 6), bool)
+        inner[1:5, 1:5, 1:5] = True
+        inner = inner.ravel()
+        C2, J2, Cf2 = C.copy(), J.copy(), Cf.copy()
+        C2[idx], J2[idx], Cf2[idx] = oracle_metrics_abi(P)
+        S.set_metrics(C2, J2, Cf2)
+        ud = torch.from_numpy(u).cuda()
+        D = torch.empty_like(ud)
+        S.residual(ud, D)
+        torch.cuda.synchronize()
+        Dref = P.dudt_abi(u[idx])[inner]
+        err = rel_l2(D.cpu().numpy()[idx[inner]], Dref)
+        print(f"bulk 64^3 block {corner}: rel L2 {err:.2e}")
+        assert err < TOL_BULK
