@@ -147,7 +147,9 @@ nsfr_status nsfr_entropy(nsfr_ctx* ctx, const double* u, double* out, void* stre
  *            control points; skipped when x_bar is NULL).
  *   u, dudt_bar, u_bar  device, [N_e][5][n^3] FP64.
  *   x_bar               device or NULL, [N_e][(p_geo+1)^3][3] FP64.
- * FP64 contexts only (NSFR_ERR_STATE otherwise).
+ * FP64 contexts with the EC face flux only (NSFR_ERR_STATE otherwise).  Runs
+ * the face-state pass of u (and, for x_bar, the residual R(u)) first;
+ * asynchronous on the stream.
  */
 nsfr_status nsfr_vjp(nsfr_ctx* ctx, const double* u, const double* dudt_bar, double* u_bar,
                      double* x_bar, void* stream);
@@ -178,6 +180,14 @@ nsfr_status nsfr_get_metrics(nsfr_ctx* ctx, double* C, double* J, double* Cf, vo
  * x_bar are not changed.
  */
 nsfr_status nsfr_set_metrics(nsfr_ctx* ctx, const double* C, const double* J, const double* Cf, void* stream);
+
+/*
+ * nsfr_quadrature -- W J at the GL nodes, [N_e][n^3] (host or device): the
+ * physical quadrature weights, so that sum_i (W J)_i f_i integrates f over the
+ * domain (used for functionals such as the kinetic energy, and for the L2
+ * error of Sec. "Manufactured Solution Convergence").
+ */
+nsfr_status nsfr_quadrature(nsfr_ctx* ctx, double* wj, void* stream);
 
 /* nsfr_info -- sizes: out[0]=N_e, [1]=p, [2]=n^3, [3]=p_geo, [4]=precision. */
 nsfr_status nsfr_info(const nsfr_ctx* ctx, long long* out);

@@ -56,7 +56,8 @@ void prof_free(nsfr_ctx* c) {
 
 void free_all(nsfr_ctx* c) {
   double* dbl[] = {c->ctrl, c->metric, c->J, c->invwj, c->wj, c->nfp_plus, c->xyz, c->face, c->lnrec,
-                   c->ustage, c->acc, c->rtmp, c->hbuf_in, c->hbuf_out, c->red};
+                   c->ustage, c->acc, c->rtmp, c->hbuf_in, c->hbuf_out, c->red,
+                   c->vjp_fown, c->vjp_fnbr, c->vjp_nfbar, c->vjp_mbar, c->vjp_jbar};
   for (double* p : dbl)
     if (p) cudaFree(p);
   if (c->metric32) cudaFree(c->metric32);
@@ -328,9 +329,25 @@ nsfr_status nsfr_vjp(nsfr_ctx* ctx, const double* u, const double* dudt_bar, dou
                      void* stream) {
   if (!ctx) return NSFR_ERR_ARG;
   if (ctx->precision != NSFR_FP64) return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp needs an FP64 context");
+  if (ctx->face_flux != NSFR_FACE_EC) return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp supports the EC face flux");
   if (!u || !dudt_bar || !u_bar) return fail(ctx, NSFR_ERR_ARG, "NULL buffer");
+  if (!is_device_ptr(u) || !is_device_ptr(dudt_bar) || !is_device_ptr(u_bar) || (x_bar && !is_device_ptr(x_bar)))
+    return fail(ctx, NSFR_ERR_ARG, "nsfr_vjp takes device buffers");
   cudaStream_t s = (cudaStream_t)stream;
   ctx->last_stream = s;
+  const size_t ne = ctx->ne, nv = ctx->nv, nfp = ctx->nfp;
+  if (!ctx->vjp_fown) {
+    CK(dalloc(&ctx->vjp_fown, ne * 30 * nfp), "cudaMalloc(vjp)");
+    CK(dalloc(&ctx->vjp_fnbr, ne * 30 * nfp), "cudaMalloc(vjp)");
+    CK(dalloc(&ctx->vjp_nfbar, ne * 18 * nfp), "cudaMalloc(vjp)");
+    CK(dalloc(&ctx->vjp_mbar, ne * 9 * nv), "cudaMalloc(vjp)");
+    CK(dalloc(&ctx->vjp_jbar, ne * nv), "cudaMalloc(vjp)");
+  }
+  if (!ctx->rtmp) CK(dalloc(&ctx->rtmp, state_count(ctx)), "cudaMalloc(rtmp)");
+  CK(cudaMemsetAsync(ctx->vjp_mbar, 0, ne * 9 * nv * sizeof(double), s), "cudaMemsetAsync");
+  CK(cudaMemsetAsync(ctx->vjp_jbar, 0, ne * nv * sizeof(double), s), "cudaMemsetAsync");
+  CK(nsfr_launch_face_states(ctx, u, s), "face_state_kernel");
+  if (x_bar) CK(nsfr_launch_volume(ctx, u, ctx->rtmp, EPI_RAW, nullptr, s), "volume_kernel(raw)");
   CK(nsfr_launch_vjp(ctx, u, dudt_bar, u_bar, x_bar, s), "vjp kernels");
   return NSFR_OK;
 }
@@ -366,6 +383,15 @@ nsfr_status nsfr_set_metrics(nsfr_ctx* ctx, const double* C, const double* J, co
   CK(cudaMemcpyAsync(ctx->nfp_plus, Cf, ne * 9 * nfp * sizeof(double), cudaMemcpyDefault, s), "copy Cf");
   CK(nsfr_launch_jacobian_derived(ctx, s), "jacobian_derived_kernel");
   return read_flag(ctx, s);
+}
+
+nsfr_status nsfr_quadrature(nsfr_ctx* ctx, double* wj, void* stream) {
+  if (!ctx) return NSFR_ERR_ARG;
+  if (!wj) return fail(ctx, NSFR_ERR_ARG, "NULL buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(wj, ctx->wj, (size_t)ctx->ne * ctx->nv * sizeof(double), cudaMemcpyDefault, s), "copy wJ");
+  CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  return NSFR_OK;
 }
 
 nsfr_status nsfr_info(const nsfr_ctx* ctx, long long* out) {

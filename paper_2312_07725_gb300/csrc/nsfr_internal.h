@@ -83,6 +83,12 @@ struct nsfr_ctx {
   double* ustage = nullptr;   // [ne][5][nv]
   double* acc = nullptr;      // [ne][5][nv]
   double* rtmp = nullptr;     // [ne][5][nv] (diagnostics / VJP scratch)
+  // VJP scratch (allocated by the first nsfr_vjp call)
+  double* vjp_fown = nullptr;  // [ne][6][5][nfp] face-state cotangents from the element itself
+  double* vjp_fnbr = nullptr;  // [ne][6][5][nfp] cotangents for the neighbour's face state
+  double* vjp_nfbar = nullptr; // [ne][6][3][nfp] face-row cotangents, per face of the element
+  double* vjp_mbar = nullptr;  // [ne][9][nv] volume metric-row cotangents
+  double* vjp_jbar = nullptr;  // [ne][nv] Jacobian cotangents
   double* hbuf_in = nullptr;  // staging for host pointers [ne][5][nv]
   double* hbuf_out = nullptr;
   double* red = nullptr;      // reduction scratch

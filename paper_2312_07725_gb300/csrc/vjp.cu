@@ -1,6 +1,721 @@
-// Reverse-mode (VJP) kernels of the residual: not built yet in this file.
-#include "nsfr_internal.h"
+// Reverse-mode (VJP) kernels of du/dt(u; x), written by hand.
+//
+// du/dt = -A R(u; C) with A = Pi~ (W J)^{-1} Pi~^T (Eq. weight-adj ESFR mass)
+// symmetric, so for a cotangent rbar:
+//   Rbar = -A rbar,  Jbar_i = -(sum_k zbar_ki y_ki) / (w_i J_i^2),  zbar = -Pi~^T rbar, y = Pi~^T R.
+// R (Eq. NSFR, sum-factorised) is reversed term by term:
+//   volume pair  R_a += c F, R_b -= c F           -> Fbar = c (Rbar_a - Rbar_b)
+//   hybrid       R_a += s w t_a (phi_a + f* - sum_b t_b phi_b)
+//                -> f*bar = sum_a s w t_a Rbar_a =: rho,  phi_a bar = s w t_a Rbar_a - t_a rho
+// and each two-point flux F(A, B; n) is reversed to cotangents of the primitive
+// records (rho, u, beta) of both states and of n.  Face states are entropy
+// projections u~_f = u(t_s . v(u)) (Sec. "Nonlinearly Stable Flux
+// Reconstruction"); their cotangents are gathered per face (own element and
+// neighbour in separate slots, no atomics) and mapped back through u(v), the
+// extrapolation and v(u) by vjp_face_kernel.  The metric cotangents (volume
+// rows, the shared face rows, J) are mapped to the control points by
+// vjp_metric_kernel, the reverse of the conservative-curl construction
+// (Sec. "Computational Space", Eq. GCL).  FP64 throughout; EC face flux.
+#include "kernel_common.cuh"
+#include "physics.cuh"
 
-cudaError_t nsfr_launch_vjp(nsfr_ctx*, const double*, const double*, double*, double*, cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace {
+using namespace nsfr_k;
+
+struct PR {
+  double r, u0, u1, u2, b;  // rho, velocity, beta = rho / (2p)
+};
+
+// log mean L(a, b) and its partial derivatives (series branch: L = (a+b) G(u)/2,
+// u = f^2, f = (a-b)/(a+b), G = f/atanh f; otherwise (a-b)/(ln a - ln b))
+__device__ __forceinline__ void logmean_grad(double a, double b, double& L, double& La, double& Lb) {
+  const double s = a + b, d = a - b;
+  const double f = d / s, u = f * f;
+  if (u < NSFR_LM_EPS) {
+    const double G = 1.0 + u * (-1.0 / 3.0 + u * (-4.0 / 45.0 + u * (-44.0 / 945.0)));
+    const double Gp = -1.0 / 3.0 + u * (-8.0 / 45.0 + u * (-132.0 / 945.0));
+    L = 0.5 * s * G;
+    La = 0.5 * G + 2.0 * Gp * f * b / s;
+    Lb = 0.5 * G - 2.0 * Gp * f * a / s;
+  } else {
+    const double D = log(a) - log(b);
+    L = d / D;
+    La = (1.0 - L / a) / D;
+    Lb = (L / b - 1.0) / D;
+  }
+}
+
+// reverse of F = f_s(A, B) . n (Chandrashekar): accumulates into Ab, Bb, nb
+__device__ __forceinline__ void ec_flux_vjp(const PR& A, const PR& B, double n0, double n1, double n2, double gamma,
+                                            const double Fb[5], PR& Ab, PR& Bb, double nb[3]) {
+  double rl, rla, rlb, bl, bla, blb;
+  logmean_grad(A.r, B.r, rl, rla, rlb);
+  logmean_grad(A.b, B.b, bl, bla, blb);
+  const double rm = 0.5 * (A.r + B.r), bm = 0.5 * (A.b + B.b);
+  const double v[3] = {0.5 * (A.u0 + B.u0), 0.5 * (A.u1 + B.u1), 0.5 * (A.u2 + B.u2)};
+  const double n[3] = {n0, n1, n2};
+  const double q2b = 0.5 * (A.u0 * A.u0 + A.u1 * A.u1 + A.u2 * A.u2 + B.u0 * B.u0 + B.u1 * B.u1 + B.u2 * B.u2);
+  const double ph = rm / (2.0 * bm);
+  const double un = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+  const double F0 = rl * un;
+  double Fm[3];
+  for (int c = 0; c < 3; ++c) Fm[c] = F0 * v[c] + ph * n[c];
+  const double h = 1.0 / (2.0 * (gamma - 1.0) * bl);
+  // reverse
+  const double t4 = Fb[4];
+  double vb[3], Fmb[3];
+  double F0b = Fb[0] + t4 * (h - 0.5 * q2b);
+  const double hb = t4 * F0;
+  const double q2bb = -0.5 * t4 * F0;
+  for (int c = 0; c < 3; ++c) {
+    vb[c] = t4 * Fm[c];
+    Fmb[c] = Fb[1 + c] + t4 * v[c];
+  }
+  double phb = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    F0b += Fmb[c] * v[c];
+    vb[c] += F0 * Fmb[c];
+    phb += Fmb[c] * n[c];
+    nb[c] += ph * Fmb[c];
+  }
+  const double rlb_ = F0b * un;
+  const double unb = F0b * rl;
+  for (int c = 0; c < 3; ++c) {
+    vb[c] += unb * n[c];
+    nb[c] += unb * v[c];
+  }
+  const double blb_ = -hb * h / bl;
+  const double rmb = phb / (2.0 * bm);
+  const double bmb = -phb * ph / bm;
+  Ab.u0 += 0.5 * vb[0] + q2bb * A.u0;
+  Ab.u1 += 0.5 * vb[1] + q2bb * A.u1;
+  Ab.u2 += 0.5 * vb[2] + q2bb * A.u2;
+  Bb.u0 += 0.5 * vb[0] + q2bb * B.u0;
+  Bb.u1 += 0.5 * vb[1] + q2bb * B.u1;
+  Bb.u2 += 0.5 * vb[2] + q2bb * B.u2;
+  Ab.r += 0.5 * rmb + rlb_ * rla;
+  Bb.r += 0.5 * rmb + rlb_ * rlb;
+  Ab.b += 0.5 * bmb + blb_ * bla;
+  Bb.b += 0.5 * bmb + blb_ * blb;
+}
+
+__device__ __forceinline__ PR pr_from_conserved(const double* U, int stride, double gamma) {
+  PR a;
+  a.r = U[0];
+  const double ir = 1.0 / a.r;
+  a.u0 = U[stride] * ir;
+  a.u1 = U[2 * stride] * ir;
+  a.u2 = U[3 * stride] * ir;
+  const double q2 = a.u0 * a.u0 + a.u1 * a.u1 + a.u2 * a.u2;
+  const double p = (gamma - 1.0) * (U[4 * stride] - 0.5 * a.r * q2);
+  a.b = 0.5 * a.r / p;
+  return a;
+}
+
+// (rho, u, beta) cotangent plus a direct pressure cotangent -> conserved cotangent
+__device__ __forceinline__ void conserved_bar(const PR& a, double gamma, const PR& pb, double pbar_direct,
+                                              double Ub[5]) {
+  const double q2 = a.u0 * a.u0 + a.u1 * a.u1 + a.u2 * a.u2;
+  const double p = 0.5 * a.r / a.b;
+  double rb = pb.r + pb.b / (2.0 * p);
+  const double pbar = pbar_direct - pb.b * a.b / p;
+  // p = (gamma-1)(E - |m|^2/(2 rho))
+  const double g1 = gamma - 1.0;
+  const double Eb = g1 * pbar;
+  double mb0 = -g1 * pbar * a.u0, mb1 = -g1 * pbar * a.u1, mb2 = -g1 * pbar * a.u2;
+  rb += g1 * pbar * 0.5 * q2;
+  // u = m / rho
+  mb0 += pb.u0 / a.r;
+  mb1 += pb.u1 / a.r;
+  mb2 += pb.u2 / a.r;
+  rb -= (pb.u0 * a.u0 + pb.u1 * a.u1 + pb.u2 * a.u2) / a.r;
+  Ub[0] = rb;
+  Ub[1] = mb0;
+  Ub[2] = mb1;
+  Ub[3] = mb2;
+  Ub[4] = Eb;
+}
+
+__device__ __forceinline__ void entropy_vars(const PR& a, double gamma, double v[5]) {
+  const double q2 = a.u0 * a.u0 + a.u1 * a.u1 + a.u2 * a.u2;
+  const double p = 0.5 * a.r / a.b;
+  const double s = log(p) - gamma * log(a.r);
+  v[0] = (gamma - s) / (gamma - 1.0) - a.b * q2;
+  v[1] = 2.0 * a.b * a.u0;
+  v[2] = 2.0 * a.b * a.u1;
+  v[3] = 2.0 * a.b * a.u2;
+  v[4] = -2.0 * a.b;
+}
+
+// face state from entropy variables (forward) as a primitive record
+__device__ __forceinline__ PR pr_from_entropy(const double v[5], double gamma) {
+  PR a;
+  const double v5 = v[4];
+  a.b = -0.5 * v5;
+  a.u0 = -v[1] / v5;
+  a.u1 = -v[2] / v5;
+  a.u2 = -v[3] / v5;
+  const double vm2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+  const double lr = -gamma / (gamma - 1.0) + v[0] - vm2 / (2.0 * v5) - log(-v5) / (gamma - 1.0);
+  a.r = exp(lr);
+  return a;
+}
+
+// reverse of pr_from_entropy: (rho, u, beta) cotangent -> v cotangent
+__device__ __forceinline__ void entropy_bar_from_pr(const double v[5], const PR& a, double gamma, const PR& pb,
+                                                    double vb[5]) {
+  const double v5 = v[4];
+  const double vm2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+  vb[0] = 0.0;
+  vb[1] = vb[2] = vb[3] = 0.0;
+  vb[4] = -0.5 * pb.b;
+  const double ub[3] = {pb.u0, pb.u1, pb.u2};
+  for (int c = 0; c < 3; ++c) {
+    vb[1 + c] += -ub[c] / v5;
+    vb[4] += ub[c] * v[1 + c] / (v5 * v5);
+  }
+  const double lb = pb.r * a.r;
+  vb[0] += lb;
+  for (int c = 0; c < 3; ++c) vb[1 + c] += -lb * v[1 + c] / v5;
+  vb[4] += lb * (vm2 / (2.0 * v5 * v5) - 1.0 / ((gamma - 1.0) * v5));
+}
+
+// reverse of entropy_vars: v cotangent -> (rho, u, beta) cotangent and direct p cotangent
+__device__ __forceinline__ void pr_bar_from_entropy_bar(const PR& a, double gamma, const double vb[5], PR& pb,
+                                                        double& pbar) {
+  const double q2 = a.u0 * a.u0 + a.u1 * a.u1 + a.u2 * a.u2;
+  const double p = 0.5 * a.r / a.b;
+  const double u[3] = {a.u0, a.u1, a.u2};
+  double bb = -2.0 * vb[4] - vb[0] * q2;
+  double ubv[3];
+  for (int c = 0; c < 3; ++c) {
+    bb += 2.0 * vb[1 + c] * u[c];
+    ubv[c] = 2.0 * a.b * vb[1 + c] - 2.0 * a.b * u[c] * vb[0];
+  }
+  const double sb = -vb[0] / (gamma - 1.0);
+  pbar = sb / p;
+  pb.r = -gamma * sb / a.r;
+  pb.u0 = ubv[0];
+  pb.u1 = ubv[1];
+  pb.u2 = ubv[2];
+  pb.b = bb;
+}
+
+__device__ __forceinline__ PR pr_load(const double* P, int stride) {
+  PR a;
+  a.r = P[0];
+  a.u0 = P[stride];
+  a.u1 = P[2 * stride];
+  a.u2 = P[3 * stride];
+  a.b = P[4 * stride];
+  return a;
+}
+
+// face record (K1 layout) -> primitive record
+__device__ __forceinline__ PR pr_from_face(const double* f, int nfp) {
+  const Rec R = load_rec(f, nfp);
+  PR a;
+  a.r = R.r;
+  a.u0 = 2.0 * R.u0;
+  a.u1 = 2.0 * R.u1;
+  a.u2 = 2.0 * R.u2;
+  a.b = 0.5 * R.b2;
+  return a;
+}
+
+// --------------------------------------------------------------------------
+// volume reverse: one thread per line, like volume_kernel
+// --------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(threads_for(N), 1)
+    vjp_volume_kernel(const double* __restrict__ u, const double* __restrict__ rbar, const double* __restrict__ Rfwd,
+                      const double* __restrict__ metric, const double* __restrict__ nf_plus,
+                      const double* __restrict__ face, const double* __restrict__ wj, OpsGL ops, int nx, int ny,
+                      int nz, int ne, double* __restrict__ ubar, double* __restrict__ fbar_own,
+                      double* __restrict__ fbar_nbr, double* __restrict__ nfbar, double* __restrict__ mbar,
+                      double* __restrict__ Jbar) {
+  constexpr int NV = N * N * N, NFP = N * N, NL = 3 * NFP;
+  extern __shared__ double sm[];
+  const int epb = blockDim.x / NL;
+  const int e0 = blockIdx.x * epb;
+  double* P = sm;                          // [epb][5][NV] primitive records
+  double* Rb = P + (size_t)epb * 5 * NV;   // [epb][5][NV] Rbar
+  double* Pb = Rb + (size_t)epb * 5 * NV;  // [epb][5][NV] record cotangents
+  double* Y = Pb + (size_t)epb * 5 * NV;   // [epb][5][NV] Pi~^T R (for Jbar)
+  const double g = ops.gamma;
+  const int nel = min(epb, ne - e0);
+  const int total = nel * 5 * NV;
+
+  for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
+    const int le = t / NV, node = t % NV;
+    const PR a = pr_from_conserved(u + (size_t)(e0 + le) * 5 * NV + node, NV, g);
+    double* p = P + (size_t)le * 5 * NV + node;
+    p[0] = a.r;
+    p[NV] = a.u0;
+    p[2 * NV] = a.u1;
+    p[3 * NV] = a.u2;
+    p[4 * NV] = a.b;
+  }
+  // zbar = -Pi~^T rbar ; (y = Pi~^T R) ; Rbar = Pi~ D zbar with D = 1/(wJ)
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    Rb[t] = -rbar[(size_t)e0 * 5 * NV + t];
+    if (Rfwd) Y[t] = Rfwd[(size_t)e0 * 5 * NV + t];
+  }
+  __syncthreads();
+  auto sweep = [&](double* X, int d, bool transpose) {
+    const int st = (d == 0) ? 1 : (d == 1 ? N : N * N);
+    for (int t = threadIdx.x; t < nel * 5 * NFP; t += blockDim.x) {
+      const int line = t % NFP, lk = t / NFP;
+      int base, stride;
+      line_geometry<N>(d, line % N, line / N, base, stride);
+      double* x = X + (size_t)lk * NV + base;
+      double dot = 0.0;
+      for (int a = 0; a < N; ++a) dot = fma(transpose ? ops.hv[a] : ops.gv[a], x[a * st], dot);
+      for (int a = 0; a < N; ++a) x[a * st] = fma(-(transpose ? ops.gv[a] : ops.hv[a]), dot, x[a * st]);
+    }
+  };
+  if (ops.has_K) {
+    for (int dd = 0; dd < 3; ++dd) {
+      sweep(Rb, dd, true);
+      if (Rfwd) sweep(Y, dd, true);
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
+    const int le = t / NV, node = t % NV;
+    const double wJ = wj[(size_t)(e0 + le) * NV + node];
+    double db = 0.0;
+    for (int k = 0; k < 5; ++k) {
+      const size_t i = (size_t)(le * 5 + k) * NV + node;
+      db += Rb[i] * Y[i];
+      Rb[i] /= wJ;
+    }
+    // D = 1/(w J) -> Jbar = Dbar * dD/dJ = -Dbar / (w J^2)
+    if (Rfwd) {
+      const int i = node % N, j = (node / N) % N, k = node / (N * N);
+      const double w3 = ops.w[i] * ops.w[j] * ops.w[k];
+      const double J = wJ / w3;
+      Jbar[(size_t)(e0 + le) * NV + node] += -db / (wJ * J);
+    }
+  }
+  __syncthreads();
+  if (ops.has_K) {
+    for (int dd = 0; dd < 3; ++dd) {
+      sweep(Rb, dd, false);
+      __syncthreads();
+    }
+  }
+
+  // line phase
+  const int le = threadIdx.x / NL, l = threadIdx.x % NL, e = e0 + le;
+  const bool valid = le < nel;
+  const int d = l / NFP, line = l % NFP, l0 = line % N, l1 = line / N;
+  int base, stride;
+  line_geometry<N>(d, l0, l1, base, stride);
+  PR ab[N];
+  double mb[N][3];
+  for (int a = 0; a < N; ++a) {
+    ab[a] = PR{0, 0, 0, 0, 0};
+    mb[a][0] = mb[a][1] = mb[a][2] = 0.0;
+  }
+  if (valid) {
+    const double* Pe = P + (size_t)le * 5 * NV + base;
+    const double* Re = Rb + (size_t)le * 5 * NV + base;
+    const double* Me = metric + ((size_t)e * 9 + 3 * d) * NV + base;
+    const double wperp = ops.w[l0] * ops.w[l1];
+    for (int a = 0; a < N; ++a) {
+      const PR A = pr_load(Pe + a * stride, NV);
+      for (int b = a + 1; b < N; ++b) {
+        const PR B = pr_load(Pe + b * stride, NV);
+        const double c = wperp * ops.S1[a * N + b];
+        double Fb[5];
+        for (int k = 0; k < 5; ++k) Fb[k] = c * (Re[k * NV + a * stride] - Re[k * NV + b * stride]);
+        double nb[3] = {0.0, 0.0, 0.0};
+        const double n0 = 0.5 * (Me[a * stride] + Me[b * stride]);
+        const double n1 = 0.5 * (Me[NV + a * stride] + Me[NV + b * stride]);
+        const double n2 = 0.5 * (Me[2 * NV + a * stride] + Me[2 * NV + b * stride]);
+        ec_flux_vjp(A, B, n0, n1, n2, g, Fb, ab[a], ab[b], nb);
+        for (int c2 = 0; c2 < 3; ++c2) {
+          mb[a][c2] += 0.5 * nb[c2];
+          mb[b][c2] += 0.5 * nb[c2];
+        }
+      }
+    }
+    for (int s = 0; s < 2; ++s) {
+      const int f = 2 * d + s;
+      const int enb = nbr_index(e, d, s, nx, ny, nz);
+      const PR Fo = pr_from_face(face + (((size_t)e * 6 + f) * NSFR_NFIELD) * NFP + line, NFP);
+      const PR Fn = pr_from_face(face + (((size_t)enb * 6 + 2 * d + 1 - s) * NSFR_NFIELD) * NFP + line, NFP);
+      const double* nf = nf_plus + (((size_t)(s ? e : enb) * 3 + d) * 3) * NFP + line;
+      const double f0 = nf[0], f1 = nf[NFP], f2 = nf[2 * NFP];
+      const double* t = s ? ops.tp : ops.tm;
+      const double sw = (s ? 1.0 : -1.0) * wperp;
+      double rho[5] = {0, 0, 0, 0, 0};
+      for (int a = 0; a < N; ++a)
+        for (int k = 0; k < 5; ++k) rho[k] += sw * t[a] * Re[k * NV + a * stride];
+      PR fob{0, 0, 0, 0, 0}, fnb{0, 0, 0, 0, 0};
+      double nfb[3] = {0.0, 0.0, 0.0};
+      // face flux f* = F(L, R; n_f)
+      if (s) ec_flux_vjp(Fo, Fn, f0, f1, f2, g, rho, fob, fnb, nfb);
+      else ec_flux_vjp(Fn, Fo, f0, f1, f2, g, rho, fnb, fob, nfb);
+      // hybrid terms
+      for (int a = 0; a < N; ++a) {
+        const PR A = pr_load(Pe + a * stride, NV);
+        double Fb[5];
+        for (int k = 0; k < 5; ++k) Fb[k] = sw * t[a] * Re[k * NV + a * stride] - t[a] * rho[k];
+        double nb[3] = {0.0, 0.0, 0.0};
+        ec_flux_vjp(A, Fo, 0.5 * (Me[a * stride] + f0), 0.5 * (Me[NV + a * stride] + f1),
+                    0.5 * (Me[2 * NV + a * stride] + f2), g, Fb, ab[a], fob, nb);
+        for (int c2 = 0; c2 < 3; ++c2) {
+          mb[a][c2] += 0.5 * nb[c2];
+          nfb[c2] += 0.5 * nb[c2];
+        }
+      }
+      double* fo = fbar_own + (((size_t)e * 6 + f) * 5) * NFP + line;
+      double* fn = fbar_nbr + (((size_t)e * 6 + f) * 5) * NFP + line;
+      fo[0] = fob.r;
+      fo[NFP] = fob.u0;
+      fo[2 * NFP] = fob.u1;
+      fo[3 * NFP] = fob.u2;
+      fo[4 * NFP] = fob.b;
+      fn[0] = fnb.r;
+      fn[NFP] = fnb.u0;
+      fn[2 * NFP] = fnb.u1;
+      fn[3 * NFP] = fnb.u2;
+      fn[4 * NFP] = fnb.b;
+      if (mbar) {
+        double* nfo = nfbar + (((size_t)e * 6 + f) * 3) * NFP + line;
+        for (int c2 = 0; c2 < 3; ++c2) nfo[c2 * NFP] = nfb[c2];
+      }
+    }
+    if (mbar)
+      for (int a = 0; a < N; ++a)
+        for (int c2 = 0; c2 < 3; ++c2) mbar[((size_t)e * 9 + 3 * d + c2) * NV + base + a * stride] += mb[a][c2];
+  }
+  // record cotangents meet in shared memory (d = 0, 1, 2)
+  for (int dd = 0; dd < 3; ++dd) {
+    if (valid && d == dd) {
+      double* pb = Pb + (size_t)le * 5 * NV + base;
+      for (int a = 0; a < N; ++a) {
+        const double x[5] = {ab[a].r, ab[a].u0, ab[a].u1, ab[a].u2, ab[a].b};
+        for (int k = 0; k < 5; ++k) {
+          if (dd == 0) pb[k * NV + a * stride] = x[k];
+          else pb[k * NV + a * stride] += x[k];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
+    const int lq = t / NV, node = t % NV;
+    const PR a = pr_load(P + (size_t)lq * 5 * NV + node, NV);
+    const PR pb = pr_load(Pb + (size_t)lq * 5 * NV + node, NV);
+    double Ub[5];
+    conserved_bar(a, g, pb, 0.0, Ub);
+    double* ub = ubar + (size_t)(e0 + lq) * 5 * NV + node;
+    for (int k = 0; k < 5; ++k) ub[k * NV] += Ub[k];
+  }
+}
+
+// --------------------------------------------------------------------------
+// face reverse: face-state cotangents -> volume state cotangents
+// --------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(threads_for(N), 1)
+    vjp_face_kernel(const double* __restrict__ u, const double* __restrict__ fbar_own,
+                    const double* __restrict__ fbar_nbr, OpsGL ops, int nx, int ny, int nz, int ne,
+                    double* __restrict__ ubar) {
+  constexpr int NV = N * N * N, NFP = N * N, NL = 3 * NFP;
+  extern __shared__ double sm[];
+  const int epb = blockDim.x / NL;
+  const int e0 = blockIdx.x * epb;
+  double* V = sm;                         // [epb][5][NV] entropy variables
+  double* Vb = V + (size_t)epb * 5 * NV;  // [epb][5][NV] their cotangents
+  const double g = ops.gamma;
+  const int nel = min(epb, ne - e0);
+  for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
+    const int le = t / NV, node = t % NV;
+    const PR a = pr_from_conserved(u + (size_t)(e0 + le) * 5 * NV + node, NV, g);
+    double v[5];
+    entropy_vars(a, g, v);
+    for (int k = 0; k < 5; ++k) V[(size_t)(le * 5 + k) * NV + node] = v[k];
+  }
+  __syncthreads();
+  const int le = threadIdx.x / NL, l = threadIdx.x % NL, e = e0 + le;
+  const bool valid = le < nel;
+  const int d = l / NFP, line = l % NFP;
+  int base, stride;
+  line_geometry<N>(d, line % N, line / N, base, stride);
+  double vbl[N][5];
+  for (int a = 0; a < N; ++a)
+    for (int k = 0; k < 5; ++k) vbl[a][k] = 0.0;
+  if (valid) {
+    const double* Ve = V + (size_t)le * 5 * NV + base;
+    for (int s = 0; s < 2; ++s) {
+      const int f = 2 * d + s;
+      const int enb = nbr_index(e, d, s, nx, ny, nz);
+      const double* t = s ? ops.tp : ops.tm;
+      double vf[5];
+      for (int k = 0; k < 5; ++k) {
+        double x = 0.0;
+        for (int a = 0; a < N; ++a) x += t[a] * Ve[k * NV + a * stride];
+        vf[k] = x;
+      }
+      const PR fa = pr_from_entropy(vf, g);
+      const double* o = fbar_own + (((size_t)e * 6 + f) * 5) * NFP + line;
+      const double* q = fbar_nbr + (((size_t)enb * 6 + 2 * d + 1 - s) * 5) * NFP + line;
+      const PR pb{o[0] + q[0], o[NFP] + q[NFP], o[2 * NFP] + q[2 * NFP], o[3 * NFP] + q[3 * NFP],
+                  o[4 * NFP] + q[4 * NFP]};
+      double vfb[5];
+      entropy_bar_from_pr(vf, fa, g, pb, vfb);
+      for (int a = 0; a < N; ++a)
+        for (int k = 0; k < 5; ++k) vbl[a][k] += t[a] * vfb[k];
+    }
+  }
+  for (int dd = 0; dd < 3; ++dd) {
+    if (valid && d == dd) {
+      double* vb = Vb + (size_t)le * 5 * NV + base;
+      for (int a = 0; a < N; ++a)
+        for (int k = 0; k < 5; ++k) {
+          if (dd == 0) vb[k * NV + a * stride] = vbl[a][k];
+          else vb[k * NV + a * stride] += vbl[a][k];
+        }
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
+    const int lq = t / NV, node = t % NV;
+    const PR a = pr_from_conserved(u + (size_t)(e0 + lq) * 5 * NV + node, NV, g);
+    double vb[5];
+    for (int k = 0; k < 5; ++k) vb[k] = Vb[(size_t)(lq * 5 + k) * NV + node];
+    PR pb;
+    double pbar;
+    pr_bar_from_entropy_bar(a, g, vb, pb, pbar);
+    double Ub[5];
+    conserved_bar(a, g, pb, pbar, Ub);
+    double* ub = ubar + (size_t)(e0 + lq) * 5 * NV + node;
+    for (int k = 0; k < 5; ++k) ub[k * NV] += Ub[k];
+  }
+}
+
+// --------------------------------------------------------------------------
+// metric reverse: (C bar, shared face-row bar, J bar) -> control-point bar
+// --------------------------------------------------------------------------
+__device__ void msweep(const double* A, bool transpose, int rows, int k, int m, const double* in, double* out, int d,
+                       int ex, int ey, int ez) {
+  // forward: out(ext with m along d) = A (m x k) applied along d; transpose: A^T (k x m)
+  int ox = ex, oy = ey, oz = ez;
+  if (d == 0) ox = m;
+  if (d == 1) oy = m;
+  if (d == 2) oz = m;
+  const int total = ox * oy * oz;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int x = t % ox, y = (t / ox) % oy, z = t / (ox * oy);
+    double s = 0.0;
+    for (int b = 0; b < k; ++b) {
+      int xi = x, yi = y, zi = z, r;
+      if (d == 0) { r = x; xi = b; }
+      else if (d == 1) { r = y; yi = b; }
+      else { r = z; zi = b; }
+      const double a = transpose ? A[b * rows + r] : A[r * rows + b];
+      s += a * in[xi + ex * (yi + ey * zi)];
+    }
+    out[t] = s;
+  }
+  __syncthreads();
+}
+
+// apply A (m x k, row stride rs) along all three directions: (k,k,k) -> (m,m,m)
+__device__ void msweep3(const double* A, bool tr, int rs, int k, int m, const double* in, double* out, double* t1,
+                        double* t2) {
+  msweep(A, tr, rs, k, m, in, t1, 0, k, k, k);
+  msweep(A, tr, rs, k, m, t1, t2, 1, m, k, k);
+  msweep(A, tr, rs, k, m, t2, out, 2, m, m, k);
+}
+
+__global__ void vjp_metric_kernel(const double* __restrict__ ctrl, OpsGeo g, const double* __restrict__ mbar,
+                                  const double* __restrict__ nfbar, const double* __restrict__ Jbar, int nx, int ny,
+                                  int nz, double* __restrict__ xbar) {
+  extern __shared__ double sm[];
+  const int n = g.n, q = g.q, nv = n * n * n, q3 = q * q * q, nfp = n * n;
+  const int S = 512;
+  double* Xe = sm;           // 3
+  double* X = Xe + 3 * S;    // 3 (LGL)
+  double* dX = X + 3 * S;    // 9
+  double* Clb = dX + 9 * S;  // 9: cotangent of the LGL metric
+  double* dXb = Clb + 9 * S; // 9
+  double* Xb = dXb + 9 * S;  // 3
+  double* T1 = Xb + 3 * S;
+  double* T2 = T1 + S;
+  double* T3 = T2 + S;
+  double* T4 = T3 + S;
+  double* V = T4 + S;        // 3
+  double* A = V + 3 * S;     // 9: a = d x / d xi at GL nodes, then its cotangent
+  const int e = blockIdx.x;
+  for (int t = threadIdx.x; t < 3 * q3; t += blockDim.x) Xe[(t % 3) * S + t / 3] = ctrl[(size_t)e * q3 * 3 + t];
+  __syncthreads();
+  for (int c = 0; c < 3; ++c) msweep3(g.E, false, q, q, n, Xe + c * S, X + c * S, T1, T2);
+  for (int k = 0; k < 3; ++k)
+    for (int m = 0; m < 3; ++m) msweep(g.Dl, false, n, n, n, X + m * S, dX + (k * 3 + m) * S, k, n, n, n);
+  // metric = I3 (C_lgl)  ->  Clb = I3^T (mbar)
+  for (int r = 0; r < 9; ++r) {
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) T3[t] = mbar[((size_t)e * 9 + r) * nv + t];
+    __syncthreads();
+    msweep3(g.I, true, n, n, n, T3, Clb + r * S, T1, T2);
+  }
+  // shared face rows: own +face (slot 2d+1) and the +neighbour's -face (slot 2d)
+  for (int d = 0; d < 3; ++d) {
+    int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
+    if (d == 0) ex = (ex + 1) % nx;
+    else if (d == 1) ey = (ey + 1) % ny;
+    else ez = (ez + 1) % nz;
+    const int ep = ex + nx * (ey + ny * ez);
+    for (int c = 0; c < 3; ++c) {
+      for (int t = threadIdx.x; t < nfp; t += blockDim.x)
+        T3[t] = nfbar[(((size_t)e * 6 + 2 * d + 1) * 3 + c) * nfp + t] +
+                nfbar[(((size_t)ep * 6 + 2 * d) * 3 + c) * nfp + t];
+      __syncthreads();
+      // forward: face = I (x) I applied to the layer: reverse with I^T along both
+      msweep(g.I, true, n, n, n, T3, T4, 1, n, n, 1);
+      msweep(g.I, true, n, n, n, T4, T3, 0, n, n, 1);
+      double* dst = Clb + (d * 3 + c) * S;
+      for (int t = threadIdx.x; t < nfp; t += blockDim.x) {
+        const int f0 = t % n, f1 = t / n;
+        int x, y, z;
+        if (d == 0) { x = n - 1; y = f0; z = f1; }
+        else if (d == 1) { x = f0; y = n - 1; z = f1; }
+        else { x = f0; y = f1; z = n - 1; }
+        dst[x + n * (y + n * z)] += T3[t];
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < 9 * S; t += blockDim.x) dXb[t] = 0.0;
+  for (int t = threadIdx.x; t < 3 * S; t += blockDim.x) Xb[t] = 0.0;
+  __syncthreads();
+  // J = det(a), a = I3(dX) at GL nodes: abar = Jbar cof(a) (in place), dXb += I3^T(abar)
+  for (int r = 0; r < 9; ++r) msweep3(g.I, false, n, n, n, dX + r * S, A + r * S, T1, T2);
+  for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+    const double a00 = A[0 * S + t], a01 = A[1 * S + t], a02 = A[2 * S + t];
+    const double a10 = A[3 * S + t], a11 = A[4 * S + t], a12 = A[5 * S + t];
+    const double a20 = A[6 * S + t], a21 = A[7 * S + t], a22 = A[8 * S + t];
+    const double jb = Jbar[(size_t)e * nv + t];
+    A[0 * S + t] = jb * (a11 * a22 - a12 * a21);
+    A[1 * S + t] = jb * (a12 * a20 - a10 * a22);
+    A[2 * S + t] = jb * (a10 * a21 - a11 * a20);
+    A[3 * S + t] = jb * (a02 * a21 - a01 * a22);
+    A[4 * S + t] = jb * (a00 * a22 - a02 * a20);
+    A[5 * S + t] = jb * (a01 * a20 - a00 * a21);
+    A[6 * S + t] = jb * (a01 * a12 - a02 * a11);
+    A[7 * S + t] = jb * (a02 * a10 - a00 * a12);
+    A[8 * S + t] = jb * (a00 * a11 - a01 * a10);
+  }
+  __syncthreads();
+  for (int r = 0; r < 9; ++r) {
+    msweep3(g.I, true, n, n, n, A + r * S, T3, T1, T2);
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) dXb[r * S + t] += T3[t];
+    __syncthreads();
+  }
+  // C_lgl[i][c] = -curl_i(V^(c)), V^(c)_k = (X_l - X_l,0) dX[k][m], (c, m, l) cyclic
+  for (int c = 0; c < 3; ++c) {
+    const int m = (c + 1) % 3, l = (c + 2) % 3;
+    // Vbar_k from Clb[.][c]: i=0: -(D1 V2 - D2 V1); i=1: -(D2 V0 - D0 V2); i=2: -(D0 V1 - D1 V0)
+    for (int t = threadIdx.x; t < 3 * S; t += blockDim.x) V[t] = 0.0;
+    __syncthreads();
+    const int da[3] = {1, 2, 0}, va[3] = {2, 0, 1};
+    const int db[3] = {2, 0, 1}, vb[3] = {1, 2, 0};
+    for (int i = 0; i < 3; ++i) {
+      msweep(g.Dl, true, n, n, n, Clb + (i * 3 + c) * S, T1, da[i], n, n, n);
+      msweep(g.Dl, true, n, n, n, Clb + (i * 3 + c) * S, T2, db[i], n, n, n);
+      for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+        V[va[i] * S + t] -= T1[t];
+        V[vb[i] * S + t] += T2[t];
+      }
+      __syncthreads();
+    }
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+      const double xl = X[l * S + t] - Xe[l * S];
+      for (int k = 0; k < 3; ++k) {
+        Xb[l * S + t] += V[k * S + t] * dX[(k * 3 + m) * S + t];
+        dXb[(k * 3 + m) * S + t] += V[k * S + t] * xl;
+      }
+    }
+    __syncthreads();
+  }
+  // dX[k][m] = D_k X_m
+  for (int k = 0; k < 3; ++k)
+    for (int m = 0; m < 3; ++m) {
+      msweep(g.Dl, true, n, n, n, dXb + (k * 3 + m) * S, T1, k, n, n, n);
+      for (int t = threadIdx.x; t < nv; t += blockDim.x) Xb[m * S + t] += T1[t];
+      __syncthreads();
+    }
+  // X = E3(Xe) -> xbar += E3^T(Xb)
+  for (int c = 0; c < 3; ++c) {
+    msweep(g.E, true, q, n, q, Xb + c * S, T1, 0, n, n, n);
+    msweep(g.E, true, q, n, q, T1, T2, 1, q, n, n);
+    msweep(g.E, true, q, n, q, T2, T3, 2, q, q, n);
+    for (int t = threadIdx.x; t < q3; t += blockDim.x) xbar[((size_t)e * q3 + t) * 3 + c] += T3[t];
+    __syncthreads();
+  }
+}
+
+template <int N>
+cudaError_t launch_vjp_n(nsfr_ctx* ctx, const double* u, const double* dbar, double* ubar, double* xbar,
+                         const double* Rfwd, cudaStream_t s) {
+  constexpr int NV = N * N * N;
+  constexpr int epb = epb_for(N);
+  const int grid = (ctx->ne + epb - 1) / epb;
+  size_t smem = (size_t)epb * 20 * NV * sizeof(double);
+  cudaError_t err =
+      cudaFuncSetAttribute(vjp_volume_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  nsfr_prof_begin(ctx, 6, s);
+  vjp_volume_kernel<N><<<grid, threads_for(N), smem, s>>>(
+      u, dbar, xbar ? Rfwd : nullptr, ctx->metric, ctx->nfp_plus, ctx->face, ctx->wj, ctx->ops, ctx->nx, ctx->ny,
+      ctx->nz, ctx->ne, ubar, ctx->vjp_fown, ctx->vjp_fnbr, ctx->vjp_nfbar, xbar ? ctx->vjp_mbar : nullptr,
+      ctx->vjp_jbar);
+  nsfr_prof_end(ctx, s);
+  ctx->launches++;
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  smem = (size_t)epb * 10 * NV * sizeof(double);
+  if ((err = cudaFuncSetAttribute(vjp_face_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+      cudaSuccess)
+    return err;
+  nsfr_prof_begin(ctx, 5, s);
+  vjp_face_kernel<N><<<grid, threads_for(N), smem, s>>>(u, ctx->vjp_fown, ctx->vjp_fnbr, ctx->ops, ctx->nx, ctx->ny,
+                                                        ctx->nz, ctx->ne, ubar);
+  nsfr_prof_end(ctx, s);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t nsfr_vjp_metric_smem() { return (size_t)52 * 512 * sizeof(double); }
+
+cudaError_t nsfr_launch_vjp(nsfr_ctx* ctx, const double* u, const double* dbar, double* ubar, double* xbar,
+                            cudaStream_t s) {
+  cudaError_t err = cudaSuccess;
+  const double* Rfwd = ctx->rtmp;
+  switch (ctx->n) {
+    case 2: err = launch_vjp_n<2>(ctx, u, dbar, ubar, xbar, Rfwd, s); break;
+    case 3: err = launch_vjp_n<3>(ctx, u, dbar, ubar, xbar, Rfwd, s); break;
+    case 4: err = launch_vjp_n<4>(ctx, u, dbar, ubar, xbar, Rfwd, s); break;
+    case 5: err = launch_vjp_n<5>(ctx, u, dbar, ubar, xbar, Rfwd, s); break;
+    case 6: err = launch_vjp_n<6>(ctx, u, dbar, ubar, xbar, Rfwd, s); break;
+    case 7: err = launch_vjp_n<7>(ctx, u, dbar, ubar, xbar, Rfwd, s); break;
+    case 8: err = launch_vjp_n<8>(ctx, u, dbar, ubar, xbar, Rfwd, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (err != cudaSuccess || !xbar) return err;
+  const size_t smem = nsfr_vjp_metric_smem();
+  if ((err = cudaFuncSetAttribute(vjp_metric_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+      cudaSuccess)
+    return err;
+  nsfr_prof_begin(ctx, 7, s);
+  vjp_metric_kernel<<<ctx->ne, 256, smem, s>>>(ctx->ctrl, ctx->gops, ctx->vjp_mbar, ctx->vjp_nfbar, ctx->vjp_jbar,
+                                                ctx->nx, ctx->ny, ctx->nz, xbar);
+  nsfr_prof_end(ctx, s);
+  ctx->launches++;
+  return cudaGetLastError();
 }

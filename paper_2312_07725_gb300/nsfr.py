@@ -25,7 +25,7 @@ PRECISION = {"fp64": 0, "fp32_bulk": 1}
 
 # every symbol include/nsfr.h declares
 EXPORTS = ["nsfr_setup", "nsfr_residual", "nsfr_residual_raw", "nsfr_rk_step", "nsfr_entropy",
-           "nsfr_vjp", "nsfr_node_coords", "nsfr_get_metrics", "nsfr_set_metrics", "nsfr_info", "nsfr_check",
+           "nsfr_vjp", "nsfr_node_coords", "nsfr_get_metrics", "nsfr_set_metrics", "nsfr_quadrature", "nsfr_info", "nsfr_check",
            "nsfr_profile", "nsfr_profile_read", "nsfr_residual_static", "nsfr_kernel_launches", "nsfr_last_error", "nsfr_destroy"]
 KERNELS = ["metrics", "face_states", "volume", "max_wavespeed", "diagnostics", "vjp_face", "vjp_volume",
            "vjp_metrics"]
@@ -59,6 +59,8 @@ def load_library(path=LIB_PATH):
     lib.nsfr_get_metrics.restype = i
     lib.nsfr_set_metrics.argtypes = [vp, vp, vp, vp, vp]
     lib.nsfr_set_metrics.restype = i
+    lib.nsfr_quadrature.argtypes = [vp, vp, vp]
+    lib.nsfr_quadrature.restype = i
     lib.nsfr_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     lib.nsfr_info.restype = i
     lib.nsfr_check.argtypes = [vp]
@@ -211,6 +213,13 @@ class Solver:
                     for x in (C, J, Cf))
         self._check(self._lib.nsfr_set_metrics(self._h, _ptr(C), _ptr(J), _ptr(Cf), _stream(stream)),
                     "nsfr_set_metrics")
+
+    def quadrature(self, out=None, stream=None):
+        """W J at the GL nodes, [N_e][n^3]."""
+        if out is None:
+            out = np.zeros((self.n_el, self.nv))
+        self._check(self._lib.nsfr_quadrature(self._h, _ptr(out), _stream(stream)), "nsfr_quadrature")
+        return out
 
     def check(self):
         self._check(self._lib.nsfr_check(self._h), "nsfr_check")
