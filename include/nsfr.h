@@ -202,9 +202,9 @@ nsfr_status nsfr_check(nsfr_ctx* ctx);
  * Kernel ids for nsfr_profile_read: 0 metric set-up, 1 face states (entropy
  * projection), 2 volume/hybrid/surface + WA inverse (+ RK stage), 3 maximum
  * wave speed, 4 diagnostics, 5 VJP face pass, 6 VJP volume pass, 7 VJP metric
- * pass.
+ * pass, 8 face numerical fluxes.
  */
-#define NSFR_NKERNELS 8
+#define NSFR_NKERNELS 9
 
 /*
  * nsfr_profile -- on != 0: from now on record a CUDA event pair around every
@@ -234,10 +234,10 @@ nsfr_status nsfr_profile_read(nsfr_ctx* ctx, double* ms, long long* count);
  *         nsfr_get_metrics; e.g. copied once from a context)
  *   nx, ny, nz, p, c, face_flux, gamma   as in nsfr_setup (FP64 only)
  *   dudt  device [N_e][5][n^3] output
- * Its working memory (face states, 1/(wJ), an error word) is a fixed
+ * Its working memory (face states, face fluxes, 1/(wJ), an error word) is a fixed
  * 16 MiB array inside the library (NSFR_STATIC_SCRATCH_BYTES), which every
  * GPU that loads the library keeps until the process exits.  A problem
- * needing more than that, 256 + 8 N_e (48 n^2 + 4 n^3) bytes, is rejected
+ * needing more than that, 256 + 8 N_e (63 n^2 + 4 n^3) bytes, is rejected
  * with NSFR_ERR_ARG before anything runs.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture.  All calls share

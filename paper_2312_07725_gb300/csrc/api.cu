@@ -55,7 +55,7 @@ void prof_free(nsfr_ctx* c) {
 }
 
 void free_all(nsfr_ctx* c) {
-  double* dbl[] = {c->ctrl, c->metric, c->J, c->invwj, c->wj, c->nfp_plus, c->xyz, c->face, c->lnrec,
+  double* dbl[] = {c->ctrl, c->metric, c->J, c->invwj, c->wj, c->nfp_plus, c->xyz, c->face, c->lnrec, c->fstar,
                    c->ustage, c->acc, c->rtmp, c->hbuf_in, c->hbuf_out, c->red,
                    c->vjp_fown, c->vjp_fnbr, c->vjp_nfbar, c->vjp_mbar, c->vjp_jbar};
   for (double* p : dbl)
@@ -100,6 +100,7 @@ cudaError_t launch_volume_any(nsfr_ctx* ctx, const double* u, double* out, int e
 
 nsfr_status residual_device(nsfr_ctx* ctx, const double* u, double* out, int epi, cudaStream_t s) {
   CK(nsfr_launch_face_states(ctx, u, s), "face_state_kernel");
+  CK(nsfr_launch_face_flux(ctx, s), "face_flux_kernel");
   CK(launch_volume_any(ctx, u, out, epi, nullptr, s), "volume_kernel");
   return NSFR_OK;
 }
@@ -158,6 +159,7 @@ nsfr_status rk_step_device(nsfr_ctx* ctx, double* u, double cfl, double dt_fixed
     rk.a_next = (st < 3) ? a[st] : 0.0;
     rk.unext = (st == 3) ? u : ctx->ustage;
     CK(nsfr_launch_face_states(ctx, in, s), "face_state_kernel");
+    CK(nsfr_launch_face_flux(ctx, s), "face_flux_kernel");
     CK(launch_volume_any(ctx, in, nullptr, EPI_RK, &rk, s), "volume_kernel(rk)");
   }
   return NSFR_OK;
@@ -218,6 +220,7 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
             dalloc(&ctx->wj, ne * nv) == cudaSuccess && dalloc(&ctx->nfp_plus, ne * 9 * nfp) == cudaSuccess &&
             dalloc(&ctx->xyz, ne * 3 * nv) == cudaSuccess &&
             dalloc(&ctx->face, ne * 6 * NSFR_NFIELD * nfp) == cudaSuccess && dalloc(&ctx->lnrec, ne * 2 * nv) == cudaSuccess &&
+            dalloc(&ctx->fstar, ne * 15 * nfp) == cudaSuccess &&
             dalloc(&ctx->ustage, ne * 5 * nv) == cudaSuccess && dalloc(&ctx->acc, ne * 5 * nv) == cudaSuccess &&
             dalloc(&ctx->flag, 1) == cudaSuccess && dalloc(&ctx->umax, 1) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->flag_host, sizeof(int)) == cudaSuccess &&
@@ -347,7 +350,10 @@ nsfr_status nsfr_vjp(nsfr_ctx* ctx, const double* u, const double* dudt_bar, dou
   CK(cudaMemsetAsync(ctx->vjp_mbar, 0, ne * 9 * nv * sizeof(double), s), "cudaMemsetAsync");
   CK(cudaMemsetAsync(ctx->vjp_jbar, 0, ne * nv * sizeof(double), s), "cudaMemsetAsync");
   CK(nsfr_launch_face_states(ctx, u, s), "face_state_kernel");
-  if (x_bar) CK(nsfr_launch_volume(ctx, u, ctx->rtmp, EPI_RAW, nullptr, s), "volume_kernel(raw)");
+  if (x_bar) {
+    CK(nsfr_launch_face_flux(ctx, s), "face_flux_kernel");
+    CK(nsfr_launch_volume(ctx, u, ctx->rtmp, EPI_RAW, nullptr, s), "volume_kernel(raw)");
+  }
   CK(nsfr_launch_vjp(ctx, u, dudt_bar, u_bar, x_bar, s), "vjp kernels");
   return NSFR_OK;
 }

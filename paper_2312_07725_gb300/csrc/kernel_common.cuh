@@ -8,6 +8,23 @@ namespace nsfr_k {
 // every thread keep up to 255 registers
 constexpr int epb_for(int n) { return n == 2 ? 16 : n == 3 ? 8 : n == 4 ? 4 : n == 5 ? 3 : n == 6 ? 2 : 1; }
 constexpr int threads_for(int n) { return epb_for(n) * 3 * n * n; }
+// The FP64 volume kernel keeps 30 n^3 doubles of shared memory per element
+// (records, metric rows, three direction slabs of line sums) and about 110
+// registers per thread; it is bound by FP64 issue, which wants as many warps
+// per SM as shared memory (228 KB) and the register file (64K, split evenly
+// over the four sub-partitions) allow.  Elements per CTA and CTAs per SM:
+constexpr int vol_epb(int n) {
+  return n == 2 ? 16 : n == 3 ? 8 : n == 4 ? 5 : n == 5 ? 2 : n == 6 ? 2 : 1;
+}
+constexpr int vol_ctas(int n) {
+  return n == 2 ? 2 : n == 3 ? 2 : n == 4 ? 2 : n == 5 ? 3 : n == 6 ? 2 : n == 7 ? 2 : 1;
+}
+constexpr int vol_threads(int n) { return vol_epb(n) * 3 * n * n; }
+// The FP32-bulk volume kernel: 7 n^3 doubles + 43 n^3 floats of shared memory
+// per element, the same thread layout.
+constexpr int bulk_epb(int n) { return vol_epb(n); }
+constexpr int bulk_ctas(int n) { return vol_ctas(n); }
+constexpr int bulk_threads(int n) { return bulk_epb(n) * 3 * n * n; }
 
 // neighbour of element e across face (d, side): side 0 is xi_d = -1 (periodic)
 __device__ __forceinline__ int nbr_index(int e, int d, int side, int nx, int ny, int nz) {

@@ -80,6 +80,7 @@ struct nsfr_ctx {
   double* xyz = nullptr;      // [ne][3][nv]
   double* face = nullptr;     // [ne][6][NSFR_NFIELD][nfp] face-state scratch
   double* lnrec = nullptr;    // [ne][2][nv] ln rho, ln beta of the last face-state pass
+  double* fstar = nullptr;    // [ne][3][5][nfp] w_perp-scaled numerical flux of each + face
   double* ustage = nullptr;   // [ne][5][nv]
   double* acc = nullptr;      // [ne][5][nv]
   double* rtmp = nullptr;     // [ne][5][nv] (diagnostics / VJP scratch)
@@ -130,6 +131,8 @@ struct RkArgs {
   int last;           // unext = acc + b dt k (final update)
 };
 cudaError_t nsfr_launch_face_states(nsfr_ctx* ctx, const double* u, cudaStream_t s);
+// numerical flux of every face once, from the face states (after nsfr_launch_face_states)
+cudaError_t nsfr_launch_face_flux(nsfr_ctx* ctx, cudaStream_t s);
 cudaError_t nsfr_launch_volume(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk,
                                cudaStream_t s);
 // residual_bulk.cu: the FP32-bulk form of nsfr_launch_volume

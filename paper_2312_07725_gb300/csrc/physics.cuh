@@ -38,6 +38,20 @@ __device__ __forceinline__ Rec load_rec(const double* P, int stride) {
   return a;
 }
 
+// the six fields without the logs (records staged without them)
+__device__ __forceinline__ Rec load_rec6(const double* P, int stride) {
+  Rec a;
+  a.r = P[P_RHO * stride];
+  a.b2 = P[P_B2 * stride];
+  a.u0 = P[P_UH * stride];
+  a.u1 = P[(P_UH + 1) * stride];
+  a.u2 = P[(P_UH + 2) * stride];
+  a.qq = P[P_QQ * stride];
+  a.lr = 0.0;
+  a.lb = 0.0;
+  return a;
+}
+
 __device__ __forceinline__ void store_rec(double* P, int stride, const Rec& a) {
   P[P_RHO * stride] = a.r;
   P[P_B2 * stride] = a.b2;
@@ -95,12 +109,28 @@ __device__ __forceinline__ Rec rec_from_conserved(double r, double m0, double m1
   return a;
 }
 
+// ln rho and ln beta of a state for the log-mean branch.  RecLogs takes them
+// from a record; PtrLogs reads them from memory only when a log mean needs
+// them, so that the common series path neither stages nor holds the logs.
+struct RecLogs {
+  const Rec& a;
+  __device__ __forceinline__ double lr() const { return a.lr; }
+  __device__ __forceinline__ double lb() const { return a.lb; }
+};
+struct PtrLogs {
+  const double* p;  // ln rho at p[0], ln beta at p[off]
+  int off;
+  __device__ __forceinline__ double lr() const { return p[0]; }
+  __device__ __forceinline__ double lb() const { return p[off]; }
+};
+
 // F = f_s(A, B) . n, n the averaged metric row (n0, n1, n2).
 //   rho_ln = (rho_a + rho_b) Gh(u_r),        1/(2(gamma-1) beta_ln) = F4g(u_b) / (2 beta_a + 2 beta_b)
 //   p_hat  = (rho_a + rho_b) / (2 beta_a + 2 beta_b)
-//   F_rho = rho_ln u.n,  F_m = F_rho u + p_hat n,  F_E = F_rho (1/(2(gamma-1)beta_ln) - |u|^2_bar/2) + u.F_m
-__device__ __forceinline__ void ec_flux(const Rec& A, const Rec& B, double n0, double n1, double n2,
-                                        const OpsGL& K, double F[5]) {
+//   F_rho = rho_ln u.n,  F_m = F_rho u + p_hat n,  F_E = F_rho (1/(2(gamma-1) beta_ln) - |u|^2_bar/2) + u.F_m
+template <class LA, class LB>
+__device__ __forceinline__ void ec_flux_l(const Rec& A, const Rec& B, double n0, double n1, double n2,
+                                          const OpsGL& K, const LA& la, const LB& lb, double F[5]) {
   const double sr = A.r + B.r, dr = A.r - B.r;
   const double s2 = A.b2 + B.b2, d2 = A.b2 - B.b2;
   const double rb2 = rcp_newton2(s2);
@@ -109,9 +139,9 @@ __device__ __forceinline__ void ec_flux(const Rec& A, const Rec& B, double n0, d
   const double ur = fr * fr, ub = fb * fb;
   double rln, ibg;
   if (lm_small(ur)) rln = sr * horner4(K.gh, ur);
-  else rln = dr / (A.lr - B.lr);
+  else rln = dr / (la.lr() - lb.lr());
   if (lm_small(ub)) ibg = horner4(K.f4g, ub) * rb2;
-  else ibg = K.inv_gm1 * (A.lb - B.lb) / d2;
+  else ibg = K.inv_gm1 * (la.lb() - lb.lb()) / d2;
   const double ph = sr * rb2;
   const double v0 = A.u0 + B.u0, v1 = A.u1 + B.u1, v2 = A.u2 + B.u2;  // u_bar
   const double un = fma(v0, n0, fma(v1, n1, v2 * n2));
@@ -121,6 +151,11 @@ __device__ __forceinline__ void ec_flux(const Rec& A, const Rec& B, double n0, d
   F[2] = fma(Fr, v1, ph * n1);
   F[3] = fma(Fr, v2, ph * n2);
   F[4] = fma(v2, F[3], fma(v1, F[2], fma(v0, F[1], Fr * (ibg - (A.qq + B.qq)))));
+}
+
+__device__ __forceinline__ void ec_flux(const Rec& A, const Rec& B, double n0, double n1, double n2,
+                                        const OpsGL& K, double F[5]) {
+  ec_flux_l(A, B, n0, n1, n2, K, RecLogs{A}, RecLogs{B}, F);
 }
 
 // D = |A_n| (u_R - u_L): Roe-averaged flux Jacobian along n (non-unit),

@@ -6,13 +6,16 @@
 //     u~_f = u(t_s . v) along the line that ends on the face node.  The
 //     kernel stores the primitive record of u~_f (rho, u, beta, ln rho,
 //     ln beta, |u|^2), which is all the face fluxes need.
+// K1b face_flux_kernel: the numerical flux f*(u~_L, u~_R; w_perp C_f) of every
+//     face node, once per face (C_f the shared face row), for both elements
+//     that share the face.
 // K2  volume_kernel: Eq. NSFR with the sum-factorised Hadamard products
 //     (Sec. "Scalable Evaluations"), one thread per line of an element:
 //       volume:  R_a += sum_{b} w_perp S1[a,b] f_s(u_a, u_b) . (C_a + C_b)/2
 //                (each unordered pair evaluated once: S1 is skew),
 //       hybrid:  R_a += s w_perp t_s[a] (phi_a + f* - sum_b t_s[b] phi_b),
 //                phi_a = f_s(u_a, u~_f) . (C_a + C_f)/2,
-//       surface: f* = f*(u~_L, u~_R; C_f) with the shared face row C_f;
+//       surface: f* read from K1b;
 //     the three directions' line sums meet in shared memory, then the
 //     epilogue applies the weight-adjusted inverse (Eq. weight-adj ESFR mass,
 //     Pi~^T, 1/(w J), Pi~, each a 1D contraction per direction) and either
@@ -101,6 +104,30 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
   }
 }
 
+// f* of the + face of element e in direction d, for every face node, scaled by
+// the node's w_perp (f* is linear in the face row, its Roe part positively
+// homogeneous): fstar[e][d][5][n^2].  L is the element's own + face state, R
+// the neighbour's - face state; both carry the same face-node index.
+template <int N>
+__global__ void __launch_bounds__(256) face_flux_kernel(const double* __restrict__ face,
+                                                        const double* __restrict__ nf_plus, OpsGL ops, int nx, int ny,
+                                                        int nz, int ne, int face_kind, double* __restrict__ fstar) {
+  constexpr int NFP = N * N;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ne * 3 * NFP) return;
+  const int node = t % NFP, ed = t / NFP, d = ed % 3, e = ed / 3;
+  const int enb = nbr_index(e, d, 1, nx, ny, nz);
+  const Rec L = load_rec(face + (((size_t)e * 6 + 2 * d + 1) * NSFR_NFIELD) * NFP + node, NFP);
+  const Rec R = load_rec(face + (((size_t)enb * 6 + 2 * d) * NSFR_NFIELD) * NFP + node, NFP);
+  const double* nf = nf_plus + (size_t)ed * 3 * NFP + node;
+  const double wperp = ops.w[node % N] * ops.w[node / N];
+  double F[5];
+  face_flux(L, R, wperp * nf[0], wperp * nf[NFP], wperp * nf[2 * NFP], ops, face_kind, F);
+  double* o = fstar + (size_t)ed * 5 * NFP + node;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) o[k * NFP] = F[k];
+}
+
 // Pi~1^T (transpose) or Pi~1 along direction d for every line of X[nel][5][NV],
 // in place: Pi~1 x = x - hv (g . x), Pi~1^T x = x - g (hv . x).
 template <int N>
@@ -125,20 +152,22 @@ __device__ __forceinline__ void rank_one_sweep(double* X, int nel, int d, bool t
 // next stage state over it (each CTA only over its own elements, after its
 // own reads).
 template <int N>
-__global__ void __launch_bounds__(threads_for(N), 1) volume_kernel(const double* u, const double* __restrict__ lnrec,
+__global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(const double* u, const double* __restrict__ lnrec,
                                                                 const double* __restrict__ metric,
                                                                 const double* __restrict__ nf_plus,
                                                                 const double* __restrict__ face,
+                                                                const double* __restrict__ fstar,
                                                                 const double* __restrict__ invwj, OpsGL ops, int nx,
-                                                                int ny, int nz, int ne, int face_kind, int epi,
-                                                                RkArgs rk, double* out, int* flag) {
+                                                                int ny, int nz, int ne, int epi, RkArgs rk,
+                                                                double* out, int* flag) {
   constexpr int NV = N * N * N, NFP = N * N, NL = 3 * NFP;
   extern __shared__ double sm[];
   const int epb = blockDim.x / NL;
   const int e0 = blockIdx.x * epb;
-  double* P = sm;                                   // [epb][8][NV] node records
-  double* Ms = P + (size_t)epb * NSFR_NFIELD * NV;  // [epb][9][NV] metric rows / 2
-  double* Rs = Ms + (size_t)epb * 9 * NV;           // [epb][5][NV] residual
+  double* P = sm;                      // [epb][6][NV] node records (the logs stay in lnrec)
+  double* Ms = P + (size_t)epb * 6 * NV;  // [epb][9][NV] metric rows / 2
+  double* Ra = Ms + (size_t)epb * 9 * NV;  // [epb][3][5][NV] line sums, one slab per direction
+  double* Rs = P;                          // [epb][5][NV] residual (after the line phase)
   const double gm1 = ops.gamma - 1.0;
 
   // prologue: node records and half metric rows of the block's elements
@@ -146,9 +175,14 @@ __global__ void __launch_bounds__(threads_for(N), 1) volume_kernel(const double*
     const int le = t / NV, node = t % NV, e = e0 + le;
     if (e >= ne) continue;
     const double* ue = u + (size_t)e * 5 * NV + node;
-    const double* ln = lnrec + (size_t)e * 2 * NV + node;
-    Rec a = rec_from_conserved(ue[0], ue[NV], ue[2 * NV], ue[3 * NV], ue[4 * NV], ln[0], ln[NV], gm1, flag);
-    store_rec(P + (size_t)le * NSFR_NFIELD * NV + node, NV, a);
+    const Rec a = rec_from_conserved(ue[0], ue[NV], ue[2 * NV], ue[3 * NV], ue[4 * NV], 0.0, 0.0, gm1, flag);
+    double* pr = P + (size_t)le * 6 * NV + node;
+    pr[P_RHO * NV] = a.r;
+    pr[P_B2 * NV] = a.b2;
+    pr[P_UH * NV] = a.u0;
+    pr[(P_UH + 1) * NV] = a.u1;
+    pr[(P_UH + 2) * NV] = a.u2;
+    pr[P_QQ * NV] = a.qq;
   }
   // metric rows of direction d scaled by w_perp / 2: w_perp (the weights of
   // the two other directions) is constant along a line of direction d, and
@@ -161,96 +195,94 @@ __global__ void __launch_bounds__(threads_for(N), 1) volume_kernel(const double*
     const double wp = dd == 0 ? ops.w[j] * ops.w[k] : (dd == 1 ? ops.w[i] * ops.w[k] : ops.w[i] * ops.w[j]);
     Ms[t] = 0.5 * wp * metric[(size_t)e0 * 9 * NV + t];
   }
+  for (int t = threadIdx.x; t < epb * 15 * NV; t += blockDim.x) Ra[t] = 0.0;
   __syncthreads();
 
+  // line phase: one thread per line; the line's sums live in the direction's
+  // slab of Ra (only this thread touches them), node a's in registers while
+  // a is the outer pair index -- the additions keep the order of a plain
+  // per-line accumulation
   const int le = threadIdx.x / NL, l = threadIdx.x % NL, e = e0 + le;
-  const bool valid = (le < epb) && (e < ne);
   const int d = l / NFP, line = l % NFP, l0 = line % N, l1 = line / N;
   int base, stride;
   line_geometry<N>(d, l0, l1, base, stride);
-  double R[N][5];
-#pragma unroll
-  for (int a = 0; a < N; ++a)
-#pragma unroll
-    for (int k = 0; k < 5; ++k) R[a][k] = 0.0;
-
-  if (valid) {
-    const double* Pe = P + (size_t)le * NSFR_NFIELD * NV + base;
+  if (le < epb && e < ne) {
+    const double* Pe = P + (size_t)le * 6 * NV + base;
+    const double* Le = lnrec + (size_t)e * 2 * NV + base;  // ln rho, ln beta (read only off the series path)
     const double* Me = Ms + ((size_t)le * 9 + 3 * d) * NV + base;
+    double* Rl = Ra + ((size_t)le * 15 + 5 * d) * NV + base;
     const double wperp = ops.w[l0] * ops.w[l1];
     // volume-volume pairs along the line: each unordered pair once (S1 is skew);
     // the metric rows already carry w_perp / 2
-#pragma unroll
-    for (int a = 0; a < N; ++a) {
-      const Rec A = load_rec(Pe + a * stride, NV);
+#pragma unroll 1
+    for (int a = 0; a < N - 1; ++a) {
+      const Rec A = load_rec6(Pe + a * stride, NV);
       const double na0 = Me[a * stride], na1 = Me[NV + a * stride], na2 = Me[2 * NV + a * stride];
+      double Racc[5];
 #pragma unroll
+      for (int k = 0; k < 5; ++k) Racc[k] = Rl[k * NV + a * stride];
+#pragma unroll 1
       for (int b = a + 1; b < N; ++b) {
-        const Rec B = load_rec(Pe + b * stride, NV);
+        const Rec B = load_rec6(Pe + b * stride, NV);
         double F[5];
-        ec_flux(A, B, na0 + Me[b * stride], na1 + Me[NV + b * stride], na2 + Me[2 * NV + b * stride], ops, F);
+        ec_flux_l(A, B, na0 + Me[b * stride], na1 + Me[NV + b * stride], na2 + Me[2 * NV + b * stride], ops,
+                  PtrLogs{Le + a * stride, NV}, PtrLogs{Le + b * stride, NV}, F);
         const double c = ops.S1[a * N + b];
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-          R[a][k] = fma(c, F[k], R[a][k]);
-          R[b][k] = fma(-c, F[k], R[b][k]);
+          Racc[k] = fma(c, F[k], Racc[k]);
+          Rl[k * NV + b * stride] = fma(-c, F[k], Rl[k * NV + b * stride]);
         }
       }
+#pragma unroll
+      for (int k = 0; k < 5; ++k) Rl[k * NV + a * stride] = Racc[k];
     }
     // hybrid volume-face terms and face fluxes, both ends of the line
-#pragma unroll
+#pragma unroll 1
     for (int s = 0; s < 2; ++s) {
       const int enb = nbr_index(e, d, s, nx, ny, nz);
       const double* fo = face + (((size_t)e * 6 + 2 * d + s) * NSFR_NFIELD) * NFP + line;
-      const double* fn = face + (((size_t)enb * 6 + 2 * d + 1 - s) * NSFR_NFIELD) * NFP + line;
-      const double* nf = nf_plus + (((size_t)(s ? e : enb) * 3 + d) * 3) * NFP + line;
+      const size_t fe = (size_t)(s ? e : enb) * 3 + d;  // the element whose + face this is
+      const double* nf = nf_plus + fe * 3 * NFP + line;
+      const double* fsp = fstar + fe * 5 * NFP + line;
       const double f0 = wperp * nf[0], f1 = wperp * nf[NFP], f2 = wperp * nf[2 * NFP];
-      const Rec Fo = load_rec(fo, NFP);
-      const Rec Fn = load_rec(fn, NFP);
-      double fs[5];
-      if (s) face_flux(Fo, Fn, f0, f1, f2, ops, face_kind, fs);
-      else face_flux(Fn, Fo, f0, f1, f2, ops, face_kind, fs);
+      const Rec Fo = load_rec6(fo, NFP);
       const double* t = s ? ops.tp : ops.tm;
       const double sw = s ? 1.0 : -1.0;
       const double h0 = 0.5 * f0, h1 = 0.5 * f1, h2 = 0.5 * f2;
       double tphi[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-#pragma unroll
+#pragma unroll 1
       for (int a = 0; a < N; ++a) {
-        const Rec A = load_rec(Pe + a * stride, NV);
+        const Rec A = load_rec6(Pe + a * stride, NV);
         double F[5];
-        ec_flux(A, Fo, Me[a * stride] + h0, Me[NV + a * stride] + h1, Me[2 * NV + a * stride] + h2, ops, F);
+        ec_flux_l(A, Fo, Me[a * stride] + h0, Me[NV + a * stride] + h1, Me[2 * NV + a * stride] + h2, ops,
+                  PtrLogs{Le + a * stride, NV}, PtrLogs{fo + P_LRHO * NFP, NFP}, F);
         const double ta = t[a], swt = sw * ta;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
           tphi[k] = fma(ta, F[k], tphi[k]);
-          R[a][k] = fma(swt, F[k], R[a][k]);
+          Rl[k * NV + a * stride] = fma(swt, F[k], Rl[k * NV + a * stride]);
         }
       }
 #pragma unroll
-      for (int k = 0; k < 5; ++k) tphi[k] = fs[k] - tphi[k];
+      for (int k = 0; k < 5; ++k) tphi[k] = fsp[k * NFP] - tphi[k];
 #pragma unroll
       for (int a = 0; a < N; ++a) {
         const double swt = sw * t[a];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) R[a][k] = fma(swt, tphi[k], R[a][k]);
+        for (int k = 0; k < 5; ++k) Rl[k * NV + a * stride] = fma(swt, tphi[k], Rl[k * NV + a * stride]);
       }
     }
   }
-  // the three directions meet in shared memory (fixed order: d = 0, 1, 2)
-#pragma unroll
-  for (int dd = 0; dd < 3; ++dd) {
-    if (valid && d == dd) {
-      double* Re = Rs + (size_t)le * 5 * NV + base;
-#pragma unroll
-      for (int a = 0; a < N; ++a)
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-          if (dd == 0) Re[k * NV + a * stride] = R[a][k];
-          else Re[k * NV + a * stride] += R[a][k];
-        }
-    }
-    __syncthreads();
+  __syncthreads();
+  // the three directions meet in a fixed order (d = 0, 1, 2); the records are
+  // no longer needed, so the sum goes over them
+  for (int t = threadIdx.x; t < min(epb, ne - e0) * 5 * NV; t += blockDim.x) {
+    const int lq = t / (5 * NV), r = t % (5 * NV);
+    const double* ra = Ra + (size_t)lq * 15 * NV + r;
+    Rs[t] = (ra[0] + ra[5 * NV]) + ra[10 * NV];
   }
+  __syncthreads();
 
   const int nel = min(epb, ne - e0);
   const int total = nel * 5 * NV;
@@ -311,19 +343,32 @@ cudaError_t launch_face_n(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
 }
 
 template <int N>
+cudaError_t launch_face_flux_n(nsfr_ctx* ctx, cudaStream_t s) {
+  const long long total = (long long)ctx->ne * 3 * N * N;
+  if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const int grid = (int)((total + 255) / 256);
+  nsfr_prof_begin(ctx, 8, s);
+  face_flux_kernel<N><<<grid, 256, 0, s>>>(ctx->face, ctx->nfp_plus, ctx->ops, ctx->nx, ctx->ny, ctx->nz, ctx->ne,
+                                           ctx->face_flux, ctx->fstar);
+  nsfr_prof_end(ctx, s);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+template <int N>
 cudaError_t launch_volume_n(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk,
                             cudaStream_t s) {
   constexpr int NV = N * N * N;
-  constexpr int epb = epb_for(N);
+  constexpr int epb = vol_epb(N);
   const int grid = (ctx->ne + epb - 1) / epb;
-  const size_t smem = (size_t)epb * (NSFR_NFIELD + 9 + 5) * NV * sizeof(double);
+  const size_t smem = (size_t)epb * (6 + 9 + 15) * NV * sizeof(double);
   cudaError_t err = cudaFuncSetAttribute(volume_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   RkArgs r = rk ? *rk : RkArgs{};
   nsfr_prof_begin(ctx, 2, s);
-  volume_kernel<N><<<grid, threads_for(N), smem, s>>>(u, ctx->lnrec, ctx->metric, ctx->nfp_plus, ctx->face, ctx->invwj,
-                                                      ctx->ops, ctx->nx, ctx->ny, ctx->nz, ctx->ne, ctx->face_flux,
-                                                      epi, r, out, ctx->flag);
+  volume_kernel<N><<<grid, vol_threads(N), smem, s>>>(u, ctx->lnrec, ctx->metric, ctx->nfp_plus, ctx->face,
+                                                      ctx->fstar, ctx->invwj, ctx->ops, ctx->nx, ctx->ny, ctx->nz,
+                                                      ctx->ne, epi, r, out, ctx->flag);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
   return cudaGetLastError();
@@ -340,6 +385,19 @@ cudaError_t nsfr_launch_face_states(nsfr_ctx* ctx, const double* u, cudaStream_t
     case 6: return launch_face_n<6>(ctx, u, s);
     case 7: return launch_face_n<7>(ctx, u, s);
     case 8: return launch_face_n<8>(ctx, u, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t nsfr_launch_face_flux(nsfr_ctx* ctx, cudaStream_t s) {
+  switch (ctx->n) {
+    case 2: return launch_face_flux_n<2>(ctx, s);
+    case 3: return launch_face_flux_n<3>(ctx, s);
+    case 4: return launch_face_flux_n<4>(ctx, s);
+    case 5: return launch_face_flux_n<5>(ctx, s);
+    case 6: return launch_face_flux_n<6>(ctx, s);
+    case 7: return launch_face_flux_n<7>(ctx, s);
+    case 8: return launch_face_flux_n<8>(ctx, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -379,8 +437,10 @@ extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, co
     return NSFR_ERR_ARG;
   const size_t ne = (size_t)nx * ny * nz, n = p + 1, nv = n * n * n, nfp = n * n;
   const size_t face_bytes = ne * 6 * NSFR_NFIELD * nfp * sizeof(double);
+  const size_t fstar_bytes = ne * 15 * nfp * sizeof(double);
   const size_t jac_bytes = ne * nv * sizeof(double);
-  const size_t need = 256 + face_bytes + 4 * jac_bytes;  // error word (padded), faces, 1/(wJ), wJ, ln rho/beta
+  // error word (padded), face states, face fluxes, 1/(wJ), wJ, ln rho/beta
+  const size_t need = 256 + face_bytes + fstar_bytes + 4 * jac_bytes;
   if (need > NSFR_STATIC_SCRATCH_BYTES || ne > (size_t)0x7fffffff) return NSFR_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return NSFR_ERR_CUDA;
@@ -415,15 +475,17 @@ extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, co
   nsfr_build_ops(p, p, c, gamma, &ctx.ops, &ctx.gops);
   ctx.flag = (int*)base;
   ctx.face = (double*)(base + 256);
-  ctx.invwj = (double*)(base + 256 + face_bytes);
-  ctx.wj = (double*)(base + 256 + face_bytes + jac_bytes);
-  ctx.lnrec = (double*)(base + 256 + face_bytes + 2 * jac_bytes);
+  ctx.fstar = (double*)(base + 256 + face_bytes);
+  ctx.invwj = (double*)(base + 256 + face_bytes + fstar_bytes);
+  ctx.wj = (double*)(base + 256 + face_bytes + fstar_bytes + jac_bytes);
+  ctx.lnrec = (double*)(base + 256 + face_bytes + fstar_bytes + 2 * jac_bytes);
   ctx.metric = const_cast<double*>(C);
   ctx.J = const_cast<double*>(J);
   ctx.nfp_plus = const_cast<double*>(Cf);
   if (cudaMemsetAsync(ctx.flag, 0, sizeof(int), s) != cudaSuccess) return NSFR_ERR_CUDA;
   if (nsfr_launch_jacobian_derived(&ctx, s) != cudaSuccess) return NSFR_ERR_CUDA;
   if (nsfr_launch_face_states(&ctx, u, s) != cudaSuccess) return NSFR_ERR_CUDA;
+  if (nsfr_launch_face_flux(&ctx, s) != cudaSuccess) return NSFR_ERR_CUDA;
   if (nsfr_launch_volume(&ctx, u, dudt, EPI_DUDT, nullptr, s) != cudaSuccess) return NSFR_ERR_CUDA;
   int flag = 0;
   if (cudaMemcpyAsync(&flag, ctx.flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return NSFR_ERR_CUDA;

@@ -29,17 +29,15 @@ namespace {
 using namespace nsfr_k;
 
 struct BNode {
-  double r, b2, lr, lb;  // FP64 log-mean inputs
-  ff u0, u1, u2;         // u/2
-  float qq;              // |u|^2/4
+  double r, b2;   // FP64 log-mean inputs (the logs are read when a log mean needs them)
+  ff u0, u1, u2;  // u/2
+  float qq;       // |u|^2/4
 };
 
 __device__ __forceinline__ BNode bnode_from_rec(const Rec& a) {
   BNode b;
   b.r = a.r;
   b.b2 = a.b2;
-  b.lr = a.lr;
-  b.lb = a.lb;
   b.u0 = ff_from_double(a.u0);
   b.u1 = ff_from_double(a.u1);
   b.u2 = ff_from_double(a.u2);
@@ -55,8 +53,10 @@ struct BRef {
 
 // deviation flux of a pair: Fr (mass, float-float), Fm = F_m - u_ref F_rho - p_ref n,
 // FE = F_E - (H_ref + |u_ref|^2/2) F_rho; (n0, n1, n2) the averaged metric row.
+template <class LA, class LB>
 __device__ __forceinline__ void bulk_flux(const BNode& A, const BNode& B, ff n0, ff n1, ff n2, const BRef& ref,
-                                          const OpsGL& K, ff& Fr, float Fm[3], float& FE) {
+                                          const OpsGL& K, const LA& la, const LB& lb, ff& Fr, float Fm[3],
+                                          float& FE) {
   const double sr = A.r + B.r, dr = A.r - B.r;
   const double s2 = A.b2 + B.b2, d2 = A.b2 - B.b2;
   const double rb2 = rcp_newton1(s2), rr = rcp_newton1(sr);
@@ -67,12 +67,12 @@ __device__ __forceinline__ void bulk_flux(const BNode& A, const BNode& B, ff n0,
     rln = sr * horner4(K.gh, ur);
     irln = horner4(K.fr2, ur) * rr;
   } else {
-    const double dl = A.lr - B.lr;
+    const double dl = la.lr() - lb.lr();
     rln = dr / dl;
     irln = dl / dr;
   }
   if (lm_small(ub)) ibg = horner4(K.f4g, ub) * rb2;
-  else ibg = K.inv_gm1 * (A.lb - B.lb) / d2;
+  else ibg = K.inv_gm1 * (la.lb() - lb.lb()) / d2;
   const double ph = sr * rb2;
   const float dp = __double2float_rn(ph - ref.p);
   const float dH = __double2float_rn(fma(ph, irln, ibg) - ref.H);
@@ -125,24 +125,25 @@ __device__ __forceinline__ void rank_one_sweep_f(float* X, int nel, int d, bool 
 }
 
 // shared-memory layout per element (SoA over the NV nodes)
-//   doubles: r, 2 beta, ln rho, ln beta                       4 NV
-//   floats : u/2 hi(3) lo(3), |u|^2/4, metric hi(9) lo(9)     25 NV
-//   floats : R_rho hi, lo, R_m(3), R_E'                        6 NV
+//   doubles: r, 2 beta                                         2 NV
 //   doubles: R (combined), epilogue                            5 NV
+//   floats : u/2 hi(3) lo(3), |u|^2/4, metric hi(9) lo(9)     25 NV
+//   floats : line sums R_rho hi, lo, R_m(3), R_E', one slab
+//            per direction                                     18 NV
 template <int N>
-__global__ void __launch_bounds__(threads_for(N), 1)
+__global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
     volume_bulk_kernel(const double* u, const double* __restrict__ lnrec, const double* __restrict__ metric,
                        const double* __restrict__ nf_plus, const double* __restrict__ face,
-                       const double* __restrict__ invwj, OpsGL ops, int nx, int ny, int nz, int ne, int face_kind,
-                       int epi, RkArgs rk, double* out, int* flag) {
+                       const double* __restrict__ fstar, const double* __restrict__ invwj, OpsGL ops, int nx, int ny,
+                       int nz, int ne, int epi, RkArgs rk, double* out, int* flag) {
   constexpr int NV = N * N * N, NFP = N * N, NL = 3 * NFP;
   extern __shared__ double sm[];
   const int epb = blockDim.x / NL;
   const int e0 = blockIdx.x * epb;
-  double* Pd = sm;                                 // [epb][4][NV]
-  double* Rd = Pd + (size_t)epb * 4 * NV;          // [epb][5][NV]
+  double* Pd = sm;                                 // [epb][2][NV]
+  double* Rd = Pd + (size_t)epb * 2 * NV;          // [epb][5][NV]
   float* Pf = (float*)(Rd + (size_t)epb * 5 * NV); // [epb][25][NV]
-  float* Ra = Pf + (size_t)epb * 25 * NV;          // [epb][6][NV]
+  float* Ra = Pf + (size_t)epb * 25 * NV;          // [epb][3][6][NV]
   float* Xf = Pf;                                  // epilogue (aliases Pf)
   const double gm1 = ops.gamma - 1.0;
 
@@ -150,13 +151,10 @@ __global__ void __launch_bounds__(threads_for(N), 1)
     const int le = t / NV, node = t % NV, e = e0 + le;
     if (e >= ne) continue;
     const double* ue = u + (size_t)e * 5 * NV + node;
-    const double* ln = lnrec + (size_t)e * 2 * NV + node;
-    const Rec a = rec_from_conserved(ue[0], ue[NV], ue[2 * NV], ue[3 * NV], ue[4 * NV], ln[0], ln[NV], gm1, flag);
-    double* pd = Pd + (size_t)le * 4 * NV + node;
+    const Rec a = rec_from_conserved(ue[0], ue[NV], ue[2 * NV], ue[3 * NV], ue[4 * NV], 0.0, 0.0, gm1, flag);
+    double* pd = Pd + (size_t)le * 2 * NV + node;
     pd[0] = a.r;
     pd[NV] = a.b2;
-    pd[2 * NV] = a.lr;
-    pd[3 * NV] = a.lb;
     float* pf = Pf + (size_t)le * 25 * NV + node;
     const ff u0 = ff_from_double(a.u0), u1 = ff_from_double(a.u1), u2 = ff_from_double(a.u2);
     pf[0] = u0.hi;
@@ -174,29 +172,26 @@ __global__ void __launch_bounds__(threads_for(N), 1)
   }
   __syncthreads();
 
+  for (int t = threadIdx.x; t < epb * 18 * NV; t += blockDim.x) Ra[t] = 0.0f;
+  __syncthreads();
+
+  // line phase: one thread per line, the line's sums in the direction's slab
+  // of Ra (node a's in registers while a is the outer pair index), added in
+  // the order of a plain per-line accumulation
   const int le = threadIdx.x / NL, l = threadIdx.x % NL, e = e0 + le;
-  const bool valid = (le < epb) && (e < ne);
   const int d = l / NFP, line = l % NFP, l0 = line % N, l1 = line / N;
   int base, stride;
   line_geometry<N>(d, l0, l1, base, stride);
-  ff Rr[N];
-  float Rm[N][3], Re[N];
-#pragma unroll
-  for (int a = 0; a < N; ++a) {
-    Rr[a] = ff{0.0f, 0.0f};
-    Rm[a][0] = Rm[a][1] = Rm[a][2] = Re[a] = 0.0f;
-  }
-  BRef ref;
-  if (valid) {
-    const double* pd = Pd + (size_t)le * 4 * NV + base;
+  if (le < epb && e < ne) {
+    const double* pd = Pd + (size_t)le * 2 * NV + base;
     const float* pf = Pf + (size_t)le * 25 * NV + base;
-    ref = element_ref(Pd + (size_t)le * 4 * NV, Pf + (size_t)le * 25 * NV, NV, ops);
+    const double* Le = lnrec + (size_t)e * 2 * NV + base;  // ln rho, ln beta (read only off the series path)
+    float* Rl = Ra + ((size_t)le * 18 + 6 * d) * NV + base;
+    const BRef ref = element_ref(Pd + (size_t)le * 2 * NV, Pf + (size_t)le * 25 * NV, NV, ops);
     auto node_at = [&](int a) {
       BNode b;
       b.r = pd[a * stride];
       b.b2 = pd[NV + a * stride];
-      b.lr = pd[2 * NV + a * stride];
-      b.lb = pd[3 * NV + a * stride];
       b.u0 = ff{pf[a * stride], pf[3 * NV + a * stride]};
       b.u1 = ff{pf[NV + a * stride], pf[4 * NV + a * stride]};
       b.u2 = ff{pf[2 * NV + a * stride], pf[5 * NV + a * stride]};
@@ -206,57 +201,66 @@ __global__ void __launch_bounds__(threads_for(N), 1)
     auto metric_at = [&](int a, int c) {
       return ff{pf[(7 + 3 * d + c) * NV + a * stride], pf[(16 + 3 * d + c) * NV + a * stride]};
     };
+    // accumulate a pair's (or hybrid) flux, scaled by c, into node a's sums
+    auto add_to = [&](int a, ff c, const ff& Fr, const float Fm[3], float FE) {
+      float* r = Rl + a * stride;
+      const ff s_ = ff_fma(c, Fr, ff{r[0], r[NV]});
+      r[0] = s_.hi;
+      r[NV] = s_.lo;
 #pragma unroll
-    for (int a = 0; a < N; ++a) {
+      for (int k = 0; k < 3; ++k) r[(2 + k) * NV] = fmaf(c.hi, Fm[k], r[(2 + k) * NV]);
+      r[5 * NV] = fmaf(c.hi, FE, r[5 * NV]);
+    };
+#pragma unroll 1
+    for (int a = 0; a < N - 1; ++a) {
       const BNode A = node_at(a);
       const ff na0 = metric_at(a, 0), na1 = metric_at(a, 1), na2 = metric_at(a, 2);
-#pragma unroll
+      float* ra = Rl + a * stride;
+      ff Rr = ff{ra[0], ra[NV]};
+      float Rm0 = ra[2 * NV], Rm1 = ra[3 * NV], Rm2 = ra[4 * NV], Re = ra[5 * NV];
+#pragma unroll 1
       for (int b = a + 1; b < N; ++b) {
         const BNode B = node_at(b);
         ff Fr;
         float Fm[3], FE;
         bulk_flux(A, B, ff_add(na0, metric_at(b, 0)), ff_add(na1, metric_at(b, 1)), ff_add(na2, metric_at(b, 2)),
-                  ref, ops, Fr, Fm, FE);
+                  ref, ops, PtrLogs{Le + a * stride, NV}, PtrLogs{Le + b * stride, NV}, Fr, Fm, FE);
         const ff c{ops.S1f[a * N + b], ops.S1lo[a * N + b]};
-        Rr[a] = ff_fma(c, Fr, Rr[a]);
-        Rr[b] = ff_fma(ff_neg(c), Fr, Rr[b]);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          Rm[a][k] = fmaf(c.hi, Fm[k], Rm[a][k]);
-          Rm[b][k] = fmaf(-c.hi, Fm[k], Rm[b][k]);
-        }
-        Re[a] = fmaf(c.hi, FE, Re[a]);
-        Re[b] = fmaf(-c.hi, FE, Re[b]);
+        Rr = ff_fma(c, Fr, Rr);
+        Rm0 = fmaf(c.hi, Fm[0], Rm0);
+        Rm1 = fmaf(c.hi, Fm[1], Rm1);
+        Rm2 = fmaf(c.hi, Fm[2], Rm2);
+        Re = fmaf(c.hi, FE, Re);
+        add_to(b, ff_neg(c), Fr, Fm, FE);
       }
+      ra[0] = Rr.hi;
+      ra[NV] = Rr.lo;
+      ra[2 * NV] = Rm0;
+      ra[3 * NV] = Rm1;
+      ra[4 * NV] = Rm2;
+      ra[5 * NV] = Re;
     }
     const double wperp = ops.w[l0] * ops.w[l1];
-#pragma unroll
+#pragma unroll 1
     for (int s = 0; s < 2; ++s) {
       const int enb = nbr_index(e, d, s, nx, ny, nz);
       const double* fo = face + (((size_t)e * 6 + 2 * d + s) * NSFR_NFIELD) * NFP + line;
-      const double* fn = face + (((size_t)enb * 6 + 2 * d + 1 - s) * NSFR_NFIELD) * NFP + line;
-      const double* nf = nf_plus + (((size_t)(s ? e : enb) * 3 + d) * 3) * NFP + line;
+      const size_t fe = (size_t)(s ? e : enb) * 3 + d;  // the element whose + face this is
+      const double* nf = nf_plus + fe * 3 * NFP + line;
+      const double* fsp = fstar + fe * 5 * NFP + line;
       const double f0 = wperp * nf[0], f1 = wperp * nf[NFP], f2 = wperp * nf[2 * NFP];
-      const Rec FoR = load_rec(fo, NFP), FnR = load_rec(fn, NFP);
-      const BNode Fo = bnode_from_rec(FoR), Fn = bnode_from_rec(FnR);
-      // face flux (EC, deviation form) and optional Roe dissipation
+      const BNode Fo = bnode_from_rec(load_rec6(fo, NFP));
+      // the FP64 face flux in the element's deviation form:
+      //   F_m' = F_m - u_ref F_rho - p_ref n,  F_E' = F_E - E_ref F_rho
       ff sr_;
       float sm_[3], se_;
       {
-        const ff g0 = ff_from_double(f0), g1 = ff_from_double(f1), g2 = ff_from_double(f2);
-        if (s) bulk_flux(Fo, Fn, g0, g1, g2, ref, ops, sr_, sm_, se_);
-        else bulk_flux(Fn, Fo, g0, g1, g2, ref, ops, sr_, sm_, se_);
-        if (face_kind == NSFR_FACE_EC_ROE) {
-          double D[5];
-          if (s) roe_dissipation(FoR, FnR, f0, f1, f2, ops.gamma, D);
-          else roe_dissipation(FnR, FoR, f0, f1, f2, ops.gamma, D);
-          // the dissipation enters the mass flux too: subtract u_ref, E_ref times its mass part
-          sr_ = ff_add(sr_, ff_from_double(-0.5 * D[0]));
-          const double ur[3] = {ff_to_double(ref.u0), ff_to_double(ref.u1), ff_to_double(ref.u2)};
-#pragma unroll
-          for (int k = 0; k < 3; ++k) sm_[k] -= __double2float_rn(0.5 * (D[1 + k] - ur[k] * D[0]));
-          se_ -= __double2float_rn(0.5 * (D[4] - (ref.H + (double)ref.kin) * D[0]));
-        }
+        const double F0 = fsp[0];
+        sr_ = ff_from_double(F0);
+        sm_[0] = __double2float_rn(fma(-ref.p, f0, fma(-ff_to_double(ref.u0), F0, fsp[NFP])));
+        sm_[1] = __double2float_rn(fma(-ref.p, f1, fma(-ff_to_double(ref.u1), F0, fsp[2 * NFP])));
+        sm_[2] = __double2float_rn(fma(-ref.p, f2, fma(-ff_to_double(ref.u2), F0, fsp[3 * NFP])));
+        se_ = __double2float_rn(fma(-(ref.H + (double)ref.kin), F0, fsp[4 * NFP]));
       }
       const ff h0 = ff_from_double(0.5 * f0), h1 = ff_from_double(0.5 * f1), h2 = ff_from_double(0.5 * f2);
       const float* tf = s ? ops.tpf : ops.tmf;
@@ -264,75 +268,48 @@ __global__ void __launch_bounds__(threads_for(N), 1)
       const float sg = s ? 1.0f : -1.0f;
       ff tr = ff{0.0f, 0.0f};
       float tm[3] = {0.0f, 0.0f, 0.0f}, te = 0.0f;
-#pragma unroll
+#pragma unroll 1
       for (int a = 0; a < N; ++a) {
         const BNode A = node_at(a);
         ff Fr;
         float Fm[3], FE;
         bulk_flux(A, Fo, ff_add(metric_at(a, 0), h0), ff_add(metric_at(a, 1), h1), ff_add(metric_at(a, 2), h2),
-                  ref, ops, Fr, Fm, FE);
+                  ref, ops, PtrLogs{Le + a * stride, NV}, PtrLogs{fo + P_LRHO * NFP, NFP}, Fr, Fm, FE);
         const ff ta{tf[a], tl[a]};
-        const ff sta{sg * tf[a], sg * tl[a]};
         tr = ff_fma(ta, Fr, tr);
-        Rr[a] = ff_fma(sta, Fr, Rr[a]);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          tm[k] = fmaf(ta.hi, Fm[k], tm[k]);
-          Rm[a][k] = fmaf(sta.hi, Fm[k], Rm[a][k]);
-        }
+        for (int k = 0; k < 3; ++k) tm[k] = fmaf(ta.hi, Fm[k], tm[k]);
         te = fmaf(ta.hi, FE, te);
-        Re[a] = fmaf(sta.hi, FE, Re[a]);
+        add_to(a, ff{sg * tf[a], sg * tl[a]}, Fr, Fm, FE);
       }
       const ff dr_ = ff_add(sr_, ff_neg(tr));
       float dm[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) dm[k] = sm_[k] - tm[k];
       const float de = se_ - te;
-#pragma unroll
-      for (int a = 0; a < N; ++a) {
-        const ff sta{sg * tf[a], sg * tl[a]};
-        Rr[a] = ff_fma(sta, dr_, Rr[a]);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) Rm[a][k] = fmaf(sta.hi, dm[k], Rm[a][k]);
-        Re[a] = fmaf(sta.hi, de, Re[a]);
-      }
+#pragma unroll 1
+      for (int a = 0; a < N; ++a) add_to(a, ff{sg * tf[a], sg * tl[a]}, dr_, dm, de);
     }
   }
-  // directions meet in shared memory (fixed order d = 0, 1, 2)
+  __syncthreads();
+  // the directions meet in a fixed order (d = 0, 1, 2), into slab 0
+  for (int t = threadIdx.x; t < min(epb, ne - e0) * NV; t += blockDim.x) {
+    const int lq = t / NV, node = t % NV;
+    float* ra = Ra + (size_t)lq * 18 * NV + node;
+    ff r = ff_add(ff_add(ff{ra[0], ra[NV]}, ff{ra[6 * NV], ra[7 * NV]}), ff{ra[12 * NV], ra[13 * NV]});
+    ra[0] = r.hi;
+    ra[NV] = r.lo;
 #pragma unroll
-  for (int dd = 0; dd < 3; ++dd) {
-    if (valid && d == dd) {
-      float* ra = Ra + (size_t)le * 6 * NV + base;
-#pragma unroll
-      for (int a = 0; a < N; ++a) {
-        const int o = a * stride;
-        if (dd == 0) {
-          ra[o] = Rr[a].hi;
-          ra[NV + o] = Rr[a].lo;
-          ra[2 * NV + o] = Rm[a][0];
-          ra[3 * NV + o] = Rm[a][1];
-          ra[4 * NV + o] = Rm[a][2];
-          ra[5 * NV + o] = Re[a];
-        } else {
-          const ff s_ = ff_add(ff{ra[o], ra[NV + o]}, Rr[a]);
-          ra[o] = s_.hi;
-          ra[NV + o] = s_.lo;
-          ra[2 * NV + o] += Rm[a][0];
-          ra[3 * NV + o] += Rm[a][1];
-          ra[4 * NV + o] += Rm[a][2];
-          ra[5 * NV + o] += Re[a];
-        }
-      }
-    }
-    __syncthreads();
+    for (int k = 2; k < 6; ++k) ra[k * NV] = (ra[k * NV] + ra[(6 + k) * NV]) + ra[(12 + k) * NV];
   }
+  __syncthreads();
   const int nel = min(epb, ne - e0);
   // R in FP64: R_m = R(F_m') + u_ref R_rho, R_E = R(F_E') + E_ref R_rho
   // (the momentum's p_ref part needs no term back: its residual vanishes)
   for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
     const int lq = t / NV, node = t % NV;
-    const float* ra = Ra + (size_t)lq * 6 * NV + node;
-    const BRef rf = element_ref(Pd + (size_t)lq * 4 * NV, Pf + (size_t)lq * 25 * NV, NV, ops);
+    const float* ra = Ra + (size_t)lq * 18 * NV + node;
+    const BRef rf = element_ref(Pd + (size_t)lq * 2 * NV, Pf + (size_t)lq * 25 * NV, NV, ops);
     const double Rrho = (double)ra[0] + (double)ra[NV];
     double* rd = Rd + (size_t)lq * 5 * NV + node;
     rd[0] = Rrho;
@@ -388,17 +365,17 @@ __global__ void __launch_bounds__(threads_for(N), 1)
 template <int N>
 cudaError_t launch_bulk_n(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk, cudaStream_t s) {
   constexpr int NV = N * N * N;
-  constexpr int epb = epb_for(N);
+  constexpr int epb = bulk_epb(N);
   const int grid = (ctx->ne + epb - 1) / epb;
-  const size_t smem = (size_t)epb * NV * (9 * sizeof(double) + 31 * sizeof(float));
+  const size_t smem = (size_t)epb * NV * (7 * sizeof(double) + 43 * sizeof(float));
   cudaError_t err =
       cudaFuncSetAttribute(volume_bulk_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   RkArgs r = rk ? *rk : RkArgs{};
   nsfr_prof_begin(ctx, 2, s);
-  volume_bulk_kernel<N><<<grid, threads_for(N), smem, s>>>(u, ctx->lnrec, ctx->metric, ctx->nfp_plus, ctx->face,
-                                                           ctx->invwj, ctx->ops, ctx->nx, ctx->ny, ctx->nz, ctx->ne,
-                                                           ctx->face_flux, epi, r, out, ctx->flag);
+  volume_bulk_kernel<N><<<grid, bulk_threads(N), smem, s>>>(u, ctx->lnrec, ctx->metric, ctx->nfp_plus, ctx->face,
+                                                           ctx->fstar, ctx->invwj, ctx->ops, ctx->nx, ctx->ny,
+                                                           ctx->nz, ctx->ne, epi, r, out, ctx->flag);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
   return cudaGetLastError();

@@ -28,7 +28,7 @@ EXPORTS = ["nsfr_setup", "nsfr_residual", "nsfr_residual_raw", "nsfr_rk_step", "
            "nsfr_vjp", "nsfr_node_coords", "nsfr_get_metrics", "nsfr_set_metrics", "nsfr_quadrature", "nsfr_info", "nsfr_check",
            "nsfr_profile", "nsfr_profile_read", "nsfr_residual_static", "nsfr_kernel_launches", "nsfr_last_error", "nsfr_destroy"]
 KERNELS = ["metrics", "face_states", "volume", "max_wavespeed", "diagnostics", "vjp_face", "vjp_volume",
-           "vjp_metrics"]
+           "vjp_metrics", "face_flux"]
 
 
 class NSFRError(RuntimeError):
