@@ -62,6 +62,7 @@ void free_all(nsfr_ctx* c) {
     if (p) cudaFree(p);
   if (c->metric32) cudaFree(c->metric32);
   if (c->nfp_plus32) cudaFree(c->nfp_plus32);
+  if (c->invwj32) cudaFree(c->invwj32);
   if (c->flag) cudaFree(c->flag);
   if (c->umax) cudaFree(c->umax);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -225,6 +226,9 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
             dalloc(&ctx->flag, 1) == cudaSuccess && dalloc(&ctx->umax, 1) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->flag_host, sizeof(int)) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->umax_host, sizeof(unsigned long long)) == cudaSuccess;
+  if (ok && precision == NSFR_FP32_BULK)
+    ok = dalloc(&ctx->metric32, ne * 18 * nv) == cudaSuccess && dalloc(&ctx->nfp_plus32, ne * 18 * nfp) == cudaSuccess &&
+         dalloc(&ctx->invwj32, ne * nv) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     return bail(NSFR_ERR_OOM);
@@ -248,6 +252,7 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
     ctx->dx = dx;
   }
   if (nsfr_launch_metrics(ctx, 0) != cudaSuccess) return bail(NSFR_ERR_CUDA);
+  if (precision == NSFR_FP32_BULK && nsfr_launch_bulk_tables(ctx, 0) != cudaSuccess) return bail(NSFR_ERR_CUDA);
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(NSFR_ERR_CUDA);
   int f = 0;
   if (cudaMemcpy(&f, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return bail(NSFR_ERR_CUDA);
@@ -388,6 +393,7 @@ nsfr_status nsfr_set_metrics(nsfr_ctx* ctx, const double* C, const double* J, co
   CK(cudaMemcpyAsync(ctx->J, J, ne * nv * sizeof(double), cudaMemcpyDefault, s), "copy J");
   CK(cudaMemcpyAsync(ctx->nfp_plus, Cf, ne * 9 * nfp * sizeof(double), cudaMemcpyDefault, s), "copy Cf");
   CK(nsfr_launch_jacobian_derived(ctx, s), "jacobian_derived_kernel");
+  if (ctx->precision == NSFR_FP32_BULK) CK(nsfr_launch_bulk_tables(ctx, s), "bulk_tables_kernel");
   return read_flag(ctx, s);
 }
 

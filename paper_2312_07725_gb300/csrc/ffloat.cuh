@@ -10,13 +10,49 @@ struct ff {
 
 __device__ __forceinline__ ff ff_make(float h) { return ff{h, 0.0f}; }
 
-// exact split of a double into hi + lo (hi the nearest float)
-__device__ __forceinline__ ff ff_from_double(double x) {
-  const float h = __double2float_rn(x);
-  return ff{h, __double2float_rn(x - (double)h)};
+// FP64 <-> FP32 conversions with integer operations.  The hardware
+// conversions execute on the FP64 pipe, which bounds every residual kernel on
+// this part; these use the integer pipe.  IEEE-754 binary64 -> binary32 drops
+// 29 fraction bits, rounding to nearest (ties away from zero): the carry of the
+// rounding add runs into the exponent field by itself.  Results below the
+// binary32 normal range become signed zero, above it signed infinity; NaN
+// stays NaN.  binary32 -> binary64 is exact for normal numbers and zero
+// (subnormal floats, which the kernels never hold, flush to zero).
+__device__ __forceinline__ float d2f_i(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long r = b + (1ull << 28);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const unsigned int ahi = (unsigned int)(r >> 32) & 0x7fffffffu;
+  // exponent (mod 2^9) and 23 fraction bits; subtracting 896 << 23 rebases the
+  // exponent from bias 1023 to 127 (mod 2^32 this adds 0x40000000)
+  unsigned int f = (unsigned int)(r >> 29) + 0x40000000u;
+  f = ahi < (897u << 20) ? 0u : f;
+  f = ahi >= (1151u << 20) ? 0x7f800000u : f;
+  f = (b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull ? 0x7fc00000u : f;
+  return __uint_as_float(f | sign);
 }
 
-__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double f2d_i(float x) {
+  const unsigned int u = __float_as_uint(x), a = u & 0x7fffffffu, sign = u & 0x80000000u;
+  unsigned int hi = sign | ((a >> 3) + (896u << 20)), lo = a << 29;
+  if (a < 0x00800000u) {  // zero (subnormals flushed)
+    hi = sign;
+    lo = 0u;
+  } else if (a >= 0x7f800000u) {  // infinity, NaN
+    hi = sign | 0x7ff00000u | (a > 0x7f800000u ? 0x00080000u : 0u);
+    lo = 0u;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// split of a double into hi + lo, hi the nearest float: x - hi is exact, so
+// hi + lo carries about 48 bits of x
+__device__ __forceinline__ ff ff_from_double(double x) {
+  const float h = d2f_i(x);
+  return ff{h, d2f_i(x - f2d_i(h))};
+}
+
+__device__ __forceinline__ double ff_to_double(ff a) { return f2d_i(a.hi) + f2d_i(a.lo); }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);

@@ -71,12 +71,13 @@ struct nsfr_ctx {
   // device buffers owned by the context
   double* ctrl = nullptr;     // [ne][q^3][3]
   double* metric = nullptr;   // [ne][9][nv]
-  float* metric32 = nullptr;  // [ne][9][nv] (FP32-bulk contexts)
+  float* metric32 = nullptr;  // [ne][18][nv] float-float w_perp/2 C (FP32-bulk contexts)
   double* J = nullptr;        // [ne][nv]
   double* invwj = nullptr;    // [ne][nv] 1/(w_i w_j w_k J)
   double* wj = nullptr;       // [ne][nv] w_i w_j w_k J
   double* nfp_plus = nullptr; // [ne][3][3][nfp]
-  float* nfp_plus32 = nullptr;
+  float* nfp_plus32 = nullptr; // [ne][3][6][nfp] float-float w_perp C_f (FP32-bulk contexts)
+  float* invwj32 = nullptr;    // [ne][nv] (FP32-bulk contexts)
   double* xyz = nullptr;      // [ne][3][nv]
   double* face = nullptr;     // [ne][6][NSFR_NFIELD][nfp] face-state scratch
   double* lnrec = nullptr;    // [ne][2][nv] ln rho, ln beta of the last face-state pass
@@ -138,6 +139,8 @@ cudaError_t nsfr_launch_volume(nsfr_ctx* ctx, const double* u, double* out, int 
 // residual_bulk.cu: the FP32-bulk form of nsfr_launch_volume
 cudaError_t nsfr_launch_volume_bulk(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk,
                                     cudaStream_t s);
+// float-float tables of the geometry for the bulk kernel (after the metrics change)
+cudaError_t nsfr_launch_bulk_tables(nsfr_ctx* ctx, cudaStream_t s);
 // geometry.cu
 cudaError_t nsfr_launch_metrics(nsfr_ctx* ctx, cudaStream_t s);
 cudaError_t nsfr_launch_jacobian_derived(nsfr_ctx* ctx, cudaStream_t s);

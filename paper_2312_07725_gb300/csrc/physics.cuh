@@ -12,7 +12,7 @@
 // FP64 work is the cost of every kernel on this part (FP32 runs ~74x
 // faster), so the per-node record (Rec) stores what makes each pair cheap:
 // rho, 2 beta, u/2, |u|^2/4, ln rho, ln beta.  Arithmetic means are then plain
-// sums, and reciprocals are Newton iterations on a hardware seed.
+// sums, and reciprocals are FP64 refinements of an FP32 seed.
 #pragma once
 
 #include "nsfr_internal.h"
@@ -63,20 +63,34 @@ __device__ __forceinline__ void store_rec(double* P, int stride, const Rec& a) {
   P[P_LBETA * stride] = a.lb;
 }
 
-// 1/x by Newton's iteration r <- r + r (1 - x r) from the hardware's ~2^-20
-// approximation: one step gives ~1e-12 relative, two give the FP64 result.
+// Reciprocals.  The seed comes from the FP32 unit: the mantissa m in [1, 2)
+// of |x|, truncated to 23 bits, goes through rcp.approx.ftz.f32 (<= 1 ulp),
+// and the exponent of 1/x = 2^(1023-e) (1/m) is rebuilt with integer
+// operations, so that the seed (relative error <= 2^-22) costs no FP64-pipe
+// slot; the FP64 reciprocal approximation, which it replaces, occupies that
+// pipe for about 2.5 FMA slots.  Valid for normal |x| in [2^-1021, 2^1021].
+// Refinement, with e = 1 - x r:
+//   Newton            r <- r + r e            (error e^2 <= 2^-44),
+//   third order       r <- r + r (e + e^2)    (error e^3 <= 2^-66: the FP64 result).
 __device__ __forceinline__ double rcp_seed(double x) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  return r;
+  const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
+  // m = 1.f, f the top 23 fraction bits of x
+  const unsigned int mb = 0x3f800000u | (__funnelshift_l(lo, hi, 3) & 0x007fffffu);
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(mb)));
+  const unsigned int rb = __float_as_uint(rf);  // 1/m in (1/2, 1]: FP32 exponent 126 or 127
+  // FP64 exponent field of the seed: (rb's FP32 exponent - 127) + (1023 - e) + 1023
+  const unsigned int shi = ((rb >> 3) + (1919u << 20) - (hi & 0x7ff00000u)) | (hi & 0x80000000u);
+  return __hiloint2double((int)shi, (int)(rb << 29));
 }
 __device__ __forceinline__ double rcp_newton1(double x) {
   const double r = rcp_seed(x);
   return fma(r, fma(-x, r, 1.0), r);
 }
-__device__ __forceinline__ double rcp_newton2(double x) {
-  const double r = rcp_newton1(x);
-  return fma(r, fma(-x, r, 1.0), r);
+__device__ __forceinline__ double rcp_full(double x) {
+  const double r = rcp_seed(x);
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 
 // u < NSFR_LM_EPS for u = f^2 >= 0, decided on the integer bit pattern
@@ -93,13 +107,13 @@ __device__ __forceinline__ double horner4(const double* c, double u) {
 __device__ __forceinline__ Rec rec_from_conserved(double r, double m0, double m1, double m2, double E, double lr,
                                                   double lb, double gm1, int* flag) {
   Rec a;
-  const double ir = rcp_newton2(r);
+  const double ir = rcp_full(r);
   const double u0 = m0 * ir, u1 = m1 * ir, u2 = m2 * ir;
   const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
   const double p = gm1 * fma(-0.5 * r, q2, E);
   if (!(r > 0.0) || !(p > 0.0)) atomicOr(flag, 1);
   a.r = r;
-  a.b2 = r * rcp_newton2(p);
+  a.b2 = r * rcp_full(p);
   a.u0 = 0.5 * u0;
   a.u1 = 0.5 * u1;
   a.u2 = 0.5 * u2;
@@ -133,7 +147,7 @@ __device__ __forceinline__ void ec_flux_l(const Rec& A, const Rec& B, double n0,
                                           const OpsGL& K, const LA& la, const LB& lb, double F[5]) {
   const double sr = A.r + B.r, dr = A.r - B.r;
   const double s2 = A.b2 + B.b2, d2 = A.b2 - B.b2;
-  const double rb2 = rcp_newton2(s2);
+  const double rb2 = rcp_full(s2);
   const double rr = rcp_newton1(sr);  // only enters f^2, a correction below 1e-4
   const double fr = dr * rr, fb = d2 * rb2;
   const double ur = fr * fr, ub = fb * fb;

@@ -41,7 +41,7 @@ __device__ __forceinline__ BNode bnode_from_rec(const Rec& a) {
   b.u0 = ff_from_double(a.u0);
   b.u1 = ff_from_double(a.u1);
   b.u2 = ff_from_double(a.u2);
-  b.qq = __double2float_rn(a.qq);
+  b.qq = d2f_i(a.qq);
   return b;
 }
 
@@ -74,8 +74,8 @@ __device__ __forceinline__ void bulk_flux(const BNode& A, const BNode& B, ff n0,
   if (lm_small(ub)) ibg = horner4(K.f4g, ub) * rb2;
   else ibg = K.inv_gm1 * (la.lb() - lb.lb()) / d2;
   const double ph = sr * rb2;
-  const float dp = __double2float_rn(ph - ref.p);
-  const float dH = __double2float_rn(fma(ph, irln, ibg) - ref.H);
+  const float dp = d2f_i(ph - ref.p);
+  const float dH = d2f_i(fma(ph, irln, ibg) - ref.H);
   const ff v0 = ff_add(A.u0, B.u0), v1 = ff_add(A.u1, B.u1), v2 = ff_add(A.u2, B.u2);
   const ff un = ff_add(ff_add(ff_mul(v0, n0), ff_mul(v1, n1)), ff_mul(v2, n2));
   Fr = ff_mul(ff_from_double(rln), un);
@@ -91,18 +91,19 @@ __device__ __forceinline__ void bulk_flux(const BNode& A, const BNode& B, ff n0,
   FE = f * (dH + du2 + ref.kin - (A.qq + B.qq));
 }
 
-// reference state of an element: its node 0 (records in shared memory; the
-// float copy of u/2 is doubled exactly)
-__device__ __forceinline__ BRef element_ref(const double* pd, const float* pf, int NV, const OpsGL& ops) {
+// reference state of an element: its node 0 (u_ref from the same float-float
+// split of u/2 that the node records hold, doubled exactly)
+__device__ __forceinline__ BRef make_ref(const Rec& a, const OpsGL& ops) {
   BRef r;
-  const double b20 = pd[NV];
-  r.p = pd[0] / b20;
-  r.H = ops.gamma * ops.inv_gm1 / b20;
-  r.u0 = ff{2.0f * pf[0], 2.0f * pf[3 * NV]};
-  r.u1 = ff{2.0f * pf[NV], 2.0f * pf[4 * NV]};
-  r.u2 = ff{2.0f * pf[2 * NV], 2.0f * pf[5 * NV]};
-  const float a = r.u0.hi, b = r.u1.hi, c = r.u2.hi;
-  r.kin = 0.5f * fmaf(a, a, fmaf(b, b, c * c));
+  const double ib2 = rcp_full(a.b2);
+  r.p = a.r * ib2;
+  r.H = ops.gamma * ops.inv_gm1 * ib2;
+  const ff h0 = ff_from_double(a.u0), h1 = ff_from_double(a.u1), h2 = ff_from_double(a.u2);
+  r.u0 = ff{2.0f * h0.hi, 2.0f * h0.lo};
+  r.u1 = ff{2.0f * h1.hi, 2.0f * h1.lo};
+  r.u2 = ff{2.0f * h2.hi, 2.0f * h2.lo};
+  const float x = r.u0.hi, y = r.u1.hi, z = r.u2.hi;
+  r.kin = 0.5f * fmaf(x, x, fmaf(y, y, z * z));
   return r;
 }
 
@@ -130,17 +131,22 @@ __device__ __forceinline__ void rank_one_sweep_f(float* X, int nel, int d, bool 
 //   floats : u/2 hi(3) lo(3), |u|^2/4, metric hi(9) lo(9)     25 NV
 //   floats : line sums R_rho hi, lo, R_m(3), R_E', one slab
 //            per direction                                     18 NV
+// preceded by the elements' reference states (BRef, 48 bytes each).
+// The float-float metric rows (w_perp / 2 C), face rows (w_perp C_f) and
+// 1/(w J) come from bulk_tables_kernel, once per geometry.
 template <int N>
 __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
-    volume_bulk_kernel(const double* u, const double* __restrict__ lnrec, const double* __restrict__ metric,
-                       const double* __restrict__ nf_plus, const double* __restrict__ face,
-                       const double* __restrict__ fstar, const double* __restrict__ invwj, OpsGL ops, int nx, int ny,
-                       int nz, int ne, int epi, RkArgs rk, double* out, int* flag) {
+    volume_bulk_kernel(const double* u, const double* __restrict__ lnrec, const float* __restrict__ metric32,
+                       const double* __restrict__ nf_plus, const float* __restrict__ nf32,
+                       const double* __restrict__ face, const double* __restrict__ fstar,
+                       const float* __restrict__ invwj32, OpsGL ops, int nx, int ny, int nz, int ne, int epi, RkArgs rk,
+                       double* out, int* flag) {
   constexpr int NV = N * N * N, NFP = N * N, NL = 3 * NFP;
   extern __shared__ double sm[];
   const int epb = blockDim.x / NL;
   const int e0 = blockIdx.x * epb;
-  double* Pd = sm;                                 // [epb][2][NV]
+  BRef* Refs = (BRef*)sm;                          // [epb]
+  double* Pd = (double*)(Refs + epb);              // [epb][2][NV]
   double* Rd = Pd + (size_t)epb * 2 * NV;          // [epb][5][NV]
   float* Pf = (float*)(Rd + (size_t)epb * 5 * NV); // [epb][25][NV]
   float* Ra = Pf + (size_t)epb * 25 * NV;          // [epb][3][6][NV]
@@ -152,6 +158,7 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
     if (e >= ne) continue;
     const double* ue = u + (size_t)e * 5 * NV + node;
     const Rec a = rec_from_conserved(ue[0], ue[NV], ue[2 * NV], ue[3 * NV], ue[4 * NV], 0.0, 0.0, gm1, flag);
+    if (node == 0) Refs[le] = make_ref(a, ops);
     double* pd = Pd + (size_t)le * 2 * NV + node;
     pd[0] = a.r;
     pd[NV] = a.b2;
@@ -163,12 +170,10 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
     pf[3 * NV] = u0.lo;
     pf[4 * NV] = u1.lo;
     pf[5 * NV] = u2.lo;
-    pf[6 * NV] = __double2float_rn(a.qq);
-    for (int r = 0; r < 9; ++r) {
-      const ff m = ff_from_double(0.5 * wperp_of(ops.w, node, N, r / 3) * metric[((size_t)e * 9 + r) * NV + node]);
-      pf[(7 + r) * NV] = m.hi;
-      pf[(16 + r) * NV] = m.lo;
-    }
+    pf[6 * NV] = d2f_i(a.qq);
+    const float* m32 = metric32 + (size_t)e * 18 * NV + node;
+#pragma unroll
+    for (int r = 0; r < 18; ++r) pf[(7 + r) * NV] = m32[r * NV];
   }
   __syncthreads();
 
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
     const float* pf = Pf + (size_t)le * 25 * NV + base;
     const double* Le = lnrec + (size_t)e * 2 * NV + base;  // ln rho, ln beta (read only off the series path)
     float* Rl = Ra + ((size_t)le * 18 + 6 * d) * NV + base;
-    const BRef ref = element_ref(Pd + (size_t)le * 2 * NV, Pf + (size_t)le * 25 * NV, NV, ops);
+    const BRef ref = Refs[le];
     auto node_at = [&](int a) {
       BNode b;
       b.r = pd[a * stride];
@@ -248,6 +253,7 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
       const size_t fe = (size_t)(s ? e : enb) * 3 + d;  // the element whose + face this is
       const double* nf = nf_plus + fe * 3 * NFP + line;
       const double* fsp = fstar + fe * 5 * NFP + line;
+      const float* g32 = nf32 + fe * 6 * NFP + line;  // w_perp C_f as float-float: hi(3), lo(3)
       const double f0 = wperp * nf[0], f1 = wperp * nf[NFP], f2 = wperp * nf[2 * NFP];
       const BNode Fo = bnode_from_rec(load_rec6(fo, NFP));
       // the FP64 face flux in the element's deviation form:
@@ -257,12 +263,13 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
       {
         const double F0 = fsp[0];
         sr_ = ff_from_double(F0);
-        sm_[0] = __double2float_rn(fma(-ref.p, f0, fma(-ff_to_double(ref.u0), F0, fsp[NFP])));
-        sm_[1] = __double2float_rn(fma(-ref.p, f1, fma(-ff_to_double(ref.u1), F0, fsp[2 * NFP])));
-        sm_[2] = __double2float_rn(fma(-ref.p, f2, fma(-ff_to_double(ref.u2), F0, fsp[3 * NFP])));
-        se_ = __double2float_rn(fma(-(ref.H + (double)ref.kin), F0, fsp[4 * NFP]));
+        sm_[0] = d2f_i(fma(-ref.p, f0, fma(-ff_to_double(ref.u0), F0, fsp[NFP])));
+        sm_[1] = d2f_i(fma(-ref.p, f1, fma(-ff_to_double(ref.u1), F0, fsp[2 * NFP])));
+        sm_[2] = d2f_i(fma(-ref.p, f2, fma(-ff_to_double(ref.u2), F0, fsp[3 * NFP])));
+        se_ = d2f_i(fma(-(ref.H + f2d_i(ref.kin)), F0, fsp[4 * NFP]));
       }
-      const ff h0 = ff_from_double(0.5 * f0), h1 = ff_from_double(0.5 * f1), h2 = ff_from_double(0.5 * f2);
+      const ff h0{0.5f * g32[0], 0.5f * g32[3 * NFP]}, h1{0.5f * g32[NFP], 0.5f * g32[4 * NFP]},
+          h2{0.5f * g32[2 * NFP], 0.5f * g32[5 * NFP]};
       const float* tf = s ? ops.tpf : ops.tmf;
       const float* tl = s ? ops.tplo : ops.tmlo;
       const float sg = s ? 1.0f : -1.0f;
@@ -309,14 +316,14 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
   for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
     const int lq = t / NV, node = t % NV;
     const float* ra = Ra + (size_t)lq * 18 * NV + node;
-    const BRef rf = element_ref(Pd + (size_t)lq * 2 * NV, Pf + (size_t)lq * 25 * NV, NV, ops);
-    const double Rrho = (double)ra[0] + (double)ra[NV];
+    const BRef rf = Refs[lq];
+    const double Rrho = f2d_i(ra[0]) + f2d_i(ra[NV]);
     double* rd = Rd + (size_t)lq * 5 * NV + node;
     rd[0] = Rrho;
-    rd[NV] = fma(ff_to_double(rf.u0), Rrho, (double)ra[2 * NV]);
-    rd[2 * NV] = fma(ff_to_double(rf.u1), Rrho, (double)ra[3 * NV]);
-    rd[3 * NV] = fma(ff_to_double(rf.u2), Rrho, (double)ra[4 * NV]);
-    rd[4 * NV] = fma(rf.H + (double)rf.kin, Rrho, (double)ra[5 * NV]);
+    rd[NV] = fma(ff_to_double(rf.u0), Rrho, f2d_i(ra[2 * NV]));
+    rd[2 * NV] = fma(ff_to_double(rf.u1), Rrho, f2d_i(ra[3 * NV]));
+    rd[3 * NV] = fma(ff_to_double(rf.u2), Rrho, f2d_i(ra[4 * NV]));
+    rd[4 * NV] = fma(rf.H + f2d_i(rf.kin), Rrho, f2d_i(ra[5 * NV]));
   }
   __syncthreads();
   const int total = nel * 5 * NV;
@@ -326,7 +333,7 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
     return;
   }
   // weight-adjusted inverse in FP32
-  for (int t = threadIdx.x; t < total; t += blockDim.x) Xf[t] = __double2float_rn(Rd[t]);
+  for (int t = threadIdx.x; t < total; t += blockDim.x) Xf[t] = d2f_i(Rd[t]);
   __syncthreads();
   if (ops.has_K) {
     for (int dd = 0; dd < 3; ++dd) {
@@ -336,7 +343,7 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
   }
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int lq = t / (5 * NV), node = t % NV;
-    Xf[t] *= __double2float_rn(invwj[(size_t)(e0 + lq) * NV + node]);
+    Xf[t] *= invwj32[(size_t)(e0 + lq) * NV + node];
   }
   __syncthreads();
   if (ops.has_K) {
@@ -346,11 +353,11 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
     }
   }
   if (epi == EPI_DUDT) {
-    for (int t = threadIdx.x; t < total; t += blockDim.x) out[off + t] = -(double)Xf[t];
+    for (int t = threadIdx.x; t < total; t += blockDim.x) out[off + t] = -f2d_i(Xf[t]);
   } else {
     const double bdt = rk.b * rk.dt, adt = rk.a_next * rk.dt;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const double k = -(double)Xf[t];
+      const double k = -f2d_i(Xf[t]);
       if (rk.last) {
         rk.unext[off + t] = fma(bdt, k, rk.acc[off + t]);
       } else {
@@ -367,21 +374,59 @@ cudaError_t launch_bulk_n(nsfr_ctx* ctx, const double* u, double* out, int epi, 
   constexpr int NV = N * N * N;
   constexpr int epb = bulk_epb(N);
   const int grid = (ctx->ne + epb - 1) / epb;
-  const size_t smem = (size_t)epb * NV * (7 * sizeof(double) + 43 * sizeof(float));
+  const size_t smem = (size_t)epb * (sizeof(BRef) + NV * (7 * sizeof(double) + 43 * sizeof(float)));
   cudaError_t err =
       cudaFuncSetAttribute(volume_bulk_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   RkArgs r = rk ? *rk : RkArgs{};
   nsfr_prof_begin(ctx, 2, s);
-  volume_bulk_kernel<N><<<grid, bulk_threads(N), smem, s>>>(u, ctx->lnrec, ctx->metric, ctx->nfp_plus, ctx->face,
-                                                           ctx->fstar, ctx->invwj, ctx->ops, ctx->nx, ctx->ny,
-                                                           ctx->nz, ctx->ne, epi, r, out, ctx->flag);
+  volume_bulk_kernel<N><<<grid, bulk_threads(N), smem, s>>>(u, ctx->lnrec, ctx->metric32, ctx->nfp_plus,
+                                                           ctx->nfp_plus32, ctx->face, ctx->fstar, ctx->invwj32,
+                                                           ctx->ops, ctx->nx, ctx->ny, ctx->nz, ctx->ne, epi, r, out,
+                                                           ctx->flag);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
   return cudaGetLastError();
 }
 
 }  // namespace
+
+namespace {
+// float-float tables of one geometry for the bulk kernel: metric rows
+// w_perp/2 C -> metric32[e][18][nv] (9 hi rows, then 9 lo rows), face rows
+// w_perp C_f -> nf32[e][3][6][nfp] (hi xyz, lo xyz), 1/(w J) -> invwj32[e][nv]
+__global__ void bulk_tables_kernel(const double* __restrict__ metric, const double* __restrict__ nf_plus,
+                                   const double* __restrict__ invwj, OpsGL ops, int ne, float* __restrict__ metric32,
+                                   float* __restrict__ nf32, float* __restrict__ invwj32) {
+  const int n = ops.n, nv = n * n * n, nfp = n * n;
+  const size_t nm = (size_t)ne * 9 * nv, nf = (size_t)ne * 9 * nfp, nj = (size_t)ne * nv;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nm + nf + nj; t += (size_t)gridDim.x * blockDim.x) {
+    if (t < nm) {
+      const size_t e = t / (9 * nv);
+      const int r = (int)(t / nv % 9), node = (int)(t % nv);
+      const ff m = ff_from_double(0.5 * wperp_of(ops.w, node, n, r / 3) * metric[t]);
+      metric32[(e * 18 + r) * nv + node] = m.hi;
+      metric32[(e * 18 + 9 + r) * nv + node] = m.lo;
+    } else if (t < nm + nf) {
+      const size_t q = t - nm, ed = q / (3 * nfp);  // e * 3 + d
+      const int c = (int)(q / nfp % 3), line = (int)(q % nfp);
+      const ff g = ff_from_double(ops.w[line % n] * ops.w[line / n] * nf_plus[q]);
+      nf32[(ed * 6 + c) * nfp + line] = g.hi;
+      nf32[(ed * 6 + 3 + c) * nfp + line] = g.lo;
+    } else {
+      const size_t q = t - nm - nf;
+      invwj32[q] = d2f_i(invwj[q]);
+    }
+  }
+}
+}  // namespace
+
+cudaError_t nsfr_launch_bulk_tables(nsfr_ctx* ctx, cudaStream_t s) {
+  bulk_tables_kernel<<<152 * 8, 256, 0, s>>>(ctx->metric, ctx->nfp_plus, ctx->invwj, ctx->ops, ctx->ne,
+                                             ctx->metric32, ctx->nfp_plus32, ctx->invwj32);
+  ctx->launches++;
+  return cudaGetLastError();
+}
 
 cudaError_t nsfr_launch_volume_bulk(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk,
                                     cudaStream_t s) {
