@@ -252,6 +252,22 @@ nsfr_status nsfr_residual_static(const double* u, const double* C, const double*
                                  int ny, int nz, int p, double c, int face_flux, double gamma, double* dudt,
                                  void* stream);
 
+/*
+ * nsfr_math_eval -- y[i] = f(x[i]), i < n, with the library's own device
+ * elementary functions, for checking them against reference values:
+ *   NSFR_FN_LOG  natural logarithm (table-driven, Tang's method; about one
+ *                ulp of max(|ln x|, ln 2))
+ *   NSFR_FN_EXP  exponential (table-driven, Tang's method; about one ulp)
+ *   NSFR_FN_RCP  1/x, FP32 seed and one third-order step (about one ulp)
+ *   NSFR_FN_RCP1 1/x, FP32 seed and one Newton step (relative error <= 2^-43)
+ * The kernels compute the entropy variables, face states and two-point
+ * fluxes with these.  x and y are device buffers of n doubles (n >= 0; they
+ * may alias); asynchronous on the stream.  NSFR_ERR_ARG for an unknown fn, a
+ * NULL or host pointer or n < 0.  No context is needed.
+ */
+typedef enum { NSFR_FN_LOG = 0, NSFR_FN_EXP = 1, NSFR_FN_RCP = 2, NSFR_FN_RCP1 = 3 } nsfr_fn;
+nsfr_status nsfr_math_eval(int fn, const double* x, double* y, long long n, void* stream);
+
 /* nsfr_kernel_launches -- kernels this context has launched so far. */
 long long nsfr_kernel_launches(const nsfr_ctx* ctx);
 

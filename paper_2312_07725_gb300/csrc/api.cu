@@ -452,6 +452,13 @@ nsfr_status nsfr_profile_read(nsfr_ctx* ctx, double* ms, long long* count) {
   return NSFR_OK;
 }
 
+nsfr_status nsfr_math_eval(int fn, const double* x, double* y, long long n, void* stream) {
+  if (fn < NSFR_FN_LOG || fn > NSFR_FN_RCP1 || n < 0) return NSFR_ERR_ARG;
+  if (n == 0) return NSFR_OK;
+  if (!x || !y || !is_device_ptr(x) || !is_device_ptr(y)) return NSFR_ERR_ARG;
+  return nsfr_launch_math_eval(fn, x, y, n, (cudaStream_t)stream) == cudaSuccess ? NSFR_OK : NSFR_ERR_CUDA;
+}
+
 long long nsfr_kernel_launches(const nsfr_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 const char* nsfr_last_error(const nsfr_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }

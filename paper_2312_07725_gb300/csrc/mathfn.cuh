@@ -1,0 +1,55 @@
+// FP64 natural logarithm and exponential for the residual kernels, by P. T. P.
+// Tang's table-driven method (ACM TOMS 15, 1989, for exp; ACM TOMS 16, 1990,
+// for log), in about 12 FP64-pipe operations each; the FP64 pipe bounds every
+// kernel on this part.  Tables: mathfn_tables.h (gen_mathfn_tables.py).
+//
+// nsfr_log: x = 2^k m, m in [1, 2); with c_j ~ 1/(1 + (j + 1/2)/128), j the
+//   top 7 fraction bits of m, r = m c_j - 1 is formed by one FMA (|r| <= 2^-8)
+//   and ln x = k ln 2 - ln c_j + log1p(r), log1p(r) by its Taylor polynomial
+//   to r^7 (truncation below 2^-58).  The error is about one ulp of
+//   max(|ln x|, ln 2): absolute accuracy near x = 1, which is what the entropy
+//   variables and the logarithmic means need.
+// nsfr_exp: x = (32 k + j) ln2/32 + r, |r| <= ln2/64, with the reduction in
+//   Cody and Waite's two-constant form; e^x = 2^k 2^(j/32) (1 + expm1(r)),
+//   expm1(r) by its Taylor polynomial to r^6 (truncation below 2^-58), 2^k
+//   added to the exponent field.  About one ulp.
+// Arguments outside the reduced ranges (x <= 0, subnormal, infinite or NaN
+// for nsfr_log; |x| >= 700 or NaN for nsfr_exp) go to the CUDA library
+// functions; the kernels never produce them for physical states.
+#pragma once
+
+#include "mathfn_tables.h"
+
+__device__ __forceinline__ double nsfr_log(double x) {
+  const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
+  if (hi - 0x00100000u >= 0x7fe00000u) return log(x);
+  const int k = (int)(hi >> 20) - 1023;
+  const int j = (int)((hi >> 13) & 127u);
+  const double m = __hiloint2double((int)((hi & 0x000fffffu) | 0x3ff00000u), (int)lo);
+  const double r = fma(m, __ldg(&NSFR_LOG_C[j]), -1.0);
+  // log1p(r) = r + r^2 q(r),  q = -1/2 + r/3 - r^2/4 + r^3/5 - r^4/6 + r^5/7
+  const double q =
+      fma(fma(fma(fma(fma(1.0 / 7.0, r, -1.0 / 6.0), r, 0.2), r, -0.25), r, 1.0 / 3.0), r, -0.5);
+  // k as a double: 2^52 + 2^31 + k read from its bit pattern, minus 2^52 + 2^31
+  const double kd = __hiloint2double(0x43300000, (int)((unsigned int)k + 0x80000000u)) - 4503601774854144.0;
+  const double t1 = fma(kd, NSFR_LN2_HI, __ldg(&NSFR_LOG_LHI[j]));
+  const double t2 = fma(kd, NSFR_LN2_LO, __ldg(&NSFR_LOG_LLO[j]));
+  return t1 + (fma(r * r, q, r) + t2);
+}
+
+__device__ __forceinline__ double nsfr_exp(double x) {
+  const unsigned int ahi = (unsigned int)__double2hiint(x) & 0x7fffffffu;
+  if (ahi >= 0x4085e000u) return exp(x);  // |x| >= 700, infinity, NaN
+  // n = round(32 x / ln 2) in the low word of t (1.5 2^52 fixes the exponent)
+  const double t = fma(x, NSFR_EXP_INV_L, 6755399441055744.0);
+  const int n = __double2loint(t);
+  const double nd = t - 6755399441055744.0;
+  const double r = fma(-nd, NSFR_EXP_L2, fma(-nd, NSFR_EXP_L1, x));
+  const int j = n & 31, k = n >> 5;
+  // expm1(r) = r + r^2 (1/2 + r/6 + r^2/24 + r^3/120 + r^4/720)
+  const double q = fma(fma(fma(fma(1.0 / 720.0, r, 1.0 / 120.0), r, 1.0 / 24.0), r, 1.0 / 6.0), r, 0.5);
+  const double p = fma(r * r, q, r);
+  const double sh = __ldg(&NSFR_EXP_SHI[j]);
+  const double y = sh + fma(sh, p, __ldg(&NSFR_EXP_SLO[j]));
+  return __hiloint2double(__double2hiint(y) + (int)((unsigned int)k << 20), __double2loint(y));
+}

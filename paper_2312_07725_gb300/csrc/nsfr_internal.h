@@ -149,6 +149,8 @@ cudaError_t nsfr_launch_max_wavespeed(nsfr_ctx* ctx, const double* u, cudaStream
 cudaError_t nsfr_launch_diagnostics(nsfr_ctx* ctx, const double* u, const double* R, double* partial,
                                     int nblocks, cudaStream_t s);
 int nsfr_diag_blocks(nsfr_ctx* ctx);
+// mathfn.cu
+cudaError_t nsfr_launch_math_eval(int fn, const double* x, double* y, long long n, cudaStream_t s);
 // vjp.cu
 cudaError_t nsfr_launch_vjp(nsfr_ctx* ctx, const double* u, const double* dbar, double* ubar,
                             double* xbar, cudaStream_t s);

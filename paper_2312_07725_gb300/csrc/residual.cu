@@ -21,6 +21,7 @@
 //     Pi~^T, 1/(w J), Pi~, each a 1D contraction per direction) and either
 //     stores du/dt or performs the RK stage update in place.
 #include "kernel_common.cuh"
+#include "mathfn.cuh"
 #include "physics.cuh"
 
 namespace {
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
     const double p = gm1 * fma(-0.5 * r, q2, E);
     if (!(r > 0.0) || !(p > 0.0)) atomicOr(flag, 1);
     const double b = 0.5 * r * rcp_full(p);
-    const double lr = log(r), lp = log(p);
+    const double lr = nsfr_log(r), lp = nsfr_log(p);
     const double s = lp - g * lr;
     double* v = sm + (size_t)le * 5 * NV + node;
     v[0] = (g - s) * ops.inv_gm1 - b * q2;
@@ -89,10 +90,10 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
     const double u0 = -w[1] * iv5, u1 = -w[2] * iv5, u2 = -w[3] * iv5;
     const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
     const double sent = g - gm1 * fma(0.5 * b2, q2, w[0]);
-    const double L5 = log(b2);                // ln(2 beta)
+    const double L5 = nsfr_log(b2);           // ln(2 beta)
     const double lr = -(sent + L5) * ops.inv_gm1;  // s = (1-gamma) ln rho - ln(2 beta)
     Rec P;
-    P.r = exp(lr);
+    P.r = nsfr_exp(lr);
     P.b2 = b2;
     P.u0 = 0.5 * u0;
     P.u1 = 0.5 * u1;

@@ -26,7 +26,8 @@ PRECISION = {"fp64": 0, "fp32_bulk": 1}
 # every symbol include/nsfr.h declares
 EXPORTS = ["nsfr_setup", "nsfr_residual", "nsfr_residual_raw", "nsfr_rk_step", "nsfr_entropy",
            "nsfr_vjp", "nsfr_node_coords", "nsfr_get_metrics", "nsfr_set_metrics", "nsfr_quadrature", "nsfr_info", "nsfr_check",
-           "nsfr_profile", "nsfr_profile_read", "nsfr_residual_static", "nsfr_kernel_launches", "nsfr_last_error", "nsfr_destroy"]
+           "nsfr_profile", "nsfr_profile_read", "nsfr_residual_static", "nsfr_math_eval", "nsfr_kernel_launches",
+           "nsfr_last_error", "nsfr_destroy"]
 KERNELS = ["metrics", "face_states", "volume", "max_wavespeed", "diagnostics", "vjp_face", "vjp_volume",
            "vjp_metrics", "face_flux"]
 
@@ -71,6 +72,8 @@ def load_library(path=LIB_PATH):
     lib.nsfr_profile_read.restype = i
     lib.nsfr_residual_static.argtypes = [vp, vp, vp, vp, i, i, i, i, d, i, d, vp, vp]
     lib.nsfr_residual_static.restype = i
+    lib.nsfr_math_eval.argtypes = [i, vp, vp, ctypes.c_longlong, vp]
+    lib.nsfr_math_eval.restype = i
     lib.nsfr_kernel_launches.argtypes = [vp]
     lib.nsfr_kernel_launches.restype = ctypes.c_longlong
     lib.nsfr_last_error.argtypes = [vp]
@@ -125,6 +128,22 @@ def residual_static(u, C, J, Cf, shape, p, c=0.0, face_flux="ec", gamma=1.4, dud
     if st != NSFR_OK:
         raise NSFRError(st, "nsfr_residual_static failed")
     return dudt
+
+
+MATH_FN = {"log": 0, "exp": 1, "rcp": 2, "rcp1": 3}
+
+
+def math_eval(fn, x, y=None, stream=None):
+    """y = fn(x) elementwise with the library's device functions (``log``, ``exp``,
+    ``rcp``: full-precision reciprocal, ``rcp1``: one Newton step), for checking
+    them; x, y contiguous float64 CUDA tensors.  Returns y."""
+    import torch
+    if y is None:
+        y = torch.empty_like(x)
+    st = lib().nsfr_math_eval(MATH_FN[fn], _ptr(x), _ptr(y), x.numel(), _stream(stream))
+    if st != NSFR_OK:
+        raise NSFRError(st, "nsfr_math_eval failed")
+    return y
 
 
 class Solver:

@@ -1,0 +1,98 @@
+"""The library's own FP64 elementary functions (nsfr_math_eval) against numpy's
+(host libm) values and against CUDA's own log/exp on the same GPU.
+
+log and exp are table-driven (Tang's method) and the reciprocals start from an
+FP32 seed; the kernels compute the entropy variables, the face states and the
+two-point fluxes with them, so their error bounds are checked here directly:
+  log   |y - ln x| <= 2 ulp(max(|ln x|, 1/2))  (absolute accuracy near x = 1)
+  exp   |y - e^x|  <= 2 ulp(e^x)
+  rcp   |y - 1/x|  <= 1 ulp(1/x)
+  rcp1  |y x - 1|  <= 2^-43
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+RNG = np.random.default_rng(20231207)
+
+
+def _eval(fn, x):
+    from paper_2312_07725_gb300 import nsfr
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    y = nsfr.math_eval(fn, xd)
+    torch.cuda.synchronize()
+    return y.cpu().numpy(), xd
+
+
+def _log_inputs():
+    m = RNG.uniform(1.0, 2.0, 200_000)
+    k = RNG.integers(-1020, 1020, 200_000)
+    near1 = 1.0 + RNG.uniform(-0.05, 0.05, 50_000)
+    physical = np.concatenate([RNG.uniform(0.5, 3.0, 50_000), RNG.uniform(50.0, 100.0, 50_000),
+                               RNG.uniform(1e-3, 1e-1, 50_000)])
+    edges = np.array([1.0, 2.0, 0.5, np.nextafter(1.0, 2.0), np.nextafter(1.0, 0.0), 2.0 ** -1022, 1.7e308])
+    return np.concatenate([np.ldexp(m, k), near1, physical, edges])
+
+
+def test_log_within_two_ulp_of_libm_and_cuda():
+    x = _log_inputs()
+    y, xd = _eval("log", x)
+    ref = np.log(x)
+    scale = np.spacing(np.maximum(np.abs(ref), 0.5))
+    assert np.max(np.abs(y - ref) / scale) <= 2.0
+    cuda = torch.log(xd).cpu().numpy()
+    assert np.max(np.abs(y - cuda) / scale) <= 3.0
+
+
+def test_log_special_arguments_follow_the_ieee_results():
+    x = np.array([0.0, -0.0, -1.0, np.inf, np.nan, 5e-324, 1e-310])
+    y, _ = _eval("log", x)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ref = np.log(x)
+    assert np.array_equal(np.isnan(y), np.isnan(ref))
+    fin = np.isfinite(ref)
+    assert np.all(y[~np.isnan(ref) & ~fin] == ref[~np.isnan(ref) & ~fin])
+    assert np.allclose(y[fin], ref[fin], rtol=1e-15, atol=0)
+
+
+def test_exp_within_two_ulp_of_libm_and_cuda():
+    x = np.concatenate([RNG.uniform(-699.0, 699.0, 200_000), RNG.uniform(-1.0, 1.0, 100_000),
+                        RNG.uniform(-10.0, 10.0, 100_000), np.array([0.0, -0.0, 1.0, -1.0, 1e-20, 699.9])])
+    y, xd = _eval("exp", x)
+    ref = np.exp(x)
+    assert np.max(np.abs(y - ref) / np.spacing(ref)) <= 2.0
+    cuda = torch.exp(xd).cpu().numpy()
+    assert np.max(np.abs(y - cuda) / np.spacing(ref)) <= 3.0
+
+
+def test_exp_special_arguments_follow_the_ieee_results():
+    x = np.array([750.0, -750.0, np.inf, -np.inf, np.nan, 709.0, -708.0])
+    y, _ = _eval("exp", x)
+    with np.errstate(over="ignore"):
+        ref = np.exp(x)
+    assert np.array_equal(np.isnan(y), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    assert np.allclose(y[ok], ref[ok], rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_reciprocals_meet_their_bounds(sign):
+    m = RNG.uniform(1.0, 2.0, 300_000)
+    k = RNG.integers(-1000, 1000, 300_000)
+    x = sign * np.concatenate([np.ldexp(m, k), RNG.uniform(0.01, 100.0, 100_000), np.array([1.0, 2.0, 3.0, 71.4])])
+    y, _ = _eval("rcp", x)
+    ref = 1.0 / x
+    assert np.max(np.abs(y - ref) / np.spacing(np.abs(ref))) <= 1.0
+    y1, _ = _eval("rcp1", x)
+    assert np.max(np.abs(y1 * x - 1.0)) <= 2.0 ** -43
+
+
+def test_math_eval_rejects_host_buffers_and_unknown_functions():
+    from paper_2312_07725_gb300 import NSFRError, nsfr
+    x = torch.ones(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(NSFRError):
+        nsfr.math_eval("log", x.cpu(), torch.empty(4, dtype=torch.float64))
+    with pytest.raises(KeyError):
+        nsfr.math_eval("sin", x)
