@@ -40,6 +40,10 @@ import workloads as wl  # noqa: E402
 # division 1): per two-point flux evaluation (the Chandrashekar flux with its
 # two log means) and per accumulation of one flux into two residual entries
 FLOPS_PER_FLUX = 55
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one volume_kernel<5>
+# launch per element, from an ncu --set full capture at 24^3 elements (633.2 MB for
+# 13,824 elements; every buffer the kernel touches scales with the element count)
+VOLUME_DRAM_BYTES_PER_ELEMENT = {4: 633.25e6 / 13824}
 FLOPS_PER_ACC = 20
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -301,7 +305,8 @@ def run_ours(args, rank, ws, dist):
     achieved = flops / (vol_ms / vol_n / 1e3) / 1e12
     peak, peak_src = fp64_peak(clk)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "volume_kernel<5> (FP64 pipe)", "peak_source": peak_src,
+            "traffic": (VOLUME_DRAM_BYTES_PER_ELEMENT[p] * N ** 3 if p in VOLUME_DRAM_BYTES_PER_ELEMENT else None),
+            "traffic_unit": "bytes per launch", "kernel": f"volume_kernel<{p + 1}> (FP64 pipe)", "peak_source": peak_src,
             "peak_measured_dfma_probe": FP64_MEASURED_TFLOPS, "frac_of_measured": achieved / FP64_MEASURED_TFLOPS,
             "flops_per_launch": flops, "flux_evals_per_element": counts}
     cpu = None

@@ -62,20 +62,21 @@ __device__ __forceinline__ void bulk_flux(const BNode& A, const BNode& B, ff n0,
   const double rb2 = rcp_newton1(s2), rr = rcp_newton1(sr);
   const double fr = dr * rr, fb = d2 * rb2;
   const double ur = fr * fr, ub = fb * fb;
-  double rln, irln, ibg;
+  // H s2 = p_hat s2 / rho_ln + s2 / (2 (gamma-1) beta_ln) = a + b, with on the
+  // series paths a = 2 atanh(f_r)/f_r and b = F4g(u_b) (the sums' s2 and sr cancel)
+  double rln, a, b;
   if (lm_small(ur)) {
     rln = sr * horner4(K.gh, ur);
-    irln = horner4(K.fr2, ur) * rr;
+    a = horner4(K.fr2, ur);
   } else {
     const double dl = la.lr() - lb.lr();
     rln = dr / dl;
-    irln = dl / dr;
+    a = sr * dl / dr;
   }
-  if (lm_small(ub)) ibg = horner4(K.f4g, ub) * rb2;
-  else ibg = K.inv_gm1 * (la.lb() - lb.lb()) / d2;
-  const double ph = sr * rb2;
-  const float dp = d2f_i(ph - ref.p);
-  const float dH = d2f_i(fma(ph, irln, ibg) - ref.H);
+  if (lm_small(ub)) b = horner4(K.f4g, ub);
+  else b = K.inv_gm1 * (la.lb() - lb.lb()) * s2 / d2;
+  const float dp = d2f_i(fma(sr, rb2, -ref.p));
+  const float dH = d2f_i(fma(a + b, rb2, -ref.H));
   const ff v0 = ff_add(A.u0, B.u0), v1 = ff_add(A.u1, B.u1), v2 = ff_add(A.u2, B.u2);
   const ff un = ff_add(ff_add(ff_mul(v0, n0), ff_mul(v1, n1)), ff_mul(v2, n2));
   Fr = ff_mul(ff_from_double(rln), un);
