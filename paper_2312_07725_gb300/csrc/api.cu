@@ -56,6 +56,7 @@ void prof_free(nsfr_ctx* c) {
 
 void free_all(nsfr_ctx* c) {
   double* dbl[] = {c->ctrl, c->metric, c->J, c->invwj, c->wj, c->nfp_plus, c->xyz, c->face, c->lnrec, c->fstar,
+                   c->metric_s, c->nf_s,
                    c->ustage, c->acc, c->rtmp, c->hbuf_in, c->hbuf_out, c->red,
                    c->vjp_fown, c->vjp_fnbr, c->vjp_nfbar, c->vjp_mbar, c->vjp_jbar};
   for (double* p : dbl)
@@ -221,7 +222,8 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
             dalloc(&ctx->wj, ne * nv) == cudaSuccess && dalloc(&ctx->nfp_plus, ne * 9 * nfp) == cudaSuccess &&
             dalloc(&ctx->xyz, ne * 3 * nv) == cudaSuccess &&
             dalloc(&ctx->face, ne * 6 * NSFR_NFIELD * nfp) == cudaSuccess && dalloc(&ctx->lnrec, ne * 2 * nv) == cudaSuccess &&
-            dalloc(&ctx->fstar, ne * 15 * nfp) == cudaSuccess &&
+            dalloc(&ctx->fstar, ne * 15 * nfp) == cudaSuccess && dalloc(&ctx->metric_s, ne * 9 * nv) == cudaSuccess &&
+            dalloc(&ctx->nf_s, ne * 9 * nfp) == cudaSuccess &&
             dalloc(&ctx->ustage, ne * 5 * nv) == cudaSuccess && dalloc(&ctx->acc, ne * 5 * nv) == cudaSuccess &&
             dalloc(&ctx->flag, 1) == cudaSuccess && dalloc(&ctx->umax, 1) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->flag_host, sizeof(int)) == cudaSuccess &&
@@ -252,6 +254,7 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
     ctx->dx = dx;
   }
   if (nsfr_launch_metrics(ctx, 0) != cudaSuccess) return bail(NSFR_ERR_CUDA);
+  if (nsfr_launch_scaled_rows(ctx, 0) != cudaSuccess) return bail(NSFR_ERR_CUDA);
   if (precision == NSFR_FP32_BULK && nsfr_launch_bulk_tables(ctx, 0) != cudaSuccess) return bail(NSFR_ERR_CUDA);
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(NSFR_ERR_CUDA);
   int f = 0;
@@ -393,6 +396,7 @@ nsfr_status nsfr_set_metrics(nsfr_ctx* ctx, const double* C, const double* J, co
   CK(cudaMemcpyAsync(ctx->J, J, ne * nv * sizeof(double), cudaMemcpyDefault, s), "copy J");
   CK(cudaMemcpyAsync(ctx->nfp_plus, Cf, ne * 9 * nfp * sizeof(double), cudaMemcpyDefault, s), "copy Cf");
   CK(nsfr_launch_jacobian_derived(ctx, s), "jacobian_derived_kernel");
+  CK(nsfr_launch_scaled_rows(ctx, s), "scaled_rows_kernel");
   if (ctx->precision == NSFR_FP32_BULK) CK(nsfr_launch_bulk_tables(ctx, s), "bulk_tables_kernel");
   return read_flag(ctx, s);
 }

@@ -76,6 +76,8 @@ struct nsfr_ctx {
   double* invwj = nullptr;    // [ne][nv] 1/(w_i w_j w_k J)
   double* wj = nullptr;       // [ne][nv] w_i w_j w_k J
   double* nfp_plus = nullptr; // [ne][3][3][nfp]
+  double* metric_s = nullptr; // [ne][9][nv] metric rows scaled by w_perp / 2
+  double* nf_s = nullptr;     // [ne][3][3][nfp] face rows scaled by w_perp
   float* nfp_plus32 = nullptr; // [ne][3][6][nfp] float-float w_perp C_f (FP32-bulk contexts)
   float* invwj32 = nullptr;    // [ne][nv] (FP32-bulk contexts)
   double* xyz = nullptr;      // [ne][3][nv]
@@ -132,6 +134,8 @@ struct RkArgs {
   int last;           // unext = acc + b dt k (final update)
 };
 cudaError_t nsfr_launch_face_states(nsfr_ctx* ctx, const double* u, cudaStream_t s);
+// w_perp-scaled metric and face rows (after the metric terms change)
+cudaError_t nsfr_launch_scaled_rows(nsfr_ctx* ctx, cudaStream_t s);
 // numerical flux of every face once, from the face states (after nsfr_launch_face_states)
 cudaError_t nsfr_launch_face_flux(nsfr_ctx* ctx, cudaStream_t s);
 cudaError_t nsfr_launch_volume(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk,

@@ -105,13 +105,13 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
   }
 }
 
-// f* of the + face of element e in direction d, for every face node, scaled by
-// the node's w_perp (f* is linear in the face row, its Roe part positively
-// homogeneous): fstar[e][d][5][n^2].  L is the element's own + face state, R
+// f* of the + face of element e in direction d, for every face node, on the
+// face row scaled by the node's w_perp (f* is linear in the face row, its Roe
+// part positively homogeneous): fstar[e][d][5][n^2].  L is the element's own + face state, R
 // the neighbour's - face state; both carry the same face-node index.
 template <int N>
 __global__ void __launch_bounds__(256) face_flux_kernel(const double* __restrict__ face,
-                                                        const double* __restrict__ nf_plus, OpsGL ops, int nx, int ny,
+                                                        const double* __restrict__ nf_s, OpsGL ops, int nx, int ny,
                                                         int nz, int ne, int face_kind, double* __restrict__ fstar) {
   constexpr int NFP = N * N;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -120,10 +120,9 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const double* __restrict
   const int enb = nbr_index(e, d, 1, nx, ny, nz);
   const Rec L = load_rec(face + (((size_t)e * 6 + 2 * d + 1) * NSFR_NFIELD) * NFP + node, NFP);
   const Rec R = load_rec(face + (((size_t)enb * 6 + 2 * d) * NSFR_NFIELD) * NFP + node, NFP);
-  const double* nf = nf_plus + (size_t)ed * 3 * NFP + node;
-  const double wperp = ops.w[node % N] * ops.w[node / N];
+  const double* nf = nf_s + (size_t)ed * 3 * NFP + node;
   double F[5];
-  face_flux(L, R, wperp * nf[0], wperp * nf[NFP], wperp * nf[2 * NFP], ops, face_kind, F);
+  face_flux(L, R, nf[0], nf[NFP], nf[2 * NFP], ops, face_kind, F);
   double* o = fstar + (size_t)ed * 5 * NFP + node;
 #pragma unroll
   for (int k = 0; k < 5; ++k) o[k * NFP] = F[k];
@@ -154,8 +153,8 @@ __device__ __forceinline__ void rank_one_sweep(double* X, int nel, int d, bool t
 // own reads).
 template <int N>
 __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(const double* u, const double* __restrict__ lnrec,
-                                                                const double* __restrict__ metric,
-                                                                const double* __restrict__ nf_plus,
+                                                                const double* __restrict__ metric_s,
+                                                                const double* __restrict__ nf_s,
                                                                 const double* __restrict__ face,
                                                                 const double* __restrict__ fstar,
                                                                 const double* __restrict__ invwj, OpsGL ops, int nx,
@@ -185,16 +184,13 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
     pr[(P_UH + 2) * NV] = a.u2;
     pr[P_QQ * NV] = a.qq;
   }
-  // metric rows of direction d scaled by w_perp / 2: w_perp (the weights of
-  // the two other directions) is constant along a line of direction d, and
-  // the fluxes are linear in the metric row, so the pair weights reduce to S1
+  // metric rows of direction d scaled by w_perp / 2 (scaled_rows_kernel):
+  // w_perp (the weights of the two other directions) is constant along a line
+  // of direction d, and the fluxes are linear in the metric row, so the pair
+  // weights reduce to S1
   for (int t = threadIdx.x; t < epb * 9 * NV; t += blockDim.x) {
-    const int le = t / (9 * NV), e = e0 + le;
-    if (e >= ne) continue;
-    const int node = t % NV, dd = (t / NV) % 9 / 3;
-    const int i = node % N, j = (node / N) % N, k = node / (N * N);
-    const double wp = dd == 0 ? ops.w[j] * ops.w[k] : (dd == 1 ? ops.w[i] * ops.w[k] : ops.w[i] * ops.w[j]);
-    Ms[t] = 0.5 * wp * metric[(size_t)e0 * 9 * NV + t];
+    if (e0 + t / (9 * NV) >= ne) continue;
+    Ms[t] = metric_s[(size_t)e0 * 9 * NV + t];
   }
   for (int t = threadIdx.x; t < epb * 15 * NV; t += blockDim.x) Ra[t] = 0.0;
   __syncthreads();
@@ -212,7 +208,6 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
     const double* Le = lnrec + (size_t)e * 2 * NV + base;  // ln rho, ln beta (read only off the series path)
     const double* Me = Ms + ((size_t)le * 9 + 3 * d) * NV + base;
     double* Rl = Ra + ((size_t)le * 15 + 5 * d) * NV + base;
-    const double wperp = ops.w[l0] * ops.w[l1];
     // volume-volume pairs along the line: each unordered pair once (S1 is skew);
     // the metric rows already carry w_perp / 2
 #pragma unroll 1
@@ -244,9 +239,9 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
       const int enb = nbr_index(e, d, s, nx, ny, nz);
       const double* fo = face + (((size_t)e * 6 + 2 * d + s) * NSFR_NFIELD) * NFP + line;
       const size_t fe = (size_t)(s ? e : enb) * 3 + d;  // the element whose + face this is
-      const double* nf = nf_plus + fe * 3 * NFP + line;
+      const double* nf = nf_s + fe * 3 * NFP + line;  // w_perp C_f
       const double* fsp = fstar + fe * 5 * NFP + line;
-      const double f0 = wperp * nf[0], f1 = wperp * nf[NFP], f2 = wperp * nf[2 * NFP];
+      const double f0 = nf[0], f1 = nf[NFP], f2 = nf[2 * NFP];
       const Rec Fo = load_rec6(fo, NFP);
       const double* t = s ? ops.tp : ops.tm;
       const double sw = s ? 1.0 : -1.0;
@@ -349,7 +344,7 @@ cudaError_t launch_face_flux_n(nsfr_ctx* ctx, cudaStream_t s) {
   if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
   const int grid = (int)((total + 255) / 256);
   nsfr_prof_begin(ctx, 8, s);
-  face_flux_kernel<N><<<grid, 256, 0, s>>>(ctx->face, ctx->nfp_plus, ctx->ops, ctx->nx, ctx->ny, ctx->nz, ctx->ne,
+  face_flux_kernel<N><<<grid, 256, 0, s>>>(ctx->face, ctx->nf_s, ctx->ops, ctx->nx, ctx->ny, ctx->nz, ctx->ne,
                                            ctx->face_flux, ctx->fstar);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
@@ -367,7 +362,7 @@ cudaError_t launch_volume_n(nsfr_ctx* ctx, const double* u, double* out, int epi
   if (err != cudaSuccess) return err;
   RkArgs r = rk ? *rk : RkArgs{};
   nsfr_prof_begin(ctx, 2, s);
-  volume_kernel<N><<<grid, vol_threads(N), smem, s>>>(u, ctx->lnrec, ctx->metric, ctx->nfp_plus, ctx->face,
+  volume_kernel<N><<<grid, vol_threads(N), smem, s>>>(u, ctx->lnrec, ctx->metric_s, ctx->nf_s, ctx->face,
                                                       ctx->fstar, ctx->invwj, ctx->ops, ctx->nx, ctx->ny, ctx->nz,
                                                       ctx->ne, epi, r, out, ctx->flag);
   nsfr_prof_end(ctx, s);
@@ -376,6 +371,36 @@ cudaError_t launch_volume_n(nsfr_ctx* ctx, const double* u, double* out, int epi
 }
 
 }  // namespace
+
+namespace {
+// geometry-only products of the residual kernels: metric rows scaled by
+// w_perp / 2 (w_perp the two GL weights transverse to the row's direction)
+// and face rows scaled by the face node's w_perp
+__global__ void scaled_rows_kernel(const double* __restrict__ metric, const double* __restrict__ nf_plus, OpsGL ops,
+                                   int ne, double* __restrict__ metric_s, double* __restrict__ nf_s) {
+  const int n = ops.n, nv = n * n * n, nfp = n * n;
+  const size_t nm = (size_t)ne * 9 * nv, nf = (size_t)ne * 9 * nfp;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nm + nf; t += (size_t)gridDim.x * blockDim.x) {
+    if (t < nm) {
+      const int node = (int)(t % nv), dd = (int)(t / nv % 9) / 3;
+      const int i = node % n, j = (node / n) % n, k = node / (n * n);
+      const double wp = dd == 0 ? ops.w[j] * ops.w[k] : (dd == 1 ? ops.w[i] * ops.w[k] : ops.w[i] * ops.w[j]);
+      metric_s[t] = 0.5 * wp * metric[t];
+    } else {
+      const size_t q = t - nm;
+      const int line = (int)(q % nfp);
+      const double wperp = ops.w[line % n] * ops.w[line / n];
+      nf_s[q] = wperp * nf_plus[q];
+    }
+  }
+}
+}  // namespace
+
+cudaError_t nsfr_launch_scaled_rows(nsfr_ctx* ctx, cudaStream_t s) {
+  scaled_rows_kernel<<<152 * 8, 256, 0, s>>>(ctx->metric, ctx->nfp_plus, ctx->ops, ctx->ne, ctx->metric_s, ctx->nf_s);
+  ctx->launches++;
+  return cudaGetLastError();
+}
 
 cudaError_t nsfr_launch_face_states(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
   switch (ctx->n) {
@@ -440,8 +465,9 @@ extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, co
   const size_t face_bytes = ne * 6 * NSFR_NFIELD * nfp * sizeof(double);
   const size_t fstar_bytes = ne * 15 * nfp * sizeof(double);
   const size_t jac_bytes = ne * nv * sizeof(double);
-  // error word (padded), face states, face fluxes, 1/(wJ), wJ, ln rho/beta
-  const size_t need = 256 + face_bytes + fstar_bytes + 4 * jac_bytes;
+  const size_t ms_bytes = ne * 9 * nv * sizeof(double), nfs_bytes = ne * 9 * nfp * sizeof(double);
+  // error word (padded), face states, face fluxes, 1/(wJ), wJ, ln rho/beta, scaled metric and face rows
+  const size_t need = 256 + face_bytes + fstar_bytes + 4 * jac_bytes + ms_bytes + nfs_bytes;
   if (need > NSFR_STATIC_SCRATCH_BYTES || ne > (size_t)0x7fffffff) return NSFR_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return NSFR_ERR_CUDA;
@@ -480,11 +506,14 @@ extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, co
   ctx.invwj = (double*)(base + 256 + face_bytes + fstar_bytes);
   ctx.wj = (double*)(base + 256 + face_bytes + fstar_bytes + jac_bytes);
   ctx.lnrec = (double*)(base + 256 + face_bytes + fstar_bytes + 2 * jac_bytes);
+  ctx.metric_s = (double*)(base + 256 + face_bytes + fstar_bytes + 4 * jac_bytes);
+  ctx.nf_s = (double*)(base + 256 + face_bytes + fstar_bytes + 4 * jac_bytes + ms_bytes);
   ctx.metric = const_cast<double*>(C);
   ctx.J = const_cast<double*>(J);
   ctx.nfp_plus = const_cast<double*>(Cf);
   if (cudaMemsetAsync(ctx.flag, 0, sizeof(int), s) != cudaSuccess) return NSFR_ERR_CUDA;
   if (nsfr_launch_jacobian_derived(&ctx, s) != cudaSuccess) return NSFR_ERR_CUDA;
+  if (nsfr_launch_scaled_rows(&ctx, s) != cudaSuccess) return NSFR_ERR_CUDA;
   if (nsfr_launch_face_states(&ctx, u, s) != cudaSuccess) return NSFR_ERR_CUDA;
   if (nsfr_launch_face_flux(&ctx, s) != cudaSuccess) return NSFR_ERR_CUDA;
   if (nsfr_launch_volume(&ctx, u, dudt, EPI_DUDT, nullptr, s) != cudaSuccess) return NSFR_ERR_CUDA;

@@ -138,7 +138,7 @@ __device__ __forceinline__ void rank_one_sweep_f(float* X, int nel, int d, bool 
 template <int N>
 __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
     volume_bulk_kernel(const double* u, const double* __restrict__ lnrec, const float* __restrict__ metric32,
-                       const double* __restrict__ nf_plus, const float* __restrict__ nf32,
+                       const double* __restrict__ nf_s, const float* __restrict__ nf32,
                        const double* __restrict__ face, const double* __restrict__ fstar,
                        const float* __restrict__ invwj32, OpsGL ops, int nx, int ny, int nz, int ne, int epi, RkArgs rk,
                        double* out, int* flag) {
@@ -246,16 +246,15 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
       ra[4 * NV] = Rm2;
       ra[5 * NV] = Re;
     }
-    const double wperp = ops.w[l0] * ops.w[l1];
 #pragma unroll 1
     for (int s = 0; s < 2; ++s) {
       const int enb = nbr_index(e, d, s, nx, ny, nz);
       const double* fo = face + (((size_t)e * 6 + 2 * d + s) * NSFR_NFIELD) * NFP + line;
       const size_t fe = (size_t)(s ? e : enb) * 3 + d;  // the element whose + face this is
-      const double* nf = nf_plus + fe * 3 * NFP + line;
+      const double* nf = nf_s + fe * 3 * NFP + line;  // w_perp C_f
       const double* fsp = fstar + fe * 5 * NFP + line;
-      const float* g32 = nf32 + fe * 6 * NFP + line;  // w_perp C_f as float-float: hi(3), lo(3)
-      const double f0 = wperp * nf[0], f1 = wperp * nf[NFP], f2 = wperp * nf[2 * NFP];
+      const float* g32 = nf32 + fe * 6 * NFP + line;  // the same as float-float: hi(3), lo(3)
+      const double f0 = nf[0], f1 = nf[NFP], f2 = nf[2 * NFP];
       const BNode Fo = bnode_from_rec(load_rec6(fo, NFP));
       // the FP64 face flux in the element's deviation form:
       //   F_m' = F_m - u_ref F_rho - p_ref n,  F_E' = F_E - E_ref F_rho
@@ -381,7 +380,7 @@ cudaError_t launch_bulk_n(nsfr_ctx* ctx, const double* u, double* out, int epi, 
   if (err != cudaSuccess) return err;
   RkArgs r = rk ? *rk : RkArgs{};
   nsfr_prof_begin(ctx, 2, s);
-  volume_bulk_kernel<N><<<grid, bulk_threads(N), smem, s>>>(u, ctx->lnrec, ctx->metric32, ctx->nfp_plus,
+  volume_bulk_kernel<N><<<grid, bulk_threads(N), smem, s>>>(u, ctx->lnrec, ctx->metric32, ctx->nf_s,
                                                            ctx->nfp_plus32, ctx->face, ctx->fstar, ctx->invwj32,
                                                            ctx->ops, ctx->nx, ctx->ny, ctx->nz, ctx->ne, epi, r, out,
                                                            ctx->flag);
@@ -393,10 +392,11 @@ cudaError_t launch_bulk_n(nsfr_ctx* ctx, const double* u, double* out, int epi, 
 }  // namespace
 
 namespace {
-// float-float tables of one geometry for the bulk kernel: metric rows
-// w_perp/2 C -> metric32[e][18][nv] (9 hi rows, then 9 lo rows), face rows
-// w_perp C_f -> nf32[e][3][6][nfp] (hi xyz, lo xyz), 1/(w J) -> invwj32[e][nv]
-__global__ void bulk_tables_kernel(const double* __restrict__ metric, const double* __restrict__ nf_plus,
+// float-float tables of one geometry for the bulk kernel, from the scaled
+// FP64 rows: metric rows w_perp/2 C -> metric32[e][18][nv] (9 hi rows, then 9
+// lo rows), face rows w_perp C_f -> nf32[e][3][6][nfp] (hi xyz, lo xyz),
+// 1/(w J) -> invwj32[e][nv]
+__global__ void bulk_tables_kernel(const double* __restrict__ metric_s, const double* __restrict__ nf_s,
                                    const double* __restrict__ invwj, OpsGL ops, int ne, float* __restrict__ metric32,
                                    float* __restrict__ nf32, float* __restrict__ invwj32) {
   const int n = ops.n, nv = n * n * n, nfp = n * n;
@@ -405,13 +405,13 @@ __global__ void bulk_tables_kernel(const double* __restrict__ metric, const doub
     if (t < nm) {
       const size_t e = t / (9 * nv);
       const int r = (int)(t / nv % 9), node = (int)(t % nv);
-      const ff m = ff_from_double(0.5 * wperp_of(ops.w, node, n, r / 3) * metric[t]);
+      const ff m = ff_from_double(metric_s[t]);
       metric32[(e * 18 + r) * nv + node] = m.hi;
       metric32[(e * 18 + 9 + r) * nv + node] = m.lo;
     } else if (t < nm + nf) {
       const size_t q = t - nm, ed = q / (3 * nfp);  // e * 3 + d
       const int c = (int)(q / nfp % 3), line = (int)(q % nfp);
-      const ff g = ff_from_double(ops.w[line % n] * ops.w[line / n] * nf_plus[q]);
+      const ff g = ff_from_double(nf_s[q]);
       nf32[(ed * 6 + c) * nfp + line] = g.hi;
       nf32[(ed * 6 + 3 + c) * nfp + line] = g.lo;
     } else {
@@ -423,7 +423,7 @@ __global__ void bulk_tables_kernel(const double* __restrict__ metric, const doub
 }  // namespace
 
 cudaError_t nsfr_launch_bulk_tables(nsfr_ctx* ctx, cudaStream_t s) {
-  bulk_tables_kernel<<<152 * 8, 256, 0, s>>>(ctx->metric, ctx->nfp_plus, ctx->invwj, ctx->ops, ctx->ne,
+  bulk_tables_kernel<<<152 * 8, 256, 0, s>>>(ctx->metric_s, ctx->nf_s, ctx->invwj, ctx->ops, ctx->ne,
                                              ctx->metric32, ctx->nfp_plus32, ctx->invwj32);
   ctx->launches++;
   return cudaGetLastError();
