@@ -234,11 +234,11 @@ nsfr_status nsfr_profile_read(nsfr_ctx* ctx, double* ms, long long* count);
  *         nsfr_get_metrics; e.g. copied once from a context)
  *   nx, ny, nz, p, c, face_flux, gamma   as in nsfr_setup (FP64 only)
  *   dudt  device [N_e][5][n^3] output
- * Its working memory (face states, face fluxes, scaled metric rows, 1/(wJ),
- * an error word) is a fixed 16 MiB array inside the library
+ * Its working memory (face states, node records, face fluxes, scaled metric
+ * rows, 1/(wJ), an error word) is a fixed 16 MiB array inside the library
  * (NSFR_STATIC_SCRATCH_BYTES), which every
  * GPU that loads the library keeps until the process exits.  A problem
- * needing more than that, 256 + 8 N_e (72 n^2 + 13 n^3) bytes, is rejected
+ * needing more than that, 256 + 8 N_e (72 n^2 + 19 n^3) bytes, is rejected
  * with NSFR_ERR_ARG before anything runs.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture.  All calls share

@@ -55,7 +55,7 @@ void prof_free(nsfr_ctx* c) {
 }
 
 void free_all(nsfr_ctx* c) {
-  double* dbl[] = {c->ctrl, c->metric, c->J, c->invwj, c->wj, c->nfp_plus, c->xyz, c->face, c->lnrec, c->fstar,
+  double* dbl[] = {c->ctrl, c->metric, c->J, c->invwj, c->wj, c->nfp_plus, c->xyz, c->face, c->nrec, c->fstar,
                    c->metric_s, c->nf_s,
                    c->ustage, c->acc, c->rtmp, c->hbuf_in, c->hbuf_out, c->red,
                    c->vjp_fown, c->vjp_fnbr, c->vjp_nfbar, c->vjp_mbar, c->vjp_jbar};
@@ -221,7 +221,7 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
             dalloc(&ctx->J, ne * nv) == cudaSuccess && dalloc(&ctx->invwj, ne * nv) == cudaSuccess &&
             dalloc(&ctx->wj, ne * nv) == cudaSuccess && dalloc(&ctx->nfp_plus, ne * 9 * nfp) == cudaSuccess &&
             dalloc(&ctx->xyz, ne * 3 * nv) == cudaSuccess &&
-            dalloc(&ctx->face, ne * 6 * NSFR_NFIELD * nfp) == cudaSuccess && dalloc(&ctx->lnrec, ne * 2 * nv) == cudaSuccess &&
+            dalloc(&ctx->face, ne * 6 * NSFR_NFIELD * nfp) == cudaSuccess && dalloc(&ctx->nrec, ne * NSFR_NFIELD * nv) == cudaSuccess &&
             dalloc(&ctx->fstar, ne * 15 * nfp) == cudaSuccess && dalloc(&ctx->metric_s, ne * 9 * nv) == cudaSuccess &&
             dalloc(&ctx->nf_s, ne * 9 * nfp) == cudaSuccess &&
             dalloc(&ctx->ustage, ne * 5 * nv) == cudaSuccess && dalloc(&ctx->acc, ne * 5 * nv) == cudaSuccess &&

@@ -82,7 +82,7 @@ struct nsfr_ctx {
   float* invwj32 = nullptr;    // [ne][nv] (FP32-bulk contexts)
   double* xyz = nullptr;      // [ne][3][nv]
   double* face = nullptr;     // [ne][6][NSFR_NFIELD][nfp] face-state scratch
-  double* lnrec = nullptr;    // [ne][2][nv] ln rho, ln beta of the last face-state pass
+  double* nrec = nullptr;     // [ne][8][nv] node records (Rec fields) of the last face-state pass
   double* fstar = nullptr;    // [ne][3][5][nfp] w_perp-scaled numerical flux of each + face
   double* ustage = nullptr;   // [ne][5][nv]
   double* acc = nullptr;      // [ne][5][nv]

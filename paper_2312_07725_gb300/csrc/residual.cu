@@ -30,15 +30,15 @@ using namespace nsfr_k;
 template <int N>
 __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double* __restrict__ u, OpsGL ops,
                                                                     double* __restrict__ face,
-                                                                    double* __restrict__ lnrec, int ne, int* flag) {
+                                                                    double* __restrict__ nrec, int ne, int* flag) {
   constexpr int NV = N * N * N, NFP = N * N, NL = 3 * NFP;
   extern __shared__ double sm[];
   const int epb = blockDim.x / NL;
   const int e0 = blockIdx.x * epb;
   const double g = ops.gamma, gm1 = g - 1.0;
   const double ln2 = 0.69314718055994530942;
-  // v(u) at every node of the block's elements; ln rho and ln beta are kept
-  // for the volume kernel, which needs them for its logarithmic means
+  // v(u) at every node of the block's elements; the node records (rho, 2 beta,
+  // u/2, |u|^2/4, ln rho, ln beta) are kept for the volume kernels
   for (int t = threadIdx.x; t < epb * NV; t += blockDim.x) {
     const int le = t / NV, node = t % NV, e = e0 + le;
     if (e >= ne) continue;
@@ -58,8 +58,16 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
     v[2 * NV] = 2.0 * b * u1;
     v[3 * NV] = 2.0 * b * u2;
     v[4 * NV] = -2.0 * b;
-    lnrec[(size_t)e * 2 * NV + node] = lr;
-    lnrec[(size_t)e * 2 * NV + NV + node] = lr - lp - ln2;  // ln beta = ln rho - ln 2p
+    Rec a;
+    a.r = r;
+    a.b2 = 2.0 * b;
+    a.u0 = 0.5 * u0;
+    a.u1 = 0.5 * u1;
+    a.u2 = 0.5 * u2;
+    a.qq = 0.25 * q2;
+    a.lr = lr;
+    a.lb = lr - lp - ln2;  // ln beta = ln rho - ln 2p
+    store_rec(nrec + (size_t)e * NSFR_NFIELD * NV + node, NV, a);
   }
   __syncthreads();
   const int le = threadIdx.x / NL, l = threadIdx.x % NL, e = e0 + le;
@@ -148,11 +156,11 @@ __device__ __forceinline__ void rank_one_sweep(double* X, int nel, int d, bool t
   }
 }
 
-// ``u`` is not __restrict__: in the middle RK stages the epilogue writes the
-// next stage state over it (each CTA only over its own elements, after its
-// own reads).
+// The stage state itself is not read: its node records come from the
+// face-state pass (nrec), so the epilogue may write the next stage state over
+// the buffer the stage started from.
 template <int N>
-__global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(const double* u, const double* __restrict__ lnrec,
+__global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(const double* __restrict__ nrec,
                                                                 const double* __restrict__ metric_s,
                                                                 const double* __restrict__ nf_s,
                                                                 const double* __restrict__ face,
@@ -164,25 +172,16 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
   extern __shared__ double sm[];
   const int epb = blockDim.x / NL;
   const int e0 = blockIdx.x * epb;
-  double* P = sm;                      // [epb][6][NV] node records (the logs stay in lnrec)
+  double* P = sm;                      // [epb][6][NV] node records (the logs stay in nrec)
   double* Ms = P + (size_t)epb * 6 * NV;  // [epb][9][NV] metric rows / 2
   double* Ra = Ms + (size_t)epb * 9 * NV;  // [epb][3][5][NV] line sums, one slab per direction
   double* Rs = P;                          // [epb][5][NV] residual (after the line phase)
-  const double gm1 = ops.gamma - 1.0;
 
-  // prologue: node records and half metric rows of the block's elements
-  for (int t = threadIdx.x; t < epb * NV; t += blockDim.x) {
-    const int le = t / NV, node = t % NV, e = e0 + le;
-    if (e >= ne) continue;
-    const double* ue = u + (size_t)e * 5 * NV + node;
-    const Rec a = rec_from_conserved(ue[0], ue[NV], ue[2 * NV], ue[3 * NV], ue[4 * NV], 0.0, 0.0, gm1, flag);
-    double* pr = P + (size_t)le * 6 * NV + node;
-    pr[P_RHO * NV] = a.r;
-    pr[P_B2 * NV] = a.b2;
-    pr[P_UH * NV] = a.u0;
-    pr[(P_UH + 1) * NV] = a.u1;
-    pr[(P_UH + 2) * NV] = a.u2;
-    pr[P_QQ * NV] = a.qq;
+  // prologue: node records (fields rho .. |u|^2/4) and half metric rows of the block's elements
+  for (int t = threadIdx.x; t < epb * 6 * NV; t += blockDim.x) {
+    const int le = t / (6 * NV);
+    if (e0 + le >= ne) continue;
+    P[t] = nrec[((size_t)(e0 + le) * NSFR_NFIELD) * NV + t % (6 * NV)];
   }
   // metric rows of direction d scaled by w_perp / 2 (scaled_rows_kernel):
   // w_perp (the weights of the two other directions) is constant along a line
@@ -205,7 +204,7 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
   line_geometry<N>(d, l0, l1, base, stride);
   if (le < epb && e < ne) {
     const double* Pe = P + (size_t)le * 6 * NV + base;
-    const double* Le = lnrec + (size_t)e * 2 * NV + base;  // ln rho, ln beta (read only off the series path)
+    const double* Le = nrec + ((size_t)e * NSFR_NFIELD + P_LRHO) * NV + base;  // ln rho, ln beta (read only off the series path)
     const double* Me = Ms + ((size_t)le * 9 + 3 * d) * NV + base;
     double* Rl = Ra + ((size_t)le * 15 + 5 * d) * NV + base;
     // volume-volume pairs along the line: each unordered pair once (S1 is skew);
@@ -332,7 +331,7 @@ cudaError_t launch_face_n(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
   cudaError_t err = cudaFuncSetAttribute(face_state_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   nsfr_prof_begin(ctx, 1, s);
-  face_state_kernel<N><<<grid, threads_for(N), smem, s>>>(u, ctx->ops, ctx->face, ctx->lnrec, ctx->ne, ctx->flag);
+  face_state_kernel<N><<<grid, threads_for(N), smem, s>>>(u, ctx->ops, ctx->face, ctx->nrec, ctx->ne, ctx->flag);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
   return cudaGetLastError();
@@ -362,7 +361,7 @@ cudaError_t launch_volume_n(nsfr_ctx* ctx, const double* u, double* out, int epi
   if (err != cudaSuccess) return err;
   RkArgs r = rk ? *rk : RkArgs{};
   nsfr_prof_begin(ctx, 2, s);
-  volume_kernel<N><<<grid, vol_threads(N), smem, s>>>(u, ctx->lnrec, ctx->metric_s, ctx->nf_s, ctx->face,
+  volume_kernel<N><<<grid, vol_threads(N), smem, s>>>(ctx->nrec, ctx->metric_s, ctx->nf_s, ctx->face,
                                                       ctx->fstar, ctx->invwj, ctx->ops, ctx->nx, ctx->ny, ctx->nz,
                                                       ctx->ne, epi, r, out, ctx->flag);
   nsfr_prof_end(ctx, s);
@@ -466,8 +465,8 @@ extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, co
   const size_t fstar_bytes = ne * 15 * nfp * sizeof(double);
   const size_t jac_bytes = ne * nv * sizeof(double);
   const size_t ms_bytes = ne * 9 * nv * sizeof(double), nfs_bytes = ne * 9 * nfp * sizeof(double);
-  // error word (padded), face states, face fluxes, 1/(wJ), wJ, ln rho/beta, scaled metric and face rows
-  const size_t need = 256 + face_bytes + fstar_bytes + 4 * jac_bytes + ms_bytes + nfs_bytes;
+  // error word (padded), face states, face fluxes, 1/(wJ), wJ, node records, scaled metric and face rows
+  const size_t need = 256 + face_bytes + fstar_bytes + (2 + NSFR_NFIELD) * jac_bytes + ms_bytes + nfs_bytes;
   if (need > NSFR_STATIC_SCRATCH_BYTES || ne > (size_t)0x7fffffff) return NSFR_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return NSFR_ERR_CUDA;
@@ -505,9 +504,9 @@ extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, co
   ctx.fstar = (double*)(base + 256 + face_bytes);
   ctx.invwj = (double*)(base + 256 + face_bytes + fstar_bytes);
   ctx.wj = (double*)(base + 256 + face_bytes + fstar_bytes + jac_bytes);
-  ctx.lnrec = (double*)(base + 256 + face_bytes + fstar_bytes + 2 * jac_bytes);
-  ctx.metric_s = (double*)(base + 256 + face_bytes + fstar_bytes + 4 * jac_bytes);
-  ctx.nf_s = (double*)(base + 256 + face_bytes + fstar_bytes + 4 * jac_bytes + ms_bytes);
+  ctx.nrec = (double*)(base + 256 + face_bytes + fstar_bytes + 2 * jac_bytes);
+  ctx.metric_s = (double*)(base + 256 + face_bytes + fstar_bytes + (2 + NSFR_NFIELD) * jac_bytes);
+  ctx.nf_s = (double*)(base + 256 + face_bytes + fstar_bytes + (2 + NSFR_NFIELD) * jac_bytes + ms_bytes);
   ctx.metric = const_cast<double*>(C);
   ctx.J = const_cast<double*>(J);
   ctx.nfp_plus = const_cast<double*>(Cf);

@@ -137,7 +137,7 @@ __device__ __forceinline__ void rank_one_sweep_f(float* X, int nel, int d, bool 
 // 1/(w J) come from bulk_tables_kernel, once per geometry.
 template <int N>
 __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
-    volume_bulk_kernel(const double* u, const double* __restrict__ lnrec, const float* __restrict__ metric32,
+    volume_bulk_kernel(const double* __restrict__ nrec, const float* __restrict__ metric32,
                        const double* __restrict__ nf_s, const float* __restrict__ nf32,
                        const double* __restrict__ face, const double* __restrict__ fstar,
                        const float* __restrict__ invwj32, OpsGL ops, int nx, int ny, int nz, int ne, int epi, RkArgs rk,
@@ -152,13 +152,11 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
   float* Pf = (float*)(Rd + (size_t)epb * 5 * NV); // [epb][25][NV]
   float* Ra = Pf + (size_t)epb * 25 * NV;          // [epb][3][6][NV]
   float* Xf = Pf;                                  // epilogue (aliases Pf)
-  const double gm1 = ops.gamma - 1.0;
 
   for (int t = threadIdx.x; t < epb * NV; t += blockDim.x) {
     const int le = t / NV, node = t % NV, e = e0 + le;
     if (e >= ne) continue;
-    const double* ue = u + (size_t)e * 5 * NV + node;
-    const Rec a = rec_from_conserved(ue[0], ue[NV], ue[2 * NV], ue[3 * NV], ue[4 * NV], 0.0, 0.0, gm1, flag);
+    const Rec a = load_rec6(nrec + (size_t)e * NSFR_NFIELD * NV + node, NV);  // from the face-state pass
     if (node == 0) Refs[le] = make_ref(a, ops);
     double* pd = Pd + (size_t)le * 2 * NV + node;
     pd[0] = a.r;
@@ -191,7 +189,7 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
   if (le < epb && e < ne) {
     const double* pd = Pd + (size_t)le * 2 * NV + base;
     const float* pf = Pf + (size_t)le * 25 * NV + base;
-    const double* Le = lnrec + (size_t)e * 2 * NV + base;  // ln rho, ln beta (read only off the series path)
+    const double* Le = nrec + ((size_t)e * NSFR_NFIELD + P_LRHO) * NV + base;  // ln rho, ln beta (read only off the series path)
     float* Rl = Ra + ((size_t)le * 18 + 6 * d) * NV + base;
     const BRef ref = Refs[le];
     auto node_at = [&](int a) {
@@ -380,7 +378,7 @@ cudaError_t launch_bulk_n(nsfr_ctx* ctx, const double* u, double* out, int epi, 
   if (err != cudaSuccess) return err;
   RkArgs r = rk ? *rk : RkArgs{};
   nsfr_prof_begin(ctx, 2, s);
-  volume_bulk_kernel<N><<<grid, bulk_threads(N), smem, s>>>(u, ctx->lnrec, ctx->metric32, ctx->nf_s,
+  volume_bulk_kernel<N><<<grid, bulk_threads(N), smem, s>>>(ctx->nrec, ctx->metric32, ctx->nf_s,
                                                            ctx->nfp_plus32, ctx->face, ctx->fstar, ctx->invwj32,
                                                            ctx->ops, ctx->nx, ctx->ny, ctx->nz, ctx->ne, epi, r, out,
                                                            ctx->flag);
