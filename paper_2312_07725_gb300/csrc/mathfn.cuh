@@ -20,24 +20,54 @@
 
 #include "mathfn_tables.h"
 
-__device__ __forceinline__ double nsfr_log(double x) {
+// where the tables are read from: the global arrays, or a copy a kernel has
+// staged in shared memory (nsfr_stage_tables)
+struct MathTables {
+  const double* c;    // [128] c_j
+  const double* lhi;  // [128] -ln c_j, leading part
+  const double* llo;  // [128] -ln c_j, trailing part
+  const double* shi;  // [32] 2^(j/32), leading part
+  const double* slo;  // [32] 2^(j/32), trailing part
+};
+#define NSFR_MATH_TABLE_DOUBLES (3 * 128 + 2 * 32)
+
+__device__ __forceinline__ MathTables nsfr_global_tables() {
+  return MathTables{NSFR_LOG_C, NSFR_LOG_LHI, NSFR_LOG_LLO, NSFR_EXP_SHI, NSFR_EXP_SLO};
+}
+
+// copy the tables into sm[0 .. NSFR_MATH_TABLE_DOUBLES) (all threads of the
+// block take part; a __syncthreads must follow before use)
+__device__ __forceinline__ MathTables nsfr_stage_tables(double* sm) {
+  for (int i = threadIdx.x; i < NSFR_MATH_TABLE_DOUBLES; i += blockDim.x) {
+    double v;
+    if (i < 128) v = NSFR_LOG_C[i];
+    else if (i < 256) v = NSFR_LOG_LHI[i - 128];
+    else if (i < 384) v = NSFR_LOG_LLO[i - 256];
+    else if (i < 416) v = NSFR_EXP_SHI[i - 384];
+    else v = NSFR_EXP_SLO[i - 416];
+    sm[i] = v;
+  }
+  return MathTables{sm, sm + 128, sm + 256, sm + 384, sm + 416};
+}
+
+__device__ __forceinline__ double nsfr_log(double x, const MathTables& T) {
   const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
   if (hi - 0x00100000u >= 0x7fe00000u) return log(x);
   const int k = (int)(hi >> 20) - 1023;
   const int j = (int)((hi >> 13) & 127u);
   const double m = __hiloint2double((int)((hi & 0x000fffffu) | 0x3ff00000u), (int)lo);
-  const double r = fma(m, __ldg(&NSFR_LOG_C[j]), -1.0);
+  const double r = fma(m, T.c[j], -1.0);
   // log1p(r) = r + r^2 q(r),  q = -1/2 + r/3 - r^2/4 + r^3/5 - r^4/6 + r^5/7
   const double q =
       fma(fma(fma(fma(fma(1.0 / 7.0, r, -1.0 / 6.0), r, 0.2), r, -0.25), r, 1.0 / 3.0), r, -0.5);
   // k as a double: 2^52 + 2^31 + k read from its bit pattern, minus 2^52 + 2^31
   const double kd = __hiloint2double(0x43300000, (int)((unsigned int)k + 0x80000000u)) - 4503601774854144.0;
-  const double t1 = fma(kd, NSFR_LN2_HI, __ldg(&NSFR_LOG_LHI[j]));
-  const double t2 = fma(kd, NSFR_LN2_LO, __ldg(&NSFR_LOG_LLO[j]));
+  const double t1 = fma(kd, NSFR_LN2_HI, T.lhi[j]);
+  const double t2 = fma(kd, NSFR_LN2_LO, T.llo[j]);
   return t1 + (fma(r * r, q, r) + t2);
 }
 
-__device__ __forceinline__ double nsfr_exp(double x) {
+__device__ __forceinline__ double nsfr_exp(double x, const MathTables& T) {
   const unsigned int ahi = (unsigned int)__double2hiint(x) & 0x7fffffffu;
   if (ahi >= 0x4085e000u) return exp(x);  // |x| >= 700, infinity, NaN
   // n = round(32 x / ln 2) in the low word of t (1.5 2^52 fixes the exponent)
@@ -49,7 +79,10 @@ __device__ __forceinline__ double nsfr_exp(double x) {
   // expm1(r) = r + r^2 (1/2 + r/6 + r^2/24 + r^3/120 + r^4/720)
   const double q = fma(fma(fma(fma(1.0 / 720.0, r, 1.0 / 120.0), r, 1.0 / 24.0), r, 1.0 / 6.0), r, 0.5);
   const double p = fma(r * r, q, r);
-  const double sh = __ldg(&NSFR_EXP_SHI[j]);
-  const double y = sh + fma(sh, p, __ldg(&NSFR_EXP_SLO[j]));
+  const double sh = T.shi[j];
+  const double y = sh + fma(sh, p, T.slo[j]);
   return __hiloint2double(__double2hiint(y) + (int)((unsigned int)k << 20), __double2loint(y));
 }
+
+__device__ __forceinline__ double nsfr_log(double x) { return nsfr_log(x, nsfr_global_tables()); }
+__device__ __forceinline__ double nsfr_exp(double x) { return nsfr_exp(x, nsfr_global_tables()); }

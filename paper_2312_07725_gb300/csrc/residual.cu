@@ -37,6 +37,8 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
   const int e0 = blockIdx.x * epb;
   const double g = ops.gamma, gm1 = g - 1.0;
   const double ln2 = 0.69314718055994530942;
+  const MathTables T = nsfr_stage_tables(sm + (size_t)epb * 5 * NV);
+  __syncthreads();
   // v(u) at every node of the block's elements; the node records (rho, 2 beta,
   // u/2, |u|^2/4, ln rho, ln beta) are kept for the volume kernels
   for (int t = threadIdx.x; t < epb * NV; t += blockDim.x) {
@@ -50,7 +52,7 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
     const double p = gm1 * fma(-0.5 * r, q2, E);
     if (!(r > 0.0) || !(p > 0.0)) atomicOr(flag, 1);
     const double b = 0.5 * r * rcp_full(p);
-    const double lr = nsfr_log(r), lp = nsfr_log(p);
+    const double lr = nsfr_log(r, T), lp = nsfr_log(p, T);
     const double s = lp - g * lr;
     double* v = sm + (size_t)le * 5 * NV + node;
     v[0] = (g - s) * ops.inv_gm1 - b * q2;
@@ -98,10 +100,10 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
     const double u0 = -w[1] * iv5, u1 = -w[2] * iv5, u2 = -w[3] * iv5;
     const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
     const double sent = g - gm1 * fma(0.5 * b2, q2, w[0]);
-    const double L5 = nsfr_log(b2);           // ln(2 beta)
+    const double L5 = nsfr_log(b2, T);        // ln(2 beta)
     const double lr = -(sent + L5) * ops.inv_gm1;  // s = (1-gamma) ln rho - ln(2 beta)
     Rec P;
-    P.r = nsfr_exp(lr);
+    P.r = nsfr_exp(lr, T);
     P.b2 = b2;
     P.u0 = 0.5 * u0;
     P.u1 = 0.5 * u1;
@@ -327,7 +329,7 @@ cudaError_t launch_face_n(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
   constexpr int NV = N * N * N;
   constexpr int epb = epb_for(N);
   const int grid = (ctx->ne + epb - 1) / epb;
-  const size_t smem = (size_t)epb * 5 * NV * sizeof(double);
+  const size_t smem = ((size_t)epb * 5 * NV + NSFR_MATH_TABLE_DOUBLES) * sizeof(double);
   cudaError_t err = cudaFuncSetAttribute(face_state_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   nsfr_prof_begin(ctx, 1, s);

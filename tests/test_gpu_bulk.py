@@ -34,6 +34,7 @@ CASES = [
     (2, (3, 2, 5), "hu", "ec", "tgv"),
     (5, (3, 3, 3), "hu", "ec_roe", "unit"),
     (7, (2, 2, 2), "dg", "ec", "tgv"),
+    (4, (3, 1, 3), "dg", "ec_roe", "unit"),  # 9 elements: ragged last CTA
 ]
 
 
