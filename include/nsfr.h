@@ -62,6 +62,7 @@ typedef enum {
 typedef enum { NSFR_FLUX_CHANDRASHEKAR = 0 } nsfr_vol_flux;
 typedef enum { NSFR_FACE_EC = 0, NSFR_FACE_EC_ROE = 1 } nsfr_face_flux;
 typedef enum { NSFR_FP64 = 0, NSFR_FP32_BULK = 1 } nsfr_precision;
+typedef enum { NSFR_NODES_GL = 0, NSFR_NODES_LGL = 1 } nsfr_nodes;
 
 /*
  * nsfr_setup -- build a context: 1D operators, metric terms, workspace.
@@ -84,6 +85,12 @@ typedef enum { NSFR_FP64 = 0, NSFR_FP32_BULK = 1 } nsfr_precision;
  *               contractions in FP32 with FP32 accumulation; log means,
  *               entropy variables, the entropy projection and all
  *               reductions stay FP64 (the state itself is always FP64).
+ *   nodes       the collocated solution / volume quadrature nodes:
+ *               NSFR_NODES_GL (Gauss-Legendre; the state lives at the GL
+ *               nodes) or NSFR_NODES_LGL (Gauss-Lobatto-Legendre, the paper's
+ *               "LGL" integration: the face nodes are boundary volume nodes,
+ *               the setting of its kinetic-energy lemma).  Everything below
+ *               that says "GL nodes" means the chosen set.
  *   out         receives the context (NULL on failure).
  * Metric terms are built on the device in conservative-curl form on the
  * degree-p Lobatto nodes and interpolated to the GL nodes (Eq. GCL); the
@@ -91,7 +98,7 @@ typedef enum { NSFR_FP64 = 0, NSFR_FP32_BULK = 1 } nsfr_precision;
  * NSFR_ERR_MESH if J <= 0 anywhere.  Synchronises the current device.
  */
 nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_geo, int p,
-                       double c, int vol_flux, int face_flux, double gamma, int precision,
+                       double c, int vol_flux, int face_flux, double gamma, int precision, int nodes,
                        nsfr_ctx** out);
 
 /*

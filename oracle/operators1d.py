@@ -1,7 +1,11 @@
-"""One-dimensional reference operators (collocated Lagrange basis on GL nodes).
+"""One-dimensional reference operators (collocated Lagrange basis).
 
 * Lagrange basis and derivative on arbitrary node sets, by the product formula.
-* SBP pieces on GL nodes: W = diag(w), D_ij = l_j'(xi_i), extrapolations
+* The solution and volume quadrature nodes are one set: Gauss-Legendre (GL,
+  the default) or Gauss-Lobatto-Legendre (LGL, the paper's kinetic-energy
+  preserving case: the face nodes are then a subset of the volume nodes,
+  Sec. "Nonlinear Stability", kinetic energy lemma).
+* SBP pieces on those nodes: W = diag(w), D_ij = l_j'(xi_i), extrapolations
   t_-[j] = l_j(-1), t_+[j] = l_j(+1), skew operator S1 = W D - D^T W
   (Sec. "Computational Space", SBP property Eq. SBP).
 * ESFR: K1 = c (D^p)^T W D^p is the 1D form of Eq. Km with J = 1
@@ -64,13 +68,20 @@ def pth_derivative_coeffs(nodes):
 
 
 class Ops1D:
-    """All 1D operators for solution degree p and ESFR parameter c."""
+    """All 1D operators for solution degree p, ESFR parameter c and node set
+    ``nodes`` ("gl" or "lgl")."""
 
-    def __init__(self, p, c=0.0):
+    def __init__(self, p, c=0.0, nodes="gl"):
         self.p = p
         self.n = n = p + 1
         self.c = float(c)
-        self.xi, self.w = quadrature.gauss_legendre(n)
+        self.nodes = nodes
+        if nodes == "gl":
+            self.xi, self.w = quadrature.gauss_legendre(n)
+        elif nodes == "lgl":
+            self.xi, self.w = quadrature.gauss_lobatto(n)
+        else:
+            raise ValueError(f"unknown node set {nodes!r}")
         self.W = np.diag(self.w)
         self.D = lagrange_deriv(self.xi, self.xi)
         self.t_minus = lagrange_eval(self.xi, -1.0)[0]

@@ -12,13 +12,13 @@ from .operators1d import Ops1D
 
 
 class Problem:
-    def __init__(self, ctrl, shape, p, p_geo=None, c=0.0, gamma=1.4, face_flux="ec"):
+    def __init__(self, ctrl, shape, p, p_geo=None, c=0.0, gamma=1.4, face_flux="ec", nodes="gl"):
         self.p = p
         self.n = p + 1
         self.p_geo = p if p_geo is None else p_geo
         self.gamma = gamma
         self.face_flux = face_flux
-        self.ops = Ops1D(p, c)
+        self.ops = Ops1D(p, c, nodes)
         self.mesh = geometry.StructuredMesh(*shape)
         self.geo = geometry.metric_terms(ctrl, self.p_geo, self.ops)
         self.nf = geometry.shared_face_normals(self.geo, self.mesh)

@@ -184,12 +184,13 @@ void nsfr_prof_end(nsfr_ctx* ctx, cudaStream_t s) {
 extern "C" {
 
 nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_geo, int p, double c,
-                       int vol_flux, int face_flux, double gamma, int precision, nsfr_ctx** out) {
+                       int vol_flux, int face_flux, double gamma, int precision, int nodes, nsfr_ctx** out) {
   if (!out) return NSFR_ERR_ARG;
   *out = nullptr;
   if (!grid_nodes || nx < 1 || ny < 1 || nz < 1 || p < 1 || p > 7 || p_geo < 1 || p_geo > p || !(gamma > 1.0) ||
       vol_flux != NSFR_FLUX_CHANDRASHEKAR || (face_flux != NSFR_FACE_EC && face_flux != NSFR_FACE_EC_ROE) ||
-      (precision != NSFR_FP64 && precision != NSFR_FP32_BULK) || !std::isfinite(c) || c < 0.0)
+      (precision != NSFR_FP64 && precision != NSFR_FP32_BULK) || (nodes != NSFR_NODES_GL && nodes != NSFR_NODES_LGL) ||
+      !std::isfinite(c) || c < 0.0)
     return NSFR_ERR_ARG;
   nsfr_ctx* ctx = new (std::nothrow) nsfr_ctx();
   if (!ctx) return NSFR_ERR_OOM;
@@ -208,8 +209,9 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
   ctx->vol_flux = vol_flux;
   ctx->face_flux = face_flux;
   ctx->precision = precision;
+  ctx->nodes = nodes;
   cudaGetDevice(&ctx->device);
-  nsfr_build_ops(p, p_geo, c, gamma, &ctx->ops, &ctx->gops);
+  nsfr_build_ops(p, p_geo, c, gamma, nodes, &ctx->ops, &ctx->gops);
 
   auto bail = [&](nsfr_status st) {
     free_all(ctx);

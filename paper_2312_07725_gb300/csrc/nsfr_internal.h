@@ -56,14 +56,14 @@ struct OpsGeo {
 };
 
 // Host construction of the operators (ops1d.cpp).
-void nsfr_build_ops(int p, int p_geo, double c, double gamma, OpsGL* gl, OpsGeo* geo);
+void nsfr_build_ops(int p, int p_geo, double c, double gamma, int nodes, OpsGL* gl, OpsGeo* geo);
 void nsfr_gauss_legendre(int n, double* x, double* w);
 void nsfr_gauss_lobatto(int n, double* x, double* w);
 
 struct nsfr_ctx {
   int nx, ny, nz, ne, p, n, pg, q, nv, nfp;
   double c, gamma;
-  int vol_flux, face_flux, precision;
+  int vol_flux, face_flux, precision, nodes;
   OpsGL ops;
   OpsGeo gops;
   int device;

@@ -1,4 +1,6 @@
-// Host construction of the 1D operators (run once per context).
+// Host construction of the 1D operators (run once per context).  The solution
+// and volume quadrature share one node set, GL or LGL; below, xg/wg are those
+// nodes and weights whichever set it is.
 //
 // GL and Lobatto rules by Newton iteration on the Legendre recurrence;
 // Lagrange interpolation and differentiation in barycentric form (Berrut &
@@ -114,14 +116,23 @@ static void diff_matrix(int n, const double* x, double* D) {
   }
 }
 
-void nsfr_build_ops(int p, int p_geo, double c, double gamma, OpsGL* gl, OpsGeo* geo) {
+void nsfr_build_ops(int p, int p_geo, double c, double gamma, int nodes, OpsGL* gl, OpsGeo* geo) {
   const int n = p + 1;
   const int q = p_geo + 1;
   std::memset(gl, 0, sizeof(*gl));
   std::memset(geo, 0, sizeof(*geo));
   double xg[NSFR_MAXN], wg[NSFR_MAXN], xl[NSFR_MAXN], wl[NSFR_MAXN], xe[NSFR_MAXN];
-  nsfr_gauss_legendre(n, xg, wg);
   nsfr_gauss_lobatto(n, xl, wl);
+  // solution = volume quadrature nodes: GL, or LGL (then the face nodes are
+  // boundary volume nodes and the extrapolations t_-, t_+ are unit vectors)
+  if (nodes == NSFR_NODES_LGL) {
+    for (int j = 0; j < n; ++j) {
+      xg[j] = xl[j];
+      wg[j] = wl[j];
+    }
+  } else {
+    nsfr_gauss_legendre(n, xg, wg);
+  }
   for (int k = 0; k < q; ++k) xe[k] = (q == 1) ? 0.0 : -1.0 + 2.0 * k / (q - 1);
 
   gl->n = n;

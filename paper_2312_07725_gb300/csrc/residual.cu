@@ -500,7 +500,8 @@ extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, co
   ctx.face_flux = face_flux;
   ctx.precision = NSFR_FP64;
   ctx.device = dev;
-  nsfr_build_ops(p, p, c, gamma, &ctx.ops, &ctx.gops);
+  ctx.nodes = NSFR_NODES_GL;
+  nsfr_build_ops(p, p, c, gamma, NSFR_NODES_GL, &ctx.ops, &ctx.gops);
   ctx.flag = (int*)base;
   ctx.face = (double*)(base + 256);
   ctx.fstar = (double*)(base + 256 + face_bytes);

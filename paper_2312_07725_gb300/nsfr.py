@@ -22,6 +22,7 @@ STATUS = {0: "NSFR_OK", -1: "NSFR_ERR_ARG", -2: "NSFR_ERR_MESH", -3: "NSFR_ERR_C
           -4: "NSFR_ERR_NONPHYSICAL", -5: "NSFR_ERR_OOM", -6: "NSFR_ERR_STATE"}
 FACE_FLUX = {"ec": 0, "ec_roe": 1}
 PRECISION = {"fp64": 0, "fp32_bulk": 1}
+NODES = {"gl": 0, "lgl": 1}
 
 # every symbol include/nsfr.h declares
 EXPORTS = ["nsfr_setup", "nsfr_residual", "nsfr_residual_raw", "nsfr_rk_step", "nsfr_entropy",
@@ -43,7 +44,7 @@ def load_library(path=LIB_PATH):
         raise ImportError(f"{path} is missing: build it with paper_2312_07725_gb300.build.build()")
     lib = ctypes.CDLL(path)
     vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
-    lib.nsfr_setup.argtypes = [vp, i, i, i, i, i, d, i, i, d, i, ctypes.POINTER(vp)]
+    lib.nsfr_setup.argtypes = [vp, i, i, i, i, i, d, i, i, d, i, i, ctypes.POINTER(vp)]
     lib.nsfr_setup.restype = i
     for name in ("nsfr_residual", "nsfr_residual_raw"):
         getattr(lib, name).argtypes = [vp, vp, vp, vp]
@@ -150,18 +151,18 @@ class Solver:
     """One NSFR-EC discretisation (mesh, p, c, fluxes, precision) on the current device."""
 
     def __init__(self, grid_nodes, shape, p, p_geo=None, c=0.0, face_flux="ec", gamma=1.4,
-                 precision="fp64"):
+                 precision="fp64", nodes="gl"):
         self._lib = lib()
         nx, ny, nz = shape
         pg = p if p_geo is None else p_geo
         self.shape, self.p, self.p_geo, self.n = tuple(shape), p, pg, p + 1
         self.nv = self.n ** 3
         self.n_el = nx * ny * nz
-        self.c, self.gamma, self.face_flux, self.precision = c, gamma, face_flux, precision
+        self.c, self.gamma, self.face_flux, self.precision, self.nodes = c, gamma, face_flux, precision, nodes
         self._keep = grid_nodes
         h = ctypes.c_void_p()
         st = self._lib.nsfr_setup(_ptr(grid_nodes), nx, ny, nz, pg, p, float(c), 0, FACE_FLUX[face_flux],
-                                  float(gamma), PRECISION[precision], ctypes.byref(h))
+                                  float(gamma), PRECISION[precision], NODES[nodes], ctypes.byref(h))
         if st != NSFR_OK:
             raise NSFRError(st, "nsfr_setup failed")
         self._h = h

@@ -32,9 +32,9 @@ def c_value(p, c_kind):
     return 0.0 if c_kind == "dg" else c_hu(p)
 
 
-def oracle_problem(shape, p, c_kind="dg", face_flux="ec", kind="tgv", p_geo=None):
+def oracle_problem(shape, p, c_kind="dg", face_flux="ec", kind="tgv", p_geo=None, nodes="gl"):
     ctrl = make_ctrl(shape, p, kind, p_geo)
-    P = Problem(ctrl, shape, p, p_geo=p_geo, c=c_value(p, c_kind), face_flux=face_flux)
+    P = Problem(ctrl, shape, p, p_geo=p_geo, c=c_value(p, c_kind), face_flux=face_flux, nodes=nodes)
     return ctrl, P
 
 

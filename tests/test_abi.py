@@ -34,14 +34,17 @@ def test_setup_rejects_bad_arguments_without_touching_a_gpu():
     lib = nsfr.lib()
     h = ctypes.c_void_p()
     buf = (ctypes.c_double * 24)()
-    # p out of range, zero elements, p_geo > p, gamma <= 1, negative c, unknown flux
-    bad = [(1, 1, 1, 1, 9, 0.0, 0, 1.4, 0), (0, 1, 1, 1, 1, 0.0, 0, 1.4, 0), (1, 1, 1, 3, 2, 0.0, 0, 1.4, 0),
-           (1, 1, 1, 1, 1, 0.0, 0, 1.0, 0), (1, 1, 1, 1, 1, -1.0, 0, 1.4, 0), (1, 1, 1, 1, 1, 0.0, 7, 1.4, 0)]
-    for nx, ny, nz, pg, p, c, ff, g, prec in bad:
-        st = lib.nsfr_setup(ctypes.cast(buf, ctypes.c_void_p), nx, ny, nz, pg, p, c, 0, ff, g, prec, ctypes.byref(h))
+    # p out of range, zero elements, p_geo > p, gamma <= 1, negative c, unknown flux, unknown node set
+    bad = [(1, 1, 1, 1, 9, 0.0, 0, 1.4, 0, 0), (0, 1, 1, 1, 1, 0.0, 0, 1.4, 0, 0),
+           (1, 1, 1, 3, 2, 0.0, 0, 1.4, 0, 0), (1, 1, 1, 1, 1, 0.0, 0, 1.0, 0, 0),
+           (1, 1, 1, 1, 1, -1.0, 0, 1.4, 0, 0), (1, 1, 1, 1, 1, 0.0, 7, 1.4, 0, 0),
+           (1, 1, 1, 1, 1, 0.0, 0, 1.4, 0, 2)]
+    for nx, ny, nz, pg, p, c, ff, g, prec, nodes in bad:
+        st = lib.nsfr_setup(ctypes.cast(buf, ctypes.c_void_p), nx, ny, nz, pg, p, c, 0, ff, g, prec, nodes,
+                            ctypes.byref(h))
         assert st == -1
         assert not h.value
-    assert lib.nsfr_setup(None, 1, 1, 1, 1, 1, 0.0, 0, 0, 1.4, 0, ctypes.byref(h)) == -1
+    assert lib.nsfr_setup(None, 1, 1, 1, 1, 1, 0.0, 0, 0, 1.4, 0, 0, ctypes.byref(h)) == -1
     assert lib.nsfr_residual(None, None, None, None) == -1
     assert lib.nsfr_last_error(None) == b"NULL context"
     lib.nsfr_destroy(None)

@@ -24,7 +24,7 @@ TOL = 1e-12
 def solver_for(ctrl, shape, P, precision="fp64"):
     from paper_2312_07725_gb300 import Solver
     return Solver(np.ascontiguousarray(ctrl), shape, P.p, p_geo=P.p_geo, c=P.ops.c, face_flux=P.face_flux,
-                  gamma=P.gamma, precision=precision)
+                  gamma=P.gamma, precision=precision, nodes=P.ops.nodes)
 
 
 def to_dev(x):
