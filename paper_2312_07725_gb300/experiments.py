@@ -60,16 +60,23 @@ def convergence(p, levels, c=0.0, face_flux="ec_roe", tf=0.1, cfl=0.1, precision
             "l2_errors": errs, "orders": orders, "seconds": times}
 
 
-def tgv_history(n_el, p, c, steps, precision="fp64", cfl=0.1, every=10):
-    ctrl = wl.tgv_mesh(n_el, p)
-    S = Solver(ctrl, (n_el,) * 3, p, c=c, precision=precision)
+def tgv_history(n_el, p, c, steps, precision="fp64", cfl=0.1, every=10, tf=None, nodes="gl", face_flux="ec",
+                warp="tgv"):
+    """Entropy, its semi-discrete rate, kinetic energy and conserved totals along a
+    Taylor-Green run: ``steps`` RK4 steps, or up to time ``tf`` when given."""
+    ctrl = wl.tgv_mesh(n_el, p, warp=warp)
+    S = Solver(ctrl, (n_el,) * 3, p, c=c, precision=precision, nodes=nodes, face_flux=face_flux)
     xyz = S.node_coords()
     u = torch.from_numpy(np.ascontiguousarray(wl.tgv_state(xyz))).cuda()
     hist = []
     t = 0.0
     d0 = S.entropy(u)
-    for n in range(steps + 1):
-        if n % every == 0 or n == steps:
+    n = 0
+    dt_prev = 0.0
+    t0 = time.perf_counter()
+    while True:
+        done = (tf is None and n == steps) or (tf is not None and t >= tf - 1e-12)
+        if n % every == 0 or done:
             d = S.entropy(u)
             hist.append({"step": n, "t": t, "entropy": d["entropy"], "entropy_rate": d["entropy_rate"],
                          "entropy_rate_rel": abs(d["entropy_rate"]) / d["entropy_rate_scale"],
@@ -79,9 +86,16 @@ def tgv_history(n_el, p, c, steps, precision="fp64", cfl=0.1, every=10):
                          "Q_drift": [abs(d["Q"][0] - d0["Q"][0]) / abs(d0["Q"][0])]
                          + [abs(d["Q"][k] - d0["Q"][k]) / abs(d0["Q"][0]) for k in (1, 2, 3)]
                          + [abs(d["Q"][4] - d0["Q"][4]) / abs(d0["Q"][4])]})
-        if n < steps:
-            t += S.rk_step(u, cfl=cfl)
-    return {"n_el": n_el, "p": p, "c": c, "precision": precision, "steps": steps, "history": hist}
+        if done:
+            break
+        if tf is not None and n > 0 and t + 1.05 * dt_prev >= tf:
+            dt_prev = S.rk_step(u, dt=tf - t)  # last step lands on tf (the CFL step changes slowly)
+        else:
+            dt_prev = S.rk_step(u, cfl=cfl)
+        t += dt_prev
+        n += 1
+    return {"n_el": n_el, "p": p, "c": c, "precision": precision, "nodes": nodes, "face_flux": face_flux,
+            "steps": n, "t_final": t, "seconds": time.perf_counter() - t0, "history": hist}
 
 
 def adjoint(n_el=16, p=4, steps=50, checkpoint=10, c=None, cfl=0.1):
@@ -167,6 +181,11 @@ def main():
     ap.add_argument("--n-el", type=int, default=32)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--precision", default="both", choices=["fp64", "fp32_bulk", "both"])
+    ap.add_argument("--tf", type=float, default=None, help="TGV: run to this time instead of --steps")
+    ap.add_argument("--every", type=int, default=10)
+    ap.add_argument("--nodes", default="gl", choices=["gl", "lgl"])
+    ap.add_argument("--face-flux", default="ec", choices=["ec", "ec_roe"])
+    ap.add_argument("--warp", default="tgv", choices=["tgv", "paper", "none"])
     args = ap.parse_args()
     import os
     with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden",
@@ -182,7 +201,9 @@ def main():
         for p in args.p:
             for ck in (["dg", "hu"] if args.c == "both" else [args.c]):
                 for prec in (["fp64", "fp32_bulk"] if args.precision == "both" else [args.precision]):
-                    out.append(tgv_history(args.n_el, p, 0.0 if ck == "dg" else c_hu[p], args.steps, prec))
+                    out.append(tgv_history(args.n_el, p, 0.0 if ck == "dg" else c_hu[p], args.steps, prec,
+                                           every=args.every, tf=args.tf, nodes=args.nodes,
+                                           face_flux=args.face_flux, warp=args.warp))
                     print(json.dumps(out[-1]), flush=True)
     else:
         print(json.dumps(adjoint(n_el=args.n_el, p=args.p[0], steps=args.steps)), flush=True)

@@ -94,3 +94,26 @@ def test_lgl_entropy_rate_and_bulk_mode():
     Sb.residual(_dev(u), D)
     torch.cuda.synchronize()
     assert rel_l2(D.cpu().numpy(), P.dudt_abi(u)) < 1e-5
+
+
+def test_kinetic_energy_lemma_holds_for_the_library_residual(monkeypatch):
+    """The kinetic-energy lemma on the library's LGL residual: v_KE . (R - R_p) = 0, with R the
+    library's residual and R_p the oracle's residual of the pressure part p_hat n of the
+    two-point flux alone (R is linear in the flux function).  On GL the same quantity is
+    O(1e-5) of its scale (see tests/test_oracle_lgl.py)."""
+    from oracle import physics
+    from tests.test_oracle_lgl import pressure_part
+    shape, p = (2, 2, 2), 4
+    ctrl, P = oracle_problem(shape, p, "hu", "ec", nodes="lgl")
+    S = _solver(ctrl, shape, P)
+    S.set_metrics(*oracle_metrics_abi(P))
+    u = state_for(P)
+    R = torch.empty(u.shape, dtype=torch.float64, device="cuda")
+    S.residual_raw(_dev(u), R)
+    torch.cuda.synchronize()
+    monkeypatch.setattr(physics, "chandrashekar", pressure_part)
+    Rp = P.to_abi(P.residual(P.to_internal(u)))
+    Rnp = R.cpu().numpy() - Rp
+    vel = u[:, 1:4] / u[:, 0:1]
+    terms = -0.5 * np.sum(vel * vel, axis=1) * Rnp[:, 0] + np.sum(vel * Rnp[:, 1:4], axis=1)
+    assert abs(terms.sum()) < 1e-11 * np.abs(terms).sum()

@@ -160,6 +160,54 @@ def test_lgl_order_of_accuracy(p, Ns):
     assert order > (p + 1) - 0.25, (errs, order)
 
 
+def pressure_part(UL, UR, nvec, gamma):
+    """The pressure part of Chandrashekar's flux: p_hat n in the momentum (p_hat =
+    rho_bar / (2 beta_bar)); zero mass flux.  Its energy component is irrelevant to the
+    kinetic-energy variables, whose energy component is zero, and is left zero."""
+    rL, _, pL = physics.primitive(UL, gamma)
+    rR, _, pR = physics.primitive(UR, gamma)
+    p_hat = 0.5 * (rL + rR) / (rL / (2.0 * pL) + rR / (2.0 * pR))
+    F = np.zeros((5,) + np.shape(p_hat), dtype=np.result_type(UL, nvec))
+    F[1:4] = p_hat * nvec
+    return F
+
+
+def ke_change_without_pressure(P, U, monkeypatch):
+    """sum_i v_KE,i . R_i with the pressure part removed from every two-point flux (volume,
+    hybrid and face), v_KE = (-|u|^2/2, u, 0): the kinetic-energy change net of the
+    pressure work (the paper's kinetic-energy lemma).  Returns (value, scale)."""
+    full = physics.chandrashekar
+
+    def no_pressure(UL, UR, nvec, gamma):
+        return full(UL, UR, nvec, gamma) - pressure_part(UL, UR, nvec, gamma)
+
+    monkeypatch.setattr(physics, "chandrashekar", no_pressure)
+    R = P.residual(U)
+    monkeypatch.setattr(physics, "chandrashekar", full)
+    _, vel, _ = physics.primitive(U, G)
+    terms = -0.5 * np.sum(vel * vel, axis=0) * R[0] + np.sum(vel * R[1:4], axis=0)
+    return diagnostics.fsum(terms), diagnostics.fsum(np.abs(terms))
+
+
+@pytest.mark.parametrize("p", [2, 4])
+def test_kinetic_energy_lemma_lgl_conserves_gl_does_not(p, monkeypatch):
+    """Kinetic-energy lemma (Sec. "Nonlinear Stability"): with a kinetic-energy preserving
+    two-point flux, the kinetic-energy change net of pressure work vanishes discretely only
+    when the face nodes are volume nodes (LGL); on GL it does not (the paper's TGV
+    kinetic-energy figures: 1e-12 on LGL, not conserved on GL)."""
+    shape = (2, 2, 2)
+    ctrl = wl.control_points(*shape, p, -math.pi, math.pi, wl.warp_tgv)
+    out = {}
+    for nodes in ("lgl", "gl"):
+        P = Problem(ctrl, shape, p, c=c_hu(p), nodes=nodes)
+        U = P.to_internal(wl.perturbed_tgv_state(P.node_coords()))
+        out[nodes] = ke_change_without_pressure(P, U, monkeypatch)
+    ke, scale = out["lgl"]
+    assert abs(ke) < 1e-13 * scale
+    ke, scale = out["gl"]
+    assert abs(ke) > 1e-8 * scale
+
+
 def test_lgl_differs_from_gl():
     """The two node sets give different schemes (guards against the option being ignored)."""
     ctrl = wl.control_points(2, 2, 2, 3, -math.pi, math.pi, wl.warp_tgv)

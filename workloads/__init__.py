@@ -87,7 +87,9 @@ def make_warp_scaled(warp, amp):
     return w
 
 
-WARPS = {"none": warp_none, "tgv": warp_tgv, "unit": warp_unit}
+WARPS = {"none": warp_none, "tgv": warp_tgv, "unit": warp_unit,
+         # the paper's Taylor-Green timing mesh: its warp with beta = 1/5 on [-pi, pi]^3
+         "paper": make_warp_paper(0.2, -math.pi, math.pi)}
 
 
 # ---------------------------------------------------------------------------
