@@ -60,7 +60,7 @@ typedef enum {
 } nsfr_status;
 
 typedef enum { NSFR_FLUX_CHANDRASHEKAR = 0 } nsfr_vol_flux;
-typedef enum { NSFR_FACE_EC = 0, NSFR_FACE_EC_ROE = 1 } nsfr_face_flux;
+typedef enum { NSFR_FACE_EC = 0, NSFR_FACE_EC_ROE = 1, NSFR_FACE_EC_ES = 2 } nsfr_face_flux;
 typedef enum { NSFR_FP64 = 0, NSFR_FP32_BULK = 1 } nsfr_precision;
 typedef enum { NSFR_NODES_GL = 0, NSFR_NODES_LGL = 1 } nsfr_nodes;
 
@@ -78,8 +78,12 @@ typedef enum { NSFR_NODES_GL = 0, NSFR_NODES_LGL = 1 } nsfr_nodes;
  *   c           ESFR parameter (c = 0: DG; Sec. "Energy Stable Flux
  *               Reconstruction", Eq. Km with c_(s,v,w) = c^{(s+v+w)/p}).
  *   vol_flux    NSFR_FLUX_CHANDRASHEKAR (the paper's EC two-point flux).
- *   face_flux   NSFR_FACE_EC (entropy conserving) or NSFR_FACE_EC_ROE (EC
- *               flux plus Roe dissipation, Sec. "Nonlinear Stability").
+ *   face_flux   NSFR_FACE_EC (entropy conserving), NSFR_FACE_EC_ROE (EC
+ *               flux plus Roe dissipation, Sec. "Nonlinear Stability") or
+ *               NSFR_FACE_EC_ES (EC flux minus (1/2) R |Lambda| T R^T [[v]]:
+ *               Roe-type dissipation written in the jump of the entropy
+ *               variables with Barth's eigenvector scaling, R T R^T = du/dv,
+ *               so that every face dissipates entropy).
  *   gamma       ratio of specific heats (> 1).
  *   precision   NSFR_FP64, or NSFR_FP32_BULK: flux differencing and operator
  *               contractions in FP32 with FP32 accumulation; log means,

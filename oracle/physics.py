@@ -182,17 +182,69 @@ def roe_matrix_apply(UL, UR, nvec, gamma, absolute=True):
     return nn * out
 
 
+def es_matrix_dissipation(UL, UR, nvec, gamma):
+    """Entropy-variable matrix dissipation R |Lambda| T R^T [[v]], scaled by |n|.
+
+    [[v]] = v(u_R) - v(u_L) is the jump of the entropy variables.  R holds the
+    right eigenvectors of the flux Jacobian along n^ = n/|n| (acoustic waves
+    q -+ a, the entropy wave and the shear waves, q = u . n^), Lambda their
+    speeds, and T Barth's scaling (rho/(2 gamma), rho (gamma-1)/gamma, p, p,
+    rho/(2 gamma)), for which R T R^T = du/dv: the dissipation is then the
+    Roe-type |A_n| [[u]] with [[u]] written through [[v]], and
+    [[v]] . R |Lambda| T R^T [[v]] >= 0 makes every face dissipate entropy.  The
+    matrices are evaluated at the state (rho_ln, u_bar, p_hat = rho_bar /
+    (2 beta_bar)) of Chandrashekar's flux.  The shear waves enter through the
+    projection P = I - n^ n^T, so no tangent basis is needed.
+    """
+    rL, uL, pL = primitive(UL, gamma)
+    rR, uR, pR = primitive(UR, gamma)
+    bL, bR = rL / (2.0 * pL), rR / (2.0 * pR)
+    rho = log_mean(rL, rR)
+    u = 0.5 * (uL + uR)
+    p = 0.5 * (rL + rR) / (bL + bR)
+    nn = np.sqrt(np.sum(nvec * nvec, axis=0))
+    nh = nvec / nn
+    a = np.sqrt(gamma * p / rho)
+    qn = np.sum(u * nh, axis=0)
+    q2 = np.sum(u * u, axis=0)
+    H = a * a / (gamma - 1.0) + 0.5 * q2
+    dv = entropy_variables(UR, gamma) - entropy_variables(UL, gamma)
+    dv0, dvm, dv4 = dv[0], dv[1:4], dv[4]
+    t_ac = rho / (2.0 * gamma)
+    t_en = rho * (gamma - 1.0) / gamma
+
+    def wave(r0, rm, r4):  # r . [[v]]
+        return r0 * dv0 + np.sum(rm * dvm, axis=0) + r4 * dv4
+
+    r1m, r1e = u - a * nh, H - a * qn
+    r5m, r5e = u + a * nh, H + a * qn
+    c1 = _cabs(qn - a) * t_ac * wave(1.0, r1m, r1e)
+    c2 = _cabs(qn) * t_en * wave(1.0, u, 0.5 * q2)
+    c5 = _cabs(qn + a) * t_ac * wave(1.0, r5m, r5e)
+    z = dvm + u * dv4
+    Pz = z - nh * np.sum(nh * z, axis=0)
+    cs = _cabs(qn) * p
+    D0 = c1 + c2 + c5
+    Dm = c1 * r1m + c2 * u + c5 * r5m + cs * Pz
+    D4 = c1 * r1e + c2 * 0.5 * q2 + c5 * r5e + cs * np.sum(u * Pz, axis=0)
+    return nn * np.concatenate([D0[None], Dm, D4[None]], axis=0)
+
+
 def numerical_flux(UL, UR, nvec, gamma, face_flux="ec"):
     """Face flux f*(u_L, u_R; n), n pointing from L to R.
 
     "ec": the EC two-point flux itself; "ec_roe": EC flux minus
-    (1/2)|A_n|(u_R - u_L) (Roe dissipation added to the EC baseline).
+    (1/2)|A_n|(u_R - u_L) (Roe dissipation added to the EC baseline);
+    "ec_es": EC flux minus (1/2) R |Lambda| T R^T [[v]] (entropy-variable
+    matrix dissipation, provably entropy dissipative).
     """
     F = chandrashekar(UL, UR, nvec, gamma)
     if face_flux == "ec":
         return F
     if face_flux == "ec_roe":
         return F - 0.5 * roe_matrix_apply(UL, UR, nvec, gamma, absolute=True)
+    if face_flux == "ec_es":
+        return F - 0.5 * es_matrix_dissipation(UL, UR, nvec, gamma)
     raise ValueError(face_flux)
 
 

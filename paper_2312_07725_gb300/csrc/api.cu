@@ -188,7 +188,7 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
   if (!out) return NSFR_ERR_ARG;
   *out = nullptr;
   if (!grid_nodes || nx < 1 || ny < 1 || nz < 1 || p < 1 || p > 7 || p_geo < 1 || p_geo > p || !(gamma > 1.0) ||
-      vol_flux != NSFR_FLUX_CHANDRASHEKAR || (face_flux != NSFR_FACE_EC && face_flux != NSFR_FACE_EC_ROE) ||
+      vol_flux != NSFR_FLUX_CHANDRASHEKAR || face_flux < NSFR_FACE_EC || face_flux > NSFR_FACE_EC_ES ||
       (precision != NSFR_FP64 && precision != NSFR_FP32_BULK) || (nodes != NSFR_NODES_GL && nodes != NSFR_NODES_LGL) ||
       !std::isfinite(c) || c < 0.0)
     return NSFR_ERR_ARG;

@@ -209,13 +209,60 @@ __device__ __forceinline__ void roe_dissipation(const Rec& L, const Rec& R, doub
   D[4] = nn * (c1 * (Hh - qh * ah) + c5 * (Hh + qh * ah) + c2 * 0.5 * q2h + cs * (uh0 * t0 + uh1 * t1 + uh2 * t2));
 }
 
-// f*(u~_L, u~_R; n): EC flux, minus (1/2)|A_n|(u_R - u_L) with Roe dissipation.
+// D = R |Lambda| T R^T [[v]]: entropy-variable matrix dissipation along n,
+// scaled by |n|.  [[v]] = v(R) - v(L) from the records (s = (1-gamma) ln rho
+// - ln 2 beta, v = ((gamma - s)/(gamma-1) - beta |u|^2, 2 beta u, -2 beta));
+// R, Lambda: eigenvectors and speeds of the flux Jacobian (acoustic q -+ a,
+// entropy and shear waves q, q = u . n^), T Barth's scaling (rho/(2 gamma),
+// rho (gamma-1)/gamma, p, p, rho/(2 gamma)) so that R T R^T = du/dv, all at
+// the state (rho_ln, u_bar, p_hat) of the EC flux.  The shear waves act
+// through the projection I - n^ n^T.
+__device__ __forceinline__ void es_dissipation(const Rec& L, const Rec& R, double n0, double n1, double n2,
+                                               const OpsGL& K, double D[5]) {
+  const double g = K.gamma, ln2 = 0.69314718055994530942;
+  const double sL = (1.0 - g) * L.lr - (L.lb + ln2), sR = (1.0 - g) * R.lr - (R.lb + ln2);
+  const double dv0 = (sL - sR) * K.inv_gm1 - 2.0 * (R.b2 * R.qq - L.b2 * L.qq);
+  const double dm0 = 2.0 * (R.b2 * R.u0 - L.b2 * L.u0), dm1 = 2.0 * (R.b2 * R.u1 - L.b2 * L.u1),
+               dm2 = 2.0 * (R.b2 * R.u2 - L.b2 * L.u2);
+  const double dv4 = L.b2 - R.b2;
+  // averaged state
+  const double sr = L.r + R.r, dr = L.r - R.r;
+  const double fr = dr / sr, ur = fr * fr;
+  const double rho = lm_small(ur) ? sr * horner4(K.gh, ur) : dr / (L.lr - R.lr);
+  const double u0 = L.u0 + R.u0, u1 = L.u1 + R.u1, u2 = L.u2 + R.u2;
+  const double p = sr / (L.b2 + R.b2);
+  const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+  const double h0 = n0 / nn, h1 = n1 / nn, h2 = n2 / nn;
+  const double a = sqrt(g * p / rho);
+  const double qn = u0 * h0 + u1 * h1 + u2 * h2;
+  const double q2 = u0 * u0 + u1 * u1 + u2 * u2;
+  const double H = a * a * K.inv_gm1 + 0.5 * q2;
+  const double t_ac = rho / (2.0 * g), t_en = rho * (g - 1.0) / g;
+  // r . [[v]] for r = (1, u -+ a n^, H -+ a q) and the entropy wave (1, u, q2/2)
+  const double wm = dv0 + (u0 - a * h0) * dm0 + (u1 - a * h1) * dm1 + (u2 - a * h2) * dm2 + (H - a * qn) * dv4;
+  const double wp = dv0 + (u0 + a * h0) * dm0 + (u1 + a * h1) * dm1 + (u2 + a * h2) * dm2 + (H + a * qn) * dv4;
+  const double we = dv0 + u0 * dm0 + u1 * dm1 + u2 * dm2 + 0.5 * q2 * dv4;
+  const double c1 = fabs(qn - a) * t_ac * wm, c5 = fabs(qn + a) * t_ac * wp, c2 = fabs(qn) * t_en * we;
+  const double z0 = dm0 + u0 * dv4, z1 = dm1 + u1 * dv4, z2 = dm2 + u2 * dv4;
+  const double zn = h0 * z0 + h1 * z1 + h2 * z2;
+  const double P0 = z0 - h0 * zn, P1 = z1 - h1 * zn, P2 = z2 - h2 * zn;
+  const double cs = fabs(qn) * p;
+  D[0] = nn * (c1 + c2 + c5);
+  D[1] = nn * (c1 * (u0 - a * h0) + c2 * u0 + c5 * (u0 + a * h0) + cs * P0);
+  D[2] = nn * (c1 * (u1 - a * h1) + c2 * u1 + c5 * (u1 + a * h1) + cs * P1);
+  D[3] = nn * (c1 * (u2 - a * h2) + c2 * u2 + c5 * (u2 + a * h2) + cs * P2);
+  D[4] = nn * (c1 * (H - a * qn) + c2 * 0.5 * q2 + c5 * (H + a * qn) + cs * (u0 * P0 + u1 * P1 + u2 * P2));
+}
+
+// f*(u~_L, u~_R; n): the EC flux, minus (1/2)|A_n|(u_R - u_L) (Roe) or minus
+// (1/2) R |Lambda| T R^T [[v]] (entropy-variable matrix dissipation).
 __device__ __forceinline__ void face_flux(const Rec& L, const Rec& R, double n0, double n1, double n2,
                                           const OpsGL& K, int kind, double F[5]) {
   ec_flux(L, R, n0, n1, n2, K, F);
-  if (kind == NSFR_FACE_EC_ROE) {
+  if (kind == NSFR_FACE_EC_ROE || kind == NSFR_FACE_EC_ES) {
     double D[5];
-    roe_dissipation(L, R, n0, n1, n2, K.gamma, D);
+    if (kind == NSFR_FACE_EC_ROE) roe_dissipation(L, R, n0, n1, n2, K.gamma, D);
+    else es_dissipation(L, R, n0, n1, n2, K, D);
 #pragma unroll
     for (int k = 0; k < 5; ++k) F[k] -= 0.5 * D[k];
   }

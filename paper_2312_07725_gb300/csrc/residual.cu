@@ -460,7 +460,7 @@ extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, co
                                             int nx, int ny, int nz, int p, double c, int face_flux, double gamma,
                                             double* dudt, void* stream) {
   if (!u || !C || !J || !Cf || !dudt || nx < 1 || ny < 1 || nz < 1 || p < 1 || p > 7 || !(gamma > 1.0) ||
-      !(c >= 0.0) || (face_flux != NSFR_FACE_EC && face_flux != NSFR_FACE_EC_ROE))
+      !(c >= 0.0) || face_flux < NSFR_FACE_EC || face_flux > NSFR_FACE_EC_ES)
     return NSFR_ERR_ARG;
   const size_t ne = (size_t)nx * ny * nz, n = p + 1, nv = n * n * n, nfp = n * n;
   const size_t face_bytes = ne * 6 * NSFR_NFIELD * nfp * sizeof(double);

@@ -184,7 +184,8 @@ def main():
     ap.add_argument("--tf", type=float, default=None, help="TGV: run to this time instead of --steps")
     ap.add_argument("--every", type=int, default=10)
     ap.add_argument("--nodes", default="gl", choices=["gl", "lgl"])
-    ap.add_argument("--face-flux", default="ec", choices=["ec", "ec_roe"])
+    ap.add_argument("--face-flux", default=None, choices=["ec", "ec_roe", "ec_es"],
+                    help="face flux (default: ec for tgv, ec_roe for convergence)")
     ap.add_argument("--warp", default="tgv", choices=["tgv", "paper", "none"])
     args = ap.parse_args()
     import os
@@ -195,7 +196,8 @@ def main():
     if args.study == "convergence":
         for p in args.p:
             for ck in (["dg", "hu"] if args.c == "both" else [args.c]):
-                out.append(convergence(p, args.levels, c=0.0 if ck == "dg" else c_hu[p]))
+                out.append(convergence(p, args.levels, c=0.0 if ck == "dg" else c_hu[p],
+                                       face_flux=args.face_flux or "ec_roe"))
                 print(json.dumps(out[-1]), flush=True)
     elif args.study == "tgv":
         for p in args.p:
@@ -203,7 +205,7 @@ def main():
                 for prec in (["fp64", "fp32_bulk"] if args.precision == "both" else [args.precision]):
                     out.append(tgv_history(args.n_el, p, 0.0 if ck == "dg" else c_hu[p], args.steps, prec,
                                            every=args.every, tf=args.tf, nodes=args.nodes,
-                                           face_flux=args.face_flux, warp=args.warp))
+                                           face_flux=args.face_flux or "ec", warp=args.warp))
                     print(json.dumps(out[-1]), flush=True)
     else:
         print(json.dumps(adjoint(n_el=args.n_el, p=args.p[0], steps=args.steps)), flush=True)

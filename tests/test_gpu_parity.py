@@ -65,6 +65,9 @@ CASES = [
     (4, (3, 3, 1), "hu", "ec", "tgv"),
     (4, (3, 1, 3), "hu", "ec_roe", "unit"),
     (6, (3, 1, 1), "hu", "ec", "paper"),
+    # entropy-variable matrix dissipation
+    (3, (3, 2, 2), "dg", "ec_es", "unit"),
+    (5, (2, 2, 1), "hu", "ec_es", "paper"),
 ]
 
 
@@ -153,6 +156,20 @@ def test_diagnostics_match_oracle():
     # EC: the semi-discrete entropy rate vanishes (paper: O(1e-13))
     assert abs(g["entropy_rate"]) < 1e-13 * g["entropy_rate_scale"]
     assert abs(g["entropy_rate_scale"] - o["entropy_rate_scale"]) < 1e-10 * o["entropy_rate_scale"]
+
+
+def test_es_face_flux_dissipates_entropy_like_the_oracle():
+    """With the entropy-variable matrix dissipation the semi-discrete entropy rate is negative
+    and equals the oracle's."""
+    p, shape = 3, (3, 2, 2)
+    ctrl, P = oracle_problem(shape, p, "hu", "ec_es", "unit")
+    S = solver_for(ctrl, shape, P)
+    S.set_metrics(*oracle_metrics_abi(P))
+    u = state_for(P, "unit")
+    g = S.entropy(to_dev(u))
+    o = P.diagnostics(P.to_internal(u))
+    assert g["entropy_rate"] < -1e-8 * g["entropy_rate_scale"]
+    assert abs(g["entropy_rate"] - o["entropy_rate"]) < 1e-10 * o["entropy_rate_scale"]
 
 
 def test_errors_are_reported_not_raised():
