@@ -106,6 +106,28 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
                        nsfr_ctx** out);
 
 /*
+ * nsfr_setup_uncollocated -- the paper's own setting: the solution's
+ * coefficients on the p+1 Lobatto (LGL) nodes, volume and face integrals on
+ * nq >= p+1 Gauss-Legendre points per direction (nq > p+1: the paper's
+ * "overintegration", Sec. "Results").  Arguments as in nsfr_setup, plus
+ *   nq          GL points per direction, p+1 <= nq <= 8.
+ * The state u, du/dt and the RK arrays are [N_e][5][(p+1)^3] values at the
+ * LGL nodes (nsfr_node_coords returns those nodes); the metric terms and the
+ * Jacobians (nsfr_get_metrics, nsfr_quadrature) live at the nq^3 GL points
+ * and nq^2 GL face points.  Each residual evaluation projects the entropy
+ * variables, v~^ = Pi v(chi u^) with chi the LGL basis at the GL points and
+ * Pi = (chi^T W chi)^{-1} chi^T W, evaluates the flux differencing of Eq.
+ * NSFR on the GL points with u~ = u(chi v~^) and the face states
+ * u(l_f v~^), and returns chi^T R_q (nsfr_residual_raw) or the weight-
+ * adjusted du/dt = -Pi~ (W J)^{-1} Pi~^T chi^T R_q, Pi~1 = (M1 + K1)^{-1}
+ * chi^T W (nsfr_residual, nsfr_rk_step).  FP64 only; nsfr_entropy and
+ * nsfr_vjp return NSFR_ERR_STATE for such a context.  With nq = p+1 the
+ * scheme is the GL-collocated one written in the LGL basis.
+ */
+nsfr_status nsfr_setup_uncollocated(const double* grid_nodes, int nx, int ny, int nz, int p_geo, int p, int nq,
+                                    double c, int vol_flux, int face_flux, double gamma, nsfr_ctx** out);
+
+/*
  * nsfr_residual -- du/dt = -Pi~ (W J)^{-1} Pi~^T R(u)  (Eq. NSFR with the
  * weight-adjusted inverse, Eq. weight-adj ESFR mass).
  *   u     host or device, [N_e][5][n^3] FP64, read only.

@@ -72,7 +72,7 @@ void free_all(nsfr_ctx* c) {
   prof_free(c);
 }
 
-size_t state_count(const nsfr_ctx* c) { return (size_t)c->ne * 5 * c->nv; }
+size_t state_count(const nsfr_ctx* c) { return (size_t)c->ne * 5 * c->nsv; }
 
 nsfr_status ensure_host_buffers(nsfr_ctx* ctx) {
   if (!ctx->hbuf_in) CK(dalloc(&ctx->hbuf_in, state_count(ctx)), "cudaMalloc(staging)");
@@ -183,8 +183,10 @@ void nsfr_prof_end(nsfr_ctx* ctx, cudaStream_t s) {
 
 extern "C" {
 
-nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_geo, int p, double c,
-                       int vol_flux, int face_flux, double gamma, int precision, int nodes, nsfr_ctx** out) {
+// nq = 0: collocated on ``nodes``; nq >= p+1: solution on the Lobatto nodes, nq GL points
+static nsfr_status setup_common(const double* grid_nodes, int nx, int ny, int nz, int p_geo, int p, int nq,
+                                double c, int vol_flux, int face_flux, double gamma, int precision, int nodes,
+                                nsfr_ctx** out) {
   if (!out) return NSFR_ERR_ARG;
   *out = nullptr;
   if (!grid_nodes || nx < 1 || ny < 1 || nz < 1 || p < 1 || p > 7 || p_geo < 1 || p_geo > p || !(gamma > 1.0) ||
@@ -199,11 +201,14 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
   ctx->nz = nz;
   ctx->ne = nx * ny * nz;
   ctx->p = p;
-  ctx->n = p + 1;
+  ctx->uncol = nq > 0 ? 1 : 0;
+  ctx->ns = p + 1;
+  ctx->n = nq > 0 ? nq : p + 1;
   ctx->pg = p_geo;
   ctx->q = p_geo + 1;
   ctx->nv = ctx->n * ctx->n * ctx->n;
   ctx->nfp = ctx->n * ctx->n;
+  ctx->nsv = ctx->ns * ctx->ns * ctx->ns;
   ctx->c = c;
   ctx->gamma = gamma;
   ctx->vol_flux = vol_flux;
@@ -211,22 +216,23 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
   ctx->precision = precision;
   ctx->nodes = nodes;
   cudaGetDevice(&ctx->device);
-  nsfr_build_ops(p, p_geo, c, gamma, nodes, &ctx->ops, &ctx->gops);
+  if (ctx->uncol) nsfr_build_ops_uncol(p, p_geo, nq, c, gamma, &ctx->ops, &ctx->gops);
+  else nsfr_build_ops(p, p_geo, c, gamma, nodes, &ctx->ops, &ctx->gops);
 
   auto bail = [&](nsfr_status st) {
     free_all(ctx);
     delete ctx;
     return st;
   };
-  const size_t ne = ctx->ne, nv = ctx->nv, nfp = ctx->nfp, q3 = (size_t)ctx->q * ctx->q * ctx->q;
+  const size_t ne = ctx->ne, nv = ctx->nv, nfp = ctx->nfp, nsv = ctx->nsv, q3 = (size_t)ctx->q * ctx->q * ctx->q;
   bool ok = dalloc(&ctx->ctrl, ne * q3 * 3) == cudaSuccess && dalloc(&ctx->metric, ne * 9 * nv) == cudaSuccess &&
             dalloc(&ctx->J, ne * nv) == cudaSuccess && dalloc(&ctx->invwj, ne * nv) == cudaSuccess &&
             dalloc(&ctx->wj, ne * nv) == cudaSuccess && dalloc(&ctx->nfp_plus, ne * 9 * nfp) == cudaSuccess &&
-            dalloc(&ctx->xyz, ne * 3 * nv) == cudaSuccess &&
+            dalloc(&ctx->xyz, ne * 3 * nsv) == cudaSuccess &&
             dalloc(&ctx->face, ne * 6 * NSFR_NFIELD * nfp) == cudaSuccess && dalloc(&ctx->nrec, ne * NSFR_NFIELD * nv) == cudaSuccess &&
             dalloc(&ctx->fstar, ne * 15 * nfp) == cudaSuccess && dalloc(&ctx->metric_s, ne * 9 * nv) == cudaSuccess &&
             dalloc(&ctx->nf_s, ne * 9 * nfp) == cudaSuccess &&
-            dalloc(&ctx->ustage, ne * 5 * nv) == cudaSuccess && dalloc(&ctx->acc, ne * 5 * nv) == cudaSuccess &&
+            dalloc(&ctx->ustage, ne * 5 * nsv) == cudaSuccess && dalloc(&ctx->acc, ne * 5 * nsv) == cudaSuccess &&
             dalloc(&ctx->flag, 1) == cudaSuccess && dalloc(&ctx->umax, 1) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->flag_host, sizeof(int)) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->umax_host, sizeof(unsigned long long)) == cudaSuccess;
@@ -266,6 +272,25 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
   return NSFR_OK;
 }
 
+nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_geo, int p, double c,
+                       int vol_flux, int face_flux, double gamma, int precision, int nodes, nsfr_ctx** out) {
+  if (nodes != NSFR_NODES_GL && nodes != NSFR_NODES_LGL) {
+    if (out) *out = nullptr;
+    return NSFR_ERR_ARG;
+  }
+  return setup_common(grid_nodes, nx, ny, nz, p_geo, p, 0, c, vol_flux, face_flux, gamma, precision, nodes, out);
+}
+
+nsfr_status nsfr_setup_uncollocated(const double* grid_nodes, int nx, int ny, int nz, int p_geo, int p, int nq,
+                                    double c, int vol_flux, int face_flux, double gamma, nsfr_ctx** out) {
+  if (nq < p + 1 || nq > NSFR_MAXN) {
+    if (out) *out = nullptr;
+    return NSFR_ERR_ARG;
+  }
+  return setup_common(grid_nodes, nx, ny, nz, p_geo, p, nq, c, vol_flux, face_flux, gamma, NSFR_FP64,
+                      NSFR_NODES_LGL, out);
+}
+
 nsfr_status nsfr_residual(nsfr_ctx* ctx, const double* u, double* dudt, void* stream) {
   return residual_any(ctx, u, dudt, EPI_DUDT, stream);
 }
@@ -293,6 +318,7 @@ nsfr_status nsfr_rk_step(nsfr_ctx* ctx, double* u, double cfl, double dt_fixed, 
 
 nsfr_status nsfr_entropy(nsfr_ctx* ctx, const double* u, double* out, void* stream) {
   if (!ctx) return NSFR_ERR_ARG;
+  if (ctx->uncol) return fail(ctx, NSFR_ERR_STATE, "nsfr_entropy needs a collocated context");
   if (!u || !out) return fail(ctx, NSFR_ERR_ARG, "NULL buffer");
   cudaStream_t s = (cudaStream_t)stream;
   ctx->last_stream = s;
@@ -341,7 +367,8 @@ nsfr_status nsfr_entropy(nsfr_ctx* ctx, const double* u, double* out, void* stre
 nsfr_status nsfr_vjp(nsfr_ctx* ctx, const double* u, const double* dudt_bar, double* u_bar, double* x_bar,
                      void* stream) {
   if (!ctx) return NSFR_ERR_ARG;
-  if (ctx->precision != NSFR_FP64) return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp needs an FP64 context");
+  if (ctx->precision != NSFR_FP64 || ctx->uncol)
+    return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp needs a collocated FP64 context");
   if (ctx->face_flux != NSFR_FACE_EC) return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp supports the EC face flux");
   if (!u || !dudt_bar || !u_bar) return fail(ctx, NSFR_ERR_ARG, "NULL buffer");
   if (!is_device_ptr(u) || !is_device_ptr(dudt_bar) || !is_device_ptr(u_bar) || (x_bar && !is_device_ptr(x_bar)))
@@ -372,7 +399,7 @@ nsfr_status nsfr_node_coords(nsfr_ctx* ctx, double* xyz, void* stream) {
   if (!ctx) return NSFR_ERR_ARG;
   if (!xyz) return fail(ctx, NSFR_ERR_ARG, "NULL buffer");
   cudaStream_t s = (cudaStream_t)stream;
-  CK(cudaMemcpyAsync(xyz, ctx->xyz, (size_t)ctx->ne * 3 * ctx->nv * sizeof(double), cudaMemcpyDefault, s),
+  CK(cudaMemcpyAsync(xyz, ctx->xyz, (size_t)ctx->ne * 3 * ctx->nsv * sizeof(double), cudaMemcpyDefault, s),
      "cudaMemcpyAsync(xyz)");
   CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
   return NSFR_OK;
@@ -416,7 +443,7 @@ nsfr_status nsfr_info(const nsfr_ctx* ctx, long long* out) {
   if (!ctx || !out) return NSFR_ERR_ARG;
   out[0] = ctx->ne;
   out[1] = ctx->p;
-  out[2] = ctx->nv;
+  out[2] = ctx->nsv;
   out[3] = ctx->pg;
   out[4] = ctx->precision;
   return NSFR_OK;

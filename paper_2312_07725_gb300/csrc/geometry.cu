@@ -56,7 +56,10 @@ __global__ void metric_kernel(const double* __restrict__ ctrl, OpsGeo g, double*
                               double* __restrict__ wj, double* __restrict__ nf_plus,
                               double* __restrict__ xyz, int* flag) {
   extern __shared__ double sm[];
-  const int n = g.n, q = g.q, nv = n * n * n, q3 = q * q * q, nfp = n * n;
+  // n: Lobatto nodes of the construction (and solution nodes, whose coordinates
+  // are returned); m: volume quadrature points the metric is evaluated at
+  const int n = g.n, q = g.q, m = g.nq, nv = n * n * n, q3 = q * q * q;
+  const int mv = m * m * m, mfp = m * m;
   const int S = 512;  // stride of the shared arrays (>= n^3, q^3)
   double* Xe = sm;             // 3 arrays: control points
   double* X = Xe + 3 * S;      // 3: map at LGL nodes
@@ -95,17 +98,17 @@ __global__ void metric_kernel(const double* __restrict__ ctrl, OpsGeo g, double*
       __syncthreads();
     }
   }
-  // 4. to the GL volume nodes
+  // 4. to the volume quadrature points
   for (int r = 0; r < 9; ++r) {
-    sweep3(g.I, n, n, Cl + r * S, T3, T1, T2);
-    for (int t = threadIdx.x; t < nv; t += blockDim.x) metric[((size_t)e * 9 + r) * nv + t] = T3[t];
+    sweep3(g.I, n, m, Cl + r * S, T3, T1, T2);
+    for (int t = threadIdx.x; t < mv; t += blockDim.x) metric[((size_t)e * 9 + r) * mv + t] = T3[t];
     __syncthreads();
   }
   // face rows: Lobatto layer xi_d = +1 of (J a^d)_c, interpolated tangentially
   for (int d = 0; d < 3; ++d)
     for (int c = 0; c < 3; ++c) {
       const double* src = Cl + (d * 3 + c) * S;
-      for (int t = threadIdx.x; t < nfp; t += blockDim.x) {
+      for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
         const int f0 = t % n, f1 = t / n;  // remaining directions, fast then slow
         int x, y, z;
         if (d == 0) { x = n - 1; y = f0; z = f1; }
@@ -114,32 +117,32 @@ __global__ void metric_kernel(const double* __restrict__ ctrl, OpsGeo g, double*
         T3[t] = src[x + n * (y + n * z)];
       }
       __syncthreads();
-      sweep(g.I, n, n, T3, T4, 0, n, n, 1);
-      sweep(g.I, n, n, T4, T3, 1, n, n, 1);
-      for (int t = threadIdx.x; t < nfp; t += blockDim.x)
-        nf_plus[(((size_t)e * 3 + d) * 3 + c) * nfp + t] = T3[t];
+      sweep(g.I, n, m, T3, T4, 0, n, n, 1);
+      sweep(g.I, n, m, T4, T3, 1, m, n, 1);
+      for (int t = threadIdx.x; t < mfp; t += blockDim.x)
+        nf_plus[(((size_t)e * 3 + d) * 3 + c) * mfp + t] = T3[t];
       __syncthreads();
     }
-  // 5. J = a_1 . (a_2 x a_3) from the map's exact derivative at GL nodes
+  // 5. J = a_1 . (a_2 x a_3) from the map's exact derivative at the quadrature points
   for (int r = 0; r < 9; ++r) {
-    sweep3(g.I, n, n, dX + r * S, T3, T1, T2);
-    for (int t = threadIdx.x; t < nv; t += blockDim.x) Cl[r * S + t] = T3[t];  // reuse Cl: a at GL
+    sweep3(g.I, n, m, dX + r * S, T3, T1, T2);
+    for (int t = threadIdx.x; t < mv; t += blockDim.x) Cl[r * S + t] = T3[t];  // reuse Cl: a there
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+  for (int t = threadIdx.x; t < mv; t += blockDim.x) {
     const double* a = Cl;
     double a00 = a[0 * S + t], a01 = a[1 * S + t], a02 = a[2 * S + t];
     double a10 = a[3 * S + t], a11 = a[4 * S + t], a12 = a[5 * S + t];
     double a20 = a[6 * S + t], a21 = a[7 * S + t], a22 = a[8 * S + t];
     double Jv = a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) + a02 * (a10 * a21 - a11 * a20);
-    const int i = t % n, j = (t / n) % n, k = t / (n * n);
+    const int i = t % m, j = (t / m) % m, k = t / (m * m);
     const double w3 = g.w[i] * g.w[j] * g.w[k];
-    Jout[(size_t)e * nv + t] = Jv;
-    wj[(size_t)e * nv + t] = w3 * Jv;
-    invwj[(size_t)e * nv + t] = 1.0 / (w3 * Jv);
+    Jout[(size_t)e * mv + t] = Jv;
+    wj[(size_t)e * mv + t] = w3 * Jv;
+    invwj[(size_t)e * mv + t] = 1.0 / (w3 * Jv);
     if (!(Jv > 0.0)) atomicOr(flag, 2);
   }
-  // physical coordinates of the GL nodes
+  // physical coordinates of the solution nodes
   for (int c = 0; c < 3; ++c) {
     sweep3(g.Eg, q, n, Xe + c * S, T3, T1, T2);
     for (int t = threadIdx.x; t < nv; t += blockDim.x) xyz[((size_t)e * 3 + c) * nv + t] = T3[t];
@@ -149,7 +152,7 @@ __global__ void metric_kernel(const double* __restrict__ ctrl, OpsGeo g, double*
 
 __global__ void jacobian_derived_kernel(const double* __restrict__ J, OpsGeo g, size_t total,
                                         double* __restrict__ invwj, double* __restrict__ wj, int* flag) {
-  const int n = g.n, nv = n * n * n;
+  const int n = g.nq, nv = n * n * n;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     const int node = (int)(t % nv);
     const int i = node % n, j = (node / n) % n, k = node / (n * n);

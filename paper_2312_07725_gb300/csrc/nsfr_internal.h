@@ -42,26 +42,47 @@ struct OpsGL {
   double f4g[4];
   double fr2[4];  // 2 atanh(f)/f (for 1/rho_ln)
   double inv_gm1;
+  // Uncollocated scheme (solution on ns Lobatto nodes, the n points above are
+  // GL quadrature points, n >= ns): chi (n x ns) the solution basis at the
+  // points, Pi = (chi^T W chi)^{-1} chi^T W (ns x n), ls_m / ls_p the solution
+  // basis at -1 / +1, A = (chi Pi~1)^T (n x n) and Pt = Pi~1 = (M1 + K1)^{-1}
+  // chi^T W (ns x n) for the weight-adjusted inverse.  uncol = 0: collocated
+  // (ns = n, and none of these is used).
+  int uncol;
+  int ns;
+  double chi[NSFR_MAXN * NSFR_MAXN];
+  double Pi[NSFR_MAXN * NSFR_MAXN];
+  double ls_m[NSFR_MAXN];
+  double ls_p[NSFR_MAXN];
+  double A[NSFR_MAXN * NSFR_MAXN];
+  double Pt[NSFR_MAXN * NSFR_MAXN];
 };
 
 // Operators of the metric construction (Lobatto nodes of degree p).
 struct OpsGeo {
-  int n;   // GL/LGL nodes per direction
+  int n;   // Lobatto nodes per direction of the metric construction (p + 1)
   int q;   // control points per direction (p_geo + 1)
+  int nq;  // volume quadrature points per direction (n unless uncollocated)
   double E[NSFR_MAXN * NSFR_MAXN];   // equispaced(q) -> LGL(n), n x q
-  double Eg[NSFR_MAXN * NSFR_MAXN];  // equispaced(q) -> GL(n),  n x q
+  double Eg[NSFR_MAXN * NSFR_MAXN];  // equispaced(q) -> solution nodes (n), n x q
   double Dl[NSFR_MAXN * NSFR_MAXN];  // LGL differentiation, n x n
-  double I[NSFR_MAXN * NSFR_MAXN];   // LGL -> GL interpolation, n x n
-  double w[NSFR_MAXN];               // GL weights
+  double I[NSFR_MAXN * NSFR_MAXN];   // LGL -> volume quadrature points, nq x n
+  double w[NSFR_MAXN];               // volume quadrature weights (nq)
 };
 
 // Host construction of the operators (ops1d.cpp).
 void nsfr_build_ops(int p, int p_geo, double c, double gamma, int nodes, OpsGL* gl, OpsGeo* geo);
+// uncollocated: solution on the p+1 Lobatto nodes, nq >= p+1 GL quadrature points
+void nsfr_build_ops_uncol(int p, int p_geo, int nq, double c, double gamma, OpsGL* gl, OpsGeo* geo);
 void nsfr_gauss_legendre(int n, double* x, double* w);
 void nsfr_gauss_lobatto(int n, double* x, double* w);
 
 struct nsfr_ctx {
+  // n, nv, nfp: volume quadrature points per direction / per element / per
+  // face; ns, nsv: solution nodes per direction / per element (equal to n, nv
+  // for the collocated schemes).  The state and the RK arrays have nsv nodes.
   int nx, ny, nz, ne, p, n, pg, q, nv, nfp;
+  int ns = 0, nsv = 0, uncol = 0;
   double c, gamma;
   int vol_flux, face_flux, precision, nodes;
   OpsGL ops;
@@ -134,6 +155,8 @@ struct RkArgs {
   int last;           // unext = acc + b dt k (final update)
 };
 cudaError_t nsfr_launch_face_states(nsfr_ctx* ctx, const double* u, cudaStream_t s);
+// uncollocated: the entropy projection through chi and Pi (projection.cu)
+cudaError_t nsfr_launch_projection(nsfr_ctx* ctx, const double* u, cudaStream_t s);
 // w_perp-scaled metric and face rows (after the metric terms change)
 cudaError_t nsfr_launch_scaled_rows(nsfr_ctx* ctx, cudaStream_t s);
 // numerical flux of every face once, from the face states (after nsfr_launch_face_states)

@@ -11,6 +11,7 @@
 // chi = I) written in Sherman-Morrison form, and its inverse I + W^{-1} K1.
 #include <cmath>
 #include <cstring>
+#include <utility>
 
 #include "nsfr_internal.h"
 
@@ -198,9 +199,134 @@ void nsfr_build_ops(int p, int p_geo, double c, double gamma, int nodes, OpsGL* 
 
   geo->n = n;
   geo->q = q;
+  geo->nq = n;
   interp_matrix(q, xe, n, xl, geo->E);
   interp_matrix(q, xe, n, xg, geo->Eg);
   diff_matrix(n, xl, geo->Dl);
   interp_matrix(n, xl, n, xg, geo->I);
   for (int j = 0; j < n; ++j) geo->w[j] = wg[j];
+  gl->uncol = 0;
+  gl->ns = n;
+}
+
+// X = A^{-1} B for an m x m matrix A and m x k B (Gaussian elimination with
+// partial pivoting; m <= NSFR_MAXN); A and B are overwritten
+static void solve_small(int m, int k, double* A, double* B) {
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < m; ++r)
+      if (std::fabs(A[r * m + c]) > std::fabs(A[piv * m + c])) piv = r;
+    if (piv != c) {
+      for (int j = 0; j < m; ++j) std::swap(A[c * m + j], A[piv * m + j]);
+      for (int j = 0; j < k; ++j) std::swap(B[c * k + j], B[piv * k + j]);
+    }
+    for (int r = c + 1; r < m; ++r) {
+      const double f = A[r * m + c] / A[c * m + c];
+      for (int j = c; j < m; ++j) A[r * m + j] -= f * A[c * m + j];
+      for (int j = 0; j < k; ++j) B[r * k + j] -= f * B[c * k + j];
+    }
+  }
+  for (int c = m - 1; c >= 0; --c)
+    for (int j = 0; j < k; ++j) {
+      double v = B[c * k + j];
+      for (int i = c + 1; i < m; ++i) v -= A[c * m + i] * B[i * k + j];
+      B[c * k + j] = v / A[c * m + c];
+    }
+}
+
+// Uncollocated operators (the scheme of the paper's runs: solution on the p+1
+// Lobatto nodes, volume and face quadrature on nq >= p+1 Gauss-Legendre
+// points).  The line kernels see the GL points: their derivative D_q = chi D
+// Pi, S_q = W D_q - D_q^T W and extrapolations E_-+ = l(-+1)^T Pi satisfy
+// W D_q + D_q^T W = E+^T E+ - E-^T E- (the quadrature integrates degree 2p).
+void nsfr_build_ops_uncol(int p, int p_geo, int nq, double c, double gamma, OpsGL* gl, OpsGeo* geo) {
+  const int ns = p + 1, q = p_geo + 1;
+  // the collocated GL operators of nq points give the series constants and layout
+  nsfr_build_ops(nq - 1, p_geo < nq - 1 ? p_geo : nq - 1, 0.0, gamma, NSFR_NODES_GL, gl, geo);
+  double xl[NSFR_MAXN], wl[NSFR_MAXN], xq[NSFR_MAXN], wq[NSFR_MAXN], xe[NSFR_MAXN];
+  nsfr_gauss_lobatto(ns, xl, wl);
+  nsfr_gauss_legendre(nq, xq, wq);
+  for (int k = 0; k < q; ++k) xe[k] = (q == 1) ? 0.0 : -1.0 + 2.0 * k / (q - 1);
+  double chi[NSFR_MAXN * NSFR_MAXN], D[NSFR_MAXN * NSFR_MAXN];
+  interp_matrix(ns, xl, nq, xq, chi);  // nq x ns
+  diff_matrix(ns, xl, D);
+  double ends[2] = {-1.0, 1.0}, L[2 * NSFR_MAXN];
+  interp_matrix(ns, xl, 2, ends, L);
+  // M1 = chi^T W chi, Pi = M1^{-1} chi^T W
+  double M1[NSFR_MAXN * NSFR_MAXN], Pi[NSFR_MAXN * NSFR_MAXN], tmp[NSFR_MAXN * NSFR_MAXN];
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b < ns; ++b) {
+      double v = 0.0;
+      for (int r = 0; r < nq; ++r) v += chi[r * ns + a] * wq[r] * chi[r * ns + b];
+      M1[a * ns + b] = v;
+    }
+  for (int a = 0; a < ns; ++a)
+    for (int r = 0; r < nq; ++r) Pi[a * nq + r] = chi[r * ns + a] * wq[r];
+  std::memcpy(tmp, M1, sizeof(tmp));
+  solve_small(ns, nq, tmp, Pi);
+  // D_q = chi D Pi (nq x nq)
+  double DPi[NSFR_MAXN * NSFR_MAXN], Dq[NSFR_MAXN * NSFR_MAXN];
+  for (int a = 0; a < ns; ++a)
+    for (int r = 0; r < nq; ++r) {
+      double v = 0.0;
+      for (int b = 0; b < ns; ++b) v += D[a * ns + b] * Pi[b * nq + r];
+      DPi[a * nq + r] = v;
+    }
+  for (int r = 0; r < nq; ++r)
+    for (int t = 0; t < nq; ++t) {
+      double v = 0.0;
+      for (int a = 0; a < ns; ++a) v += chi[r * ns + a] * DPi[a * nq + t];
+      Dq[r * nq + t] = v;
+    }
+  gl->uncol = 1;
+  gl->ns = ns;
+  gl->has_K = (c != 0.0);
+  for (int r = 0; r < nq; ++r)
+    for (int t = 0; t < nq; ++t) gl->S1[r * nq + t] = wq[r] * Dq[r * nq + t] - Dq[t * nq + r] * wq[t];
+  for (int r = 0; r < nq; ++r) {
+    double em = 0.0, ep = 0.0;
+    for (int a = 0; a < ns; ++a) {
+      em += L[a] * Pi[a * nq + r];
+      ep += L[ns + a] * Pi[a * nq + r];
+    }
+    gl->tm[r] = em;
+    gl->tp[r] = ep;
+    gl->w[r] = wq[r];
+  }
+  std::memcpy(gl->chi, chi, sizeof(gl->chi));
+  std::memcpy(gl->Pi, Pi, sizeof(gl->Pi));
+  for (int a = 0; a < ns; ++a) {
+    gl->ls_m[a] = L[a];
+    gl->ls_p[a] = L[ns + a];
+  }
+  // Pi~1 = (M1 + K1)^{-1} chi^T W, K1 = c (D^p)^T M1 D^p = 2c g g^T (rows of D^p are g^T)
+  double lam[NSFR_MAXN], g[NSFR_MAXN];
+  bary_weights(ns, xl, lam);
+  double fact = 1.0;
+  for (int k = 2; k <= p; ++k) fact *= k;
+  for (int j = 0; j < ns; ++j) g[j] = fact * lam[j];
+  double MK[NSFR_MAXN * NSFR_MAXN], Pt[NSFR_MAXN * NSFR_MAXN];
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b < ns; ++b) MK[a * ns + b] = M1[a * ns + b] + 2.0 * c * g[a] * g[b];
+  for (int a = 0; a < ns; ++a)
+    for (int r = 0; r < nq; ++r) Pt[a * nq + r] = chi[r * ns + a] * wq[r];
+  solve_small(ns, nq, MK, Pt);
+  std::memcpy(gl->Pt, Pt, sizeof(gl->Pt));
+  // A = (chi Pi~1)^T, nq x nq
+  for (int r = 0; r < nq; ++r)
+    for (int t = 0; t < nq; ++t) {
+      double v = 0.0;
+      for (int a = 0; a < ns; ++a) v += chi[t * ns + a] * Pt[a * nq + r];
+      gl->A[r * nq + t] = v;
+    }
+  // metric construction: degree-p Lobatto layer, evaluated at the GL points;
+  // node coordinates at the Lobatto solution nodes
+  geo->n = ns;
+  geo->q = q;
+  geo->nq = nq;
+  interp_matrix(q, xe, ns, xl, geo->E);
+  interp_matrix(q, xe, ns, xl, geo->Eg);
+  diff_matrix(ns, xl, geo->Dl);
+  interp_matrix(ns, xl, nq, xq, geo->I);
+  for (int r = 0; r < nq; ++r) geo->w[r] = wq[r];
 }

@@ -141,11 +141,11 @@ int nsfr_diag_blocks(nsfr_ctx* ctx) { return ctx->ne < 1024 ? ctx->ne : 1024; }
 cudaError_t nsfr_launch_max_wavespeed(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
   cudaError_t err = cudaMemsetAsync(ctx->umax, 0, sizeof(unsigned long long), s);
   if (err != cudaSuccess) return err;
-  const size_t nodes = (size_t)ctx->ne * ctx->nv;
+  const size_t nodes = (size_t)ctx->ne * ctx->nsv;
   int grid = (int)((nodes + 255) / 256);
   if (grid > 152 * 8) grid = 152 * 8;
   nsfr_prof_begin(ctx, 3, s);
-  max_wavespeed_kernel<<<grid, 256, 0, s>>>(u, (size_t)ctx->ne, ctx->nv, ctx->gamma, ctx->umax, ctx->flag);
+  max_wavespeed_kernel<<<grid, 256, 0, s>>>(u, (size_t)ctx->ne, ctx->nsv, ctx->gamma, ctx->umax, ctx->flag);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
   return cudaGetLastError();

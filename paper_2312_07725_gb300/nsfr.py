@@ -25,7 +25,7 @@ PRECISION = {"fp64": 0, "fp32_bulk": 1}
 NODES = {"gl": 0, "lgl": 1}
 
 # every symbol include/nsfr.h declares
-EXPORTS = ["nsfr_setup", "nsfr_residual", "nsfr_residual_raw", "nsfr_rk_step", "nsfr_entropy",
+EXPORTS = ["nsfr_setup", "nsfr_setup_uncollocated", "nsfr_residual", "nsfr_residual_raw", "nsfr_rk_step", "nsfr_entropy",
            "nsfr_vjp", "nsfr_node_coords", "nsfr_get_metrics", "nsfr_set_metrics", "nsfr_quadrature", "nsfr_info", "nsfr_check",
            "nsfr_profile", "nsfr_profile_read", "nsfr_residual_static", "nsfr_math_eval", "nsfr_kernel_launches",
            "nsfr_last_error", "nsfr_destroy"]
@@ -45,6 +45,8 @@ def load_library(path=LIB_PATH):
     lib = ctypes.CDLL(path)
     vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     lib.nsfr_setup.argtypes = [vp, i, i, i, i, i, d, i, i, d, i, i, ctypes.POINTER(vp)]
+    lib.nsfr_setup_uncollocated.argtypes = [vp, i, i, i, i, i, i, d, i, i, d, ctypes.POINTER(vp)]
+    lib.nsfr_setup_uncollocated.restype = i
     lib.nsfr_setup.restype = i
     for name in ("nsfr_residual", "nsfr_residual_raw"):
         getattr(lib, name).argtypes = [vp, vp, vp, vp]
@@ -151,7 +153,9 @@ class Solver:
     """One NSFR-EC discretisation (mesh, p, c, fluxes, precision) on the current device."""
 
     def __init__(self, grid_nodes, shape, p, p_geo=None, c=0.0, face_flux="ec", gamma=1.4,
-                 precision="fp64", nodes="gl"):
+                 precision="fp64", nodes="gl", nq=None):
+        """``nodes``: "gl" or "lgl" collocated; with ``nq`` (>= p+1) the uncollocated scheme:
+        solution on the LGL nodes, nq GL quadrature points per direction."""
         self._lib = lib()
         nx, ny, nz = shape
         pg = p if p_geo is None else p_geo
@@ -161,8 +165,17 @@ class Solver:
         self.c, self.gamma, self.face_flux, self.precision, self.nodes = c, gamma, face_flux, precision, nodes
         self._keep = grid_nodes
         h = ctypes.c_void_p()
-        st = self._lib.nsfr_setup(_ptr(grid_nodes), nx, ny, nz, pg, p, float(c), 0, FACE_FLUX[face_flux],
-                                  float(gamma), PRECISION[precision], NODES[nodes], ctypes.byref(h))
+        self.nq = nq
+        npt = self.n if nq is None else int(nq)
+        self.nqv, self.nqf = npt ** 3, npt ** 2  # quadrature points per element / per face
+        if nq is None:
+            st = self._lib.nsfr_setup(_ptr(grid_nodes), nx, ny, nz, pg, p, float(c), 0, FACE_FLUX[face_flux],
+                                      float(gamma), PRECISION[precision], NODES[nodes], ctypes.byref(h))
+        else:
+            if precision != "fp64":
+                raise ValueError("the uncollocated scheme is FP64 only")
+            st = self._lib.nsfr_setup_uncollocated(_ptr(grid_nodes), nx, ny, nz, pg, p, int(nq), float(c), 0,
+                                                   FACE_FLUX[face_flux], float(gamma), ctypes.byref(h))
         if st != NSFR_OK:
             raise NSFRError(st, "nsfr_setup failed")
         self._h = h
@@ -220,9 +233,11 @@ class Solver:
         return out
 
     def metrics(self, stream=None):
-        C = np.zeros((self.n_el, 9, self.nv))
-        J = np.zeros((self.n_el, self.nv))
-        Cf = np.zeros((self.n_el, 3, 3, self.n ** 2))
+        """Metric rows [N_e][9][points], Jacobians [N_e][points] and shared face rows
+        [N_e][3][3][face points] at the volume / face quadrature points."""
+        C = np.zeros((self.n_el, 9, self.nqv))
+        J = np.zeros((self.n_el, self.nqv))
+        Cf = np.zeros((self.n_el, 3, 3, self.nqf))
         self._check(self._lib.nsfr_get_metrics(self._h, _ptr(C), _ptr(J), _ptr(Cf), _stream(stream)),
                     "nsfr_get_metrics")
         return C, J, Cf
@@ -235,9 +250,9 @@ class Solver:
                     "nsfr_set_metrics")
 
     def quadrature(self, out=None, stream=None):
-        """W J at the GL nodes, [N_e][n^3]."""
+        """W J at the volume quadrature points, [N_e][points]."""
         if out is None:
-            out = np.zeros((self.n_el, self.nv))
+            out = np.zeros((self.n_el, self.nqv))
         self._check(self._lib.nsfr_quadrature(self._h, _ptr(out), _stream(stream)), "nsfr_quadrature")
         return out
 

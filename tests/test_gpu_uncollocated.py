@@ -1,0 +1,103 @@
+"""GPU parity of the uncollocated scheme (nsfr_setup_uncollocated: solution on the
+p+1 Lobatto nodes, nq >= p+1 Gauss-Legendre quadrature points, nq > p+1 the paper's
+overintegration) against the oracle's UncollocatedProblem.
+
+Bars as for the collocated path: the library's metric terms at the GL points and its
+node coordinates at 1e-12, R^ = chi^T R_q, du^/dt and one RK4 step at 1e-12 with the
+oracle's metric terms injected (the residual is ill-conditioned, see test_gpu_parity).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads as wl  # noqa: E402
+from oracle.operators1d import c_hu  # noqa: E402
+from oracle.uncollocated import UncollocatedProblem  # noqa: E402
+from tests._pairs import rel_l2  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def _metrics_abi(P):
+    ne, m = P.mesh.n_el, P.nq
+    C = np.ascontiguousarray(np.moveaxis(P.C.reshape(3, 3, ne, m ** 3), 2, 0).reshape(ne, 9, m ** 3))
+    J = np.ascontiguousarray(P.J.reshape(ne, m ** 3))
+    Cf = np.ascontiguousarray(np.moveaxis(P.geo["Cf"].reshape(3, 3, ne, m * m), 2, 0))
+    return C, J, Cf
+
+
+def _case(shape, p, nq, c_kind="dg", face_flux="ec", kind="tgv"):
+    from paper_2312_07725_gb300 import Solver
+    c = 0.0 if c_kind == "dg" else c_hu(p)
+    if kind == "tgv":
+        ctrl = wl.control_points(*shape, p, -math.pi, math.pi, wl.warp_tgv)
+    else:
+        ctrl = wl.control_points(*shape, p, 0.0, 1.0, wl.warp_unit)
+    P = UncollocatedProblem(ctrl, shape, p, nq=nq, c=c, face_flux=face_flux)
+    S = Solver(np.ascontiguousarray(ctrl), shape, p, c=c, face_flux=face_flux, nq=nq)
+    xs = P.node_coords(ctrl)
+    u = wl.perturbed_tgv_state(xs) if kind == "tgv" else wl.perturbed_density_wave_state(xs)
+    return ctrl, P, S, np.ascontiguousarray(u)
+
+
+@pytest.mark.parametrize("p,nq", [(2, 3), (2, 5), (4, 6), (7, 8)])
+def test_uncollocated_metrics_and_nodes_match_oracle(p, nq):
+    ctrl, P, S, _ = _case((3, 2, 2), p, nq)
+    C, J, Cf = S.metrics()
+    Co, Jo, Cfo = _metrics_abi(P)
+    assert rel_l2(C, Co) < TOL and rel_l2(J, Jo) < TOL and rel_l2(Cf, Cfo) < TOL
+    assert np.abs(S.node_coords() - P.node_coords(ctrl)).max() < 1e-13 * np.pi
+
+
+CASES = [
+    (1, 2, (2, 3, 2), "dg", "ec", "tgv"),
+    (2, 3, (3, 2, 2), "hu", "ec", "tgv"),       # nq = p+1: the collocated scheme in the LGL basis
+    (2, 5, (3, 2, 1), "dg", "ec", "tgv"),       # overintegration by 2
+    (3, 5, (2, 2, 2), "hu", "ec_roe", "unit"),
+    (3, 7, (2, 1, 2), "dg", "ec_es", "unit"),
+    (4, 6, (3, 3, 1), "hu", "ec", "tgv"),       # 9 elements: ragged last CTA
+    (5, 7, (2, 1, 1), "dg", "ec", "tgv"),
+]
+
+
+@pytest.mark.parametrize("p,nq,shape,c_kind,face_flux,kind", CASES)
+def test_uncollocated_residual_and_dudt_match_oracle(p, nq, shape, c_kind, face_flux, kind):
+    _, P, S, u = _case(shape, p, nq, c_kind, face_flux, kind)
+    S.set_metrics(*_metrics_abi(P))
+    ud = torch.from_numpy(u).cuda()
+    R = torch.empty_like(ud)
+    D = torch.empty_like(ud)
+    S.residual_raw(ud, R)
+    S.residual(ud, D)
+    torch.cuda.synchronize()
+    U = P.to_internal(u)
+    assert rel_l2(R.cpu().numpy(), P.to_abi(P.residual(U))) < TOL
+    assert rel_l2(D.cpu().numpy(), P.to_abi(P.dudt(U))) < TOL
+
+
+def test_uncollocated_rk4_step_matches_oracle():
+    _, P, S, u = _case((3, 2, 2), 3, 5, "hu", "ec")
+    S.set_metrics(*_metrics_abi(P))
+    dt = 2e-3
+    u1 = P.rk4_step_abi(u, dt)
+    ud = torch.from_numpy(u).cuda()
+    S.rk_step(ud, dt=dt)
+    torch.cuda.synchronize()
+    du = u1 - u
+    bar = TOL + 4 * np.finfo(np.float64).eps * np.linalg.norm(u1) / np.linalg.norm(du)
+    assert rel_l2(ud.cpu().numpy() - u, du) < bar
+
+
+def test_uncollocated_context_rejects_what_it_does_not_support():
+    from paper_2312_07725_gb300 import NSFRError, Solver
+    ctrl, P, S, u = _case((2, 2, 2), 2, 4)
+    with pytest.raises(NSFRError):
+        S.entropy(torch.from_numpy(u).cuda())
+    with pytest.raises(ValueError):
+        Solver(np.ascontiguousarray(ctrl), (2, 2, 2), 2, nq=4, precision="fp32_bulk")
+    with pytest.raises(NSFRError):
+        Solver(np.ascontiguousarray(ctrl), (2, 2, 2), 2, nq=2)  # nq < p+1
