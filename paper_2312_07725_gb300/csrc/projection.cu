@@ -8,8 +8,9 @@
 //   u~_f = u(l_s v~^)       at the GL points of each face (l_s: the solution
 //                           basis at xi_d = -1 / +1, chi along the face).
 //
-// One CTA per element; every step is a 1D contraction along one direction
-// (sum factorisation) on shared memory.  The kernel writes the node records
+// A CTA takes a batch of elements; every step is a 1D contraction along one
+// direction (sum factorisation) over all of the batch's elements and
+// variables at once, on shared memory.  The kernel writes the node records
 // of u~ at the GL points (rho, 2 beta, u/2, |u|^2/4, ln rho, ln beta) and the
 // face records, the two inputs of the face-flux and volume kernels, exactly
 // as the collocated face-state kernel does for its nodes.
@@ -20,35 +21,28 @@
 namespace {
 using namespace nsfr_k;
 
-// out = A along direction d of in; A is (m x k) row-major, in has extents
-// (ex, ey, ez) with extent k along d, out has extent m along d
-__device__ void psweep(const double* __restrict__ A, int k, int m, const double* in, double* out, int d, int ex,
-                       int ey, int ez) {
+// Y = A along direction d of X for nslab slabs of stride st (extents (ex, ey,
+// ez) in, extent m along d out); A is m x k row-major.  Ends with a barrier.
+__device__ void psweep(const double* __restrict__ A, int k, int m, const double* X, double* Y, int nslab, int st,
+                       int d, int ex, int ey, int ez) {
   int ox = ex, oy = ey, oz = ez;
   if (d == 0) ox = m;
   if (d == 1) oy = m;
   if (d == 2) oz = m;
-  const int total = ox * oy * oz;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int x = t % ox, y = (t / ox) % oy, z = t / (ox * oy);
-    double s = 0.0;
-    for (int b = 0; b < k; ++b) {
-      int xi = x, yi = y, zi = z, r;
-      if (d == 0) { r = x; xi = b; }
-      else if (d == 1) { r = y; yi = b; }
-      else { r = z; zi = b; }
-      s = fma(A[r * k + b], in[xi + ex * (yi + ey * zi)], s);
-    }
-    out[t] = s;
+  const int per = ox * oy * oz;
+  const int sx = 1, sy = ex, sz = ex * ey;
+  const int sd = d == 0 ? sx : (d == 1 ? sy : sz);
+  for (int t = threadIdx.x; t < nslab * per; t += blockDim.x) {
+    const int sl = t / per, q = t % per;
+    const int x = q % ox, y = (q / ox) % oy, z = q / (ox * oy);
+    const int r = d == 0 ? x : (d == 1 ? y : z);
+    const double* in = X + (size_t)sl * st + (d == 0 ? 0 : x) * sx + (d == 1 ? 0 : y) * sy + (d == 2 ? 0 : z) * sz;
+    const double* a = A + r * k;
+    double acc = 0.0;
+    for (int b = 0; b < k; ++b) acc = fma(a[b], in[b * sd], acc);
+    Y[(size_t)sl * st + q] = acc;
   }
   __syncthreads();
-}
-
-// three sweeps of the same (m x k) matrix: (k,k,k) -> (m,m,m)
-__device__ void psweep3(const double* A, int k, int m, const double* in, double* out, double* t1, double* t2) {
-  psweep(A, k, m, in, t1, 0, k, k, k);
-  psweep(A, k, m, t1, t2, 1, m, k, k);
-  psweep(A, k, m, t2, out, 2, m, m, k);
 }
 
 // the record of u(w), w entropy variables (the face-state conversion); flags
@@ -75,27 +69,34 @@ __device__ __forceinline__ Rec rec_from_entropy(const double w[5], const OpsGL& 
   return P;
 }
 
-// shared memory: Us [5][S] solution-node values, Vq [5][S] point values, two temps
-constexpr int PS = NSFR_MAXN * NSFR_MAXN * NSFR_MAXN;
+// elements per CTA: four arrays of 5 N^3 doubles per element in shared memory
+__host__ __device__ constexpr int proj_epb(int n) { return n <= 4 ? 8 : n == 5 ? 4 : n == 6 ? 2 : 1; }
 
-__global__ void projection_kernel(const double* __restrict__ u, OpsGL ops, double* __restrict__ face,
-                                  double* __restrict__ nrec, int* flag) {
+template <int N>
+__global__ void __launch_bounds__(256) projection_kernel(const double* __restrict__ u, OpsGL ops,
+                                                         double* __restrict__ face, double* __restrict__ nrec,
+                                                         int ne, int* flag) {
+  constexpr int NV = N * N * N, NFP = N * N, SL = 5 * NV, EPB = proj_epb(N);
   extern __shared__ double sm[];
-  const int N = ops.n, ns = ops.ns, NV = N * N * N, NFP = N * N, nsv = ns * ns * ns;
-  double* Us = sm;             // [5][PS]
-  double* Vq = Us + 5 * PS;    // [5][PS]
-  double* T1 = Vq + 5 * PS;
-  double* T2 = T1 + PS;
-  const MathTables T = nsfr_stage_tables(T2 + PS);
-  const int e = blockIdx.x;
+  const int ns = ops.ns, nsv = ns * ns * ns;
+  const int e0 = blockIdx.x * EPB, nel = min(EPB, ne - e0), nsl = 5 * nel;
+  double* Us = sm;                  // [EPB*5][NV] solution-node values (first nsv of each slab)
+  double* Vq = Us + EPB * SL;       // [EPB*5][NV] point values
+  double* T1 = Vq + EPB * SL;
+  double* T2 = T1 + EPB * SL;
+  const MathTables T = nsfr_stage_tables(T2 + EPB * SL);
   const double g = ops.gamma, gm1 = g - 1.0;
-  for (int t = threadIdx.x; t < 5 * nsv; t += blockDim.x) Us[(t / nsv) * PS + t % nsv] = u[(size_t)e * 5 * nsv + t];
+  for (int t = threadIdx.x; t < nsl * nsv; t += blockDim.x)
+    Us[(size_t)(t / nsv) * NV + t % nsv] = u[(size_t)e0 * 5 * nsv + t];
   __syncthreads();
-  // u_q = chi u^
-  for (int k = 0; k < 5; ++k) psweep3(ops.chi, ns, N, Us + k * PS, Vq + k * PS, T1, T2);
+  // u_q = chi u^ (all elements and variables at once)
+  psweep(ops.chi, ns, N, Us, T1, nsl, NV, 0, ns, ns, ns);
+  psweep(ops.chi, ns, N, T1, T2, nsl, NV, 1, N, ns, ns);
+  psweep(ops.chi, ns, N, T2, Vq, nsl, NV, 2, N, N, ns);
   // v(u_q) in place
-  for (int t = threadIdx.x; t < NV; t += blockDim.x) {
-    const double r = Vq[t], m0 = Vq[PS + t], m1 = Vq[2 * PS + t], m2 = Vq[3 * PS + t], E = Vq[4 * PS + t];
+  for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
+    double* v = Vq + (size_t)(t / NV) * SL + t % NV;
+    const double r = v[0], m0 = v[NV], m1 = v[2 * NV], m2 = v[3 * NV], E = v[4 * NV];
     const double ir = rcp_full(r);
     const double u0 = m0 * ir, u1 = m1 * ir, u2 = m2 * ir;
     const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
@@ -103,65 +104,79 @@ __global__ void projection_kernel(const double* __restrict__ u, OpsGL ops, doubl
     if (!(r > 0.0) || !(p > 0.0)) atomicOr(flag, 1);
     const double b = 0.5 * r * rcp_full(p);
     const double s = nsfr_log(p, T) - g * nsfr_log(r, T);
-    Vq[t] = (g - s) * ops.inv_gm1 - b * q2;
-    Vq[PS + t] = 2.0 * b * u0;
-    Vq[2 * PS + t] = 2.0 * b * u1;
-    Vq[3 * PS + t] = 2.0 * b * u2;
-    Vq[4 * PS + t] = -2.0 * b;
+    v[0] = (g - s) * ops.inv_gm1 - b * q2;
+    v[NV] = 2.0 * b * u0;
+    v[2 * NV] = 2.0 * b * u1;
+    v[3 * NV] = 2.0 * b * u2;
+    v[4 * NV] = -2.0 * b;
   }
   __syncthreads();
   // v~^ = Pi v(u_q), into Us
-  for (int k = 0; k < 5; ++k) psweep3(ops.Pi, N, ns, Vq + k * PS, Us + k * PS, T1, T2);
+  psweep(ops.Pi, N, ns, Vq, T1, nsl, NV, 0, N, N, N);
+  psweep(ops.Pi, N, ns, T1, T2, nsl, NV, 1, ns, N, N);
+  psweep(ops.Pi, N, ns, T2, Us, nsl, NV, 2, ns, ns, N);
   // chi v~^ at the GL points -> node records of u~
-  for (int k = 0; k < 5; ++k) psweep3(ops.chi, ns, N, Us + k * PS, Vq + k * PS, T1, T2);
-  for (int t = threadIdx.x; t < NV; t += blockDim.x) {
-    double w[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) w[k] = Vq[k * PS + t];
-    store_rec(nrec + (size_t)e * NSFR_NFIELD * NV + t, NV, rec_from_entropy(w, ops, T, flag));
+  psweep(ops.chi, ns, N, Us, T1, nsl, NV, 0, ns, ns, ns);
+  psweep(ops.chi, ns, N, T1, T2, nsl, NV, 1, N, ns, ns);
+  psweep(ops.chi, ns, N, T2, Vq, nsl, NV, 2, N, N, ns);
+  for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
+    const int le = t / NV, node = t % NV;
+    const double* v = Vq + (size_t)le * SL + node;
+    const double w[5] = {v[0], v[NV], v[2 * NV], v[3 * NV], v[4 * NV]};
+    store_rec(nrec + (size_t)(e0 + le) * NSFR_NFIELD * NV + node, NV, rec_from_entropy(w, ops, T, flag));
   }
   __syncthreads();
-  // faces: l_s along d, chi along the two face directions
+  // faces: l_s along d (to extent 1), then chi along the two face directions
   for (int d = 0; d < 3; ++d)
     for (int s = 0; s < 2; ++s) {
       const double* ls = s ? ops.ls_p : ops.ls_m;
-      for (int k = 0; k < 5; ++k) {
-        // contract along d: (ns,ns,ns) -> the face layer (f0, f1) over the two other directions
-        for (int t = threadIdx.x; t < ns * ns; t += blockDim.x) {
-          const int f0 = t % ns, f1 = t / ns;
-          double acc = 0.0;
-          for (int a = 0; a < ns; ++a) {
-            int x, y, z;
-            if (d == 0) { x = a; y = f0; z = f1; }
-            else if (d == 1) { x = f0; y = a; z = f1; }
-            else { x = f0; y = f1; z = a; }
-            acc = fma(ls[a], Us[k * PS + x + ns * (y + ns * z)], acc);
-          }
-          T1[t] = acc;
-        }
-        __syncthreads();
-        psweep(ops.chi, ns, N, T1, T2, 0, ns, ns, 1);
-        psweep(ops.chi, ns, N, T2, Vq + k * PS, 1, N, ns, 1);
+      psweep(ls, ns, 1, Us, T1, nsl, NV, d, ns, ns, ns);
+      if (d == 0) {
+        psweep(ops.chi, ns, N, T1, T2, nsl, NV, 1, 1, ns, ns);
+        psweep(ops.chi, ns, N, T2, Vq, nsl, NV, 2, 1, N, ns);
+      } else if (d == 1) {
+        psweep(ops.chi, ns, N, T1, T2, nsl, NV, 0, ns, 1, ns);
+        psweep(ops.chi, ns, N, T2, Vq, nsl, NV, 2, N, 1, ns);
+      } else {
+        psweep(ops.chi, ns, N, T1, T2, nsl, NV, 0, ns, ns, 1);
+        psweep(ops.chi, ns, N, T2, Vq, nsl, NV, 1, N, ns, 1);
       }
-      for (int t = threadIdx.x; t < NFP; t += blockDim.x) {
-        double w[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) w[k] = Vq[k * PS + t];
-        store_rec(face + (((size_t)e * 6 + 2 * d + s) * NSFR_NFIELD) * NFP + t, NFP, rec_from_entropy(w, ops, T, flag));
+      for (int t = threadIdx.x; t < nel * NFP; t += blockDim.x) {
+        const int le = t / NFP, fn = t % NFP;
+        const double* v = Vq + (size_t)le * SL + fn;
+        const double w[5] = {v[0], v[NV], v[2 * NV], v[3 * NV], v[4 * NV]};
+        store_rec(face + (((size_t)(e0 + le) * 6 + 2 * d + s) * NSFR_NFIELD) * NFP + fn, NFP,
+                  rec_from_entropy(w, ops, T, flag));
       }
       __syncthreads();
     }
 }
 
-}  // namespace
-
-cudaError_t nsfr_launch_projection(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
-  const size_t smem = ((size_t)12 * PS + NSFR_MATH_TABLE_DOUBLES) * sizeof(double);
-  cudaError_t err = cudaFuncSetAttribute(projection_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int N>
+cudaError_t launch_projection_n(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
+  constexpr int NV = N * N * N, EPB = proj_epb(N);
+  const size_t smem = ((size_t)EPB * 20 * NV + NSFR_MATH_TABLE_DOUBLES) * sizeof(double);
+  cudaError_t err = cudaFuncSetAttribute(projection_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   nsfr_prof_begin(ctx, 1, s);
-  projection_kernel<<<ctx->ne, 256, smem, s>>>(u, ctx->ops, ctx->face, ctx->nrec, ctx->flag);
+  projection_kernel<N><<<(ctx->ne + EPB - 1) / EPB, 256, smem, s>>>(u, ctx->ops, ctx->face, ctx->nrec, ctx->ne,
+                                                                   ctx->flag);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t nsfr_launch_projection(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
+  switch (ctx->n) {
+    case 2: return launch_projection_n<2>(ctx, u, s);
+    case 3: return launch_projection_n<3>(ctx, u, s);
+    case 4: return launch_projection_n<4>(ctx, u, s);
+    case 5: return launch_projection_n<5>(ctx, u, s);
+    case 6: return launch_projection_n<6>(ctx, u, s);
+    case 7: return launch_projection_n<7>(ctx, u, s);
+    case 8: return launch_projection_n<8>(ctx, u, s);
+  }
+  return cudaErrorInvalidValue;
 }

@@ -101,3 +101,18 @@ def test_uncollocated_context_rejects_what_it_does_not_support():
         Solver(np.ascontiguousarray(ctrl), (2, 2, 2), 2, nq=4, precision="fp32_bulk")
     with pytest.raises(NSFRError):
         Solver(np.ascontiguousarray(ctrl), (2, 2, 2), 2, nq=2)  # nq < p+1
+
+
+@pytest.mark.parametrize("p,nq", [(3, 4), (3, 6), (4, 7)])
+def test_uncollocated_entropy_conservation_of_the_library_residual(p, nq):
+    """The paper's overintegrated NSFR-EC rows: -v~^ . R^ = 0, with R^ the library's residual
+    and v~^ = Pi v(chi u^) the projected entropy variables (from the oracle)."""
+    _, P, S, u = _case((2, 2, 2), p, nq, "hu", "ec")
+    S.set_metrics(*_metrics_abi(P))
+    ud = torch.from_numpy(u).cuda()
+    R = torch.empty_like(ud)
+    S.residual_raw(ud, R)
+    torch.cuda.synchronize()
+    Vh, _ = P.projected(P.to_internal(u))
+    prod = P.to_abi(Vh) * R.cpu().numpy()
+    assert abs(prod.sum()) < 1e-13 * np.abs(prod).sum()
