@@ -56,7 +56,7 @@ void prof_free(nsfr_ctx* c) {
 
 void free_all(nsfr_ctx* c) {
   double* dbl[] = {c->ctrl, c->metric, c->J, c->invwj, c->wj, c->nfp_plus, c->xyz, c->face, c->nrec, c->fstar,
-                   c->metric_s, c->nf_s,
+                   c->metric_s, c->nf_s, c->uq,
                    c->ustage, c->acc, c->rtmp, c->hbuf_in, c->hbuf_out, c->red,
                    c->vjp_fown, c->vjp_fnbr, c->vjp_nfbar, c->vjp_mbar, c->vjp_jbar};
   for (double* p : dbl)
@@ -236,6 +236,7 @@ static nsfr_status setup_common(const double* grid_nodes, int nx, int ny, int nz
             dalloc(&ctx->flag, 1) == cudaSuccess && dalloc(&ctx->umax, 1) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->flag_host, sizeof(int)) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->umax_host, sizeof(unsigned long long)) == cudaSuccess;
+  if (ok && ctx->uncol && ctx->n == ctx->ns) ok = dalloc(&ctx->uq, ne * 5 * nv) == cudaSuccess;
   if (ok && precision == NSFR_FP32_BULK)
     ok = dalloc(&ctx->metric32, ne * 18 * nv) == cudaSuccess && dalloc(&ctx->nfp_plus32, ne * 18 * nfp) == cudaSuccess &&
          dalloc(&ctx->invwj32, ne * nv) == cudaSuccess;

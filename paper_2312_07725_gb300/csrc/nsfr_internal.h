@@ -104,6 +104,7 @@ struct nsfr_ctx {
   double* xyz = nullptr;      // [ne][3][nv]
   double* face = nullptr;     // [ne][6][NSFR_NFIELD][nfp] face-state scratch
   double* nrec = nullptr;     // [ne][8][nv] node records (Rec fields) of the last face-state pass
+  double* uq = nullptr;       // [ne][5][nv] chi u^ (uncollocated contexts with square chi)
   double* fstar = nullptr;    // [ne][3][5][nfp] w_perp-scaled numerical flux of each + face
   double* ustage = nullptr;   // [ne][5][nv]
   double* acc = nullptr;      // [ne][5][nv]
@@ -157,6 +158,8 @@ struct RkArgs {
 cudaError_t nsfr_launch_face_states(nsfr_ctx* ctx, const double* u, cudaStream_t s);
 // uncollocated: the entropy projection through chi and Pi (projection.cu)
 cudaError_t nsfr_launch_projection(nsfr_ctx* ctx, const double* u, cudaStream_t s);
+// uncollocated with square chi: u_q = chi u^ into ctx->uq (projection.cu)
+cudaError_t nsfr_launch_interp_square(nsfr_ctx* ctx, const double* u, cudaStream_t s);
 // w_perp-scaled metric and face rows (after the metric terms change)
 cudaError_t nsfr_launch_scaled_rows(nsfr_ctx* ctx, cudaStream_t s);
 // numerical flux of every face once, from the face states (after nsfr_launch_face_states)

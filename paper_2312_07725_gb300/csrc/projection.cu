@@ -168,6 +168,53 @@ cudaError_t launch_projection_n(nsfr_ctx* ctx, const double* u, cudaStream_t s) 
 
 }  // namespace
 
+// u_q = chi u^ for every element (square chi: the GL points carry as many
+// nodes as the solution), written to uq[N_e][5][N^3]
+template <int N>
+__global__ void __launch_bounds__(256) interp_kernel(const double* __restrict__ u, OpsGL ops,
+                                                     double* __restrict__ uq, int ne) {
+  constexpr int NV = N * N * N, SL = 5 * NV, EPB = proj_epb(N);
+  extern __shared__ double sm[];
+  const int ns = ops.ns, nsv = ns * ns * ns;
+  const int e0 = blockIdx.x * EPB, nel = min(EPB, ne - e0), nsl = 5 * nel;
+  double* Us = sm;
+  double* T1 = Us + EPB * SL;
+  double* T2 = T1 + EPB * SL;
+  for (int t = threadIdx.x; t < nsl * nsv; t += blockDim.x)
+    Us[(size_t)(t / nsv) * NV + t % nsv] = u[(size_t)e0 * 5 * nsv + t];
+  __syncthreads();
+  psweep(ops.chi, ns, N, Us, T1, nsl, NV, 0, ns, ns, ns);
+  psweep(ops.chi, ns, N, T1, T2, nsl, NV, 1, N, ns, ns);
+  psweep(ops.chi, ns, N, T2, Us, nsl, NV, 2, N, N, ns);
+  for (int t = threadIdx.x; t < nsl * NV; t += blockDim.x) uq[(size_t)e0 * SL + t] = Us[t];
+}
+
+template <int N>
+cudaError_t launch_interp_n(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
+  constexpr int NV = N * N * N, EPB = proj_epb(N);
+  const size_t smem = (size_t)EPB * 15 * NV * sizeof(double);
+  cudaError_t err = cudaFuncSetAttribute(interp_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  nsfr_prof_begin(ctx, 1, s);
+  interp_kernel<N><<<(ctx->ne + EPB - 1) / EPB, 256, smem, s>>>(u, ctx->ops, ctx->uq, ctx->ne);
+  nsfr_prof_end(ctx, s);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t nsfr_launch_interp_square(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
+  switch (ctx->n) {
+    case 2: return launch_interp_n<2>(ctx, u, s);
+    case 3: return launch_interp_n<3>(ctx, u, s);
+    case 4: return launch_interp_n<4>(ctx, u, s);
+    case 5: return launch_interp_n<5>(ctx, u, s);
+    case 6: return launch_interp_n<6>(ctx, u, s);
+    case 7: return launch_interp_n<7>(ctx, u, s);
+    case 8: return launch_interp_n<8>(ctx, u, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t nsfr_launch_projection(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
   switch (ctx->n) {
     case 2: return launch_projection_n<2>(ctx, u, s);

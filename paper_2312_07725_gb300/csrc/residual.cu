@@ -484,7 +484,15 @@ cudaError_t nsfr_launch_scaled_rows(nsfr_ctx* ctx, cudaStream_t s) {
 }
 
 cudaError_t nsfr_launch_face_states(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
-  if (ctx->uncol) return nsfr_launch_projection(ctx, u, s);
+  if (ctx->uncol && ctx->n != ctx->ns) return nsfr_launch_projection(ctx, u, s);
+  if (ctx->uncol) {
+    // square chi (as many GL points as solution nodes): chi Pi = I, so the projected
+    // state at the GL points is chi u^ itself and the face states follow from
+    // E_-+ = l(-+1)^T Pi applied to v(chi u^): the collocated pass on u_q = chi u^
+    cudaError_t err = nsfr_launch_interp_square(ctx, u, s);
+    if (err != cudaSuccess) return err;
+    u = ctx->uq;
+  }
   switch (ctx->n) {
     case 2: return launch_face_n<2>(ctx, u, s);
     case 3: return launch_face_n<3>(ctx, u, s);
