@@ -158,6 +158,28 @@ nsfr_status nsfr_rk_step(nsfr_ctx* ctx, double* u, double cfl, double dt_fixed, 
                          void* stream);
 
 /*
+ * nsfr_rk_stage -- one stage of the classic RK4 step of nsfr_rk_step, on
+ * caller-owned arrays, for drivers that act between stages (a domain split
+ * into slabs exchanges the ghost-layer states there).  Stage `stage`
+ * (0..3) reads u for stage 0 and ustage otherwise; stages 0..2 write
+ * u + a_s dt k_s (a = 1/2, 1/2, 1) to ustage and accumulate acc (stage 0
+ * sets acc = u + dt/6 k_0); stage 3 writes acc + dt/6 k_3 to u.  u, ustage,
+ * acc: device [N_e][5][solution nodes]; ustage may be read by the next
+ * stage only.  dt > 0.  Asynchronous on the stream; NSFR_ERR_ARG for host
+ * or NULL buffers.  Four calls (stages 0..3) equal one nsfr_rk_step with
+ * dt_fixed = dt.
+ */
+nsfr_status nsfr_rk_stage(nsfr_ctx* ctx, double* u, double* ustage, double* acc, int stage, double dt,
+                          void* stream);
+
+/*
+ * nsfr_max_wavespeed -- max over the nodes of |u| + a for the device state
+ * u (the CFL step of nsfr_rk_step is cfl * dx / this, dx = min_d L_d /
+ * (N_d (p+1))); synchronises the stream and reports a non-physical state.
+ */
+nsfr_status nsfr_max_wavespeed(nsfr_ctx* ctx, const double* u, double* lam, void* stream);
+
+/*
  * nsfr_entropy -- diagnostics of a state (synchronises; FP64 compensated sums).
  *   u    host or device, [N_e][5][n^3].
  *   out  host, 14 doubles:

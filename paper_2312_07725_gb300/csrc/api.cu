@@ -130,39 +130,56 @@ nsfr_status residual_any(nsfr_ctx* ctx, const double* u, double* out, int epi, v
   return NSFR_OK;
 }
 
+// max(|u| + a) over the nodes of u (device); synchronises the stream
+nsfr_status max_wavespeed(nsfr_ctx* ctx, const double* u, double* lam, cudaStream_t s) {
+  CK(nsfr_launch_max_wavespeed(ctx, u, s), "max_wavespeed_kernel");
+  CK(cudaMemcpyAsync(ctx->umax_host, ctx->umax, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s),
+     "cudaMemcpyAsync(max)");
+  nsfr_status st = read_flag(ctx, s);  // synchronises
+  if (st != NSFR_OK) return st;
+  std::memcpy(lam, ctx->umax_host, sizeof(double));
+  if (!(*lam > 0.0)) return fail(ctx, NSFR_ERR_NONPHYSICAL, "zero or invalid wave speed");
+  return NSFR_OK;
+}
+
+// one stage of classic RK4 on the caller's arrays: stage st reads
+// (st == 0 ? u : ustage); u_{st+1} = u^n + a_st dt k_st goes to ustage,
+// acc = u^n + sum b_st dt k_st, and the last stage writes acc + b_3 dt k_3 to u
+nsfr_status rk_stage_device(nsfr_ctx* ctx, double* u, double* ustage, double* acc, int st, double dt,
+                            cudaStream_t s) {
+  const double a[3] = {0.5, 0.5, 1.0};
+  const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  const double* in = (st == 0) ? u : ustage;
+  RkArgs rk;
+  rk.u0 = u;
+  rk.acc = acc;
+  rk.dt = dt;
+  rk.b = b[st];
+  rk.first = (st == 0);
+  rk.last = (st == 3);
+  rk.a_next = (st < 3) ? a[st] : 0.0;
+  rk.unext = (st == 3) ? u : ustage;
+  CK(nsfr_launch_face_states(ctx, in, s), "face_state_kernel");
+  CK(nsfr_launch_face_flux(ctx, s), "face_flux_kernel");
+  CK(launch_volume_any(ctx, in, nullptr, EPI_RK, &rk, s), "volume_kernel(rk)");
+  return NSFR_OK;
+}
+
 nsfr_status rk_step_device(nsfr_ctx* ctx, double* u, double cfl, double dt_fixed, double* dt_used,
                            cudaStream_t s) {
   double dt = dt_fixed;
   if (!(dt_fixed > 0.0)) {
     if (!(cfl > 0.0)) return fail(ctx, NSFR_ERR_ARG, "need cfl > 0 or dt_fixed > 0");
-    CK(nsfr_launch_max_wavespeed(ctx, u, s), "max_wavespeed_kernel");
-    CK(cudaMemcpyAsync(ctx->umax_host, ctx->umax, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s),
-       "cudaMemcpyAsync(max)");
-    nsfr_status st = read_flag(ctx, s);  // synchronises
-    if (st != NSFR_OK) return st;
     double lam;
-    std::memcpy(&lam, ctx->umax_host, sizeof(double));
-    if (!(lam > 0.0)) return fail(ctx, NSFR_ERR_NONPHYSICAL, "zero or invalid wave speed");
+    nsfr_status st = max_wavespeed(ctx, u, &lam, s);
+    if (st != NSFR_OK) return st;
     dt = cfl * ctx->dx / lam;
   }
   if (dt_used) *dt_used = dt;
   // classic RK4: u_{s+1} = u^n + a_s dt k_s, acc = u^n + sum b_s dt k_s
-  const double a[3] = {0.5, 0.5, 1.0};
-  const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
   for (int st = 0; st < 4; ++st) {
-    const double* in = (st == 0) ? u : ctx->ustage;
-    RkArgs rk;
-    rk.u0 = u;
-    rk.acc = ctx->acc;
-    rk.dt = dt;
-    rk.b = b[st];
-    rk.first = (st == 0);
-    rk.last = (st == 3);
-    rk.a_next = (st < 3) ? a[st] : 0.0;
-    rk.unext = (st == 3) ? u : ctx->ustage;
-    CK(nsfr_launch_face_states(ctx, in, s), "face_state_kernel");
-    CK(nsfr_launch_face_flux(ctx, s), "face_flux_kernel");
-    CK(launch_volume_any(ctx, in, nullptr, EPI_RK, &rk, s), "volume_kernel(rk)");
+    nsfr_status r = rk_stage_device(ctx, u, ctx->ustage, ctx->acc, st, dt, s);
+    if (r != NSFR_OK) return r;
   }
   return NSFR_OK;
 }
@@ -315,6 +332,27 @@ nsfr_status nsfr_rk_step(nsfr_ctx* ctx, double* u, double cfl, double dt_fixed, 
   CK(cudaMemcpyAsync(u, ctx->hbuf_in, bytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(D2H)");
   CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
   return NSFR_OK;
+}
+
+nsfr_status nsfr_rk_stage(nsfr_ctx* ctx, double* u, double* ustage, double* acc, int stage, double dt,
+                          void* stream) {
+  if (!ctx) return NSFR_ERR_ARG;
+  if (!u || !ustage || !acc || stage < 0 || stage > 3 || !(dt > 0.0))
+    return fail(ctx, NSFR_ERR_ARG, "nsfr_rk_stage: NULL buffer, stage outside 0..3 or dt <= 0");
+  if (!is_device_ptr(u) || !is_device_ptr(ustage) || !is_device_ptr(acc))
+    return fail(ctx, NSFR_ERR_ARG, "nsfr_rk_stage takes device buffers");
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  return rk_stage_device(ctx, u, ustage, acc, stage, dt, s);
+}
+
+nsfr_status nsfr_max_wavespeed(nsfr_ctx* ctx, const double* u, double* lam, void* stream) {
+  if (!ctx) return NSFR_ERR_ARG;
+  if (!u || !lam) return fail(ctx, NSFR_ERR_ARG, "NULL buffer");
+  if (!is_device_ptr(u)) return fail(ctx, NSFR_ERR_ARG, "nsfr_max_wavespeed takes a device state");
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  return max_wavespeed(ctx, u, lam, s);
 }
 
 nsfr_status nsfr_entropy(nsfr_ctx* ctx, const double* u, double* out, void* stream) {

@@ -26,7 +26,7 @@ NODES = {"gl": 0, "lgl": 1}
 
 # every symbol include/nsfr.h declares
 EXPORTS = ["nsfr_setup", "nsfr_setup_uncollocated", "nsfr_residual", "nsfr_residual_raw", "nsfr_rk_step", "nsfr_entropy",
-           "nsfr_vjp", "nsfr_node_coords", "nsfr_get_metrics", "nsfr_set_metrics", "nsfr_quadrature", "nsfr_info", "nsfr_check",
+           "nsfr_rk_stage", "nsfr_max_wavespeed", "nsfr_vjp", "nsfr_node_coords", "nsfr_get_metrics", "nsfr_set_metrics", "nsfr_quadrature", "nsfr_info", "nsfr_check",
            "nsfr_profile", "nsfr_profile_read", "nsfr_residual_static", "nsfr_math_eval", "nsfr_kernel_launches",
            "nsfr_last_error", "nsfr_destroy"]
 KERNELS = ["metrics", "face_states", "volume", "max_wavespeed", "diagnostics", "vjp_face", "vjp_volume",
@@ -75,6 +75,10 @@ def load_library(path=LIB_PATH):
     lib.nsfr_profile_read.restype = i
     lib.nsfr_residual_static.argtypes = [vp, vp, vp, vp, i, i, i, i, d, i, d, vp, vp]
     lib.nsfr_residual_static.restype = i
+    lib.nsfr_rk_stage.argtypes = [vp, vp, vp, vp, i, d, vp]
+    lib.nsfr_rk_stage.restype = i
+    lib.nsfr_max_wavespeed.argtypes = [vp, vp, ctypes.POINTER(d), vp]
+    lib.nsfr_max_wavespeed.restype = i
     lib.nsfr_math_eval.argtypes = [i, vp, vp, ctypes.c_longlong, vp]
     lib.nsfr_math_eval.restype = i
     lib.nsfr_kernel_launches.argtypes = [vp]
@@ -215,6 +219,24 @@ class Solver:
         self._check(self._lib.nsfr_rk_step(self._h, _ptr(u), float(cfl), float(dt), ctypes.byref(used),
                                            _stream(stream)), "nsfr_rk_step")
         return used.value
+
+    def rk_stage(self, u, ustage, acc, stage, dt, stream=None):
+        """One RK4 stage on caller-owned device arrays (see nsfr_rk_stage)."""
+        self._check(self._lib.nsfr_rk_stage(self._h, _ptr(u), _ptr(ustage), _ptr(acc), int(stage), float(dt),
+                                            _stream(stream)), "nsfr_rk_stage")
+
+    def max_wavespeed(self, u, stream=None):
+        lam = ctypes.c_double(0.0)
+        self._check(self._lib.nsfr_max_wavespeed(self._h, _ptr(u), ctypes.byref(lam), _stream(stream)),
+                    "nsfr_max_wavespeed")
+        return lam.value
+
+    @property
+    def dx(self):
+        """min_d L_d / (N_d (p+1)), the node spacing of the CFL step (from the control points)."""
+        lo = self._keep.reshape(-1, 3).min(axis=0)
+        hi = self._keep.reshape(-1, 3).max(axis=0)
+        return float(min((hi[d] - lo[d]) / (self.shape[d] * (self.p + 1)) for d in range(3)))
 
     def entropy(self, u, stream=None):
         out = np.zeros(14)

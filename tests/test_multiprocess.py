@@ -13,6 +13,7 @@ import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -67,3 +68,87 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_zero():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+# --------------------------------------------------------------------------
+# the z-slab decomposition's host logic (paper_2312_07725_gb300.slab)
+# --------------------------------------------------------------------------
+def test_extended_layers_take_the_neighbour_layers():
+    import math
+
+    import workloads as wl
+    from paper_2312_07725_gb300.slab import extended_layers, slab_range
+    shape = (3, 2, 6)
+    ctrl = wl.control_points(*shape, 2, -math.pi, math.pi, wl.warp_tgv)
+    L = 6
+    for ws in (1, 2, 3):
+        for r in range(ws):
+            z0, nz = slab_range(6, ws, r)
+            ext = extended_layers(ctrl, shape, z0, nz)
+            assert ext.shape[0] == (nz + 2) * L
+            for k in range(nz + 2):
+                z = (z0 - 1 + k) % 6
+                assert np.array_equal(ext[k * L:(k + 1) * L], ctrl[z * L:(z + 1) * L])
+    with pytest.raises(ValueError):
+        slab_range(7, 2, 0)
+
+
+def _halo_rank(rank, ws, port, out_dir, late):
+    os.environ.update({"RANK": str(rank), "WORLD_SIZE": str(ws), "MASTER_ADDR": "127.0.0.1",
+                       "MASTER_PORT": str(port)})
+    sys.path.insert(0, ROOT)
+    import time
+
+    import torch
+    import torch.distributed as dist
+    from paper_2312_07725_gb300.slab import DistExchanger, HaloTimeout
+    dist.init_process_group("gloo")
+    L, nz = 4, 3
+    t = torch.zeros(((nz + 2) * L, 5, 8), dtype=torch.float64)
+    for k in range(nz):  # interior layer k of rank r holds 100 r + k
+        t[(k + 1) * L:(k + 2) * L] = 100.0 * rank + k
+    res = {"rank": rank}
+    ex = DistExchanger(dist, rank, ws, timeout_s=2.0 if late else 60.0)
+    if late and rank == 1:
+        time.sleep(6.0)  # a late neighbour: rank 0 must give up with HaloTimeout
+    try:
+        ex.exchange(t, L)
+        res["top"] = float(t[-L:].mean())
+        res["bottom"] = float(t[:L].mean())
+        res["max"] = ex.global_max(float(rank) + 0.5)
+    except HaloTimeout:
+        res["timeout"] = True
+    with open(os.path.join(out_dir, f"halo{rank}.json"), "w") as f:
+        json.dump(res, f)
+    os._exit(0)  # no collective teardown after a deliberately broken exchange
+
+
+@pytest.mark.parametrize("ws", [2, 3])
+def test_halo_exchange_fills_the_ghost_layers_with_gloo(tmp_path, ws):
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_halo_rank, args=(r, ws, port, str(tmp_path), False)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    res = [json.load(open(tmp_path / f"halo{r}.json")) for r in range(ws)]
+    for r, x in enumerate(res):
+        above, below = (r + 1) % ws, (r - 1) % ws
+        assert x["top"] == 100.0 * above + 0            # first interior layer of the rank above
+        assert x["bottom"] == 100.0 * below + 2         # last interior layer of the rank below
+        assert x["max"] == ws - 1 + 0.5
+
+
+def test_a_late_neighbour_raises_halo_timeout(tmp_path):
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_halo_rank, args=(r, 2, port, str(tmp_path), True)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    r0 = json.load(open(tmp_path / "halo0.json"))
+    assert r0.get("timeout") is True
