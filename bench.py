@@ -14,8 +14,14 @@ solution node (the paper's count); x5 per conserved component is printed
 separately.  The state (1.3 GB) is larger than L2 (129 MB), so no L2 flush is
 needed between steps.
 
+With --decomp slab the ranks hold the z-slabs of a periodic stack of N copies
+of the mesh (one copy per rank, one ghost element layer per side) and exchange
+the boundary layers before every stage; at N = 1 the slab exchanges with
+itself, which measures the ghost-layer and exchange overhead on one GPU.
+
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                        [--precision fp64|fp32_bulk] [--n-el E] [--p P]
+                        [--precision fp64|fp32_bulk] [--n-el E] [--p P] [--nq Q]
+                        [--decomp replicas|slab]
 """
 from __future__ import annotations
 
@@ -60,6 +66,9 @@ def parse():
     ap.add_argument("--cfl", type=float, default=0.1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--decomp", default="replicas", choices=["replicas", "slab"],
+                    help="replicas: every rank steps its own copy of the mesh; slab: the ranks "
+                         "hold the z-slabs of ws stacked copies (halo exchange every stage)")
     ap.add_argument("--nq", type=int, default=None,
                     help="uncollocated scheme: solution on the p+1 Lobatto nodes, NQ Gauss-Legendre "
                          "quadrature points per direction (FP64 only)")
@@ -71,7 +80,14 @@ def c_value(p):
         return float(json.load(f)["c_hu"][str(p)])
 
 
-def workload_config(args):
+def workload_config(args, ws):
+    N = args.n_el
+    if args.decomp == "slab":
+        par = (f"z-slabs: rank r holds layers {N}r..{N}r+{N - 1} of a periodic {N}x{N}x{N * ws} stack "
+               f"of {ws} copies, one ghost layer per side, halo exchange before every stage, "
+               "all-reduce max for dt")
+    else:
+        par = f"{ws} independent replica(s), no data-path collective"
     n = args.p + 1
     nodes = args.n_el ** 3 * n ** 3
     quad = "GL collocated" if args.nq is None else f"LGL solution, {args.nq} GL quadrature points per direction"
@@ -80,7 +96,7 @@ def workload_config(args):
         "elements": args.n_el ** 3, "p": args.p, "nodes": nodes, "variables": 5,
         "c": c_value(args.p), "c_kind": "c_HU (stand-in for c_+)", "volume_flux": "chandrashekar",
         "face_flux": "ec", "quadrature": quad, "cfl": args.cfl, "step": "RK4 step = 4 stages",
-        "l2_flush": "not needed: state 40 B/node x nodes > 129 MB L2",
+        "l2_flush": "not needed: state 40 B/node x nodes > 129 MB L2", "parallelism": par,
     }
 
 
@@ -138,7 +154,8 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------
-# distributed plumbing: each rank runs an independent replica (weak scaling)
+# distributed plumbing: each rank runs an independent replica, or one z-slab of a
+# stack of copies (--decomp slab); weak scaling either way
 # --------------------------------------------------------------------------
 def dist_init(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -202,7 +219,7 @@ def oracle_sample_rate(p, n_sample=8, budget_s=20.0):
 def run_reference(args, rank, ws, dist):
     if rank != 0:
         return
-    cfg = workload_config(args)
+    cfg = workload_config(args, ws)
     val, cores, sample = oracle_sample_rate(args.p)
     line = {"impl": "reference", "metric": "NSFR-EC residual GDOF/s per RK stage", "value": val,
             "unit": "GDOF/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -239,19 +256,80 @@ def volume_kernel_flops(n_el, p, has_k=True, nq=None):
     return per_el * n_el, {"volume_pairs": fluxes_vol, "hybrid": fluxes_hyb, "flops_per_element": per_el}
 
 
-def measure(args, ctrl, u0, precision, dist, ws, steps):
+class _Replica:
+    """The whole mesh on this GPU (every rank an independent replica)."""
+
+    def __init__(self, args, ctrl, u0, precision, dist, rank, ws):
+        import torch
+        from paper_2312_07725_gb300 import Solver
+        N = args.n_el
+        self.S = Solver(ctrl, (N, N, N), args.p, c=c_value(args.p), face_flux="ec", precision=precision,
+                        nq=args.nq)
+        self.u0 = u0
+        self.u = torch.from_numpy(u0).cuda()
+        self.cfl = args.cfl
+
+    def step(self, u):
+        self.S.rk_step(u, cfl=self.cfl)
+
+    def e2e_setup(self):
+        import torch
+        self.uh = torch.from_numpy(self.u0).pin_memory()
+        self.S.rk_step(self.uh.numpy(), cfl=self.cfl)  # sizes the library's staging buffers
+        return self.uh.numel() * 8
+
+    def e2e_step(self):
+        # through the C ABI with pinned host buffers: the library copies in and out
+        self.S.rk_step(self.uh.numpy(), cfl=self.cfl)
+
+    def interior(self, t):
+        return t
+
+
+class _SlabRank:
+    """One z-slab of a z-stack of ws copies of the mesh (weak scaling), with ghost
+    layers refreshed by a halo exchange before every RK stage."""
+
+    def __init__(self, args, ctrl, u0, precision, dist, rank, ws):
+        from paper_2312_07725_gb300.slab import DistExchanger, Slab
+        N = args.n_el
+        self.slab = Slab(ctrl, (N, N, N), args.p, rank, ws, DistExchanger(dist, rank, ws), copies=ws,
+                         c=c_value(args.p), face_flux="ec", precision=precision, nq=args.nq)
+        self.S = self.slab.solver
+        self.u = self.slab.extend(u0)
+        self.cfl = args.cfl
+
+    def step(self, u):
+        self.slab.step(u, cfl=self.cfl)
+
+    def e2e_setup(self):
+        import torch
+        self.uh = self.u.cpu().pin_memory()
+        self.ud = torch.empty_like(self.u)
+        return self.uh.numel() * 8
+
+    def e2e_step(self):
+        import torch
+        self.ud.copy_(self.uh, non_blocking=True)
+        self.slab.step(self.ud, cfl=self.cfl)
+        self.uh.copy_(self.ud, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    def interior(self, t):
+        return self.slab.interior(t)
+
+
+def measure(args, ctrl, u0, precision, dist, rank, ws, steps):
     """Time `steps` RK4 steps of one precision mode, plus its e2e variant."""
     import torch
-    from paper_2312_07725_gb300 import Solver
 
     p, N = args.p, args.n_el
-    c = c_value(p)
-    S = Solver(ctrl, (N, N, N), p, c=c, face_flux="ec", precision=precision, nq=args.nq)
-    u = torch.from_numpy(u0).cuda()
+    run = (_SlabRank if args.decomp == "slab" else _Replica)(args, ctrl, u0, precision, dist, rank, ws)
+    S, u = run.S, run.u
     stream = torch.cuda.current_stream()
-    nodes = N ** 3 * (p + 1) ** 3
+    nodes = N ** 3 * (p + 1) ** 3  # this rank's own nodes (ghost layers not counted)
     for _ in range(args.warmup):
-        S.rk_step(u, cfl=args.cfl)
+        run.step(u)
     torch.cuda.synchronize()
     barrier(dist)
     launches0 = S.kernel_launches()
@@ -263,7 +341,7 @@ def measure(args, ctrl, u0, precision, dist, ws, steps):
     torch.cuda.synchronize()
     ev0.record(stream)
     for _ in range(steps):
-        S.rk_step(u, cfl=args.cfl)
+        run.step(u)
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -272,18 +350,17 @@ def measure(args, ctrl, u0, precision, dist, ws, steps):
     launches = S.kernel_launches() - launches0
     ms = max_over_ranks(dist, ev0.elapsed_time(ev1))
     value = nodes * 4 * steps * ws / (ms / 1e3) / 1e9
-    # e2e: the same RK4 step through the C ABI with pinned host buffers
-    uh = torch.from_numpy(u0).pin_memory()
-    S.rk_step(uh.numpy(), cfl=args.cfl)  # sizes the staging buffers
+    # e2e: the same RK4 step from and back to pinned host memory
+    e2e_bytes = run.e2e_setup()
     barrier(dist)
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        S.rk_step(uh.numpy(), cfl=args.cfl)
+        run.e2e_step()
     e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
     e2e = nodes * 4 * args.e2e_steps * ws / e2e_s / 1e9
     # one du/dt of the initial state, to compare the two precision modes
-    D = torch.empty_like(u)
-    uin = torch.from_numpy(u0).cuda()
+    uin = torch.from_numpy(u0).cuda() if args.decomp != "slab" else run.slab.extend(u0)
+    D = torch.empty_like(uin)
     S.residual(uin, D)
     torch.cuda.synchronize()
     # residual only (entropy projection, face fluxes, volume terms and the WA inverse, no RK
@@ -302,17 +379,18 @@ def measure(args, ctrl, u0, precision, dist, ws, steps):
     residual_only = nodes * ws / (rms / 1e3) / 1e9
     del uin
     kern = {k: {"ms_total": v[0], "launches": v[1], "ms_avg": v[0] / v[1]} for k, v in prof.items()}
-    res = {"value": value, "ms_per_step": ms / steps, "e2e": e2e, "gpu_launches": launches, "kernels": kern,
-           "clocks": clk, "dudt": D.cpu().numpy(),
+    res = {"value": value, "ms_per_step": ms / steps, "e2e": e2e, "e2e_bytes": e2e_bytes,
+           "gpu_launches": launches, "kernels": kern, "clocks": clk,
+           "dudt": run.interior(D).cpu().numpy(), "n_el_computed": S.n_el,
            "residual_only": {"value": residual_only, "unit": "GDOF/s", "ms_per_evaluation": rms}}
     S.close()
-    del u, D
+    del u, D, run
     torch.cuda.empty_cache()
     return res
 
 
 def run_ours(args, rank, ws, dist):
-    cfg = workload_config(args)
+    cfg = workload_config(args, ws)
     p, N = args.p, args.n_el
     ctrl = wl.tgv_mesh(N, p)
     from paper_2312_07725_gb300 import Solver
@@ -321,13 +399,12 @@ def run_ours(args, rank, ws, dist):
     S0.close()
     u0 = np.ascontiguousarray(wl.tgv_state(xyz))
     del xyz
-    state_bytes = u0.nbytes
 
-    m64 = measure(args, ctrl, u0, "fp64", dist, ws, args.steps)
+    m64 = measure(args, ctrl, u0, "fp64", dist, rank, ws, args.steps)
     d64 = m64.pop("dudt")
     m32 = None
     if args.nq is None:  # the FP32-bulk form exists for the collocated scheme
-        m32 = measure(args, ctrl, u0, "fp32_bulk", dist, ws, args.steps)
+        m32 = measure(args, ctrl, u0, "fp32_bulk", dist, rank, ws, args.steps)
         d32 = m32.pop("dudt")
         bulk_err = float(np.linalg.norm((d32 - d64).ravel()) / np.linalg.norm(d64.ravel()))
         del d32
@@ -335,11 +412,12 @@ def run_ours(args, rank, ws, dist):
 
     clk = m64["clocks"]
     vol_ms, vol_n = m64["kernels"]["volume"]["ms_total"], m64["kernels"]["volume"]["launches"]
-    flops, counts = volume_kernel_flops(N ** 3, p, cfg["c"] != 0.0, args.nq)
+    ne_launch = m64["n_el_computed"]  # elements one volume launch processes (slabs: with ghost layers)
+    flops, counts = volume_kernel_flops(ne_launch, p, cfg["c"] != 0.0, args.nq)
     achieved = flops / (vol_ms / vol_n / 1e3) / 1e12
     peak, peak_src = fp64_peak(clk)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": (VOLUME_DRAM_BYTES_PER_ELEMENT[p] * N ** 3
+            "traffic": (VOLUME_DRAM_BYTES_PER_ELEMENT[p] * ne_launch
                         if p in VOLUME_DRAM_BYTES_PER_ELEMENT and args.nq is None else None),
             "traffic_unit": "bytes per launch", "kernel": f"volume_kernel<{args.nq or p + 1}> (FP64 pipe)",
             "peak_source": peak_src,
@@ -354,8 +432,8 @@ def run_ours(args, rank, ws, dist):
                 "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": m64["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": cfg, "gdof_per_s_x5_components": 5 * m64["value"],
-                "e2e": {"value": m64["e2e"], "unit": "GDOF/s", "h2d_bytes_per_step": state_bytes,
-                        "d2h_bytes_per_step": state_bytes},
+                "e2e": {"value": m64["e2e"], "unit": "GDOF/s", "h2d_bytes_per_step": m64["e2e_bytes"],
+                        "d2h_bytes_per_step": m64["e2e_bytes"]},
                 "gpu_launches": m64["gpu_launches"], "kernels": m64["kernels"], "roofline": roof, "clocks": clk,
                 "residual_only": m64["residual_only"],
                 "cpu_baseline": cpu,
@@ -363,8 +441,8 @@ def run_ours(args, rank, ws, dist):
                 {"value": m32["value"], "unit": "GDOF/s", "ms_per_step": m32["ms_per_step"],
                  "speedup_vs_fp64": m32["value"] / m64["value"],
                  "dudt_rel_l2_vs_fp64_path": bulk_err,
-                 "e2e": {"value": m32["e2e"], "unit": "GDOF/s", "h2d_bytes_per_step": state_bytes,
-                         "d2h_bytes_per_step": state_bytes},
+                 "e2e": {"value": m32["e2e"], "unit": "GDOF/s", "h2d_bytes_per_step": m32["e2e_bytes"],
+                         "d2h_bytes_per_step": m32["e2e_bytes"]},
                  "gpu_launches": m32["gpu_launches"], "kernels": m32["kernels"],
                  "residual_only": m32["residual_only"],
                  "clocks": m32["clocks"], "dtype": "f32 bulk, f64 log means/state"}}

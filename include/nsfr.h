@@ -165,12 +165,16 @@ nsfr_status nsfr_rk_step(nsfr_ctx* ctx, double* u, double cfl, double dt_fixed, 
  * u + a_s dt k_s (a = 1/2, 1/2, 1) to ustage and accumulate acc (stage 0
  * sets acc = u + dt/6 k_0); stage 3 writes acc + dt/6 k_3 to u.  u, ustage,
  * acc: device [N_e][5][solution nodes]; ustage may be read by the next
- * stage only.  dt > 0.  Asynchronous on the stream; NSFR_ERR_ARG for host
- * or NULL buffers.  Four calls (stages 0..3) equal one nsfr_rk_step with
- * dt_fixed = dt.
+ * stage only.  dt > 0.  Only elements e_begin <= e < e_end are updated
+ * (their entries of ustage, acc and u); the face states of every element
+ * enter their face terms, and the other elements' entries are left as they
+ * are (0 and N_e: all; a slab's ghost layers need no update).  Asynchronous
+ * on the stream; NSFR_ERR_ARG for host or NULL buffers or a range outside
+ * 0 <= e_begin <= e_end <= N_e.  Four calls (stages 0..3) over all elements
+ * equal one nsfr_rk_step with dt_fixed = dt.
  */
 nsfr_status nsfr_rk_stage(nsfr_ctx* ctx, double* u, double* ustage, double* acc, int stage, double dt,
-                          void* stream);
+                          int e_begin, int e_end, void* stream);
 
 /*
  * nsfr_max_wavespeed -- max over the nodes of |u| + a for the device state

@@ -335,15 +335,22 @@ nsfr_status nsfr_rk_step(nsfr_ctx* ctx, double* u, double cfl, double dt_fixed, 
 }
 
 nsfr_status nsfr_rk_stage(nsfr_ctx* ctx, double* u, double* ustage, double* acc, int stage, double dt,
-                          void* stream) {
+                          int e_begin, int e_end, void* stream) {
   if (!ctx) return NSFR_ERR_ARG;
   if (!u || !ustage || !acc || stage < 0 || stage > 3 || !(dt > 0.0))
     return fail(ctx, NSFR_ERR_ARG, "nsfr_rk_stage: NULL buffer, stage outside 0..3 or dt <= 0");
+  if (e_begin < 0 || e_end < e_begin || e_end > ctx->ne)
+    return fail(ctx, NSFR_ERR_ARG, "nsfr_rk_stage: element range outside 0 <= e_begin <= e_end <= N_e");
   if (!is_device_ptr(u) || !is_device_ptr(ustage) || !is_device_ptr(acc))
     return fail(ctx, NSFR_ERR_ARG, "nsfr_rk_stage takes device buffers");
   cudaStream_t s = (cudaStream_t)stream;
   ctx->last_stream = s;
-  return rk_stage_device(ctx, u, ustage, acc, stage, dt, s);
+  ctx->vol_b = e_begin;
+  ctx->vol_e = e_end;
+  const nsfr_status st = rk_stage_device(ctx, u, ustage, acc, stage, dt, s);
+  ctx->vol_b = 0;
+  ctx->vol_e = -1;
+  return st;
 }
 
 nsfr_status nsfr_max_wavespeed(nsfr_ctx* ctx, const double* u, double* lam, void* stream) {

@@ -83,6 +83,8 @@ struct nsfr_ctx {
   // for the collocated schemes).  The state and the RK arrays have nsv nodes.
   int nx, ny, nz, ne, p, n, pg, q, nv, nfp;
   int ns = 0, nsv = 0, uncol = 0;
+  // elements [vol_b, vol_e) get the volume pass (nsfr_rk_stage's range); vol_e < 0: all
+  int vol_b = 0, vol_e = -1;
   double c, gamma;
   int vol_flux, face_flux, precision, nodes;
   OpsGL ops;

@@ -244,12 +244,13 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
                                                                 const double* __restrict__ face,
                                                                 const double* __restrict__ fstar,
                                                                 const double* __restrict__ invwj, OpsGL ops, int nx,
-                                                                int ny, int nz, int ne, int epi, RkArgs rk,
-                                                                double* out, int* flag) {
+                                                                int ny, int nz, int e_beg, int ne, int epi,
+                                                                RkArgs rk, double* out, int* flag) {
+  // elements e_beg .. ne-1 (the whole mesh's neighbours stay reachable)
   constexpr int NV = N * N * N, NFP = N * N, NL = 3 * NFP;
   extern __shared__ double sm[];
   const int epb = blockDim.x / NL;
-  const int e0 = blockIdx.x * epb;
+  const int e0 = e_beg + blockIdx.x * epb;
   double* P = sm;                      // [epb][6][NV] node records (the logs stay in nrec)
   double* Ms = P + (size_t)epb * 6 * NV;  // [epb][9][NV] metric rows / 2
   double* Ra = Ms + (size_t)epb * 9 * NV;  // [epb][3][5][NV] line sums, one slab per direction
@@ -437,7 +438,9 @@ cudaError_t launch_volume_n(nsfr_ctx* ctx, const double* u, double* out, int epi
                             cudaStream_t s) {
   constexpr int NV = N * N * N;
   constexpr int epb = vol_epb(N);
-  const int grid = (ctx->ne + epb - 1) / epb;
+  const int eb = ctx->vol_b, ee = ctx->vol_e < 0 ? ctx->ne : ctx->vol_e;
+  const int grid = (ee - eb + epb - 1) / epb;
+  if (grid <= 0) return cudaSuccess;
   const size_t smem = (size_t)epb * (6 + 9 + 15) * NV * sizeof(double);
   cudaError_t err = cudaFuncSetAttribute(volume_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
@@ -445,7 +448,7 @@ cudaError_t launch_volume_n(nsfr_ctx* ctx, const double* u, double* out, int epi
   nsfr_prof_begin(ctx, 2, s);
   volume_kernel<N><<<grid, vol_threads(N), smem, s>>>(ctx->nrec, ctx->metric_s, ctx->nf_s, ctx->face,
                                                       ctx->fstar, ctx->invwj, ctx->ops, ctx->nx, ctx->ny, ctx->nz,
-                                                      ctx->ne, epi, r, out, ctx->flag);
+                                                      eb, ee, epi, r, out, ctx->flag);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
   return cudaGetLastError();

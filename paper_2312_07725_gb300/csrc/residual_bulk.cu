@@ -140,12 +140,13 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
     volume_bulk_kernel(const double* __restrict__ nrec, const float* __restrict__ metric32,
                        const double* __restrict__ nf_s, const float* __restrict__ nf32,
                        const double* __restrict__ face, const double* __restrict__ fstar,
-                       const float* __restrict__ invwj32, OpsGL ops, int nx, int ny, int nz, int ne, int epi, RkArgs rk,
-                       double* out, int* flag) {
+                       const float* __restrict__ invwj32, OpsGL ops, int nx, int ny, int nz, int e_beg, int ne,
+                       int epi, RkArgs rk, double* out, int* flag) {
+  // elements e_beg .. ne-1 (the whole mesh's neighbours stay reachable)
   constexpr int NV = N * N * N, NFP = N * N, NL = 3 * NFP;
   extern __shared__ double sm[];
   const int epb = blockDim.x / NL;
-  const int e0 = blockIdx.x * epb;
+  const int e0 = e_beg + blockIdx.x * epb;
   BRef* Refs = (BRef*)sm;                          // [epb]
   double* Pd = (double*)(Refs + epb);              // [epb][2][NV]
   double* Rd = Pd + (size_t)epb * 2 * NV;          // [epb][5][NV]
@@ -371,7 +372,9 @@ template <int N>
 cudaError_t launch_bulk_n(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk, cudaStream_t s) {
   constexpr int NV = N * N * N;
   constexpr int epb = bulk_epb(N);
-  const int grid = (ctx->ne + epb - 1) / epb;
+  const int eb = ctx->vol_b, ee = ctx->vol_e < 0 ? ctx->ne : ctx->vol_e;
+  const int grid = (ee - eb + epb - 1) / epb;
+  if (grid <= 0) return cudaSuccess;
   const size_t smem = (size_t)epb * (sizeof(BRef) + NV * (7 * sizeof(double) + 43 * sizeof(float)));
   cudaError_t err =
       cudaFuncSetAttribute(volume_bulk_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -380,7 +383,7 @@ cudaError_t launch_bulk_n(nsfr_ctx* ctx, const double* u, double* out, int epi, 
   nsfr_prof_begin(ctx, 2, s);
   volume_bulk_kernel<N><<<grid, bulk_threads(N), smem, s>>>(ctx->nrec, ctx->metric32, ctx->nf_s,
                                                            ctx->nfp_plus32, ctx->face, ctx->fstar, ctx->invwj32,
-                                                           ctx->ops, ctx->nx, ctx->ny, ctx->nz, ctx->ne, epi, r, out,
+                                                           ctx->ops, ctx->nx, ctx->ny, ctx->nz, eb, ee, epi, r, out,
                                                            ctx->flag);
   nsfr_prof_end(ctx, s);
   ctx->launches++;

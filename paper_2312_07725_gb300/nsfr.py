@@ -75,7 +75,7 @@ def load_library(path=LIB_PATH):
     lib.nsfr_profile_read.restype = i
     lib.nsfr_residual_static.argtypes = [vp, vp, vp, vp, i, i, i, i, d, i, d, vp, vp]
     lib.nsfr_residual_static.restype = i
-    lib.nsfr_rk_stage.argtypes = [vp, vp, vp, vp, i, d, vp]
+    lib.nsfr_rk_stage.argtypes = [vp, vp, vp, vp, i, d, i, i, vp]
     lib.nsfr_rk_stage.restype = i
     lib.nsfr_max_wavespeed.argtypes = [vp, vp, ctypes.POINTER(d), vp]
     lib.nsfr_max_wavespeed.restype = i
@@ -220,10 +220,12 @@ class Solver:
                                            _stream(stream)), "nsfr_rk_step")
         return used.value
 
-    def rk_stage(self, u, ustage, acc, stage, dt, stream=None):
-        """One RK4 stage on caller-owned device arrays (see nsfr_rk_stage)."""
+    def rk_stage(self, u, ustage, acc, stage, dt, elements=None, stream=None):
+        """One RK4 stage on caller-owned device arrays (see nsfr_rk_stage); ``elements``
+        (begin, end) limits the update to that element range."""
+        b, e = (0, self.n_el) if elements is None else elements
         self._check(self._lib.nsfr_rk_stage(self._h, _ptr(u), _ptr(ustage), _ptr(acc), int(stage), float(dt),
-                                            _stream(stream)), "nsfr_rk_stage")
+                                            int(b), int(e), _stream(stream)), "nsfr_rk_stage")
 
     def max_wavespeed(self, u, stream=None):
         lam = ctypes.c_double(0.0)

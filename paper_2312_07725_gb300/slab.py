@@ -9,9 +9,10 @@ interior element.  The state of an element layer is a contiguous
 [nx*ny][5][n^3] slice, so before every RK stage a rank sends its first and last
 interior layers to the ranks below and above, which store them in their ghost
 layers: the one exchange of the method (the face states of the partition
-faces follow from the ghost states).  Ghost elements compute throw-away values
-(their outer neighbours are wrong) that the next exchange overwrites.  The time
-step is the CFL step of the largest wave speed over all ranks.
+faces follow from the ghost states).  Ghost elements get face states but no
+volume pass and no stage update (their outer neighbours are not theirs); the
+next exchange refills them.  The time step is the CFL step of the largest wave
+speed over all ranks.
 
 Two exchangers move the layers: ``DistExchanger`` (torch.distributed point-to-
 point operations, NCCL between GPUs or gloo, with a timeout that turns a
@@ -109,13 +110,16 @@ class DistExchanger:
 class Slab:
     """One rank's slab of the global mesh, with its ghost layers and RK arrays."""
 
-    def __init__(self, ctrl, shape, p, rank, ws, exchanger=None, **solver_kw):
+    def __init__(self, ctrl, shape, p, rank, ws, exchanger=None, copies=1, **solver_kw):
+        """``ctrl`` [nx*ny*NZ][q^3][3] and ``shape`` (nx, ny, NZ) describe the periodic mesh;
+        with ``copies`` > 1 the decomposed mesh is that many copies of it stacked along z
+        (nx x ny x copies*NZ elements, a weak-scaling workload that needs one copy in memory)."""
         import torch
         nx, ny, NZ = shape
         self.shape, self.p, self.rank, self.ws = tuple(shape), p, rank, ws
-        self.z0, self.nz = slab_range(NZ, ws, rank)
+        self.z0, self.nz = slab_range(NZ * copies, ws, rank)
         self.layer = nx * ny
-        self.ctrl = extended_layers(ctrl, shape, self.z0, self.nz)
+        self.ctrl = extended_layers(ctrl, shape, self.z0, self.nz)  # layer indices wrap mod NZ
         self.solver = Solver(self.ctrl, (nx, ny, self.nz + 2), p, **solver_kw)
         self.exchanger = exchanger
         n = self.solver.n
@@ -131,7 +135,8 @@ class Slab:
         return t[self.layer:-self.layer]
 
     def extend(self, u_global):
-        """This rank's extended state (device) cut from a global host state."""
+        """This rank's extended state (device) cut from a global host state (one copy of
+        the mesh's state with ``copies`` > 1)."""
         import torch
         return torch.from_numpy(extended_layers(u_global, self.shape, self.z0, self.nz)).cuda()
 
@@ -139,7 +144,9 @@ class Slab:
         return self.solver.node_coords()
 
     def stage(self, u, st, dt):
-        self.solver.rk_stage(u, self.ustage, self.acc, st, dt)
+        # the interior elements only: the ghost layers are refilled by the next exchange
+        self.solver.rk_stage(u, self.ustage, self.acc, st, dt,
+                             elements=(self.layer, self.layer * (self.nz + 1)))
 
     def step(self, u, cfl=0.1, dt=None):
         """One RK4 step of the decomposed problem (every rank calls it); returns dt."""

@@ -131,3 +131,39 @@ def test_two_process_slabs_with_the_distributed_exchanger(tmp_path):
         assert meta["dts"] == dts
         got = np.load(tmp_path / f"slab{r}.npy")
         assert np.array_equal(got, ug[meta["z0"] * L:(meta["z0"] + meta["nz"]) * L])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_rk_stage_element_range_updates_only_its_elements(precision):
+    from paper_2312_07725_gb300 import NSFRError, Solver
+    shape, p = (2, 3, 3), 3
+    ctrl = _mesh(shape, p)
+    S = Solver(ctrl, shape, p, precision=precision)
+    u0 = torch.from_numpy(np.ascontiguousarray(wl.perturbed_tgv_state(S.node_coords()))).cuda()
+    L, dt = 6, 1e-3
+    full = [torch.empty_like(u0) for _ in range(3)]  # u, ustage, acc of the whole-mesh stages
+    full[0].copy_(u0)
+    seen = []
+    for st in range(4):
+        S.rk_stage(*full, st, dt)
+        seen.append([t.clone() for t in full])
+    b, e = L, 2 * L + 3  # a range that is not a whole layer
+    # stage 0: reads u only
+    us, acc = torch.full_like(u0, 7.0), torch.full_like(u0, 7.0)
+    u = u0.clone()
+    S.rk_stage(u, us, acc, 0, dt, elements=(b, e))
+    torch.cuda.synchronize()
+    assert torch.equal(us[b:e], seen[0][1][b:e]) and torch.equal(acc[b:e], seen[0][2][b:e])
+    assert bool((us[:b] == 7.0).all()) and bool((us[e:] == 7.0).all()) and bool((acc[e:] == 7.0).all())
+    # stage 3 from the whole-mesh stage-2 arrays: u changes inside the range only
+    u, us, acc = (t.clone() for t in seen[2])
+    S.rk_stage(u, us, acc, 3, dt, elements=(b, e))
+    torch.cuda.synchronize()
+    assert torch.equal(u[b:e], seen[3][0][b:e])
+    assert torch.equal(u[:b], seen[2][0][:b]) and torch.equal(u[e:], seen[2][0][e:])
+    # an empty range launches nothing and changes nothing
+    S.rk_stage(u, us, acc, 3, dt, elements=(4, 4))
+    torch.cuda.synchronize()
+    assert torch.equal(u[:b], seen[2][0][:b])
+    with pytest.raises(NSFRError):
+        S.rk_stage(u, us, acc, 0, dt, elements=(3, S.n_el + 1))
