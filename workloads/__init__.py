@@ -89,7 +89,9 @@ def make_warp_scaled(warp, amp):
 
 WARPS = {"none": warp_none, "tgv": warp_tgv, "unit": warp_unit,
          # the paper's Taylor-Green timing mesh: its warp with beta = 1/5 on [-pi, pi]^3
-         "paper": make_warp_paper(0.2, -math.pi, math.pi)}
+         "paper": make_warp_paper(0.2, -math.pi, math.pi),
+         # the paper's manufactured-solution mesh: its warp with beta = 1/50 on [-1, 1]^3
+         "mms": make_warp_paper(0.02, -1.0, 1.0)}
 
 
 # ---------------------------------------------------------------------------
@@ -213,6 +215,12 @@ def tgv_mesh(n_el, p, warp="tgv", p_geo=None):
     """Control points of the warped periodic Taylor-Green cube [-pi, pi]^3."""
     pg = p if p_geo is None else p_geo
     return control_points(n_el, n_el, n_el, pg, -math.pi, math.pi, WARPS[warp])
+
+
+def mms_mesh(n_el, p, warp="mms", p_geo=None):
+    """n_el^3 elements on [-1, 1]^3 (the manufactured solution's period)."""
+    pg = p if p_geo is None else p_geo
+    return control_points(n_el, n_el, n_el, pg, -1.0, 1.0, WARPS[warp])
 
 
 def unit_mesh(n_el, p, warp="unit", p_geo=None):
