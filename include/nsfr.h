@@ -63,6 +63,7 @@ typedef enum { NSFR_FLUX_CHANDRASHEKAR = 0 } nsfr_vol_flux;
 typedef enum { NSFR_FACE_EC = 0, NSFR_FACE_EC_ROE = 1, NSFR_FACE_EC_ES = 2 } nsfr_face_flux;
 typedef enum { NSFR_FP64 = 0, NSFR_FP32_BULK = 1 } nsfr_precision;
 typedef enum { NSFR_NODES_GL = 0, NSFR_NODES_LGL = 1 } nsfr_nodes;
+typedef enum { NSFR_SOURCE_NONE = 0, NSFR_SOURCE_MANUFACTURED = 1 } nsfr_source;
 
 /*
  * nsfr_setup -- build a context: 1D operators, metric terms, workspace.
@@ -184,6 +185,29 @@ nsfr_status nsfr_rk_stage(nsfr_ctx* ctx, double* u, double* ustage, double* acc,
 nsfr_status nsfr_max_wavespeed(nsfr_ctx* ctx, const double* u, double* lam, void* stream);
 
 /*
+ * nsfr_set_source -- add a volume source q(x, t) to the semi-discrete
+ * system, (M_m + K_m) du/dt = -R + W J q, i.e. du/dt = -Pi~ (W J)^{-1} Pi~^T
+ * (R - W J q) with q at the volume nodes (the source integrated like the
+ * residual's volume terms; the paper does not spell its discretisation out).
+ *   kind  NSFR_SOURCE_NONE (remove) or NSFR_SOURCE_MANUFACTURED: the source of
+ *         the manufactured solution of Sec. "Manufactured Solution
+ *         Convergence", rho = 2 + sin(pi (x+y+z-2t))/10, u = v = w = 1,
+ *         rho e = rho^2 (q derived from that definition; its periodic box is
+ *         [-1, 1]^3).
+ *   t     the context's time: nsfr_residual evaluates q at t; nsfr_rk_step
+ *         and nsfr_rk_stage use the stage times t, t + dt/2, t + dt/2, t + dt
+ *         and advance t by dt with the last stage (they advance it with or
+ *         without a source).
+ * nsfr_residual_raw returns R without the source.  Collocated contexts only
+ * (NSFR_ERR_STATE otherwise); the first call with a source allocates
+ * 40 B per volume node (NSFR_ERR_OOM).  Synchronous.
+ */
+nsfr_status nsfr_set_source(nsfr_ctx* ctx, int kind, double t);
+
+/* nsfr_get_time -- the context's time (see nsfr_set_source). */
+nsfr_status nsfr_get_time(const nsfr_ctx* ctx, double* t);
+
+/*
  * nsfr_entropy -- diagnostics of a state (synchronises; FP64 compensated sums).
  *   u    host or device, [N_e][5][n^3].
  *   out  host, 14 doubles:
@@ -261,9 +285,9 @@ nsfr_status nsfr_check(nsfr_ctx* ctx);
  * Kernel ids for nsfr_profile_read: 0 metric set-up, 1 face states (entropy
  * projection), 2 volume/hybrid/surface + WA inverse (+ RK stage), 3 maximum
  * wave speed, 4 diagnostics, 5 VJP face pass, 6 VJP volume pass, 7 VJP metric
- * pass, 8 face numerical fluxes.
+ * pass, 8 face numerical fluxes, 9 volume source.
  */
-#define NSFR_NKERNELS 9
+#define NSFR_NKERNELS 10
 
 /*
  * nsfr_profile -- on != 0: from now on record a CUDA event pair around every

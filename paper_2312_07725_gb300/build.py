@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnsfr.so")
-SOURCES = ["api.cu", "ops1d.cpp", "geometry.cu", "residual.cu", "residual_bulk.cu", "reduce.cu", "vjp.cu", "mathfn.cu", "projection.cu"]
+SOURCES = ["api.cu", "ops1d.cpp", "geometry.cu", "residual.cu", "residual_bulk.cu", "reduce.cu", "vjp.cu", "mathfn.cu", "projection.cu", "source.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

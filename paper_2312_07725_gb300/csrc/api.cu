@@ -58,7 +58,7 @@ void free_all(nsfr_ctx* c) {
   double* dbl[] = {c->ctrl, c->metric, c->J, c->invwj, c->wj, c->nfp_plus, c->xyz, c->face, c->nrec, c->fstar,
                    c->metric_s, c->nf_s, c->uq,
                    c->ustage, c->acc, c->rtmp, c->hbuf_in, c->hbuf_out, c->red,
-                   c->vjp_fown, c->vjp_fnbr, c->vjp_nfbar, c->vjp_mbar, c->vjp_jbar};
+                   c->vjp_fown, c->vjp_fnbr, c->vjp_nfbar, c->vjp_mbar, c->vjp_jbar, c->src};
   for (double* p : dbl)
     if (p) cudaFree(p);
   if (c->metric32) cudaFree(c->metric32);
@@ -101,6 +101,7 @@ cudaError_t launch_volume_any(nsfr_ctx* ctx, const double* u, double* out, int e
 }
 
 nsfr_status residual_device(nsfr_ctx* ctx, const double* u, double* out, int epi, cudaStream_t s) {
+  if (ctx->src_on && epi != EPI_RAW) CK(nsfr_launch_source(ctx, ctx->t, s), "manufactured_source_kernel");
   CK(nsfr_launch_face_states(ctx, u, s), "face_state_kernel");
   CK(nsfr_launch_face_flux(ctx, s), "face_flux_kernel");
   CK(launch_volume_any(ctx, u, out, epi, nullptr, s), "volume_kernel");
@@ -159,9 +160,12 @@ nsfr_status rk_stage_device(nsfr_ctx* ctx, double* u, double* ustage, double* ac
   rk.last = (st == 3);
   rk.a_next = (st < 3) ? a[st] : 0.0;
   rk.unext = (st == 3) ? u : ustage;
+  const double c_stage[4] = {0.0, 0.5, 0.5, 1.0};  // stage times t + c dt
+  if (ctx->src_on) CK(nsfr_launch_source(ctx, ctx->t + c_stage[st] * dt, s), "manufactured_source_kernel");
   CK(nsfr_launch_face_states(ctx, in, s), "face_state_kernel");
   CK(nsfr_launch_face_flux(ctx, s), "face_flux_kernel");
   CK(launch_volume_any(ctx, in, nullptr, EPI_RK, &rk, s), "volume_kernel(rk)");
+  if (st == 3) ctx->t += dt;
   return NSFR_OK;
 }
 
@@ -416,6 +420,8 @@ nsfr_status nsfr_vjp(nsfr_ctx* ctx, const double* u, const double* dudt_bar, dou
   if (ctx->precision != NSFR_FP64 || ctx->uncol)
     return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp needs a collocated FP64 context");
   if (ctx->face_flux != NSFR_FACE_EC) return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp supports the EC face flux");
+  if (ctx->src_on && x_bar)
+    return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp with x_bar does not differentiate a volume source");
   if (!u || !dudt_bar || !u_bar) return fail(ctx, NSFR_ERR_ARG, "NULL buffer");
   if (!is_device_ptr(u) || !is_device_ptr(dudt_bar) || !is_device_ptr(u_bar) || (x_bar && !is_device_ptr(x_bar)))
     return fail(ctx, NSFR_ERR_ARG, "nsfr_vjp takes device buffers");
@@ -438,6 +444,26 @@ nsfr_status nsfr_vjp(nsfr_ctx* ctx, const double* u, const double* dudt_bar, dou
     CK(nsfr_launch_volume(ctx, u, ctx->rtmp, EPI_RAW, nullptr, s), "volume_kernel(raw)");
   }
   CK(nsfr_launch_vjp(ctx, u, dudt_bar, u_bar, x_bar, s), "vjp kernels");
+  return NSFR_OK;
+}
+
+nsfr_status nsfr_set_source(nsfr_ctx* ctx, int kind, double t) {
+  if (!ctx) return NSFR_ERR_ARG;
+  if (kind != NSFR_SOURCE_NONE && kind != NSFR_SOURCE_MANUFACTURED)
+    return fail(ctx, NSFR_ERR_ARG, "unknown source kind");
+  if (!(t == t)) return fail(ctx, NSFR_ERR_ARG, "t is NaN");
+  if (kind != NSFR_SOURCE_NONE && ctx->uncol)
+    return fail(ctx, NSFR_ERR_STATE, "volume sources need a collocated context");
+  if (kind != NSFR_SOURCE_NONE && !ctx->src) CK(dalloc(&ctx->src, state_count(ctx)), "cudaMalloc(source)");
+  ctx->source = kind;
+  ctx->src_on = kind == NSFR_SOURCE_NONE ? nullptr : ctx->src;
+  ctx->t = t;
+  return NSFR_OK;
+}
+
+nsfr_status nsfr_get_time(const nsfr_ctx* ctx, double* t) {
+  if (!ctx || !t) return NSFR_ERR_ARG;
+  *t = ctx->t;
   return NSFR_OK;
 }
 

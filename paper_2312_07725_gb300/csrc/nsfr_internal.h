@@ -85,6 +85,12 @@ struct nsfr_ctx {
   int ns = 0, nsv = 0, uncol = 0;
   // elements [vol_b, vol_e) get the volume pass (nsfr_rk_stage's range); vol_e < 0: all
   int vol_b = 0, vol_e = -1;
+  // volume source (nsfr_set_source): kind, the time of the next stage 0 / residual,
+  // W J q at the volume nodes [ne][5][nv] (src), and src_on = src while a source is set
+  int source = 0;
+  double t = 0.0;
+  double* src = nullptr;
+  const double* src_on = nullptr;
   double c, gamma;
   int vol_flux, face_flux, precision, nodes;
   OpsGL ops;
@@ -158,6 +164,8 @@ struct RkArgs {
   int last;           // unext = acc + b dt k (final update)
 };
 cudaError_t nsfr_launch_face_states(nsfr_ctx* ctx, const double* u, cudaStream_t s);
+// W J q(t) of the context's source into ctx->src (source.cu)
+cudaError_t nsfr_launch_source(nsfr_ctx* ctx, double t, cudaStream_t s);
 // uncollocated: the entropy projection through chi and Pi (projection.cu)
 cudaError_t nsfr_launch_projection(nsfr_ctx* ctx, const double* u, cudaStream_t s);
 // uncollocated with square chi: u_q = chi u^ into ctx->uq (projection.cu)

@@ -243,7 +243,8 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
                                                                 const double* __restrict__ nf_s,
                                                                 const double* __restrict__ face,
                                                                 const double* __restrict__ fstar,
-                                                                const double* __restrict__ invwj, OpsGL ops, int nx,
+                                                                const double* __restrict__ invwj,
+                                                                const double* __restrict__ src, OpsGL ops, int nx,
                                                                 int ny, int nz, int e_beg, int ne, int epi,
                                                                 RkArgs rk, double* out, int* flag) {
   // elements e_beg .. ne-1 (the whole mesh's neighbours stay reachable)
@@ -354,7 +355,9 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
   for (int t = threadIdx.x; t < min(epb, ne - e0) * 5 * NV; t += blockDim.x) {
     const int lq = t / (5 * NV), r = t % (5 * NV);
     const double* ra = Ra + (size_t)lq * 15 * NV + r;
-    Rs[t] = (ra[0] + ra[5 * NV]) + ra[10 * NV];
+    double rv = (ra[0] + ra[5 * NV]) + ra[10 * NV];
+    if (src) rv -= src[(size_t)e0 * 5 * NV + t];  // a volume source: R - W J q
+    Rs[t] = rv;
   }
   __syncthreads();
 
@@ -447,8 +450,9 @@ cudaError_t launch_volume_n(nsfr_ctx* ctx, const double* u, double* out, int epi
   RkArgs r = rk ? *rk : RkArgs{};
   nsfr_prof_begin(ctx, 2, s);
   volume_kernel<N><<<grid, vol_threads(N), smem, s>>>(ctx->nrec, ctx->metric_s, ctx->nf_s, ctx->face,
-                                                      ctx->fstar, ctx->invwj, ctx->ops, ctx->nx, ctx->ny, ctx->nz,
-                                                      eb, ee, epi, r, out, ctx->flag);
+                                                      ctx->fstar, ctx->invwj, epi == EPI_RAW ? nullptr : ctx->src_on,
+                                                      ctx->ops, ctx->nx, ctx->ny, ctx->nz, eb, ee, epi, r, out,
+                                                      ctx->flag);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
   return cudaGetLastError();

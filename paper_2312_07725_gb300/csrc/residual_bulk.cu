@@ -140,8 +140,8 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
     volume_bulk_kernel(const double* __restrict__ nrec, const float* __restrict__ metric32,
                        const double* __restrict__ nf_s, const float* __restrict__ nf32,
                        const double* __restrict__ face, const double* __restrict__ fstar,
-                       const float* __restrict__ invwj32, OpsGL ops, int nx, int ny, int nz, int e_beg, int ne,
-                       int epi, RkArgs rk, double* out, int* flag) {
+                       const float* __restrict__ invwj32, const double* __restrict__ src, OpsGL ops, int nx,
+                       int ny, int nz, int e_beg, int ne, int epi, RkArgs rk, double* out, int* flag) {
   // elements e_beg .. ne-1 (the whole mesh's neighbours stay reachable)
   constexpr int NV = N * N * N, NFP = N * N, NL = 3 * NFP;
   extern __shared__ double sm[];
@@ -323,6 +323,11 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
     rd[2 * NV] = fma(ff_to_double(rf.u1), Rrho, f2d_i(ra[3 * NV]));
     rd[3 * NV] = fma(ff_to_double(rf.u2), Rrho, f2d_i(ra[4 * NV]));
     rd[4 * NV] = fma(rf.H + f2d_i(rf.kin), Rrho, f2d_i(ra[5 * NV]));
+    if (src) {  // a volume source: R - W J q
+      const double* q = src + ((size_t)(e0 + lq) * 5) * NV + node;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) rd[k * NV] -= q[k * NV];
+    }
   }
   __syncthreads();
   const int total = nel * 5 * NV;
@@ -383,8 +388,8 @@ cudaError_t launch_bulk_n(nsfr_ctx* ctx, const double* u, double* out, int epi, 
   nsfr_prof_begin(ctx, 2, s);
   volume_bulk_kernel<N><<<grid, bulk_threads(N), smem, s>>>(ctx->nrec, ctx->metric32, ctx->nf_s,
                                                            ctx->nfp_plus32, ctx->face, ctx->fstar, ctx->invwj32,
-                                                           ctx->ops, ctx->nx, ctx->ny, ctx->nz, eb, ee, epi, r, out,
-                                                           ctx->flag);
+                                                           epi == EPI_RAW ? nullptr : ctx->src_on, ctx->ops, ctx->nx,
+                                                           ctx->ny, ctx->nz, eb, ee, epi, r, out, ctx->flag);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
   return cudaGetLastError();

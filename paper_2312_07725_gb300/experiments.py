@@ -6,8 +6,12 @@
                 along a Taylor-Green run, FP64 or FP32-bulk
   adjoint       gradient of the kinetic energy after N RK4 steps with respect to the
                 initial state and the mesh control points (checkpointed discrete adjoint)
+  manufactured  the paper's grid study with the manufactured solution and its source
+                on the warped [-1, 1]^3 (Roe faces, CFL 0.2, t_f = 2): L2 errors of
+                density and pressure, orders
+  max_cfl       the paper's maximum-CFL study on 4^3 elements (t_f = 1)
 
-Usage: python -m paper_2312_07725_gb300.experiments convergence|tgv|adjoint [options]
+Usage: python -m paper_2312_07725_gb300.experiments convergence|tgv|adjoint|manufactured|max_cfl [options]
 Each prints one JSON document.  Inputs come from ``workloads``; everything that
 computes runs in libnsfr.so.
 """
@@ -172,9 +176,96 @@ def adjoint(n_el=16, p=4, steps=50, checkpoint=10, c=None, cfl=0.1):
     return out
 
 
+# --------------------------------------------------------------------------
+# the manufactured solution (Sec. "Manufactured Solution Convergence") and the
+# maximum CFL study (Sec. "Maximum CFL")
+# --------------------------------------------------------------------------
+def manufactured_errors(S, u, t, gamma=1.4):
+    """L2 errors of density and pressure against the manufactured solution at time t,
+    sqrt(sum (u - u_exact)^T W J (u - u_exact)) over the volume nodes."""
+    xyz = S.node_coords()
+    ex = wl.manufactured_state(xyz, t)
+    wj = S.quadrature()
+    rho = u[:, 0]
+    p = (gamma - 1.0) * (u[:, 4] - 0.5 * (u[:, 1] ** 2 + u[:, 2] ** 2 + u[:, 3] ** 2) / rho)
+    p_ex = (gamma - 1.0) * (ex[:, 4] - 1.5 * ex[:, 0])
+    return (math.sqrt(float(np.sum(wj * (rho - ex[:, 0]) ** 2))),
+            math.sqrt(float(np.sum(wj * (p - p_ex) ** 2))))
+
+
+def run_manufactured(N, p, c, tf, nodes="gl", face_flux="ec_roe", dt_fixed=None, cfl=None,
+                     precision="fp64"):
+    """Integrate the manufactured solution on the paper's warped N^3 mesh of [-1, 1]^3
+    from its exact state to t_f, with a fixed step dt_fixed or the CFL step of the
+    maximum wave speed (the last step shortened to land on t_f); returns (errors, steps)."""
+    ctrl = wl.mms_mesh(N, p)
+    S = Solver(ctrl, (N, N, N), p, c=c, face_flux=face_flux, nodes=nodes, precision=precision)
+    try:
+        S.set_source("manufactured", 0.0)
+        u = torch.from_numpy(np.ascontiguousarray(wl.manufactured_state(S.node_coords(), 0.0))).cuda()
+        dx = S.dx
+        t, steps = 0.0, 0
+        while tf - t > 1e-12 * tf:
+            dt = dt_fixed if dt_fixed is not None else cfl * dx / S.max_wavespeed(u)
+            dt = min(dt, tf - t)
+            S.rk_step(u, dt=dt)
+            t += dt
+            steps += 1
+        S.check()
+        assert abs(S.time - t) <= 1e-12 * tf
+        return manufactured_errors(S, u.cpu().numpy(), tf), steps
+    finally:
+        S.close()
+
+
+def manufactured_convergence(p, levels, c=0.0, nodes="gl", tf=2.0, cfl=0.2, face_flux="ec_roe"):
+    """The paper's grid study: the adaptive step dt = 0.2 dx / max(|u| + a) (its
+    "dt = 0.2 dx" read as CFL 0.2: a fixed 0.2 dx would be CFL 0.46 at this solution's
+    wave speed of about 2.3), dx = 2 / (N (p+1)), one period (t_f = 2); L2 errors of
+    density and pressure and the observed orders."""
+    errs, times, steps = [], [], []
+    for N in levels:
+        t0 = time.perf_counter()
+        e, k = run_manufactured(N, p, c, tf, nodes, face_flux, cfl=cfl)
+        times.append(time.perf_counter() - t0)
+        errs.append(e)
+        steps.append(k)
+    orders = [[math.log(errs[i - 1][k] / errs[i][k]) / math.log(levels[i] / levels[i - 1]) for k in (0, 1)]
+              for i in range(1, len(errs))]
+    return {"study": "manufactured", "p": p, "levels": list(levels), "c": c, "nodes": nodes, "tf": tf,
+            "cfl": cfl, "face_flux": face_flux, "steps": steps,
+            "l2_errors_rho_p": errs, "orders_rho_p": orders, "seconds": times}
+
+
+def max_cfl(p, c=0.0, nodes="gl", n_el=4, tf=1.0, cfl0=0.1, dcfl=0.01, cfl_max=1.0, digits=7):
+    """Sec. "Maximum CFL": the pressure L2 error at t_f = 1 with CFL 0.1 is the reference;
+    the CFL grows by 0.01 until the error no longer agrees with it to ``digits``
+    significant digits (|e - e_ref| > 0.5 * 10^(1 - digits) |e_ref|) or the run fails;
+    the last agreeing CFL is the maximum."""
+    from .nsfr import NSFRError
+    ref, _ = run_manufactured(n_el, p, c, tf, nodes, cfl=cfl0)
+    tol = 0.5 * 10.0 ** (1 - digits) * ref[1]
+    rows, best = [], cfl0
+    k = 1
+    while cfl0 + k * dcfl <= cfl_max + 1e-12:
+        cfl = round(cfl0 + k * dcfl, 10)
+        try:
+            e, steps = run_manufactured(n_el, p, c, tf, nodes, cfl=cfl)
+            ok = math.isfinite(e[1]) and abs(e[1] - ref[1]) <= tol
+        except NSFRError:
+            e, steps, ok = (float("nan"), float("nan")), 0, False
+        rows.append({"cfl": cfl, "pressure_error": e[1], "steps": steps, "agrees": ok})
+        if not ok:
+            break
+        best = cfl
+        k += 1
+    return {"study": "max_cfl", "p": p, "c": c, "nodes": nodes, "n_el": n_el, "tf": tf,
+            "reference_pressure_error": ref[1], "max_cfl": best, "sweep": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["convergence", "tgv", "adjoint"])
+    ap.add_argument("study", choices=["convergence", "tgv", "adjoint", "manufactured", "max_cfl"])
     ap.add_argument("--p", type=int, nargs="+", default=[2, 3, 4, 5])
     ap.add_argument("--levels", type=int, nargs="+", default=[4, 8, 16, 32])
     ap.add_argument("--c", default="both", choices=["dg", "hu", "both"])
@@ -207,6 +298,19 @@ def main():
                                            every=args.every, tf=args.tf, nodes=args.nodes,
                                            face_flux=args.face_flux or "ec", warp=args.warp))
                     print(json.dumps(out[-1]), flush=True)
+    elif args.study == "manufactured":
+        for p in args.p:
+            for ck in (["dg", "hu"] if args.c == "both" else [args.c]):
+                out.append(manufactured_convergence(p, args.levels, c=0.0 if ck == "dg" else c_hu[p],
+                                                    nodes=args.nodes, tf=args.tf or 2.0))
+                print(json.dumps(out[-1]), flush=True)
+    elif args.study == "max_cfl":
+        for p in args.p:
+            for nodes in ("gl", "lgl"):
+                for ck in (["dg", "hu"] if args.c == "both" else [args.c]):
+                    r = max_cfl(p, c=0.0 if ck == "dg" else c_hu[p], nodes=nodes, tf=args.tf or 1.0)
+                    r["c_kind"] = ck
+                    print(json.dumps(r), flush=True)
     else:
         print(json.dumps(adjoint(n_el=args.n_el, p=args.p[0], steps=args.steps)), flush=True)
 

@@ -23,14 +23,15 @@ STATUS = {0: "NSFR_OK", -1: "NSFR_ERR_ARG", -2: "NSFR_ERR_MESH", -3: "NSFR_ERR_C
 FACE_FLUX = {"ec": 0, "ec_roe": 1, "ec_es": 2}
 PRECISION = {"fp64": 0, "fp32_bulk": 1}
 NODES = {"gl": 0, "lgl": 1}
+SOURCES = {"none": 0, "manufactured": 1}
 
 # every symbol include/nsfr.h declares
 EXPORTS = ["nsfr_setup", "nsfr_setup_uncollocated", "nsfr_residual", "nsfr_residual_raw", "nsfr_rk_step", "nsfr_entropy",
-           "nsfr_rk_stage", "nsfr_max_wavespeed", "nsfr_vjp", "nsfr_node_coords", "nsfr_get_metrics", "nsfr_set_metrics", "nsfr_quadrature", "nsfr_info", "nsfr_check",
+           "nsfr_rk_stage", "nsfr_max_wavespeed", "nsfr_set_source", "nsfr_get_time", "nsfr_vjp", "nsfr_node_coords", "nsfr_get_metrics", "nsfr_set_metrics", "nsfr_quadrature", "nsfr_info", "nsfr_check",
            "nsfr_profile", "nsfr_profile_read", "nsfr_residual_static", "nsfr_math_eval", "nsfr_kernel_launches",
            "nsfr_last_error", "nsfr_destroy"]
 KERNELS = ["metrics", "face_states", "volume", "max_wavespeed", "diagnostics", "vjp_face", "vjp_volume",
-           "vjp_metrics", "face_flux"]
+           "vjp_metrics", "face_flux", "source"]
 
 
 class NSFRError(RuntimeError):
@@ -79,6 +80,10 @@ def load_library(path=LIB_PATH):
     lib.nsfr_rk_stage.restype = i
     lib.nsfr_max_wavespeed.argtypes = [vp, vp, ctypes.POINTER(d), vp]
     lib.nsfr_max_wavespeed.restype = i
+    lib.nsfr_set_source.argtypes = [vp, i, d]
+    lib.nsfr_set_source.restype = i
+    lib.nsfr_get_time.argtypes = [vp, ctypes.POINTER(d)]
+    lib.nsfr_get_time.restype = i
     lib.nsfr_math_eval.argtypes = [i, vp, vp, ctypes.c_longlong, vp]
     lib.nsfr_math_eval.restype = i
     lib.nsfr_kernel_launches.argtypes = [vp]
@@ -232,6 +237,16 @@ class Solver:
         self._check(self._lib.nsfr_max_wavespeed(self._h, _ptr(u), ctypes.byref(lam), _stream(stream)),
                     "nsfr_max_wavespeed")
         return lam.value
+
+    def set_source(self, kind="manufactured", t=0.0):
+        """Volume source ("none" or "manufactured") and the context's time (nsfr_set_source)."""
+        self._check(self._lib.nsfr_set_source(self._h, SOURCES[kind], float(t)), "nsfr_set_source")
+
+    @property
+    def time(self):
+        t = ctypes.c_double(0.0)
+        self._check(self._lib.nsfr_get_time(self._h, ctypes.byref(t)), "nsfr_get_time")
+        return t.value
 
     @property
     def dx(self):

@@ -151,6 +151,14 @@ def density_wave_state(xyz, t=0.0, gamma=GAMMA):
     return conserved_from_primitive(rho, one, one, one, one, gamma)
 
 
+def manufactured_state(xyz, t=0.0):
+    """Gassner et al.'s manufactured solution (the paper's convergence test) at
+    coordinates [N_e][3][n^3]: rho = 2 + 0.1 sin(pi(x+y+z-2t)), u=v=w=1, rho e = rho^2."""
+    x, y, z = xyz[..., 0, :], xyz[..., 1, :], xyz[..., 2, :]
+    rho = 2.0 + 0.1 * np.sin(math.pi * (x + y + z - 2.0 * t))
+    return np.stack([rho, rho, rho, rho, rho * rho], axis=-2)
+
+
 def free_stream_state(xyz, rho=1.3, vel=(0.7, -0.4, 0.25), p=2.1, gamma=GAMMA):
     x = xyz[..., 0, :]
     o = np.ones_like(x)
