@@ -42,6 +42,13 @@ struct OpsGL {
   double f4g[4];
   double fr2[4];  // 2 atanh(f)/f (for 1/rho_ln)
   double inv_gm1;
+  // the same series as FP32 corrections for the FP32-bulk kernel: with
+  // P(u) = c0 + u (c1 + u c2), G = 1 + u P_g, 2 atanh(f)/f = 2 + u P_a and
+  // F4g = 2/(gamma-1) + u P_b; cab = 2 + 2/(gamma-1) as float-float
+  float lmg[3];
+  float lma[3];
+  float lmb[3];
+  float cab_hi, cab_lo;
   // Uncollocated scheme (solution on ns Lobatto nodes, the n points above are
   // GL quadrature points, n >= ns): chi (n x ns) the solution basis at the
   // points, Pi = (chi^T W chi)^{-1} chi^T W (ns x n), ls_m / ls_p the solution

@@ -184,6 +184,16 @@ void nsfr_build_ops(int p, int p_geo, double c, double gamma, int nodes, OpsGL* 
     gl->fr2[k] = 2.0 * F[k];
   }
   gl->inv_gm1 = 1.0 / (gamma - 1.0);
+  for (int k = 0; k < 3; ++k) {
+    gl->lmg[k] = (float)G[k + 1];
+    gl->lma[k] = (float)(2.0 * F[k + 1]);
+    gl->lmb[k] = (float)(2.0 / (gamma - 1.0) * F[k + 1]);
+  }
+  {
+    const double cab = 2.0 + 2.0 / (gamma - 1.0);
+    gl->cab_hi = (float)cab;
+    gl->cab_lo = (float)(cab - (double)gl->cab_hi);
+  }
   for (int k = 0; k < n * n; ++k) {
     gl->S1f[k] = (float)gl->S1[k];
     gl->Pi1f[k] = (float)gl->Pi1[k];

@@ -3,12 +3,17 @@
 // Same discretisation as volume_kernel (Eq. NSFR with sum-factorised
 // Hadamard products, Eq. weight-adj ESFR mass, fused RK stage), with the work
 // split by precision:
-//   FP64  the logarithmic means and the two scalars formed from them (p_hat
-//         and the energy coefficient H = 1/(2(gamma-1) beta_ln) + p_hat/rho_ln),
-//         the entropy projection (the shared face-state kernel) and the state;
+//   FP64  the entropy projection (the shared face-state kernel), the state,
+//         and the logarithmic means of pairs whose values differ by more than
+//         about 3% (the log branch, with the face-state pass's logs);
+//   float-float (FP32 pairs, ~48 bits)  the scalars made from the log means
+//         -- rho_ln, p_hat = rho_bar / (2 beta_bar) and the energy coefficient
+//         H = 1/(2(gamma-1) beta_ln) + p_hat/rho_ln -- on the series branch,
+//         where each is a constant plus an O(f^2) correction that FP32 carries
+//         to ~1e-7 of itself, and the mass flux rho_ln u.n with its
+//         accumulation;
 //   FP32  the momentum and energy flux arithmetic and their accumulation, and
-//         the mass-inverse contractions;
-//   float-float (FP32 pairs)  the mass flux rho_ln u.n and its accumulation.
+//         the mass-inverse contractions.
 // The fluxes are formed as deviations from the state of the element's first
 // node (rho_ref, u_ref, p_ref): subtracting p_ref n from the momentum flux
 // leaves R unchanged (the scheme is free-stream preserving, Sec. "Free-stream
@@ -29,15 +34,15 @@ namespace {
 using namespace nsfr_k;
 
 struct BNode {
-  double r, b2;   // FP64 log-mean inputs (the logs are read when a log mean needs them)
+  ff r, b2;       // log-mean inputs rho, 2 beta (the logs are read when a log mean needs them)
   ff u0, u1, u2;  // u/2
   float qq;       // |u|^2/4
 };
 
 __device__ __forceinline__ BNode bnode_from_rec(const Rec& a) {
   BNode b;
-  b.r = a.r;
-  b.b2 = a.b2;
+  b.r = ff_from_double(a.r);
+  b.b2 = ff_from_double(a.b2);
   b.u0 = ff_from_double(a.u0);
   b.u1 = ff_from_double(a.u1);
   b.u2 = ff_from_double(a.u2);
@@ -47,39 +52,77 @@ __device__ __forceinline__ BNode bnode_from_rec(const Rec& a) {
 
 struct BRef {
   double p, H;       // p_ref, H_ref = gamma p_ref / ((gamma - 1) rho_ref)
+  ff pf, Hf;         // the same as float-float
   ff u0, u1, u2;     // u_ref
   float kin;         // |u_ref|^2 / 2
 };
 
+// 1/x as float-float for x > 0 (normal): the FP32 seed r0 and one correction
+// r0 (1 - x r0), with 1 - x r0 formed by FMAs (error ~2^-46 relative)
+__device__ __forceinline__ ff ff_rcp(ff x) {
+  float r0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(x.hi));
+  const float e = __fmaf_rn(-x.lo, r0, __fmaf_rn(-x.hi, r0, 1.0f));
+  ff r;
+  fast_two_sum(r0, __fmul_rn(r0, e), r.hi, r.lo);
+  return r;
+}
+
+// a - b for close float-float values (|a - b| << |a|): the hi difference is exact
+__device__ __forceinline__ float ff_diff(ff a, ff b) { return (a.hi - b.hi) + (a.lo - b.lo); }
+
+// c + x for a float-float constant c and a correction |x| << |c|
+__device__ __forceinline__ ff ff_add_small(ff c, float x) {
+  ff r;
+  fast_two_sum(c.hi, __fadd_rn(x, c.lo), r.hi, r.lo);
+  return r;
+}
+
+// series branch of the log means in float-float: u = f^2 below this
+#define NSFR_LM_EPS32 1.0e-3f
+
 // deviation flux of a pair: Fr (mass, float-float), Fm = F_m - u_ref F_rho - p_ref n,
 // FE = F_E - (H_ref + |u_ref|^2/2) F_rho; (n0, n1, n2) the averaged metric row.
+// With f = (a - b)/(a + b), u = f^2 for rho and for 2 beta:
+//   rho_ln = (rho_bar) G(u_r),  G = f/atanh(f) = 1 - u/3 - 4u^2/45 - 44u^3/945 - ...
+//   H s2 = p_hat s2 / rho_ln + s2 / (2 (gamma-1) beta_ln) = 2 atanh(f_r)/f_r + F4g(u_b)
+//        = (2 + 2/(gamma-1)) + u_r P_a(u_r) + u_b P_b(u_b)
+// (s2 = 2 beta_a + 2 beta_b), truncated where the next term is below 1e-13 (u < 1e-3).
 template <class LA, class LB>
 __device__ __forceinline__ void bulk_flux(const BNode& A, const BNode& B, ff n0, ff n1, ff n2, const BRef& ref,
                                           const OpsGL& K, const LA& la, const LB& lb, ff& Fr, float Fm[3],
                                           float& FE) {
-  const double sr = A.r + B.r, dr = A.r - B.r;
-  const double s2 = A.b2 + B.b2, d2 = A.b2 - B.b2;
-  const double rb2 = rcp_newton1(s2), rr = rcp_newton1(sr);
-  const double fr = dr * rr, fb = d2 * rb2;
-  const double ur = fr * fr, ub = fb * fb;
-  // H s2 = p_hat s2 / rho_ln + s2 / (2 (gamma-1) beta_ln) = a + b, with on the
-  // series paths a = 2 atanh(f_r)/f_r and b = F4g(u_b) (the sums' s2 and sr cancel)
-  double rln, a, b;
-  if (lm_small(ur)) {
-    rln = sr * horner4(K.gh, ur);
-    a = horner4(K.fr2, ur);
-  } else {
+  const ff sr = ff_add(A.r, B.r), s2 = ff_add(A.b2, B.b2);
+  const float dr = ff_diff(A.r, B.r), d2 = ff_diff(A.b2, B.b2);
+  const ff rb2 = ff_rcp(s2);
+  float rsr;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rsr) : "f"(sr.hi));
+  const float fr = dr * rsr, fb = d2 * rb2.hi;
+  const float ur = fr * fr, ub = fb * fb;
+  ff rln;
+  float cx;  // H s2 - (2 + 2/(gamma-1))
+  if (ur < NSFR_LM_EPS32) {
+    const float g = ur * fmaf(fmaf(K.lmg[2], ur, K.lmg[1]), ur, K.lmg[0]);
+    rln = ff_add_small(ff{0.5f * sr.hi, 0.5f * sr.lo}, 0.5f * sr.hi * g);
+    cx = ur * fmaf(fmaf(K.lma[2], ur, K.lma[1]), ur, K.lma[0]);
+  } else {  // FP64 with the logs of the face-state pass
+    const double srd = ff_to_double(sr), drd = ff_to_double(A.r) - ff_to_double(B.r);
     const double dl = la.lr() - lb.lr();
-    rln = dr / dl;
-    a = sr * dl / dr;
+    rln = ff_from_double(drd / dl);
+    cx = d2f_i(fma(srd, dl / drd, -2.0));
   }
-  if (lm_small(ub)) b = horner4(K.f4g, ub);
-  else b = K.inv_gm1 * (la.lb() - lb.lb()) * s2 / d2;
-  const float dp = d2f_i(fma(sr, rb2, -ref.p));
-  const float dH = d2f_i(fma(a + b, rb2, -ref.H));
+  if (ub < NSFR_LM_EPS32) {
+    cx += ub * fmaf(fmaf(K.lmb[2], ub, K.lmb[1]), ub, K.lmb[0]);
+  } else {
+    const double s2d = ff_to_double(s2), d2d = ff_to_double(A.b2) - ff_to_double(B.b2);
+    cx += d2f_i(fma(K.inv_gm1 * (la.lb() - lb.lb()), s2d / d2d, -2.0 * K.inv_gm1));
+  }
+  const ff H = ff_mul(ff_add_small(ff{K.cab_hi, K.cab_lo}, cx), rb2);
+  const float dp = ff_diff(ff_mul(sr, rb2), ref.pf);
+  const float dH = ff_diff(H, ref.Hf);
   const ff v0 = ff_add(A.u0, B.u0), v1 = ff_add(A.u1, B.u1), v2 = ff_add(A.u2, B.u2);
   const ff un = ff_add(ff_add(ff_mul(v0, n0), ff_mul(v1, n1)), ff_mul(v2, n2));
-  Fr = ff_mul(ff_from_double(rln), un);
+  Fr = ff_mul(rln, un);
   const float f = Fr.hi;
   // velocity deviations, exact to the float-float level before rounding
   const float w0 = ff_add(v0, ff_neg(ref.u0)).hi, w1 = ff_add(v1, ff_neg(ref.u1)).hi,
@@ -99,6 +142,8 @@ __device__ __forceinline__ BRef make_ref(const Rec& a, const OpsGL& ops) {
   const double ib2 = rcp_full(a.b2);
   r.p = a.r * ib2;
   r.H = ops.gamma * ops.inv_gm1 * ib2;
+  r.pf = ff_from_double(r.p);
+  r.Hf = ff_from_double(r.H);
   const ff h0 = ff_from_double(a.u0), h1 = ff_from_double(a.u1), h2 = ff_from_double(a.u2);
   r.u0 = ff{2.0f * h0.hi, 2.0f * h0.lo};
   r.u1 = ff{2.0f * h1.hi, 2.0f * h1.lo};
@@ -127,12 +172,12 @@ __device__ __forceinline__ void rank_one_sweep_f(float* X, int nel, int d, bool 
 }
 
 // shared-memory layout per element (SoA over the NV nodes)
-//   doubles: r, 2 beta                                         2 NV
+//   floats : r, 2 beta as float-float (the bytes of 2 doubles) 4 NV
 //   doubles: R (combined), epilogue                            5 NV
 //   floats : u/2 hi(3) lo(3), |u|^2/4, metric hi(9) lo(9)     25 NV
 //   floats : line sums R_rho hi, lo, R_m(3), R_E', one slab
 //            per direction                                     18 NV
-// preceded by the elements' reference states (BRef, 48 bytes each).
+// preceded by the elements' reference states (BRef, 64 bytes each).
 // The float-float metric rows (w_perp / 2 C), face rows (w_perp C_f) and
 // 1/(w J) come from bulk_tables_kernel, once per geometry.
 template <int N>
@@ -148,8 +193,8 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
   const int epb = blockDim.x / NL;
   const int e0 = e_beg + blockIdx.x * epb;
   BRef* Refs = (BRef*)sm;                          // [epb]
-  double* Pd = (double*)(Refs + epb);              // [epb][2][NV]
-  double* Rd = Pd + (size_t)epb * 2 * NV;          // [epb][5][NV]
+  float* Pd = (float*)(Refs + epb);                // [epb][4][NV]: rho, 2 beta as float-float
+  double* Rd = (double*)(Pd + (size_t)epb * 4 * NV);  // [epb][5][NV]
   float* Pf = (float*)(Rd + (size_t)epb * 5 * NV); // [epb][25][NV]
   float* Ra = Pf + (size_t)epb * 25 * NV;          // [epb][3][6][NV]
   float* Xf = Pf;                                  // epilogue (aliases Pf)
@@ -159,9 +204,12 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
     if (e >= ne) continue;
     const Rec a = load_rec6(nrec + (size_t)e * NSFR_NFIELD * NV + node, NV);  // from the face-state pass
     if (node == 0) Refs[le] = make_ref(a, ops);
-    double* pd = Pd + (size_t)le * 2 * NV + node;
-    pd[0] = a.r;
-    pd[NV] = a.b2;
+    float* pd = Pd + (size_t)le * 4 * NV + node;
+    const ff fr_ = ff_from_double(a.r), fb_ = ff_from_double(a.b2);
+    pd[0] = fr_.hi;
+    pd[NV] = fr_.lo;
+    pd[2 * NV] = fb_.hi;
+    pd[3 * NV] = fb_.lo;
     float* pf = Pf + (size_t)le * 25 * NV + node;
     const ff u0 = ff_from_double(a.u0), u1 = ff_from_double(a.u1), u2 = ff_from_double(a.u2);
     pf[0] = u0.hi;
@@ -188,15 +236,15 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
   int base, stride;
   line_geometry<N>(d, l0, l1, base, stride);
   if (le < epb && e < ne) {
-    const double* pd = Pd + (size_t)le * 2 * NV + base;
+    const float* pd = Pd + (size_t)le * 4 * NV + base;
     const float* pf = Pf + (size_t)le * 25 * NV + base;
     const double* Le = nrec + ((size_t)e * NSFR_NFIELD + P_LRHO) * NV + base;  // ln rho, ln beta (read only off the series path)
     float* Rl = Ra + ((size_t)le * 18 + 6 * d) * NV + base;
     const BRef ref = Refs[le];
     auto node_at = [&](int a) {
       BNode b;
-      b.r = pd[a * stride];
-      b.b2 = pd[NV + a * stride];
+      b.r = ff{pd[a * stride], pd[NV + a * stride]};
+      b.b2 = ff{pd[2 * NV + a * stride], pd[3 * NV + a * stride]};
       b.u0 = ff{pf[a * stride], pf[3 * NV + a * stride]};
       b.u1 = ff{pf[NV + a * stride], pf[4 * NV + a * stride]};
       b.u2 = ff{pf[2 * NV + a * stride], pf[5 * NV + a * stride]};
