@@ -47,9 +47,9 @@ import workloads as wl  # noqa: E402
 # two log means) and per accumulation of one flux into two residual entries
 FLOPS_PER_FLUX = 55
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one volume_kernel<5>
-# launch per element, from an ncu --set full capture at 24^3 elements (652.7 MB for
+# launch per element, from an ncu --set full capture at 24^3 elements (653.3 MB for
 # 13,824 elements; every buffer the kernel touches scales with the element count)
-VOLUME_DRAM_BYTES_PER_ELEMENT = {4: 652.72e6 / 13824}
+VOLUME_DRAM_BYTES_PER_ELEMENT = {4: 653.33e6 / 13824}
 FLOPS_PER_ACC = 20
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
