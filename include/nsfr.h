@@ -344,12 +344,23 @@ nsfr_status nsfr_residual_static(const double* u, const double* C, const double*
  *   NSFR_FN_EXP  exponential (table-driven, Tang's method; about one ulp)
  *   NSFR_FN_RCP  1/x, FP32 seed and one third-order step (about one ulp)
  *   NSFR_FN_RCP1 1/x, FP32 seed and one Newton step (relative error <= 2^-43)
+ *   NSFR_FN_LOG_FF, NSFR_FN_EXP_FF  the float-float log and exp of the
+ *                FP32-bulk kernels (x split into two floats, the result
+ *                summed back; about 2^-46 of max(|ln x|, 0.7), and relative
+ *                2^-46; x.hi positive and normal for the log, |x| < 87 for exp)
  * The kernels compute the entropy variables, face states and two-point
  * fluxes with these.  x and y are device buffers of n doubles (n >= 0; they
  * may alias); asynchronous on the stream.  NSFR_ERR_ARG for an unknown fn, a
  * NULL or host pointer or n < 0.  No context is needed.
  */
-typedef enum { NSFR_FN_LOG = 0, NSFR_FN_EXP = 1, NSFR_FN_RCP = 2, NSFR_FN_RCP1 = 3 } nsfr_fn;
+typedef enum {
+  NSFR_FN_LOG = 0,
+  NSFR_FN_EXP = 1,
+  NSFR_FN_RCP = 2,
+  NSFR_FN_RCP1 = 3,
+  NSFR_FN_LOG_FF = 4,
+  NSFR_FN_EXP_FF = 5
+} nsfr_fn;
 nsfr_status nsfr_math_eval(int fn, const double* x, double* y, long long n, void* stream);
 
 /* nsfr_kernel_launches -- kernels this context has launched so far. */

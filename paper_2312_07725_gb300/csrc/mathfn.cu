@@ -1,7 +1,9 @@
 // Elementwise evaluation of the library's own device elementary functions
-// (nsfr_math_eval): the FP64 log and exp of mathfn.cuh and the reciprocals of
-// physics.cuh, so that they can be checked against reference values.
+// (nsfr_math_eval): the FP64 log and exp of mathfn.cuh, the float-float ones
+// of mathfn_ff.cuh and the reciprocals of physics.cuh, so that they can be
+// checked against reference values.
 #include "mathfn.cuh"
+#include "mathfn_ff.cuh"
 #include "physics.cuh"
 
 namespace {
@@ -14,6 +16,8 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
       case NSFR_FN_LOG: r = nsfr_log(v); break;
       case NSFR_FN_EXP: r = nsfr_exp(v); break;
       case NSFR_FN_RCP: r = rcp_full(v); break;
+      case NSFR_FN_LOG_FF: r = ff_to_double(ff_log(ff_from_double(v), nsfr_global_tables_f())); break;
+      case NSFR_FN_EXP_FF: r = ff_to_double(ff_exp(ff_from_double(v), nsfr_global_tables_f())); break;
       default: r = rcp_newton1(v); break;
     }
     y[i] = r;

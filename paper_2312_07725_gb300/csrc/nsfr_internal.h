@@ -171,6 +171,9 @@ struct RkArgs {
   int last;           // unext = acc + b dt k (final update)
 };
 cudaError_t nsfr_launch_face_states(nsfr_ctx* ctx, const double* u, cudaStream_t s);
+// the same pass in float-float for FP32-bulk contexts (residual_bulk.cu); its
+// node records hold rho .. |u|^2/4 as packed float-float pairs
+cudaError_t nsfr_launch_face_states_bulk(nsfr_ctx* ctx, const double* u, cudaStream_t s);
 // W J q(t) of the context's source into ctx->src (source.cu)
 cudaError_t nsfr_launch_source(nsfr_ctx* ctx, double t, cudaStream_t s);
 // uncollocated: the entropy projection through chi and Pi (projection.cu)

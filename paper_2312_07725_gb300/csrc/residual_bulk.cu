@@ -28,6 +28,7 @@
 // is kept to ~48 bits.
 #include "ffloat.cuh"
 #include "kernel_common.cuh"
+#include "mathfn_ff.cuh"
 #include "physics.cuh"
 
 namespace {
@@ -135,16 +136,119 @@ __device__ __forceinline__ void bulk_flux(const BNode& A, const BNode& B, ff n0,
   FE = f * (dH + du2 + ref.kin - (A.qq + B.qq));
 }
 
+// a x for a power of two a (exact)
+__device__ __forceinline__ ff ff_scale(ff x, float a) { return ff{x.hi * a, x.lo * a}; }
+
+__device__ __forceinline__ float2 ff_pack(ff x) { return make_float2(x.hi, x.lo); }
+
+// K1 for FP32-bulk contexts: the entropy projection of face_state_kernel --
+// v(u) at the nodes, t_s . v along every line to both faces, u(v~) at the face
+// nodes -- in float-float arithmetic with the float-float log and exp, so that
+// it does not wait on the FP64 pipe (about 1e-14 relative in every output).
+// Node records: rho, 2 beta, u/2, |u|^2/4 as float-float pairs packed in the
+// 8-byte slots (read by volume_bulk_kernel only), ln rho and ln beta in FP64;
+// face records in FP64, as the face-flux kernel reads them.
+template <int N>
+__global__ void __launch_bounds__(threads_for(N)) face_state_bulk_kernel(const double* __restrict__ u, OpsGL ops,
+                                                                         double* __restrict__ face,
+                                                                         double* __restrict__ nrec, int ne,
+                                                                         int* flag) {
+  constexpr int NV = N * N * N, NFP = N * N, NL = 3 * NFP;
+  extern __shared__ double sm[];
+  const int epb = blockDim.x / NL;
+  const int e0 = blockIdx.x * epb;
+  ff* V = reinterpret_cast<ff*>(sm);  // [epb][5][NV] entropy variables
+  const MathTablesF T = nsfr_stage_tables_f(reinterpret_cast<float*>(V + (size_t)epb * 5 * NV));
+  const ff G = ff_from_double(ops.gamma), GM1 = ff_from_double(ops.gamma - 1.0);
+  const ff IGM1 = ff_from_double(ops.inv_gm1), LN2 = ff_from_double(0.69314718055994530942);
+  __syncthreads();
+  for (int t = threadIdx.x; t < epb * NV; t += blockDim.x) {
+    const int le = t / NV, node = t % NV, e = e0 + le;
+    if (e >= ne) continue;
+    const double* ue = u + (size_t)e * 5 * NV + node;
+    const ff r = ff_from_double(ue[0]), m0 = ff_from_double(ue[NV]), m1 = ff_from_double(ue[2 * NV]),
+             m2 = ff_from_double(ue[3 * NV]), E = ff_from_double(ue[4 * NV]);
+    const ff ir = ff_rcp(r);
+    const ff u0 = ff_mul(m0, ir), u1 = ff_mul(m1, ir), u2 = ff_mul(m2, ir);
+    const ff q2 = ff_add(ff_add(ff_mul(u0, u0), ff_mul(u1, u1)), ff_mul(u2, u2));
+    const ff p = ff_mul(ff_add(E, ff_neg(ff_mul(ff_scale(r, 0.5f), q2))), GM1);
+    if (!(r.hi > 0.0f) || !(p.hi > 0.0f)) atomicOr(flag, 1);
+    const ff b2 = ff_mul(r, ff_rcp(p));  // 2 beta = rho / p
+    const ff lr = ff_log(r, T), lp = ff_log(p, T);
+    // v0 = (gamma - s)/(gamma - 1) - beta |u|^2,  s = ln p - gamma ln rho
+    const ff gs = ff_add(ff_add(G, ff_neg(lp)), ff_mul(G, lr));
+    ff* v = V + (size_t)le * 5 * NV + node;
+    v[0] = ff_add(ff_mul(gs, IGM1), ff_neg(ff_mul(ff_scale(b2, 0.5f), q2)));
+    v[NV] = ff_mul(b2, u0);
+    v[2 * NV] = ff_mul(b2, u1);
+    v[3 * NV] = ff_mul(b2, u2);
+    v[4 * NV] = ff_neg(b2);
+    float2* rec = reinterpret_cast<float2*>(nrec + (size_t)e * NSFR_NFIELD * NV) + node;
+    rec[P_RHO * NV] = ff_pack(r);
+    rec[P_B2 * NV] = ff_pack(b2);
+    rec[P_UH * NV] = ff_pack(ff_scale(u0, 0.5f));
+    rec[(P_UH + 1) * NV] = ff_pack(ff_scale(u1, 0.5f));
+    rec[(P_UH + 2) * NV] = ff_pack(ff_scale(u2, 0.5f));
+    rec[P_QQ * NV] = ff_pack(ff_scale(q2, 0.25f));
+    double* recd = nrec + (size_t)e * NSFR_NFIELD * NV + node;
+    recd[P_LRHO * NV] = ff_to_double(lr);
+    recd[P_LBETA * NV] = ff_to_double(ff_add(ff_add(lr, ff_neg(lp)), ff_neg(LN2)));  // ln rho - ln 2p
+  }
+  __syncthreads();
+  const int le = threadIdx.x / NL, l = threadIdx.x % NL, e = e0 + le;
+  if (le >= epb || e >= ne) return;
+  const int d = l / NFP, line = l % NFP;
+  int base, stride;
+  line_geometry<N>(d, line % N, line / N, base, stride);
+  const ff* v = V + (size_t)le * 5 * NV + base;
+  ff vm[5], vp[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    ff am{0.0f, 0.0f}, ap{0.0f, 0.0f};
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      const ff x = v[k * NV + a * stride];
+      am = ff_fma(ff{ops.tmf[a], ops.tmlo[a]}, x, am);
+      ap = ff_fma(ff{ops.tpf[a], ops.tplo[a]}, x, ap);
+    }
+    vm[k] = am;
+    vp[k] = ap;
+  }
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const ff* w = s ? vp : vm;
+    if (!(w[4].hi < 0.0f)) atomicOr(flag, 1);
+    const ff b2 = ff_neg(w[4]);  // 2 beta
+    const ff ib2 = ff_rcp(b2);
+    const ff u0 = ff_mul(w[1], ib2), u1 = ff_mul(w[2], ib2), u2 = ff_mul(w[3], ib2);
+    const ff q2 = ff_add(ff_add(ff_mul(u0, u0), ff_mul(u1, u1)), ff_mul(u2, u2));
+    // s = gamma - (gamma - 1)(v0 + beta |u|^2), ln rho = -(s + ln 2 beta)/(gamma - 1)
+    const ff sent = ff_add(G, ff_neg(ff_mul(GM1, ff_add(ff_mul(ff_scale(b2, 0.5f), q2), w[0]))));
+    const ff L5 = ff_log(b2, T);
+    const ff lr = ff_neg(ff_mul(ff_add(sent, L5), IGM1));
+    Rec P;
+    P.r = ff_to_double(ff_exp(lr, T));
+    P.b2 = ff_to_double(b2);
+    P.u0 = ff_to_double(ff_scale(u0, 0.5f));
+    P.u1 = ff_to_double(ff_scale(u1, 0.5f));
+    P.u2 = ff_to_double(ff_scale(u2, 0.5f));
+    P.qq = ff_to_double(ff_scale(q2, 0.25f));
+    P.lr = ff_to_double(lr);
+    P.lb = ff_to_double(ff_add(L5, ff_neg(LN2)));
+    store_rec(face + (((size_t)e * 6 + 2 * d + s) * NSFR_NFIELD) * NFP + line, NFP, P);
+  }
+}
+
 // reference state of an element: its node 0 (u_ref from the same float-float
 // split of u/2 that the node records hold, doubled exactly)
-__device__ __forceinline__ BRef make_ref(const Rec& a, const OpsGL& ops) {
+// from the float-float fields of its node record: rho, 2 beta, u/2
+__device__ __forceinline__ BRef make_ref(ff rho, ff b2, ff h0, ff h1, ff h2, const OpsGL& ops) {
   BRef r;
-  const double ib2 = rcp_full(a.b2);
-  r.p = a.r * ib2;
+  const double ib2 = rcp_full(ff_to_double(b2));
+  r.p = ff_to_double(rho) * ib2;
   r.H = ops.gamma * ops.inv_gm1 * ib2;
   r.pf = ff_from_double(r.p);
   r.Hf = ff_from_double(r.H);
-  const ff h0 = ff_from_double(a.u0), h1 = ff_from_double(a.u1), h2 = ff_from_double(a.u2);
   r.u0 = ff{2.0f * h0.hi, 2.0f * h0.lo};
   r.u1 = ff{2.0f * h1.hi, 2.0f * h1.lo};
   r.u2 = ff{2.0f * h2.hi, 2.0f * h2.lo};
@@ -202,23 +306,25 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
   for (int t = threadIdx.x; t < epb * NV; t += blockDim.x) {
     const int le = t / NV, node = t % NV, e = e0 + le;
     if (e >= ne) continue;
-    const Rec a = load_rec6(nrec + (size_t)e * NSFR_NFIELD * NV + node, NV);  // from the face-state pass
-    if (node == 0) Refs[le] = make_ref(a, ops);
+    // the float-float fields of the node record (face_state_bulk_kernel)
+    const float2* rec = reinterpret_cast<const float2*>(nrec + (size_t)e * NSFR_NFIELD * NV) + node;
+    const float2 fr2 = rec[P_RHO * NV], fb2 = rec[P_B2 * NV], f0 = rec[P_UH * NV], f1 = rec[(P_UH + 1) * NV],
+                 f2 = rec[(P_UH + 2) * NV], fq = rec[P_QQ * NV];
+    const ff u0{f0.x, f0.y}, u1{f1.x, f1.y}, u2{f2.x, f2.y};
+    if (node == 0) Refs[le] = make_ref(ff{fr2.x, fr2.y}, ff{fb2.x, fb2.y}, u0, u1, u2, ops);
     float* pd = Pd + (size_t)le * 4 * NV + node;
-    const ff fr_ = ff_from_double(a.r), fb_ = ff_from_double(a.b2);
-    pd[0] = fr_.hi;
-    pd[NV] = fr_.lo;
-    pd[2 * NV] = fb_.hi;
-    pd[3 * NV] = fb_.lo;
+    pd[0] = fr2.x;
+    pd[NV] = fr2.y;
+    pd[2 * NV] = fb2.x;
+    pd[3 * NV] = fb2.y;
     float* pf = Pf + (size_t)le * 25 * NV + node;
-    const ff u0 = ff_from_double(a.u0), u1 = ff_from_double(a.u1), u2 = ff_from_double(a.u2);
     pf[0] = u0.hi;
     pf[NV] = u1.hi;
     pf[2 * NV] = u2.hi;
     pf[3 * NV] = u0.lo;
     pf[4 * NV] = u1.lo;
     pf[5 * NV] = u2.lo;
-    pf[6 * NV] = d2f_i(a.qq);
+    pf[6 * NV] = fq.x;
     const float* m32 = metric32 + (size_t)e * 18 * NV + node;
 #pragma unroll
     for (int r = 0; r < 18; ++r) pf[(7 + r) * NV] = m32[r * NV];
@@ -481,6 +587,36 @@ cudaError_t nsfr_launch_bulk_tables(nsfr_ctx* ctx, cudaStream_t s) {
                                              ctx->metric32, ctx->nfp_plus32, ctx->invwj32);
   ctx->launches++;
   return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_face_bulk_n(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
+  constexpr int NV = N * N * N;
+  constexpr int epb = epb_for(N);
+  const int grid = (ctx->ne + epb - 1) / epb;
+  const size_t smem = (size_t)epb * 5 * NV * sizeof(ff) + NSFR_MATH_TABLE_FLOATS * sizeof(float);
+  cudaError_t err =
+      cudaFuncSetAttribute(face_state_bulk_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  nsfr_prof_begin(ctx, 1, s);
+  face_state_bulk_kernel<N><<<grid, threads_for(N), smem, s>>>(u, ctx->ops, ctx->face, ctx->nrec, ctx->ne,
+                                                                ctx->flag);
+  nsfr_prof_end(ctx, s);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t nsfr_launch_face_states_bulk(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
+  switch (ctx->n) {
+    case 2: return launch_face_bulk_n<2>(ctx, u, s);
+    case 3: return launch_face_bulk_n<3>(ctx, u, s);
+    case 4: return launch_face_bulk_n<4>(ctx, u, s);
+    case 5: return launch_face_bulk_n<5>(ctx, u, s);
+    case 6: return launch_face_bulk_n<6>(ctx, u, s);
+    case 7: return launch_face_bulk_n<7>(ctx, u, s);
+    case 8: return launch_face_bulk_n<8>(ctx, u, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t nsfr_launch_volume_bulk(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk,

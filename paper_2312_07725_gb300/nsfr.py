@@ -142,12 +142,13 @@ def residual_static(u, C, J, Cf, shape, p, c=0.0, face_flux="ec", gamma=1.4, dud
     return dudt
 
 
-MATH_FN = {"log": 0, "exp": 1, "rcp": 2, "rcp1": 3}
+MATH_FN = {"log": 0, "exp": 1, "rcp": 2, "rcp1": 3, "log_ff": 4, "exp_ff": 5}
 
 
 def math_eval(fn, x, y=None, stream=None):
     """y = fn(x) elementwise with the library's device functions (``log``, ``exp``,
-    ``rcp``: full-precision reciprocal, ``rcp1``: one Newton step), for checking
+    ``rcp``: full-precision reciprocal, ``rcp1``: one Newton step, ``log_ff``,
+    ``exp_ff``: the float-float functions of the FP32-bulk kernels), for checking
     them; x, y contiguous float64 CUDA tensors.  Returns y."""
     import torch
     if y is None:

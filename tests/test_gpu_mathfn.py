@@ -96,3 +96,38 @@ def test_math_eval_rejects_host_buffers_and_unknown_functions():
         nsfr.math_eval("log", x.cpu(), torch.empty(4, dtype=torch.float64))
     with pytest.raises(KeyError):
         nsfr.math_eval("sin", x)
+
+
+def _ff_round(x):
+    """The float-float value the library's functions see: x split into the nearest
+    float and the nearest float of the remainder, summed back exactly."""
+    hi = x.astype(np.float32).astype(np.float64)
+    lo = (x - hi).astype(np.float32).astype(np.float64)
+    return hi + lo
+
+
+def test_float_float_log_within_2_pow_minus_44_of_libm():
+    """ff_log (FP32-bulk kernels): |y - ln x| <= 2^-44 max(|ln x|, 0.7) over the
+    float-normal range the kernels use (densities, pressures, 2 beta)."""
+    m = RNG.uniform(1.0, 2.0, 200_000)
+    k = RNG.integers(-60, 60, 200_000)
+    near1 = 1.0 + RNG.uniform(-0.02, 0.02, 100_000)
+    physical = np.concatenate([RNG.uniform(0.5, 3.0, 50_000), RNG.uniform(50.0, 100.0, 50_000),
+                               RNG.uniform(1e-3, 1e-1, 50_000)])
+    x = _ff_round(np.concatenate([np.ldexp(m, k), near1, physical, [1.0, 2.0, 0.5, 0.75]]))
+    y, _ = _eval("log_ff", x)
+    ref = np.log(x)
+    err = np.abs(y - ref) / np.maximum(np.abs(ref), 0.7)
+    assert err.max() <= 2.0 ** -44, err.max()
+    assert abs(y[-4]) < 2.0 ** -48  # ln 1: the float r^3 q term leaves ~2^-51
+
+
+def test_float_float_exp_within_2_pow_minus_44_of_libm():
+    # down to -60: below about -64 the trailing float of e^x is subnormal
+    x = _ff_round(np.concatenate([RNG.uniform(-60.0, 80.0, 200_000), RNG.uniform(-1.0, 1.0, 100_000),
+                                  [0.0, 1.0, -1.0, np.log(2.0)]]))
+    y, _ = _eval("exp_ff", x)
+    ref = np.exp(x)
+    err = np.abs(y - ref) / ref
+    assert err.max() <= 2.0 ** -44, err.max()
+    assert y[-4] == 1.0
