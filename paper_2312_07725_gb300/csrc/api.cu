@@ -254,7 +254,7 @@ static nsfr_status setup_common(const double* grid_nodes, int nx, int ny, int nz
             dalloc(&ctx->fstar, ne * 15 * nfp) == cudaSuccess && dalloc(&ctx->metric_s, ne * 9 * nv) == cudaSuccess &&
             dalloc(&ctx->nf_s, ne * 9 * nfp) == cudaSuccess &&
             dalloc(&ctx->ustage, ne * 5 * nsv) == cudaSuccess && dalloc(&ctx->acc, ne * 5 * nsv) == cudaSuccess &&
-            dalloc(&ctx->flag, 1) == cudaSuccess && dalloc(&ctx->umax, 1) == cudaSuccess &&
+            dalloc(&ctx->flag, 1) == cudaSuccess && dalloc(&ctx->umax, 2) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->flag_host, sizeof(int)) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->umax_host, sizeof(unsigned long long)) == cudaSuccess;
   if (ok && ctx->uncol && ctx->n == ctx->ns) ok = dalloc(&ctx->uq, ne * 5 * nv) == cudaSuccess;

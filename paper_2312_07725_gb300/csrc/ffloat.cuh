@@ -74,6 +74,16 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
   return r;
 }
 
+// a + b without the final renormalisation (7 instead of 10 additions): hi + lo
+// carries the same sum, but |lo| may exceed half an ulp of hi by a little.  For
+// operands of further float-float products, reciprocals and differences only,
+// not for accumulators.
+__device__ __forceinline__ ff ff_add_nn(ff a, ff b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return ff{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+}
+
 __device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
 
 __device__ __forceinline__ ff ff_mul(ff a, ff b) {

@@ -137,7 +137,7 @@ struct nsfr_ctx {
   double* red_host = nullptr; // pinned
   int* flag = nullptr;        // device error word
   int* flag_host = nullptr;   // pinned
-  unsigned long long* umax = nullptr;  // max wave speed (bit pattern)
+  unsigned long long* umax = nullptr;  // [2]: max wave speed (FP64 bit pattern), FP32 candidate bound
   unsigned long long* umax_host = nullptr;
   long long launches = 0;
   // per-launch event pairs (nsfr_profile)

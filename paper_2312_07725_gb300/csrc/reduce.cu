@@ -8,17 +8,61 @@
 // S = sum W J U(u) and the kinetic energy.  Sums are compensated (Neumaier)
 // per thread, combined with TwoSum across the block, and the per-block
 // (sum, error) pairs are finished on the host.
+#include <cfloat>
+
+#include "ffloat.cuh"
 #include "nsfr_internal.h"
 
 namespace {
 
+// The maximum is found in two passes over the state.  The first evaluates
+// |u| + a in FP32 (the state rounded to float by integer operations, so that
+// the FP64 pipe stays free) and keeps the largest value M; a node that is not
+// physical in FP32 counts as +infinity.  The second evaluates the same FP32
+// value again and, only where it reaches M (1 - 1e-4), the FP64 |u| + a, whose
+// maximum is the result: the FP32 values are within a few 1e-6 of the FP64
+// ones (up to Mach numbers in the hundreds), so the node of the FP64 maximum is
+// always among them and the result is the FP64 maximum over all nodes.  With
+// M infinite every node is evaluated in FP64 (and non-physical states are
+// flagged there).
+__device__ __forceinline__ float wavespeed32(const double* __restrict__ ue, int nv, float g) {
+  const float r = d2f_i(ue[0]), m0 = d2f_i(ue[nv]), m1 = d2f_i(ue[2 * nv]), m2 = d2f_i(ue[3 * nv]),
+              E = d2f_i(ue[4 * nv]);
+  const float q2 = (m0 * m0 + m1 * m1 + m2 * m2) / (r * r);
+  const float p = (g - 1.0f) * (E - 0.5f * r * q2);
+  const float lam = sqrtf(q2) + sqrtf(g * p / r);
+  return (r > 0.0f && p > 0.0f && lam <= FLT_MAX) ? lam : INFINITY;
+}
+
+__global__ void max_wavespeed32_kernel(const double* __restrict__ u, size_t ne, int nv, float g,
+                                       unsigned int* m32) {
+  float m = 0.0f;
+  const size_t nodes = ne * (size_t)nv;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nodes; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t e = t / nv, node = t % nv;
+    m = fmaxf(m, wavespeed32(u + e * 5 * nv + node, nv, g));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ float sm[32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = (threadIdx.x < (blockDim.x >> 5)) ? sm[threadIdx.x] : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) atomicMax(m32, __float_as_uint(m));  // non-negative floats order as integers
+  }
+}
+
 __global__ void max_wavespeed_kernel(const double* __restrict__ u, size_t ne, int nv, double gamma,
-                                     unsigned long long* out, int* flag) {
+                                     const unsigned int* __restrict__ m32, unsigned long long* out, int* flag) {
   double m = 0.0;
+  const float M = __uint_as_float(*m32);
+  const float T = (M <= FLT_MAX) ? M * (1.0f - 1.0e-4f) : 0.0f;
   const size_t nodes = ne * (size_t)nv;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nodes; t += (size_t)gridDim.x * blockDim.x) {
     const size_t e = t / nv, node = t % nv;
     const double* ue = u + e * 5 * nv + node;
+    if (!(wavespeed32(ue, nv, (float)gamma) >= T)) continue;
     const double r = ue[0], m0 = ue[nv], m1 = ue[2 * nv], m2 = ue[3 * nv], E = ue[4 * nv];
     const double q2 = (m0 * m0 + m1 * m1 + m2 * m2) / (r * r);
     const double p = (gamma - 1.0) * (E - 0.5 * r * q2);
@@ -139,15 +183,18 @@ __global__ void diagnostics_kernel(const double* __restrict__ u, const double* _
 int nsfr_diag_blocks(nsfr_ctx* ctx) { return ctx->ne < 1024 ? ctx->ne : 1024; }
 
 cudaError_t nsfr_launch_max_wavespeed(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
-  cudaError_t err = cudaMemsetAsync(ctx->umax, 0, sizeof(unsigned long long), s);
+  // umax[0]: the FP64 maximum (bit pattern), umax[1]: the FP32 candidate bound
+  cudaError_t err = cudaMemsetAsync(ctx->umax, 0, 2 * sizeof(unsigned long long), s);
   if (err != cudaSuccess) return err;
   const size_t nodes = (size_t)ctx->ne * ctx->nsv;
   int grid = (int)((nodes + 255) / 256);
   if (grid > 152 * 8) grid = 152 * 8;
+  unsigned int* m32 = reinterpret_cast<unsigned int*>(ctx->umax + 1);
   nsfr_prof_begin(ctx, 3, s);
-  max_wavespeed_kernel<<<grid, 256, 0, s>>>(u, (size_t)ctx->ne, ctx->nsv, ctx->gamma, ctx->umax, ctx->flag);
+  max_wavespeed32_kernel<<<grid, 256, 0, s>>>(u, (size_t)ctx->ne, ctx->nsv, (float)ctx->gamma, m32);
+  max_wavespeed_kernel<<<grid, 256, 0, s>>>(u, (size_t)ctx->ne, ctx->nsv, ctx->gamma, m32, ctx->umax, ctx->flag);
   nsfr_prof_end(ctx, s);
-  ctx->launches++;
+  ctx->launches += 2;
   return cudaGetLastError();
 }
 

@@ -93,7 +93,7 @@ template <class LA, class LB>
 __device__ __forceinline__ void bulk_flux(const BNode& A, const BNode& B, ff n0, ff n1, ff n2, const BRef& ref,
                                           const OpsGL& K, const LA& la, const LB& lb, ff& Fr, float Fm[3],
                                           float& FE) {
-  const ff sr = ff_add(A.r, B.r), s2 = ff_add(A.b2, B.b2);
+  const ff sr = ff_add_nn(A.r, B.r), s2 = ff_add_nn(A.b2, B.b2);
   const float dr = ff_diff(A.r, B.r), d2 = ff_diff(A.b2, B.b2);
   const ff rb2 = ff_rcp(s2);
   float rsr;
@@ -121,13 +121,13 @@ __device__ __forceinline__ void bulk_flux(const BNode& A, const BNode& B, ff n0,
   const ff H = ff_mul(ff_add_small(ff{K.cab_hi, K.cab_lo}, cx), rb2);
   const float dp = ff_diff(ff_mul(sr, rb2), ref.pf);
   const float dH = ff_diff(H, ref.Hf);
-  const ff v0 = ff_add(A.u0, B.u0), v1 = ff_add(A.u1, B.u1), v2 = ff_add(A.u2, B.u2);
-  const ff un = ff_add(ff_add(ff_mul(v0, n0), ff_mul(v1, n1)), ff_mul(v2, n2));
+  const ff v0 = ff_add_nn(A.u0, B.u0), v1 = ff_add_nn(A.u1, B.u1), v2 = ff_add_nn(A.u2, B.u2);
+  const ff un = ff_add_nn(ff_add_nn(ff_mul(v0, n0), ff_mul(v1, n1)), ff_mul(v2, n2));
   Fr = ff_mul(rln, un);
   const float f = Fr.hi;
-  // velocity deviations, exact to the float-float level before rounding
-  const float w0 = ff_add(v0, ff_neg(ref.u0)).hi, w1 = ff_add(v1, ff_neg(ref.u1)).hi,
-              w2 = ff_add(v2, ff_neg(ref.u2)).hi;
+  // velocity deviations to float accuracy (the hi difference rounded once, the lo
+  // difference added)
+  const float w0 = ff_diff(v0, ref.u0), w1 = ff_diff(v1, ref.u1), w2 = ff_diff(v2, ref.u2);
   Fm[0] = fmaf(f, w0, dp * n0.hi);
   Fm[1] = fmaf(f, w1, dp * n1.hi);
   Fm[2] = fmaf(f, w2, dp * n2.hi);
@@ -382,7 +382,8 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
         const BNode B = node_at(b);
         ff Fr;
         float Fm[3], FE;
-        bulk_flux(A, B, ff_add(na0, metric_at(b, 0)), ff_add(na1, metric_at(b, 1)), ff_add(na2, metric_at(b, 2)),
+        bulk_flux(A, B, ff_add_nn(na0, metric_at(b, 0)), ff_add_nn(na1, metric_at(b, 1)),
+                  ff_add_nn(na2, metric_at(b, 2)),
                   ref, ops, PtrLogs{Le + a * stride, NV}, PtrLogs{Le + b * stride, NV}, Fr, Fm, FE);
         const ff c{ops.S1f[a * N + b], ops.S1lo[a * N + b]};
         Rr = ff_fma(c, Fr, Rr);
@@ -433,7 +434,8 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
         const BNode A = node_at(a);
         ff Fr;
         float Fm[3], FE;
-        bulk_flux(A, Fo, ff_add(metric_at(a, 0), h0), ff_add(metric_at(a, 1), h1), ff_add(metric_at(a, 2), h2),
+        bulk_flux(A, Fo, ff_add_nn(metric_at(a, 0), h0), ff_add_nn(metric_at(a, 1), h1),
+                  ff_add_nn(metric_at(a, 2), h2),
                   ref, ops, PtrLogs{Le + a * stride, NV}, PtrLogs{fo + P_LRHO * NFP, NFP}, Fr, Fm, FE);
         const ff ta{tf[a], tl[a]};
         tr = ff_fma(ta, Fr, tr);
