@@ -1,10 +1,11 @@
 """FP32-bulk path against the FP64 oracle.
 
-The bulk path does the flux arithmetic and contractions in FP32 (mass flux in
-float-float), keeping the log means, the entropy projection, the state and the
-reductions in FP64.  Bar: relative L2 error of du/dt over all five variables
-<= 1e-5 (the target for this mode); per-variable errors are checked loosely and
-the conservation drift is reported.
+The bulk path does the flux arithmetic and contractions in FP32, the mass flux,
+the log-mean scalars and the entropy projection (with its log and exp) in
+float-float, and keeps the state, the face fluxes, the log branch of wide
+jumps and the reductions in FP64.  Bar: relative L2 error of du/dt over all five
+variables <= 1e-5 (the target for this mode); per-variable errors are checked
+loosely and the conservation drift is reported.
 """
 import numpy as np
 import pytest
@@ -35,6 +36,7 @@ CASES = [
     (5, (3, 3, 3), "hu", "ec_roe", "unit"),
     (7, (2, 2, 2), "dg", "ec", "tgv"),
     (4, (3, 1, 3), "dg", "ec_roe", "unit"),  # 9 elements: ragged last CTA
+    (3, (3, 2, 2), "hu", "ec_es", "unit"),   # entropy-variable dissipation
 ]
 
 
@@ -108,3 +110,31 @@ def test_bulk_at_full_size_sampled():
         err = rel_l2(D.cpu().numpy()[idx[inner]], Dref)
         print(f"bulk 64^3 block {corner}: rel L2 {err:.2e}")
         assert err < TOL_BULK
+
+
+@pytest.mark.parametrize("nodes", ["gl", "lgl"])
+def test_bulk_on_a_developed_taylor_green_state(nodes):
+    """The FP64 library runs the Taylor-Green vortex (4^3 elements, the paper's warp with
+    beta = 1/5, p = 4, c_DG) to t = 7, past the vortices' break-down: density varies by
+    up to 5% inside an element, so the float-float face states and log means work on
+    wide deviations and some pairs take the FP64 log branch.  The bulk du/dt on that
+    state stays within 1e-5 of the oracle's."""
+    from paper_2312_07725_gb300 import Solver
+    n_el, p = 4, 4
+    ctrl = np.ascontiguousarray(wl.tgv_mesh(n_el, p, warp="paper"))
+    S = Solver(ctrl, (n_el,) * 3, p, c=0.0, nodes=nodes)
+    u = torch.from_numpy(np.ascontiguousarray(wl.tgv_state(S.node_coords()))).cuda()
+    t = 0.0
+    while t < 7.0:
+        t += S.rk_step(u, cfl=0.1)
+    un = np.ascontiguousarray(u.cpu().numpy())
+    P = Problem(ctrl, (n_el,) * 3, p, c=0.0, nodes=nodes)
+    B = Solver(ctrl, (n_el,) * 3, p, c=0.0, nodes=nodes, precision="fp32_bulk")
+    B.set_metrics(*oracle_metrics_abi(P))
+    D = np.zeros_like(un)
+    B.residual(un, D)
+    err = rel_l2(D, P.dudt_abi(un))
+    rho = un[:, 0]
+    spread = float(np.max((rho.max(axis=1) - rho.min(axis=1)) / rho.mean(axis=1)))
+    print(f"bulk developed TGV ({nodes}): rel L2 {err:.2e}, density spread in an element up to {spread:.3f}")
+    assert spread > 0.02 and err < TOL_BULK
