@@ -69,6 +69,11 @@ void free_all(nsfr_ctx* c) {
   if (c->red_host) cudaFreeHost(c->red_host);
   if (c->flag_host) cudaFreeHost(c->flag_host);
   if (c->umax_host) cudaFreeHost(c->umax_host);
+  if (c->cev) {
+    for (int i = 0; i < 2 * NSFR_COPY_CHUNKS + 1; ++i) cudaEventDestroy(c->cev[i]);
+    delete[] c->cev;
+  }
+  if (c->cs) cudaStreamDestroy(c->cs);
   prof_free(c);
 }
 
@@ -145,9 +150,11 @@ nsfr_status max_wavespeed(nsfr_ctx* ctx, const double* u, double* lam, cudaStrea
 
 // one stage of classic RK4 on the caller's arrays: stage st reads
 // (st == 0 ? u : ustage); u_{st+1} = u^n + a_st dt k_st goes to ustage,
-// acc = u^n + sum b_st dt k_st, and the last stage writes acc + b_3 dt k_3 to u
-nsfr_status rk_stage_device(nsfr_ctx* ctx, double* u, double* ustage, double* acc, int st, double dt,
-                            cudaStream_t s) {
+// acc = u^n + sum b_st dt k_st, and the last stage writes acc + b_3 dt k_3 to u.
+// `parts` selects the launches (a host-state step interleaves them with copies):
+enum { PART_FACE_STATES = 1, PART_FACE_FLUX = 2, PART_SOURCE = 4, PART_VOLUME = 8, PART_TIME = 16, PART_ALL = 31 };
+nsfr_status rk_stage_parts(nsfr_ctx* ctx, double* u, double* ustage, double* acc, int st, double dt,
+                           cudaStream_t s, int parts) {
   const double a[3] = {0.5, 0.5, 1.0};
   const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
   const double* in = (st == 0) ? u : ustage;
@@ -161,12 +168,18 @@ nsfr_status rk_stage_device(nsfr_ctx* ctx, double* u, double* ustage, double* ac
   rk.a_next = (st < 3) ? a[st] : 0.0;
   rk.unext = (st == 3) ? u : ustage;
   const double c_stage[4] = {0.0, 0.5, 0.5, 1.0};  // stage times t + c dt
-  if (ctx->src_on) CK(nsfr_launch_source(ctx, ctx->t + c_stage[st] * dt, s), "manufactured_source_kernel");
-  CK(nsfr_launch_face_states(ctx, in, s), "face_state_kernel");
-  CK(nsfr_launch_face_flux(ctx, s), "face_flux_kernel");
-  CK(launch_volume_any(ctx, in, nullptr, EPI_RK, &rk, s), "volume_kernel(rk)");
-  if (st == 3) ctx->t += dt;
+  if ((parts & PART_SOURCE) && ctx->src_on)
+    CK(nsfr_launch_source(ctx, ctx->t + c_stage[st] * dt, s), "manufactured_source_kernel");
+  if (parts & PART_FACE_STATES) CK(nsfr_launch_face_states(ctx, in, s), "face_state_kernel");
+  if (parts & PART_FACE_FLUX) CK(nsfr_launch_face_flux(ctx, s), "face_flux_kernel");
+  if (parts & PART_VOLUME) CK(launch_volume_any(ctx, in, nullptr, EPI_RK, &rk, s), "volume_kernel(rk)");
+  if ((parts & PART_TIME) && st == 3) ctx->t += dt;
   return NSFR_OK;
+}
+
+nsfr_status rk_stage_device(nsfr_ctx* ctx, double* u, double* ustage, double* acc, int st, double dt,
+                            cudaStream_t s) {
+  return rk_stage_parts(ctx, u, ustage, acc, st, dt, s, PART_ALL);
 }
 
 nsfr_status rk_step_device(nsfr_ctx* ctx, double* u, double cfl, double dt_fixed, double* dt_used,
@@ -185,6 +198,96 @@ nsfr_status rk_step_device(nsfr_ctx* ctx, double* u, double cfl, double dt_fixed
     nsfr_status r = rk_stage_device(ctx, u, ctx->ustage, ctx->acc, st, dt, s);
     if (r != NSFR_OK) return r;
   }
+  return NSFR_OK;
+}
+
+nsfr_status ensure_copy_stream(nsfr_ctx* ctx) {
+  if (!ctx->cs) CK(cudaStreamCreateWithFlags(&ctx->cs, cudaStreamNonBlocking), "cudaStreamCreateWithFlags");
+  if (!ctx->cev) {
+    ctx->cev = new cudaEvent_t[2 * NSFR_COPY_CHUNKS + 1];
+    for (int i = 0; i < 2 * NSFR_COPY_CHUNKS + 1; ++i)
+      CK(cudaEventCreateWithFlags(&ctx->cev[i], cudaEventDisableTiming), "cudaEventCreateWithFlags");
+  }
+  return NSFR_OK;
+}
+
+// An RK4 step of a host state (collocated contexts): the state goes to the device
+// in z-chunks on a copy stream, and each chunk's face states (and FP32 wave-speed
+// candidates) run as soon as it has arrived, neither needing dt; after the CFL
+// step, stages 0 .. 2 run whole, and stage 3's volume pass runs chunk by chunk,
+// each chunk copied back while the next is computed.  Same results as copy in,
+// rk_step_device, copy out.
+nsfr_status rk_step_host(nsfr_ctx* ctx, double* uh, double cfl, double dt_fixed, double* dt_used,
+                         cudaStream_t s) {
+  nsfr_status st = ensure_host_buffers(ctx);
+  if (st != NSFR_OK) return st;
+  st = ensure_copy_stream(ctx);
+  if (st != NSFR_OK) return st;
+  const bool need_lam = !(dt_fixed > 0.0);
+  if (need_lam && !(cfl > 0.0)) return fail(ctx, NSFR_ERR_ARG, "need cfl > 0 or dt_fixed > 0");
+  const int L = ctx->nx * ctx->ny, nzc = ctx->nz < NSFR_COPY_CHUNKS ? ctx->nz : NSFR_COPY_CHUNKS;
+  int cb[NSFR_COPY_CHUNKS + 1];
+  for (int j = 0; j <= nzc; ++j) cb[j] = L * (int)(((long long)ctx->nz * j) / nzc);
+  const size_t per = (size_t)5 * ctx->nsv;  // doubles per element
+  double* ud = ctx->hbuf_in;
+  cudaStream_t cs = ctx->cs;
+  cudaEvent_t* ev_in = ctx->cev;
+  cudaEvent_t* ev_out = ctx->cev + NSFR_COPY_CHUNKS;
+  cudaEvent_t ev_start = ctx->cev[2 * NSFR_COPY_CHUNKS];
+  // the copies start after the work already queued on the caller's stream
+  CK(cudaEventRecord(ev_start, s), "cudaEventRecord");
+  CK(cudaStreamWaitEvent(cs, ev_start, 0), "cudaStreamWaitEvent");
+  for (int j = 0; j < nzc; ++j) {
+    CK(cudaMemcpyAsync(ud + cb[j] * per, uh + cb[j] * per, (size_t)(cb[j + 1] - cb[j]) * per * sizeof(double),
+                       cudaMemcpyHostToDevice, cs),
+       "cudaMemcpyAsync(H2D)");
+    CK(cudaEventRecord(ev_in[j], cs), "cudaEventRecord");
+  }
+  if (need_lam) CK(nsfr_wavespeed_begin(ctx, s), "cudaMemsetAsync(max)");
+  for (int j = 0; j < nzc; ++j) {
+    CK(cudaStreamWaitEvent(s, ev_in[j], 0), "cudaStreamWaitEvent");
+    ctx->fs_b = cb[j];
+    ctx->fs_e = cb[j + 1];
+    const cudaError_t err = nsfr_launch_face_states(ctx, ud, s);
+    ctx->fs_b = 0;
+    ctx->fs_e = -1;
+    CK(err, "face_state_kernel");
+    if (need_lam) CK(nsfr_wavespeed_candidates(ctx, ud, cb[j], cb[j + 1], s), "max_wavespeed32_kernel");
+  }
+  double dt = dt_fixed;
+  if (need_lam) {
+    CK(nsfr_wavespeed_finish(ctx, ud, s), "max_wavespeed_kernel");
+    CK(cudaMemcpyAsync(ctx->umax_host, ctx->umax, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s),
+       "cudaMemcpyAsync(max)");
+    st = read_flag(ctx, s);  // synchronises
+    if (st != NSFR_OK) return st;
+    double lam;
+    std::memcpy(&lam, ctx->umax_host, sizeof(double));
+    if (!(lam > 0.0)) return fail(ctx, NSFR_ERR_NONPHYSICAL, "zero or invalid wave speed");
+    dt = cfl * ctx->dx / lam;
+  }
+  if (dt_used) *dt_used = dt;
+  st = rk_stage_parts(ctx, ud, ctx->ustage, ctx->acc, 0, dt, s, PART_ALL & ~PART_FACE_STATES);
+  for (int k = 1; k < 3 && st == NSFR_OK; ++k) st = rk_stage_device(ctx, ud, ctx->ustage, ctx->acc, k, dt, s);
+  if (st == NSFR_OK)
+    st = rk_stage_parts(ctx, ud, ctx->ustage, ctx->acc, 3, dt, s, PART_SOURCE | PART_FACE_STATES | PART_FACE_FLUX);
+  if (st != NSFR_OK) return st;
+  for (int j = 0; j < nzc; ++j) {
+    ctx->vol_b = cb[j];
+    ctx->vol_e = cb[j + 1];
+    st = rk_stage_parts(ctx, ud, ctx->ustage, ctx->acc, 3, dt, s, PART_VOLUME);
+    ctx->vol_b = 0;
+    ctx->vol_e = -1;
+    if (st != NSFR_OK) return st;
+    CK(cudaEventRecord(ev_out[j], s), "cudaEventRecord");
+    CK(cudaStreamWaitEvent(cs, ev_out[j], 0), "cudaStreamWaitEvent");
+    CK(cudaMemcpyAsync(uh + cb[j] * per, ud + cb[j] * per, (size_t)(cb[j + 1] - cb[j]) * per * sizeof(double),
+                       cudaMemcpyDeviceToHost, cs),
+       "cudaMemcpyAsync(D2H)");
+  }
+  ctx->t += dt;
+  CK(cudaStreamSynchronize(cs), "cudaStreamSynchronize");
+  CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
   return NSFR_OK;
 }
 
@@ -327,6 +430,7 @@ nsfr_status nsfr_rk_step(nsfr_ctx* ctx, double* u, double cfl, double dt_fixed, 
   cudaStream_t s = (cudaStream_t)stream;
   ctx->last_stream = s;
   if (is_device_ptr(u)) return rk_step_device(ctx, u, cfl, dt_fixed, dt_used, s);
+  if (!ctx->uncol) return rk_step_host(ctx, u, cfl, dt_fixed, dt_used, s);
   nsfr_status st = ensure_host_buffers(ctx);
   if (st != NSFR_OK) return st;
   const size_t bytes = state_count(ctx) * sizeof(double);

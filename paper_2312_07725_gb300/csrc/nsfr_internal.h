@@ -9,6 +9,7 @@
 
 #define NSFR_MAXN 8   // n = p+1 <= 8
 #define NSFR_NFIELD 8 // per-node primitive record, see Prim below
+#define NSFR_COPY_CHUNKS 8  // z-chunks of a host-state RK step (copies overlapped with kernels)
 
 // 1D operators of the collocated GL basis, passed to kernels by value (they
 // land in the constant bank).  Row-major n x n matrices.
@@ -90,8 +91,13 @@ struct nsfr_ctx {
   // for the collocated schemes).  The state and the RK arrays have nsv nodes.
   int nx, ny, nz, ne, p, n, pg, q, nv, nfp;
   int ns = 0, nsv = 0, uncol = 0;
-  // elements [vol_b, vol_e) get the volume pass (nsfr_rk_stage's range); vol_e < 0: all
+  // elements [vol_b, vol_e) get the volume pass (nsfr_rk_stage's range), elements
+  // [fs_b, fs_e) the face-state pass; an end < 0 means all
   int vol_b = 0, vol_e = -1;
+  int fs_b = 0, fs_e = -1;
+  // host-state RK steps: a copy stream and its events (created on first use)
+  cudaStream_t cs = nullptr;
+  cudaEvent_t* cev = nullptr;  // [2 NSFR_COPY_CHUNKS + 1]
   // volume source (nsfr_set_source): kind, the time of the next stage 0 / residual,
   // W J q at the volume nodes [ne][5][nv] (src), and src_on = src while a source is set
   int source = 0;
@@ -196,6 +202,10 @@ cudaError_t nsfr_launch_metrics(nsfr_ctx* ctx, cudaStream_t s);
 cudaError_t nsfr_launch_jacobian_derived(nsfr_ctx* ctx, cudaStream_t s);
 // reduce.cu
 cudaError_t nsfr_launch_max_wavespeed(nsfr_ctx* ctx, const double* u, cudaStream_t s);
+// the same in pieces (reduce.cu): clear, FP32 candidates over elements [e_b, e_e), FP64 pass
+cudaError_t nsfr_wavespeed_begin(nsfr_ctx* ctx, cudaStream_t s);
+cudaError_t nsfr_wavespeed_candidates(nsfr_ctx* ctx, const double* u, int e_b, int e_e, cudaStream_t s);
+cudaError_t nsfr_wavespeed_finish(nsfr_ctx* ctx, const double* u, cudaStream_t s);
 cudaError_t nsfr_launch_diagnostics(nsfr_ctx* ctx, const double* u, const double* R, double* partial,
                                     int nblocks, cudaStream_t s);
 int nsfr_diag_blocks(nsfr_ctx* ctx);

@@ -182,20 +182,45 @@ __global__ void diagnostics_kernel(const double* __restrict__ u, const double* _
 
 int nsfr_diag_blocks(nsfr_ctx* ctx) { return ctx->ne < 1024 ? ctx->ne : 1024; }
 
-cudaError_t nsfr_launch_max_wavespeed(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
+// the two passes of the wave-speed maximum, callable piecewise: begin clears the
+// results, candidates runs the FP32 pass over elements [e_b, e_e) (any number of
+// calls covering the mesh), finish runs the FP64 pass over the whole state
+cudaError_t nsfr_wavespeed_begin(nsfr_ctx* ctx, cudaStream_t s) {
   // umax[0]: the FP64 maximum (bit pattern), umax[1]: the FP32 candidate bound
-  cudaError_t err = cudaMemsetAsync(ctx->umax, 0, 2 * sizeof(unsigned long long), s);
-  if (err != cudaSuccess) return err;
-  const size_t nodes = (size_t)ctx->ne * ctx->nsv;
-  int grid = (int)((nodes + 255) / 256);
-  if (grid > 152 * 8) grid = 152 * 8;
+  return cudaMemsetAsync(ctx->umax, 0, 2 * sizeof(unsigned long long), s);
+}
+
+static int wavespeed_grid(size_t nodes) {
+  const size_t g = (nodes + 255) / 256;
+  return g > 152 * 8 ? 152 * 8 : (int)g;
+}
+
+cudaError_t nsfr_wavespeed_candidates(nsfr_ctx* ctx, const double* u, int e_b, int e_e, cudaStream_t s) {
+  if (e_e <= e_b) return cudaSuccess;
   unsigned int* m32 = reinterpret_cast<unsigned int*>(ctx->umax + 1);
   nsfr_prof_begin(ctx, 3, s);
-  max_wavespeed32_kernel<<<grid, 256, 0, s>>>(u, (size_t)ctx->ne, ctx->nsv, (float)ctx->gamma, m32);
-  max_wavespeed_kernel<<<grid, 256, 0, s>>>(u, (size_t)ctx->ne, ctx->nsv, ctx->gamma, m32, ctx->umax, ctx->flag);
+  max_wavespeed32_kernel<<<wavespeed_grid((size_t)(e_e - e_b) * ctx->nsv), 256, 0, s>>>(
+      u + (size_t)e_b * 5 * ctx->nsv, (size_t)(e_e - e_b), ctx->nsv, (float)ctx->gamma, m32);
   nsfr_prof_end(ctx, s);
-  ctx->launches += 2;
+  ctx->launches++;
   return cudaGetLastError();
+}
+
+cudaError_t nsfr_wavespeed_finish(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
+  const unsigned int* m32 = reinterpret_cast<const unsigned int*>(ctx->umax + 1);
+  nsfr_prof_begin(ctx, 3, s);
+  max_wavespeed_kernel<<<wavespeed_grid((size_t)ctx->ne * ctx->nsv), 256, 0, s>>>(
+      u, (size_t)ctx->ne, ctx->nsv, ctx->gamma, m32, ctx->umax, ctx->flag);
+  nsfr_prof_end(ctx, s);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t nsfr_launch_max_wavespeed(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
+  cudaError_t err = nsfr_wavespeed_begin(ctx, s);
+  if (err == cudaSuccess) err = nsfr_wavespeed_candidates(ctx, u, 0, ctx->ne, s);
+  if (err == cudaSuccess) err = nsfr_wavespeed_finish(ctx, u, s);
+  return err;
 }
 
 cudaError_t nsfr_launch_diagnostics(nsfr_ctx* ctx, const double* u, const double* R, double* partial, int nblocks,

@@ -593,16 +593,19 @@ cudaError_t nsfr_launch_bulk_tables(nsfr_ctx* ctx, cudaStream_t s) {
 
 template <int N>
 cudaError_t launch_face_bulk_n(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
-  constexpr int NV = N * N * N;
+  constexpr int NV = N * N * N, NFP = N * N;
   constexpr int epb = epb_for(N);
-  const int grid = (ctx->ne + epb - 1) / epb;
+  const int eb = ctx->fs_b, ee = ctx->fs_e < 0 ? ctx->ne : ctx->fs_e;  // as launch_face_n
+  const int grid = (ee - eb + epb - 1) / epb;
+  if (grid <= 0) return cudaSuccess;
   const size_t smem = (size_t)epb * 5 * NV * sizeof(ff) + NSFR_MATH_TABLE_FLOATS * sizeof(float);
   cudaError_t err =
       cudaFuncSetAttribute(face_state_bulk_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   nsfr_prof_begin(ctx, 1, s);
-  face_state_bulk_kernel<N><<<grid, threads_for(N), smem, s>>>(u, ctx->ops, ctx->face, ctx->nrec, ctx->ne,
-                                                                ctx->flag);
+  face_state_bulk_kernel<N><<<grid, threads_for(N), smem, s>>>(
+      u + (size_t)eb * 5 * NV, ctx->ops, ctx->face + (size_t)eb * 6 * NSFR_NFIELD * NFP,
+      ctx->nrec + (size_t)eb * NSFR_NFIELD * NV, ee - eb, ctx->flag);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
   return cudaGetLastError();

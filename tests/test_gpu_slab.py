@@ -1,4 +1,5 @@
-"""The z-slab decomposition on the GPU against the undecomposed solver.
+"""The z-slab decomposition on the GPU against the undecomposed solver, and the host-state
+RK step (copies in z-chunks overlapped with kernels) against the device-state one.
 
 A periodic block cut into ws slabs, each with one ghost element layer on either
 side filled by the halo exchange before every RK stage, must reproduce the
@@ -167,3 +168,51 @@ def test_rk_stage_element_range_updates_only_its_elements(precision):
     assert torch.equal(u[:b], seen[2][0][:b])
     with pytest.raises(NSFRError):
         S.rk_stage(u, us, acc, 0, dt, elements=(3, S.n_el + 1))
+
+
+@pytest.mark.parametrize("shape,p,kw", [
+    ((2, 3, 11), 3, {}),                                  # 11 layers in 8 copy chunks
+    ((3, 2, 5), 4, {"precision": "fp32_bulk"}),
+    ((2, 2, 3), 2, {"face_flux": "ec_roe", "nodes": "lgl"}),
+    ((2, 2, 9), 3, {"c": 1e-3, "source": True}),
+])
+def test_host_state_step_equals_device_state_step(shape, p, kw):
+    """nsfr_rk_step on a host state copies it in z-chunks overlapped with the face-state
+    pass and copies stage 3's chunks back while the next is computed: the result, the
+    CFL step and the context's time equal those of the step on a device state."""
+    from paper_2312_07725_gb300 import Solver
+    kw = dict(kw)
+    source = kw.pop("source", False)
+    ctrl = (np.ascontiguousarray(wl.control_points(*shape, p, -1.0, 1.0, wl.WARPS["mms"])) if source
+            else _mesh(shape, p))
+    A = Solver(ctrl, shape, p, **kw)
+    B = Solver(ctrl, shape, p, **kw)
+    xs = A.node_coords()
+    u0 = np.ascontiguousarray(wl.manufactured_state(xs, 0.0) if source else wl.perturbed_tgv_state(xs))
+    if source:
+        A.set_source("manufactured", 0.0)
+        B.set_source("manufactured", 0.0)
+    ud = torch.from_numpy(u0.copy()).cuda()
+    uh = torch.from_numpy(u0.copy()).pin_memory()
+    for k in range(3):
+        if k < 2:
+            da, db = A.rk_step(ud, cfl=0.1), B.rk_step(uh.numpy(), cfl=0.1)
+        else:
+            da, db = A.rk_step(ud, dt=1e-3), B.rk_step(uh.numpy(), dt=1e-3)
+        assert da == db
+    torch.cuda.synchronize()
+    assert np.array_equal(ud.cpu().numpy(), uh.numpy())
+    assert A.time == B.time
+    # a pageable numpy state takes the same path
+    un = u0.copy()
+    A2 = Solver(ctrl, shape, p, **kw)
+    if source:
+        A2.set_source("manufactured", 0.0)
+    A2.rk_step(un, cfl=0.1)
+    ud2 = torch.from_numpy(u0.copy()).cuda()
+    B2 = Solver(ctrl, shape, p, **kw)
+    if source:
+        B2.set_source("manufactured", 0.0)
+    B2.rk_step(ud2, cfl=0.1)
+    torch.cuda.synchronize()
+    assert np.array_equal(un, ud2.cpu().numpy())
