@@ -87,9 +87,13 @@ typedef enum { NSFR_SOURCE_NONE = 0, NSFR_SOURCE_MANUFACTURED = 1 } nsfr_source;
  *               so that every face dissipates entropy).
  *   gamma       ratio of specific heats (> 1).
  *   precision   NSFR_FP64, or NSFR_FP32_BULK: flux differencing and operator
- *               contractions in FP32 with FP32 accumulation; log means,
- *               entropy variables, the entropy projection and all
- *               reductions stay FP64 (the state itself is always FP64).
+ *               contractions in FP32 with FP32 accumulation (fluxes as
+ *               deviations from each element's first node); the mass flux,
+ *               the log-mean scalars (rho_ln, p_hat, H) and the entropy
+ *               projection in float-float (pairs of floats, ~48 bits, with
+ *               float-float log and exp); the state, the face fluxes, log
+ *               means across jumps wider than ~3% and all reductions stay
+ *               FP64.  du/dt within about 1e-5 of the FP64 path.
  *   nodes       the collocated solution / volume quadrature nodes:
  *               NSFR_NODES_GL (Gauss-Legendre; the state lives at the GL
  *               nodes) or NSFR_NODES_LGL (Gauss-Lobatto-Legendre, the paper's
