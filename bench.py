@@ -20,7 +20,7 @@ the boundary layers before every stage; at N = 1 the slab exchanges with
 itself, which measures the ghost-layer and exchange overhead on one GPU.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                        [--precision fp64|fp32_bulk] [--n-el E] [--p P] [--nq Q]
+                        [--modes both|fp64] [--n-el E] [--p P] [--nq Q]
                         [--decomp replicas|slab]
 """
 from __future__ import annotations
@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=6)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
+    ap.add_argument("--modes", default="both", choices=["both", "fp64"],
+                    help="both: the FP64 line plus the fp32_bulk object; fp64: skip the bulk measurement")
     ap.add_argument("--n-el", type=int, default=64)
     ap.add_argument("--p", type=int, default=4)
     ap.add_argument("--cfl", type=float, default=0.1)
@@ -403,7 +404,7 @@ def run_ours(args, rank, ws, dist):
     m64 = measure(args, ctrl, u0, "fp64", dist, rank, ws, args.steps)
     d64 = m64.pop("dudt")
     m32 = None
-    if args.nq is None:  # the FP32-bulk form exists for the collocated scheme
+    if args.nq is None and args.modes == "both":  # the FP32-bulk form exists for the collocated scheme
         m32 = measure(args, ctrl, u0, "fp32_bulk", dist, rank, ws, args.steps)
         d32 = m32.pop("dudt")
         bulk_err = float(np.linalg.norm((d32 - d64).ravel()) / np.linalg.norm(d64.ravel()))
