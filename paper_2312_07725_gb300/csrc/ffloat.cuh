@@ -8,8 +8,6 @@ struct ff {
   float hi, lo;
 };
 
-__device__ __forceinline__ ff ff_make(float h) { return ff{h, 0.0f}; }
-
 // FP64 <-> FP32 conversions with integer operations.  The hardware
 // conversions execute on the FP64 pipe, which bounds every residual kernel on
 // this part; these use the integer pipe.  IEEE-754 binary64 -> binary32 drops

@@ -24,8 +24,6 @@ struct OpsGL {
   double Pi1[NSFR_MAXN * NSFR_MAXN];  // (W + K1)^{-1} W
   double Pinv1[NSFR_MAXN * NSFR_MAXN];  // Pi1^{-1} = I + W^{-1} K1
   float S1f[NSFR_MAXN * NSFR_MAXN];
-  float Pi1f[NSFR_MAXN * NSFR_MAXN];
-  float wf[NSFR_MAXN];
   float tmf[NSFR_MAXN];
   float tpf[NSFR_MAXN];
   // low parts: S1 = S1f + S1lo, t = tf + tlo as float-float constants
@@ -41,7 +39,6 @@ struct OpsGL {
   //   Gh(u) = G(u)/2 with G = f/atanh(f), F4g(u) = 2/(gamma-1) atanh(f)/f, u = f^2
   double gh[4];
   double f4g[4];
-  double fr2[4];  // 2 atanh(f)/f (for 1/rho_ln)
   double inv_gm1;
   // the same series as FP32 corrections for the FP32-bulk kernel: with
   // P(u) = c0 + u (c1 + u c2), G = 1 + u P_g, 2 atanh(f)/f = 2 + u P_a and

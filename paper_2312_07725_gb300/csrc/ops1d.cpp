@@ -181,7 +181,6 @@ void nsfr_build_ops(int p, int p_geo, double c, double gamma, int nodes, OpsGL* 
   for (int k = 0; k < 4; ++k) {
     gl->gh[k] = 0.5 * G[k];
     gl->f4g[k] = 2.0 / (gamma - 1.0) * F[k];
-    gl->fr2[k] = 2.0 * F[k];
   }
   gl->inv_gm1 = 1.0 / (gamma - 1.0);
   for (int k = 0; k < 3; ++k) {
@@ -196,10 +195,8 @@ void nsfr_build_ops(int p, int p_geo, double c, double gamma, int nodes, OpsGL* 
   }
   for (int k = 0; k < n * n; ++k) {
     gl->S1f[k] = (float)gl->S1[k];
-    gl->Pi1f[k] = (float)gl->Pi1[k];
   }
   for (int j = 0; j < n; ++j) {
-    gl->wf[j] = (float)gl->w[j];
     gl->tmf[j] = (float)gl->tm[j];
     gl->tpf[j] = (float)gl->tp[j];
     gl->tmlo[j] = (float)(gl->tm[j] - (double)gl->tmf[j]);
