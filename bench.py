@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--cfl", type=float, default=0.1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the VJP and diagnostics timings")
     ap.add_argument("--decomp", default="replicas", choices=["replicas", "slab"],
                     help="replicas: every rank steps its own copy of the mesh; slab: the ranks "
                          "hold the z-slabs of ws stacked copies (halo exchange every stage)")
@@ -390,6 +391,50 @@ def measure(args, ctrl, u0, precision, dist, rank, ws, steps):
     return res
 
 
+def measure_adjoint(args, ctrl, u0, residual_ms):
+    """The hand-written VJP of du/dt (nsfr_vjp: with respect to the state, and to the
+    state and the grid control points) and the diagnostics (nsfr_entropy) on the same
+    workload, FP64, device-timed with CUDA events on the launching stream."""
+    import torch
+    from paper_2312_07725_gb300 import Solver
+    N, p = args.n_el, args.p
+    S = Solver(ctrl, (N, N, N), p, c=c_value(p), face_flux="ec")
+    u = torch.from_numpy(u0).cuda()
+    dbar = torch.from_numpy(np.ascontiguousarray(wl.random_cotangent(u0.shape))).cuda()
+    ubar = torch.zeros_like(u)
+    xbar = torch.zeros((S.n_el, (S.p_geo + 1) ** 3, 3), dtype=torch.float64, device="cuda")
+    for _ in range(2):  # the first call allocates the VJP scratch
+        S.vjp(u, dbar, ubar, xbar)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, k=3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    S.profile(True)
+    t_full = timed(lambda: S.vjp(u, dbar, ubar, xbar))
+    S.profile(False)
+    prof = S.profile_read()
+    t_state = timed(lambda: S.vjp(u, dbar, ubar))
+    t_diag = timed(lambda: S.entropy(u))  # synchronises: includes the host-side finish
+    nodes = N ** 3 * (p + 1) ** 3
+    kern = {k: {"ms_total": v[0], "launches": v[1], "ms_avg": v[0] / v[1]} for k, v in prof.items()}
+    S.close()
+    del u, dbar, ubar, xbar
+    torch.cuda.empty_cache()
+    return {"vjp_state_and_grid": {"ms": t_full, "gdof_per_s": nodes / (t_full / 1e3) / 1e9},
+            "vjp_state": {"ms": t_state, "gdof_per_s": nodes / (t_state / 1e3) / 1e9},
+            "ratio_to_residual": t_full / residual_ms, "kernels": kern,
+            "diagnostics": {"ms": t_diag, "gdof_per_s": nodes / (t_diag / 1e3) / 1e9}}
+
+
 def run_ours(args, rank, ws, dist):
     cfg = workload_config(args, ws)
     p, N = args.p, args.n_el
@@ -410,6 +455,10 @@ def run_ours(args, rank, ws, dist):
         bulk_err = float(np.linalg.norm((d32 - d64).ravel()) / np.linalg.norm(d64.ravel()))
         del d32
     del d64
+
+    adj = None
+    if args.nq is None and not args.no_adjoint and args.decomp == "replicas":
+        adj = measure_adjoint(args, ctrl, u0, m64["residual_only"]["ms_per_evaluation"])
 
     clk = m64["clocks"]
     vol_ms, vol_n = m64["kernels"]["volume"]["ms_total"], m64["kernels"]["volume"]["launches"]
@@ -437,6 +486,7 @@ def run_ours(args, rank, ws, dist):
                         "d2h_bytes_per_step": m64["e2e_bytes"]},
                 "gpu_launches": m64["gpu_launches"], "kernels": m64["kernels"], "roofline": roof, "clocks": clk,
                 "residual_only": m64["residual_only"],
+                "adjoint": adj,
                 "cpu_baseline": cpu,
                 "fp32_bulk": None if m32 is None else
                 {"value": m32["value"], "unit": "GDOF/s", "ms_per_step": m32["ms_per_step"],

@@ -28,15 +28,19 @@ struct PR {
 
 // log mean L(a, b) and its partial derivatives (series branch: L = (a+b) G(u)/2,
 // u = f^2, f = (a-b)/(a+b), G = f/atanh f; otherwise (a-b)/(ln a - ln b))
+// (reciprocals by an FP32 seed and a third-order step, rcp_full: a division
+// costs several times as many FP64-pipe operations)
 __device__ __forceinline__ void logmean_grad(double a, double b, double& L, double& La, double& Lb) {
   const double s = a + b, d = a - b;
-  const double f = d / s, u = f * f;
+  const double is = rcp_full(s);
+  const double f = d * is, u = f * f;
   if (u < NSFR_LM_EPS) {
     const double G = 1.0 + u * (-1.0 / 3.0 + u * (-4.0 / 45.0 + u * (-44.0 / 945.0)));
     const double Gp = -1.0 / 3.0 + u * (-8.0 / 45.0 + u * (-132.0 / 945.0));
+    const double g2 = 2.0 * Gp * f * is;
     L = 0.5 * s * G;
-    La = 0.5 * G + 2.0 * Gp * f * b / s;
-    Lb = 0.5 * G - 2.0 * Gp * f * a / s;
+    La = 0.5 * G + g2 * b;
+    Lb = 0.5 * G - g2 * a;
   } else {
     const double D = log(a) - log(b);
     L = d / D;
@@ -46,7 +50,7 @@ __device__ __forceinline__ void logmean_grad(double a, double b, double& L, doub
 }
 
 // reverse of F = f_s(A, B) . n (Chandrashekar): accumulates into Ab, Bb, nb
-__device__ __forceinline__ void ec_flux_vjp(const PR& A, const PR& B, double n0, double n1, double n2, double gamma,
+__device__ __forceinline__ void ec_flux_vjp(const PR& A, const PR& B, double n0, double n1, double n2, double igm1,
                                             const double Fb[5], PR& Ab, PR& Bb, double nb[3]) {
   double rl, rla, rlb, bl, bla, blb;
   logmean_grad(A.r, B.r, rl, rla, rlb);
@@ -55,12 +59,14 @@ __device__ __forceinline__ void ec_flux_vjp(const PR& A, const PR& B, double n0,
   const double v[3] = {0.5 * (A.u0 + B.u0), 0.5 * (A.u1 + B.u1), 0.5 * (A.u2 + B.u2)};
   const double n[3] = {n0, n1, n2};
   const double q2b = 0.5 * (A.u0 * A.u0 + A.u1 * A.u1 + A.u2 * A.u2 + B.u0 * B.u0 + B.u1 * B.u1 + B.u2 * B.u2);
-  const double ph = rm / (2.0 * bm);
+  const double ibm = rcp_full(bm);
+  const double ph = 0.5 * rm * ibm;
   const double un = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
   const double F0 = rl * un;
   double Fm[3];
   for (int c = 0; c < 3; ++c) Fm[c] = F0 * v[c] + ph * n[c];
-  const double h = 1.0 / (2.0 * (gamma - 1.0) * bl);
+  const double ibl = rcp_full(bl);
+  const double h = 0.5 * igm1 * ibl;  // 1 / (2 (gamma - 1) beta_ln)
   // reverse
   const double t4 = Fb[4];
   double vb[3], Fmb[3];
@@ -84,9 +90,9 @@ __device__ __forceinline__ void ec_flux_vjp(const PR& A, const PR& B, double n0,
     vb[c] += unb * n[c];
     nb[c] += unb * v[c];
   }
-  const double blb_ = -hb * h / bl;
-  const double rmb = phb / (2.0 * bm);
-  const double bmb = -phb * ph / bm;
+  const double blb_ = -hb * h * ibl;
+  const double rmb = 0.5 * phb * ibm;
+  const double bmb = -phb * ph * ibm;
   Ab.u0 += 0.5 * vb[0] + q2bb * A.u0;
   Ab.u1 += 0.5 * vb[1] + q2bb * A.u1;
   Ab.u2 += 0.5 * vb[2] + q2bb * A.u2;
@@ -334,7 +340,7 @@ __global__ void __launch_bounds__(threads_for(N), 1)
         const double n0 = 0.5 * (Me[a * stride] + Me[b * stride]);
         const double n1 = 0.5 * (Me[NV + a * stride] + Me[NV + b * stride]);
         const double n2 = 0.5 * (Me[2 * NV + a * stride] + Me[2 * NV + b * stride]);
-        ec_flux_vjp(A, B, n0, n1, n2, g, Fb, ab[a], ab[b], nb);
+        ec_flux_vjp(A, B, n0, n1, n2, ops.inv_gm1, Fb, ab[a], ab[b], nb);
         for (int c2 = 0; c2 < 3; ++c2) {
           mb[a][c2] += 0.5 * nb[c2];
           mb[b][c2] += 0.5 * nb[c2];
@@ -356,8 +362,8 @@ __global__ void __launch_bounds__(threads_for(N), 1)
       PR fob{0, 0, 0, 0, 0}, fnb{0, 0, 0, 0, 0};
       double nfb[3] = {0.0, 0.0, 0.0};
       // face flux f* = F(L, R; n_f)
-      if (s) ec_flux_vjp(Fo, Fn, f0, f1, f2, g, rho, fob, fnb, nfb);
-      else ec_flux_vjp(Fn, Fo, f0, f1, f2, g, rho, fnb, fob, nfb);
+      if (s) ec_flux_vjp(Fo, Fn, f0, f1, f2, ops.inv_gm1, rho, fob, fnb, nfb);
+      else ec_flux_vjp(Fn, Fo, f0, f1, f2, ops.inv_gm1, rho, fnb, fob, nfb);
       // hybrid terms
       for (int a = 0; a < N; ++a) {
         const PR A = pr_load(Pe + a * stride, NV);
@@ -365,7 +371,7 @@ __global__ void __launch_bounds__(threads_for(N), 1)
         for (int k = 0; k < 5; ++k) Fb[k] = sw * t[a] * Re[k * NV + a * stride] - t[a] * rho[k];
         double nb[3] = {0.0, 0.0, 0.0};
         ec_flux_vjp(A, Fo, 0.5 * (Me[a * stride] + f0), 0.5 * (Me[NV + a * stride] + f1),
-                    0.5 * (Me[2 * NV + a * stride] + f2), g, Fb, ab[a], fob, nb);
+                    0.5 * (Me[2 * NV + a * stride] + f2), ops.inv_gm1, Fb, ab[a], fob, nb);
         for (int c2 = 0; c2 < 3; ++c2) {
           mb[a][c2] += 0.5 * nb[c2];
           nfb[c2] += 0.5 * nb[c2];
@@ -533,12 +539,12 @@ __device__ void msweep3(const double* A, bool tr, int rs, int k, int m, const do
   msweep(A, tr, rs, k, m, t2, out, 2, m, m, k);
 }
 
+// S: doubles per field slot, at least max(n^3, q^3) (52 slots per element)
 __global__ void vjp_metric_kernel(const double* __restrict__ ctrl, OpsGeo g, const double* __restrict__ mbar,
                                   const double* __restrict__ nfbar, const double* __restrict__ Jbar, int nx, int ny,
-                                  int nz, double* __restrict__ xbar) {
+                                  int nz, int S, double* __restrict__ xbar) {
   extern __shared__ double sm[];
   const int n = g.n, q = g.q, nv = n * n * n, q3 = q * q * q, nfp = n * n;
-  const int S = 512;
   double* Xe = sm;           // 3
   double* X = Xe + 3 * S;    // 3 (LGL)
   double* dX = X + 3 * S;    // 9
@@ -691,7 +697,14 @@ cudaError_t launch_vjp_n(nsfr_ctx* ctx, const double* u, const double* dbar, dou
 
 }  // namespace
 
-size_t nsfr_vjp_metric_smem() { return (size_t)52 * 512 * sizeof(double); }
+// field slot of the metric reverse: max(n^3, q^3) doubles rounded up to 32; the
+// block has as many threads (at most 256), so that a pass over a field is one sweep
+static int vjp_metric_slot(const nsfr_ctx* ctx) {
+  const int nv = ctx->gops.n * ctx->gops.n * ctx->gops.n, q3 = ctx->gops.q * ctx->gops.q * ctx->gops.q;
+  const int m = nv > q3 ? nv : q3;
+  return (m + 31) / 32 * 32;
+}
+size_t nsfr_vjp_metric_smem(const nsfr_ctx* ctx) { return (size_t)52 * vjp_metric_slot(ctx) * sizeof(double); }
 
 cudaError_t nsfr_launch_vjp(nsfr_ctx* ctx, const double* u, const double* dbar, double* ubar, double* xbar,
                             cudaStream_t s) {
@@ -708,13 +721,14 @@ cudaError_t nsfr_launch_vjp(nsfr_ctx* ctx, const double* u, const double* dbar, 
     default: return cudaErrorInvalidValue;
   }
   if (err != cudaSuccess || !xbar) return err;
-  const size_t smem = nsfr_vjp_metric_smem();
+  const int S = vjp_metric_slot(ctx);
+  const size_t smem = nsfr_vjp_metric_smem(ctx);
   if ((err = cudaFuncSetAttribute(vjp_metric_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
       cudaSuccess)
     return err;
   nsfr_prof_begin(ctx, 7, s);
-  vjp_metric_kernel<<<ctx->ne, 256, smem, s>>>(ctx->ctrl, ctx->gops, ctx->vjp_mbar, ctx->vjp_nfbar, ctx->vjp_jbar,
-                                                ctx->nx, ctx->ny, ctx->nz, xbar);
+  vjp_metric_kernel<<<ctx->ne, S < 256 ? S : 256, smem, s>>>(ctx->ctrl, ctx->gops, ctx->vjp_mbar, ctx->vjp_nfbar,
+                                                              ctx->vjp_jbar, ctx->nx, ctx->ny, ctx->nz, S, xbar);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
   return cudaGetLastError();
