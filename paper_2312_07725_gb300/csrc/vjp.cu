@@ -17,6 +17,7 @@
 // vjp_metric_kernel, the reverse of the conservative-curl construction
 // (Sec. "Computational Space", Eq. GCL).  FP64 throughout; EC face flux.
 #include "kernel_common.cuh"
+#include "mathfn.cuh"
 #include "physics.cuh"
 
 namespace {
@@ -42,10 +43,10 @@ __device__ __forceinline__ void logmean_grad(double a, double b, double& L, doub
     La = 0.5 * G + g2 * b;
     Lb = 0.5 * G - g2 * a;
   } else {
-    const double D = log(a) - log(b);
-    L = d / D;
-    La = (1.0 - L / a) / D;
-    Lb = (L / b - 1.0) / D;
+    const double iD = rcp_full(nsfr_log(a) - nsfr_log(b));
+    L = d * iD;
+    La = (1.0 - L * rcp_full(a)) * iD;
+    Lb = (L * rcp_full(b) - 1.0) * iD;
   }
 }
 
@@ -108,33 +109,34 @@ __device__ __forceinline__ void ec_flux_vjp(const PR& A, const PR& B, double n0,
 __device__ __forceinline__ PR pr_from_conserved(const double* U, int stride, double gamma) {
   PR a;
   a.r = U[0];
-  const double ir = 1.0 / a.r;
+  const double ir = rcp_full(a.r);
   a.u0 = U[stride] * ir;
   a.u1 = U[2 * stride] * ir;
   a.u2 = U[3 * stride] * ir;
   const double q2 = a.u0 * a.u0 + a.u1 * a.u1 + a.u2 * a.u2;
   const double p = (gamma - 1.0) * (U[4 * stride] - 0.5 * a.r * q2);
-  a.b = 0.5 * a.r / p;
+  a.b = 0.5 * a.r * rcp_full(p);
   return a;
 }
 
 // (rho, u, beta) cotangent plus a direct pressure cotangent -> conserved cotangent
 __device__ __forceinline__ void conserved_bar(const PR& a, double gamma, const PR& pb, double pbar_direct,
                                               double Ub[5]) {
+  // p = rho / (2 beta): 1/(2p) = beta/rho, beta/p = 2 beta^2/rho
   const double q2 = a.u0 * a.u0 + a.u1 * a.u1 + a.u2 * a.u2;
-  const double p = 0.5 * a.r / a.b;
-  double rb = pb.r + pb.b / (2.0 * p);
-  const double pbar = pbar_direct - pb.b * a.b / p;
+  const double ir = rcp_full(a.r);
+  double rb = pb.r + pb.b * a.b * ir;
+  const double pbar = pbar_direct - 2.0 * pb.b * a.b * a.b * ir;
   // p = (gamma-1)(E - |m|^2/(2 rho))
   const double g1 = gamma - 1.0;
   const double Eb = g1 * pbar;
   double mb0 = -g1 * pbar * a.u0, mb1 = -g1 * pbar * a.u1, mb2 = -g1 * pbar * a.u2;
   rb += g1 * pbar * 0.5 * q2;
   // u = m / rho
-  mb0 += pb.u0 / a.r;
-  mb1 += pb.u1 / a.r;
-  mb2 += pb.u2 / a.r;
-  rb -= (pb.u0 * a.u0 + pb.u1 * a.u1 + pb.u2 * a.u2) / a.r;
+  mb0 += pb.u0 * ir;
+  mb1 += pb.u1 * ir;
+  mb2 += pb.u2 * ir;
+  rb -= (pb.u0 * a.u0 + pb.u1 * a.u1 + pb.u2 * a.u2) * ir;
   Ub[0] = rb;
   Ub[1] = mb0;
   Ub[2] = mb1;
@@ -144,9 +146,9 @@ __device__ __forceinline__ void conserved_bar(const PR& a, double gamma, const P
 
 __device__ __forceinline__ void entropy_vars(const PR& a, double gamma, double v[5]) {
   const double q2 = a.u0 * a.u0 + a.u1 * a.u1 + a.u2 * a.u2;
-  const double p = 0.5 * a.r / a.b;
-  const double s = log(p) - gamma * log(a.r);
-  v[0] = (gamma - s) / (gamma - 1.0) - a.b * q2;
+  const double p = 0.5 * a.r * rcp_full(a.b);
+  const double s = nsfr_log(p) - gamma * nsfr_log(a.r);
+  v[0] = (gamma - s) * rcp_full(gamma - 1.0) - a.b * q2;
   v[1] = 2.0 * a.b * a.u0;
   v[2] = 2.0 * a.b * a.u1;
   v[3] = 2.0 * a.b * a.u2;
@@ -156,41 +158,41 @@ __device__ __forceinline__ void entropy_vars(const PR& a, double gamma, double v
 // face state from entropy variables (forward) as a primitive record
 __device__ __forceinline__ PR pr_from_entropy(const double v[5], double gamma) {
   PR a;
-  const double v5 = v[4];
+  const double v5 = v[4], iv5 = rcp_full(v5), igm1 = rcp_full(gamma - 1.0);
   a.b = -0.5 * v5;
-  a.u0 = -v[1] / v5;
-  a.u1 = -v[2] / v5;
-  a.u2 = -v[3] / v5;
+  a.u0 = -v[1] * iv5;
+  a.u1 = -v[2] * iv5;
+  a.u2 = -v[3] * iv5;
   const double vm2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
-  const double lr = -gamma / (gamma - 1.0) + v[0] - vm2 / (2.0 * v5) - log(-v5) / (gamma - 1.0);
-  a.r = exp(lr);
+  const double lr = -gamma * igm1 + v[0] - 0.5 * vm2 * iv5 - nsfr_log(-v5) * igm1;
+  a.r = nsfr_exp(lr);
   return a;
 }
 
 // reverse of pr_from_entropy: (rho, u, beta) cotangent -> v cotangent
 __device__ __forceinline__ void entropy_bar_from_pr(const double v[5], const PR& a, double gamma, const PR& pb,
                                                     double vb[5]) {
-  const double v5 = v[4];
+  const double v5 = v[4], iv5 = rcp_full(v5), iv52 = iv5 * iv5, igm1 = rcp_full(gamma - 1.0);
   const double vm2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
   vb[0] = 0.0;
   vb[1] = vb[2] = vb[3] = 0.0;
   vb[4] = -0.5 * pb.b;
   const double ub[3] = {pb.u0, pb.u1, pb.u2};
   for (int c = 0; c < 3; ++c) {
-    vb[1 + c] += -ub[c] / v5;
-    vb[4] += ub[c] * v[1 + c] / (v5 * v5);
+    vb[1 + c] += -ub[c] * iv5;
+    vb[4] += ub[c] * v[1 + c] * iv52;
   }
   const double lb = pb.r * a.r;
   vb[0] += lb;
-  for (int c = 0; c < 3; ++c) vb[1 + c] += -lb * v[1 + c] / v5;
-  vb[4] += lb * (vm2 / (2.0 * v5 * v5) - 1.0 / ((gamma - 1.0) * v5));
+  for (int c = 0; c < 3; ++c) vb[1 + c] += -lb * v[1 + c] * iv5;
+  vb[4] += lb * (0.5 * vm2 * iv52 - igm1 * iv5);
 }
 
 // reverse of entropy_vars: v cotangent -> (rho, u, beta) cotangent and direct p cotangent
 __device__ __forceinline__ void pr_bar_from_entropy_bar(const PR& a, double gamma, const double vb[5], PR& pb,
                                                         double& pbar) {
   const double q2 = a.u0 * a.u0 + a.u1 * a.u1 + a.u2 * a.u2;
-  const double p = 0.5 * a.r / a.b;
+  const double ir = rcp_full(a.r);  // 1/p = 2 beta / rho
   const double u[3] = {a.u0, a.u1, a.u2};
   double bb = -2.0 * vb[4] - vb[0] * q2;
   double ubv[3];
@@ -198,9 +200,9 @@ __device__ __forceinline__ void pr_bar_from_entropy_bar(const PR& a, double gamm
     bb += 2.0 * vb[1 + c] * u[c];
     ubv[c] = 2.0 * a.b * vb[1 + c] - 2.0 * a.b * u[c] * vb[0];
   }
-  const double sb = -vb[0] / (gamma - 1.0);
-  pbar = sb / p;
-  pb.r = -gamma * sb / a.r;
+  const double sb = -vb[0] * rcp_full(gamma - 1.0);
+  pbar = 2.0 * sb * a.b * ir;
+  pb.r = -gamma * sb * ir;
   pb.u0 = ubv[0];
   pb.u1 = ubv[1];
   pb.u2 = ubv[2];
