@@ -54,6 +54,7 @@ struct OpsGL {
   // chi^T W (ns x n) for the weight-adjusted inverse.  uncol = 0: collocated
   // (ns = n, and none of these is used).
   int uncol;
+  int lgl;  // collocated LGL nodes: t_-, t_+ are the unit vectors of the end nodes
   int ns;
   double chi[NSFR_MAXN * NSFR_MAXN];
   double Pi[NSFR_MAXN * NSFR_MAXN];

@@ -138,6 +138,7 @@ void nsfr_build_ops(int p, int p_geo, double c, double gamma, int nodes, OpsGL* 
 
   gl->n = n;
   gl->gamma = gamma;
+  gl->lgl = (nodes == NSFR_NODES_LGL);
   gl->has_K = (c != 0.0);
   double D[NSFR_MAXN * NSFR_MAXN];
   diff_matrix(n, xg, D);

@@ -320,10 +320,18 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
       const size_t fe = (size_t)(s ? e : enb) * 3 + d;  // the element whose + face this is
       const double* nf = nf_s + fe * 3 * NFP + line;  // w_perp C_f
       const double* fsp = fstar + fe * 5 * NFP + line;
+      const double sw = s ? 1.0 : -1.0;
+      if (ops.lgl) {
+        // LGL: t_s is the unit vector of the end node, so the hybrid terms
+        // t_a (phi_a + f* - sum_b t_b phi_b) reduce to f* at that node
+        double* Re = Rl + (s ? N - 1 : 0) * stride;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) Re[k * NV] = fma(sw, fsp[k * NFP], Re[k * NV]);
+        continue;
+      }
       const double f0 = nf[0], f1 = nf[NFP], f2 = nf[2 * NFP];
       const Rec Fo = load_rec6(fo, NFP);
       const double* t = s ? ops.tp : ops.tm;
-      const double sw = s ? 1.0 : -1.0;
       const double h0 = 0.5 * f0, h1 = 0.5 * f1, h2 = 0.5 * f2;
       double tphi[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll 1

@@ -409,7 +409,6 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
       const double* fsp = fstar + fe * 5 * NFP + line;
       const float* g32 = nf32 + fe * 6 * NFP + line;  // the same as float-float: hi(3), lo(3)
       const double f0 = nf[0], f1 = nf[NFP], f2 = nf[2 * NFP];
-      const BNode Fo = bnode_from_rec(load_rec6(fo, NFP));
       // the FP64 face flux in the element's deviation form:
       //   F_m' = F_m - u_ref F_rho - p_ref n,  F_E' = F_E - E_ref F_rho
       ff sr_;
@@ -422,6 +421,13 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
         sm_[2] = d2f_i(fma(-ref.p, f2, fma(-ff_to_double(ref.u2), F0, fsp[3 * NFP])));
         se_ = d2f_i(fma(-(ref.H + f2d_i(ref.kin)), F0, fsp[4 * NFP]));
       }
+      if (ops.lgl) {
+        // LGL: t_s is the unit vector of the end node, so the hybrid terms reduce
+        // to f* at that node
+        add_to(s ? N - 1 : 0, ff{s ? 1.0f : -1.0f, 0.0f}, sr_, sm_, se_);
+        continue;
+      }
+      const BNode Fo = bnode_from_rec(load_rec6(fo, NFP));
       const ff h0{0.5f * g32[0], 0.5f * g32[3 * NFP]}, h1{0.5f * g32[NFP], 0.5f * g32[4 * NFP]},
           h2{0.5f * g32[2 * NFP], 0.5f * g32[5 * NFP]};
       const float* tf = s ? ops.tpf : ops.tmf;
