@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--modes", default="both", choices=["both", "fp64"],
-                    help="both: the FP64 line plus the fp32_bulk object; fp64: skip the bulk measurement")
+                    help="both: the FP64 line plus the fp32_bulk and fp32_bulk_ff objects; fp64: skip them")
     ap.add_argument("--n-el", type=int, default=64)
     ap.add_argument("--p", type=int, default=4)
     ap.add_argument("--cfl", type=float, default=0.1)
@@ -448,12 +448,16 @@ def run_ours(args, rank, ws, dist):
 
     m64 = measure(args, ctrl, u0, "fp64", dist, rank, ws, args.steps)
     d64 = m64.pop("dudt")
-    m32 = None
-    if args.nq is None and args.modes == "both":  # the FP32-bulk form exists for the collocated scheme
+    m32, mff = None, None
+    if args.nq is None and args.modes == "both":  # the FP32-bulk forms exist for the collocated scheme
         m32 = measure(args, ctrl, u0, "fp32_bulk", dist, rank, ws, args.steps)
         d32 = m32.pop("dudt")
         bulk_err = float(np.linalg.norm((d32 - d64).ravel()) / np.linalg.norm(d64.ravel()))
         del d32
+        mff = measure(args, ctrl, u0, "fp32_bulk_ff", dist, rank, ws, args.steps)
+        dff = mff.pop("dudt")
+        ff_err = float(np.linalg.norm((dff - d64).ravel()) / np.linalg.norm(d64.ravel()))
+        del dff
     del d64
 
     adj = None
@@ -496,7 +500,18 @@ def run_ours(args, rank, ws, dist):
                          "d2h_bytes_per_step": m32["e2e_bytes"]},
                  "gpu_launches": m32["gpu_launches"], "kernels": m32["kernels"],
                  "residual_only": m32["residual_only"],
-                 "clocks": m32["clocks"], "dtype": "f32 bulk, f64 log means/state"}}
+                 "clocks": m32["clocks"],
+                 "dtype": "f32 flux arithmetic and contractions; f64 log means, entropy projection, state"},
+                "fp32_bulk_ff": None if mff is None else
+                {"value": mff["value"], "unit": "GDOF/s", "ms_per_step": mff["ms_per_step"],
+                 "speedup_vs_fp64": mff["value"] / m64["value"],
+                 "dudt_rel_l2_vs_fp64_path": ff_err,
+                 "e2e": {"value": mff["e2e"], "unit": "GDOF/s", "h2d_bytes_per_step": mff["e2e_bytes"],
+                         "d2h_bytes_per_step": mff["e2e_bytes"]},
+                 "gpu_launches": mff["gpu_launches"], "kernels": mff["kernels"],
+                 "residual_only": mff["residual_only"], "clocks": mff["clocks"],
+                 "dtype": "f32 flux arithmetic and contractions; float-float log-mean scalars and entropy "
+                          "projection (f64 log means across wide jumps); f64 state"}}
         print(json.dumps(line), flush=True)
 
 

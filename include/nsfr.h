@@ -61,7 +61,7 @@ typedef enum {
 
 typedef enum { NSFR_FLUX_CHANDRASHEKAR = 0 } nsfr_vol_flux;
 typedef enum { NSFR_FACE_EC = 0, NSFR_FACE_EC_ROE = 1, NSFR_FACE_EC_ES = 2 } nsfr_face_flux;
-typedef enum { NSFR_FP64 = 0, NSFR_FP32_BULK = 1 } nsfr_precision;
+typedef enum { NSFR_FP64 = 0, NSFR_FP32_BULK = 1, NSFR_FP32_BULK_FF = 2 } nsfr_precision;
 typedef enum { NSFR_NODES_GL = 0, NSFR_NODES_LGL = 1 } nsfr_nodes;
 typedef enum { NSFR_SOURCE_NONE = 0, NSFR_SOURCE_MANUFACTURED = 1 } nsfr_source;
 
@@ -86,14 +86,17 @@ typedef enum { NSFR_SOURCE_NONE = 0, NSFR_SOURCE_MANUFACTURED = 1 } nsfr_source;
  *               variables with Barth's eigenvector scaling, R T R^T = du/dv,
  *               so that every face dissipates entropy).
  *   gamma       ratio of specific heats (> 1).
- *   precision   NSFR_FP64, or NSFR_FP32_BULK: flux differencing and operator
+ *   precision   NSFR_FP64; NSFR_FP32_BULK: flux differencing and operator
  *               contractions in FP32 with FP32 accumulation (fluxes as
- *               deviations from each element's first node); the mass flux,
- *               the log-mean scalars (rho_ln, p_hat, H) and the entropy
- *               projection in float-float (pairs of floats, ~48 bits, with
- *               float-float log and exp); the state, the face fluxes, log
- *               means across jumps wider than ~3% and all reductions stay
- *               FP64.  du/dt within about 1e-5 of the FP64 path.
+ *               deviations from each element's first node, the mass flux in
+ *               float-float); the log means and the scalars made from them,
+ *               the entropy variables and projection, the face fluxes, the
+ *               state and all reductions stay FP64.  NSFR_FP32_BULK_FF: the
+ *               same, but the log-mean scalars (rho_ln, p_hat, H) and the
+ *               entropy projection in float-float (pairs of floats, ~48
+ *               bits, with float-float log and exp; FP64 for log means
+ *               across jumps wider than ~3%), so that almost nothing waits
+ *               on the FP64 pipe.  Both within about 1e-5 of the FP64 path.
  *   nodes       the collocated solution / volume quadrature nodes:
  *               NSFR_NODES_GL (Gauss-Legendre; the state lives at the GL
  *               nodes) or NSFR_NODES_LGL (Gauss-Lobatto-Legendre, the paper's

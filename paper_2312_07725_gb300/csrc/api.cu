@@ -101,7 +101,7 @@ nsfr_status read_flag(nsfr_ctx* ctx, cudaStream_t s) {
 
 cudaError_t launch_volume_any(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk,
                               cudaStream_t s) {
-  return ctx->precision == NSFR_FP32_BULK ? nsfr_launch_volume_bulk(ctx, u, out, epi, rk, s)
+  return ctx->precision != NSFR_FP64 ? nsfr_launch_volume_bulk(ctx, u, out, epi, rk, s)
                                           : nsfr_launch_volume(ctx, u, out, epi, rk, s);
 }
 
@@ -315,7 +315,7 @@ static nsfr_status setup_common(const double* grid_nodes, int nx, int ny, int nz
   *out = nullptr;
   if (!grid_nodes || nx < 1 || ny < 1 || nz < 1 || p < 1 || p > 7 || p_geo < 1 || p_geo > p || !(gamma > 1.0) ||
       vol_flux != NSFR_FLUX_CHANDRASHEKAR || face_flux < NSFR_FACE_EC || face_flux > NSFR_FACE_EC_ES ||
-      (precision != NSFR_FP64 && precision != NSFR_FP32_BULK) || (nodes != NSFR_NODES_GL && nodes != NSFR_NODES_LGL) ||
+      (precision != NSFR_FP64 && precision != NSFR_FP32_BULK && precision != NSFR_FP32_BULK_FF) || (nodes != NSFR_NODES_GL && nodes != NSFR_NODES_LGL) ||
       !std::isfinite(c) || c < 0.0)
     return NSFR_ERR_ARG;
   nsfr_ctx* ctx = new (std::nothrow) nsfr_ctx();
@@ -361,7 +361,7 @@ static nsfr_status setup_common(const double* grid_nodes, int nx, int ny, int nz
             cudaMallocHost((void**)&ctx->flag_host, sizeof(int)) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->umax_host, sizeof(unsigned long long)) == cudaSuccess;
   if (ok && ctx->uncol && ctx->n == ctx->ns) ok = dalloc(&ctx->uq, ne * 5 * nv) == cudaSuccess;
-  if (ok && precision == NSFR_FP32_BULK)
+  if (ok && precision != NSFR_FP64)
     ok = dalloc(&ctx->metric32, ne * 18 * nv) == cudaSuccess && dalloc(&ctx->nfp_plus32, ne * 18 * nfp) == cudaSuccess &&
          dalloc(&ctx->invwj32, ne * nv) == cudaSuccess;
   if (!ok) {
@@ -388,7 +388,7 @@ static nsfr_status setup_common(const double* grid_nodes, int nx, int ny, int nz
   }
   if (nsfr_launch_metrics(ctx, 0) != cudaSuccess) return bail(NSFR_ERR_CUDA);
   if (nsfr_launch_scaled_rows(ctx, 0) != cudaSuccess) return bail(NSFR_ERR_CUDA);
-  if (precision == NSFR_FP32_BULK && nsfr_launch_bulk_tables(ctx, 0) != cudaSuccess) return bail(NSFR_ERR_CUDA);
+  if (precision != NSFR_FP64 && nsfr_launch_bulk_tables(ctx, 0) != cudaSuccess) return bail(NSFR_ERR_CUDA);
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(NSFR_ERR_CUDA);
   int f = 0;
   if (cudaMemcpy(&f, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return bail(NSFR_ERR_CUDA);
@@ -602,7 +602,7 @@ nsfr_status nsfr_set_metrics(nsfr_ctx* ctx, const double* C, const double* J, co
   CK(cudaMemcpyAsync(ctx->nfp_plus, Cf, ne * 9 * nfp * sizeof(double), cudaMemcpyDefault, s), "copy Cf");
   CK(nsfr_launch_jacobian_derived(ctx, s), "jacobian_derived_kernel");
   CK(nsfr_launch_scaled_rows(ctx, s), "scaled_rows_kernel");
-  if (ctx->precision == NSFR_FP32_BULK) CK(nsfr_launch_bulk_tables(ctx, s), "bulk_tables_kernel");
+  if (ctx->precision != NSFR_FP64) CK(nsfr_launch_bulk_tables(ctx, s), "bulk_tables_kernel");
   return read_flag(ctx, s);
 }
 

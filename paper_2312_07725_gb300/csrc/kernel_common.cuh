@@ -20,14 +20,16 @@ constexpr int vol_ctas(int n) {
   return n == 2 ? 2 : n == 3 ? 2 : n == 4 ? 2 : n == 5 ? 3 : n == 6 ? 2 : n == 7 ? 2 : 1;
 }
 constexpr int vol_threads(int n) { return vol_epb(n) * 3 * n * n; }
-// The FP32-bulk volume kernel: 7 n^3 doubles + 43 n^3 floats of shared memory
-// per element, the same thread layout.  Its pair arithmetic runs on the FP32
-// pipe and is bound by latency at the 128-register cap, where 16 warps per SM
-// is the most the register file holds: at n = 5, 3 elements x 2 CTAs (16
-// warps) measured 2% faster than 2 x 3 (15 warps) and 9% faster than 2 x 2.
-constexpr int bulk_epb(int n) { return n == 5 ? 3 : vol_epb(n); }
-constexpr int bulk_ctas(int n) { return n == 5 ? 2 : vol_ctas(n); }
-constexpr int bulk_threads(int n) { return bulk_epb(n) * 3 * n * n; }
+// The FP32-bulk volume kernels: 7 n^3 doubles + 43 n^3 floats of shared memory
+// per element, the same thread layout.  The FP32-bulk form (FP64 log means) is
+// bound by the FP64 pipe like the FP64 kernel and takes its shapes; the
+// float-float variant runs on the FP32 pipe and is bound by latency at the
+// 128-register cap, where 16 warps per SM is the most the register file holds:
+// at n = 5, 3 elements x 2 CTAs (16 warps) measured 2% faster than 2 x 3 (15
+// warps) and 9% faster than 2 x 2.
+constexpr int bulk_epb(int n, bool ff) { return (ff && n == 5) ? 3 : vol_epb(n); }
+constexpr int bulk_ctas(int n, bool ff) { return (ff && n == 5) ? 2 : vol_ctas(n); }
+constexpr int bulk_threads(int n, bool ff) { return bulk_epb(n, ff) * 3 * n * n; }
 
 // neighbour of element e across face (d, side): side 0 is xi_d = -1 (periodic)
 __device__ __forceinline__ int nbr_index(int e, int d, int side, int nx, int ny, int nz) {

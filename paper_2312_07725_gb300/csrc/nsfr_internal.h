@@ -39,6 +39,7 @@ struct OpsGL {
   //   Gh(u) = G(u)/2 with G = f/atanh(f), F4g(u) = 2/(gamma-1) atanh(f)/f, u = f^2
   double gh[4];
   double f4g[4];
+  double fr2[4];  // 2 atanh(f)/f (the FP32-bulk form's H)
   double inv_gm1;
   // the same series as FP32 corrections for the FP32-bulk kernel: with
   // P(u) = c0 + u (c1 + u c2), G = 1 + u P_g, 2 atanh(f)/f = 2 + u P_a and

@@ -182,6 +182,7 @@ void nsfr_build_ops(int p, int p_geo, double c, double gamma, int nodes, OpsGL* 
   for (int k = 0; k < 4; ++k) {
     gl->gh[k] = 0.5 * G[k];
     gl->f4g[k] = 2.0 / (gamma - 1.0) * F[k];
+    gl->fr2[k] = 2.0 * F[k];
   }
   gl->inv_gm1 = 1.0 / (gamma - 1.0);
   for (int k = 0; k < 3; ++k) {

@@ -505,7 +505,7 @@ cudaError_t nsfr_launch_scaled_rows(nsfr_ctx* ctx, cudaStream_t s) {
 }
 
 cudaError_t nsfr_launch_face_states(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
-  if (ctx->precision == NSFR_FP32_BULK) return nsfr_launch_face_states_bulk(ctx, u, s);
+  if (ctx->precision == NSFR_FP32_BULK_FF) return nsfr_launch_face_states_bulk(ctx, u, s);
   if (ctx->uncol && ctx->n != ctx->ns) return nsfr_launch_projection(ctx, u, s);
   if (ctx->uncol) {
     // square chi (as many GL points as solution nodes): chi Pi = I, so the projected

@@ -26,6 +26,8 @@
 // exactly.  Only O(deviation) quantities then meet FP32 rounding; the mass
 // residual, which u_ref and E_ref (~250 for the Taylor-Green vortex) multiply,
 // is kept to ~48 bits.
+#include <type_traits>
+
 #include "ffloat.cuh"
 #include "kernel_common.cuh"
 #include "mathfn_ff.cuh"
@@ -34,16 +36,25 @@
 namespace {
 using namespace nsfr_k;
 
+// log-mean inputs rho, 2 beta: FP64 in the FP32-bulk form, float-float in its
+// float-float variant (the logs are read when a log mean needs them)
+template <bool FF>
 struct BNode {
-  ff r, b2;       // log-mean inputs rho, 2 beta (the logs are read when a log mean needs them)
+  typename std::conditional<FF, ff, double>::type r, b2;
   ff u0, u1, u2;  // u/2
   float qq;       // |u|^2/4
 };
 
-__device__ __forceinline__ BNode bnode_from_rec(const Rec& a) {
-  BNode b;
-  b.r = ff_from_double(a.r);
-  b.b2 = ff_from_double(a.b2);
+template <bool FF>
+__device__ __forceinline__ BNode<FF> bnode_from_rec(const Rec& a) {
+  BNode<FF> b;
+  if constexpr (FF) {
+    b.r = ff_from_double(a.r);
+    b.b2 = ff_from_double(a.b2);
+  } else {
+    b.r = a.r;
+    b.b2 = a.b2;
+  }
   b.u0 = ff_from_double(a.u0);
   b.u1 = ff_from_double(a.u1);
   b.u2 = ff_from_double(a.u2);
@@ -89,10 +100,47 @@ __device__ __forceinline__ ff ff_add_small(ff c, float x) {
 //   H s2 = p_hat s2 / rho_ln + s2 / (2 (gamma-1) beta_ln) = 2 atanh(f_r)/f_r + F4g(u_b)
 //        = (2 + 2/(gamma-1)) + u_r P_a(u_r) + u_b P_b(u_b)
 // (s2 = 2 beta_a + 2 beta_b), truncated where the next term is below 1e-13 (u < 1e-3).
+// The FP32-bulk form: the log means and the scalars made from them in FP64,
+// with H s2 = 2 atanh(f_r)/f_r + F4g(u_b) on the series branches as below.
 template <class LA, class LB>
-__device__ __forceinline__ void bulk_flux(const BNode& A, const BNode& B, ff n0, ff n1, ff n2, const BRef& ref,
-                                          const OpsGL& K, const LA& la, const LB& lb, ff& Fr, float Fm[3],
-                                          float& FE) {
+__device__ __forceinline__ void bulk_flux(const BNode<false>& A, const BNode<false>& B, ff n0, ff n1, ff n2,
+                                          const BRef& ref, const OpsGL& K, const LA& la, const LB& lb, ff& Fr,
+                                          float Fm[3], float& FE) {
+  const double sr = A.r + B.r, dr = A.r - B.r;
+  const double s2 = A.b2 + B.b2, d2 = A.b2 - B.b2;
+  const double rb2 = rcp_newton1(s2), rr = rcp_newton1(sr);
+  const double fr = dr * rr, fb = d2 * rb2;
+  const double ur = fr * fr, ub = fb * fb;
+  double rln, a, b;  // rho_ln and the two parts of H s2
+  if (lm_small(ur)) {
+    rln = sr * horner4(K.gh, ur);
+    a = horner4(K.fr2, ur);
+  } else {
+    const double dl = la.lr() - lb.lr();
+    rln = dr / dl;
+    a = sr * dl / dr;
+  }
+  if (lm_small(ub)) b = horner4(K.f4g, ub);
+  else b = K.inv_gm1 * (la.lb() - lb.lb()) * s2 / d2;
+  const float dp = d2f_i(fma(sr, rb2, -ref.p));
+  const float dH = d2f_i(fma(a + b, rb2, -ref.H));
+  const ff v0 = ff_add_nn(A.u0, B.u0), v1 = ff_add_nn(A.u1, B.u1), v2 = ff_add_nn(A.u2, B.u2);
+  const ff un = ff_add_nn(ff_add_nn(ff_mul(v0, n0), ff_mul(v1, n1)), ff_mul(v2, n2));
+  Fr = ff_mul(ff_from_double(rln), un);
+  const float f = Fr.hi;
+  const float w0 = ff_diff(v0, ref.u0), w1 = ff_diff(v1, ref.u1), w2 = ff_diff(v2, ref.u2);
+  Fm[0] = fmaf(f, w0, dp * n0.hi);
+  Fm[1] = fmaf(f, w1, dp * n1.hi);
+  Fm[2] = fmaf(f, w2, dp * n2.hi);
+  const float du2 = fmaf(w0, v0.hi + ref.u0.hi, fmaf(w1, v1.hi + ref.u1.hi, w2 * (v2.hi + ref.u2.hi)));
+  FE = f * (dH + du2 + ref.kin - (A.qq + B.qq));
+}
+
+// The float-float variant: the same scalars in float-float on the series branch.
+template <class LA, class LB>
+__device__ __forceinline__ void bulk_flux(const BNode<true>& A, const BNode<true>& B, ff n0, ff n1, ff n2,
+                                          const BRef& ref, const OpsGL& K, const LA& la, const LB& lb, ff& Fr,
+                                          float Fm[3], float& FE) {
   const ff sr = ff_add_nn(A.r, B.r), s2 = ff_add_nn(A.b2, B.b2);
   const float dr = ff_diff(A.r, B.r), d2 = ff_diff(A.b2, B.b2);
   const ff rb2 = ff_rcp(s2);
@@ -241,7 +289,24 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_bulk_kernel(const d
 
 // reference state of an element: its node 0 (u_ref from the same float-float
 // split of u/2 that the node records hold, doubled exactly)
-// from the float-float fields of its node record: rho, 2 beta, u/2
+// from an FP64 node record (FP32-bulk form)
+__device__ __forceinline__ BRef make_ref(const Rec& a, const OpsGL& ops) {
+  BRef r;
+  const double ib2 = rcp_full(a.b2);
+  r.p = a.r * ib2;
+  r.H = ops.gamma * ops.inv_gm1 * ib2;
+  r.pf = ff_from_double(r.p);
+  r.Hf = ff_from_double(r.H);
+  const ff h0 = ff_from_double(a.u0), h1 = ff_from_double(a.u1), h2 = ff_from_double(a.u2);
+  r.u0 = ff{2.0f * h0.hi, 2.0f * h0.lo};
+  r.u1 = ff{2.0f * h1.hi, 2.0f * h1.lo};
+  r.u2 = ff{2.0f * h2.hi, 2.0f * h2.lo};
+  const float x = r.u0.hi, y = r.u1.hi, z = r.u2.hi;
+  r.kin = 0.5f * fmaf(x, x, fmaf(y, y, z * z));
+  return r;
+}
+
+// from the float-float fields of its node record: rho, 2 beta, u/2 (float-float variant)
 __device__ __forceinline__ BRef make_ref(ff rho, ff b2, ff h0, ff h1, ff h2, const OpsGL& ops) {
   BRef r;
   const double ib2 = rcp_full(ff_to_double(b2));
@@ -284,8 +349,8 @@ __device__ __forceinline__ void rank_one_sweep_f(float* X, int nel, int d, bool 
 // preceded by the elements' reference states (BRef, 64 bytes each).
 // The float-float metric rows (w_perp / 2 C), face rows (w_perp C_f) and
 // 1/(w J) come from bulk_tables_kernel, once per geometry.
-template <int N>
-__global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
+template <int N, bool FF>
+__global__ void __launch_bounds__(bulk_threads(N, FF), bulk_ctas(N, FF))
     volume_bulk_kernel(const double* __restrict__ nrec, const float* __restrict__ metric32,
                        const double* __restrict__ nf_s, const float* __restrict__ nf32,
                        const double* __restrict__ face, const double* __restrict__ fstar,
@@ -297,8 +362,10 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
   const int epb = blockDim.x / NL;
   const int e0 = e_beg + blockIdx.x * epb;
   BRef* Refs = (BRef*)sm;                          // [epb]
-  float* Pd = (float*)(Refs + epb);                // [epb][4][NV]: rho, 2 beta as float-float
-  double* Rd = (double*)(Pd + (size_t)epb * 4 * NV);  // [epb][5][NV]
+  // [epb][2][NV] doubles (FP32-bulk) or [epb][4][NV] floats (float-float): rho, 2 beta
+  double* Pdd = (double*)(Refs + epb);
+  float* Pdf = (float*)Pdd;
+  double* Rd = Pdd + (size_t)epb * 2 * NV;         // [epb][5][NV]
   float* Pf = (float*)(Rd + (size_t)epb * 5 * NV); // [epb][25][NV]
   float* Ra = Pf + (size_t)epb * 25 * NV;          // [epb][3][6][NV]
   float* Xf = Pf;                                  // epilogue (aliases Pf)
@@ -306,17 +373,35 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
   for (int t = threadIdx.x; t < epb * NV; t += blockDim.x) {
     const int le = t / NV, node = t % NV, e = e0 + le;
     if (e >= ne) continue;
-    // the float-float fields of the node record (face_state_bulk_kernel)
-    const float2* rec = reinterpret_cast<const float2*>(nrec + (size_t)e * NSFR_NFIELD * NV) + node;
-    const float2 fr2 = rec[P_RHO * NV], fb2 = rec[P_B2 * NV], f0 = rec[P_UH * NV], f1 = rec[(P_UH + 1) * NV],
-                 f2 = rec[(P_UH + 2) * NV], fq = rec[P_QQ * NV];
-    const ff u0{f0.x, f0.y}, u1{f1.x, f1.y}, u2{f2.x, f2.y};
-    if (node == 0) Refs[le] = make_ref(ff{fr2.x, fr2.y}, ff{fb2.x, fb2.y}, u0, u1, u2, ops);
-    float* pd = Pd + (size_t)le * 4 * NV + node;
-    pd[0] = fr2.x;
-    pd[NV] = fr2.y;
-    pd[2 * NV] = fb2.x;
-    pd[3 * NV] = fb2.y;
+    ff u0, u1, u2;
+    float qq;
+    if constexpr (FF) {
+      // the float-float fields of the node record (face_state_bulk_kernel)
+      const float2* rec = reinterpret_cast<const float2*>(nrec + (size_t)e * NSFR_NFIELD * NV) + node;
+      const float2 fr2 = rec[P_RHO * NV], fb2 = rec[P_B2 * NV], f0 = rec[P_UH * NV], f1 = rec[(P_UH + 1) * NV],
+                   f2 = rec[(P_UH + 2) * NV], fq = rec[P_QQ * NV];
+      u0 = ff{f0.x, f0.y};
+      u1 = ff{f1.x, f1.y};
+      u2 = ff{f2.x, f2.y};
+      qq = fq.x;
+      if (node == 0) Refs[le] = make_ref(ff{fr2.x, fr2.y}, ff{fb2.x, fb2.y}, u0, u1, u2, ops);
+      float* pd = Pdf + (size_t)le * 4 * NV + node;
+      pd[0] = fr2.x;
+      pd[NV] = fr2.y;
+      pd[2 * NV] = fb2.x;
+      pd[3 * NV] = fb2.y;
+    } else {
+      // the FP64 node record (face_state_kernel)
+      const Rec a = load_rec6(nrec + (size_t)e * NSFR_NFIELD * NV + node, NV);
+      if (node == 0) Refs[le] = make_ref(a, ops);
+      double* pd = Pdd + (size_t)le * 2 * NV + node;
+      pd[0] = a.r;
+      pd[NV] = a.b2;
+      u0 = ff_from_double(a.u0);
+      u1 = ff_from_double(a.u1);
+      u2 = ff_from_double(a.u2);
+      qq = d2f_i(a.qq);
+    }
     float* pf = Pf + (size_t)le * 25 * NV + node;
     pf[0] = u0.hi;
     pf[NV] = u1.hi;
@@ -324,7 +409,7 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
     pf[3 * NV] = u0.lo;
     pf[4 * NV] = u1.lo;
     pf[5 * NV] = u2.lo;
-    pf[6 * NV] = fq.x;
+    pf[6 * NV] = qq;
     const float* m32 = metric32 + (size_t)e * 18 * NV + node;
 #pragma unroll
     for (int r = 0; r < 18; ++r) pf[(7 + r) * NV] = m32[r * NV];
@@ -342,15 +427,21 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
   int base, stride;
   line_geometry<N>(d, l0, l1, base, stride);
   if (le < epb && e < ne) {
-    const float* pd = Pd + (size_t)le * 4 * NV + base;
+    const float* pdf = Pdf + (size_t)le * 4 * NV + base;
+    const double* pdd = Pdd + (size_t)le * 2 * NV + base;
     const float* pf = Pf + (size_t)le * 25 * NV + base;
     const double* Le = nrec + ((size_t)e * NSFR_NFIELD + P_LRHO) * NV + base;  // ln rho, ln beta (read only off the series path)
     float* Rl = Ra + ((size_t)le * 18 + 6 * d) * NV + base;
     const BRef ref = Refs[le];
     auto node_at = [&](int a) {
-      BNode b;
-      b.r = ff{pd[a * stride], pd[NV + a * stride]};
-      b.b2 = ff{pd[2 * NV + a * stride], pd[3 * NV + a * stride]};
+      BNode<FF> b;
+      if constexpr (FF) {
+        b.r = ff{pdf[a * stride], pdf[NV + a * stride]};
+        b.b2 = ff{pdf[2 * NV + a * stride], pdf[3 * NV + a * stride]};
+      } else {
+        b.r = pdd[a * stride];
+        b.b2 = pdd[NV + a * stride];
+      }
       b.u0 = ff{pf[a * stride], pf[3 * NV + a * stride]};
       b.u1 = ff{pf[NV + a * stride], pf[4 * NV + a * stride]};
       b.u2 = ff{pf[2 * NV + a * stride], pf[5 * NV + a * stride]};
@@ -372,14 +463,14 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
     };
 #pragma unroll 1
     for (int a = 0; a < N - 1; ++a) {
-      const BNode A = node_at(a);
+      const BNode<FF> A = node_at(a);
       const ff na0 = metric_at(a, 0), na1 = metric_at(a, 1), na2 = metric_at(a, 2);
       float* ra = Rl + a * stride;
       ff Rr = ff{ra[0], ra[NV]};
       float Rm0 = ra[2 * NV], Rm1 = ra[3 * NV], Rm2 = ra[4 * NV], Re = ra[5 * NV];
 #pragma unroll 1
       for (int b = a + 1; b < N; ++b) {
-        const BNode B = node_at(b);
+        const BNode<FF> B = node_at(b);
         ff Fr;
         float Fm[3], FE;
         bulk_flux(A, B, ff_add_nn(na0, metric_at(b, 0)), ff_add_nn(na1, metric_at(b, 1)),
@@ -427,7 +518,7 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
         add_to(s ? N - 1 : 0, ff{s ? 1.0f : -1.0f, 0.0f}, sr_, sm_, se_);
         continue;
       }
-      const BNode Fo = bnode_from_rec(load_rec6(fo, NFP));
+      const BNode<FF> Fo = bnode_from_rec<FF>(load_rec6(fo, NFP));
       const ff h0{0.5f * g32[0], 0.5f * g32[3 * NFP]}, h1{0.5f * g32[NFP], 0.5f * g32[4 * NFP]},
           h2{0.5f * g32[2 * NFP], 0.5f * g32[5 * NFP]};
       const float* tf = s ? ops.tpf : ops.tmf;
@@ -437,7 +528,7 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
       float tm[3] = {0.0f, 0.0f, 0.0f}, te = 0.0f;
 #pragma unroll 1
       for (int a = 0; a < N; ++a) {
-        const BNode A = node_at(a);
+        const BNode<FF> A = node_at(a);
         ff Fr;
         float Fm[3], FE;
         bulk_flux(A, Fo, ff_add_nn(metric_at(a, 0), h0), ff_add_nn(metric_at(a, 1), h1),
@@ -535,20 +626,20 @@ __global__ void __launch_bounds__(bulk_threads(N), bulk_ctas(N))
   }
 }
 
-template <int N>
+template <int N, bool FF>
 cudaError_t launch_bulk_n(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk, cudaStream_t s) {
   constexpr int NV = N * N * N;
-  constexpr int epb = bulk_epb(N);
+  constexpr int epb = bulk_epb(N, FF);
   const int eb = ctx->vol_b, ee = ctx->vol_e < 0 ? ctx->ne : ctx->vol_e;
   const int grid = (ee - eb + epb - 1) / epb;
   if (grid <= 0) return cudaSuccess;
   const size_t smem = (size_t)epb * (sizeof(BRef) + NV * (7 * sizeof(double) + 43 * sizeof(float)));
   cudaError_t err =
-      cudaFuncSetAttribute(volume_bulk_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(volume_bulk_kernel<N, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   RkArgs r = rk ? *rk : RkArgs{};
   nsfr_prof_begin(ctx, 2, s);
-  volume_bulk_kernel<N><<<grid, bulk_threads(N), smem, s>>>(ctx->nrec, ctx->metric32, ctx->nf_s,
+  volume_bulk_kernel<N, FF><<<grid, bulk_threads(N, FF), smem, s>>>(ctx->nrec, ctx->metric32, ctx->nf_s,
                                                            ctx->nfp_plus32, ctx->face, ctx->fstar, ctx->invwj32,
                                                            epi == EPI_RAW ? nullptr : ctx->src_on, ctx->ops, ctx->nx,
                                                            ctx->ny, ctx->nz, eb, ee, epi, r, out, ctx->flag);
@@ -632,14 +723,15 @@ cudaError_t nsfr_launch_face_states_bulk(nsfr_ctx* ctx, const double* u, cudaStr
 
 cudaError_t nsfr_launch_volume_bulk(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk,
                                     cudaStream_t s) {
+  const bool ff = ctx->precision == NSFR_FP32_BULK_FF;
   switch (ctx->n) {
-    case 2: return launch_bulk_n<2>(ctx, u, out, epi, rk, s);
-    case 3: return launch_bulk_n<3>(ctx, u, out, epi, rk, s);
-    case 4: return launch_bulk_n<4>(ctx, u, out, epi, rk, s);
-    case 5: return launch_bulk_n<5>(ctx, u, out, epi, rk, s);
-    case 6: return launch_bulk_n<6>(ctx, u, out, epi, rk, s);
-    case 7: return launch_bulk_n<7>(ctx, u, out, epi, rk, s);
-    case 8: return launch_bulk_n<8>(ctx, u, out, epi, rk, s);
+    case 2: return ff ? launch_bulk_n<2, true>(ctx, u, out, epi, rk, s) : launch_bulk_n<2, false>(ctx, u, out, epi, rk, s);
+    case 3: return ff ? launch_bulk_n<3, true>(ctx, u, out, epi, rk, s) : launch_bulk_n<3, false>(ctx, u, out, epi, rk, s);
+    case 4: return ff ? launch_bulk_n<4, true>(ctx, u, out, epi, rk, s) : launch_bulk_n<4, false>(ctx, u, out, epi, rk, s);
+    case 5: return ff ? launch_bulk_n<5, true>(ctx, u, out, epi, rk, s) : launch_bulk_n<5, false>(ctx, u, out, epi, rk, s);
+    case 6: return ff ? launch_bulk_n<6, true>(ctx, u, out, epi, rk, s) : launch_bulk_n<6, false>(ctx, u, out, epi, rk, s);
+    case 7: return ff ? launch_bulk_n<7, true>(ctx, u, out, epi, rk, s) : launch_bulk_n<7, false>(ctx, u, out, epi, rk, s);
+    case 8: return ff ? launch_bulk_n<8, true>(ctx, u, out, epi, rk, s) : launch_bulk_n<8, false>(ctx, u, out, epi, rk, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -271,7 +271,7 @@ def main():
     ap.add_argument("--c", default="both", choices=["dg", "hu", "both"])
     ap.add_argument("--n-el", type=int, default=32)
     ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--precision", default="both", choices=["fp64", "fp32_bulk", "both"])
+    ap.add_argument("--precision", default="both", choices=["fp64", "fp32_bulk", "fp32_bulk_ff", "both"])
     ap.add_argument("--tf", type=float, default=None, help="TGV: run to this time instead of --steps")
     ap.add_argument("--every", type=int, default=10)
     ap.add_argument("--nodes", default="gl", choices=["gl", "lgl"])

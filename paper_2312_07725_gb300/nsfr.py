@@ -21,7 +21,7 @@ NSFR_OK = 0
 STATUS = {0: "NSFR_OK", -1: "NSFR_ERR_ARG", -2: "NSFR_ERR_MESH", -3: "NSFR_ERR_CUDA",
           -4: "NSFR_ERR_NONPHYSICAL", -5: "NSFR_ERR_OOM", -6: "NSFR_ERR_STATE"}
 FACE_FLUX = {"ec": 0, "ec_roe": 1, "ec_es": 2}
-PRECISION = {"fp64": 0, "fp32_bulk": 1}
+PRECISION = {"fp64": 0, "fp32_bulk": 1, "fp32_bulk_ff": 2}
 NODES = {"gl": 0, "lgl": 1}
 SOURCES = {"none": 0, "manufactured": 1}
 

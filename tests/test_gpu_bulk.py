@@ -1,9 +1,10 @@
-"""FP32-bulk path against the FP64 oracle.
+"""FP32-bulk paths against the FP64 oracle.
 
-The bulk path does the flux arithmetic and contractions in FP32, the mass flux,
-the log-mean scalars and the entropy projection (with its log and exp) in
-float-float, and keeps the state, the face fluxes, the log branch of wide
-jumps and the reductions in FP64.  Bar: relative L2 error of du/dt over all five
+Both do the flux arithmetic and contractions in FP32 (the mass flux in
+float-float).  fp32_bulk keeps the log means, the entropy projection, the state,
+the face fluxes and the reductions in FP64; fp32_bulk_ff moves the log-mean
+scalars and the entropy projection (with its log and exp) to float-float as
+well (FP64 for log means across wide jumps).  Bar: relative L2 error of du/dt over all five
 variables <= 1e-5 (the target for this mode); per-variable errors are checked
 loosely and the conservation drift is reported.
 """
@@ -21,10 +22,10 @@ pytestmark = pytest.mark.gpu
 TOL_BULK = 1e-5
 
 
-def bulk_solver(ctrl, shape, P):
+def bulk_solver(ctrl, shape, P, precision="fp32_bulk"):
     from paper_2312_07725_gb300 import Solver
     S = Solver(np.ascontiguousarray(ctrl), shape, P.p, p_geo=P.p_geo, c=P.ops.c, face_flux=P.face_flux,
-               precision="fp32_bulk")
+               precision=precision)
     S.set_metrics(*oracle_metrics_abi(P))
     return S
 
@@ -40,11 +41,12 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("precision", ["fp32_bulk", "fp32_bulk_ff"])
 @pytest.mark.parametrize("p,shape,c_kind,face_flux,kind", CASES)
 @pytest.mark.parametrize("state", ["perturbed", "exact_ic"])
-def test_bulk_dudt_within_1e5(p, shape, c_kind, face_flux, kind, state):
+def test_bulk_dudt_within_1e5(p, shape, c_kind, face_flux, kind, state, precision):
     ctrl, P = oracle_problem(shape, p, c_kind, face_flux, kind)
-    S = bulk_solver(ctrl, shape, P)
+    S = bulk_solver(ctrl, shape, P, precision)
     xyz = P.node_coords()
     if state == "perturbed":
         u = state_for(P, kind)
@@ -58,7 +60,7 @@ def test_bulk_dudt_within_1e5(p, shape, c_kind, face_flux, kind, state):
     err = rel_l2(D, D_ref)
     per = [rel_l2(D[:, k], D_ref[:, k]) if np.linalg.norm(D_ref[:, k]) > 1e-8 * np.linalg.norm(D_ref) else 0.0
            for k in range(5)]
-    print(f"bulk p={p} {shape} {state}: rel L2 {err:.2e} per var {['%.1e' % x for x in per]}")
+    print(f"{precision} p={p} {shape} {state}: rel L2 {err:.2e} per var {['%.1e' % x for x in per]}")
     assert err < TOL_BULK
 
 
@@ -79,13 +81,14 @@ def test_bulk_conservation_and_entropy_are_reported():
     assert abs(d["entropy_rate"]) < 1e-5 * d["entropy_rate_scale"]
 
 
-def test_bulk_at_full_size_sampled():
+@pytest.mark.parametrize("precision", ["fp32_bulk", "fp32_bulk_ff"])
+def test_bulk_at_full_size_sampled(precision):
     """64^3 elements at p = 4 (the benchmark size): sampled 4^3 blocks against the oracle
     on 6^3 patches, oracle metric terms injected for the patch."""
     from paper_2312_07725_gb300 import Solver
     NE, p = 64, 4
     ctrl = wl.tgv_mesh(NE, p)
-    S = Solver(ctrl, (NE,) * 3, p, c=c_hu(p), precision="fp32_bulk")
+    S = Solver(ctrl, (NE,) * 3, p, c=c_hu(p), precision=precision)
     from oracle import geometry
     from oracle.operators1d import Ops1D
     X = geometry.node_coordinates(ctrl, p, Ops1D(p))
@@ -108,12 +111,13 @@ def test_bulk_at_full_size_sampled():
         torch.cuda.synchronize()
         Dref = P.dudt_abi(u[idx])[inner]
         err = rel_l2(D.cpu().numpy()[idx[inner]], Dref)
-        print(f"bulk 64^3 block {corner}: rel L2 {err:.2e}")
+        print(f"{precision} 64^3 block {corner}: rel L2 {err:.2e}")
         assert err < TOL_BULK
 
 
+@pytest.mark.parametrize("precision", ["fp32_bulk", "fp32_bulk_ff"])
 @pytest.mark.parametrize("nodes", ["gl", "lgl"])
-def test_bulk_on_a_developed_taylor_green_state(nodes):
+def test_bulk_on_a_developed_taylor_green_state(nodes, precision):
     """The FP64 library runs the Taylor-Green vortex (4^3 elements, the paper's warp with
     beta = 1/5, p = 4, c_DG) to t = 7, past the vortices' break-down: density varies by
     up to 5% inside an element, so the float-float face states and log means work on
@@ -129,12 +133,12 @@ def test_bulk_on_a_developed_taylor_green_state(nodes):
         t += S.rk_step(u, cfl=0.1)
     un = np.ascontiguousarray(u.cpu().numpy())
     P = Problem(ctrl, (n_el,) * 3, p, c=0.0, nodes=nodes)
-    B = Solver(ctrl, (n_el,) * 3, p, c=0.0, nodes=nodes, precision="fp32_bulk")
+    B = Solver(ctrl, (n_el,) * 3, p, c=0.0, nodes=nodes, precision=precision)
     B.set_metrics(*oracle_metrics_abi(P))
     D = np.zeros_like(un)
     B.residual(un, D)
     err = rel_l2(D, P.dudt_abi(un))
     rho = un[:, 0]
     spread = float(np.max((rho.max(axis=1) - rho.min(axis=1)) / rho.mean(axis=1)))
-    print(f"bulk developed TGV ({nodes}): rel L2 {err:.2e}, density spread in an element up to {spread:.3f}")
+    print(f"{precision} developed TGV ({nodes}): rel L2 {err:.2e}, density spread in an element up to {spread:.3f}")
     assert spread > 0.02 and err < TOL_BULK

@@ -88,12 +88,13 @@ def test_lgl_entropy_rate_and_bulk_mode():
     u = state_for(P)
     d = S.entropy(_dev(u))
     assert abs(d["entropy_rate"]) < 1e-13 * d["entropy_rate_scale"]
-    Sb = _solver(ctrl, shape, P, precision="fp32_bulk")
-    Sb.set_metrics(*oracle_metrics_abi(P))
-    D = torch.empty(u.shape, dtype=torch.float64, device="cuda")
-    Sb.residual(_dev(u), D)
-    torch.cuda.synchronize()
-    assert rel_l2(D.cpu().numpy(), P.dudt_abi(u)) < 1e-5
+    for prec in ("fp32_bulk", "fp32_bulk_ff"):
+        Sb = _solver(ctrl, shape, P, precision=prec)
+        Sb.set_metrics(*oracle_metrics_abi(P))
+        D = torch.empty(u.shape, dtype=torch.float64, device="cuda")
+        Sb.residual(_dev(u), D)
+        torch.cuda.synchronize()
+        assert rel_l2(D.cpu().numpy(), P.dudt_abi(u)) < 1e-5, prec
 
 
 def test_kinetic_energy_lemma_holds_for_the_library_residual(monkeypatch):

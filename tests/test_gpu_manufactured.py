@@ -99,9 +99,10 @@ def test_stage_entry_point_equals_rk_step_with_the_source():
     assert torch.equal(a, b) and S.time == t_a == 0.25 + 5e-3
 
 
-def test_fp32_bulk_with_the_source_is_within_1e5_of_fp64():
+@pytest.mark.parametrize("precision", ["fp32_bulk", "fp32_bulk_ff"])
+def test_fp32_bulk_with_the_source_is_within_1e5_of_fp64(precision):
     _, S64, xyz = _case((3, 2, 2), 4, "hu", "ec_roe", "gl", metrics=False)
-    _, S32, _ = _case((3, 2, 2), 4, "hu", "ec_roe", "gl", precision="fp32_bulk", metrics=False)
+    _, S32, _ = _case((3, 2, 2), 4, "hu", "ec_roe", "gl", precision=precision, metrics=False)
     u = torch.from_numpy(np.ascontiguousarray(wl.manufactured_state(xyz, 0.7))).cuda()
     D64, D32 = torch.empty_like(u), torch.empty_like(u)
     for S, D in ((S64, D64), (S32, D32)):

@@ -51,6 +51,7 @@ CASES = [
     ((2, 2, 6), 2, {"face_flux": "ec_roe"}, "unit"),
     ((2, 2, 4), 3, {"face_flux": "ec_es", "nodes": "lgl"}, "unit"),
     ((3, 1, 4), 4, {"precision": "fp32_bulk"}, "tgv"),
+    ((2, 3, 4), 4, {"precision": "fp32_bulk_ff"}, "tgv"),
     ((2, 2, 4), 2, {"nq": 4}, "tgv"),             # uncollocated, overintegrated
 ]
 
@@ -134,7 +135,7 @@ def test_two_process_slabs_with_the_distributed_exchanger(tmp_path):
         assert np.array_equal(got, ug[meta["z0"] * L:(meta["z0"] + meta["nz"]) * L])
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk", "fp32_bulk_ff"])
 def test_rk_stage_element_range_updates_only_its_elements(precision):
     from paper_2312_07725_gb300 import NSFRError, Solver
     shape, p = (2, 3, 3), 3
@@ -173,6 +174,7 @@ def test_rk_stage_element_range_updates_only_its_elements(precision):
 @pytest.mark.parametrize("shape,p,kw", [
     ((2, 3, 11), 3, {}),                                  # 11 layers in 8 copy chunks
     ((3, 2, 5), 4, {"precision": "fp32_bulk"}),
+    ((2, 3, 5), 3, {"precision": "fp32_bulk_ff"}),
     ((2, 2, 3), 2, {"face_flux": "ec_roe", "nodes": "lgl"}),
     ((2, 2, 9), 3, {"c": 1e-3, "source": True}),
 ])
