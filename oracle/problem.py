@@ -7,7 +7,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import diagnostics, geometry, mass, physics, residual, timestep
+from . import diagnostics, geometry, mass, residual, timestep
 from .operators1d import Ops1D
 
 

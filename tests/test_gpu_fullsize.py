@@ -11,7 +11,6 @@
 * properties that hold at any size: conservation (sum R = 0), the entropy rate of
   the EC scheme and free-stream preservation.
 """
-import math
 
 import numpy as np
 import pytest

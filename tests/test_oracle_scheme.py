@@ -4,7 +4,6 @@ import json
 import math
 import os
 
-import numpy as np
 import pytest
 
 import workloads as wl
