@@ -27,21 +27,23 @@ struct PR {
   double r, u0, u1, u2, b;  // rho, velocity, beta = rho / (2p)
 };
 
-// log mean L(a, b) and its partial derivatives (series branch: L = (a+b) G(u)/2,
-// u = f^2, f = (a-b)/(a+b), G = f/atanh f; otherwise (a-b)/(ln a - ln b))
+// log mean L(a, b) and its partial derivatives; also 1/(a + b).  Series
+// branch: L = s G(u)/2 with s = a + b, f = (a - b)/s, u = f^2 and
+// G = f/atanh f = 1 - u/3 - 4u^2/45 - 44u^3/945 (next term below 1e-16 for
+// u < NSFR_LM_EPS), so that dL/da = G/2 + 2 G'(u) f b/s and
+// dL/db = G/2 - 2 G'(u) f a/s; otherwise L = (a - b)/(ln a - ln b).
 // (reciprocals by an FP32 seed and a third-order step, rcp_full: a division
 // costs several times as many FP64-pipe operations)
-__device__ __forceinline__ void logmean_grad(double a, double b, double& L, double& La, double& Lb) {
+__device__ __forceinline__ void logmean_grad(double a, double b, double& L, double& La, double& Lb, double& is) {
   const double s = a + b, d = a - b;
-  const double is = rcp_full(s);
+  is = rcp_full(s);
   const double f = d * is, u = f * f;
   if (u < NSFR_LM_EPS) {
-    const double G = 1.0 + u * (-1.0 / 3.0 + u * (-4.0 / 45.0 + u * (-44.0 / 945.0)));
-    const double Gp = -1.0 / 3.0 + u * (-8.0 / 45.0 + u * (-132.0 / 945.0));
-    const double g2 = 2.0 * Gp * f * is;
-    L = 0.5 * s * G;
-    La = 0.5 * G + g2 * b;
-    Lb = 0.5 * G - g2 * a;
+    const double h = fma(fma(fma(-22.0 / 945.0, u, -2.0 / 45.0), u, -1.0 / 6.0), u, 0.5);    // G/2
+    const double g2 = fma(fma(-264.0 / 945.0, u, -16.0 / 45.0), u, -2.0 / 3.0) * (f * is);  // 2 G' f/s
+    L = s * h;
+    La = fma(g2, b, h);
+    Lb = fma(-g2, a, h);
   } else {
     const double iD = rcp_full(nsfr_log(a) - nsfr_log(b));
     L = d * iD;
@@ -50,60 +52,53 @@ __device__ __forceinline__ void logmean_grad(double a, double b, double& L, doub
   }
 }
 
-// reverse of F = f_s(A, B) . n (Chandrashekar): accumulates into Ab, Bb, nb
+// reverse of F = f_s(A, B) . n (Chandrashekar): accumulates into Ab, Bb, nb.
+// The forward flux, with u_bar = (u_A + u_B)/2, s_b = beta_A + beta_B and
+// h = 1/(2 (gamma-1) beta_ln):
+//   F_rho = rho_ln (u_bar . n),   F_m = F_rho u_bar + p_hat n,   p_hat = (rho_A + rho_B)/(2 s_b),
+//   F_E = F_rho (h - |u|^2_bar/2) + u_bar . F_m = F_rho (h + u_A . u_B/2) + p_hat (u_bar . n)
+// (|u_bar|^2 - |u|^2_bar/2 = u_A . u_B/2), reversed term by term.  F is
+// linear in n, so a caller may pass a multiple of n with Fb divided by it.
 __device__ __forceinline__ void ec_flux_vjp(const PR& A, const PR& B, double n0, double n1, double n2, double igm1,
                                             const double Fb[5], PR& Ab, PR& Bb, double nb[3]) {
-  double rl, rla, rlb, bl, bla, blb;
-  logmean_grad(A.r, B.r, rl, rla, rlb);
-  logmean_grad(A.b, B.b, bl, bla, blb);
-  const double rm = 0.5 * (A.r + B.r), bm = 0.5 * (A.b + B.b);
-  const double v[3] = {0.5 * (A.u0 + B.u0), 0.5 * (A.u1 + B.u1), 0.5 * (A.u2 + B.u2)};
-  const double n[3] = {n0, n1, n2};
-  const double q2b = 0.5 * (A.u0 * A.u0 + A.u1 * A.u1 + A.u2 * A.u2 + B.u0 * B.u0 + B.u1 * B.u1 + B.u2 * B.u2);
-  const double ibm = rcp_full(bm);
-  const double ph = 0.5 * rm * ibm;
-  const double un = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+  double rl, rla, rlb, isr, bl, bla, blb, isb;
+  logmean_grad(A.r, B.r, rl, rla, rlb, isr);
+  logmean_grad(A.b, B.b, bl, bla, blb, isb);
+  const double v0 = 0.5 * (A.u0 + B.u0), v1 = 0.5 * (A.u1 + B.u1), v2 = 0.5 * (A.u2 + B.u2);
+  const double un = fma(v0, n0, fma(v1, n1, v2 * n2));
   const double F0 = rl * un;
-  double Fm[3];
-  for (int c = 0; c < 3; ++c) Fm[c] = F0 * v[c] + ph * n[c];
+  const double hs = 0.5 * isb;  // dp_hat/drho_A = dp_hat/drho_B
+  const double ph = (A.r + B.r) * hs;
   const double ibl = rcp_full(bl);
-  const double h = 0.5 * igm1 * ibl;  // 1 / (2 (gamma - 1) beta_ln)
+  const double h = 0.5 * igm1 * ibl;
+  const double uab = fma(A.u0, B.u0, fma(A.u1, B.u1, A.u2 * B.u2));
   // reverse
   const double t4 = Fb[4];
-  double vb[3], Fmb[3];
-  double F0b = Fb[0] + t4 * (h - 0.5 * q2b);
+  const double F0b = fma(t4, fma(0.5, uab, h), fma(Fb[1], v0, fma(Fb[2], v1, fma(Fb[3], v2, Fb[0]))));
+  const double phb = fma(t4, un, fma(Fb[1], n0, fma(Fb[2], n1, Fb[3] * n2)));
   const double hb = t4 * F0;
-  const double q2bb = -0.5 * t4 * F0;
-  for (int c = 0; c < 3; ++c) {
-    vb[c] = t4 * Fm[c];
-    Fmb[c] = Fb[1 + c] + t4 * v[c];
-  }
-  double phb = 0.0;
-  for (int c = 0; c < 3; ++c) {
-    F0b += Fmb[c] * v[c];
-    vb[c] += F0 * Fmb[c];
-    phb += Fmb[c] * n[c];
-    nb[c] += ph * Fmb[c];
-  }
+  const double uabb = 0.5 * hb;
+  const double unb = fma(F0b, rl, t4 * ph);  // u_bar . n: through F_rho and F_E
+  // u_bar cotangent (F_rho Fb_m + unb n) shared by both sides, halved, plus the u_A . u_B term
+  const double F0h = 0.5 * F0, unbh = 0.5 * unb;
+  const double g0 = fma(unbh, n0, F0h * Fb[1]), g1 = fma(unbh, n1, F0h * Fb[2]), g2 = fma(unbh, n2, F0h * Fb[3]);
+  Ab.u0 += fma(uabb, B.u0, g0);
+  Ab.u1 += fma(uabb, B.u1, g1);
+  Ab.u2 += fma(uabb, B.u2, g2);
+  Bb.u0 += fma(uabb, A.u0, g0);
+  Bb.u1 += fma(uabb, A.u1, g1);
+  Bb.u2 += fma(uabb, A.u2, g2);
+  nb[0] += fma(ph, Fb[1], unb * v0);
+  nb[1] += fma(ph, Fb[2], unb * v1);
+  nb[2] += fma(ph, Fb[3], unb * v2);
   const double rlb_ = F0b * un;
-  const double unb = F0b * rl;
-  for (int c = 0; c < 3; ++c) {
-    vb[c] += unb * n[c];
-    nb[c] += unb * v[c];
-  }
   const double blb_ = -hb * h * ibl;
-  const double rmb = 0.5 * phb * ibm;
-  const double bmb = -phb * ph * ibm;
-  Ab.u0 += 0.5 * vb[0] + q2bb * A.u0;
-  Ab.u1 += 0.5 * vb[1] + q2bb * A.u1;
-  Ab.u2 += 0.5 * vb[2] + q2bb * A.u2;
-  Bb.u0 += 0.5 * vb[0] + q2bb * B.u0;
-  Bb.u1 += 0.5 * vb[1] + q2bb * B.u1;
-  Bb.u2 += 0.5 * vb[2] + q2bb * B.u2;
-  Ab.r += 0.5 * rmb + rlb_ * rla;
-  Bb.r += 0.5 * rmb + rlb_ * rlb;
-  Ab.b += 0.5 * bmb + blb_ * bla;
-  Bb.b += 0.5 * bmb + blb_ * blb;
+  const double rq = phb * hs;         // p_hat's share of the rho cotangents
+  const double bq = -phb * ph * isb;  // and of the beta cotangents (dp_hat/dbeta = -p_hat/s_b)
+  Ab.r += fma(rlb_, rla, rq);
+  Bb.r += fma(rlb_, rlb, rq);
+  Ab.b += fma(blb_, bla, bq);
+  Bb.b += fma(blb_, blb, bq);
 }
 
 __device__ __forceinline__ PR pr_from_conserved(const double* U, int stride, double gamma) {
@@ -331,21 +326,22 @@ __global__ void __launch_bounds__(threads_for(N), 1)
     const double* Re = Rb + (size_t)le * 5 * NV + base;
     const double* Me = metric + ((size_t)e * 9 + 3 * d) * NV + base;
     const double wperp = ops.w[l0] * ops.w[l1];
+    // the fluxes take the sums of the two metric rows with halved cotangents (F
+    // is linear in n), so that the row cotangent is nb itself
+    const double hw = 0.5 * wperp;
     for (int a = 0; a < N; ++a) {
       const PR A = pr_load(Pe + a * stride, NV);
       for (int b = a + 1; b < N; ++b) {
         const PR B = pr_load(Pe + b * stride, NV);
-        const double c = wperp * ops.S1[a * N + b];
+        const double c = hw * ops.S1[a * N + b];
         double Fb[5];
         for (int k = 0; k < 5; ++k) Fb[k] = c * (Re[k * NV + a * stride] - Re[k * NV + b * stride]);
         double nb[3] = {0.0, 0.0, 0.0};
-        const double n0 = 0.5 * (Me[a * stride] + Me[b * stride]);
-        const double n1 = 0.5 * (Me[NV + a * stride] + Me[NV + b * stride]);
-        const double n2 = 0.5 * (Me[2 * NV + a * stride] + Me[2 * NV + b * stride]);
-        ec_flux_vjp(A, B, n0, n1, n2, ops.inv_gm1, Fb, ab[a], ab[b], nb);
+        ec_flux_vjp(A, B, Me[a * stride] + Me[b * stride], Me[NV + a * stride] + Me[NV + b * stride],
+                    Me[2 * NV + a * stride] + Me[2 * NV + b * stride], ops.inv_gm1, Fb, ab[a], ab[b], nb);
         for (int c2 = 0; c2 < 3; ++c2) {
-          mb[a][c2] += 0.5 * nb[c2];
-          mb[b][c2] += 0.5 * nb[c2];
+          mb[a][c2] += nb[c2];
+          mb[b][c2] += nb[c2];
         }
       }
     }
@@ -359,24 +355,27 @@ __global__ void __launch_bounds__(threads_for(N), 1)
       const double* t = s ? ops.tp : ops.tm;
       const double sw = (s ? 1.0 : -1.0) * wperp;
       double rho[5] = {0, 0, 0, 0, 0};
-      for (int a = 0; a < N; ++a)
-        for (int k = 0; k < 5; ++k) rho[k] += sw * t[a] * Re[k * NV + a * stride];
+      for (int a = 0; a < N; ++a) {
+        const double st = sw * t[a];
+        for (int k = 0; k < 5; ++k) rho[k] = fma(st, Re[k * NV + a * stride], rho[k]);
+      }
       PR fob{0, 0, 0, 0, 0}, fnb{0, 0, 0, 0, 0};
       double nfb[3] = {0.0, 0.0, 0.0};
       // face flux f* = F(L, R; n_f)
       if (s) ec_flux_vjp(Fo, Fn, f0, f1, f2, ops.inv_gm1, rho, fob, fnb, nfb);
       else ec_flux_vjp(Fn, Fo, f0, f1, f2, ops.inv_gm1, rho, fnb, fob, nfb);
-      // hybrid terms
+      // hybrid terms (metric-row sums with halved cotangents, as above)
       for (int a = 0; a < N; ++a) {
         const PR A = pr_load(Pe + a * stride, NV);
+        const double th = 0.5 * t[a];
         double Fb[5];
-        for (int k = 0; k < 5; ++k) Fb[k] = sw * t[a] * Re[k * NV + a * stride] - t[a] * rho[k];
+        for (int k = 0; k < 5; ++k) Fb[k] = th * fma(sw, Re[k * NV + a * stride], -rho[k]);
         double nb[3] = {0.0, 0.0, 0.0};
-        ec_flux_vjp(A, Fo, 0.5 * (Me[a * stride] + f0), 0.5 * (Me[NV + a * stride] + f1),
-                    0.5 * (Me[2 * NV + a * stride] + f2), ops.inv_gm1, Fb, ab[a], fob, nb);
+        ec_flux_vjp(A, Fo, Me[a * stride] + f0, Me[NV + a * stride] + f1, Me[2 * NV + a * stride] + f2,
+                    ops.inv_gm1, Fb, ab[a], fob, nb);
         for (int c2 = 0; c2 < 3; ++c2) {
-          mb[a][c2] += 0.5 * nb[c2];
-          nfb[c2] += 0.5 * nb[c2];
+          mb[a][c2] += nb[c2];
+          nfb[c2] += nb[c2];
         }
       }
       double* fo = fbar_own + (((size_t)e * 6 + f) * 5) * NFP + line;
