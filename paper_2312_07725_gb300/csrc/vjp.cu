@@ -532,20 +532,44 @@ __device__ void msweep(const double* A, bool transpose, int rows, int k, int m, 
   __syncthreads();
 }
 
-// apply A (m x k, row stride rs) along all three directions: (k,k,k) -> (m,m,m)
-__device__ void msweep3(const double* A, bool tr, int rs, int k, int m, const double* in, double* out, double* t1,
-                        double* t2) {
-  msweep(A, tr, rs, k, m, in, t1, 0, k, k, k);
-  msweep(A, tr, rs, k, m, t1, t2, 1, m, k, k);
-  msweep(A, tr, rs, k, m, t2, out, 2, m, m, k);
+// out = A (N x N, or A^T) applied along direction D of an N x N x L block
+// (x fastest; L = N for a cube, 1 for a face layer), A in shared memory
+template <int N, int L, int D, bool TR>
+__device__ __forceinline__ void nsweep(const double* A, const double* in, double* out) {
+  constexpr int NT = N * N * L, ST = D == 0 ? 1 : (D == 1 ? N : N * N);
+  for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+    const int r = (t / ST) % N;
+    const double* src = in + (t - r * ST);
+    double s = 0.0;
+#pragma unroll
+    for (int b = 0; b < N; ++b) s = fma(TR ? A[b * N + r] : A[r * N + b], src[b * ST], s);
+    out[t] = s;
+  }
+  __syncthreads();
+}
+template <int N, bool TR>
+__device__ __forceinline__ void nsweep_d(const double* A, const double* in, double* out, int d) {
+  if (d == 0) nsweep<N, N, 0, TR>(A, in, out);
+  else if (d == 1) nsweep<N, N, 1, TR>(A, in, out);
+  else nsweep<N, N, 2, TR>(A, in, out);
+}
+// along all three directions
+template <int N, bool TR>
+__device__ __forceinline__ void nsweep3(const double* A, const double* in, double* out, double* t1, double* t2) {
+  nsweep<N, N, 0, TR>(A, in, t1);
+  nsweep<N, N, 1, TR>(A, t1, t2);
+  nsweep<N, N, 2, TR>(A, t2, out);
 }
 
-// S: doubles per field slot, at least max(n^3, q^3) (52 slots per element)
+// S: doubles per field slot, at least max(n^3, q^3) (52 slots per element), then
+// the operators E (n x q), D (n x n) and I (n x n)
+template <int N>
 __global__ void vjp_metric_kernel(const double* __restrict__ ctrl, OpsGeo g, const double* __restrict__ mbar,
                                   const double* __restrict__ nfbar, const double* __restrict__ Jbar, int nx, int ny,
                                   int nz, int S, double* __restrict__ xbar) {
   extern __shared__ double sm[];
-  const int n = g.n, q = g.q, nv = n * n * n, q3 = q * q * q, nfp = n * n;
+  constexpr int n = N, nv = N * N * N, nfp = N * N;
+  const int q = g.q, q3 = q * q * q;
   double* Xe = sm;           // 3
   double* X = Xe + 3 * S;    // 3 (LGL)
   double* dX = X + 3 * S;    // 9
@@ -558,17 +582,29 @@ __global__ void vjp_metric_kernel(const double* __restrict__ ctrl, OpsGeo g, con
   double* T4 = T3 + S;
   double* V = T4 + S;        // 3
   double* A = V + 3 * S;     // 9: a = d x / d xi at GL nodes, then its cotangent
+  double* Es = A + 9 * S;    // n x q
+  double* Dl = Es + N * NSFR_MAXN;
+  double* Ig = Dl + N * N;
   const int e = blockIdx.x;
+  for (int t = threadIdx.x; t < N * q; t += blockDim.x) Es[t] = g.E[t];
+  for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+    Dl[t] = g.Dl[t];
+    Ig[t] = g.I[t];
+  }
   for (int t = threadIdx.x; t < 3 * q3; t += blockDim.x) Xe[(t % 3) * S + t / 3] = ctrl[(size_t)e * q3 * 3 + t];
   __syncthreads();
-  for (int c = 0; c < 3; ++c) msweep3(g.E, false, q, q, n, Xe + c * S, X + c * S, T1, T2);
+  for (int c = 0; c < 3; ++c) {
+    msweep(Es, false, q, q, n, Xe + c * S, T1, 0, q, q, q);
+    msweep(Es, false, q, q, n, T1, T2, 1, n, q, q);
+    msweep(Es, false, q, q, n, T2, X + c * S, 2, n, n, q);
+  }
   for (int k = 0; k < 3; ++k)
-    for (int m = 0; m < 3; ++m) msweep(g.Dl, false, n, n, n, X + m * S, dX + (k * 3 + m) * S, k, n, n, n);
+    for (int m = 0; m < 3; ++m) nsweep_d<N, false>(Dl, X + m * S, dX + (k * 3 + m) * S, k);
   // metric = I3 (C_lgl)  ->  Clb = I3^T (mbar)
   for (int r = 0; r < 9; ++r) {
     for (int t = threadIdx.x; t < nv; t += blockDim.x) T3[t] = mbar[((size_t)e * 9 + r) * nv + t];
     __syncthreads();
-    msweep3(g.I, true, n, n, n, T3, Clb + r * S, T1, T2);
+    nsweep3<N, true>(Ig, T3, Clb + r * S, T1, T2);
   }
   // shared face rows: own +face (slot 2d+1) and the +neighbour's -face (slot 2d)
   for (int d = 0; d < 3; ++d) {
@@ -583,8 +619,8 @@ __global__ void vjp_metric_kernel(const double* __restrict__ ctrl, OpsGeo g, con
                 nfbar[(((size_t)ep * 6 + 2 * d) * 3 + c) * nfp + t];
       __syncthreads();
       // forward: face = I (x) I applied to the layer: reverse with I^T along both
-      msweep(g.I, true, n, n, n, T3, T4, 1, n, n, 1);
-      msweep(g.I, true, n, n, n, T4, T3, 0, n, n, 1);
+      nsweep<N, 1, 1, true>(Ig, T3, T4);
+      nsweep<N, 1, 0, true>(Ig, T4, T3);
       double* dst = Clb + (d * 3 + c) * S;
       for (int t = threadIdx.x; t < nfp; t += blockDim.x) {
         const int f0 = t % n, f1 = t / n;
@@ -601,7 +637,7 @@ __global__ void vjp_metric_kernel(const double* __restrict__ ctrl, OpsGeo g, con
   for (int t = threadIdx.x; t < 3 * S; t += blockDim.x) Xb[t] = 0.0;
   __syncthreads();
   // J = det(a), a = I3(dX) at GL nodes: abar = Jbar cof(a) (in place), dXb += I3^T(abar)
-  for (int r = 0; r < 9; ++r) msweep3(g.I, false, n, n, n, dX + r * S, A + r * S, T1, T2);
+  for (int r = 0; r < 9; ++r) nsweep3<N, false>(Ig, dX + r * S, A + r * S, T1, T2);
   for (int t = threadIdx.x; t < nv; t += blockDim.x) {
     const double a00 = A[0 * S + t], a01 = A[1 * S + t], a02 = A[2 * S + t];
     const double a10 = A[3 * S + t], a11 = A[4 * S + t], a12 = A[5 * S + t];
@@ -619,7 +655,7 @@ __global__ void vjp_metric_kernel(const double* __restrict__ ctrl, OpsGeo g, con
   }
   __syncthreads();
   for (int r = 0; r < 9; ++r) {
-    msweep3(g.I, true, n, n, n, A + r * S, T3, T1, T2);
+    nsweep3<N, true>(Ig, A + r * S, T3, T1, T2);
     for (int t = threadIdx.x; t < nv; t += blockDim.x) dXb[r * S + t] += T3[t];
     __syncthreads();
   }
@@ -632,8 +668,8 @@ __global__ void vjp_metric_kernel(const double* __restrict__ ctrl, OpsGeo g, con
     const int da[3] = {1, 2, 0}, va[3] = {2, 0, 1};
     const int db[3] = {2, 0, 1}, vb[3] = {1, 2, 0};
     for (int i = 0; i < 3; ++i) {
-      msweep(g.Dl, true, n, n, n, Clb + (i * 3 + c) * S, T1, da[i], n, n, n);
-      msweep(g.Dl, true, n, n, n, Clb + (i * 3 + c) * S, T2, db[i], n, n, n);
+      nsweep_d<N, true>(Dl, Clb + (i * 3 + c) * S, T1, da[i]);
+      nsweep_d<N, true>(Dl, Clb + (i * 3 + c) * S, T2, db[i]);
       for (int t = threadIdx.x; t < nv; t += blockDim.x) {
         V[va[i] * S + t] -= T1[t];
         V[vb[i] * S + t] += T2[t];
@@ -652,15 +688,15 @@ __global__ void vjp_metric_kernel(const double* __restrict__ ctrl, OpsGeo g, con
   // dX[k][m] = D_k X_m
   for (int k = 0; k < 3; ++k)
     for (int m = 0; m < 3; ++m) {
-      msweep(g.Dl, true, n, n, n, dXb + (k * 3 + m) * S, T1, k, n, n, n);
+      nsweep_d<N, true>(Dl, dXb + (k * 3 + m) * S, T1, k);
       for (int t = threadIdx.x; t < nv; t += blockDim.x) Xb[m * S + t] += T1[t];
       __syncthreads();
     }
   // X = E3(Xe) -> xbar += E3^T(Xb)
   for (int c = 0; c < 3; ++c) {
-    msweep(g.E, true, q, n, q, Xb + c * S, T1, 0, n, n, n);
-    msweep(g.E, true, q, n, q, T1, T2, 1, q, n, n);
-    msweep(g.E, true, q, n, q, T2, T3, 2, q, q, n);
+    msweep(Es, true, q, n, q, Xb + c * S, T1, 0, n, n, n);
+    msweep(Es, true, q, n, q, T1, T2, 1, q, n, n);
+    msweep(Es, true, q, n, q, T2, T3, 2, q, q, n);
     for (int t = threadIdx.x; t < q3; t += blockDim.x) xbar[((size_t)e * q3 + t) * 3 + c] += T3[t];
     __syncthreads();
   }
@@ -705,7 +741,11 @@ static int vjp_metric_slot(const nsfr_ctx* ctx) {
   const int m = nv > q3 ? nv : q3;
   return (m + 31) / 32 * 32;
 }
-size_t nsfr_vjp_metric_smem(const nsfr_ctx* ctx) { return (size_t)52 * vjp_metric_slot(ctx) * sizeof(double); }
+// 52 field slots and the operators E (n x NSFR_MAXN), D and I (n x n)
+size_t nsfr_vjp_metric_smem(const nsfr_ctx* ctx) {
+  const int n = ctx->gops.n;
+  return ((size_t)52 * vjp_metric_slot(ctx) + (size_t)n * NSFR_MAXN + 2 * (size_t)n * n) * sizeof(double);
+}
 
 cudaError_t nsfr_launch_vjp(nsfr_ctx* ctx, const double* u, const double* dbar, double* ubar, double* xbar,
                             cudaStream_t s) {
@@ -724,12 +764,24 @@ cudaError_t nsfr_launch_vjp(nsfr_ctx* ctx, const double* u, const double* dbar, 
   if (err != cudaSuccess || !xbar) return err;
   const int S = vjp_metric_slot(ctx);
   const size_t smem = nsfr_vjp_metric_smem(ctx);
-  if ((err = cudaFuncSetAttribute(vjp_metric_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+  void (*vjp_metric_kernel_p)(const double*, OpsGeo, const double*, const double*, const double*, int, int, int, int,
+                              double*) = nullptr;
+  switch (ctx->gops.n) {
+    case 2: vjp_metric_kernel_p = vjp_metric_kernel<2>; break;
+    case 3: vjp_metric_kernel_p = vjp_metric_kernel<3>; break;
+    case 4: vjp_metric_kernel_p = vjp_metric_kernel<4>; break;
+    case 5: vjp_metric_kernel_p = vjp_metric_kernel<5>; break;
+    case 6: vjp_metric_kernel_p = vjp_metric_kernel<6>; break;
+    case 7: vjp_metric_kernel_p = vjp_metric_kernel<7>; break;
+    case 8: vjp_metric_kernel_p = vjp_metric_kernel<8>; break;
+    default: return cudaErrorInvalidValue;
+  }
+  if ((err = cudaFuncSetAttribute(vjp_metric_kernel_p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
       cudaSuccess)
     return err;
   nsfr_prof_begin(ctx, 7, s);
-  vjp_metric_kernel<<<ctx->ne, S < 256 ? S : 256, smem, s>>>(ctx->ctrl, ctx->gops, ctx->vjp_mbar, ctx->vjp_nfbar,
-                                                              ctx->vjp_jbar, ctx->nx, ctx->ny, ctx->nz, S, xbar);
+  vjp_metric_kernel_p<<<ctx->ne, S < 256 ? S : 256, smem, s>>>(ctx->ctrl, ctx->gops, ctx->vjp_mbar, ctx->vjp_nfbar,
+                                                                ctx->vjp_jbar, ctx->nx, ctx->ny, ctx->nz, S, xbar);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
   return cudaGetLastError();
