@@ -108,6 +108,9 @@ __global__ void diagnostics_kernel(const double* __restrict__ u, const double* _
   const int n = ops.n, nv = n * n * n;
   __shared__ double buf[2][5 * 512];
   __shared__ Comp red[NDIAG][32];
+  // Pi~1^{-1} in shared memory: its rows differ across a warp
+  __shared__ double P1[NSFR_MAXN * NSFR_MAXN];
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) P1[t] = ops.Pinv1[t];
   const double g = ops.gamma, gm1 = g - 1.0;
   Comp acc[NDIAG];
   for (int k = 0; k < NDIAG; ++k) acc[k] = Comp{0.0, 0.0};
@@ -129,7 +132,7 @@ __global__ void diagnostics_kernel(const double* __restrict__ u, const double* _
           for (int k = 0; k < 5; ++k) {
             const double* col = buf[cur] + k * nv + node - r * st;
             double s = 0.0;
-            for (int b = 0; b < n; ++b) s += ops.Pinv1[r * n + b] * col[b * st];
+            for (int b = 0; b < n; ++b) s += P1[r * n + b] * col[b * st];
             buf[1 - cur][k * nv + node] = s;
           }
         }

@@ -499,22 +499,23 @@ __global__ void __launch_bounds__(bulk_threads(N, FF), bulk_ctas(N, FF))
       const double* nf = nf_s + fe * 3 * NFP + line;  // w_perp C_f
       const double* fsp = fstar + fe * 5 * NFP + line;
       const float* g32 = nf32 + fe * 6 * NFP + line;  // the same as float-float: hi(3), lo(3)
-      const double f0 = nf[0], f1 = nf[NFP], f2 = nf[2 * NFP];
       // the FP64 face flux in the element's deviation form:
       //   F_m' = F_m - u_ref F_rho - p_ref n,  F_E' = F_E - E_ref F_rho
-      ff sr_;
-      float sm_[3], se_;
-      {
+      // (formed where it is used, so that it is not live across the hybrid loop)
+      auto face_flux_dev = [&](ff& sr_, float sm_[3], float& se_) {
         const double F0 = fsp[0];
         sr_ = ff_from_double(F0);
-        sm_[0] = d2f_i(fma(-ref.p, f0, fma(-ff_to_double(ref.u0), F0, fsp[NFP])));
-        sm_[1] = d2f_i(fma(-ref.p, f1, fma(-ff_to_double(ref.u1), F0, fsp[2 * NFP])));
-        sm_[2] = d2f_i(fma(-ref.p, f2, fma(-ff_to_double(ref.u2), F0, fsp[3 * NFP])));
+        sm_[0] = d2f_i(fma(-ref.p, nf[0], fma(-ff_to_double(ref.u0), F0, fsp[NFP])));
+        sm_[1] = d2f_i(fma(-ref.p, nf[NFP], fma(-ff_to_double(ref.u1), F0, fsp[2 * NFP])));
+        sm_[2] = d2f_i(fma(-ref.p, nf[2 * NFP], fma(-ff_to_double(ref.u2), F0, fsp[3 * NFP])));
         se_ = d2f_i(fma(-(ref.H + f2d_i(ref.kin)), F0, fsp[4 * NFP]));
-      }
+      };
+      ff sr_;
+      float sm_[3], se_;
       if (ops.lgl) {
         // LGL: t_s is the unit vector of the end node, so the hybrid terms reduce
         // to f* at that node
+        face_flux_dev(sr_, sm_, se_);
         add_to(s ? N - 1 : 0, ff{s ? 1.0f : -1.0f, 0.0f}, sr_, sm_, se_);
         continue;
       }
@@ -541,6 +542,7 @@ __global__ void __launch_bounds__(bulk_threads(N, FF), bulk_ctas(N, FF))
         te = fmaf(ta.hi, FE, te);
         add_to(a, ff{sg * tf[a], sg * tl[a]}, Fr, Fm, FE);
       }
+      face_flux_dev(sr_, sm_, se_);
       const ff dr_ = ff_add(sr_, ff_neg(tr));
       float dm[3];
 #pragma unroll
