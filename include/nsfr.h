@@ -292,9 +292,10 @@ nsfr_status nsfr_check(nsfr_ctx* ctx);
  * Kernel ids for nsfr_profile_read: 0 metric set-up, 1 face states (entropy
  * projection), 2 volume/hybrid/surface + WA inverse (+ RK stage), 3 maximum
  * wave speed, 4 diagnostics, 5 VJP face pass, 6 VJP volume pass, 7 VJP metric
- * pass, 8 face numerical fluxes, 9 volume source.
+ * pass, 8 face numerical fluxes, 9 volume source, 10 the first RK stage's
+ * update when it is not fused into the volume pass (a host-state step).
  */
-#define NSFR_NKERNELS 10
+#define NSFR_NKERNELS 11
 
 /*
  * nsfr_profile -- on != 0: from now on record a CUDA event pair around every

@@ -212,11 +212,16 @@ nsfr_status ensure_copy_stream(nsfr_ctx* ctx) {
 }
 
 // An RK4 step of a host state (collocated contexts): the state goes to the device
-// in z-chunks on a copy stream, and each chunk's face states (and FP32 wave-speed
-// candidates) run as soon as it has arrived, neither needing dt; after the CFL
-// step, stages 0 .. 2 run whole, and stage 3's volume pass runs chunk by chunk,
-// each chunk copied back while the next is computed.  Same results as copy in,
-// rk_step_device, copy out.
+// in z-chunks on a copy stream, and stage 0 runs behind it chunk by chunk without
+// dt: chunk j's face states (and FP32 wave-speed candidates) as soon as it has
+// arrived, then the face fluxes of chunk j-1 (whose + neighbours now have face
+// states) and the volume pass of chunk j-1 (whose - neighbours' fluxes exist),
+// storing k = du/dt; chunk 0 (its - neighbour is the last chunk, the mesh being
+// periodic) and the last chunk follow the last copy.  With dt from the wave
+// speed, one pass applies stage 0's update exactly as the fused epilogue does;
+// stages 1, 2 run whole, and stage 3's volume pass runs chunk by chunk, each
+// chunk copied back while the next is computed.  Same results, bit for bit, as
+// copy in, rk_step_device, copy out.
 nsfr_status rk_step_host(nsfr_ctx* ctx, double* uh, double cfl, double dt_fixed, double* dt_used,
                          cudaStream_t s) {
   nsfr_status st = ensure_host_buffers(ctx);
@@ -244,6 +249,27 @@ nsfr_status rk_step_host(nsfr_ctx* ctx, double* uh, double cfl, double dt_fixed,
     CK(cudaEventRecord(ev_in[j], cs), "cudaEventRecord");
   }
   if (need_lam) CK(nsfr_wavespeed_begin(ctx, s), "cudaMemsetAsync(max)");
+  // stage 0's source term (at time t) does not depend on the state
+  if (ctx->src_on) CK(nsfr_launch_source(ctx, ctx->t, s), "manufactured_source_kernel");
+  // stage 0 without dt: k = du/dt of chunk c into ustage
+  auto stage0_chunk = [&](int c) -> nsfr_status {
+    ctx->ff_b = cb[c];
+    ctx->ff_e = cb[c + 1];
+    cudaError_t err = nsfr_launch_face_flux(ctx, s);
+    ctx->ff_b = 0;
+    ctx->ff_e = -1;
+    CK(err, "face_flux_kernel");
+    return NSFR_OK;
+  };
+  auto stage0_volume = [&](int c) -> nsfr_status {
+    ctx->vol_b = cb[c];
+    ctx->vol_e = cb[c + 1];
+    const cudaError_t err = launch_volume_any(ctx, ud, ctx->ustage, EPI_DUDT, nullptr, s);
+    ctx->vol_b = 0;
+    ctx->vol_e = -1;
+    CK(err, "volume_kernel");
+    return NSFR_OK;
+  };
   for (int j = 0; j < nzc; ++j) {
     CK(cudaStreamWaitEvent(s, ev_in[j], 0), "cudaStreamWaitEvent");
     ctx->fs_b = cb[j];
@@ -253,12 +279,21 @@ nsfr_status rk_step_host(nsfr_ctx* ctx, double* uh, double cfl, double dt_fixed,
     ctx->fs_e = -1;
     CK(err, "face_state_kernel");
     if (need_lam) CK(nsfr_wavespeed_candidates(ctx, ud, cb[j], cb[j + 1], s), "max_wavespeed32_kernel");
+    if (j >= 1) {
+      if ((st = stage0_chunk(j - 1)) != NSFR_OK) return st;
+      if (j >= 2 && (st = stage0_volume(j - 1)) != NSFR_OK) return st;
+    }
   }
-  double dt = dt_fixed;
   if (need_lam) {
     CK(nsfr_wavespeed_finish(ctx, ud, s), "max_wavespeed_kernel");
     CK(cudaMemcpyAsync(ctx->umax_host, ctx->umax, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s),
        "cudaMemcpyAsync(max)");
+  }
+  if ((st = stage0_chunk(nzc - 1)) != NSFR_OK) return st;
+  if (nzc >= 2 && (st = stage0_volume(nzc - 1)) != NSFR_OK) return st;
+  if ((st = stage0_volume(0)) != NSFR_OK) return st;
+  double dt = dt_fixed;
+  if (need_lam) {
     st = read_flag(ctx, s);  // synchronises
     if (st != NSFR_OK) return st;
     double lam;
@@ -267,7 +302,9 @@ nsfr_status rk_step_host(nsfr_ctx* ctx, double* uh, double cfl, double dt_fixed,
     dt = cfl * ctx->dx / lam;
   }
   if (dt_used) *dt_used = dt;
-  st = rk_stage_parts(ctx, ud, ctx->ustage, ctx->acc, 0, dt, s, PART_ALL & ~PART_FACE_STATES);
+  // the fused epilogue's stage-0 update: b_0 = 1/6, a_0 = 1/2
+  const double b0 = 1.0 / 6.0, a0 = 0.5;
+  CK(nsfr_launch_rk_first_update(ctx, ud, ctx->ustage, ctx->acc, b0 * dt, a0 * dt, s), "rk_first_update_kernel");
   for (int k = 1; k < 3 && st == NSFR_OK; ++k) st = rk_stage_device(ctx, ud, ctx->ustage, ctx->acc, k, dt, s);
   if (st == NSFR_OK)
     st = rk_stage_parts(ctx, ud, ctx->ustage, ctx->acc, 3, dt, s, PART_SOURCE | PART_FACE_STATES | PART_FACE_FLUX);

@@ -91,9 +91,11 @@ struct nsfr_ctx {
   int nx, ny, nz, ne, p, n, pg, q, nv, nfp;
   int ns = 0, nsv = 0, uncol = 0;
   // elements [vol_b, vol_e) get the volume pass (nsfr_rk_stage's range), elements
-  // [fs_b, fs_e) the face-state pass; an end < 0 means all
+  // [fs_b, fs_e) the face-state pass, [ff_b, ff_e) the face-flux pass; an end < 0
+  // means all
   int vol_b = 0, vol_e = -1;
   int fs_b = 0, fs_e = -1;
+  int ff_b = 0, ff_e = -1;
   // host-state RK steps: a copy stream and its events (created on first use)
   cudaStream_t cs = nullptr;
   cudaEvent_t* cev = nullptr;  // [2 NSFR_COPY_CHUNKS + 1]
@@ -189,6 +191,9 @@ cudaError_t nsfr_launch_interp_square(nsfr_ctx* ctx, const double* u, cudaStream
 cudaError_t nsfr_launch_scaled_rows(nsfr_ctx* ctx, cudaStream_t s);
 // numerical flux of every face once, from the face states (after nsfr_launch_face_states)
 cudaError_t nsfr_launch_face_flux(nsfr_ctx* ctx, cudaStream_t s);
+// acc = u0 + bdt k, k <- u0 + adt k over the whole state (the first RK stage)
+cudaError_t nsfr_launch_rk_first_update(nsfr_ctx* ctx, const double* u0, double* k, double* acc, double bdt,
+                                        double adt, cudaStream_t s);
 cudaError_t nsfr_launch_volume(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk,
                                cudaStream_t s);
 // residual_bulk.cu: the FP32-bulk form of nsfr_launch_volume

@@ -119,13 +119,15 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
 // face row scaled by the node's w_perp (f* is linear in the face row, its Roe
 // part positively homogeneous): fstar[e][d][5][n^2].  L is the element's own + face state, R
 // the neighbour's - face state; both carry the same face-node index.
+// Elements [e_beg, e_end).
 template <int N>
 __global__ void __launch_bounds__(256) face_flux_kernel(const double* __restrict__ face,
                                                         const double* __restrict__ nf_s, OpsGL ops, int nx, int ny,
-                                                        int nz, int ne, int face_kind, double* __restrict__ fstar) {
+                                                        int nz, int e_beg, int e_end, int face_kind,
+                                                        double* __restrict__ fstar) {
   constexpr int NFP = N * N;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ne * 3 * NFP) return;
+  const int t = e_beg * 3 * NFP + blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= e_end * 3 * NFP) return;
   const int node = t % NFP, ed = t / NFP, d = ed % 3, e = ed / 3;
   const int enb = nbr_index(e, d, 1, nx, ny, nz);
   const Rec L = load_rec(face + (((size_t)e * 6 + 2 * d + 1) * NSFR_NFIELD) * NFP + node, NFP);
@@ -136,6 +138,18 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const double* __restrict
   double* o = fstar + (size_t)ed * 5 * NFP + node;
 #pragma unroll
   for (int k = 0; k < 5; ++k) o[k * NFP] = F[k];
+}
+
+// The first RK4 stage's update from a stored k = du/dt, as the volume kernel's
+// fused epilogue performs it: acc = u0 + b dt k and, in place, k <- u0 + a dt k.
+__global__ void __launch_bounds__(256) rk_first_update_kernel(const double* __restrict__ u0, double* __restrict__ k,
+                                                              double* __restrict__ acc, double bdt, double adt,
+                                                              long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double kk = k[i], u = u0[i];
+    acc[i] = fma(bdt, kk, u);
+    k[i] = fma(adt, kk, u);
+  }
 }
 
 // Pi~1^T (transpose) or Pi~1 along direction d for every line of X[nel][5][NV],
@@ -439,11 +453,14 @@ cudaError_t launch_face_n(nsfr_ctx* ctx, const double* u, cudaStream_t s) {
 
 template <int N>
 cudaError_t launch_face_flux_n(nsfr_ctx* ctx, cudaStream_t s) {
-  const long long total = (long long)ctx->ne * 3 * N * N;
-  if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
+  // elements [ff_b, ff_e): each writes only its own + faces' fluxes
+  const int eb = ctx->ff_b, ee = ctx->ff_e < 0 ? ctx->ne : ctx->ff_e;
+  if ((long long)ctx->ne * 3 * N * N > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const long long total = (long long)(ee - eb) * 3 * N * N;
+  if (total <= 0) return cudaSuccess;
   const int grid = (int)((total + 255) / 256);
   nsfr_prof_begin(ctx, 8, s);
-  face_flux_kernel<N><<<grid, 256, 0, s>>>(ctx->face, ctx->nf_s, ctx->ops, ctx->nx, ctx->ny, ctx->nz, ctx->ne,
+  face_flux_kernel<N><<<grid, 256, 0, s>>>(ctx->face, ctx->nf_s, ctx->ops, ctx->nx, ctx->ny, ctx->nz, eb, ee,
                                            ctx->face_flux, ctx->fstar);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
@@ -538,6 +555,19 @@ cudaError_t nsfr_launch_face_flux(nsfr_ctx* ctx, cudaStream_t s) {
     case 8: return launch_face_flux_n<8>(ctx, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t nsfr_launch_rk_first_update(nsfr_ctx* ctx, const double* u0, double* k, double* acc, double bdt,
+                                        double adt, cudaStream_t s) {
+  const long long n = (long long)ctx->ne * 5 * ctx->nsv;
+  if (n <= 0) return cudaSuccess;
+  const long long want = (n + 255) / 256;
+  const int grid = (int)(want < 152 * 16 ? want : 152 * 16);
+  nsfr_prof_begin(ctx, 10, s);
+  rk_first_update_kernel<<<grid, 256, 0, s>>>(u0, k, acc, bdt, adt, n);
+  nsfr_prof_end(ctx, s);
+  ctx->launches++;
+  return cudaGetLastError();
 }
 
 cudaError_t nsfr_launch_volume(nsfr_ctx* ctx, const double* u, double* out, int epi, const RkArgs* rk,

@@ -31,7 +31,7 @@ EXPORTS = ["nsfr_setup", "nsfr_setup_uncollocated", "nsfr_residual", "nsfr_resid
            "nsfr_profile", "nsfr_profile_read", "nsfr_residual_static", "nsfr_math_eval", "nsfr_kernel_launches",
            "nsfr_last_error", "nsfr_destroy"]
 KERNELS = ["metrics", "face_states", "volume", "max_wavespeed", "diagnostics", "vjp_face", "vjp_volume",
-           "vjp_metrics", "face_flux", "source"]
+           "vjp_metrics", "face_flux", "source", "rk_update"]
 
 
 class NSFRError(RuntimeError):
