@@ -532,6 +532,9 @@ __device__ void msweep(const double* A, bool transpose, int rows, int k, int m, 
   __syncthreads();
 }
 
+// field slots of the metric reverse (see vjp_metric_kernel)
+#define NSFR_VJP_METRIC_SLOTS 40
+
 // out = A (N x N, or A^T) applied along direction D of an N x N x L block
 // (x fastest; L = N for a cube, 1 for a face layer), A in shared memory
 template <int N, int L, int D, bool TR>
@@ -561,8 +564,12 @@ __device__ __forceinline__ void nsweep3(const double* A, const double* in, doubl
   nsweep<N, N, 2, TR>(A, t2, out);
 }
 
-// S: doubles per field slot, at least max(n^3, q^3) (52 slots per element), then
-// the operators E (n x q), D (n x n) and I (n x n)
+// S: doubles per field slot, at least max(n^3, q^3) (NSFR_VJP_METRIC_SLOTS
+// slots), then the operators E (n x q), D (n x n), I (n x n) and the element's
+// first control point.  Slots whose lifetimes do not overlap are shared: the
+// control points become V once the Lobatto coordinates exist, and the Jacobian
+// a = I3(dX) of the determinant part, which runs first, gives way to the metric
+// cotangent Clb; the accumulation order is that of the plain sequence.
 template <int N>
 __global__ void vjp_metric_kernel(const double* __restrict__ ctrl, OpsGeo g, const double* __restrict__ mbar,
                                   const double* __restrict__ nfbar, const double* __restrict__ Jbar, int nx, int ny,
@@ -570,21 +577,22 @@ __global__ void vjp_metric_kernel(const double* __restrict__ ctrl, OpsGeo g, con
   extern __shared__ double sm[];
   constexpr int n = N, nv = N * N * N, nfp = N * N;
   const int q = g.q, q3 = q * q * q;
-  double* Xe = sm;           // 3
+  double* Xe = sm;           // 3: control points; V (3) once X exists
+  double* V = Xe;
   double* X = Xe + 3 * S;    // 3 (LGL)
   double* dX = X + 3 * S;    // 9
-  double* Clb = dX + 9 * S;  // 9: cotangent of the LGL metric
-  double* dXb = Clb + 9 * S; // 9
+  double* A = dX + 9 * S;    // 9: a = d x / d xi at GL nodes, then its cotangent; then Clb
+  double* Clb = A;           //    (the cotangent of the LGL metric)
+  double* dXb = A + 9 * S;   // 9
   double* Xb = dXb + 9 * S;  // 3
   double* T1 = Xb + 3 * S;
   double* T2 = T1 + S;
   double* T3 = T2 + S;
   double* T4 = T3 + S;
-  double* V = T4 + S;        // 3
-  double* A = V + 3 * S;     // 9: a = d x / d xi at GL nodes, then its cotangent
-  double* Es = A + 9 * S;    // n x q
+  double* Es = T4 + S;       // n x q
   double* Dl = Es + N * NSFR_MAXN;
   double* Ig = Dl + N * N;
+  double* X0 = Ig + N * N;   // the first control point
   const int e = blockIdx.x;
   for (int t = threadIdx.x; t < N * q; t += blockDim.x) Es[t] = g.E[t];
   for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
@@ -592,6 +600,7 @@ __global__ void vjp_metric_kernel(const double* __restrict__ ctrl, OpsGeo g, con
     Ig[t] = g.I[t];
   }
   for (int t = threadIdx.x; t < 3 * q3; t += blockDim.x) Xe[(t % 3) * S + t / 3] = ctrl[(size_t)e * q3 * 3 + t];
+  if (threadIdx.x < 3) X0[threadIdx.x] = ctrl[(size_t)e * q3 * 3 + threadIdx.x];
   __syncthreads();
   for (int c = 0; c < 3; ++c) {
     msweep(Es, false, q, q, n, Xe + c * S, T1, 0, q, q, q);
@@ -600,7 +609,33 @@ __global__ void vjp_metric_kernel(const double* __restrict__ ctrl, OpsGeo g, con
   }
   for (int k = 0; k < 3; ++k)
     for (int m = 0; m < 3; ++m) nsweep_d<N, false>(Dl, X + m * S, dX + (k * 3 + m) * S, k);
-  // metric = I3 (C_lgl)  ->  Clb = I3^T (mbar)
+  for (int t = threadIdx.x; t < 9 * S; t += blockDim.x) dXb[t] = 0.0;
+  for (int t = threadIdx.x; t < 3 * S; t += blockDim.x) Xb[t] = 0.0;
+  __syncthreads();
+  // J = det(a), a = I3(dX) at GL nodes: abar = Jbar cof(a) (in place), dXb += I3^T(abar)
+  for (int r = 0; r < 9; ++r) nsweep3<N, false>(Ig, dX + r * S, A + r * S, T1, T2);
+  for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+    const double a00 = A[0 * S + t], a01 = A[1 * S + t], a02 = A[2 * S + t];
+    const double a10 = A[3 * S + t], a11 = A[4 * S + t], a12 = A[5 * S + t];
+    const double a20 = A[6 * S + t], a21 = A[7 * S + t], a22 = A[8 * S + t];
+    const double jb = Jbar[(size_t)e * nv + t];
+    A[0 * S + t] = jb * (a11 * a22 - a12 * a21);
+    A[1 * S + t] = jb * (a12 * a20 - a10 * a22);
+    A[2 * S + t] = jb * (a10 * a21 - a11 * a20);
+    A[3 * S + t] = jb * (a02 * a21 - a01 * a22);
+    A[4 * S + t] = jb * (a00 * a22 - a02 * a20);
+    A[5 * S + t] = jb * (a01 * a20 - a00 * a21);
+    A[6 * S + t] = jb * (a01 * a12 - a02 * a11);
+    A[7 * S + t] = jb * (a02 * a10 - a00 * a12);
+    A[8 * S + t] = jb * (a00 * a11 - a01 * a10);
+  }
+  __syncthreads();
+  for (int r = 0; r < 9; ++r) {
+    nsweep3<N, true>(Ig, A + r * S, T3, T1, T2);
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) dXb[r * S + t] += T3[t];
+    __syncthreads();
+  }
+  // metric = I3 (C_lgl)  ->  Clb = I3^T (mbar), in the slots a no longer needs
   for (int r = 0; r < 9; ++r) {
     for (int t = threadIdx.x; t < nv; t += blockDim.x) T3[t] = mbar[((size_t)e * 9 + r) * nv + t];
     __syncthreads();
@@ -633,32 +668,6 @@ __global__ void vjp_metric_kernel(const double* __restrict__ ctrl, OpsGeo g, con
       __syncthreads();
     }
   }
-  for (int t = threadIdx.x; t < 9 * S; t += blockDim.x) dXb[t] = 0.0;
-  for (int t = threadIdx.x; t < 3 * S; t += blockDim.x) Xb[t] = 0.0;
-  __syncthreads();
-  // J = det(a), a = I3(dX) at GL nodes: abar = Jbar cof(a) (in place), dXb += I3^T(abar)
-  for (int r = 0; r < 9; ++r) nsweep3<N, false>(Ig, dX + r * S, A + r * S, T1, T2);
-  for (int t = threadIdx.x; t < nv; t += blockDim.x) {
-    const double a00 = A[0 * S + t], a01 = A[1 * S + t], a02 = A[2 * S + t];
-    const double a10 = A[3 * S + t], a11 = A[4 * S + t], a12 = A[5 * S + t];
-    const double a20 = A[6 * S + t], a21 = A[7 * S + t], a22 = A[8 * S + t];
-    const double jb = Jbar[(size_t)e * nv + t];
-    A[0 * S + t] = jb * (a11 * a22 - a12 * a21);
-    A[1 * S + t] = jb * (a12 * a20 - a10 * a22);
-    A[2 * S + t] = jb * (a10 * a21 - a11 * a20);
-    A[3 * S + t] = jb * (a02 * a21 - a01 * a22);
-    A[4 * S + t] = jb * (a00 * a22 - a02 * a20);
-    A[5 * S + t] = jb * (a01 * a20 - a00 * a21);
-    A[6 * S + t] = jb * (a01 * a12 - a02 * a11);
-    A[7 * S + t] = jb * (a02 * a10 - a00 * a12);
-    A[8 * S + t] = jb * (a00 * a11 - a01 * a10);
-  }
-  __syncthreads();
-  for (int r = 0; r < 9; ++r) {
-    nsweep3<N, true>(Ig, A + r * S, T3, T1, T2);
-    for (int t = threadIdx.x; t < nv; t += blockDim.x) dXb[r * S + t] += T3[t];
-    __syncthreads();
-  }
   // C_lgl[i][c] = -curl_i(V^(c)), V^(c)_k = (X_l - X_l,0) dX[k][m], (c, m, l) cyclic
   for (int c = 0; c < 3; ++c) {
     const int m = (c + 1) % 3, l = (c + 2) % 3;
@@ -676,8 +685,9 @@ __global__ void vjp_metric_kernel(const double* __restrict__ ctrl, OpsGeo g, con
       }
       __syncthreads();
     }
+    const double x0 = X0[l];
     for (int t = threadIdx.x; t < nv; t += blockDim.x) {
-      const double xl = X[l * S + t] - Xe[l * S];
+      const double xl = X[l * S + t] - x0;
       for (int k = 0; k < 3; ++k) {
         Xb[l * S + t] += V[k * S + t] * dX[(k * 3 + m) * S + t];
         dXb[(k * 3 + m) * S + t] += V[k * S + t] * xl;
@@ -741,10 +751,12 @@ static int vjp_metric_slot(const nsfr_ctx* ctx) {
   const int m = nv > q3 ? nv : q3;
   return (m + 31) / 32 * 32;
 }
-// 52 field slots and the operators E (n x NSFR_MAXN), D and I (n x n)
+// the field slots, the operators E (n x NSFR_MAXN), D and I (n x n) and the first
+// control point (4 doubles)
 size_t nsfr_vjp_metric_smem(const nsfr_ctx* ctx) {
   const int n = ctx->gops.n;
-  return ((size_t)52 * vjp_metric_slot(ctx) + (size_t)n * NSFR_MAXN + 2 * (size_t)n * n) * sizeof(double);
+  return ((size_t)NSFR_VJP_METRIC_SLOTS * vjp_metric_slot(ctx) + (size_t)n * NSFR_MAXN + 2 * (size_t)n * n + 4) *
+         sizeof(double);
 }
 
 cudaError_t nsfr_launch_vjp(nsfr_ctx* ctx, const double* u, const double* dbar, double* ubar, double* xbar,

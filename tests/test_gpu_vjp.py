@@ -58,7 +58,7 @@ def test_state_vjp_matches_complex_step(p, shape, c_kind):
 
 
 @pytest.mark.parametrize("p,shape,c_kind", [(2, (2, 2, 1), "dg"), (3, (1, 2, 2), "hu"), (4, (2, 1, 1), "hu"),
-                                            (5, (1, 1, 2), "dg")])
+                                            (5, (1, 1, 2), "dg"), (6, (1, 2, 1), "hu"), (7, (2, 1, 1), "hu")])
 def test_control_point_vjp_matches_complex_step(p, shape, c_kind):
     c = 0.0 if c_kind == "dg" else c_hu(p)
     ctrl, P, S = _setup(shape, p, c)
