@@ -161,6 +161,12 @@ nsfr_status nsfr_residual_raw(nsfr_ctx* ctx, const double* u, double* R, void* s
  *             needs one device->host read of the max (synchronises).
  *   dt_fixed  > 0: use this step and do not read anything back.
  *   dt_used   host, receives dt (may be NULL).
+ * A host u (collocated contexts) is copied to the device in z-chunks while
+ * stage 0 runs behind the copy (its face states, face fluxes and du/dt chunk
+ * by chunk, the stage update once dt is known), and stage 3's result is
+ * copied back chunk by chunk while the next is computed; the result, dt and
+ * the time equal those of the same step on a device u, bit for bit.  The call
+ * returns when the host u holds the new state.
  */
 nsfr_status nsfr_rk_step(nsfr_ctx* ctx, double* u, double cfl, double dt_fixed, double* dt_used,
                          void* stream);
