@@ -1,0 +1,57 @@
+"""Host-side logic of bench.py (no GPU): the algorithmic work model behind the
+roofline fraction, and the parsing of the clock samples that flags throttling."""
+import bench
+
+
+# two-point flux evaluations per element: 3 n^2 n(n-1)/2 volume pairs + 6 n^3 hybrid
+# pairs + 3 n^2 face fluxes, tabulated independently of the code for p = 3..7
+FLUX_EVALS = {3: 720, 4: 1575, 5: 3024, 6: 5292, 7: 8640}
+
+
+def test_flux_evaluation_counts():
+    for p, total in FLUX_EVALS.items():
+        n = p + 1
+        _, counts = bench.volume_kernel_flops(1, p)
+        assert counts["volume_pairs"] + counts["hybrid"] + 3 * n * n == total
+
+
+def test_volume_flops_at_p4():
+    # 1,500 fluxes x (55 + 20) + face combination 6 n^2 (5 + 10 n) + 5 n^3 + rank-one
+    # sweeps 120 n^3, n = 5
+    flops, counts = bench.volume_kernel_flops(13824, 4)
+    assert counts["flops_per_element"] == 1500 * 75 + 150 * 55 + 625 + 120 * 125 == 136375
+    assert flops == 136375 * 13824
+    # c = 0: no weight-adjusted sweeps
+    _, c0 = bench.volume_kernel_flops(1, 4, has_k=False)
+    assert c0["flops_per_element"] == 136375 - 120 * 125
+
+
+class _FakeProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _sampler(lines):
+    s = bench.ClockSampler(0)
+    s.proc = _FakeProc()
+    s.lines = lines
+    return s
+
+
+def test_clock_samples_report_throttle_reasons():
+    ok = "0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+    hot = "0, 1800, 2070, 1300.0, 0x40, Not Active, Active, Not Active, Not Active"
+    cap = "0, 1950, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active"
+    r = _sampler([ok, ok, ok]).stop()
+    assert r == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
+    r = _sampler([ok, hot, cap, "garbled"]).stop()
+    assert r["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    assert r["samples"] == 3 and r["sm_mhz"] == 1950.0
+
+
+def test_clock_sampler_without_nvidia_smi():
+    r = bench.ClockSampler(0).stop()
+    assert r["sm_mhz"] is None and r["reasons"] == ["nvidia-smi unavailable"]
