@@ -26,6 +26,7 @@ Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|referen
 from __future__ import annotations
 
 import argparse
+import functools
 import json
 import os
 import statistics
@@ -104,6 +105,28 @@ def workload_config(args, ws):
 # --------------------------------------------------------------------------
 # clocks sampled during the timed region
 # --------------------------------------------------------------------------
+@functools.lru_cache(maxsize=None)
+def smi_id(device):
+    """nvidia-smi's --id for a torch CUDA device: its PCI bus id, because CUDA
+    ordinals follow CUDA_VISIBLE_DEVICES and nvidia-smi's indices do not; the
+    ordinal when the bus id is unavailable or nvidia-smi does not accept it."""
+    import torch
+    ordinal = str(device)
+    try:
+        pr = torch.cuda.get_device_properties(device)
+        bus = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+    except (AttributeError, RuntimeError, AssertionError):
+        return ordinal
+    try:
+        r = subprocess.run(["nvidia-smi", f"--id={bus}", "--query-gpu=index", "--format=csv,noheader"],
+                           capture_output=True, text=True, timeout=20)
+        if r.returncode == 0 and r.stdout.strip():
+            return bus
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    return ordinal
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -335,7 +358,7 @@ def measure(args, ctrl, u0, precision, dist, rank, ws, steps):
     barrier(dist)
     launches0 = S.kernel_launches()
     S.profile(True)
-    clocks = ClockSampler(torch.cuda.current_device())
+    clocks = ClockSampler(smi_id(torch.cuda.current_device()))
     clocks.start()
     time.sleep(0.3)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

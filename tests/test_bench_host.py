@@ -55,3 +55,36 @@ def test_clock_samples_report_throttle_reasons():
 def test_clock_sampler_without_nvidia_smi():
     r = bench.ClockSampler(0).stop()
     assert r["sm_mhz"] is None and r["reasons"] == ["nvidia-smi unavailable"]
+
+
+class _Props:
+    pci_domain_id, pci_bus_id, pci_device_id = 0, 0x1B, 0
+
+
+def test_smi_id_is_the_pci_bus_id_when_nvidia_smi_accepts_it(monkeypatch):
+    import subprocess
+    import torch
+    calls = []
+
+    def fake_run(cmd, **kw):
+        calls.append(cmd)
+        return subprocess.CompletedProcess(cmd, 0, stdout="3\n", stderr="")
+
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda d: _Props())
+    monkeypatch.setattr(bench.subprocess, "run", fake_run)
+    bench.smi_id.cache_clear()
+    assert bench.smi_id(0) == "00000000:1B:00.0"
+    assert calls[0][1] == "--id=00000000:1B:00.0"
+    # refused by nvidia-smi, or no bus id: the CUDA ordinal
+    monkeypatch.setattr(bench.subprocess, "run",
+                        lambda cmd, **kw: subprocess.CompletedProcess(cmd, 6, stdout="", stderr="no"))
+    bench.smi_id.cache_clear()
+    assert bench.smi_id(1) == "1"
+
+    def no_props(d):
+        raise RuntimeError("no CUDA")
+
+    monkeypatch.setattr(torch.cuda, "get_device_properties", no_props)
+    bench.smi_id.cache_clear()
+    assert bench.smi_id(2) == "2"
+    bench.smi_id.cache_clear()
