@@ -19,6 +19,24 @@ def test_header_and_binding_agree():
     assert declared_symbols() == sorted(nsfr.EXPORTS)
 
 
+def test_header_and_binding_agree_on_enums_and_kernel_ids():
+    """The binding's tables are the header's: nsfr_profile_read writes
+    NSFR_NKERNELS values into the buffer the binding sizes from KERNELS."""
+    from paper_2312_07725_gb300 import nsfr
+    text = open(os.path.join(ROOT, "include", "nsfr.h")).read()
+    assert int(re.search(r"#define NSFR_NKERNELS (\d+)", text).group(1)) == len(nsfr.KERNELS)
+    enums = dict((k, int(v)) for k, v in re.findall(r"\b(NSFR_[A-Z0-9_]+) = (-?\d+)", text))
+    assert nsfr.FACE_FLUX == {"ec": enums["NSFR_FACE_EC"], "ec_roe": enums["NSFR_FACE_EC_ROE"],
+                              "ec_es": enums["NSFR_FACE_EC_ES"]}
+    assert nsfr.PRECISION == {"fp64": enums["NSFR_FP64"], "fp32_bulk": enums["NSFR_FP32_BULK"],
+                              "fp32_bulk_ff": enums["NSFR_FP32_BULK_FF"]}
+    assert nsfr.NODES == {"gl": enums["NSFR_NODES_GL"], "lgl": enums["NSFR_NODES_LGL"]}
+    assert nsfr.SOURCES == {"none": enums["NSFR_SOURCE_NONE"], "manufactured": enums["NSFR_SOURCE_MANUFACTURED"]}
+    assert {v: k for k, v in nsfr.STATUS.items()} == {k: v for k, v in enums.items() if k.startswith("NSFR_OK")
+                                                      or k.startswith("NSFR_ERR")}
+    assert nsfr.MATH_FN == {k[len("NSFR_FN_"):].lower(): v for k, v in enums.items() if k.startswith("NSFR_FN_")}
+
+
 def test_library_exports_every_declared_symbol():
     from paper_2312_07725_gb300 import nsfr
     if not os.path.exists(nsfr.LIB_PATH):
