@@ -222,7 +222,7 @@ def oracle_sample_rate(p, n_sample=8, budget_s=20.0):
     U = P.to_internal(wl.tgv_state(P.node_coords()))
     nodes = n_sample ** 3 * (p + 1) ** 3
     stages = 0
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     while True:
         k = P.dudt(U)
         U = U + 1e-4 * k  # stage update
@@ -230,14 +230,13 @@ def oracle_sample_rate(p, n_sample=8, budget_s=20.0):
         if time.perf_counter() - t0 > budget_s or stages >= 40:
             break
     dt = time.perf_counter() - t0
-    cores = 1
-    try:
-        import threadpoolctl
-        info = threadpoolctl.threadpool_info()
-        cores = max([1] + [i.get("num_threads", 1) for i in info])
-    except Exception:
-        pass
-    return nodes * stages / dt / 1e9, cores, f"{n_sample}^3 elements at p={p} ({nodes} nodes), {stages} stages, {dt:.1f} s"
+    # the cores the oracle kept busy: CPU time of all the process's threads over wall
+    # time (numpy's BLAS may run several threads)
+    busy = (time.process_time() - c0) / dt
+    cores = max(1, round(busy))
+    return (nodes * stages / dt / 1e9, cores,
+            f"{n_sample}^3 elements at p={p} ({nodes} nodes), {stages} stages, {dt:.1f} s, "
+            f"{busy:.1f} cores busy on average")
 
 
 def run_reference(args, rank, ws, dist):

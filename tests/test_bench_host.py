@@ -88,3 +88,9 @@ def test_smi_id_is_the_pci_bus_id_when_nvidia_smi_accepts_it(monkeypatch):
     bench.smi_id.cache_clear()
     assert bench.smi_id(2) == "2"
     bench.smi_id.cache_clear()
+
+
+def test_oracle_sample_rate_reports_the_cores_it_kept_busy():
+    val, cores, sample = bench.oracle_sample_rate(2, n_sample=2, budget_s=0.5)
+    assert val > 0 and cores >= 1
+    assert "cores busy on average" in sample
