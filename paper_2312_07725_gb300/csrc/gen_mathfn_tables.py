@@ -58,7 +58,7 @@ def fmtf(x):
     return float.hex(x) + "f"
 
 
-def main():
+def main(path=None):
     c, lhi, llo = [], [], []
     for j in range(128):
         cj = float(1 / (1 + (mpmath.mpf(j) + mpmath.mpf(0.5)) / 128))
@@ -146,7 +146,7 @@ def main():
               f"#define NSFR_EXP_INV_L {fmt(inv)}  // 32 / ln 2",
               f"#define NSFR_EXP_L1 {fmt(l1)}      // ln 2 / 32, 36 bits",
               f"#define NSFR_EXP_L2 {fmt(l2)}      // ln 2 / 32 - L1", ""]
-    with open(os.path.join(HERE, "mathfn_tables.h"), "w") as f:
+    with open(path or os.path.join(HERE, "mathfn_tables.h"), "w") as f:
         f.write("\n".join(lines))
 
 
