@@ -7,7 +7,9 @@
                         initial state and to the mesh control points, with the
                         trajectory checkpointed every ``checkpoint_every`` steps and
                         recomputed segment by segment in the reverse sweep.
-Every computation runs in libnsfr.so; torch only holds the buffers.
+The residuals, RK steps and VJPs run in libnsfr.so; the adjoint's stage
+combinations (u + a dt k and the cotangent sums) are torch element-wise
+operations on the library's outputs.
 """
 from __future__ import annotations
 
