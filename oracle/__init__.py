@@ -33,8 +33,11 @@ Modules:
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
 closed forms, library routines, identities proved in the paper, or a dense
-brute-force assembly.  The exact values of c_+ and c_HU as used in the paper,
-Ranocha's pressure fix and the paper's exact Roe form are not printed in the
-paper and are therefore not part of this oracle (parity unpinned for those
-readings; the oracle takes c as an input).
+brute-force assembly; the time step, wave speed, RK4 weights, kinetic energy
+and entropy total by tests/test_oracle_time_diagnostics.py (closed-form wave
+speeds, the RK4 stability polynomial and observed order 4, the Taylor-Green
+kinetic energy pi^3, the entropy of a constant state).  Parity unpinned: the
+numerical value of c_+ (not printed; the oracle takes c as an input) and the
+paper's exact Roe variant (not printed; classical Roe is pinned by its
+linearisation property only).
 """
