@@ -5,8 +5,11 @@ float-float).  fp32_bulk keeps the log means, the entropy projection, the state,
 the face fluxes and the reductions in FP64; fp32_bulk_ff moves the log-mean
 scalars and the entropy projection (with its log and exp) to float-float as
 well (FP64 for log means across wide jumps).  Bar: relative L2 error of du/dt over all five
-variables <= 1e-5 (the target for this mode); per-variable errors are checked
-loosely and the conservation drift is reported.
+variables <= 1e-5 (the target for this mode); per variable, in L2 and element-wise,
+within max(1e-5, 4x the oracle's own change under a 2^-24 (one FP32 ulp) relative
+change of the state), since the FP32 flux arithmetic rounds at that level and the
+momentum du/dt of the low-Mach vortex is a small difference of large pressure fluxes;
+the conservation drift is reported.
 """
 import numpy as np
 import pytest
@@ -16,10 +19,11 @@ torch = pytest.importorskip("torch")
 import workloads as wl  # noqa: E402
 from oracle.operators1d import c_hu  # noqa: E402
 from oracle.problem import Problem  # noqa: E402
-from tests._pairs import oracle_metrics_abi, oracle_problem, rel_l2, state_for  # noqa: E402
+from tests._pairs import check_parity, oracle_metrics_abi, oracle_problem, rel_l2, state_for, ulp_sensitivity  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 TOL_BULK = 1e-5
+FP32_ULP = 2.0 ** -24
 
 
 def bulk_solver(ctrl, shape, P, precision="fp32_bulk"):
@@ -57,11 +61,10 @@ def test_bulk_dudt_within_1e5(p, shape, c_kind, face_flux, kind, state, precisio
     D_ref = P.dudt_abi(u)
     D = np.zeros_like(u)
     S.residual(u, D)
-    err = rel_l2(D, D_ref)
-    per = [rel_l2(D[:, k], D_ref[:, k]) if np.linalg.norm(D_ref[:, k]) > 1e-8 * np.linalg.norm(D_ref) else 0.0
-           for k in range(5)]
-    print(f"{precision} p={p} {shape} {state}: rel L2 {err:.2e} per var {['%.1e' % x for x in per]}")
-    assert err < TOL_BULK
+    sens = ulp_sensitivity(P.dudt_abi, u, rel=FP32_ULP)
+    per = check_parity(D, D_ref, TOL_BULK, sens, what=f"{precision} p={p} {shape} {state}")
+    print(f"{precision} p={p} {shape} {state}: rel L2 {rel_l2(D, D_ref):.2e} per var "
+          f"{['%.1e/%.1e' % x for x in per]}")
 
 
 def test_bulk_conservation_and_entropy_are_reported():
@@ -110,9 +113,10 @@ def test_bulk_at_full_size_sampled(precision):
         S.residual(ud, D)
         torch.cuda.synchronize()
         Dref = P.dudt_abi(u[idx])[inner]
-        err = rel_l2(D.cpu().numpy()[idx[inner]], Dref)
-        print(f"{precision} 64^3 block {corner}: rel L2 {err:.2e}")
-        assert err < TOL_BULK
+        sens = ulp_sensitivity(lambda x: P.dudt_abi(x)[inner], u[idx], rel=FP32_ULP)
+        per = check_parity(D.cpu().numpy()[idx[inner]], Dref, TOL_BULK, sens, what=f"{precision} 64^3 {corner}")
+        print(f"{precision} 64^3 block {corner}: rel L2 {rel_l2(D.cpu().numpy()[idx[inner]], Dref):.2e} "
+              f"per var {['%.1e/%.1e' % x for x in per]}")
 
 
 @pytest.mark.parametrize("precision", ["fp32_bulk", "fp32_bulk_ff"])
@@ -138,6 +142,8 @@ def test_bulk_on_a_developed_taylor_green_state(nodes, precision):
     D = np.zeros_like(un)
     B.residual(un, D)
     err = rel_l2(D, P.dudt_abi(un))
+    check_parity(D, P.dudt_abi(un), TOL_BULK, ulp_sensitivity(P.dudt_abi, un, rel=FP32_ULP),
+                 what=f"{precision} developed TGV ({nodes})")
     rho = un[:, 0]
     spread = float(np.max((rho.max(axis=1) - rho.min(axis=1)) / rho.mean(axis=1)))
     print(f"{precision} developed TGV ({nodes}): rel L2 {err:.2e}, density spread in an element up to {spread:.3f}")

@@ -2,7 +2,7 @@
 solution and volume quadrature on Gauss-Lobatto-Legendre nodes) against the
 oracle's LGL variant, with the same bars as the GL path: the library's metric
 terms at 1e-12, R, du/dt and one RK4 step at 1e-12 with the oracle's metric
-terms injected, the FP32-bulk du/dt within 1e-5, and the semi-discrete entropy
+terms injected (per variable and element-wise as ``tests._pairs.check_parity`` states), the FP32-bulk du/dt within 1e-5, and the semi-discrete entropy
 rate of the EC scheme at the paper's 1e-13.
 """
 import numpy as np
@@ -10,7 +10,8 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from tests._pairs import oracle_metrics_abi, oracle_problem, rel_l2, state_for  # noqa: E402
+from tests._pairs import (check_parity, difference_floor, oracle_metrics_abi, oracle_problem, rel_l2,  # noqa: E402
+                          state_for, ulp_sensitivity)
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -60,8 +61,8 @@ def test_lgl_residual_and_dudt_match_oracle(p, shape, c_kind, face_flux, kind):
     S.residual_raw(ud, R)
     S.residual(ud, D)
     torch.cuda.synchronize()
-    assert rel_l2(R.cpu().numpy(), P.to_abi(P.residual(U))) < TOL
-    assert rel_l2(D.cpu().numpy(), P.to_abi(P.dudt(U))) < TOL
+    check_parity(R.cpu().numpy(), P.to_abi(P.residual(U)), TOL, ulp_sensitivity(P.residual_abi, u), what="R")
+    check_parity(D.cpu().numpy(), P.to_abi(P.dudt(U)), TOL, ulp_sensitivity(P.dudt_abi, u), what="du/dt")
 
 
 def test_lgl_rk4_step_matches_oracle():
@@ -76,8 +77,8 @@ def test_lgl_rk4_step_matches_oracle():
     S.rk_step(ud, dt=dt)
     torch.cuda.synchronize()
     du_ref = u1_ref - u
-    bar = TOL + 4 * np.finfo(np.float64).eps * np.linalg.norm(u1_ref) / np.linalg.norm(du_ref)
-    assert rel_l2(ud.cpu().numpy() - u, du_ref) < bar
+    sens = ulp_sensitivity(lambda x: P.rk4_step_abi(x, dt) - x, u)
+    check_parity(ud.cpu().numpy() - u, du_ref, TOL, sens, difference_floor(u1_ref, du_ref), what="RK4 step")
 
 
 def test_lgl_entropy_rate_and_bulk_mode():

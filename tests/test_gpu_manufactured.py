@@ -3,7 +3,7 @@
 
 Bars as for the rest of the FP64 path: du/dt with the source and RK4 steps with the
 stage times t, t + dt/2, t + dt/2, t + dt at 1e-12 with the oracle's metric terms
-injected; nsfr_residual_raw stays the source-free R; the stage entry point gives the
+injected (per variable and element-wise as ``tests._pairs.check_parity`` states); nsfr_residual_raw stays the source-free R; the stage entry point gives the
 same steps and time; FP32-bulk within 1e-5 of FP64.
 """
 import numpy as np
@@ -14,7 +14,7 @@ torch = pytest.importorskip("torch")
 import workloads as wl  # noqa: E402
 from oracle import manufactured as mm  # noqa: E402
 from oracle.operators1d import c_hu  # noqa: E402
-from tests._pairs import oracle_metrics_abi, rel_l2  # noqa: E402
+from tests._pairs import check_parity, difference_floor, oracle_metrics_abi, rel_l2, ulp_sensitivity  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -54,15 +54,23 @@ def test_dudt_with_the_manufactured_source_matches_oracle(shape, p, c_kind, face
     S.residual(ud, D)
     S.residual_raw(ud, R)
     torch.cuda.synchronize()
-    U = P.to_internal(u)
-    assert rel_l2(D.cpu().numpy(), P.to_abi(P.dudt_t(U, t))) < TOL
-    assert rel_l2(R.cpu().numpy(), P.to_abi(P.residual(U))) < TOL  # raw R: no source
+    def dudt_t(x):
+        return P.to_abi(P.dudt_t(P.to_internal(x), t))
+
+    def res(x):
+        return P.to_abi(P.residual(P.to_internal(x)))
+
+    def dudt(x):
+        return P.to_abi(P.dudt(P.to_internal(x)))
+
+    check_parity(D.cpu().numpy(), dudt_t(u), TOL, ulp_sensitivity(dudt_t, u), what="du/dt with source")
+    check_parity(R.cpu().numpy(), res(u), TOL, ulp_sensitivity(res, u), what="R (no source)")
     assert S.time == t
     # without the source again: the plain du/dt
     S.set_source("none", t)
     S.residual(ud, D)
     torch.cuda.synchronize()
-    assert rel_l2(D.cpu().numpy(), P.to_abi(P.dudt(U))) < TOL
+    check_parity(D.cpu().numpy(), dudt(u), TOL, ulp_sensitivity(dudt, u), what="du/dt")
 
 
 @pytest.mark.parametrize("nodes", ["gl", "lgl"])
@@ -75,12 +83,15 @@ def test_rk4_steps_with_the_source_match_oracle_and_advance_time(nodes):
     S.rk_step(ud, dt=dt)
     S.rk_step(ud, dt=dt)
     torch.cuda.synchronize()
-    U = P.to_internal(u)
-    U = P.rk4_step_t(P.rk4_step_t(U, t0, dt), t0 + dt, dt)
-    ref = P.to_abi(U)
+    def two_steps(x):
+        return P.to_abi(P.rk4_step_t(P.rk4_step_t(P.to_internal(x), t0, dt), t0 + dt, dt))
+
+    ref = two_steps(u)
     du = ref - u
-    bar = TOL + 8 * np.finfo(np.float64).eps * np.linalg.norm(ref) / np.linalg.norm(du)
-    assert rel_l2(ud.cpu().numpy() - u, du) < bar
+    allv, per = difference_floor(ref, du)  # two steps: twice the rounding of one
+    floor = (2 * allv, [(2 * a, 2 * b) for a, b in per])
+    sens = ulp_sensitivity(lambda x: two_steps(x) - x, u)
+    check_parity(ud.cpu().numpy() - u, du, TOL, sens, floor, what="two RK4 steps")
     assert abs(S.time - (t0 + 2 * dt)) < 1e-15
 
 

@@ -1,7 +1,12 @@
 """GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
 
 Bar (FP64 path): relative L2 error over all five variables <= 1e-12 for the
-residual R, for du/dt and for one RK4 step, and for the metric terms.
+residual R, for du/dt and for one RK4 step, and for the metric terms; per
+variable, the relative L2 error and the largest element-wise error (against the
+variable's largest entry) within max(1e-12, 4x the oracle's own change under a
+1-ulp change of the state) (``tests._pairs.check_parity``).  On the low-Mach
+Taylor-Green state that floor matters for the momentum components only: their
+du/dt is the small difference of pressure fluxes ~70x larger.
 
 The residual is ill-conditioned: the fluxes are O(p |J a|) while R is their
 small divergence, so a 1 ulp change of the state moves du/dt by up to ~4e-13
@@ -15,7 +20,8 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from tests._pairs import oracle_metrics_abi, oracle_problem, rel_l2, state_for  # noqa: E402
+from tests._pairs import (check_parity, difference_floor, oracle_metrics_abi, oracle_problem, rel_l2,  # noqa: E402
+                          state_for, ulp_sensitivity)
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -86,8 +92,8 @@ def test_residual_and_dudt_match_oracle(p, shape, c_kind, face_flux, kind):
     S.residual_raw(ud, R)
     S.residual(ud, D)
     torch.cuda.synchronize()
-    assert rel_l2(R.cpu().numpy(), R_ref) < TOL
-    assert rel_l2(D.cpu().numpy(), D_ref) < TOL
+    check_parity(R.cpu().numpy(), R_ref, TOL, ulp_sensitivity(P.residual_abi, u), what="R")
+    check_parity(D.cpu().numpy(), D_ref, TOL, ulp_sensitivity(P.dudt_abi, u), what="du/dt")
     # host buffers through the same entry point give the same numbers
     Dh = np.zeros_like(u)
     S.residual(u, Dh)
@@ -107,10 +113,9 @@ def test_rk4_step_matches_oracle(p, c_kind, face_flux):
     S.rk_step(ud, dt=dt)
     torch.cuda.synchronize()
     du_ref = u1_ref - u
-    # u1 - u is formed from rounded u1 (|u| ~ 180 in energy): add that rounding to the bar
-    eps = np.finfo(np.float64).eps
-    bar = TOL + 4 * eps * np.linalg.norm(u1_ref) / np.linalg.norm(du_ref)
-    assert rel_l2(ud.cpu().numpy() - u, du_ref) < bar
+    # u1 - u is formed from rounded u1 (|u| ~ 180 in energy): that rounding joins the bars
+    sens = ulp_sensitivity(lambda x: P.rk4_step_abi(x, dt) - x, u)
+    check_parity(ud.cpu().numpy() - u, du_ref, TOL, sens, difference_floor(u1_ref, du_ref), what="RK4 step")
     # CFL step: dt from the maximum wave speed
     ud = to_dev(u)
     dt_used = S.rk_step(ud, cfl=0.1)
@@ -217,4 +222,4 @@ def test_residual_matches_oracle_on_a_developed_taylor_green_state(p):
     S.residual_raw(u, R)
     torch.cuda.synchronize()
     un = u.cpu().numpy()
-    assert rel_l2(R.cpu().numpy(), P.to_abi(P.residual(P.to_internal(un)))) < TOL
+    check_parity(R.cpu().numpy(), P.residual_abi(un), TOL, ulp_sensitivity(P.residual_abi, un), what="R at t = 7")

@@ -4,7 +4,8 @@ overintegration) against the oracle's UncollocatedProblem.
 
 Bars as for the collocated path: the library's metric terms at the GL points and its
 node coordinates at 1e-12, R^ = chi^T R_q, du^/dt and one RK4 step at 1e-12 with the
-oracle's metric terms injected (the residual is ill-conditioned, see test_gpu_parity).
+oracle's metric terms injected (the residual is ill-conditioned, see test_gpu_parity), per
+variable and element-wise as ``tests._pairs.check_parity`` states.
 """
 import math
 
@@ -16,7 +17,7 @@ torch = pytest.importorskip("torch")
 import workloads as wl  # noqa: E402
 from oracle.operators1d import c_hu  # noqa: E402
 from oracle.uncollocated import UncollocatedProblem  # noqa: E402
-from tests._pairs import rel_l2  # noqa: E402
+from tests._pairs import check_parity, difference_floor, rel_l2, ulp_sensitivity  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -74,9 +75,14 @@ def test_uncollocated_residual_and_dudt_match_oracle(p, nq, shape, c_kind, face_
     S.residual_raw(ud, R)
     S.residual(ud, D)
     torch.cuda.synchronize()
-    U = P.to_internal(u)
-    assert rel_l2(R.cpu().numpy(), P.to_abi(P.residual(U))) < TOL
-    assert rel_l2(D.cpu().numpy(), P.to_abi(P.dudt(U))) < TOL
+    def res(x):
+        return P.to_abi(P.residual(P.to_internal(x)))
+
+    def dudt(x):
+        return P.to_abi(P.dudt(P.to_internal(x)))
+
+    check_parity(R.cpu().numpy(), res(u), TOL, ulp_sensitivity(res, u), what="R^")
+    check_parity(D.cpu().numpy(), dudt(u), TOL, ulp_sensitivity(dudt, u), what="du^/dt")
 
 
 def test_uncollocated_rk4_step_matches_oracle():
@@ -88,8 +94,8 @@ def test_uncollocated_rk4_step_matches_oracle():
     S.rk_step(ud, dt=dt)
     torch.cuda.synchronize()
     du = u1 - u
-    bar = TOL + 4 * np.finfo(np.float64).eps * np.linalg.norm(u1) / np.linalg.norm(du)
-    assert rel_l2(ud.cpu().numpy() - u, du) < bar
+    sens = ulp_sensitivity(lambda x: P.rk4_step_abi(x, dt) - x, u)
+    check_parity(ud.cpu().numpy() - u, du, TOL, sens, difference_floor(u1, du), what="RK4 step")
 
 
 def test_uncollocated_context_rejects_what_it_does_not_support():
