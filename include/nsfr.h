@@ -59,7 +59,7 @@ typedef enum {
   NSFR_ERR_STATE = -6        /* call not valid for this context */
 } nsfr_status;
 
-typedef enum { NSFR_FLUX_CHANDRASHEKAR = 0 } nsfr_vol_flux;
+typedef enum { NSFR_FLUX_CHANDRASHEKAR = 0, NSFR_FLUX_RANOCHA = 1 } nsfr_vol_flux;
 typedef enum { NSFR_FACE_EC = 0, NSFR_FACE_EC_ROE = 1, NSFR_FACE_EC_ES = 2 } nsfr_face_flux;
 typedef enum { NSFR_FP64 = 0, NSFR_FP32_BULK = 1, NSFR_FP32_BULK_FF = 2 } nsfr_precision;
 typedef enum { NSFR_NODES_GL = 0, NSFR_NODES_LGL = 1 } nsfr_nodes;
@@ -78,7 +78,15 @@ typedef enum { NSFR_SOURCE_NONE = 0, NSFR_SOURCE_MANUFACTURED = 1 } nsfr_source;
  *   p           solution degree, 1 <= p <= 7.
  *   c           ESFR parameter (c = 0: DG; Sec. "Energy Stable Flux
  *               Reconstruction", Eq. Km with c_(s,v,w) = c^{(s+v+w)/p}).
- *   vol_flux    NSFR_FLUX_CHANDRASHEKAR (the paper's EC two-point flux).
+ *   vol_flux    the entropy-conserving two-point flux of the volume, hybrid
+ *               and face terms: NSFR_FLUX_CHANDRASHEKAR (Chandrashekar's EC,
+ *               kinetic-energy preserving flux) or NSFR_FLUX_RANOCHA (the
+ *               flux the paper's EC runs use, Sec. "Results": Chandrashekar's
+ *               with Ranocha's pressure terms, the arithmetic pressure mean in
+ *               the momentum flux and (p_L u_R.n + p_R u_L.n)/2 as the pressure
+ *               work in the energy flux).  NSFR_FLUX_RANOCHA needs precision
+ *               NSFR_FP64 (else NSFR_ERR_ARG), and nsfr_vjp returns
+ *               NSFR_ERR_STATE for such a context.
  *   face_flux   NSFR_FACE_EC (entropy conserving), NSFR_FACE_EC_ROE (EC
  *               flux plus Roe dissipation, Sec. "Nonlinear Stability") or
  *               NSFR_FACE_EC_ES (EC flux minus (1/2) R |Lambda| T R^T [[v]]:
@@ -318,14 +326,18 @@ nsfr_status nsfr_profile(nsfr_ctx* ctx, int on);
 nsfr_status nsfr_profile_read(nsfr_ctx* ctx, double* ms, long long* count);
 
 /*
- * nsfr_residual_static -- du/dt exactly as nsfr_residual computes it, for
- * callers that must not allocate device memory: code running under a memory
+ * nsfr_residual_static -- du/dt as nsfr_residual computes it for an FP64
+ * context on GL nodes with the Chandrashekar volume flux and no volume source
+ * (nsfr_set_source), for callers that must not allocate device memory: code
+ * running under a memory
  * manager that owns the whole device (a framework's caching allocator, an
  * application with a fixed memory budget) or code that cannot afford the
  * implicit device synchronisation of cudaMalloc/cudaFree.  It needs no
  * context and calls no cudaMalloc, cudaFree or other allocating routine; the
  * paper has no counterpart of this call.
- *   u     device [N_e][5][n^3] state
+ *   u     device [N_e][5][n^3] state (every buffer must be device memory of
+ *         the current device: anything else, NULL included, is NSFR_ERR_ARG
+ *         before anything runs)
  *   C     device [N_e][9][n^3] metric rows, J device [N_e][n^3] Jacobians,
  *   Cf    device [N_e][3][3][n^2] shared face rows (layouts of
  *         nsfr_get_metrics; e.g. copied once from a context)
@@ -338,7 +350,9 @@ nsfr_status nsfr_profile_read(nsfr_ctx* ctx, double* ms, long long* count);
  * needing more than that, 256 + 8 N_e (72 n^2 + 19 n^3) bytes, is rejected
  * with NSFR_ERR_ARG before anything runs.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
+ * current and keeps it for the process; make that first call before any
+ * stream capture, and make no call after cudaDeviceReset on that device (the
+ * kept address belongs to the context the reset destroyed).  All calls share
  * the one array and the last call's contents stay in it; the error word is
  * cleared at the start of every call.  Calls that overlap on the GPU (other
  * streams, other threads) race on the array: serialise them.  The call

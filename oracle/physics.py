@@ -1,4 +1,4 @@
-"""Euler physics: entropy variables, EC two-point flux, Roe dissipation.
+"""Euler physics: entropy variables, EC two-point fluxes, Roe dissipation.
 
 States U have shape (5, ...) = (rho, rho u, rho v, rho w, rho e); normals
 nvec have shape (3, ...) and need not be unit vectors (they are rows of the
@@ -134,6 +134,52 @@ def chandrashekar(UL, UR, nvec, gamma):
     return np.concatenate([F0[None], Fm, F4[None]], axis=0)
 
 
+def ranocha(UL, UR, nvec, gamma):
+    """Chandrashekar's flux with Ranocha's pressure terms, f_s(u_L, u_R) . n.
+
+    The paper's EC runs use Chandrashekar's flux "with Ranocha's pressure fix"
+    (Sec. "Results"; Ranocha and Gassner, Commun. Appl. Math. Comput. 2022).
+    Read here as Ranocha's EC/KEP flux (J. Sci. Comput. 2018), which keeps
+    Chandrashekar's mass flux and internal-energy term and replaces his pressure
+    average p_hat = rho_bar/(2 beta_bar) in the momentum flux by the arithmetic
+    mean p_bar, and the pressure work p_hat (u_bar . n) in the energy flux by the
+    product mean (p_L (u_R . n) + p_R (u_L . n))/2:
+      F_rho = rho_ln (u_bar . n)
+      F_m   = F_rho u_bar + p_bar n
+      F_E   = F_rho (1/(2(gamma-1) beta_ln) + (u_L . u_R)/2)
+              + (p_L (u_R . n) + p_R (u_L . n))/2.
+    Both pressure changes contribute rho_bar [[u]] . n to [[v]] . F, as
+    Chandrashekar's p_hat terms do, so the Tadmor shuffle still holds; with
+    constant u and p both give the pressure-equilibrium values p n and p u . n.
+    """
+    rL, uL, pL = primitive(UL, gamma)
+    rR, uR, pR = primitive(UR, gamma)
+    bL = rL / (2.0 * pL)
+    bR = rR / (2.0 * pR)
+    r_ln = log_mean(rL, rR)
+    b_ln = log_mean(bL, bR)
+    u_bar = 0.5 * (uL + uR)
+    p_bar = 0.5 * (pL + pR)
+    un = np.sum(u_bar * nvec, axis=0)
+    F0 = r_ln * un
+    Fm = F0 * u_bar + p_bar * nvec
+    uLuR = np.sum(uL * uR, axis=0)
+    work = 0.5 * (pL * np.sum(uR * nvec, axis=0) + pR * np.sum(uL * nvec, axis=0))
+    F4 = F0 * (1.0 / (2.0 * (gamma - 1.0) * b_ln) + 0.5 * uLuR) + work
+    return np.concatenate([F0[None], Fm, F4[None]], axis=0)
+
+
+TWO_POINT = ("chandrashekar", "ranocha")
+
+
+def two_point(vol_flux):
+    """The entropy-conserving two-point flux named by ``vol_flux`` (looked up by name at
+    call time, so that a test may replace a flux function of this module)."""
+    if vol_flux not in TWO_POINT:
+        raise ValueError(vol_flux)
+    return globals()[vol_flux]
+
+
 def _cabs(x):
     """|x| written so that complex-step derivatives follow the real branch."""
     return x * np.sign(_re(x))
@@ -230,15 +276,16 @@ def es_matrix_dissipation(UL, UR, nvec, gamma):
     return nn * np.concatenate([D0[None], Dm, D4[None]], axis=0)
 
 
-def numerical_flux(UL, UR, nvec, gamma, face_flux="ec"):
+def numerical_flux(UL, UR, nvec, gamma, face_flux="ec", vol_flux="chandrashekar"):
     """Face flux f*(u_L, u_R; n), n pointing from L to R.
 
+    The EC baseline is the volume's two-point flux (``vol_flux``).
     "ec": the EC two-point flux itself; "ec_roe": EC flux minus
     (1/2)|A_n|(u_R - u_L) (Roe dissipation added to the EC baseline);
     "ec_es": EC flux minus (1/2) R |Lambda| T R^T [[v]] (entropy-variable
     matrix dissipation, provably entropy dissipative).
     """
-    F = chandrashekar(UL, UR, nvec, gamma)
+    F = two_point(vol_flux)(UL, UR, nvec, gamma)
     if face_flux == "ec":
         return F
     if face_flux == "ec_roe":

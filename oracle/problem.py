@@ -12,12 +12,14 @@ from .operators1d import Ops1D
 
 
 class Problem:
-    def __init__(self, ctrl, shape, p, p_geo=None, c=0.0, gamma=1.4, face_flux="ec", nodes="gl"):
+    def __init__(self, ctrl, shape, p, p_geo=None, c=0.0, gamma=1.4, face_flux="ec", nodes="gl",
+                 vol_flux="chandrashekar"):
         self.p = p
         self.n = p + 1
         self.p_geo = p if p_geo is None else p_geo
         self.gamma = gamma
         self.face_flux = face_flux
+        self.vol_flux = vol_flux
         self.ops = Ops1D(p, c, nodes)
         self.mesh = geometry.StructuredMesh(*shape)
         self.geo = geometry.metric_terms(ctrl, self.p_geo, self.ops)
@@ -41,11 +43,12 @@ class Problem:
 
     # the scheme --------------------------------------------------------------
     def residual(self, U):
-        return residual.residual(U, self.C, self.nf, self.mesh, self.ops, self.gamma, self.face_flux)
+        return residual.residual(U, self.C, self.nf, self.mesh, self.ops, self.gamma, self.face_flux,
+                                 self.vol_flux)
 
     def dense_residual(self, U):
         return residual.dense_residual(U, self.C, self.nf, self.mesh, self.ops, self.gamma,
-                                       self.face_flux)
+                                       self.face_flux, self.vol_flux)
 
     def dudt(self, U):
         return mass.dudt_from_residual(self.residual(U), self.J, self.ops)

@@ -62,8 +62,9 @@ def face_states(U, ops, gamma):
     return Uf
 
 
-def volume_term(U, C, ops, gamma):
+def volume_term(U, C, ops, gamma, vol_flux="chandrashekar"):
     """Volume-volume block of Eq. NSFR, summed along lines (all ordered pairs)."""
+    fs = physics.two_point(vol_flux)
     n = ops.n
     R = np.zeros_like(U)
     wperp = np.outer(ops.w, ops.w)
@@ -76,14 +77,15 @@ def volume_term(U, C, ops, gamma):
             for b in range(n):
                 if b == a:
                     continue
-                F = physics.chandrashekar(ua, _take(U, b, d), 0.5 * (na + _take(Cd, b, d)), gamma)
+                F = fs(ua, _take(U, b, d), 0.5 * (na + _take(Cd, b, d)), gamma)
                 acc = acc + ops.S1[a, b] * F
             R[_index(R.ndim, a, d)] += wperp * acc
     return R
 
 
-def face_terms(U, C, nf, Uf, mesh, ops, gamma, face_flux="ec"):
+def face_terms(U, C, nf, Uf, mesh, ops, gamma, face_flux="ec", vol_flux="chandrashekar"):
     """Hybrid volume-face blocks and surface term of Eq. NSFR, line by line."""
+    fs = physics.two_point(vol_flux)
     n = ops.n
     R = np.zeros_like(U)
     wperp = np.outer(ops.w, ops.w)
@@ -96,22 +98,21 @@ def face_terms(U, C, nf, Uf, mesh, ops, gamma, face_flux="ec"):
             uf_nbr = Uf[d][1 - s][:, nb]
             nfs = nf[d][s]
             if s == 1:   # this element is the face's minus side
-                fstar = physics.numerical_flux(uf_own, uf_nbr, nfs, gamma, face_flux)
+                fstar = physics.numerical_flux(uf_own, uf_nbr, nfs, gamma, face_flux, vol_flux)
             else:
-                fstar = physics.numerical_flux(uf_nbr, uf_own, nfs, gamma, face_flux)
-            phi = [physics.chandrashekar(_take(U, a, d), uf_own,
-                                         0.5 * (_take(C[d], a, d) + nfs), gamma)
-                   for a in range(n)]
+                fstar = physics.numerical_flux(uf_nbr, uf_own, nfs, gamma, face_flux, vol_flux)
+            phi = [fs(_take(U, a, d), uf_own, 0.5 * (_take(C[d], a, d) + nfs), gamma) for a in range(n)]
             tphi = sum(t[b] * phi[b] for b in range(n))
             for a in range(n):
                 R[_index(R.ndim, a, d)] += sgn * wperp * t[a] * (phi[a] + fstar - tphi)
     return R
 
 
-def residual(U, C, nf, mesh, ops, gamma, face_flux="ec"):
+def residual(U, C, nf, mesh, ops, gamma, face_flux="ec", vol_flux="chandrashekar"):
     """R of Eq. NSFR (sum-factorised), so that (M_m + K_m) du/dt = -R."""
     Uf = face_states(U, ops, gamma)
-    return volume_term(U, C, ops, gamma) + face_terms(U, C, nf, Uf, mesh, ops, gamma, face_flux)
+    return (volume_term(U, C, ops, gamma, vol_flux)
+            + face_terms(U, C, nf, Uf, mesh, ops, gamma, face_flux, vol_flux))
 
 
 # ---------------------------------------------------------------------------
@@ -163,7 +164,7 @@ def hybrid_qtilde(ops, d):
     return Q
 
 
-def dense_residual(U, C, nf, mesh, ops, gamma, face_flux="ec"):
+def dense_residual(U, C, nf, mesh, ops, gamma, face_flux="ec", vol_flux="chandrashekar"):
     """Eq. NSFR assembled literally, element by element (small p only)."""
     n = ops.n
     nv, nfp = n ** 3, n ** 2
@@ -202,8 +203,7 @@ def dense_residual(U, C, nf, mesh, ops, gamma, face_flux="ec"):
                     Ch[:, :, sl] = np.einsum("kv,xev->xek", E[(dd, s)], Cv[d])
         A = QmQT[d]
         ii, jj = np.nonzero(A)
-        F = physics.chandrashekar(Uh[:, :, ii], Uh[:, :, jj],
-                                  0.5 * (Ch[:, :, ii] + Ch[:, :, jj]), gamma)
+        F = physics.two_point(vol_flux)(Uh[:, :, ii], Uh[:, :, jj], 0.5 * (Ch[:, :, ii] + Ch[:, :, jj]), gamma)
         h = np.zeros((5, ne, N), dtype=U.dtype)
         np.add.at(h, (slice(None), slice(None), ii), A[ii, jj] * F)
         R += h[:, :, :nv]
@@ -221,9 +221,9 @@ def dense_residual(U, C, nf, mesh, ops, gamma, face_flux="ec"):
             nbr = Uh[:, nb, nv + fo * nfp: nv + (fo + 1) * nfp]
             nvec = nf[d][s].reshape(3, ne, nfp)
             if s == 1:
-                fs = physics.numerical_flux(own, nbr, nvec, gamma, face_flux)
+                fs = physics.numerical_flux(own, nbr, nvec, gamma, face_flux, vol_flux)
             else:
-                fs = physics.numerical_flux(nbr, own, nvec, gamma, face_flux)
+                fs = physics.numerical_flux(nbr, own, nvec, gamma, face_flux, vol_flux)
             sgn = 1.0 if s == 1 else -1.0
             R += np.einsum("kv,k,xek->xev", E[(d, s)], np.diag(Wf) * sgn, fs)
     return R.reshape(U.shape)

@@ -44,7 +44,8 @@ def tensor3(A, X):
 class UncollocatedProblem:
     """One structured periodic mesh; solution degree p on LGL nodes, N_q GL points."""
 
-    def __init__(self, ctrl, shape, p, nq=None, p_geo=None, c=0.0, gamma=1.4, face_flux="ec"):
+    def __init__(self, ctrl, shape, p, nq=None, p_geo=None, c=0.0, gamma=1.4, face_flux="ec",
+                 vol_flux="chandrashekar"):
         n = p + 1
         nq = n if nq is None else nq
         if nq < n:
@@ -52,6 +53,7 @@ class UncollocatedProblem:
         self.p, self.n, self.nq = p, n, nq
         self.p_geo = p if p_geo is None else p_geo
         self.gamma, self.face_flux, self.c = gamma, face_flux, float(c)
+        self.vol_flux = vol_flux
         xs, _ = quadrature.gauss_lobatto(n)
         xq, wq = quadrature.gauss_legendre(nq)
         self.xs, self.xq, self.wq = xs, xq, wq
@@ -112,7 +114,8 @@ class UncollocatedProblem:
         """R^ = chi^T R_q; R_q the collocated line-wise residual of u~ on the GL points
         (its face states t . v(u~) equal l_f v~^ because Pi chi = I)."""
         _, Uq = self.projected(U)
-        Rq = residual.residual(Uq, self.C, self.nf, self.mesh, self.qops, self.gamma, self.face_flux)
+        Rq = residual.residual(Uq, self.C, self.nf, self.mesh, self.qops, self.gamma, self.face_flux,
+                               self.vol_flux)
         return tensor3(self.chi.T, Rq)
 
     def dudt(self, U):

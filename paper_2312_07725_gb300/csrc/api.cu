@@ -351,7 +351,9 @@ static nsfr_status setup_common(const double* grid_nodes, int nx, int ny, int nz
   if (!out) return NSFR_ERR_ARG;
   *out = nullptr;
   if (!grid_nodes || nx < 1 || ny < 1 || nz < 1 || p < 1 || p > 7 || p_geo < 1 || p_geo > p || !(gamma > 1.0) ||
-      vol_flux != NSFR_FLUX_CHANDRASHEKAR || face_flux < NSFR_FACE_EC || face_flux > NSFR_FACE_EC_ES ||
+      (vol_flux != NSFR_FLUX_CHANDRASHEKAR && vol_flux != NSFR_FLUX_RANOCHA) ||
+      (vol_flux == NSFR_FLUX_RANOCHA && precision != NSFR_FP64) || face_flux < NSFR_FACE_EC ||
+      face_flux > NSFR_FACE_EC_ES ||
       (precision != NSFR_FP64 && precision != NSFR_FP32_BULK && precision != NSFR_FP32_BULK_FF) || (nodes != NSFR_NODES_GL && nodes != NSFR_NODES_LGL) ||
       !std::isfinite(c) || c < 0.0)
     return NSFR_ERR_ARG;
@@ -561,6 +563,8 @@ nsfr_status nsfr_vjp(nsfr_ctx* ctx, const double* u, const double* dudt_bar, dou
   if (ctx->precision != NSFR_FP64 || ctx->uncol)
     return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp needs a collocated FP64 context");
   if (ctx->face_flux != NSFR_FACE_EC) return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp supports the EC face flux");
+  if (ctx->vol_flux != NSFR_FLUX_CHANDRASHEKAR)
+    return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp supports the Chandrashekar volume flux");
   if (ctx->src_on && x_bar)
     return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp with x_bar does not differentiate a volume source");
   if (!u || !dudt_bar || !u_bar) return fail(ctx, NSFR_ERR_ARG, "NULL buffer");

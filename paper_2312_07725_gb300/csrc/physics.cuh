@@ -172,6 +172,44 @@ __device__ __forceinline__ void ec_flux(const Rec& A, const Rec& B, double n0, d
   ec_flux_l(A, B, n0, n1, n2, K, RecLogs{A}, RecLogs{B}, F);
 }
 
+// Chandrashekar's flux with Ranocha's pressure terms (Sec. "Results": the EC
+// runs use Chandrashekar's flux with Ranocha's pressure fix), F = f_s(A, B) . n:
+// the same mass flux and internal-energy term, the arithmetic pressure mean in
+// the momentum flux and the cross product mean as the pressure work,
+//   F_m = F_rho u_bar + (p_a + p_b)/2 n,
+//   F_E = F_rho (1/(2(gamma-1) beta_ln) + u_a . u_b / 2) + (p_a u_b.n + p_b u_a.n)/2.
+// pa, pb are the two pressures (rho / (2 beta)); with the half velocities h of
+// the records u_a . u_b / 2 = 2 h_a . h_b and u_b . n / 2 = u_bar . n - h_a . n.
+template <class LA, class LB>
+__device__ __forceinline__ void ranocha_flux_l(const Rec& A, const Rec& B, double pa, double pb, double n0,
+                                               double n1, double n2, const OpsGL& K, const LA& la, const LB& lb,
+                                               double F[5]) {
+  const double sr = A.r + B.r, dr = A.r - B.r;
+  const double s2 = A.b2 + B.b2, d2 = A.b2 - B.b2;
+  const double rb2 = rcp_full(s2);
+  const double rr = rcp_newton1(sr);
+  const double fr = dr * rr, fb = d2 * rb2;
+  const double ur = fr * fr, ub = fb * fb;
+  double rln, ibg;
+  if (lm_small(ur)) rln = sr * horner4(K.gh, ur);
+  else rln = dr / (la.lr() - lb.lr());
+  if (lm_small(ub)) ibg = horner4(K.f4g, ub) * rb2;
+  else ibg = K.inv_gm1 * (la.lb() - lb.lb()) / d2;
+  const double v0 = A.u0 + B.u0, v1 = A.u1 + B.u1, v2 = A.u2 + B.u2;  // u_bar
+  const double un = fma(v0, n0, fma(v1, n1, v2 * n2));
+  const double an = fma(A.u0, n0, fma(A.u1, n1, A.u2 * n2));     // u_a . n / 2
+  const double hab = fma(A.u0, B.u0, fma(A.u1, B.u1, A.u2 * B.u2));  // u_a . u_b / 4
+  const double Fr = rln * un;
+  const double pm = 0.5 * (pa + pb);
+  F[0] = Fr;
+  F[1] = fma(Fr, v0, pm * n0);
+  F[2] = fma(Fr, v1, pm * n1);
+  F[3] = fma(Fr, v2, pm * n2);
+  F[4] = fma(Fr, fma(2.0, hab, ibg), fma(pa, un - an, pb * an));
+}
+
+__device__ __forceinline__ double pressure_of(const Rec& a) { return a.r * rcp_full(a.b2); }
+
 // D = |A_n| (u_R - u_L): Roe-averaged flux Jacobian along n (non-unit),
 // applied through its eigen-decomposition (acoustic waves q -+ a, entropy
 // and shear waves q), scaled by |n|.
@@ -254,11 +292,15 @@ __device__ __forceinline__ void es_dissipation(const Rec& L, const Rec& R, doubl
   D[4] = nn * (c1 * (H - a * qn) + c2 * 0.5 * q2 + c5 * (H + a * qn) + cs * (u0 * P0 + u1 * P1 + u2 * P2));
 }
 
-// f*(u~_L, u~_R; n): the EC flux, minus (1/2)|A_n|(u_R - u_L) (Roe) or minus
+// f*(u~_L, u~_R; n): the EC flux (Chandrashekar's or, vf = NSFR_FLUX_RANOCHA,
+// with Ranocha's pressure terms), minus (1/2)|A_n|(u_R - u_L) (Roe) or minus
 // (1/2) R |Lambda| T R^T [[v]] (entropy-variable matrix dissipation).
 __device__ __forceinline__ void face_flux(const Rec& L, const Rec& R, double n0, double n1, double n2,
-                                          const OpsGL& K, int kind, double F[5]) {
-  ec_flux(L, R, n0, n1, n2, K, F);
+                                          const OpsGL& K, int kind, int vf, double F[5]) {
+  if (vf == NSFR_FLUX_RANOCHA)
+    ranocha_flux_l(L, R, pressure_of(L), pressure_of(R), n0, n1, n2, K, RecLogs{L}, RecLogs{R}, F);
+  else
+    ec_flux(L, R, n0, n1, n2, K, F);
   if (kind == NSFR_FACE_EC_ROE || kind == NSFR_FACE_EC_ES) {
     double D[5];
     if (kind == NSFR_FACE_EC_ROE) roe_dissipation(L, R, n0, n1, n2, K.gamma, D);

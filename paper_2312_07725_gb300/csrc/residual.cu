@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
 template <int N>
 __global__ void __launch_bounds__(256) face_flux_kernel(const double* __restrict__ face,
                                                         const double* __restrict__ nf_s, OpsGL ops, int nx, int ny,
-                                                        int nz, int e_beg, int e_end, int face_kind,
+                                                        int nz, int e_beg, int e_end, int face_kind, int vf,
                                                         double* __restrict__ fstar) {
   constexpr int NFP = N * N;
   const int t = e_beg * 3 * NFP + blockIdx.x * blockDim.x + threadIdx.x;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const double* __restrict
   const Rec R = load_rec(face + (((size_t)enb * 6 + 2 * d) * NSFR_NFIELD) * NFP + node, NFP);
   const double* nf = nf_s + (size_t)ed * 3 * NFP + node;
   double F[5];
-  face_flux(L, R, nf[0], nf[NFP], nf[2 * NFP], ops, face_kind, F);
+  face_flux(L, R, nf[0], nf[NFP], nf[2 * NFP], ops, face_kind, vf, F);
   double* o = fstar + (size_t)ed * 5 * NFP + node;
 #pragma unroll
   for (int k = 0; k < 5; ++k) o[k * NFP] = F[k];
@@ -248,10 +248,20 @@ __device__ void uncol_epilogue(double* X, double* Y, int nel, int e0, const OpsG
   }
 }
 
+// Two-point flux of the line phase: Chandrashekar's (VF = NSFR_FLUX_CHANDRASHEKAR)
+// or with Ranocha's pressure terms, whose node pressures ride in the records'
+// |u|^2/4 slot (that flux has no use for |u|^2).
+template <int VF, class LA, class LB>
+__device__ __forceinline__ void vol_flux(const Rec& A, const Rec& B, double n0, double n1, double n2,
+                                         const OpsGL& K, const LA& la, const LB& lb, double F[5]) {
+  if (VF == NSFR_FLUX_RANOCHA) ranocha_flux_l(A, B, A.qq, B.qq, n0, n1, n2, K, la, lb, F);
+  else ec_flux_l(A, B, n0, n1, n2, K, la, lb, F);
+}
+
 // The stage state itself is not read: its node records come from the
 // face-state pass (nrec), so the epilogue may write the next stage state over
 // the buffer the stage started from.
-template <int N>
+template <int N, int VF>
 __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(const double* __restrict__ nrec,
                                                                 const double* __restrict__ metric_s,
                                                                 const double* __restrict__ nf_s,
@@ -276,6 +286,15 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
     const int le = t / (6 * NV);
     if (e0 + le >= ne) continue;
     P[t] = nrec[((size_t)(e0 + le) * NSFR_NFIELD) * NV + t % (6 * NV)];
+  }
+  if (VF == NSFR_FLUX_RANOCHA) {
+    // the pressure rho / (2 beta) in place of |u|^2/4
+    __syncthreads();
+    for (int t = threadIdx.x; t < epb * NV; t += blockDim.x) {
+      if (e0 + t / NV >= ne) continue;
+      double* pe = P + (size_t)(t / NV) * 6 * NV + t % NV;
+      pe[P_QQ * NV] = pe[P_RHO * NV] * rcp_full(pe[P_B2 * NV]);
+    }
   }
   // metric rows of direction d scaled by w_perp / 2 (scaled_rows_kernel):
   // w_perp (the weights of the two other directions) is constant along a line
@@ -314,8 +333,8 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
       for (int b = a + 1; b < N; ++b) {
         const Rec B = load_rec6(Pe + b * stride, NV);
         double F[5];
-        ec_flux_l(A, B, na0 + Me[b * stride], na1 + Me[NV + b * stride], na2 + Me[2 * NV + b * stride], ops,
-                  PtrLogs{Le + a * stride, NV}, PtrLogs{Le + b * stride, NV}, F);
+        vol_flux<VF>(A, B, na0 + Me[b * stride], na1 + Me[NV + b * stride], na2 + Me[2 * NV + b * stride], ops,
+                     PtrLogs{Le + a * stride, NV}, PtrLogs{Le + b * stride, NV}, F);
         const double c = ops.S1[a * N + b];
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -344,7 +363,8 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
         continue;
       }
       const double f0 = nf[0], f1 = nf[NFP], f2 = nf[2 * NFP];
-      const Rec Fo = load_rec6(fo, NFP);
+      Rec Fo = load_rec6(fo, NFP);
+      if (VF == NSFR_FLUX_RANOCHA) Fo.qq = pressure_of(Fo);
       const double* t = s ? ops.tp : ops.tm;
       const double h0 = 0.5 * f0, h1 = 0.5 * f1, h2 = 0.5 * f2;
       double tphi[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -352,8 +372,8 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
       for (int a = 0; a < N; ++a) {
         const Rec A = load_rec6(Pe + a * stride, NV);
         double F[5];
-        ec_flux_l(A, Fo, Me[a * stride] + h0, Me[NV + a * stride] + h1, Me[2 * NV + a * stride] + h2, ops,
-                  PtrLogs{Le + a * stride, NV}, PtrLogs{fo + P_LRHO * NFP, NFP}, F);
+        vol_flux<VF>(A, Fo, Me[a * stride] + h0, Me[NV + a * stride] + h1, Me[2 * NV + a * stride] + h2, ops,
+                     PtrLogs{Le + a * stride, NV}, PtrLogs{fo + P_LRHO * NFP, NFP}, F);
         const double ta = t[a], swt = sw * ta;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -461,7 +481,7 @@ cudaError_t launch_face_flux_n(nsfr_ctx* ctx, cudaStream_t s) {
   const int grid = (int)((total + 255) / 256);
   nsfr_prof_begin(ctx, 8, s);
   face_flux_kernel<N><<<grid, 256, 0, s>>>(ctx->face, ctx->nf_s, ctx->ops, ctx->nx, ctx->ny, ctx->nz, eb, ee,
-                                           ctx->face_flux, ctx->fstar);
+                                           ctx->face_flux, ctx->vol_flux, ctx->fstar);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
   return cudaGetLastError();
@@ -476,14 +496,15 @@ cudaError_t launch_volume_n(nsfr_ctx* ctx, const double* u, double* out, int epi
   const int grid = (ee - eb + epb - 1) / epb;
   if (grid <= 0) return cudaSuccess;
   const size_t smem = (size_t)epb * (6 + 9 + 15) * NV * sizeof(double);
-  cudaError_t err = cudaFuncSetAttribute(volume_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = ctx->vol_flux == NSFR_FLUX_RANOCHA ? volume_kernel<N, NSFR_FLUX_RANOCHA>
+                                                 : volume_kernel<N, NSFR_FLUX_CHANDRASHEKAR>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   RkArgs r = rk ? *rk : RkArgs{};
   nsfr_prof_begin(ctx, 2, s);
-  volume_kernel<N><<<grid, vol_threads(N), smem, s>>>(ctx->nrec, ctx->metric_s, ctx->nf_s, ctx->face,
-                                                      ctx->fstar, ctx->invwj, epi == EPI_RAW ? nullptr : ctx->src_on,
-                                                      ctx->ops, ctx->nx, ctx->ny, ctx->nz, eb, ee, epi, r, out,
-                                                      ctx->flag);
+  kern<<<grid, vol_threads(N), smem, s>>>(ctx->nrec, ctx->metric_s, ctx->nf_s, ctx->face, ctx->fstar, ctx->invwj,
+                                          epi == EPI_RAW ? nullptr : ctx->src_on, ctx->ops, ctx->nx, ctx->ny,
+                                          ctx->nz, eb, ee, epi, r, out, ctx->flag);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
   return cudaGetLastError();
@@ -595,6 +616,17 @@ static __device__ __align__(256) unsigned char g_static_scratch[NSFR_STATIC_SCRA
 namespace {
 std::mutex g_static_mu;
 void* g_static_addr[256] = {nullptr};  // device address of g_static_scratch, per device ordinal
+
+// p is device (or managed) memory of device dev; host memory, memory of another
+// device and unknown pointers are refused before anything is launched
+bool static_dev_ptr(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
 }  // namespace
 
 extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, const double* J, const double* Cf,
@@ -613,6 +645,9 @@ extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, co
   if (need > NSFR_STATIC_SCRATCH_BYTES || ne > (size_t)0x7fffffff) return NSFR_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return NSFR_ERR_CUDA;
+  if (!static_dev_ptr(u, dev) || !static_dev_ptr(C, dev) || !static_dev_ptr(J, dev) || !static_dev_ptr(Cf, dev) ||
+      !static_dev_ptr(dudt, dev))
+    return NSFR_ERR_ARG;
   unsigned char* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_static_mu);

@@ -18,9 +18,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnsfr.so")
 
 NSFR_OK = 0
+NSFR_ERR_ARG = -1
 STATUS = {0: "NSFR_OK", -1: "NSFR_ERR_ARG", -2: "NSFR_ERR_MESH", -3: "NSFR_ERR_CUDA",
           -4: "NSFR_ERR_NONPHYSICAL", -5: "NSFR_ERR_OOM", -6: "NSFR_ERR_STATE"}
 FACE_FLUX = {"ec": 0, "ec_roe": 1, "ec_es": 2}
+VOL_FLUX = {"chandrashekar": 0, "ranocha": 1}
 PRECISION = {"fp64": 0, "fp32_bulk": 1, "fp32_bulk_ff": 2}
 NODES = {"gl": 0, "lgl": 1}
 SOURCES = {"none": 0, "manufactured": 1}
@@ -133,8 +135,21 @@ def _stream(stream):
 def residual_static(u, C, J, Cf, shape, p, c=0.0, face_flux="ec", gamma=1.4, dudt=None, stream=None):
     """du/dt through nsfr_residual_static: no context and no device allocation by the
     library (its working memory is a fixed array inside libnsfr.so).  All buffers
-    are caller-owned device tensors; returns ``dudt``."""
+    are caller-owned contiguous float64 CUDA tensors on the current device, sized for
+    the mesh (u and dudt N_e*5*n^3, C N_e*9*n^3, J N_e*n^3, Cf N_e*9*n^2 entries);
+    anything else raises NSFRError with NSFR_ERR_ARG before the library is called.
+    Returns ``dudt``."""
+    import torch
     nx, ny, nz = shape
+    ne, n = nx * ny * nz, p + 1
+    want = {"u": (u, ne * 5 * n ** 3), "C": (C, ne * 9 * n ** 3), "J": (J, ne * n ** 3),
+            "Cf": (Cf, ne * 9 * n * n), "dudt": (dudt, ne * 5 * n ** 3)}
+    dev = torch.cuda.current_device()
+    for name, (x, size) in want.items():
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.device.index == dev and x.dtype == torch.float64
+                and x.is_contiguous() and x.numel() == size):
+            raise NSFRError(NSFR_ERR_ARG, f"nsfr_residual_static: {name} must be a contiguous float64 tensor "
+                                          f"of {size} entries on cuda:{dev}")
     st = lib().nsfr_residual_static(_ptr(u), _ptr(C), _ptr(J), _ptr(Cf), nx, ny, nz, p, float(c),
                                     FACE_FLUX[face_flux], float(gamma), _ptr(dudt), _stream(stream))
     if st != NSFR_OK:
@@ -163,9 +178,10 @@ class Solver:
     """One NSFR-EC discretisation (mesh, p, c, fluxes, precision) on the current device."""
 
     def __init__(self, grid_nodes, shape, p, p_geo=None, c=0.0, face_flux="ec", gamma=1.4,
-                 precision="fp64", nodes="gl", nq=None):
+                 precision="fp64", nodes="gl", nq=None, vol_flux="chandrashekar"):
         """``nodes``: "gl" or "lgl" collocated; with ``nq`` (>= p+1) the uncollocated scheme:
-        solution on the LGL nodes, nq GL quadrature points per direction."""
+        solution on the LGL nodes, nq GL quadrature points per direction.  ``vol_flux``:
+        "chandrashekar" or "ranocha" (Chandrashekar's flux with Ranocha's pressure terms)."""
         self._lib = lib()
         nx, ny, nz = shape
         pg = p if p_geo is None else p_geo
@@ -173,19 +189,22 @@ class Solver:
         self.nv = self.n ** 3
         self.n_el = nx * ny * nz
         self.c, self.gamma, self.face_flux, self.precision, self.nodes = c, gamma, face_flux, precision, nodes
+        self.vol_flux = vol_flux
         self._keep = grid_nodes
         h = ctypes.c_void_p()
         self.nq = nq
         npt = self.n if nq is None else int(nq)
         self.nqv, self.nqf = npt ** 3, npt ** 2  # quadrature points per element / per face
         if nq is None:
-            st = self._lib.nsfr_setup(_ptr(grid_nodes), nx, ny, nz, pg, p, float(c), 0, FACE_FLUX[face_flux],
+            st = self._lib.nsfr_setup(_ptr(grid_nodes), nx, ny, nz, pg, p, float(c), VOL_FLUX[vol_flux],
+                                      FACE_FLUX[face_flux],
                                       float(gamma), PRECISION[precision], NODES[nodes], ctypes.byref(h))
         else:
             if precision != "fp64":
                 raise ValueError("the uncollocated scheme is FP64 only")
-            st = self._lib.nsfr_setup_uncollocated(_ptr(grid_nodes), nx, ny, nz, pg, p, int(nq), float(c), 0,
-                                                   FACE_FLUX[face_flux], float(gamma), ctypes.byref(h))
+            st = self._lib.nsfr_setup_uncollocated(_ptr(grid_nodes), nx, ny, nz, pg, p, int(nq), float(c),
+                                                   VOL_FLUX[vol_flux], FACE_FLUX[face_flux], float(gamma),
+                                                   ctypes.byref(h))
         if st != NSFR_OK:
             raise NSFRError(st, "nsfr_setup failed")
         self._h = h

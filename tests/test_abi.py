@@ -31,6 +31,7 @@ def test_header_and_binding_agree_on_enums_and_kernel_ids():
     assert nsfr.PRECISION == {"fp64": enums["NSFR_FP64"], "fp32_bulk": enums["NSFR_FP32_BULK"],
                               "fp32_bulk_ff": enums["NSFR_FP32_BULK_FF"]}
     assert nsfr.NODES == {"gl": enums["NSFR_NODES_GL"], "lgl": enums["NSFR_NODES_LGL"]}
+    assert nsfr.VOL_FLUX == {"chandrashekar": enums["NSFR_FLUX_CHANDRASHEKAR"], "ranocha": enums["NSFR_FLUX_RANOCHA"]}
     assert nsfr.SOURCES == {"none": enums["NSFR_SOURCE_NONE"], "manufactured": enums["NSFR_SOURCE_MANUFACTURED"]}
     assert {v: k for k, v in nsfr.STATUS.items()} == {k: v for k, v in enums.items() if k.startswith("NSFR_OK")
                                                       or k.startswith("NSFR_ERR")}
@@ -63,6 +64,11 @@ def test_setup_rejects_bad_arguments_without_touching_a_gpu():
         assert st == -1
         assert not h.value
     assert lib.nsfr_setup(None, 1, 1, 1, 1, 1, 0.0, 0, 0, 1.4, 0, 0, ctypes.byref(h)) == -1
+    # unknown volume flux; Ranocha's pressure terms with an FP32-bulk precision
+    for vf, prec in ((2, 0), (-1, 0), (1, 1), (1, 2)):
+        st = lib.nsfr_setup(ctypes.cast(buf, ctypes.c_void_p), 1, 1, 1, 1, 1, 0.0, vf, 0, 1.4, prec, 0,
+                            ctypes.byref(h))
+        assert st == -1 and not h.value
     assert lib.nsfr_residual(None, None, None, None) == -1
     assert lib.nsfr_last_error(None) == b"NULL context"
     lib.nsfr_destroy(None)
