@@ -344,11 +344,12 @@ nsfr_status nsfr_profile_read(nsfr_ctx* ctx, double* ms, long long* count);
  *   nx, ny, nz, p, c, face_flux, gamma   as in nsfr_setup (FP64 only)
  *   dudt  device [N_e][5][n^3] output
  * Its working memory (face states, node records, face fluxes, scaled metric
- * rows, 1/(wJ), an error word) is a fixed 16 MiB array inside the library
- * (NSFR_STATIC_SCRATCH_BYTES), which every
+ * rows, the volume kernel's pair table, 1/(wJ), an error word) is a fixed
+ * 16 MiB array inside the library (NSFR_STATIC_SCRATCH_BYTES), which every
  * GPU that loads the library keeps until the process exits.  A problem
- * needing more than that, 256 + 8 N_e (72 n^2 + 19 n^3) bytes, is rejected
- * with NSFR_ERR_ARG before anything runs.  The first call on a device looks
+ * needing more than that, 256 + N_e (36 n^4 + 260 n^3 + 576 n^2) bytes
+ * (about 470 elements at p = 3, 240 at p = 4), is rejected with
+ * NSFR_ERR_ARG before anything runs.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
  * current and keeps it for the process; make that first call before any
  * stream capture, and make no call after cudaDeviceReset on that device (the
@@ -390,6 +391,19 @@ typedef enum {
   NSFR_FN_EXP_FF = 5
 } nsfr_fn;
 nsfr_status nsfr_math_eval(int fn, const double* x, double* y, long long n, void* stream);
+
+/*
+ * nsfr_fma_probe -- a throughput probe of the FP64 (fp32 = 0) or FP32
+ * (fp32 = 1) fused multiply-add pipe, the measured denominator of the
+ * kernels' ALU rooflines (the paper has no counterpart).  Launches `blocks`
+ * CTAs of 256 threads, each thread running 8 independent chains
+ * x <- x a + b for `iters` steps, asynchronously on `stream`; the caller
+ * times the launch (CUDA events on the same stream) and divides *fmas, the
+ * number of multiply-adds it performs, by the time.  sink: device buffer of
+ * two doubles (written; keeps the chains live).  NSFR_ERR_ARG for iters or
+ * blocks < 1 or a NULL or host pointer.  No context is needed.
+ */
+nsfr_status nsfr_fma_probe(int fp32, long long iters, int blocks, double* sink, long long* fmas, void* stream);
 
 /* nsfr_kernel_launches -- kernels this context has launched so far. */
 long long nsfr_kernel_launches(const nsfr_ctx* ctx);

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnsfr.so")
-SOURCES = ["api.cu", "ops1d.cpp", "geometry.cu", "residual.cu", "residual_bulk.cu", "reduce.cu", "vjp.cu", "mathfn.cu", "projection.cu", "source.cu"]
+SOURCES = ["api.cu", "ops1d.cpp", "geometry.cu", "residual.cu", "residual_bulk.cu", "reduce.cu", "vjp.cu", "mathfn.cu", "projection.cu", "source.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,6 +29,8 @@ def _compile(src, verbose_ptxas=False):
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj, "-O3", "-std=c++17", "-lineinfo",
            "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC] + ARCH
+    # extra definitions for measuring a variant, e.g. NSFR_NVCC_DEFINES="-DNSFR_VOL_STAGE_TMA=0"
+    cmd += [f for f in os.environ.get("NSFR_NVCC_DEFINES", "").split() if f.startswith("-D")]
     if src.endswith(".cpp"):
         cmd += ["-x", "cu"]
     if verbose_ptxas:

@@ -56,7 +56,7 @@ void prof_free(nsfr_ctx* c) {
 
 void free_all(nsfr_ctx* c) {
   double* dbl[] = {c->ctrl, c->metric, c->J, c->invwj, c->wj, c->nfp_plus, c->xyz, c->face, c->nrec, c->fstar,
-                   c->metric_s, c->nf_s, c->uq,
+                   c->metric_s, c->nf_s, c->pair_rows, c->uq,
                    c->ustage, c->acc, c->rtmp, c->hbuf_in, c->hbuf_out, c->red,
                    c->vjp_fown, c->vjp_fnbr, c->vjp_nfbar, c->vjp_mbar, c->vjp_jbar, c->src};
   for (double* p : dbl)
@@ -93,6 +93,7 @@ nsfr_status read_flag(nsfr_ctx* ctx, cudaStream_t s) {
   if (f) {
     CK(cudaMemsetAsync(ctx->flag, 0, sizeof(int), s), "cudaMemsetAsync(flag)");
     CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (f & 4) return fail(ctx, NSFR_ERR_CUDA, "a kernel's bounded wait for its staged data timed out");
     if (f & 2) return fail(ctx, NSFR_ERR_MESH, "non-positive Jacobian at a GL node");
     return fail(ctx, NSFR_ERR_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or NaN) met on the device");
   }
@@ -400,6 +401,8 @@ static nsfr_status setup_common(const double* grid_nodes, int nx, int ny, int nz
             cudaMallocHost((void**)&ctx->flag_host, sizeof(int)) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->umax_host, sizeof(unsigned long long)) == cudaSuccess;
   if (ok && ctx->uncol && ctx->n == ctx->ns) ok = dalloc(&ctx->uq, ne * 5 * nv) == cudaSuccess;
+  if (ok && precision == NSFR_FP64)
+    ok = dalloc(&ctx->pair_rows, nsfr_pair_rows_count(ctx->n, ctx->ne)) == cudaSuccess;
   if (ok && precision != NSFR_FP64)
     ok = dalloc(&ctx->metric32, ne * 18 * nv) == cudaSuccess && dalloc(&ctx->nfp_plus32, ne * 18 * nfp) == cudaSuccess &&
          dalloc(&ctx->invwj32, ne * nv) == cudaSuccess;

@@ -121,6 +121,7 @@ struct nsfr_ctx {
   double* nfp_plus = nullptr; // [ne][3][3][nfp]
   double* metric_s = nullptr; // [ne][9][nv] metric rows scaled by w_perp / 2
   double* nf_s = nullptr;     // [ne][3][3][nfp] face rows scaled by w_perp
+  double* pair_rows = nullptr; // [ne][3][n(n-1)/2 + 2n][3][nfp] averaged metric rows of the line pairs (FP64 contexts)
   float* nfp_plus32 = nullptr; // [ne][3][6][nfp] float-float w_perp C_f (FP32-bulk contexts)
   float* invwj32 = nullptr;    // [ne][nv] (FP32-bulk contexts)
   double* xyz = nullptr;      // [ne][3][nv]
@@ -187,8 +188,11 @@ cudaError_t nsfr_launch_source(nsfr_ctx* ctx, double t, cudaStream_t s);
 cudaError_t nsfr_launch_projection(nsfr_ctx* ctx, const double* u, cudaStream_t s);
 // uncollocated with square chi: u_q = chi u^ into ctx->uq (projection.cu)
 cudaError_t nsfr_launch_interp_square(nsfr_ctx* ctx, const double* u, cudaStream_t s);
-// w_perp-scaled metric and face rows (after the metric terms change)
+// w_perp-scaled metric and face rows and, where the context has one, the volume
+// kernel's pair table (after the metric terms change)
 cudaError_t nsfr_launch_scaled_rows(nsfr_ctx* ctx, cudaStream_t s);
+// doubles of the pair table of ne elements with n points per direction
+size_t nsfr_pair_rows_count(int n, int ne);
 // numerical flux of every face once, from the face states (after nsfr_launch_face_states)
 cudaError_t nsfr_launch_face_flux(nsfr_ctx* ctx, cudaStream_t s);
 // acc = u0 + bdt k, k <- u0 + adt k over the whole state (the first RK stage)

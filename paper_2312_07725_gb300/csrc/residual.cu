@@ -20,9 +20,16 @@
 //     epilogue applies the weight-adjusted inverse (Eq. weight-adj ESFR mass,
 //     Pi~^T, 1/(w J), Pi~, each a 1D contraction per direction) and either
 //     stores du/dt or performs the RK stage update in place.
+#include "async_copy.cuh"
 #include "kernel_common.cuh"
 #include "mathfn.cuh"
 #include "physics.cuh"
+
+// stage the volume kernel's node records with bulk asynchronous copies (1) or a
+// plain load loop (0)
+#ifndef NSFR_VOL_STAGE_TMA
+#define NSFR_VOL_STAGE_TMA 1
+#endif
 
 namespace {
 using namespace nsfr_k;
@@ -258,13 +265,17 @@ __device__ __forceinline__ void vol_flux(const Rec& A, const Rec& B, double n0, 
   else ec_flux_l(A, B, n0, n1, n2, K, la, lb, F);
 }
 
+// Rows of the pair table pm of one element and direction: the n(n-1)/2 volume
+// pairs a < b in the line phase's loop order, then the hybrid rows s n + a of
+// node a and side s.  pm is [ne][3 d][NPP][3 comps][n^2 lines].
+__host__ __device__ constexpr int pair_rows(int n) { return n * (n - 1) / 2 + 2 * n; }
+
 // The stage state itself is not read: its node records come from the
 // face-state pass (nrec), so the epilogue may write the next stage state over
 // the buffer the stage started from.
 template <int N, int VF>
 __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(const double* __restrict__ nrec,
-                                                                const double* __restrict__ metric_s,
-                                                                const double* __restrict__ nf_s,
+                                                                const double* __restrict__ pm,
                                                                 const double* __restrict__ face,
                                                                 const double* __restrict__ fstar,
                                                                 const double* __restrict__ invwj,
@@ -272,69 +283,93 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
                                                                 int ny, int nz, int e_beg, int ne, int epi,
                                                                 RkArgs rk, double* out, int* flag) {
   // elements e_beg .. ne-1 (the whole mesh's neighbours stay reachable)
-  constexpr int NV = N * N * N, NFP = N * N, NL = 3 * NFP;
-  extern __shared__ double sm[];
+  constexpr int NV = N * N * N, NFP = N * N, NL = 3 * NFP, NPP = pair_rows(N);
+  extern __shared__ __align__(128) double sm[];
   const int epb = blockDim.x / NL;
   const int e0 = e_beg + blockIdx.x * epb;
-  double* P = sm;                      // [epb][6][NV] node records (the logs stay in nrec)
-  double* Ms = P + (size_t)epb * 6 * NV;  // [epb][9][NV] metric rows / 2
-  double* Ra = Ms + (size_t)epb * 9 * NV;  // [epb][3][5][NV] line sums, one slab per direction
+  const int nel = min(epb, ne - e0);
+  double* P = sm;                          // [epb][6][NV] node records (the logs stay in nrec)
+  double* Ra = P + (size_t)epb * 6 * NV;   // [epb][3][5][NV] line sums, one slab per direction
   double* Rs = P;                          // [epb][5][NV] residual (after the line phase)
 
-  // prologue: node records (fields rho .. |u|^2/4) and half metric rows of the block's elements
+  // prologue: node records (fields rho .. |u|^2/4) of the block's elements
+#if NSFR_VOL_STAGE_TMA
+  // one bulk copy per element: the six fields are contiguous in nrec (48 NV
+  // bytes at a 64 NV-byte element stride, both multiples of 16)
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    nsfr_async::mbar_init(&bar, 1);
+    nsfr_async::mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    constexpr uint32_t bytes = 6 * NV * sizeof(double);
+    nsfr_async::mbar_arrive_expect_tx(&bar, bytes * nel);
+    for (int le = 0; le < nel; ++le)
+      nsfr_async::bulk_g2s(P + (size_t)le * 6 * NV, nrec + (size_t)(e0 + le) * NSFR_NFIELD * NV, bytes, &bar);
+  }
+  for (int t = threadIdx.x; t < epb * 15 * NV; t += blockDim.x) Ra[t] = 0.0;
+  const bool arrived = nsfr_async::mbar_wait_bounded(&bar, 0);
+  if (__syncthreads_or(!arrived)) {
+    // the copies did not complete in time: report it, give them one more
+    // bounded wait and leave without using the buffer
+    if (threadIdx.x == 0) atomicOr(flag, NSFR_FLAG_WAIT_TIMEOUT);
+    nsfr_async::mbar_wait_bounded(&bar, 0);
+    return;
+  }
+#else
   for (int t = threadIdx.x; t < epb * 6 * NV; t += blockDim.x) {
     const int le = t / (6 * NV);
-    if (e0 + le >= ne) continue;
+    if (le >= nel) continue;
     P[t] = nrec[((size_t)(e0 + le) * NSFR_NFIELD) * NV + t % (6 * NV)];
   }
+  for (int t = threadIdx.x; t < epb * 15 * NV; t += blockDim.x) Ra[t] = 0.0;
+#endif
   if (VF == NSFR_FLUX_RANOCHA) {
     // the pressure rho / (2 beta) in place of |u|^2/4
     __syncthreads();
-    for (int t = threadIdx.x; t < epb * NV; t += blockDim.x) {
-      if (e0 + t / NV >= ne) continue;
+    for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
       double* pe = P + (size_t)(t / NV) * 6 * NV + t % NV;
       pe[P_QQ * NV] = pe[P_RHO * NV] * rcp_full(pe[P_B2 * NV]);
     }
   }
-  // metric rows of direction d scaled by w_perp / 2 (scaled_rows_kernel):
-  // w_perp (the weights of the two other directions) is constant along a line
-  // of direction d, and the fluxes are linear in the metric row, so the pair
-  // weights reduce to S1
-  for (int t = threadIdx.x; t < epb * 9 * NV; t += blockDim.x) {
-    if (e0 + t / (9 * NV) >= ne) continue;
-    Ms[t] = metric_s[(size_t)e0 * 9 * NV + t];
-  }
-  for (int t = threadIdx.x; t < epb * 15 * NV; t += blockDim.x) Ra[t] = 0.0;
   __syncthreads();
 
   // line phase: one thread per line; the line's sums live in the direction's
   // slab of Ra (only this thread touches them), node a's in registers while
   // a is the outer pair index -- the additions keep the order of a plain
-  // per-line accumulation
+  // per-line accumulation.  The averaged metric row of each pair comes from
+  // the pair table (rows scaled by w_perp / 2: w_perp is constant along a line
+  // and the fluxes are linear in the metric row, so the pair weights reduce to
+  // S1); the next row is loaded while the current flux is evaluated.
   const int le = threadIdx.x / NL, l = threadIdx.x % NL, e = e0 + le;
   const int d = l / NFP, line = l % NFP, l0 = line % N, l1 = line / N;
   int base, stride;
   line_geometry<N>(d, l0, l1, base, stride);
-  if (le < epb && e < ne) {
+  if (le < nel) {
     const double* Pe = P + (size_t)le * 6 * NV + base;
     const double* Le = nrec + ((size_t)e * NSFR_NFIELD + P_LRHO) * NV + base;  // ln rho, ln beta (read only off the series path)
-    const double* Me = Ms + ((size_t)le * 9 + 3 * d) * NV + base;
+    const double* Pm = pm + ((size_t)e * 3 + d) * NPP * 3 * NFP + line;      // row q, component c at Pm[(3 q + c) NFP]
     double* Rl = Ra + ((size_t)le * 15 + 5 * d) * NV + base;
-    // volume-volume pairs along the line: each unordered pair once (S1 is skew);
-    // the metric rows already carry w_perp / 2
+    // volume-volume pairs along the line: each unordered pair once (S1 is skew)
+    double m0 = Pm[0], m1 = Pm[NFP], m2 = Pm[2 * NFP];
+    int q = 0;
 #pragma unroll 1
     for (int a = 0; a < N - 1; ++a) {
       const Rec A = load_rec6(Pe + a * stride, NV);
-      const double na0 = Me[a * stride], na1 = Me[NV + a * stride], na2 = Me[2 * NV + a * stride];
       double Racc[5];
 #pragma unroll
       for (int k = 0; k < 5; ++k) Racc[k] = Rl[k * NV + a * stride];
 #pragma unroll 1
       for (int b = a + 1; b < N; ++b) {
+        const double n0 = m0, n1 = m1, n2 = m2;
+        ++q;  // the rows run on into the hybrid rows, so row q exists
+        m0 = Pm[3 * q * NFP];
+        m1 = Pm[(3 * q + 1) * NFP];
+        m2 = Pm[(3 * q + 2) * NFP];
         const Rec B = load_rec6(Pe + b * stride, NV);
         double F[5];
-        vol_flux<VF>(A, B, na0 + Me[b * stride], na1 + Me[NV + b * stride], na2 + Me[2 * NV + b * stride], ops,
-                     PtrLogs{Le + a * stride, NV}, PtrLogs{Le + b * stride, NV}, F);
+        vol_flux<VF>(A, B, n0, n1, n2, ops, PtrLogs{Le + a * stride, NV}, PtrLogs{Le + b * stride, NV}, F);
         const double c = ops.S1[a * N + b];
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -351,7 +386,6 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
       const int enb = nbr_index(e, d, s, nx, ny, nz);
       const double* fo = face + (((size_t)e * 6 + 2 * d + s) * NSFR_NFIELD) * NFP + line;
       const size_t fe = (size_t)(s ? e : enb) * 3 + d;  // the element whose + face this is
-      const double* nf = nf_s + fe * 3 * NFP + line;  // w_perp C_f
       const double* fsp = fstar + fe * 5 * NFP + line;
       const double sw = s ? 1.0 : -1.0;
       if (ops.lgl) {
@@ -362,17 +396,16 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
         for (int k = 0; k < 5; ++k) Re[k * NV] = fma(sw, fsp[k * NFP], Re[k * NV]);
         continue;
       }
-      const double f0 = nf[0], f1 = nf[NFP], f2 = nf[2 * NFP];
       Rec Fo = load_rec6(fo, NFP);
       if (VF == NSFR_FLUX_RANOCHA) Fo.qq = pressure_of(Fo);
       const double* t = s ? ops.tp : ops.tm;
-      const double h0 = 0.5 * f0, h1 = 0.5 * f1, h2 = 0.5 * f2;
+      const double* Ph = Pm + 3 * (N * (N - 1) / 2 + s * N) * NFP;  // hybrid rows: (C_a + C_f) w_perp / 2
       double tphi[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll 1
       for (int a = 0; a < N; ++a) {
         const Rec A = load_rec6(Pe + a * stride, NV);
         double F[5];
-        vol_flux<VF>(A, Fo, Me[a * stride] + h0, Me[NV + a * stride] + h1, Me[2 * NV + a * stride] + h2, ops,
+        vol_flux<VF>(A, Fo, Ph[3 * a * NFP], Ph[(3 * a + 1) * NFP], Ph[(3 * a + 2) * NFP], ops,
                      PtrLogs{Le + a * stride, NV}, PtrLogs{fo + P_LRHO * NFP, NFP}, F);
         const double ta = t[a], swt = sw * ta;
 #pragma unroll
@@ -394,7 +427,7 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
   __syncthreads();
   // the three directions meet in a fixed order (d = 0, 1, 2); the records are
   // no longer needed, so the sum goes over them
-  for (int t = threadIdx.x; t < min(epb, ne - e0) * 5 * NV; t += blockDim.x) {
+  for (int t = threadIdx.x; t < nel * 5 * NV; t += blockDim.x) {
     const int lq = t / (5 * NV), r = t % (5 * NV);
     const double* ra = Ra + (size_t)lq * 15 * NV + r;
     double rv = (ra[0] + ra[5 * NV]) + ra[10 * NV];
@@ -403,10 +436,9 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
   }
   __syncthreads();
 
-  const int nel = min(epb, ne - e0);
   const int total = nel * 5 * NV;
-  if (ops.uncol) {  // solution on the Lobatto nodes: back from the GL points
-    uncol_epilogue<N>(Rs, Ms, nel, e0, ops, invwj, epi, rk, out);
+  if (ops.uncol) {  // solution on the Lobatto nodes: back from the GL points (Ra is free again)
+    uncol_epilogue<N>(Rs, Ra, nel, e0, ops, invwj, epi, rk, out);
     return;
   }
   if (epi != EPI_RAW) {
@@ -495,14 +527,14 @@ cudaError_t launch_volume_n(nsfr_ctx* ctx, const double* u, double* out, int epi
   const int eb = ctx->vol_b, ee = ctx->vol_e < 0 ? ctx->ne : ctx->vol_e;
   const int grid = (ee - eb + epb - 1) / epb;
   if (grid <= 0) return cudaSuccess;
-  const size_t smem = (size_t)epb * (6 + 9 + 15) * NV * sizeof(double);
+  const size_t smem = (size_t)epb * (6 + 15) * NV * sizeof(double);
   auto kern = ctx->vol_flux == NSFR_FLUX_RANOCHA ? volume_kernel<N, NSFR_FLUX_RANOCHA>
                                                  : volume_kernel<N, NSFR_FLUX_CHANDRASHEKAR>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   RkArgs r = rk ? *rk : RkArgs{};
   nsfr_prof_begin(ctx, 2, s);
-  kern<<<grid, vol_threads(N), smem, s>>>(ctx->nrec, ctx->metric_s, ctx->nf_s, ctx->face, ctx->fstar, ctx->invwj,
+  kern<<<grid, vol_threads(N), smem, s>>>(ctx->nrec, ctx->pair_rows, ctx->face, ctx->fstar, ctx->invwj,
                                           epi == EPI_RAW ? nullptr : ctx->src_on, ctx->ops, ctx->nx, ctx->ny,
                                           ctx->nz, eb, ee, epi, r, out, ctx->flag);
   nsfr_prof_end(ctx, s);
@@ -536,8 +568,50 @@ __global__ void scaled_rows_kernel(const double* __restrict__ metric, const doub
 }
 }  // namespace
 
+namespace {
+// The pair table of the volume kernel, from the scaled rows (geometry only): for
+// element e, direction d, line l, component c, row q < n(n-1)/2 holds
+// M_a + M_b for the q-th pair a < b of the line (the volume kernel's loop
+// order), row n(n-1)/2 + s n + a holds M_a + (w_perp C_f)/2 for node a and
+// the face of side s (C_f the face's shared row), M = w_perp C / 2 the scaled
+// metric row of the node: the same sums the line phase would form per pair.
+__global__ void pair_rows_kernel(const double* __restrict__ metric_s, const double* __restrict__ nf_s, int n, int nx,
+                                 int ny, int nz, double* __restrict__ pm) {
+  const int nv = n * n * n, nfp = n * n, np = n * (n - 1) / 2, npp = pair_rows(n);
+  const size_t ne = (size_t)nx * ny * nz, total = ne * 3 * npp * 3 * nfp;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int line = (int)(t % nfp), c = (int)(t / nfp % 3), q = (int)(t / ((size_t)3 * nfp) % npp);
+    const int d = (int)(t / ((size_t)3 * nfp * npp) % 3);
+    const size_t e = t / ((size_t)9 * nfp * npp);
+    const int l0 = line % n, l1 = line / n;
+    const int base = d == 0 ? n * (l0 + n * l1) : (d == 1 ? l0 + n * n * l1 : l0 + n * l1);
+    const int stride = d == 0 ? 1 : (d == 1 ? n : n * n);
+    const double* M = metric_s + (e * 9 + 3 * d + c) * nv + base;
+    if (q < np) {
+      int a = 0, r = q;
+      while (r >= n - 1 - a) {
+        r -= n - 1 - a;
+        ++a;
+      }
+      pm[t] = M[a * stride] + M[(a + 1 + r) * stride];
+    } else {
+      const int side = (q - np) / n, a = (q - np) % n;
+      const int en = nsfr_k::nbr_index((int)e, d, side, nx, ny, nz);
+      const size_t fe = (size_t)(side ? e : en) * 3 + d;
+      pm[t] = M[a * stride] + 0.5 * nf_s[(fe * 3 + c) * nfp + line];
+    }
+  }
+}
+}  // namespace
+
+size_t nsfr_pair_rows_count(int n, int ne) { return (size_t)ne * 9 * pair_rows(n) * n * n; }
+
 cudaError_t nsfr_launch_scaled_rows(nsfr_ctx* ctx, cudaStream_t s) {
   scaled_rows_kernel<<<152 * 8, 256, 0, s>>>(ctx->metric, ctx->nfp_plus, ctx->ops, ctx->ne, ctx->metric_s, ctx->nf_s);
+  ctx->launches++;
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess || !ctx->pair_rows) return err;
+  pair_rows_kernel<<<152 * 8, 256, 0, s>>>(ctx->metric_s, ctx->nf_s, ctx->n, ctx->nx, ctx->ny, ctx->nz, ctx->pair_rows);
   ctx->launches++;
   return cudaGetLastError();
 }
@@ -640,8 +714,10 @@ extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, co
   const size_t fstar_bytes = ne * 15 * nfp * sizeof(double);
   const size_t jac_bytes = ne * nv * sizeof(double);
   const size_t ms_bytes = ne * 9 * nv * sizeof(double), nfs_bytes = ne * 9 * nfp * sizeof(double);
-  // error word (padded), face states, face fluxes, 1/(wJ), wJ, node records, scaled metric and face rows
-  const size_t need = 256 + face_bytes + fstar_bytes + (2 + NSFR_NFIELD) * jac_bytes + ms_bytes + nfs_bytes;
+  const size_t pm_bytes = nsfr_pair_rows_count((int)n, (int)ne) * sizeof(double);
+  // error word (padded), face states, face fluxes, 1/(wJ), wJ, node records, scaled metric and face
+  // rows, the volume kernel's pair table
+  const size_t need = 256 + face_bytes + fstar_bytes + (2 + NSFR_NFIELD) * jac_bytes + ms_bytes + nfs_bytes + pm_bytes;
   if (need > NSFR_STATIC_SCRATCH_BYTES || ne > (size_t)0x7fffffff) return NSFR_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return NSFR_ERR_CUDA;
@@ -689,6 +765,8 @@ extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, co
   ctx.nrec = (double*)(base + 256 + face_bytes + fstar_bytes + 2 * jac_bytes);
   ctx.metric_s = (double*)(base + 256 + face_bytes + fstar_bytes + (2 + NSFR_NFIELD) * jac_bytes);
   ctx.nf_s = (double*)(base + 256 + face_bytes + fstar_bytes + (2 + NSFR_NFIELD) * jac_bytes + ms_bytes);
+  ctx.pair_rows = (double*)(base + 256 + face_bytes + fstar_bytes + (2 + NSFR_NFIELD) * jac_bytes + ms_bytes +
+                            nfs_bytes);
   ctx.metric = const_cast<double*>(C);
   ctx.J = const_cast<double*>(J);
   ctx.nfp_plus = const_cast<double*>(Cf);
@@ -701,6 +779,7 @@ extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, co
   int flag = 0;
   if (cudaMemcpyAsync(&flag, ctx.flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return NSFR_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return NSFR_ERR_CUDA;
+  if (flag & NSFR_FLAG_WAIT_TIMEOUT) return NSFR_ERR_CUDA;
   if (flag & 2) return NSFR_ERR_MESH;
   if (flag & 1) return NSFR_ERR_NONPHYSICAL;
   return NSFR_OK;

@@ -30,7 +30,8 @@ SOURCES = {"none": 0, "manufactured": 1}
 # every symbol include/nsfr.h declares
 EXPORTS = ["nsfr_setup", "nsfr_setup_uncollocated", "nsfr_residual", "nsfr_residual_raw", "nsfr_rk_step", "nsfr_entropy",
            "nsfr_rk_stage", "nsfr_max_wavespeed", "nsfr_set_source", "nsfr_get_time", "nsfr_vjp", "nsfr_node_coords", "nsfr_get_metrics", "nsfr_set_metrics", "nsfr_quadrature", "nsfr_info", "nsfr_check",
-           "nsfr_profile", "nsfr_profile_read", "nsfr_residual_static", "nsfr_math_eval", "nsfr_kernel_launches",
+           "nsfr_profile", "nsfr_profile_read", "nsfr_residual_static", "nsfr_math_eval", "nsfr_fma_probe",
+           "nsfr_kernel_launches",
            "nsfr_last_error", "nsfr_destroy"]
 KERNELS = ["metrics", "face_states", "volume", "max_wavespeed", "diagnostics", "vjp_face", "vjp_volume",
            "vjp_metrics", "face_flux", "source", "rk_update"]
@@ -88,6 +89,8 @@ def load_library(path=LIB_PATH):
     lib.nsfr_get_time.restype = i
     lib.nsfr_math_eval.argtypes = [i, vp, vp, ctypes.c_longlong, vp]
     lib.nsfr_math_eval.restype = i
+    lib.nsfr_fma_probe.argtypes = [i, ctypes.c_longlong, i, vp, ctypes.POINTER(ctypes.c_longlong), vp]
+    lib.nsfr_fma_probe.restype = i
     lib.nsfr_kernel_launches.argtypes = [vp]
     lib.nsfr_kernel_launches.restype = ctypes.c_longlong
     lib.nsfr_last_error.argtypes = [vp]
@@ -155,6 +158,16 @@ def residual_static(u, C, J, Cf, shape, p, c=0.0, face_flux="ec", gamma=1.4, dud
     if st != NSFR_OK:
         raise NSFRError(st, "nsfr_residual_static failed")
     return dudt
+
+
+def fma_probe(fp32, iters, blocks, sink, stream=None):
+    """Launch nsfr_fma_probe (FP64 or FP32 multiply-add chains) on ``stream``; returns the
+    number of multiply-adds the launch performs (the caller times it)."""
+    n = ctypes.c_longlong(0)
+    st = lib().nsfr_fma_probe(int(bool(fp32)), int(iters), int(blocks), _ptr(sink), ctypes.byref(n), _stream(stream))
+    if st != NSFR_OK:
+        raise NSFRError(st, "nsfr_fma_probe failed")
+    return n.value
 
 
 MATH_FN = {"log": 0, "exp": 1, "rcp": 2, "rcp1": 3, "log_ff": 4, "exp_ff": 5}
