@@ -213,42 +213,115 @@ def max_over_ranks(dist, x):
 # --------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the same workload
 # --------------------------------------------------------------------------
-def oracle_sample_rate(p, n_sample=8, budget_s=20.0):
-    """GDOF/s of the oracle (one RK stage = residual + WA inverse + stage update)
-    on an n_sample^3-element periodic sample of the warped Taylor-Green cube."""
+# the workloads the oracle is timed on, each on a bounded periodic sample of the same
+# element geometry and degree (the oracle's cost per node depends on p, not on the
+# mesh size): (label, p, mesh elements per direction, sample elements per direction)
+CPU_CONFIGS = [("taylor-green 4^3 p=3", 3, 4, 4), ("taylor-green 32^3 p=3", 3, 32, 6),
+               ("taylor-green 16^3 p=7", 7, 16, 3), ("taylor-green 64^3 p=4", 4, 64, 6)]
+BLAS_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+
+
+def _oracle_worker(job):
+    """One spawned process: the oracle steps its own copy of an n_sample^3 sample (one
+    stage = du/dt with the WA inverse + a stage update), after a barrier shared with
+    the other workers, for about budget_s of wall time.  Returns (nodes, per-stage
+    seconds, wall seconds, CPU seconds)."""
+    p, n_sample, budget_s, bar = job
     from oracle.problem import Problem
     ctrl = wl.tgv_mesh(n_sample, p)
     P = Problem(ctrl, (n_sample,) * 3, p, c=c_value(p))
     U = P.to_internal(wl.tgv_state(P.node_coords()))
-    nodes = n_sample ** 3 * (p + 1) ** 3
-    stages = 0
+    U = U + 1e-4 * P.dudt(U)  # warm-up stage
+    if bar is not None:
+        bar.wait()
+    times = []
     t0, c0 = time.perf_counter(), time.process_time()
     while True:
-        k = P.dudt(U)
-        U = U + 1e-4 * k  # stage update
-        stages += 1
-        if time.perf_counter() - t0 > budget_s or stages >= 40:
+        ts = time.perf_counter()
+        U = U + 1e-4 * P.dudt(U)
+        times.append(time.perf_counter() - ts)
+        if time.perf_counter() - t0 > budget_s:
             break
-    dt = time.perf_counter() - t0
-    # the cores the oracle kept busy: CPU time of all the process's threads over wall
-    # time (numpy's BLAS may run several threads)
-    busy = (time.process_time() - c0) / dt
-    cores = max(1, round(busy))
-    return (nodes * stages / dt / 1e9, cores,
-            f"{n_sample}^3 elements at p={p} ({nodes} nodes), {stages} stages, {dt:.1f} s, "
-            f"{busy:.1f} cores busy on average")
+    return n_sample ** 3 * (p + 1) ** 3, times, time.perf_counter() - t0, time.process_time() - c0
+
+
+def _pool_run(p, n_sample, budget_s, workers):
+    """The oracle on `workers` spawned processes (numpy single-threaded in each), every one
+    stepping its own copy of the sample: aggregate GDOF/s, median seconds per stage."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")  # never fork a process that may hold a CUDA context
+    saved = {k: os.environ.get(k) for k in BLAS_ENV}
+    for k in BLAS_ENV:
+        os.environ[k] = "1"
+    try:
+        with ctx.Manager() as mgr:
+            bar = mgr.Barrier(workers)
+            with ctx.Pool(workers) as pool:
+                out = pool.map(_oracle_worker, [(p, n_sample, budget_s, bar)] * workers)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    nodes = out[0][0]
+    wall = max(o[2] for o in out)
+    stages = sum(len(o[1]) for o in out)
+    med = statistics.median(t for o in out for t in o[1])
+    return nodes * stages / wall / 1e9, med, stages
+
+
+def host_info():
+    info = {"nproc": os.cpu_count()}
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20)
+        for ln in r.stdout.splitlines():
+            k, _, v = ln.partition(":")
+            if k.strip() in ("Architecture", "Model name", "CPU(s)", "Thread(s) per core"):
+                info[k.strip()] = v.strip()
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    return info
+
+
+def cpu_baseline(p, budget_s=3.0, configs=None, n_mesh_p=64):
+    """The FP64 oracle, as it stands, on this host's cores: for each workload of
+    ``configs`` (default CPU_CONFIGS, plus degree p's workload if it is not among them)
+    a bounded sample timed with one worker (one thread) and with one worker per core.
+    Returns the cpu_baseline object (value: all cores on degree p's workload)."""
+    host = host_info()
+    cores = host["nproc"] or 1
+    configs = list(CPU_CONFIGS if configs is None else configs)
+    if not any(c[1] == p for c in configs):
+        configs.append((f"taylor-green {n_mesh_p}^3 p={p}", p, n_mesh_p, 6 if p <= 4 else 3))
+    rows, value, sample = [], None, ""
+    for label, pc, n_mesh, n_s in configs:
+        r1, m1, s1 = _pool_run(pc, n_s, budget_s, 1)
+        rn, mn, sn = _pool_run(pc, n_s, budget_s, cores)
+        rows.append({"workload": label, "p": pc, "sample": f"{n_s}^3 elements", "one_thread_gdof_per_s": r1,
+                     "one_thread_median_stage_s": m1, "all_cores_gdof_per_s": rn, "all_cores_median_stage_s": mn,
+                     "workers": cores, "stages": [s1, sn]})
+        if pc == p and (value is None or n_mesh == n_mesh_p):
+            value = rn
+            sample = (f"{label}: {n_s}^3-element periodic sample, {cores} spawned worker processes (one per "
+                      f"core, numpy single-threaded) each stepping its own copy for {budget_s:.0f} s; "
+                      f"one-thread rate {r1:.2e} GDOF/s")
+    return {"value": value, "unit": "GDOF/s", "cores": cores, "kind": "oracle", "sample": sample,
+            "host": host, "configs": rows}
 
 
 def run_reference(args, rank, ws, dist):
     if rank != 0:
         return
     cfg = workload_config(args, ws)
-    val, cores, sample = oracle_sample_rate(args.p)
+    # the oracle on the same workload only: a bounded sample per timed window
+    cpu = cpu_baseline(args.p, configs=[], n_mesh_p=args.n_el)
+    val = cpu["value"]
     line = {"impl": "reference", "metric": "NSFR-EC residual GDOF/s per RK stage", "value": val,
             "unit": "GDOF/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": val, "unit": "GDOF/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": cpu,
             "e2e": {"value": val, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -282,12 +355,12 @@ def volume_kernel_flops(n_el, p, has_k=True, nq=None):
 class _Replica:
     """The whole mesh on this GPU (every rank an independent replica)."""
 
-    def __init__(self, args, ctrl, u0, precision, dist, rank, ws):
+    def __init__(self, args, ctrl, u0, precision, dist, rank, ws, vol_flux="chandrashekar"):
         import torch
         from paper_2312_07725_gb300 import Solver
         N = args.n_el
         self.S = Solver(ctrl, (N, N, N), args.p, c=c_value(args.p), face_flux="ec", precision=precision,
-                        nq=args.nq)
+                        nq=args.nq, vol_flux=vol_flux)
         self.u0 = u0
         self.u = torch.from_numpy(u0).cuda()
         self.cfl = args.cfl
@@ -313,7 +386,7 @@ class _SlabRank:
     """One z-slab of a z-stack of ws copies of the mesh (weak scaling), with ghost
     layers refreshed by a halo exchange before every RK stage."""
 
-    def __init__(self, args, ctrl, u0, precision, dist, rank, ws):
+    def __init__(self, args, ctrl, u0, precision, dist, rank, ws, vol_flux="chandrashekar"):
         from paper_2312_07725_gb300.slab import DistExchanger, Slab
         N = args.n_el
         self.slab = Slab(ctrl, (N, N, N), args.p, rank, ws, DistExchanger(dist, rank, ws), copies=ws,
@@ -342,12 +415,15 @@ class _SlabRank:
         return self.slab.interior(t)
 
 
-def measure(args, ctrl, u0, precision, dist, rank, ws, steps):
+def measure(args, ctrl, u0, precision, dist, rank, ws, steps, vol_flux="chandrashekar"):
     """Time `steps` RK4 steps of one precision mode, plus its e2e variant."""
     import torch
 
     p, N = args.p, args.n_el
-    run = (_SlabRank if args.decomp == "slab" else _Replica)(args, ctrl, u0, precision, dist, rank, ws)
+    if vol_flux != "chandrashekar":
+        run = _Replica(args, ctrl, u0, precision, dist, rank, ws, vol_flux=vol_flux)
+    else:
+        run = (_SlabRank if args.decomp == "slab" else _Replica)(args, ctrl, u0, precision, dist, rank, ws)
     S, u = run.S, run.u
     stream = torch.cuda.current_stream()
     nodes = N ** 3 * (p + 1) ** 3  # this rank's own nodes (ghost layers not counted)
@@ -481,6 +557,12 @@ def run_ours(args, rank, ws, dist):
         del dff
     del d64
 
+    mra = None
+    if args.nq is None and args.modes == "both" and args.decomp == "replicas":
+        # the paper's EC runs' flux: Chandrashekar's with Ranocha's pressure terms (FP64)
+        mra = measure(args, ctrl, u0, "fp64", dist, rank, ws, args.steps, vol_flux="ranocha")
+        mra.pop("dudt")
+
     adj = None
     if args.nq is None and not args.no_adjoint and args.decomp == "replicas":
         adj = measure_adjoint(args, ctrl, u0, m64["residual_only"]["ms_per_evaluation"])
@@ -491,17 +573,31 @@ def run_ours(args, rank, ws, dist):
     flops, counts = volume_kernel_flops(ne_launch, p, cfg["c"] != 0.0, args.nq)
     achieved = flops / (vol_ms / vol_n / 1e3) / 1e12
     peak, peak_src = fp64_peak(clk)
+    peaks = measure_fma_peaks() if args.nq is None else None
+    probe64 = peaks["fp64"]["tflops"] if peaks else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": (VOLUME_DRAM_BYTES_PER_ELEMENT[p] * ne_launch
                         if p in VOLUME_DRAM_BYTES_PER_ELEMENT and args.nq is None else None),
             "traffic_unit": "bytes per launch", "kernel": f"volume_kernel<{args.nq or p + 1}> (FP64 pipe)",
             "peak_source": peak_src,
-            "peak_measured_dfma_probe": FP64_MEASURED_TFLOPS, "frac_of_measured": achieved / FP64_MEASURED_TFLOPS,
+            "peak_measured_probe": probe64, "frac_of_measured_probe": achieved / probe64 if probe64 else None,
             "flops_per_launch": flops, "flux_evals_per_element": counts}
+    rk = {"fp64": roofline_kernels(m64["kernels"], p, ne_launch, "fp64", clk, peaks, cfg["c"] != 0.0)}
+    for nm, m in (("fp32_bulk", m32), ("fp32_bulk_ff", mff)):
+        if m is not None:
+            rk[nm] = roofline_kernels(m["kernels"], p, ne_launch, nm, m["clocks"], peaks, cfg["c"] != 0.0)
+    if adj is not None:
+        fp64_nom = peak
+        rk["adjoint"] = {}
+        for nm, work in adjoint_kernel_models(p, ne_launch, cfg["c"] != 0.0).items():
+            if nm in adj["kernels"]:
+                t = adj["kernels"][nm]["ms_avg"] / 1e3
+                rk["adjoint"][nm] = {"bound": "alu", "pipe": "fp64", "work_per_launch": work, "work_unit": "flops",
+                                     "ms_avg": t * 1e3, "achieved": work / t / 1e12, "unit": "TFLOP/s",
+                                     "peak": fp64_nom, "frac": work / t / 1e12 / fp64_nom}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        val, cores, sample = oracle_sample_rate(p)
-        cpu = {"value": val, "unit": "GDOF/s", "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = cpu_baseline(p, n_mesh_p=N)
     if rank == 0:
         line = {"metric": "NSFR-EC residual GDOF/s per RK stage", "value": m64["value"], "unit": "GDOF/s",
                 "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": m64["ms_per_step"],
@@ -509,10 +605,19 @@ def run_ours(args, rank, ws, dist):
                 "data": "synthetic", "config": cfg, "gdof_per_s_x5_components": 5 * m64["value"],
                 "e2e": {"value": m64["e2e"], "unit": "GDOF/s", "h2d_bytes_per_step": m64["e2e_bytes"],
                         "d2h_bytes_per_step": m64["e2e_bytes"]},
-                "gpu_launches": m64["gpu_launches"], "kernels": m64["kernels"], "roofline": roof, "clocks": clk,
+                "gpu_launches": m64["gpu_launches"], "kernels": m64["kernels"], "roofline": roof,
+                "roofline_kernels": rk, "fma_probe": peaks, "clocks": clk,
                 "residual_only": m64["residual_only"],
                 "adjoint": adj,
                 "cpu_baseline": cpu,
+                "ranocha": None if mra is None else
+                {"value": mra["value"], "unit": "GDOF/s", "ms_per_step": mra["ms_per_step"],
+                 "vs_chandrashekar": mra["value"] / m64["value"],
+                 "e2e": {"value": mra["e2e"], "unit": "GDOF/s", "h2d_bytes_per_step": mra["e2e_bytes"],
+                         "d2h_bytes_per_step": mra["e2e_bytes"]},
+                 "gpu_launches": mra["gpu_launches"], "kernels": mra["kernels"],
+                 "residual_only": mra["residual_only"], "clocks": mra["clocks"],
+                 "flux": "Chandrashekar's with Ranocha's pressure terms (volume, hybrid and face), FP64"},
                 "fp32_bulk": None if m32 is None else
                 {"value": m32["value"], "unit": "GDOF/s", "ms_per_step": m32["ms_per_step"],
                  "speedup_vs_fp64": m32["value"] / m64["value"],
@@ -548,7 +653,136 @@ def fp64_peak(clk):
 
 
 FP64_LANES_PER_SM = 2.0  # ncu: 2 DFMA thread-instructions per SM per cycle (nominal 1.26 TFLOP/s at 2070 MHz)
-FP64_MEASURED_TFLOPS = 1.008  # DFMA-chain microbenchmark on this machine's GB300 (0.504 T DFMA/s)
+FP32_LANES_PER_SM = 128.0  # FP32 FMA lanes per SM (4 sub-partitions x 32)
+HBM_FALLBACK_GBS = 6800.0  # the profiling recipe's fallback copy bandwidth, if no measured figure exists
+
+
+def hbm_peak():
+    """Measured copy bandwidth (GB/s) from MEASURED_PEAKS.json, else the fallback."""
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (copy, measured)"
+    except (OSError, KeyError, ValueError, TypeError):
+        return HBM_FALLBACK_GBS, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
+def measure_fma_peaks():
+    """The FMA pipes' throughput, measured with nsfr_fma_probe (FP64 and FP32 chains on
+    every SM, about 0.4 s each, CUDA events on the launching stream), with the SM clock
+    sampled during each: TFLOP/s (an FMA = 2 flops) and the clock."""
+    import torch
+    from paper_2312_07725_gb300 import nsfr
+    sink = torch.zeros(2, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, fp32, iters in (("fp64", 0, 100_000), ("fp32", 1, 6_000_000)):
+        blocks = 152 * 8
+        nsfr.fma_probe(fp32, max(1, iters // 100), blocks, sink)  # warm-up
+        torch.cuda.synchronize()
+        clocks = ClockSampler(smi_id(torch.cuda.current_device()))
+        clocks.start()
+        time.sleep(0.2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fmas = sum(nsfr.fma_probe(fp32, iters, blocks, sink) for _ in range(2))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"tflops": 2.0 * fmas / (ms / 1e3) / 1e12, "ms": ms, "clocks": clk,
+                     "probe": f"nsfr_fma_probe: {blocks} CTAs x 256 threads x 8 chains x {iters} steps, 2 launches"}
+    return out
+
+
+def stage_kernel_models(p, ne, precision, has_k=True):
+    """Algorithmic work of one launch of each kernel of an RK stage over ne elements
+    (n = p+1; an FMA counts 2 flops; a division, reciprocal, square root, log or exp 1):
+      face_states  v(u) at n^3 nodes (32 each: u, |u|^2, p, beta, ln rho, ln p, s, v,
+                   the record fields), t_s . v to the six faces (30 n^3 multiply-adds),
+                   u(v~) at 6 n^2 face nodes (22 each: u, |u|^2, s~, ln 2 beta~, rho~ by
+                   exp, the record fields)
+      face_flux    3 n^2 face fluxes of 55 flops (the EC flux of the bench's faces)
+      volume       volume_kernel_flops
+      max_wavespeed  40 bytes (the state) read per node and launch
+    Returns {kernel: (kind, work, unit)}."""
+    n = p + 1
+    fs = (32 * n ** 3 + 60 * n ** 3 + 6 * n * n * 22) * ne
+    vol, _ = volume_kernel_flops(ne, p, has_k)
+    return {"face_states": ("flops", fs), "face_flux": ("flops", 3 * n * n * FLOPS_PER_FLUX * ne),
+            "volume": ("flops", vol), "max_wavespeed": ("bytes", 40 * n ** 3 * ne)}
+
+
+# FP64 flops per two-point flux that the fp32_bulk form keeps in FP64: the two log
+# means (sums, the reciprocal and f^2, the series) and the scalars p_hat and H made of them
+BULK_FP64_FLOPS_PER_FLUX = 28
+
+
+def roofline_kernels(kern, p, ne, precision, clk, peaks, has_k=True):
+    """Per-kernel rooflines of one precision mode's timed step: algorithmic work per launch
+    (stage_kernel_models) over the kernel's mean launch time from the library's CUDA events,
+    against the bounding resource: the FP64 FMA pipe (nominal from 152 SMs x 2 lanes x the
+    sampled clock, and the probe's measured rate), the FP32 FMA pipe (the FP32-bulk kernels'
+    float and float-float arithmetic) or HBM (the measured copy bandwidth)."""
+    mhz = clk.get("sm_mhz") or 2070.0
+    fp64_nom = 152 * FP64_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    fp32_nom = 152 * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    hbm, hbm_src = hbm_peak()
+    models = stage_kernel_models(p, ne, precision, has_k)
+    n = p + 1
+    out = {}
+    for name, (kind, work) in models.items():
+        if name not in kern:
+            continue
+        t = kern[name]["ms_avg"] / 1e3
+        if kind == "bytes":
+            ach = work / t / 1e9
+            out[name] = {"bound": "hbm", "work_per_launch": work, "work_unit": "bytes", "ms_avg": t * 1e3,
+                         "achieved": ach, "unit": "GB/s", "peak": hbm, "frac": ach / hbm, "peak_source": hbm_src}
+            continue
+        ach = work / t / 1e12
+        fp64_part = work
+        pipe = "fp64"
+        if precision != "fp64" and name == "volume":
+            fluxes = 3 * n ** 3 * (n - 1) // 2 + 6 * n ** 3
+            fp64_part = BULK_FP64_FLOPS_PER_FLUX * fluxes * ne if precision == "fp32_bulk" else 0
+            pipe = "fp32"
+        if precision == "fp32_bulk_ff" and name == "face_states":
+            fp64_part, pipe = 0, "fp32"
+        e = {"bound": "alu", "work_per_launch": work, "work_unit": "flops", "ms_avg": t * 1e3, "achieved": ach,
+             "unit": "TFLOP/s"}
+        if pipe == "fp64":
+            e.update({"pipe": "fp64", "peak": fp64_nom, "frac": ach / fp64_nom,
+                      "peak_source": f"152 SMs x 2 FP64 FMA/clk/SM x 2 x {mhz:.0f} MHz"})
+        else:
+            e.update({"pipe": "fp32 (the flux arithmetic; float-float where the form says so)", "peak": fp32_nom,
+                      "frac": ach / fp32_nom, "peak_source": f"152 SMs x 128 FP32 FMA/clk/SM x 2 x {mhz:.0f} MHz"})
+            if fp64_part:
+                a64 = fp64_part / t / 1e12
+                e["fp64_part"] = {"flops_per_launch": fp64_part, "achieved": a64, "peak": fp64_nom,
+                                  "frac": a64 / fp64_nom,
+                                  "model": f"{BULK_FP64_FLOPS_PER_FLUX} FP64 flops per flux (log means, p_hat, H)"}
+        if peaks and pipe == "fp64" and "fp64" in peaks:
+            e["frac_of_measured_probe"] = ach / peaks["fp64"]["tflops"]
+        out[name] = e
+    return out
+
+
+def adjoint_kernel_models(p, ne, has_k=True):
+    """Algorithmic work of the adjoint kernels (models, n = p+1): the VJP of every two-point
+    flux (1,500 volume and hybrid plus 3 n^2 face fluxes at p = 4) as a forward recompute
+    (55) plus a reverse sweep counted at twice the forward flops (110) plus the cotangent
+    accumulation (20), and the transposed WA-inverse sweeps; the face-state VJP as three
+    times the forward face-state flops (recompute and reverse); the metric VJP as the
+    reverse of the conservative-curl construction, whose sweeps are linear (90 n^4
+    multiply-adds: interpolation, derivatives, curl, transfer to the GL nodes, J)."""
+    n = p + 1
+    fluxes = 3 * n ** 3 * (n - 1) // 2 + 6 * n ** 3 + 3 * n * n
+    vol = fluxes * (FLOPS_PER_FLUX * 3 + FLOPS_PER_ACC) + 6 * n * n * (5 + 10 * n) + 5 * n ** 3
+    if has_k:
+        vol += 6 * 5 * n * n * 4 * n
+    fs = 3 * (32 * n ** 3 + 60 * n ** 3 + 6 * n * n * 22)
+    return {"vjp_volume": vol * ne, "vjp_face": fs * ne, "vjp_metrics": 180 * n ** 4 * ne}
 
 
 def main():

@@ -90,7 +90,10 @@ def test_smi_id_is_the_pci_bus_id_when_nvidia_smi_accepts_it(monkeypatch):
     bench.smi_id.cache_clear()
 
 
-def test_oracle_sample_rate_reports_the_cores_it_kept_busy():
-    val, cores, sample = bench.oracle_sample_rate(2, n_sample=2, budget_s=0.5)
-    assert val > 0 and cores >= 1
-    assert "cores busy on average" in sample
+def test_cpu_baseline_times_the_oracle_on_one_and_on_several_workers():
+    val, med, stages = bench._pool_run(2, 2, 0.5, 1)
+    assert val > 0 and med > 0 and stages >= 1
+    val2, med2, stages2 = bench._pool_run(2, 2, 0.5, 2)
+    assert val2 > 0 and stages2 >= 2
+    info = bench.host_info()
+    assert info["nproc"] >= 1
