@@ -151,11 +151,13 @@ __device__ __forceinline__ void ec_flux_l(const Rec& A, const Rec& B, double n0,
   const double rr = rcp_newton1(sr);  // only enters f^2, a correction below 1e-4
   const double fr = dr * rr, fb = d2 * rb2;
   const double ur = fr * fr, ub = fb * fb;
-  double rln, ibg;
+  // h = 1/(2(gamma-1) beta_ln) - |u|^2_bar/2; on the series branch one FMA forms it
+  const double qs = A.qq + B.qq;
+  double rln, h;
   if (lm_small(ur)) rln = sr * horner4(K.gh, ur);
   else rln = dr / (la.lr() - lb.lr());
-  if (lm_small(ub)) ibg = horner4(K.f4g, ub) * rb2;
-  else ibg = K.inv_gm1 * (la.lb() - lb.lb()) / d2;
+  if (lm_small(ub)) h = fma(horner4(K.f4g, ub), rb2, -qs);
+  else h = K.inv_gm1 * (la.lb() - lb.lb()) / d2 - qs;
   const double ph = sr * rb2;
   const double v0 = A.u0 + B.u0, v1 = A.u1 + B.u1, v2 = A.u2 + B.u2;  // u_bar
   const double un = fma(v0, n0, fma(v1, n1, v2 * n2));
@@ -164,7 +166,38 @@ __device__ __forceinline__ void ec_flux_l(const Rec& A, const Rec& B, double n0,
   F[1] = fma(Fr, v0, ph * n0);
   F[2] = fma(Fr, v1, ph * n1);
   F[3] = fma(Fr, v2, ph * n2);
-  F[4] = fma(v2, F[3], fma(v1, F[2], fma(v0, F[1], Fr * (ibg - (A.qq + B.qq)))));
+  F[4] = fma(v2, F[3], fma(v1, F[2], fma(v0, F[1], Fr * h)));
+}
+
+// The same flux divided by s = rho_a + rho_b, returned with s: every component
+// carries that factor (rho_ln = s G(u_r), p_hat = s / (2 beta_a + 2 beta_b), and
+// F_E is linear in both), so a caller that accumulates w F folds s into the
+// weight and saves the two products by s.  Off the series branch rho_ln / s
+// is dr / ((ln rho_a - ln rho_b) s).
+template <class LA, class LB>
+__device__ __forceinline__ double ec_flux_over_sr(const Rec& A, const Rec& B, double n0, double n1, double n2,
+                                                  const OpsGL& K, const LA& la, const LB& lb, double F[5]) {
+  const double sr = A.r + B.r, dr = A.r - B.r;
+  const double s2 = A.b2 + B.b2, d2 = A.b2 - B.b2;
+  const double rb2 = rcp_full(s2);
+  const double rr = rcp_newton1(sr);  // only enters f^2, a correction below 1e-4
+  const double fr = dr * rr, fb = d2 * rb2;
+  const double ur = fr * fr, ub = fb * fb;
+  const double qs = A.qq + B.qq;
+  double gr, h;
+  if (lm_small(ur)) gr = horner4(K.gh, ur);
+  else gr = dr / ((la.lr() - lb.lr()) * sr);
+  if (lm_small(ub)) h = fma(horner4(K.f4g, ub), rb2, -qs);
+  else h = K.inv_gm1 * (la.lb() - lb.lb()) / d2 - qs;
+  const double v0 = A.u0 + B.u0, v1 = A.u1 + B.u1, v2 = A.u2 + B.u2;  // u_bar
+  const double un = fma(v0, n0, fma(v1, n1, v2 * n2));
+  const double Fr = gr * un;
+  F[0] = Fr;
+  F[1] = fma(Fr, v0, rb2 * n0);
+  F[2] = fma(Fr, v1, rb2 * n1);
+  F[3] = fma(Fr, v2, rb2 * n2);
+  F[4] = fma(v2, F[3], fma(v1, F[2], fma(v0, F[1], Fr * h)));
+  return sr;
 }
 
 __device__ __forceinline__ void ec_flux(const Rec& A, const Rec& B, double n0, double n1, double n2,

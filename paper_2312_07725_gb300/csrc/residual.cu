@@ -255,14 +255,19 @@ __device__ void uncol_epilogue(double* X, double* Y, int nel, int e0, const OpsG
   }
 }
 
-// Two-point flux of the line phase: Chandrashekar's (VF = NSFR_FLUX_CHANDRASHEKAR)
-// or with Ranocha's pressure terms, whose node pressures ride in the records'
-// |u|^2/4 slot (that flux has no use for |u|^2).
+// Two-point flux of the line phase, up to a factor it returns (the caller folds
+// it into its accumulation weights): Chandrashekar's (VF =
+// NSFR_FLUX_CHANDRASHEKAR) divided by rho_a + rho_b, or Ranocha's pressure
+// terms with factor 1, its node pressures riding in the records' |u|^2/4 slot
+// (that flux has no use for |u|^2).
 template <int VF, class LA, class LB>
-__device__ __forceinline__ void vol_flux(const Rec& A, const Rec& B, double n0, double n1, double n2,
-                                         const OpsGL& K, const LA& la, const LB& lb, double F[5]) {
-  if (VF == NSFR_FLUX_RANOCHA) ranocha_flux_l(A, B, A.qq, B.qq, n0, n1, n2, K, la, lb, F);
-  else ec_flux_l(A, B, n0, n1, n2, K, la, lb, F);
+__device__ __forceinline__ double vol_flux(const Rec& A, const Rec& B, double n0, double n1, double n2,
+                                           const OpsGL& K, const LA& la, const LB& lb, double F[5]) {
+  if (VF == NSFR_FLUX_RANOCHA) {
+    ranocha_flux_l(A, B, A.qq, B.qq, n0, n1, n2, K, la, lb, F);
+    return 1.0;
+  }
+  return ec_flux_over_sr(A, B, n0, n1, n2, K, la, lb, F);
 }
 
 // Rows of the pair table pm of one element and direction: the n(n-1)/2 volume
@@ -369,8 +374,9 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
         m2 = Pm[(3 * q + 2) * NFP];
         const Rec B = load_rec6(Pe + b * stride, NV);
         double F[5];
-        vol_flux<VF>(A, B, n0, n1, n2, ops, PtrLogs{Le + a * stride, NV}, PtrLogs{Le + b * stride, NV}, F);
-        const double c = ops.S1[a * N + b];
+        const double fs = vol_flux<VF>(A, B, n0, n1, n2, ops, PtrLogs{Le + a * stride, NV},
+                                       PtrLogs{Le + b * stride, NV}, F);
+        const double c = VF == NSFR_FLUX_RANOCHA ? ops.S1[a * N + b] : ops.S1[a * N + b] * fs;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
           Racc[k] = fma(c, F[k], Racc[k]);
@@ -405,9 +411,10 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
       for (int a = 0; a < N; ++a) {
         const Rec A = load_rec6(Pe + a * stride, NV);
         double F[5];
-        vol_flux<VF>(A, Fo, Ph[3 * a * NFP], Ph[(3 * a + 1) * NFP], Ph[(3 * a + 2) * NFP], ops,
-                     PtrLogs{Le + a * stride, NV}, PtrLogs{fo + P_LRHO * NFP, NFP}, F);
-        const double ta = t[a], swt = sw * ta;
+        const double fs = vol_flux<VF>(A, Fo, Ph[3 * a * NFP], Ph[(3 * a + 1) * NFP], Ph[(3 * a + 2) * NFP], ops,
+                                       PtrLogs{Le + a * stride, NV}, PtrLogs{fo + P_LRHO * NFP, NFP}, F);
+        const double ta = VF == NSFR_FLUX_RANOCHA ? t[a] : t[a] * fs;
+        const double swt = s ? ta : -ta;  // s t_a, the sign without a multiply
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
           tphi[k] = fma(ta, F[k], tphi[k]);
@@ -418,7 +425,7 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
       for (int k = 0; k < 5; ++k) tphi[k] = fsp[k * NFP] - tphi[k];
 #pragma unroll
       for (int a = 0; a < N; ++a) {
-        const double swt = sw * t[a];
+        const double swt = s ? t[a] : -t[a];
 #pragma unroll
         for (int k = 0; k < 5; ++k) Rl[k * NV + a * stride] = fma(swt, tphi[k], Rl[k * NV + a * stride]);
       }
