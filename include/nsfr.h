@@ -136,12 +136,17 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
  * NSFR on the GL points with u~ = u(chi v~^) and the face states
  * u(l_f v~^), and returns chi^T R_q (nsfr_residual_raw) or the weight-
  * adjusted du/dt = -Pi~ (W J)^{-1} Pi~^T chi^T R_q, Pi~1 = (M1 + K1)^{-1}
- * chi^T W (nsfr_residual, nsfr_rk_step).  FP64 only; nsfr_entropy and
- * nsfr_vjp return NSFR_ERR_STATE for such a context.  With nq = p+1 the
- * scheme is the GL-collocated one written in the LGL basis.
+ * chi^T W (nsfr_residual, nsfr_rk_step).  precision: NSFR_FP64, or
+ * NSFR_FP32_BULK (the flux differencing in FP32 as for nsfr_setup, the
+ * entropy projection and the face fluxes in FP64, and the return to the
+ * solution nodes -- chi^T, or (chi Pi~1)^T, 1/(W J), Pi~1 -- as FP32 sweeps);
+ * anything else is NSFR_ERR_ARG.  nsfr_vjp returns NSFR_ERR_STATE for such a
+ * context.  With nq = p+1 the scheme is the GL-collocated one written in the
+ * LGL basis.
  */
 nsfr_status nsfr_setup_uncollocated(const double* grid_nodes, int nx, int ny, int nz, int p_geo, int p, int nq,
-                                    double c, int vol_flux, int face_flux, double gamma, nsfr_ctx** out);
+                                    double c, int vol_flux, int face_flux, double gamma, int precision,
+                                    nsfr_ctx** out);
 
 /*
  * nsfr_residual -- du/dt = -Pi~ (W J)^{-1} Pi~^T R(u)  (Eq. NSFR with the
@@ -240,6 +245,13 @@ nsfr_status nsfr_get_time(const nsfr_ctx* ctx, double* t);
  *                      (Sec. "Global Conservation")
  *        [8] KE      = sum W J rho |u|^2 / 2
  *        [9..13] sum_i R_{i,k}  (0 to round-off on a periodic mesh)
+ * For an uncollocated context (nsfr_setup_uncollocated) the sums take the
+ * solution at the GL points, u_q = chi u^, with the point weights W J:
+ * S = sum W J U(u_q), Q_k = sum W J (u_q)_k (the GL quadrature of the
+ * solution), KE = sum W J rho|u|^2/2 at the points; the entropy rate is
+ * -sum_i v~^_i . R^_i at the Lobatto nodes with the projected entropy
+ * variables v~^ = Pi v(u_q) and R^ = chi^T R_q (the paper's statement for
+ * the uncollocated scheme), [2] its scale, and [9..13] sum_i R^_{i,k}.
  */
 nsfr_status nsfr_entropy(nsfr_ctx* ctx, const double* u, double* out, void* stream);
 

@@ -135,6 +135,25 @@ class UncollocatedProblem:
         prod = Vh * R
         return -diagnostics.fsum(prod), diagnostics.fsum(np.abs(prod))
 
+    def diagnostics(self, U):
+        """The scheme's scalars with the solution at the GL points, u_q = chi u^, and the point
+        weights W J: S = sum W J U(u_q), Q_k = sum W J (u_q)_k, KE = sum W J rho|u|^2/2 (the
+        GL quadrature of the solution); the entropy rate -sum_i v~^_i . R^_i and its scale
+        sum_i |v~^_i . R^_i| (per solution node); sum R^."""
+        Uq = tensor3(self.chi, U)
+        wq = self.wq
+        wj = wq[:, None, None] * wq[None, :, None] * wq[None, None, :] * self.J
+        rho, vel, _ = physics.primitive(Uq, self.gamma)
+        Vh, _ = self.projected(U)
+        R = self.residual(U)
+        vr = np.sum(Vh * R, axis=0)  # v~^_i . R^_i per solution node, as the collocated diagnostics
+        rate, scale = -diagnostics.fsum(vr), diagnostics.fsum(np.abs(vr))
+        return {"entropy": diagnostics.fsum(wj * physics.entropy_function(Uq, self.gamma)),
+                "entropy_rate": rate, "entropy_rate_scale": scale,
+                "Q": [diagnostics.fsum(wj * Uq[k]) for k in range(5)],
+                "kinetic_energy": diagnostics.fsum(wj * 0.5 * rho * np.sum(vel * vel, axis=0)),
+                "sum_R": [diagnostics.fsum(R[k]) for k in range(5)]}
+
     # ABI conveniences
     def dudt_abi(self, u):
         return self.to_abi(self.dudt(self.to_internal(u)))

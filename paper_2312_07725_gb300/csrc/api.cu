@@ -449,12 +449,13 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
 }
 
 nsfr_status nsfr_setup_uncollocated(const double* grid_nodes, int nx, int ny, int nz, int p_geo, int p, int nq,
-                                    double c, int vol_flux, int face_flux, double gamma, nsfr_ctx** out) {
-  if (nq < p + 1 || nq > NSFR_MAXN) {
+                                    double c, int vol_flux, int face_flux, double gamma, int precision,
+                                    nsfr_ctx** out) {
+  if (nq < p + 1 || nq > NSFR_MAXN || (precision != NSFR_FP64 && precision != NSFR_FP32_BULK)) {
     if (out) *out = nullptr;
     return NSFR_ERR_ARG;
   }
-  return setup_common(grid_nodes, nx, ny, nz, p_geo, p, nq, c, vol_flux, face_flux, gamma, NSFR_FP64,
+  return setup_common(grid_nodes, nx, ny, nz, p_geo, p, nq, c, vol_flux, face_flux, gamma, precision,
                       NSFR_NODES_LGL, out);
 }
 
@@ -514,7 +515,6 @@ nsfr_status nsfr_max_wavespeed(nsfr_ctx* ctx, const double* u, double* lam, void
 
 nsfr_status nsfr_entropy(nsfr_ctx* ctx, const double* u, double* out, void* stream) {
   if (!ctx) return NSFR_ERR_ARG;
-  if (ctx->uncol) return fail(ctx, NSFR_ERR_STATE, "nsfr_entropy needs a collocated context");
   if (!u || !out) return fail(ctx, NSFR_ERR_ARG, "NULL buffer");
   cudaStream_t s = (cudaStream_t)stream;
   ctx->last_stream = s;

@@ -8,16 +8,23 @@ namespace nsfr_k {
 // every thread keep up to 255 registers
 constexpr int epb_for(int n) { return n == 2 ? 16 : n == 3 ? 8 : n == 4 ? 4 : n == 5 ? 3 : n == 6 ? 2 : 1; }
 constexpr int threads_for(int n) { return epb_for(n) * 3 * n * n; }
-// The FP64 volume kernel keeps 30 n^3 doubles of shared memory per element
-// (records, metric rows, three direction slabs of line sums) and about 110
+// The FP64 volume kernel keeps 21 n^3 doubles of shared memory per element
+// (records, three direction slabs of line sums) and about 110
 // registers per thread; it is bound by FP64 issue, which wants as many warps
 // per SM as shared memory (228 KB) and the register file (64K, split evenly
 // over the four sub-partitions) allow.  Elements per CTA and CTAs per SM:
+// (the n = 5 shape can be set at build time, NSFR_VOL_EPB5 / NSFR_VOL_CTAS5, to measure others)
+#ifndef NSFR_VOL_EPB5
+#define NSFR_VOL_EPB5 2
+#endif
+#ifndef NSFR_VOL_CTAS5
+#define NSFR_VOL_CTAS5 3
+#endif
 constexpr int vol_epb(int n) {
-  return n == 2 ? 16 : n == 3 ? 8 : n == 4 ? 5 : n == 5 ? 2 : n == 6 ? 2 : 1;
+  return n == 2 ? 16 : n == 3 ? 8 : n == 4 ? 5 : n == 5 ? NSFR_VOL_EPB5 : n == 6 ? 2 : 1;
 }
 constexpr int vol_ctas(int n) {
-  return n == 2 ? 2 : n == 3 ? 2 : n == 4 ? 2 : n == 5 ? 3 : n == 6 ? 2 : n == 7 ? 2 : 1;
+  return n == 2 ? 2 : n == 3 ? 2 : n == 4 ? 2 : n == 5 ? NSFR_VOL_CTAS5 : n == 6 ? 2 : n == 7 ? 2 : 1;
 }
 constexpr int vol_threads(int n) { return vol_epb(n) * 3 * n * n; }
 // The FP32-bulk volume kernels: 7 n^3 doubles + 43 n^3 floats of shared memory
@@ -53,6 +60,30 @@ __device__ __forceinline__ void line_geometry(int d, int l0, int l1, int& base, 
 __device__ __forceinline__ double wperp_of(const double* w, int node, int n, int d) {
   const int i = node % n, j = (node / n) % n, k = node / (n * n);
   return d == 0 ? w[j] * w[k] : (d == 1 ? w[i] * w[k] : w[i] * w[j]);
+}
+
+// Y = A along direction d of X for nslab slabs of stride st (extents (ex, ey,
+// ez) in, extent m along d out); A is m x k row-major.  Ends with a barrier.
+__device__ inline void psweep(const double* __restrict__ A, int k, int m, const double* X, double* Y, int nslab, int st,
+                       int d, int ex, int ey, int ez) {
+  int ox = ex, oy = ey, oz = ez;
+  if (d == 0) ox = m;
+  if (d == 1) oy = m;
+  if (d == 2) oz = m;
+  const int per = ox * oy * oz;
+  const int sx = 1, sy = ex, sz = ex * ey;
+  const int sd = d == 0 ? sx : (d == 1 ? sy : sz);
+  for (int t = threadIdx.x; t < nslab * per; t += blockDim.x) {
+    const int sl = t / per, q = t % per;
+    const int x = q % ox, y = (q / ox) % oy, z = q / (ox * oy);
+    const int r = d == 0 ? x : (d == 1 ? y : z);
+    const double* in = X + (size_t)sl * st + (d == 0 ? 0 : x) * sx + (d == 1 ? 0 : y) * sy + (d == 2 ? 0 : z) * sz;
+    const double* a = A + r * k;
+    double acc = 0.0;
+    for (int b = 0; b < k; ++b) acc = fma(a[b], in[b * sd], acc);
+    Y[(size_t)sl * st + q] = acc;
+  }
+  __syncthreads();
 }
 
 }  // namespace nsfr_k

@@ -63,6 +63,10 @@ struct OpsGL {
   double ls_p[NSFR_MAXN];
   double A[NSFR_MAXN * NSFR_MAXN];
   double Pt[NSFR_MAXN * NSFR_MAXN];
+  // the same three in FP32 (the FP32-bulk epilogue of the uncollocated scheme)
+  float chif[NSFR_MAXN * NSFR_MAXN];
+  float Af[NSFR_MAXN * NSFR_MAXN];
+  float Ptf[NSFR_MAXN * NSFR_MAXN];
 };
 
 // Operators of the metric construction (Lobatto nodes of degree p).

@@ -328,6 +328,22 @@ void nsfr_build_ops_uncol(int p, int p_geo, int nq, double c, double gamma, OpsG
       for (int a = 0; a < ns; ++a) v += chi[t * ns + a] * Pt[a * nq + r];
       gl->A[r * nq + t] = v;
     }
+  // FP32 (and float-float) copies of what this function replaced, for the FP32-bulk kernel
+  for (int k = 0; k < nq * nq; ++k) {
+    gl->S1f[k] = (float)gl->S1[k];
+    gl->S1lo[k] = (float)(gl->S1[k] - (double)gl->S1f[k]);
+  }
+  for (int j = 0; j < nq; ++j) {
+    gl->tmf[j] = (float)gl->tm[j];
+    gl->tpf[j] = (float)gl->tp[j];
+    gl->tmlo[j] = (float)(gl->tm[j] - (double)gl->tmf[j]);
+    gl->tplo[j] = (float)(gl->tp[j] - (double)gl->tpf[j]);
+  }
+  for (int k = 0; k < NSFR_MAXN * NSFR_MAXN; ++k) {
+    gl->chif[k] = (float)gl->chi[k];
+    gl->Af[k] = (float)gl->A[k];
+    gl->Ptf[k] = (float)gl->Pt[k];
+  }
   // metric construction: degree-p Lobatto layer, evaluated at the GL points;
   // node coordinates at the Lobatto solution nodes
   geo->n = ns;

@@ -21,30 +21,6 @@
 namespace {
 using namespace nsfr_k;
 
-// Y = A along direction d of X for nslab slabs of stride st (extents (ex, ey,
-// ez) in, extent m along d out); A is m x k row-major.  Ends with a barrier.
-__device__ void psweep(const double* __restrict__ A, int k, int m, const double* X, double* Y, int nslab, int st,
-                       int d, int ex, int ey, int ez) {
-  int ox = ex, oy = ey, oz = ez;
-  if (d == 0) ox = m;
-  if (d == 1) oy = m;
-  if (d == 2) oz = m;
-  const int per = ox * oy * oz;
-  const int sx = 1, sy = ex, sz = ex * ey;
-  const int sd = d == 0 ? sx : (d == 1 ? sy : sz);
-  for (int t = threadIdx.x; t < nslab * per; t += blockDim.x) {
-    const int sl = t / per, q = t % per;
-    const int x = q % ox, y = (q / ox) % oy, z = q / (ox * oy);
-    const int r = d == 0 ? x : (d == 1 ? y : z);
-    const double* in = X + (size_t)sl * st + (d == 0 ? 0 : x) * sx + (d == 1 ? 0 : y) * sy + (d == 2 ? 0 : z) * sz;
-    const double* a = A + r * k;
-    double acc = 0.0;
-    for (int b = 0; b < k; ++b) acc = fma(a[b], in[b * sd], acc);
-    Y[(size_t)sl * st + q] = acc;
-  }
-  __syncthreads();
-}
-
 // the record of u(w), w entropy variables (the face-state conversion); flags
 // 2 beta <= 0 or NaN
 __device__ __forceinline__ Rec rec_from_entropy(const double w[5], const OpsGL& ops, const MathTables& T, int* flag) {

@@ -11,6 +11,7 @@
 #include <cfloat>
 
 #include "ffloat.cuh"
+#include "kernel_common.cuh"
 #include "nsfr_internal.h"
 
 namespace {
@@ -181,6 +182,107 @@ __global__ void diagnostics_kernel(const double* __restrict__ u, const double* _
   }
 }
 
+// the block's compensated pairs to partial[block][NDIAG][2]
+__device__ __forceinline__ void diag_block_out(Comp (&acc)[NDIAG], Comp (*red)[32], double* partial) {
+  for (int k = 0; k < NDIAG; ++k) {
+    Comp a = acc[k];
+    for (int o = 16; o > 0; o >>= 1) {
+      Comp b{__shfl_xor_sync(0xffffffffu, a.s, o), __shfl_xor_sync(0xffffffffu, a.c, o)};
+      a = comp_add(a, b);
+    }
+    if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < NDIAG) {
+    const int k = threadIdx.x;
+    Comp a{0.0, 0.0};
+    for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) a = comp_add(a, red[k][wi]);
+    partial[((size_t)blockIdx.x * NDIAG + k) * 2 + 0] = a.s;
+    partial[((size_t)blockIdx.x * NDIAG + k) * 2 + 1] = a.c;
+  }
+}
+
+// Diagnostics of the uncollocated scheme (solution coefficients on the ns
+// Lobatto nodes, N Gauss-Legendre points per direction), one element per CTA
+// (grid-stride).  With u_q = chi u^ the solution at the points and W J the
+// point weights: S = sum W J U(u_q), Q = sum W J u_q and KE = sum W J rho
+// |u|^2 / 2 (the GL quadrature of the solution); with the projected entropy
+// variables v~^ = Pi v(u_q) at the solution nodes and R^ = chi^T R_q the raw
+// residual there, the semi-discrete entropy rate -sum v~^ . R^ (Sec.
+// "Nonlinear Stability": the projected variables make the volume terms
+// telescope), its scale sum |v~^ . R^|, and sum R^.  Same outputs as
+// diagnostics_kernel.
+template <int N>
+__global__ void __launch_bounds__(256) diagnostics_uncol_kernel(const double* __restrict__ u,
+                                                                const double* __restrict__ R,
+                                                                const double* __restrict__ wj, OpsGL ops, int ne,
+                                                                double* partial) {
+  constexpr int NV = N * N * N, SL = 5 * NV;
+  extern __shared__ double sm[];
+  double* Us = sm;  // [5][NV]: u^ (first nsv of each slab), later v~^
+  double* Vq = Us + SL;
+  double* T1 = Vq + SL;
+  double* T2 = T1 + SL;
+  __shared__ Comp red[NDIAG][32];
+  const int ns = ops.ns, nsv = ns * ns * ns;
+  const double g = ops.gamma, gm1 = g - 1.0;
+  Comp acc[NDIAG];
+  for (int k = 0; k < NDIAG; ++k) acc[k] = Comp{0.0, 0.0};
+  for (int e = blockIdx.x; e < ne; e += gridDim.x) {
+    for (int t = threadIdx.x; t < 5 * nsv; t += blockDim.x) Us[(t / nsv) * NV + t % nsv] = u[(size_t)e * 5 * nsv + t];
+    __syncthreads();
+    nsfr_k::psweep(ops.chi, ns, N, Us, T1, 5, NV, 0, ns, ns, ns);
+    nsfr_k::psweep(ops.chi, ns, N, T1, T2, 5, NV, 1, N, ns, ns);
+    nsfr_k::psweep(ops.chi, ns, N, T2, Vq, 5, NV, 2, N, N, ns);
+    for (int t = threadIdx.x; t < NV; t += blockDim.x) {
+      double* v = Vq + t;
+      const double w = wj[(size_t)e * NV + t];
+      const double r = v[0], m0 = v[NV], m1 = v[2 * NV], m2 = v[3 * NV], E = v[4 * NV];
+      const double ir = 1.0 / r;
+      const double u0 = m0 * ir, u1 = m1 * ir, u2 = m2 * ir;
+      const double q2 = u0 * u0 + u1 * u1 + u2 * u2;
+      const double p = gm1 * (E - 0.5 * r * q2);
+      const double s = log(p) - g * log(r);
+      const double b = 0.5 * r / p;
+      neumaier(acc[0], w * (-r * s / gm1));
+      for (int k = 0; k < 5; ++k) neumaier(acc[3 + k], w * v[k * NV]);
+      neumaier(acc[8], w * 0.5 * r * q2);
+      v[0] = (g - s) / gm1 - b * q2;
+      v[NV] = 2.0 * b * u0;
+      v[2 * NV] = 2.0 * b * u1;
+      v[3 * NV] = 2.0 * b * u2;
+      v[4 * NV] = -2.0 * b;
+    }
+    __syncthreads();
+    nsfr_k::psweep(ops.Pi, N, ns, Vq, T1, 5, NV, 0, N, N, N);
+    nsfr_k::psweep(ops.Pi, N, ns, T1, T2, 5, NV, 1, ns, N, N);
+    nsfr_k::psweep(ops.Pi, N, ns, T2, Us, 5, NV, 2, ns, ns, N);
+    for (int t = threadIdx.x; t < nsv; t += blockDim.x) {
+      const double* Re = R + (size_t)e * 5 * nsv + t;
+      double vr = 0.0;
+      for (int k = 0; k < 5; ++k) {
+        vr += Us[k * NV + t] * Re[k * nsv];
+        neumaier(acc[9 + k], Re[k * nsv]);
+      }
+      neumaier(acc[1], -vr);
+      neumaier(acc[2], fabs(vr));
+    }
+    __syncthreads();
+  }
+  diag_block_out(acc, red, partial);
+}
+
+template <int N>
+cudaError_t launch_diag_uncol(nsfr_ctx* ctx, const double* u, const double* R, double* partial, int nblocks,
+                              cudaStream_t s) {
+  const size_t smem = (size_t)4 * 5 * N * N * N * sizeof(double);
+  cudaError_t err = cudaFuncSetAttribute(diagnostics_uncol_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  diagnostics_uncol_kernel<N><<<nblocks, 256, smem, s>>>(u, R, ctx->wj, ctx->ops, ctx->ne, partial);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 int nsfr_diag_blocks(nsfr_ctx* ctx) { return ctx->ne < 1024 ? ctx->ne : 1024; }
@@ -228,6 +330,22 @@ cudaError_t nsfr_launch_max_wavespeed(nsfr_ctx* ctx, const double* u, cudaStream
 
 cudaError_t nsfr_launch_diagnostics(nsfr_ctx* ctx, const double* u, const double* R, double* partial, int nblocks,
                                     cudaStream_t s) {
+  if (ctx->uncol) {
+    cudaError_t err = cudaErrorInvalidValue;
+    nsfr_prof_begin(ctx, 4, s);
+    switch (ctx->n) {
+      case 2: err = launch_diag_uncol<2>(ctx, u, R, partial, nblocks, s); break;
+      case 3: err = launch_diag_uncol<3>(ctx, u, R, partial, nblocks, s); break;
+      case 4: err = launch_diag_uncol<4>(ctx, u, R, partial, nblocks, s); break;
+      case 5: err = launch_diag_uncol<5>(ctx, u, R, partial, nblocks, s); break;
+      case 6: err = launch_diag_uncol<6>(ctx, u, R, partial, nblocks, s); break;
+      case 7: err = launch_diag_uncol<7>(ctx, u, R, partial, nblocks, s); break;
+      case 8: err = launch_diag_uncol<8>(ctx, u, R, partial, nblocks, s); break;
+    }
+    nsfr_prof_end(ctx, s);
+    ctx->launches++;
+    return err;
+  }
   int threads = ((ctx->nv + 31) / 32) * 32;
   if (threads < 64) threads = 64;
   nsfr_prof_begin(ctx, 4, s);

@@ -340,6 +340,84 @@ __device__ __forceinline__ void rank_one_sweep_f(float* X, int nel, int d, bool 
   }
 }
 
+// Y = A along direction d of X (FP32), nslab slabs of stride st, extents (ex, ey,
+// ez) in and m along d out; A is m x k row-major, or with trans the transpose of
+// a k x m row-major matrix.  Ends with a barrier.
+__device__ void fsweep(const float* __restrict__ A, bool trans, int k, int m, const float* X, float* Y, int nslab,
+                       int st, int d, int ex, int ey, int ez) {
+  int ox = ex, oy = ey, oz = ez;
+  if (d == 0) ox = m;
+  if (d == 1) oy = m;
+  if (d == 2) oz = m;
+  const int per = ox * oy * oz;
+  for (int t = threadIdx.x; t < nslab * per; t += blockDim.x) {
+    const int sl = t / per, q = t % per;
+    const int x = q % ox, y = (q / ox) % oy, z = q / (ox * oy);
+    const float* in = X + (size_t)sl * st;
+    float acc = 0.0f;
+    for (int b = 0; b < k; ++b) {
+      int xi = x, yi = y, zi = z, r;
+      if (d == 0) { r = x; xi = b; }
+      else if (d == 1) { r = y; yi = b; }
+      else { r = z; zi = b; }
+      const float a = trans ? A[b * m + r] : A[r * k + b];
+      acc = fmaf(a, in[xi + ex * (yi + ey * zi)], acc);
+    }
+    Y[(size_t)sl * st + q] = acc;
+  }
+  __syncthreads();
+}
+
+// The FP32-bulk epilogue of the uncollocated scheme (solution on the ns Lobatto
+// nodes, the N GL points of the line phase), the FP32 form of the FP64 kernel's:
+// R_q (FP64, [nel][5][NV]) in FP32, then R^ = chi^T R_q (raw residual) or
+// du^/dt = -Pi~ (W J)^{-1} (chi Pi~1)^T R_q by dense 1D sweeps, and the store or
+// the RK stage update on the ns^3 solution nodes.  X and Y: [nel][5][NV] floats.
+template <int N>
+__device__ void uncol_epilogue_f(const double* Rd, float* X, float* Y, int nel, int e0, const OpsGL& ops,
+                                 const float* __restrict__ invwj32, int epi, const RkArgs& rk, double* out) {
+  constexpr int NV = N * N * N;
+  const int ns = ops.ns, nsv = ns * ns * ns, nsl = nel * 5;
+  for (int t = threadIdx.x; t < nsl * NV; t += blockDim.x) X[t] = d2f_i(Rd[t]);
+  __syncthreads();
+  const float* res;
+  if (epi == EPI_RAW) {
+    fsweep(ops.chif, true, N, ns, X, Y, nsl, NV, 0, N, N, N);
+    fsweep(ops.chif, true, N, ns, Y, X, nsl, NV, 1, ns, N, N);
+    fsweep(ops.chif, true, N, ns, X, Y, nsl, NV, 2, ns, ns, N);
+    res = Y;
+  } else {
+    fsweep(ops.Af, false, N, N, X, Y, nsl, NV, 0, N, N, N);
+    fsweep(ops.Af, false, N, N, Y, X, nsl, NV, 1, N, N, N);
+    fsweep(ops.Af, false, N, N, X, Y, nsl, NV, 2, N, N, N);
+    for (int t = threadIdx.x; t < nsl * NV; t += blockDim.x) Y[t] *= invwj32[(size_t)(e0 + t / (5 * NV)) * NV + t % NV];
+    __syncthreads();
+    fsweep(ops.Ptf, false, N, ns, Y, X, nsl, NV, 0, N, N, N);
+    fsweep(ops.Ptf, false, N, ns, X, Y, nsl, NV, 1, ns, N, N);
+    fsweep(ops.Ptf, false, N, ns, Y, X, nsl, NV, 2, ns, ns, N);
+    res = X;
+  }
+  const size_t off = (size_t)e0 * 5 * nsv;
+  const double bdt = rk.b * rk.dt, adt = rk.a_next * rk.dt;
+  for (int t = threadIdx.x; t < nsl * nsv; t += blockDim.x) {
+    const double r = f2d_i(res[(size_t)(t / nsv) * NV + t % nsv]);
+    if (epi == EPI_RAW) {
+      out[off + t] = r;
+    } else if (epi == EPI_DUDT) {
+      out[off + t] = -r;
+    } else {
+      const double k = -r;
+      if (rk.last) {
+        rk.unext[off + t] = fma(bdt, k, rk.acc[off + t]);
+      } else {
+        const double u0 = rk.u0[off + t];
+        rk.acc[off + t] = fma(bdt, k, rk.first ? u0 : rk.acc[off + t]);
+        rk.unext[off + t] = fma(adt, k, u0);
+      }
+    }
+  }
+}
+
 // shared-memory layout per element (SoA over the NV nodes)
 //   floats : r, 2 beta as float-float (the bytes of 2 doubles) 4 NV
 //   doubles: R (combined), epilogue                            5 NV
@@ -585,6 +663,10 @@ __global__ void __launch_bounds__(bulk_threads(N, FF), bulk_ctas(N, FF))
     }
   }
   __syncthreads();
+  if (ops.uncol) {  // solution on the Lobatto nodes: back from the GL points (Pf is free again)
+    uncol_epilogue_f<N>(Rd, Xf, Xf + (size_t)epb * 5 * NV, nel, e0, ops, invwj32, epi, rk, out);
+    return;
+  }
   const int total = nel * 5 * NV;
   const size_t off = (size_t)e0 * 5 * NV;
   if (epi == EPI_RAW) {

@@ -49,7 +49,7 @@ def load_library(path=LIB_PATH):
     lib = ctypes.CDLL(path)
     vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     lib.nsfr_setup.argtypes = [vp, i, i, i, i, i, d, i, i, d, i, i, ctypes.POINTER(vp)]
-    lib.nsfr_setup_uncollocated.argtypes = [vp, i, i, i, i, i, i, d, i, i, d, ctypes.POINTER(vp)]
+    lib.nsfr_setup_uncollocated.argtypes = [vp, i, i, i, i, i, i, d, i, i, d, i, ctypes.POINTER(vp)]
     lib.nsfr_setup_uncollocated.restype = i
     lib.nsfr_setup.restype = i
     for name in ("nsfr_residual", "nsfr_residual_raw"):
@@ -213,11 +213,11 @@ class Solver:
                                       FACE_FLUX[face_flux],
                                       float(gamma), PRECISION[precision], NODES[nodes], ctypes.byref(h))
         else:
-            if precision != "fp64":
-                raise ValueError("the uncollocated scheme is FP64 only")
+            if precision not in ("fp64", "fp32_bulk"):
+                raise ValueError("the uncollocated scheme has the fp64 and fp32_bulk precisions")
             st = self._lib.nsfr_setup_uncollocated(_ptr(grid_nodes), nx, ny, nz, pg, p, int(nq), float(c),
                                                    VOL_FLUX[vol_flux], FACE_FLUX[face_flux], float(gamma),
-                                                   ctypes.byref(h))
+                                                   PRECISION[precision], ctypes.byref(h))
         if st != NSFR_OK:
             raise NSFRError(st, "nsfr_setup failed")
         self._h = h

@@ -101,10 +101,11 @@ def test_uncollocated_rk4_step_matches_oracle():
 def test_uncollocated_context_rejects_what_it_does_not_support():
     from paper_2312_07725_gb300 import NSFRError, Solver
     ctrl, P, S, u = _case((2, 2, 2), 2, 4)
+    ud = torch.from_numpy(u).cuda()
     with pytest.raises(NSFRError):
-        S.entropy(torch.from_numpy(u).cuda())
+        S.vjp(ud, torch.ones_like(ud), torch.zeros_like(ud))
     with pytest.raises(ValueError):
-        Solver(np.ascontiguousarray(ctrl), (2, 2, 2), 2, nq=4, precision="fp32_bulk")
+        Solver(np.ascontiguousarray(ctrl), (2, 2, 2), 2, nq=4, precision="fp32_bulk_ff")
     with pytest.raises(NSFRError):
         Solver(np.ascontiguousarray(ctrl), (2, 2, 2), 2, nq=2)  # nq < p+1
 
@@ -122,3 +123,59 @@ def test_uncollocated_entropy_conservation_of_the_library_residual(p, nq):
     Vh, _ = P.projected(P.to_internal(u))
     prod = P.to_abi(Vh) * R.cpu().numpy()
     assert abs(prod.sum()) < 1e-13 * np.abs(prod).sum()
+
+
+@pytest.mark.parametrize("p,nq,face_flux", [(3, 4, "ec"), (3, 6, "ec"), (4, 7, "ec"), (2, 5, "ec_roe")])
+def test_uncollocated_diagnostics_match_oracle(p, nq, face_flux):
+    """nsfr_entropy on the uncollocated scheme against the oracle's diagnostics: the entropy,
+    kinetic energy and GL quadrature of the solution at 1e-13 relative, the entropy rate
+    -v~^ . R^ at the paper's 1e-13 of its scale for EC faces (negative with Roe), the scale
+    and sum R^ against the oracle's."""
+    _, P, S, u = _case((2, 2, 2), p, nq, "hu", face_flux)
+    S.set_metrics(*_metrics_abi(P))
+    g = S.entropy(torch.from_numpy(u).cuda())
+    o = P.diagnostics(P.to_internal(u))
+    assert abs(g["entropy"] - o["entropy"]) < 1e-13 * abs(o["entropy"])
+    assert abs(g["kinetic_energy"] - o["kinetic_energy"]) < 1e-13 * abs(o["kinetic_energy"])
+    qabs = sum(abs(q) for q in o["Q"])
+    for k in range(5):
+        assert abs(g["Q"][k] - o["Q"][k]) < 1e-13 * qabs
+    assert abs(g["entropy_rate_scale"] - o["entropy_rate_scale"]) < 1e-10 * o["entropy_rate_scale"]
+    if face_flux == "ec":
+        assert abs(g["entropy_rate"]) < 1e-13 * g["entropy_rate_scale"]
+    else:
+        assert g["entropy_rate"] < -1e-8 * g["entropy_rate_scale"]
+        assert abs(g["entropy_rate"] - o["entropy_rate"]) < 1e-10 * o["entropy_rate_scale"]
+
+
+@pytest.mark.parametrize("p,nq,shape,c_kind,face_flux", [(2, 3, (3, 2, 2), "hu", "ec"), (3, 5, (2, 2, 2), "hu", "ec"),
+                                                         (4, 6, (3, 3, 1), "dg", "ec_roe"), (3, 6, (2, 1, 2), "hu", "ec_es")])
+def test_uncollocated_fp32_bulk_within_1e5(p, nq, shape, c_kind, face_flux):
+    """The FP32-bulk form of the uncollocated scheme (FP32 flux differencing and return to
+    the solution nodes, FP64 entropy projection and face fluxes): du^/dt within 1e-5 of the
+    oracle over all variables, per variable within max(1e-5, 4x the oracle's change under a
+    2^-24 relative change of the state); the raw residual likewise, and one RK4 step."""
+    from paper_2312_07725_gb300 import Solver
+    ctrl, P, _, u = _case(shape, p, nq, c_kind, face_flux)
+    c = 0.0 if c_kind == "dg" else c_hu(p)
+    B = Solver(np.ascontiguousarray(ctrl), shape, p, c=c, face_flux=face_flux, nq=nq, precision="fp32_bulk")
+    B.set_metrics(*_metrics_abi(P))
+    ud = torch.from_numpy(u).cuda()
+    D, R = torch.empty_like(ud), torch.empty_like(ud)
+    B.residual(ud, D)
+    B.residual_raw(ud, R)
+    torch.cuda.synchronize()
+
+    def dudt(x):
+        return P.to_abi(P.dudt(P.to_internal(x)))
+
+    def res(x):
+        return P.to_abi(P.residual(P.to_internal(x)))
+
+    check_parity(D.cpu().numpy(), dudt(u), 1e-5, ulp_sensitivity(dudt, u, rel=2.0 ** -24), what="bulk du^/dt")
+    check_parity(R.cpu().numpy(), res(u), 1e-5, ulp_sensitivity(res, u, rel=2.0 ** -24), what="bulk R^")
+    dt = 2e-3
+    u1 = P.rk4_step_abi(u, dt)
+    B.rk_step(ud, dt=dt)
+    torch.cuda.synchronize()
+    assert rel_l2(ud.cpu().numpy() - u, u1 - u) < 1e-5

@@ -122,3 +122,38 @@ def test_overintegrated_order_of_accuracy():
     errs = [_wave_error(p, p + 3, N) for N in (4, 8, 16)]
     order = math.log(errs[-2] / errs[-1]) / math.log(2.0)
     assert order > (p + 1) - 0.25, (errs, order)
+
+
+@pytest.mark.parametrize("nq", [4, 6])
+def test_uncollocated_diagnostics_of_a_constant_state(nq):
+    """A constant state is a polynomial of every degree, so chi reproduces it at the GL
+    points: S = -rho s/(gamma-1) V, Q = u V and KE = rho|u|^2/2 V with V = (2 pi)^3; its
+    residual and entropy rate vanish."""
+    p = 3
+    ctrl = wl.control_points(2, 2, 1, p, -math.pi, math.pi, wl.warp_tgv)
+    P = UncollocatedProblem(ctrl, (2, 2, 1), p, nq=nq)
+    rho, vel, pr = 1.3, (0.7, -0.4, 0.25), 2.1
+    U = P.to_internal(wl.free_stream_state(P.node_coords(ctrl), rho, vel, pr))
+    d = P.diagnostics(U)
+    V = (2 * math.pi) ** 3
+    s = math.log(pr) - 1.4 * math.log(rho)
+    assert abs(d["entropy"] - (-rho * s / 0.4 * V)) < 1e-12 * abs(rho * s / 0.4 * V)
+    E = pr / 0.4 + 0.5 * rho * sum(v * v for v in vel)
+    for k, q in enumerate([rho, rho * vel[0], rho * vel[1], rho * vel[2], E]):
+        assert abs(d["Q"][k] - q * V) < 1e-12 * abs(q * V)
+    ke = 0.5 * rho * sum(v * v for v in vel) * V
+    assert abs(d["kinetic_energy"] - ke) < 1e-12 * ke
+    assert abs(d["entropy_rate"]) < 1e-12 * abs(ke)
+
+
+def test_uncollocated_taylor_green_kinetic_energy_is_pi_cubed():
+    """(1/2) int rho |u|^2 = pi^3 at t = 0 on the warped [-pi, pi]^3; the GL quadrature of the
+    Lobatto interpolant converges to it as p grows (over-integration does not change the
+    interpolant, only its quadrature)."""
+    errs = []
+    for p in (3, 4, 5):
+        ctrl = wl.control_points(4, 4, 4, p, -math.pi, math.pi, wl.warp_tgv)
+        P = UncollocatedProblem(ctrl, (4, 4, 4), p, nq=p + 2)
+        U = P.to_internal(wl.tgv_state(P.node_coords(ctrl)))
+        errs.append(abs(P.diagnostics(U)["kinetic_energy"] - math.pi ** 3) / math.pi ** 3)
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-5, errs
