@@ -93,6 +93,15 @@ __device__ __forceinline__ double rcp_full(double x) {
   return fma(r, fma(e, e, e), r);
 }
 
+// x 2^k (k small) by moving the exponent field: exact, and off the FP64 pipe.
+// Zero stays zero; a subnormal x (never a state quantity) takes the multiply.
+template <int K>
+__device__ __forceinline__ double mul_pow2(double x) {
+  const int hi = __double2hiint(x);
+  if ((hi & 0x7ff00000) == 0) return x * (K >= 0 ? (double)(1LL << K) : 1.0 / (double)(1LL << -K));
+  return __hiloint2double(hi + K * (1 << 20), __double2loint(x));
+}
+
 // u < NSFR_LM_EPS for u = f^2 >= 0, decided on the integer bit pattern
 __device__ __forceinline__ bool lm_small(double u) {
   return __double_as_longlong(u) < __double_as_longlong(NSFR_LM_EPS);

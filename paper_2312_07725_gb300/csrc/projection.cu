@@ -30,16 +30,16 @@ __device__ __forceinline__ Rec rec_from_entropy(const double w[5], const OpsGL& 
   const double iv5 = rcp_full(w[4]);
   const double u0 = -w[1] * iv5, u1 = -w[2] * iv5, u2 = -w[3] * iv5;
   const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
-  const double sent = g - gm1 * fma(0.5 * b2, q2, w[0]);
+  const double sent = g - gm1 * fma(mul_pow2<-1>(b2), q2, w[0]);
   const double L5 = nsfr_log(b2, T);
   const double lr = -(sent + L5) * ops.inv_gm1;
   Rec P;
   P.r = nsfr_exp(lr, T);
   P.b2 = b2;
-  P.u0 = 0.5 * u0;
-  P.u1 = 0.5 * u1;
-  P.u2 = 0.5 * u2;
-  P.qq = 0.25 * q2;
+  P.u0 = mul_pow2<-1>(u0);
+  P.u1 = mul_pow2<-1>(u1);
+  P.u2 = mul_pow2<-1>(u2);
+  P.qq = mul_pow2<-2>(q2);
   P.lr = lr;
   P.lb = L5 - ln2;
   return P;
@@ -78,13 +78,13 @@ __global__ void __launch_bounds__(256) projection_kernel(const double* __restric
     const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
     const double p = gm1 * fma(-0.5 * r, q2, E);
     if (!(r > 0.0) || !(p > 0.0)) atomicOr(flag, 1);
-    const double b = 0.5 * r * rcp_full(p);
+    const double b2 = r * rcp_full(p);  // 2 beta
     const double s = nsfr_log(p, T) - g * nsfr_log(r, T);
-    v[0] = (g - s) * ops.inv_gm1 - b * q2;
-    v[NV] = 2.0 * b * u0;
-    v[2 * NV] = 2.0 * b * u1;
-    v[3 * NV] = 2.0 * b * u2;
-    v[4 * NV] = -2.0 * b;
+    v[0] = fma(-mul_pow2<-1>(b2), q2, (g - s) * ops.inv_gm1);
+    v[NV] = b2 * u0;
+    v[2 * NV] = b2 * u1;
+    v[3 * NV] = b2 * u2;
+    v[4 * NV] = -b2;
   }
   __syncthreads();
   // v~^ = Pi v(u_q), into Us

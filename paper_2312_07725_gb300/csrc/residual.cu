@@ -58,22 +58,22 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
     const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
     const double p = gm1 * fma(-0.5 * r, q2, E);
     if (!(r > 0.0) || !(p > 0.0)) atomicOr(flag, 1);
-    const double b = 0.5 * r * rcp_full(p);
+    const double b2 = r * rcp_full(p);  // 2 beta = rho / p
     const double lr = nsfr_log(r, T), lp = nsfr_log(p, T);
     const double s = lp - g * lr;
     double* v = sm + (size_t)le * 5 * NV + node;
-    v[0] = (g - s) * ops.inv_gm1 - b * q2;
-    v[NV] = 2.0 * b * u0;
-    v[2 * NV] = 2.0 * b * u1;
-    v[3 * NV] = 2.0 * b * u2;
-    v[4 * NV] = -2.0 * b;
+    v[0] = fma(-mul_pow2<-1>(b2), q2, (g - s) * ops.inv_gm1);
+    v[NV] = b2 * u0;
+    v[2 * NV] = b2 * u1;
+    v[3 * NV] = b2 * u2;
+    v[4 * NV] = -b2;
     Rec a;
     a.r = r;
-    a.b2 = 2.0 * b;
-    a.u0 = 0.5 * u0;
-    a.u1 = 0.5 * u1;
-    a.u2 = 0.5 * u2;
-    a.qq = 0.25 * q2;
+    a.b2 = b2;
+    a.u0 = mul_pow2<-1>(u0);
+    a.u1 = mul_pow2<-1>(u1);
+    a.u2 = mul_pow2<-1>(u2);
+    a.qq = mul_pow2<-2>(q2);
     a.lr = lr;
     a.lb = lr - lp - ln2;  // ln beta = ln rho - ln 2p
     store_rec(nrec + (size_t)e * NSFR_NFIELD * NV + node, NV, a);
@@ -106,16 +106,16 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
     const double iv5 = rcp_full(w[4]);
     const double u0 = -w[1] * iv5, u1 = -w[2] * iv5, u2 = -w[3] * iv5;
     const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
-    const double sent = g - gm1 * fma(0.5 * b2, q2, w[0]);
+    const double sent = g - gm1 * fma(mul_pow2<-1>(b2), q2, w[0]);
     const double L5 = nsfr_log(b2, T);        // ln(2 beta)
     const double lr = -(sent + L5) * ops.inv_gm1;  // s = (1-gamma) ln rho - ln(2 beta)
     Rec P;
     P.r = nsfr_exp(lr, T);
     P.b2 = b2;
-    P.u0 = 0.5 * u0;
-    P.u1 = 0.5 * u1;
-    P.u2 = 0.5 * u2;
-    P.qq = 0.25 * q2;
+    P.u0 = mul_pow2<-1>(u0);
+    P.u1 = mul_pow2<-1>(u1);
+    P.u2 = mul_pow2<-1>(u2);
+    P.qq = mul_pow2<-2>(q2);
     P.lr = lr;
     P.lb = L5 - ln2;
     store_rec(face + (((size_t)e * 6 + 2 * d + s) * NSFR_NFIELD) * NFP + line, NFP, P);
