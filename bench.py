@@ -547,11 +547,12 @@ def run_ours(args, rank, ws, dist):
     m64 = measure(args, ctrl, u0, "fp64", dist, rank, ws, args.steps)
     d64 = m64.pop("dudt")
     m32, mff = None, None
-    if args.nq is None and args.modes == "both":  # the FP32-bulk forms exist for the collocated scheme
+    if args.modes == "both":  # the uncollocated scheme has the fp32_bulk form, not the float-float one
         m32 = measure(args, ctrl, u0, "fp32_bulk", dist, rank, ws, args.steps)
         d32 = m32.pop("dudt")
         bulk_err = float(np.linalg.norm((d32 - d64).ravel()) / np.linalg.norm(d64.ravel()))
         del d32
+    if args.nq is None and args.modes == "both":
         mff = measure(args, ctrl, u0, "fp32_bulk_ff", dist, rank, ws, args.steps)
         dff = mff.pop("dudt")
         ff_err = float(np.linalg.norm((dff - d64).ravel()) / np.linalg.norm(d64.ravel()))
@@ -583,11 +584,13 @@ def run_ours(args, rank, ws, dist):
             "peak_source": peak_src,
             "peak_measured_probe": probe64, "frac_of_measured_probe": achieved / probe64 if probe64 else None,
             "flops_per_launch": flops, "flux_evals_per_element": counts}
-    rk = {"fp64": roofline_kernels(m64["kernels"], p, ne_launch, "fp64", clk, peaks, cfg["c"] != 0.0)}
-    for nm, m in (("fp32_bulk", m32), ("fp32_bulk_ff", mff)):
-        if m is not None:
-            rk[nm] = roofline_kernels(m["kernels"], p, ne_launch, nm, m["clocks"], peaks, cfg["c"] != 0.0)
-    if adj is not None:
+    rk = None
+    if args.nq is None:  # the stage models are those of the collocated scheme
+        rk = {"fp64": roofline_kernels(m64["kernels"], p, ne_launch, "fp64", clk, peaks, cfg["c"] != 0.0)}
+        for nm, m in (("fp32_bulk", m32), ("fp32_bulk_ff", mff)):
+            if m is not None:
+                rk[nm] = roofline_kernels(m["kernels"], p, ne_launch, nm, m["clocks"], peaks, cfg["c"] != 0.0)
+    if adj is not None and rk is not None:
         fp64_nom = peak
         rk["adjoint"] = {}
         for nm, work in adjoint_kernel_models(p, ne_launch, cfg["c"] != 0.0).items():

@@ -140,9 +140,9 @@ nsfr_status nsfr_setup(const double* grid_nodes, int nx, int ny, int nz, int p_g
  * NSFR_FP32_BULK (the flux differencing in FP32 as for nsfr_setup, the
  * entropy projection and the face fluxes in FP64, and the return to the
  * solution nodes -- chi^T, or (chi Pi~1)^T, 1/(W J), Pi~1 -- as FP32 sweeps);
- * anything else is NSFR_ERR_ARG.  nsfr_vjp returns NSFR_ERR_STATE for such a
- * context.  With nq = p+1 the scheme is the GL-collocated one written in the
- * LGL basis.
+ * anything else is NSFR_ERR_ARG.  nsfr_vjp offers the state cotangent only
+ * (x_bar NULL).  With nq = p+1 the scheme is the GL-collocated one written in
+ * the LGL basis.
  */
 nsfr_status nsfr_setup_uncollocated(const double* grid_nodes, int nx, int ny, int nz, int p_geo, int p, int nq,
                                     double c, int vol_flux, int face_flux, double gamma, int precision,
@@ -263,9 +263,13 @@ nsfr_status nsfr_entropy(nsfr_ctx* ctx, const double* u, double* out, void* stre
  *            control points; skipped when x_bar is NULL).
  *   u, dudt_bar, u_bar  device, [N_e][5][n^3] FP64.
  *   x_bar               device or NULL, [N_e][(p_geo+1)^3][3] FP64.
- * FP64 contexts with the EC face flux only (NSFR_ERR_STATE otherwise).  Runs
- * the face-state pass of u (and, for x_bar, the residual R(u)) first;
- * asynchronous on the stream.
+ * FP64 contexts with the EC face flux and Chandrashekar's volume flux only
+ * (NSFR_ERR_STATE otherwise).  For an uncollocated context (state on the
+ * Lobatto nodes) the state cotangent is offered (x_bar must be NULL): the
+ * flux differencing is reversed on the GL points and the entropy projection
+ * (chi, v(u), Pi, u(v) at the points and the faces) back to the solution
+ * nodes.  Runs the face-state pass of u (and, for x_bar, the residual R(u))
+ * first; asynchronous on the stream.
  */
 nsfr_status nsfr_vjp(nsfr_ctx* ctx, const double* u, const double* dudt_bar, double* u_bar,
                      double* x_bar, void* stream);

@@ -58,7 +58,7 @@ void free_all(nsfr_ctx* c) {
   double* dbl[] = {c->ctrl, c->metric, c->J, c->invwj, c->wj, c->nfp_plus, c->xyz, c->face, c->nrec, c->fstar,
                    c->metric_s, c->nf_s, c->pair_rows, c->uq,
                    c->ustage, c->acc, c->rtmp, c->hbuf_in, c->hbuf_out, c->red,
-                   c->vjp_fown, c->vjp_fnbr, c->vjp_nfbar, c->vjp_mbar, c->vjp_jbar, c->src};
+                   c->vjp_fown, c->vjp_fnbr, c->vjp_nfbar, c->vjp_mbar, c->vjp_jbar, c->vjp_pbq, c->src};
   for (double* p : dbl)
     if (p) cudaFree(p);
   if (c->metric32) cudaFree(c->metric32);
@@ -563,8 +563,9 @@ nsfr_status nsfr_entropy(nsfr_ctx* ctx, const double* u, double* out, void* stre
 nsfr_status nsfr_vjp(nsfr_ctx* ctx, const double* u, const double* dudt_bar, double* u_bar, double* x_bar,
                      void* stream) {
   if (!ctx) return NSFR_ERR_ARG;
-  if (ctx->precision != NSFR_FP64 || ctx->uncol)
-    return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp needs a collocated FP64 context");
+  if (ctx->precision != NSFR_FP64) return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp needs an FP64 context");
+  if (ctx->uncol && x_bar)
+    return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp of an uncollocated context offers the state cotangent only");
   if (ctx->face_flux != NSFR_FACE_EC) return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp supports the EC face flux");
   if (ctx->vol_flux != NSFR_FLUX_CHANDRASHEKAR)
     return fail(ctx, NSFR_ERR_STATE, "nsfr_vjp supports the Chandrashekar volume flux");
@@ -583,6 +584,7 @@ nsfr_status nsfr_vjp(nsfr_ctx* ctx, const double* u, const double* dudt_bar, dou
     CK(dalloc(&ctx->vjp_mbar, ne * 9 * nv), "cudaMalloc(vjp)");
     CK(dalloc(&ctx->vjp_jbar, ne * nv), "cudaMalloc(vjp)");
   }
+  if (ctx->uncol && !ctx->vjp_pbq) CK(dalloc(&ctx->vjp_pbq, ne * 5 * nv), "cudaMalloc(vjp)");
   if (!ctx->rtmp) CK(dalloc(&ctx->rtmp, state_count(ctx)), "cudaMalloc(rtmp)");
   CK(cudaMemsetAsync(ctx->vjp_mbar, 0, ne * 9 * nv * sizeof(double), s), "cudaMemsetAsync");
   CK(cudaMemsetAsync(ctx->vjp_jbar, 0, ne * nv * sizeof(double), s), "cudaMemsetAsync");

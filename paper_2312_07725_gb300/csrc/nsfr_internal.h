@@ -142,6 +142,7 @@ struct nsfr_ctx {
   double* vjp_nfbar = nullptr; // [ne][6][3][nfp] face-row cotangents, per face of the element
   double* vjp_mbar = nullptr;  // [ne][9][nv] volume metric-row cotangents
   double* vjp_jbar = nullptr;  // [ne][nv] Jacobian cotangents
+  double* vjp_pbq = nullptr;   // [ne][5][nv] record cotangents at the GL points (uncollocated contexts)
   double* hbuf_in = nullptr;  // staging for host pointers [ne][5][nv]
   double* hbuf_out = nullptr;
   double* red = nullptr;      // reduction scratch

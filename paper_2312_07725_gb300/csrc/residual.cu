@@ -179,82 +179,6 @@ __device__ __forceinline__ void rank_one_sweep(double* X, int nel, int d, bool t
   }
 }
 
-// Y = A along direction d of X for nslab slabs (stride st each, extents
-// (ex, ey, ez) in, extent m along d out); A is m x k row-major, or, with
-// trans, the transpose of a k x m row-major matrix.  Ends with a barrier.
-__device__ void slab_sweep(const double* __restrict__ A, bool trans, int k, int m, const double* X, double* Y,
-                           int nslab, int st, int d, int ex, int ey, int ez) {
-  int ox = ex, oy = ey, oz = ez;
-  if (d == 0) ox = m;
-  if (d == 1) oy = m;
-  if (d == 2) oz = m;
-  const int per = ox * oy * oz;
-  for (int t = threadIdx.x; t < nslab * per; t += blockDim.x) {
-    const int sl = t / per, q = t % per;
-    const int x = q % ox, y = (q / ox) % oy, z = q / (ox * oy);
-    const double* in = X + (size_t)sl * st;
-    double acc = 0.0;
-    for (int b = 0; b < k; ++b) {
-      int xi = x, yi = y, zi = z, r;
-      if (d == 0) { r = x; xi = b; }
-      else if (d == 1) { r = y; yi = b; }
-      else { r = z; zi = b; }
-      const double a = trans ? A[b * m + r] : A[r * k + b];
-      acc = fma(a, in[xi + ex * (yi + ey * zi)], acc);
-    }
-    Y[(size_t)sl * st + q] = acc;
-  }
-  __syncthreads();
-}
-
-// Epilogue of the uncollocated scheme for the nel elements of a CTA, R_q (the
-// line-wise residual at the N^3 GL points) in X[nel*5][NV]; Y is a second
-// buffer of the same size.  R^ = chi^T R_q (raw residual) or
-// du^/dt = -Pi~ (W J)^{-1} Pi~^T chi^T R_q = -Pi~ (W J)^{-1} A R_q with
-// A = (chi Pi~1)^T per direction, on the ns^3 solution nodes; then the store
-// or the RK stage update as in the collocated epilogue.
-template <int N>
-__device__ void uncol_epilogue(double* X, double* Y, int nel, int e0, const OpsGL& ops,
-                               const double* __restrict__ invwj, int epi, const RkArgs& rk, double* out) {
-  constexpr int NV = N * N * N;
-  const int ns = ops.ns, nsv = ns * ns * ns, nsl = nel * 5;
-  double* res;
-  if (epi == EPI_RAW) {
-    slab_sweep(ops.chi, true, N, ns, X, Y, nsl, NV, 0, N, N, N);
-    slab_sweep(ops.chi, true, N, ns, Y, X, nsl, NV, 1, ns, N, N);
-    slab_sweep(ops.chi, true, N, ns, X, Y, nsl, NV, 2, ns, ns, N);
-    res = Y;
-  } else {
-    slab_sweep(ops.A, false, N, N, X, Y, nsl, NV, 0, N, N, N);
-    slab_sweep(ops.A, false, N, N, Y, X, nsl, NV, 1, N, N, N);
-    slab_sweep(ops.A, false, N, N, X, Y, nsl, NV, 2, N, N, N);
-    for (int t = threadIdx.x; t < nsl * NV; t += blockDim.x) Y[t] *= invwj[(size_t)(e0 + t / (5 * NV)) * NV + t % NV];
-    __syncthreads();
-    slab_sweep(ops.Pt, false, N, ns, Y, X, nsl, NV, 0, N, N, N);
-    slab_sweep(ops.Pt, false, N, ns, X, Y, nsl, NV, 1, ns, N, N);
-    slab_sweep(ops.Pt, false, N, ns, Y, X, nsl, NV, 2, ns, ns, N);
-    res = X;
-  }
-  const size_t off = (size_t)e0 * 5 * nsv;
-  for (int t = threadIdx.x; t < nsl * nsv; t += blockDim.x) {
-    const double r = res[(size_t)(t / nsv) * NV + t % nsv];
-    if (epi == EPI_RAW) {
-      out[off + t] = r;
-    } else if (epi == EPI_DUDT) {
-      out[off + t] = -r;
-    } else {
-      const double k = -r;
-      if (rk.last) {
-        rk.unext[off + t] = fma(rk.b * rk.dt, k, rk.acc[off + t]);
-      } else {
-        const double u0 = rk.u0[off + t];
-        rk.acc[off + t] = fma(rk.b * rk.dt, k, rk.first ? u0 : rk.acc[off + t]);
-        rk.unext[off + t] = fma(rk.a_next * rk.dt, k, u0);
-      }
-    }
-  }
-}
-
 // Two-point flux of the line phase, up to a factor it returns (the caller folds
 // it into its accumulation weights): Chandrashekar's (VF =
 // NSFR_FLUX_CHANDRASHEKAR) divided by rho_a + rho_b, or Ranocha's pressure

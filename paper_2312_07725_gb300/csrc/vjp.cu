@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(threads_for(N), 1)
                       const double* __restrict__ face, const double* __restrict__ wj, OpsGL ops, int nx, int ny,
                       int nz, int ne, double* __restrict__ ubar, double* __restrict__ fbar_own,
                       double* __restrict__ fbar_nbr, double* __restrict__ nfbar, double* __restrict__ mbar,
-                      double* __restrict__ Jbar) {
+                      double* __restrict__ Jbar, const double* __restrict__ nrec, double* __restrict__ pbq) {
   constexpr int NV = N * N * N, NFP = N * N, NL = 3 * NFP;
   extern __shared__ double sm[];
   const int epb = blockDim.x / NL;
@@ -249,6 +249,38 @@ __global__ void __launch_bounds__(threads_for(N), 1)
   const int nel = min(epb, ne - e0);
   const int total = nel * 5 * NV;
 
+  if (ops.uncol) {
+    // The uncollocated scheme: the line phase runs on the N GL points with the
+    // projected state's records (the forward projection pass's node records),
+    // and du^/dt = -Pt (W J)^{-1} A R_q (A = (chi Pi~1)^T, Pt = Pi~1, dense 1D
+    // sweeps), so Rbar_q = A^T (W J)^{-1} Pt^T (-rbar), rbar at the ns^3
+    // solution nodes.
+    __shared__ double AT[NSFR_MAXN * NSFR_MAXN], PtT[NSFR_MAXN * NSFR_MAXN];
+    const int ns = ops.ns, nsv = ns * ns * ns;
+    for (int t = threadIdx.x; t < N * N; t += blockDim.x) AT[(t % N) * N + t / N] = ops.A[t];
+    for (int t = threadIdx.x; t < ns * N; t += blockDim.x) PtT[(t % N) * ns + t / N] = ops.Pt[t];  // Pt: ns x N
+    for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
+      const int le = t / NV, node = t % NV;
+      const double* rec = nrec + (size_t)(e0 + le) * NSFR_NFIELD * NV + node;
+      double* p = P + (size_t)le * 5 * NV + node;
+      p[0] = rec[P_RHO * NV];
+      p[NV] = 2.0 * rec[P_UH * NV];
+      p[2 * NV] = 2.0 * rec[(P_UH + 1) * NV];
+      p[3 * NV] = 2.0 * rec[(P_UH + 2) * NV];
+      p[4 * NV] = 0.5 * rec[P_B2 * NV];
+    }
+    for (int t = threadIdx.x; t < nel * 5 * nsv; t += blockDim.x)
+      Y[(size_t)(t / nsv) * NV + t % nsv] = -rbar[(size_t)e0 * 5 * nsv + t];
+    __syncthreads();
+    psweep(PtT, ns, N, Y, Pb, 5 * nel, NV, 0, ns, ns, ns);
+    psweep(PtT, ns, N, Pb, Rb, 5 * nel, NV, 1, N, ns, ns);
+    psweep(PtT, ns, N, Rb, Y, 5 * nel, NV, 2, N, N, ns);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) Y[t] /= wj[(size_t)(e0 + t / (5 * NV)) * NV + t % NV];
+    __syncthreads();
+    psweep(AT, N, N, Y, Pb, 5 * nel, NV, 0, N, N, N);
+    psweep(AT, N, N, Pb, Y, 5 * nel, NV, 1, N, N, N);
+    psweep(AT, N, N, Y, Rb, 5 * nel, NV, 2, N, N, N);
+  } else {
   for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
     const int le = t / NV, node = t % NV;
     const PR a = pr_from_conserved(u + (size_t)(e0 + le) * 5 * NV + node, NV, g);
@@ -308,6 +340,7 @@ __global__ void __launch_bounds__(threads_for(N), 1)
       __syncthreads();
     }
   }
+  }  // collocated
 
   // line phase
   const int le = threadIdx.x / NL, l = threadIdx.x % NL, e = e0 + le;
@@ -415,8 +448,17 @@ __global__ void __launch_bounds__(threads_for(N), 1)
   }
   for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
     const int lq = t / NV, node = t % NV;
-    const PR a = pr_load(P + (size_t)lq * 5 * NV + node, NV);
     const PR pb = pr_load(Pb + (size_t)lq * 5 * NV + node, NV);
+    if (ops.uncol) {  // record cotangents at the GL points, for the projection's reverse
+      double* q = pbq + (size_t)(e0 + lq) * 5 * NV + node;
+      q[0] = pb.r;
+      q[NV] = pb.u0;
+      q[2 * NV] = pb.u1;
+      q[3 * NV] = pb.u2;
+      q[4 * NV] = pb.b;
+      continue;
+    }
+    const PR a = pr_load(P + (size_t)lq * 5 * NV + node, NV);
     double Ub[5];
     conserved_bar(a, g, pb, 0.0, Ub);
     double* ub = ubar + (size_t)(e0 + lq) * 5 * NV + node;
@@ -502,6 +544,171 @@ __global__ void __launch_bounds__(threads_for(N), 1)
     conserved_bar(a, g, pb, pbar, Ub);
     double* ub = ubar + (size_t)(e0 + lq) * 5 * NV + node;
     for (int k = 0; k < 5; ++k) ub[k * NV] += Ub[k];
+  }
+}
+
+// --------------------------------------------------------------------------
+// projection reverse (uncollocated scheme): record cotangents at the GL points
+// and at the face points -> cotangent of the solution coefficients u^
+// --------------------------------------------------------------------------
+// The forward projection (projection.cu), with ns Lobatto solution nodes and N
+// GL points per direction:
+//   u_q = chi u^,  v_q = v(u_q),  v~^ = Pi v_q,
+//   w_q = chi v~^  -> the volume records u(w_q),
+//   w_f = (l_s along d) (chi, chi across) v~^  -> the face records u(w_f).
+// Reversed: wbar from the record cotangents through u(w) (entropy_bar_from_pr),
+// v~^bar = chi^T wbar_q + sum_faces (l_s, chi, chi)^T wbar_f, v_q bar = Pi^T v~^bar,
+// u_q bar through v(u) (pr_bar_from_entropy_bar, conserved_bar), u^bar = chi^T u_q bar.
+// One element per CTA (grid-stride); all sweeps on shared memory.
+template <int N>
+__global__ void __launch_bounds__(256) vjp_projection_kernel(const double* __restrict__ u,
+                                                             const double* __restrict__ pbq,
+                                                             const double* __restrict__ fbar_own,
+                                                             const double* __restrict__ fbar_nbr, OpsGL ops, int nx,
+                                                             int ny, int nz, int ne, double* __restrict__ ubar) {
+  constexpr int NV = N * N * N, NFP = N * N, SL = 5 * NV;
+  extern __shared__ double sm[];
+  double* B0 = sm;  // six [5][NV] buffers
+  double* B1 = B0 + SL;
+  double* B2 = B1 + SL;
+  double* B3 = B2 + SL;
+  double* B4 = B3 + SL;
+  double* B5 = B4 + SL;
+  __shared__ double chiT[NSFR_MAXN * NSFR_MAXN], PiT[NSFR_MAXN * NSFR_MAXN];
+  __shared__ double lay[5 * NSFR_MAXN * NSFR_MAXN], mid[5 * NSFR_MAXN * NSFR_MAXN];
+  const int ns = ops.ns, nsv = ns * ns * ns;
+  const double g = ops.gamma;
+  for (int t = threadIdx.x; t < N * ns; t += blockDim.x) {
+    chiT[(t % ns) * N + t / ns] = ops.chi[t];  // chi: N x ns
+    PiT[(t % N) * ns + t / N] = ops.Pi[t];     // Pi: ns x N
+  }
+  for (int e = blockIdx.x; e < ne; e += gridDim.x) {
+    for (int t = threadIdx.x; t < 5 * nsv; t += blockDim.x) B0[(t / nsv) * NV + t % nsv] = u[(size_t)e * 5 * nsv + t];
+    __syncthreads();
+    // forward: u_q (B1), v_q (B2), v~^ (B3), w_q (B4)
+    psweep(ops.chi, ns, N, B0, B2, 5, NV, 0, ns, ns, ns);
+    psweep(ops.chi, ns, N, B2, B3, 5, NV, 1, N, ns, ns);
+    psweep(ops.chi, ns, N, B3, B1, 5, NV, 2, N, N, ns);
+    for (int t = threadIdx.x; t < NV; t += blockDim.x) {
+      const PR a = pr_from_conserved(B1 + t, NV, g);
+      double v[5];
+      entropy_vars(a, g, v);
+      for (int k = 0; k < 5; ++k) B2[k * NV + t] = v[k];
+    }
+    __syncthreads();
+    psweep(ops.Pi, N, ns, B2, B4, 5, NV, 0, N, N, N);
+    psweep(ops.Pi, N, ns, B4, B5, 5, NV, 1, ns, N, N);
+    psweep(ops.Pi, N, ns, B5, B3, 5, NV, 2, ns, ns, N);
+    psweep(ops.chi, ns, N, B3, B5, 5, NV, 0, ns, ns, ns);
+    psweep(ops.chi, ns, N, B5, B0, 5, NV, 1, N, ns, ns);
+    psweep(ops.chi, ns, N, B0, B4, 5, NV, 2, N, N, ns);
+    // wbar_q (B5) from the volume record cotangents
+    for (int t = threadIdx.x; t < NV; t += blockDim.x) {
+      double w[5], wb[5];
+      for (int k = 0; k < 5; ++k) w[k] = B4[k * NV + t];
+      const PR a = pr_from_entropy(w, g);
+      const double* q = pbq + (size_t)e * 5 * NV + t;
+      const PR pb{q[0], q[NV], q[2 * NV], q[3 * NV], q[4 * NV]};
+      entropy_bar_from_pr(w, a, g, pb, wb);
+      for (int k = 0; k < 5; ++k) B5[k * NV + t] = wb[k];
+    }
+    __syncthreads();
+    // v~^bar = chi^T wbar_q -> B0 (ns^3)
+    psweep(chiT, N, ns, B5, B4, 5, NV, 0, N, N, N);
+    psweep(chiT, N, ns, B4, B2, 5, NV, 1, ns, N, N);
+    psweep(chiT, N, ns, B2, B0, 5, NV, 2, ns, ns, N);
+    // faces, one at a time: the layer l_s . v~^ along d (lay, ns^2), across the
+    // first transverse direction (mid, N x ns), across the second (the face
+    // points, N^2); reversed the same way into B0
+    for (int f = 0; f < 6; ++f) {
+      const int d = f / 2, side = f % 2;
+      const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;  // transverse directions, lower first
+      const double* ls = side ? ops.ls_p : ops.ls_m;
+      auto vidx = [&](int a, int b, int c) {  // node of v~^ with index a along d, b along t1, c along t2
+        int x[3];
+        x[d] = a;
+        x[t1] = b;
+        x[t2] = c;
+        return x[0] + ns * (x[1] + ns * x[2]);
+      };
+      for (int t = threadIdx.x; t < 5 * ns * ns; t += blockDim.x) {
+        const int k = t / (ns * ns), b = (t / ns) % ns, c = t % ns;
+        double acc = 0.0;
+        for (int a = 0; a < ns; ++a) acc = fma(ls[a], B3[k * NV + vidx(a, b, c)], acc);
+        lay[(k * ns + b) * ns + c] = acc;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < 5 * N * ns; t += blockDim.x) {
+        const int k = t / (N * ns), i = (t / ns) % N, c = t % ns;
+        double acc = 0.0;
+        for (int b = 0; b < ns; ++b) acc = fma(ops.chi[i * ns + b], lay[(k * ns + b) * ns + c], acc);
+        mid[(k * N + i) * ns + c] = acc;
+      }
+      __syncthreads();
+      // w_f at the face points and its cotangent (own + neighbour's slot), into B2 (5 x N^2)
+      const int enb = nbr_index(e, d, side, nx, ny, nz);
+      for (int t = threadIdx.x; t < NFP; t += blockDim.x) {
+        const int i = t % N, j = t / N;  // face point t = i + N j (i along t1, j along t2)
+        double w[5], wb[5];
+        for (int k = 0; k < 5; ++k) {
+          double acc = 0.0;
+          for (int c = 0; c < ns; ++c) acc = fma(ops.chi[j * ns + c], mid[(k * N + i) * ns + c], acc);
+          w[k] = acc;
+        }
+        const PR a = pr_from_entropy(w, g);
+        const double* o = fbar_own + (((size_t)e * 6 + f) * 5) * NFP + t;
+        const double* q = fbar_nbr + (((size_t)enb * 6 + 2 * d + 1 - side) * 5) * NFP + t;
+        const PR pb{o[0] + q[0], o[NFP] + q[NFP], o[2 * NFP] + q[2 * NFP], o[3 * NFP] + q[3 * NFP],
+                    o[4 * NFP] + q[4 * NFP]};
+        entropy_bar_from_pr(w, a, g, pb, wb);
+        for (int k = 0; k < 5; ++k) B2[k * NFP + t] = wb[k];
+      }
+      __syncthreads();
+      // reverse across t2 (mid bar), across t1 (layer bar), along d into B0
+      for (int t = threadIdx.x; t < 5 * N * ns; t += blockDim.x) {
+        const int k = t / (N * ns), i = (t / ns) % N, c = t % ns;
+        double acc = 0.0;
+        for (int j = 0; j < N; ++j) acc = fma(ops.chi[j * ns + c], B2[k * NFP + i + N * j], acc);
+        mid[(k * N + i) * ns + c] = acc;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < 5 * ns * ns; t += blockDim.x) {
+        const int k = t / (ns * ns), b = (t / ns) % ns, c = t % ns;
+        double acc = 0.0;
+        for (int i = 0; i < N; ++i) acc = fma(ops.chi[i * ns + b], mid[(k * N + i) * ns + c], acc);
+        lay[(k * ns + b) * ns + c] = acc;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < 5 * nsv; t += blockDim.x) {
+        const int k = t / nsv, node = t % nsv;
+        const int x[3] = {node % ns, (node / ns) % ns, node / (ns * ns)};
+        B0[k * NV + node] = fma(ls[x[d]], lay[(k * ns + x[t1]) * ns + x[t2]], B0[k * NV + node]);
+      }
+      __syncthreads();
+    }
+    // v_q bar = Pi^T v~^bar -> B2 (N^3)
+    psweep(PiT, ns, N, B0, B4, 5, NV, 0, ns, ns, ns);
+    psweep(PiT, ns, N, B4, B5, 5, NV, 1, N, ns, ns);
+    psweep(PiT, ns, N, B5, B2, 5, NV, 2, N, N, ns);
+    // u_q bar through v(u) -> B4
+    for (int t = threadIdx.x; t < NV; t += blockDim.x) {
+      const PR a = pr_from_conserved(B1 + t, NV, g);
+      double vb[5], Ub[5];
+      for (int k = 0; k < 5; ++k) vb[k] = B2[k * NV + t];
+      PR pb;
+      double pbar;
+      pr_bar_from_entropy_bar(a, g, vb, pb, pbar);
+      conserved_bar(a, g, pb, pbar, Ub);
+      for (int k = 0; k < 5; ++k) B4[k * NV + t] = Ub[k];
+    }
+    __syncthreads();
+    // u^bar += chi^T u_q bar
+    psweep(chiT, N, ns, B4, B5, 5, NV, 0, N, N, N);
+    psweep(chiT, N, ns, B5, B2, 5, NV, 1, ns, N, N);
+    psweep(chiT, N, ns, B2, B0, 5, NV, 2, ns, ns, N);
+    for (int t = threadIdx.x; t < 5 * nsv; t += blockDim.x)
+      ubar[(size_t)e * 5 * nsv + t] += B0[(t / nsv) * NV + t % nsv];
+    __syncthreads();
   }
 }
 
@@ -726,10 +933,22 @@ cudaError_t launch_vjp_n(nsfr_ctx* ctx, const double* u, const double* dbar, dou
   vjp_volume_kernel<N><<<grid, threads_for(N), smem, s>>>(
       u, dbar, xbar ? Rfwd : nullptr, ctx->metric, ctx->nfp_plus, ctx->face, ctx->wj, ctx->ops, ctx->nx, ctx->ny,
       ctx->nz, ctx->ne, ubar, ctx->vjp_fown, ctx->vjp_fnbr, ctx->vjp_nfbar, xbar ? ctx->vjp_mbar : nullptr,
-      ctx->vjp_jbar);
+      ctx->vjp_jbar, ctx->nrec, ctx->vjp_pbq);
   nsfr_prof_end(ctx, s);
   ctx->launches++;
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if (ctx->uncol) {
+    smem = (size_t)6 * 5 * NV * sizeof(double);
+    if ((err = cudaFuncSetAttribute(vjp_projection_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem)) != cudaSuccess)
+      return err;
+    nsfr_prof_begin(ctx, 5, s);
+    vjp_projection_kernel<N><<<ctx->ne < 152 * 16 ? ctx->ne : 152 * 16, 256, smem, s>>>(
+        u, ctx->vjp_pbq, ctx->vjp_fown, ctx->vjp_fnbr, ctx->ops, ctx->nx, ctx->ny, ctx->nz, ctx->ne, ubar);
+    nsfr_prof_end(ctx, s);
+    ctx->launches++;
+    return cudaGetLastError();
+  }
   smem = (size_t)epb * 10 * NV * sizeof(double);
   if ((err = cudaFuncSetAttribute(vjp_face_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
       cudaSuccess)

@@ -102,8 +102,9 @@ def test_uncollocated_context_rejects_what_it_does_not_support():
     from paper_2312_07725_gb300 import NSFRError, Solver
     ctrl, P, S, u = _case((2, 2, 2), 2, 4)
     ud = torch.from_numpy(u).cuda()
-    with pytest.raises(NSFRError):
-        S.vjp(ud, torch.ones_like(ud), torch.zeros_like(ud))
+    with pytest.raises(NSFRError):  # the grid cotangent is not offered for this scheme
+        S.vjp(ud, torch.ones_like(ud), torch.zeros_like(ud),
+              torch.zeros((S.n_el, (S.p_geo + 1) ** 3, 3), dtype=torch.float64, device="cuda"))
     with pytest.raises(ValueError):
         Solver(np.ascontiguousarray(ctrl), (2, 2, 2), 2, nq=4, precision="fp32_bulk_ff")
     with pytest.raises(NSFRError):
@@ -149,7 +150,8 @@ def test_uncollocated_diagnostics_match_oracle(p, nq, face_flux):
 
 
 @pytest.mark.parametrize("p,nq,shape,c_kind,face_flux", [(2, 3, (3, 2, 2), "hu", "ec"), (3, 5, (2, 2, 2), "hu", "ec"),
-                                                         (4, 6, (3, 3, 1), "dg", "ec_roe"), (3, 6, (2, 1, 2), "hu", "ec_es")])
+                                                         (4, 6, (3, 3, 1), "dg", "ec_roe"), (3, 6, (2, 1, 2), "hu", "ec_es"),
+                                                         (6, 7, (2, 1, 1), "hu", "ec"), (7, 8, (1, 2, 1), "hu", "ec")])
 def test_uncollocated_fp32_bulk_within_1e5(p, nq, shape, c_kind, face_flux):
     """The FP32-bulk form of the uncollocated scheme (FP32 flux differencing and return to
     the solution nodes, FP64 entropy projection and face fluxes): du^/dt within 1e-5 of the
@@ -179,3 +181,27 @@ def test_uncollocated_fp32_bulk_within_1e5(p, nq, shape, c_kind, face_flux):
     B.rk_step(ud, dt=dt)
     torch.cuda.synchronize()
     assert rel_l2(ud.cpu().numpy() - u, u1 - u) < 1e-5
+
+
+@pytest.mark.parametrize("p,nq,shape,c_kind", [(2, 3, (2, 2, 1), "dg"), (2, 4, (2, 1, 2), "hu"),
+                                               (3, 5, (1, 2, 2), "hu"), (4, 6, (2, 1, 1), "dg")])
+def test_uncollocated_state_vjp_matches_complex_step(p, nq, shape, c_kind):
+    """The adjoint of du^/dt for the uncollocated scheme (the reverse of the flux differencing
+    on the GL points and of the entropy projection chi, v(u), Pi, u(v)) against the oracle's
+    complex-step derivatives, through dot products <rbar, J d> = <J^T rbar, d> at 1e-10;
+    nq = p+1 (square chi) and overintegration."""
+    _, P, S, u = _case(shape, p, nq, c_kind, "ec")
+    S.set_metrics(*_metrics_abi(P))
+    rng = np.random.default_rng(7)
+    rbar = rng.standard_normal(u.shape)
+    ub = torch.zeros(u.shape, dtype=torch.float64, device="cuda")
+    S.vjp(torch.from_numpy(u).cuda(), torch.from_numpy(rbar).cuda(), ub)
+    ub = ub.cpu().numpy()
+    U = P.to_internal(u)
+    scale_u = np.abs(u).max(axis=(0, 2), keepdims=True)
+    h = 1e-30
+    for _ in range(3):
+        du = rng.standard_normal(u.shape) * scale_u
+        jd = P.to_abi(np.imag(P.dudt(U + 1j * h * P.to_internal(du))) / h)
+        lhs, rhs = float(np.sum(rbar * jd)), float(np.sum(ub * du))
+        assert abs(lhs - rhs) < 1e-10 * float(np.sum(np.abs(rbar * jd))), (lhs, rhs)
