@@ -24,7 +24,7 @@ Modules:
   quadrature   Gauss-Legendre / Gauss-Lobatto nodes and weights
   operators1d  Lagrange interpolation/differentiation, SBP, ESFR K and Pi~
   geometry     conservative-curl metric terms, Jacobians, face normals
-  physics      entropy variables, Chandrashekar EC flux, Roe dissipation
+  physics      entropy variables, EC fluxes (Chandrashekar; with Ranocha's pressure terms), dissipations
   residual     NSFR residual, line-wise (sum-factorised) and dense forms
   mass         weight-adjusted inverse of the FR mass matrix
   timestep     classic RK4, CFL time step
