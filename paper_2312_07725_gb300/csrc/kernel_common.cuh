@@ -10,7 +10,7 @@ namespace nsfr_k {
 // every thread keep up to 255 registers
 constexpr int epb_for(int n) { return n == 2 ? 16 : n == 3 ? 8 : n == 4 ? 4 : n == 5 ? 3 : n == 6 ? 2 : 1; }
 constexpr int threads_for(int n) { return epb_for(n) * 3 * n * n; }
-// The FP64 volume kernel keeps 21 n^3 doubles of shared memory per element
+// The FP64 volume kernel keeps 23 n^3 doubles of shared memory per element
 // (records, three direction slabs of line sums) and about 110
 // registers per thread; it is bound by FP64 issue, which wants as many warps
 // per SM as shared memory (228 KB) and the register file (64K, split evenly

@@ -191,6 +191,18 @@ void nsfr_build_ops(int p, int p_geo, double c, double gamma, int nodes, OpsGL* 
     gl->lmb[k] = (float)(2.0 / (gamma - 1.0) * F[k + 1]);
   }
   {
+    auto split = [](double x, float* hl) {
+      hl[0] = (float)x;
+      hl[1] = (float)(x - (double)hl[0]);
+    };
+    split(G[1], gl->lmg_ff);
+    split(G[2], gl->lmg_ff + 2);
+    gl->lmg_ff[4] = (float)G[3];
+    split(gl->f4g[1], gl->lmb_ff);
+    split(gl->f4g[2], gl->lmb_ff + 2);
+    gl->lmb_ff[4] = (float)gl->f4g[3];
+  }
+  {
     const double cab = 2.0 + 2.0 / (gamma - 1.0);
     gl->cab_hi = (float)cab;
     gl->cab_lo = (float)(cab - (double)gl->cab_hi);

@@ -15,6 +15,7 @@
 // sums, and reciprocals are FP64 refinements of an FP32 seed.
 #pragma once
 
+#include "ffloat.cuh"
 #include "nsfr_internal.h"
 
 // Below this value of f^2 = ((a-b)/(a+b))^2 the log mean uses its series; the
@@ -109,6 +110,61 @@ __device__ __forceinline__ bool lm_small(double u) {
 
 __device__ __forceinline__ double horner4(const double* c, double u) {
   return fma(fma(fma(c[3], u, c[2]), u, c[1]), u, c[0]);
+}
+
+// Float-float rho and 2 beta of a record, split once per node, for the series
+// branch of the log means below.
+struct RecF {
+  ff r, b2;
+};
+__device__ __forceinline__ RecF recf_of(const Rec& a) { return RecF{ff_from_double(a.r), ff_from_double(a.b2)}; }
+
+// a / b, b > 0, in float-float from one FP32 reciprocal and one correction
+// (about 2^-44 relative; the result is not renormalised)
+__device__ __forceinline__ ff ff_div_nn(ff a, ff b) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b.hi));
+  const float q1 = __fmul_rn(a.hi, r);
+  const float p = __fmul_rn(q1, b.hi);
+  const float pe = __fmaf_rn(q1, b.hi, -p);
+  // a - q1 b: a.hi - p is exact (the two are within a few ulps of each other)
+  const float rem = __fmaf_rn(-q1, b.lo, __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo));
+  return ff{q1, __fmul_rn(rem, r)};
+}
+
+// a b without the final renormalisation (operands of further products only)
+__device__ __forceinline__ ff ff_mul_nn(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ff{p, e};
+}
+
+// The series branch of a logarithmic mean on the FP32 pipe.  With
+// f = (a - b)/(a + b) and u = f^2 formed in float-float from float-float a, b,
+// it returns false when u >= NSFR_LM_EPS (the caller takes the log branch in
+// FP64); otherwise it sets eps = u (c1 + u (c2 + u c3)) -- the series' part
+// beyond its constant term, c = {c1 hi, c1 lo, c2 hi, c2 lo, c3} -- as a
+// double.  |eps| <= 1e-4 |c1|, and eps is good to about 2^-40 of itself, so
+// c0 + eps in FP64 matches the FP64 Horner form to its rounding: the series
+// costs one FP64 addition (the join of eps's two floats) instead of the FP64
+// ratio, square and Horner chain.  f, u and the tail keep ~44 bits: the
+// float-float inputs (2^-48) and the sum and difference (2^-47 of the larger
+// operand) put ~2^-49 into f, i.e. below 2^-55 into c0 + eps when u < 1e-4.
+// Arguments outside the FP32 range give an Inf or NaN u, i.e. the log branch.
+__device__ __forceinline__ bool lm_series_ff(ff a, ff b, const float* c, double& eps) {
+  const ff f = ff_div_nn(ff_add_nn(a, ff_neg(b)), ff_add_nn(a, b));
+  const float uh = __fmul_rn(f.hi, f.hi);
+  const ff u{uh, __fmaf_rn(__fmul_rn(2.0f, f.hi), f.lo, __fmaf_rn(f.hi, f.hi, -uh))};
+  if (!(uh < (float)NSFR_LM_EPS)) return false;
+  float s, e;
+  two_sum(c[2], __fmul_rn(uh, c[4]), s, e);
+  const ff t{s, __fadd_rn(e, c[3])};                   // c2 + u c3
+  const ff q = ff_add_nn(ff{c[0], c[1]}, ff_mul_nn(u, t));  // c1 + u (c2 + u c3)
+  const ff w = ff_mul_nn(u, q);
+  eps = f2d_i(w.hi) + f2d_i(w.lo);
+  return true;
 }
 
 // Record of a conserved state; flags rho <= 0, p <= 0 or NaN.  ln rho and
@@ -209,6 +265,39 @@ __device__ __forceinline__ double ec_flux_over_sr(const Rec& A, const Rec& B, do
   return sr;
 }
 
+// ec_flux_over_sr with the log means' series branch on the FP32 pipe
+// (lm_series_ff, from the float-float rho and 2 beta of the two nodes): there
+//   F_rho / s = Gh(u_r) u.n = (u.n / 2) (1 + eps_r),
+//   h = F4g(u_b) / s2 - qs = (F4g(0) + eps_b) / s2 - qs,
+// and the FP64 work left is the sums, 1/s2, the two joins of eps and the flux.
+// The differences rho_a - rho_b and 2 beta_a - 2 beta_b are formed in FP64 on
+// the log branch only.
+template <class LA, class LB>
+__device__ __forceinline__ double ec_flux_over_sr_ff(const Rec& A, const Rec& B, const RecF& Af, const RecF& Bf,
+                                                     double n0, double n1, double n2, const OpsGL& K, const LA& la,
+                                                     const LB& lb, double F[5]) {
+  const double sr = A.r + B.r, s2 = A.b2 + B.b2;
+  const double rb2 = rcp_full(s2);
+  const double qs = A.qq + B.qq;
+  const double v0 = A.u0 + B.u0, v1 = A.u1 + B.u1, v2 = A.u2 + B.u2;  // u_bar
+  const double un = fma(v0, n0, fma(v1, n1, v2 * n2));
+  double er, eb, Fr, h;
+  if (lm_series_ff(Af.r, Bf.r, K.lmg_ff, er)) {
+    const double uh = mul_pow2<-1>(un);
+    Fr = fma(uh, er, uh);
+  } else {
+    Fr = (A.r - B.r) / ((la.lr() - lb.lr()) * sr) * un;
+  }
+  if (lm_series_ff(Af.b2, Bf.b2, K.lmb_ff, eb)) h = fma(eb, rb2, fma(K.f4g[0], rb2, -qs));
+  else h = K.inv_gm1 * (la.lb() - lb.lb()) / (A.b2 - B.b2) - qs;
+  F[0] = Fr;
+  F[1] = fma(Fr, v0, rb2 * n0);
+  F[2] = fma(Fr, v1, rb2 * n1);
+  F[3] = fma(Fr, v2, rb2 * n2);
+  F[4] = fma(v2, F[3], fma(v1, F[2], fma(v0, F[1], Fr * h)));
+  return sr;
+}
+
 __device__ __forceinline__ void ec_flux(const Rec& A, const Rec& B, double n0, double n1, double n2,
                                         const OpsGL& K, double F[5]) {
   ec_flux_l(A, B, n0, n1, n2, K, RecLogs{A}, RecLogs{B}, F);
@@ -243,6 +332,39 @@ __device__ __forceinline__ void ranocha_flux_l(const Rec& A, const Rec& B, doubl
   const double hab = fma(A.u0, B.u0, fma(A.u1, B.u1, A.u2 * B.u2));  // u_a . u_b / 4
   const double Fr = rln * un;
   const double pm = 0.5 * (pa + pb);
+  F[0] = Fr;
+  F[1] = fma(Fr, v0, pm * n0);
+  F[2] = fma(Fr, v1, pm * n1);
+  F[3] = fma(Fr, v2, pm * n2);
+  F[4] = fma(Fr, fma(2.0, hab, ibg), fma(pa, un - an, pb * an));
+}
+
+// ranocha_flux_l with the log means' series branch on the FP32 pipe, as in
+// ec_flux_over_sr_ff: rho_ln = (s/2)(1 + eps_r), 1/(2(gamma-1) beta_ln) =
+// (F4g(0) + eps_b) / s2.
+template <class LA, class LB>
+__device__ __forceinline__ void ranocha_flux_ff(const Rec& A, const Rec& B, const RecF& Af, const RecF& Bf,
+                                                double pa, double pb, double n0, double n1, double n2,
+                                                const OpsGL& K, const LA& la, const LB& lb, double F[5]) {
+  double er, eb, rln, ibg;
+  if (lm_series_ff(Af.r, Bf.r, K.lmg_ff, er)) {
+    const double sh = mul_pow2<-1>(A.r + B.r);
+    rln = fma(sh, er, sh);
+  } else {
+    rln = (A.r - B.r) / (la.lr() - lb.lr());
+  }
+  if (lm_series_ff(Af.b2, Bf.b2, K.lmb_ff, eb)) {
+    const double rb2 = rcp_full(A.b2 + B.b2);
+    ibg = fma(eb, rb2, K.f4g[0] * rb2);
+  } else {
+    ibg = K.inv_gm1 * (la.lb() - lb.lb()) / (A.b2 - B.b2);
+  }
+  const double v0 = A.u0 + B.u0, v1 = A.u1 + B.u1, v2 = A.u2 + B.u2;  // u_bar
+  const double un = fma(v0, n0, fma(v1, n1, v2 * n2));
+  const double an = fma(A.u0, n0, fma(A.u1, n1, A.u2 * n2));     // u_a . n / 2
+  const double hab = fma(A.u0, B.u0, fma(A.u1, B.u1, A.u2 * B.u2));  // u_a . u_b / 4
+  const double Fr = rln * un;
+  const double pm = mul_pow2<-1>(pa + pb);
   F[0] = Fr;
   F[1] = fma(Fr, v0, pm * n0);
   F[2] = fma(Fr, v1, pm * n1);

@@ -185,13 +185,14 @@ __device__ __forceinline__ void rank_one_sweep(double* X, int nel, int d, bool t
 // terms with factor 1, its node pressures riding in the records' |u|^2/4 slot
 // (that flux has no use for |u|^2).
 template <int VF, class LA, class LB>
-__device__ __forceinline__ double vol_flux(const Rec& A, const Rec& B, double n0, double n1, double n2,
-                                           const OpsGL& K, const LA& la, const LB& lb, double F[5]) {
+__device__ __forceinline__ double vol_flux(const Rec& A, const Rec& B, const RecF& Af, const RecF& Bf, double n0,
+                                           double n1, double n2, const OpsGL& K, const LA& la, const LB& lb,
+                                           double F[5]) {
   if (VF == NSFR_FLUX_RANOCHA) {
-    ranocha_flux_l(A, B, A.qq, B.qq, n0, n1, n2, K, la, lb, F);
+    ranocha_flux_ff(A, B, Af, Bf, A.qq, B.qq, n0, n1, n2, K, la, lb, F);
     return 1.0;
   }
-  return ec_flux_over_sr(A, B, n0, n1, n2, K, la, lb, F);
+  return ec_flux_over_sr_ff(A, B, Af, Bf, n0, n1, n2, K, la, lb, F);
 }
 
 // Rows of the pair table pm of one element and direction: the n(n-1)/2 volume
@@ -220,6 +221,7 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
   double* P = sm;                          // [epb][6][NV] node records (the logs stay in nrec)
   double* Ra = P + (size_t)epb * 6 * NV;   // [epb][3][5][NV] line sums, one slab per direction
   double* Rs = P;                          // [epb][5][NV] residual (after the line phase)
+  ff* Pf = (ff*)(Ra + (size_t)epb * 15 * NV);  // [epb][2][NV] rho, 2 beta as float-float
 
   // prologue: node records (fields rho .. |u|^2/4) of the block's elements
 #if NSFR_VOL_STAGE_TMA
@@ -254,13 +256,16 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
   }
   for (int t = threadIdx.x; t < epb * 15 * NV; t += blockDim.x) Ra[t] = 0.0;
 #endif
-  if (VF == NSFR_FLUX_RANOCHA) {
-    // the pressure rho / (2 beta) in place of |u|^2/4
-    __syncthreads();
-    for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
-      double* pe = P + (size_t)(t / NV) * 6 * NV + t % NV;
-      pe[P_QQ * NV] = pe[P_RHO * NV] * rcp_full(pe[P_B2 * NV]);
-    }
+  __syncthreads();
+  // float-float rho and 2 beta of every node (the log means' series branch);
+  // Ranocha's flux takes the pressure rho / (2 beta) in place of |u|^2/4
+  for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
+    const int le = t / NV, node = t % NV;
+    double* pe = P + (size_t)le * 6 * NV + node;
+    const double r = pe[P_RHO * NV], b2 = pe[P_B2 * NV];
+    Pf[(size_t)le * 2 * NV + node] = ff_from_double(r);
+    Pf[((size_t)le * 2 + 1) * NV + node] = ff_from_double(b2);
+    if (VF == NSFR_FLUX_RANOCHA) pe[P_QQ * NV] = r * rcp_full(b2);
   }
   __syncthreads();
 
@@ -277,6 +282,8 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
   line_geometry<N>(d, l0, l1, base, stride);
   if (le < nel) {
     const double* Pe = P + (size_t)le * 6 * NV + base;
+    const ff* Pfe = Pf + (size_t)le * 2 * NV + base;
+    auto recf_at = [&](int a) { return RecF{Pfe[a * stride], Pfe[NV + a * stride]}; };
     const double* Le = nrec + ((size_t)e * NSFR_NFIELD + P_LRHO) * NV + base;  // ln rho, ln beta (read only off the series path)
     const double* Pm = pm + ((size_t)e * 3 + d) * NPP * 3 * NFP + line;      // row q, component c at Pm[(3 q + c) NFP]
     double* Rl = Ra + ((size_t)le * 15 + 5 * d) * NV + base;
@@ -286,6 +293,7 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
 #pragma unroll 1
     for (int a = 0; a < N - 1; ++a) {
       const Rec A = load_rec6(Pe + a * stride, NV);
+      const RecF Af = recf_at(a);
       double Racc[5];
 #pragma unroll
       for (int k = 0; k < 5; ++k) Racc[k] = Rl[k * NV + a * stride];
@@ -298,7 +306,7 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
         m2 = Pm[(3 * q + 2) * NFP];
         const Rec B = load_rec6(Pe + b * stride, NV);
         double F[5];
-        const double fs = vol_flux<VF>(A, B, n0, n1, n2, ops, PtrLogs{Le + a * stride, NV},
+        const double fs = vol_flux<VF>(A, B, Af, recf_at(b), n0, n1, n2, ops, PtrLogs{Le + a * stride, NV},
                                        PtrLogs{Le + b * stride, NV}, F);
         const double c = VF == NSFR_FLUX_RANOCHA ? ops.S1[a * N + b] : ops.S1[a * N + b] * fs;
 #pragma unroll
@@ -328,6 +336,7 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
       }
       Rec Fo = load_rec6(fo, NFP);
       if (VF == NSFR_FLUX_RANOCHA) Fo.qq = pressure_of(Fo);
+      const RecF Fof = recf_of(Fo);
       const double* t = s ? ops.tp : ops.tm;
       const double* Ph = Pm + 3 * (N * (N - 1) / 2 + s * N) * NFP;  // hybrid rows: (C_a + C_f) w_perp / 2
       double tphi[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -335,7 +344,8 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
       for (int a = 0; a < N; ++a) {
         const Rec A = load_rec6(Pe + a * stride, NV);
         double F[5];
-        const double fs = vol_flux<VF>(A, Fo, Ph[3 * a * NFP], Ph[(3 * a + 1) * NFP], Ph[(3 * a + 2) * NFP], ops,
+        const double fs = vol_flux<VF>(A, Fo, recf_at(a), Fof, Ph[3 * a * NFP], Ph[(3 * a + 1) * NFP],
+                                       Ph[(3 * a + 2) * NFP], ops,
                                        PtrLogs{Le + a * stride, NV}, PtrLogs{fo + P_LRHO * NFP, NFP}, F);
         const double ta = VF == NSFR_FLUX_RANOCHA ? t[a] : t[a] * fs;
         const double swt = s ? ta : -ta;  // s t_a, the sign without a multiply
@@ -458,7 +468,7 @@ cudaError_t launch_volume_n(nsfr_ctx* ctx, const double* u, double* out, int epi
   const int eb = ctx->vol_b, ee = ctx->vol_e < 0 ? ctx->ne : ctx->vol_e;
   const int grid = (ee - eb + epb - 1) / epb;
   if (grid <= 0) return cudaSuccess;
-  const size_t smem = (size_t)epb * (6 + 15) * NV * sizeof(double);
+  const size_t smem = (size_t)epb * (6 + 15 + 2) * NV * sizeof(double);
   auto kern = ctx->vol_flux == NSFR_FLUX_RANOCHA ? volume_kernel<N, NSFR_FLUX_RANOCHA>
                                                  : volume_kernel<N, NSFR_FLUX_CHANDRASHEKAR>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
