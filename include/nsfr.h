@@ -393,6 +393,17 @@ nsfr_status nsfr_residual_static(const double* u, const double* C, const double*
  *                FP32-bulk kernels (x split into two floats, the result
  *                summed back; about 2^-46 of max(|ln x|, 0.7), and relative
  *                2^-46; x.hi positive and normal for the log, |x| < 87 for exp)
+ *   NSFR_FN_JOIN  the integer-pipe join of a float-float pair into a double:
+ *                the 64 bits of x are the pair (hi in the high 32 bits, lo in
+ *                the low), y = hi + lo with its bits below 2^-52 |y|
+ *                truncated (exact when the sum fits 53 bits); for
+ *                |lo| < |hi| / 2 or hi = 0, finite hi
+ *   NSFR_FN_LOGMEAN1 the logarithmic mean (x - 1) / ln x of x > 0 and 1 as
+ *                the FP64 volume kernels form the log means of Chandrashekar's
+ *                flux (Sec. "Nonlinearly Stable Flux Reconstruction"): for
+ *                u = ((x-1)/(x+1))^2 < 1e-4 the series of f/atanh(f) in u,
+ *                its terms beyond the constant in float-float, plus one FP64
+ *                FMA (about one ulp); else (x - 1) / ln x in FP64
  * The kernels compute the entropy variables, face states and two-point
  * fluxes with these.  x and y are device buffers of n doubles (n >= 0; they
  * may alias); asynchronous on the stream.  NSFR_ERR_ARG for an unknown fn, a
@@ -404,7 +415,9 @@ typedef enum {
   NSFR_FN_RCP = 2,
   NSFR_FN_RCP1 = 3,
   NSFR_FN_LOG_FF = 4,
-  NSFR_FN_EXP_FF = 5
+  NSFR_FN_EXP_FF = 5,
+  NSFR_FN_JOIN = 6,
+  NSFR_FN_LOGMEAN1 = 7
 } nsfr_fn;
 nsfr_status nsfr_math_eval(int fn, const double* x, double* y, long long n, void* stream);
 

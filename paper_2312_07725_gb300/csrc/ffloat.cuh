@@ -52,6 +52,36 @@ __device__ __forceinline__ ff ff_from_double(double x) {
 
 __device__ __forceinline__ double ff_to_double(ff a) { return f2d_i(a.hi) + f2d_i(a.lo); }
 
+// hi + lo as a double on the integer pipe (ff_to_double without its FP64
+// addition): the two 24-bit significands are added as integers at their
+// offset, the sum is renormalised by at most one position and its top 53 bits
+// kept (truncated: an error below 2^-52 of the value; exact when lo lies
+// within 29 bits below hi's last bit).  Requires |lo| < |hi| / 2 or hi == 0;
+// subnormal floats count as zero, and hi must not be Inf or NaN.
+__device__ __forceinline__ double ff_join_i(ff a) {
+  const unsigned int bh = __float_as_uint(a.hi), bl = __float_as_uint(a.lo);
+  const unsigned int eh = (bh >> 23) & 0xffu, el = (bl >> 23) & 0xffu;
+  if (eh == 0u) return f2d_i(a.lo);
+  if (el == 0u) return f2d_i(a.hi);
+  const unsigned int sh = eh - el;  // >= 1 when |lo| < |hi| / 2
+  // significands with their leading bits at bit 62 (hi) and 62 - sh (lo)
+  const unsigned long long H = (unsigned long long)((bh & 0x7fffffu) | 0x800000u) << 39;
+  const unsigned long long L =
+      sh < 63u ? ((unsigned long long)((bl & 0x7fffffu) | 0x800000u) << 39) >> sh : 0ull;
+  unsigned long long S = ((bh ^ bl) & 0x80000000u) ? H - L : H + L;
+  unsigned int e = eh + 896u;  // binary64 biased exponent of bit 62
+  if (S >> 63) {
+    S >>= 1;
+    ++e;
+  } else if (!(S >> 62)) {
+    S <<= 1;
+    --e;
+  }
+  const unsigned long long bits = ((unsigned long long)(bh & 0x80000000u) << 32) |
+                                  ((unsigned long long)e << 52) | ((S >> 10) & 0xfffffffffffffull);
+  return __longlong_as_double((long long)bits);
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);

@@ -1,7 +1,8 @@
 // Elementwise evaluation of the library's own device elementary functions
 // (nsfr_math_eval): the FP64 log and exp of mathfn.cuh, the float-float ones
-// of mathfn_ff.cuh and the reciprocals of physics.cuh, so that they can be
-// checked against reference values.
+// of mathfn_ff.cuh, the reciprocals of physics.cuh, the integer-pipe join of
+// float-float pairs and the volume kernels' logarithmic mean, so that they can
+// be checked against reference values.
 #include "mathfn.cuh"
 #include "mathfn_ff.cuh"
 #include "physics.cuh"
@@ -18,6 +19,25 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
       case NSFR_FN_RCP: r = rcp_full(v); break;
       case NSFR_FN_LOG_FF: r = ff_to_double(ff_log(ff_from_double(v), nsfr_global_tables_f())); break;
       case NSFR_FN_EXP_FF: r = ff_to_double(ff_exp(ff_from_double(v), nsfr_global_tables_f())); break;
+      case NSFR_FN_JOIN: {  // the 64 bits of v as two floats, hi in the high word
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        r = ff_join_i(ff{__uint_as_float((unsigned int)(b >> 32)), __uint_as_float((unsigned int)b)});
+        break;
+      }
+      case NSFR_FN_LOGMEAN1: {  // logarithmic mean of v and 1 as the volume kernels form it
+        // G(u) - 1 = u (c1 + u (c2 + u c3)): c1 = -1/3, c2 = -4/45 (hi, lo), c3 = -44/945
+        const double c1 = -1.0 / 3.0, c2 = -4.0 / 45.0;
+        const float c[5] = {d2f_i(c1), d2f_i(c1 - f2d_i(d2f_i(c1))), d2f_i(c2), d2f_i(c2 - f2d_i(d2f_i(c2))),
+                            d2f_i(-44.0 / 945.0)};
+        double eps;
+        if (lm_series_ff(ff_from_double(v), ff{1.0f, 0.0f}, c, eps)) {
+          const double sh = mul_pow2<-1>(v + 1.0);
+          r = fma(sh, eps, sh);
+        } else {
+          r = (v - 1.0) / nsfr_log(v);
+        }
+        break;
+      }
       default: r = rcp_newton1(v); break;
     }
     y[i] = r;

@@ -119,11 +119,15 @@ struct RecF {
 };
 __device__ __forceinline__ RecF recf_of(const Rec& a) { return RecF{ff_from_double(a.r), ff_from_double(a.b2)}; }
 
-// a / b, b > 0, in float-float from one FP32 reciprocal and one correction
-// (about 2^-44 relative; the result is not renormalised)
-__device__ __forceinline__ ff ff_div_nn(ff a, ff b) {
+__device__ __forceinline__ float rcp32(float x) {
   float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b.hi));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// a / b, b > 0, in float-float from r, the FP32 reciprocal of b.hi, and one
+// correction (about 2^-44 relative; the result is not renormalised)
+__device__ __forceinline__ ff ff_div_nn(ff a, ff b, float r) {
   const float q1 = __fmul_rn(a.hi, r);
   const float p = __fmul_rn(q1, b.hi);
   const float pe = __fmaf_rn(q1, b.hi, -p);
@@ -141,30 +145,49 @@ __device__ __forceinline__ ff ff_mul_nn(ff a, ff b) {
   return ff{p, e};
 }
 
+// 1/x for an FP64 x > 0 from a float-float approximation xf of it and r, the
+// FP32 reciprocal of xf.hi: the float-float seed r + r (1 - xf r) (~2^-45),
+// joined on the integer pipe, and one FP64 Newton step -- two FP64
+// operations, to the accuracy of rcp_full's three.
+__device__ __forceinline__ double rcp_from_ff(double x, ff xf, float r) {
+  if (!(xf.hi > 1.0e-37f && xf.hi < 1.0e37f)) return rcp_full(x);  // outside the FP32 seed's range
+  const float e = __fmaf_rn(-xf.lo, r, __fmaf_rn(-xf.hi, r, 1.0f));
+  const double r0 = ff_join_i(ff{r, __fmul_rn(r, e)});
+  return fma(r0, fma(-x, r0, 1.0), r0);
+}
+
 // The series branch of a logarithmic mean on the FP32 pipe.  With
-// f = (a - b)/(a + b) and u = f^2 formed in float-float from float-float a, b,
+// f = d / s = (a - b)/(a + b) and u = f^2 formed in float-float from the
+// float-float difference and sum of a, b (rs the FP32 reciprocal of s.hi),
 // it returns false when u >= NSFR_LM_EPS (the caller takes the log branch in
 // FP64); otherwise it sets eps = u (c1 + u (c2 + u c3)) -- the series' part
 // beyond its constant term, c = {c1 hi, c1 lo, c2 hi, c2 lo, c3} -- as a
 // double.  |eps| <= 1e-4 |c1|, and eps is good to about 2^-40 of itself, so
 // c0 + eps in FP64 matches the FP64 Horner form to its rounding: the series
-// costs one FP64 addition (the join of eps's two floats) instead of the FP64
-// ratio, square and Horner chain.  f, u and the tail keep ~44 bits: the
-// float-float inputs (2^-48) and the sum and difference (2^-47 of the larger
-// operand) put ~2^-49 into f, i.e. below 2^-55 into c0 + eps when u < 1e-4.
-// Arguments outside the FP32 range give an Inf or NaN u, i.e. the log branch.
-__device__ __forceinline__ bool lm_series_ff(ff a, ff b, const float* c, double& eps) {
-  const ff f = ff_div_nn(ff_add_nn(a, ff_neg(b)), ff_add_nn(a, b));
+// costs no FP64 operation (eps's two floats are joined on the integer pipe)
+// instead of the FP64 ratio, square and Horner chain.  f, u and the tail keep
+// ~44 bits: the float-float inputs (2^-48) and the sum and difference (2^-47
+// of the larger operand) put ~2^-49 into f, i.e. below 2^-55 into c0 + eps
+// when u < 1e-4.
+// A sum outside the FP32 range (and a NaN) takes the log branch.
+__device__ __forceinline__ bool lm_series_ff(ff d, ff s, float rs, const float* c, double& eps) {
+  if (!(s.hi > 1.0e-37f && s.hi < 1.0e37f)) return false;
+  const ff f = ff_div_nn(d, s, rs);
   const float uh = __fmul_rn(f.hi, f.hi);
   const ff u{uh, __fmaf_rn(__fmul_rn(2.0f, f.hi), f.lo, __fmaf_rn(f.hi, f.hi, -uh))};
   if (!(uh < (float)NSFR_LM_EPS)) return false;
-  float s, e;
-  two_sum(c[2], __fmul_rn(uh, c[4]), s, e);
-  const ff t{s, __fadd_rn(e, c[3])};                   // c2 + u c3
+  float ts, te;
+  two_sum(c[2], __fmul_rn(uh, c[4]), ts, te);
+  const ff t{ts, __fadd_rn(te, c[3])};                 // c2 + u c3
   const ff q = ff_add_nn(ff{c[0], c[1]}, ff_mul_nn(u, t));  // c1 + u (c2 + u c3)
-  const ff w = ff_mul_nn(u, q);
-  eps = f2d_i(w.hi) + f2d_i(w.lo);
+  eps = ff_join_i(ff_mul_nn(u, q));
   return true;
+}
+
+// the same from float-float a, b
+__device__ __forceinline__ bool lm_series_ff(ff a, ff b, const float* c, double& eps) {
+  const ff s = ff_add_nn(a, b);
+  return lm_series_ff(ff_add_nn(a, ff_neg(b)), s, rcp32(s.hi), c, eps);
 }
 
 // Record of a conserved state; flags rho <= 0, p <= 0 or NaN.  ln rho and
@@ -277,7 +300,9 @@ __device__ __forceinline__ double ec_flux_over_sr_ff(const Rec& A, const Rec& B,
                                                      double n0, double n1, double n2, const OpsGL& K, const LA& la,
                                                      const LB& lb, double F[5]) {
   const double sr = A.r + B.r, s2 = A.b2 + B.b2;
-  const double rb2 = rcp_full(s2);
+  const ff s2f = ff_add_nn(Af.b2, Bf.b2);
+  const float rs2 = rcp32(s2f.hi);
+  const double rb2 = rcp_from_ff(s2, s2f, rs2);
   const double qs = A.qq + B.qq;
   const double v0 = A.u0 + B.u0, v1 = A.u1 + B.u1, v2 = A.u2 + B.u2;  // u_bar
   const double un = fma(v0, n0, fma(v1, n1, v2 * n2));
@@ -288,8 +313,10 @@ __device__ __forceinline__ double ec_flux_over_sr_ff(const Rec& A, const Rec& B,
   } else {
     Fr = (A.r - B.r) / ((la.lr() - lb.lr()) * sr) * un;
   }
-  if (lm_series_ff(Af.b2, Bf.b2, K.lmb_ff, eb)) h = fma(eb, rb2, fma(K.f4g[0], rb2, -qs));
-  else h = K.inv_gm1 * (la.lb() - lb.lb()) / (A.b2 - B.b2) - qs;
+  if (lm_series_ff(ff_add_nn(Af.b2, ff_neg(Bf.b2)), s2f, rs2, K.lmb_ff, eb))
+    h = fma(eb, rb2, fma(K.f4g[0], rb2, -qs));
+  else
+    h = K.inv_gm1 * (la.lb() - lb.lb()) / (A.b2 - B.b2) - qs;
   F[0] = Fr;
   F[1] = fma(Fr, v0, rb2 * n0);
   F[2] = fma(Fr, v1, rb2 * n1);
@@ -353,8 +380,10 @@ __device__ __forceinline__ void ranocha_flux_ff(const Rec& A, const Rec& B, cons
   } else {
     rln = (A.r - B.r) / (la.lr() - lb.lr());
   }
-  if (lm_series_ff(Af.b2, Bf.b2, K.lmb_ff, eb)) {
-    const double rb2 = rcp_full(A.b2 + B.b2);
+  const ff s2f = ff_add_nn(Af.b2, Bf.b2);
+  const float rs2 = rcp32(s2f.hi);
+  if (lm_series_ff(ff_add_nn(Af.b2, ff_neg(Bf.b2)), s2f, rs2, K.lmb_ff, eb)) {
+    const double rb2 = rcp_from_ff(A.b2 + B.b2, s2f, rs2);
     ibg = fma(eb, rb2, K.f4g[0] * rb2);
   } else {
     ibg = K.inv_gm1 * (la.lb() - lb.lb()) / (A.b2 - B.b2);

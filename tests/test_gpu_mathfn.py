@@ -131,3 +131,71 @@ def test_float_float_exp_within_2_pow_minus_44_of_libm():
     err = np.abs(y - ref) / ref
     assert err.max() <= 2.0 ** -44, err.max()
     assert y[-4] == 1.0
+
+
+def _pack_pairs(hi, lo):
+    """float32 pairs as the 64 bits of float64 values (hi in the high word)."""
+    bits = (hi.astype(np.float32).view(np.uint32).astype(np.uint64) << np.uint64(32)) | \
+        lo.astype(np.float32).view(np.uint32).astype(np.uint64)
+    return bits.view(np.float64)
+
+
+def test_join_of_float_pairs_is_their_exact_sum():
+    """ff_join_i (integer-pipe join of a float-float pair, used by the FP64 volume
+    kernels): y equals hi + lo exactly whenever that sum fits a double, and is
+    within 2^-52 of it otherwise, including the borrow below a power of two and the
+    carry past an all-ones significand."""
+    from fractions import Fraction
+    n = 6000
+    e = RNG.integers(-60, 100, n)
+    hi = np.ldexp(RNG.uniform(1.0, 2.0, n), e).astype(np.float32) * RNG.choice([-1.0, 1.0], n).astype(np.float32)
+    k = RNG.integers(0, 45, n)
+    lo = (hi.astype(np.float64) * RNG.uniform(-0.49, 0.49, n) * np.ldexp(1.0, -k)).astype(np.float32)
+    lo[np.abs(lo) < np.float32(2.0 ** -126)] = 0.0  # subnormal floats count as zero: not tested here
+    pw = np.ldexp(1.0, RNG.integers(-60, 60, 2000)).astype(np.float32)  # borrow: hi = 2^e, lo < 0
+    lo_pw = (-pw.astype(np.float64) * RNG.uniform(1e-9, 0.49, 2000)).astype(np.float32)
+    ones = (np.ldexp(2.0 - 2.0 ** -23, RNG.integers(-60, 60, 2000))).astype(np.float32)  # carry
+    lo_ones = (ones.astype(np.float64) * RNG.uniform(1e-9, 0.49, 2000)).astype(np.float32)
+    special_hi = np.array([1.0, -1.0, 0.0, 3.0, 1.5, -2.0], np.float32)
+    special_lo = np.array([0.0, 0.0, 0.0, 2.0 ** -30, -2.0 ** -40, 2.0 ** -80], np.float32)
+    H = np.concatenate([hi, pw, ones, special_hi])
+    L = np.concatenate([lo, lo_pw, lo_ones, special_lo])
+    y, _ = _eval("join", _pack_pairs(H, L))
+    for h, l, v in zip(H.astype(np.float64), L.astype(np.float64), y):
+        exact = Fraction(h) + Fraction(l)
+        if float(exact) == exact:
+            assert v == float(exact), (h, l, v)
+        else:
+            assert abs(Fraction(v) - exact) <= abs(exact) * Fraction(1, 2 ** 52), (h, l, v)
+
+
+def _logmean1_ref(x):
+    from decimal import Decimal, getcontext
+    getcontext().prec = 50
+    out = np.empty_like(x)
+    for i, v in enumerate(x):
+        d = Decimal(float(v))
+        out[i] = 1.0 if d == 1 else float((d - 1) / d.ln())
+    return out
+
+
+def test_logmean_series_branch_within_two_ulp():
+    """The volume kernels' logarithmic mean (x - 1)/ln x of x and 1 against its
+    closed form in 50-digit decimal arithmetic.  On the series branch
+    (u = ((x-1)/(x+1))^2 < 1e-4, the float-float tail plus one FP64 FMA) it is
+    within 2 ulp; on the log branch, (x - 1)/ln x with the library's log, within
+    the log's absolute accuracy divided by |ln x| (1e-14 relative near the
+    threshold)."""
+    near = 1.0 + np.concatenate([RNG.uniform(-0.021, 0.021, 4000), RNG.uniform(-1e-6, 1e-6, 500),
+                                 np.array([0.0, 2.0 ** -52, -2.0 ** -53, 0.0198, 0.0202, -0.0198, -0.0194])])
+    far = np.concatenate([RNG.uniform(0.1, 0.97, 500), RNG.uniform(1.03, 10.0, 500)])
+    x = np.concatenate([near, far])
+    y, _ = _eval("logmean1", x)
+    ref = _logmean1_ref(x)
+    u = ((x - 1.0) / (x + 1.0)) ** 2
+    series = u < 0.99e-4
+    logb = u > 1.01e-4
+    assert series.sum() > 3000 and logb.sum() > 1000
+    ulps = np.abs(y - ref) / np.spacing(np.abs(ref))
+    assert np.max(ulps[series]) <= 2.0, np.max(ulps[series])
+    assert np.max(np.abs(y - ref)[logb] / ref[logb]) <= 1e-14
