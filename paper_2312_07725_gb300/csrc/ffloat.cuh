@@ -52,6 +52,39 @@ __device__ __forceinline__ ff ff_from_double(double x) {
 
 __device__ __forceinline__ double ff_to_double(ff a) { return f2d_i(a.hi) + f2d_i(a.lo); }
 
+// x as hi + lo on the integer pipe (ff_from_double without its FP64
+// subtraction): hi the nearest float (d2f_i, ties away from zero), lo the
+// leading 24 bits of the remainder x - hi (truncated: x - hi - lo is below
+// 2^-48 |x|).  For normal x with 2^-100 < |x| < 2^100, where hi and lo are
+// normal floats (lo below the FP32 range becomes 0).
+__device__ __forceinline__ ff ff_split_i(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const float h = d2f_i(x);
+  // remainder of the 53-bit significand after rounding it to 24 bits
+  const unsigned int low = (unsigned int)b & 0x1fffffffu;
+  const int R = (int)low - ((low & 0x10000000u) ? 0x20000000 : 0);
+  if (R == 0) return ff{h, 0.0f};
+  const unsigned int a = R < 0 ? (unsigned int)(-R) : (unsigned int)R;
+  const int p = 31 - __clz((int)a);  // leading bit of |R| (<= 28)
+  const unsigned int sig = p >= 23 ? (a >> (p - 23)) : (a << (23 - p));
+  // |lo| = a 2^(E - 1075), E the binary64 exponent field: FP32 exponent field p + E - 948
+  const int fe = p + (int)((b >> 52) & 0x7ffu) - 948;
+  if (fe <= 0) return ff{h, 0.0f};
+  const unsigned int sign = ((unsigned int)(b >> 32) & 0x80000000u) ^ (R < 0 ? 0x80000000u : 0u);
+  return ff{h, __uint_as_float(sign | ((unsigned int)fe << 23) | (sig & 0x7fffffu))};
+}
+
+// an int as a double on the integer pipe (exact)
+__device__ __forceinline__ double i2d_i(int n) {
+  if (n == 0) return 0.0;
+  const unsigned int a = n < 0 ? 0u - (unsigned int)n : (unsigned int)n;
+  const int p = 31 - __clz((int)a);
+  const unsigned long long bits = ((unsigned long long)(n < 0 ? 1u : 0u) << 63) |
+                                  ((unsigned long long)(1023 + p) << 52) |
+                                  (((unsigned long long)a << (52 - p)) & 0xfffffffffffffull);
+  return __longlong_as_double((long long)bits);
+}
+
 // hi + lo as a double on the integer pipe (ff_to_double without its FP64
 // addition): the two 24-bit significands are added as integers at their
 // offset, the sum is renormalised by at most one position and its top 53 bits
@@ -126,3 +159,19 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
 
 // acc + c * x
 __device__ __forceinline__ ff ff_fma(ff c, ff x, ff acc) { return ff_add(acc, ff_mul(c, x)); }
+
+// a b without the final renormalisation (operands of further products only)
+__device__ __forceinline__ ff ff_mul_nn(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ff{p, e};
+}
+
+// c + x for a float-float c and a float |x| << |c| (x + c.lo rounded once)
+__device__ __forceinline__ ff ff_add_small(ff c, float x) {
+  ff r;
+  fast_two_sum(c.hi, __fadd_rn(x, c.lo), r.hi, r.lo);
+  return r;
+}

@@ -1,24 +1,32 @@
 // FP64 natural logarithm and exponential for the residual kernels, by P. T. P.
 // Tang's table-driven method (ACM TOMS 15, 1989, for exp; ACM TOMS 16, 1990,
-// for log), in about 10 (log) and 11 (exp) FP64-pipe operations; the FP64
-// pipe bounds every kernel on this part.  Tables: mathfn_tables.h
-// (gen_mathfn_tables.py).
+// for log), in 4 FP64-pipe operations each: the FP64 pipe bounds every kernel
+// on this part, so only the reduced argument and the additions that carry the
+// result's leading bits are FP64, and the small correction terms (below 2^-13
+// of the result) are float-float on the FP32 pipe, joined to a double on the
+// integer pipe.  Tables: mathfn_tables.h (gen_mathfn_tables.py).
 //
 // nsfr_log: x = 2^k m, m in [1, 2); with c_j ~ 1/(1 + (j + 1/2)/128), j the
 //   top 7 fraction bits of m, r = m c_j - 1 is formed by one FMA (|r| <= 2^-8)
-//   and ln x = k ln 2 - ln c_j + log1p(r), log1p(r) by its Taylor polynomial
-//   to r^7 (truncation below 2^-58), the terms from r^4 on in FP32.  The error
-//   is about one ulp of max(|ln x|, ln 2): absolute accuracy near x = 1, which
-//   is what the entropy variables and the logarithmic means need.
-// nsfr_exp: x = (32 k + j) ln2/32 + r, |r| <= ln2/64, with the reduction in
-//   Cody and Waite's two-constant form; e^x = 2^k 2^(j/32) (1 + expm1(r)),
-//   expm1(r) by its Taylor polynomial to r^6 (truncation below 2^-58), the
-//   terms from r^5 on in FP32, 2^k added to the exponent field.  About one ulp.
+//   and ln x = k ln 2 - ln c_j + log1p(r), log1p(r) = r + r^2 q(r) by its
+//   Taylor polynomial to r^7 (truncation below 2^-58): ln x = t1 + (r + c),
+//   t1 = k ln2_hi - ln c_j (hi) in FP64, c = r^2 q(r) + k ln2_lo - ln c_j (lo)
+//   (|c| < 2^-16) in float-float.  The error is about one ulp of
+//   max(|ln x|, ln 2): absolute accuracy near x = 1, which is what the entropy
+//   variables and the logarithmic means need.
+// nsfr_exp: x = (32 k + j) ln2/32 + r, |r| <= ln2/64 (n = 32 k + j rounded in
+//   FP32: off by one at most, near a tie, which leaves |r| below 1.01 ln2/64),
+//   with the reduction in Cody and Waite's two-constant form;
+//   e^x = 2^k 2^(j/32) (1 + expm1(r)), expm1(r) = r + r^2 q(r) by its Taylor
+//   polynomial to r^6 (truncation below 2^-58): with s = 2^(j/32) (hi, lo),
+//   e^x = 2^k (s_hi + (s_hi r + c)), c = s_hi r^2 q(r) + s_lo (|c| < 2^-13) in
+//   float-float, 2^k added to the exponent field.  About one ulp.
 // Arguments outside the reduced ranges (x <= 0, subnormal, infinite or NaN
 // for nsfr_log; |x| >= 700 or NaN for nsfr_exp) go to the CUDA library
 // functions; the kernels never produce them for physical states.
 #pragma once
 
+#include "ffloat.cuh"
 #include "mathfn_tables.h"
 
 // where the tables are read from: the global arrays, or a copy a kernel has
@@ -51,24 +59,6 @@ __device__ __forceinline__ MathTables nsfr_stage_tables(double* sm) {
   return MathTables{sm, sm + 128, sm + 256, sm + 384, sm + 416};
 }
 
-// FP32 tails of the polynomials: the log's r^4 q2(r) and the exp's r^5 q3(r)
-// carry factors |r|^4 <= 2^-32 and |r|^5 <= 2^-32, so FP32's relative rounding
-// (below 2^-22 after three operations, plus the truncation of r) contributes
-// less than 2^-56 absolute, while every leading term stays FP64.  The
-// conversions are integer bit operations (the FP64 pipe is the bound).
-__device__ __forceinline__ float tail_arg_f(double r) {
-  // r truncated to float; |r| < 2^-126 (zero included) gives 0
-  const unsigned int hi = (unsigned int)__double2hiint(r), lo = (unsigned int)__double2loint(r);
-  const unsigned int a = hi & 0x7fffffffu;
-  const unsigned int f = a < (897u << 20) ? 0u : (((a - (896u << 20)) << 3) | (lo >> 29));
-  return __uint_as_float(f | (hi & 0x80000000u));
-}
-__device__ __forceinline__ double tail_val_d(float t) {
-  // a normal float to double (exactly)
-  const unsigned int u = __float_as_uint(t), a = u & 0x7fffffffu;
-  return __hiloint2double((int)((u & 0x80000000u) | ((a >> 3) + (896u << 20))), (int)(a << 29));
-}
-
 __device__ __forceinline__ double nsfr_log(double x, const MathTables& T) {
   const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
   if (hi - 0x00100000u >= 0x7fe00000u) return log(x);
@@ -76,32 +66,41 @@ __device__ __forceinline__ double nsfr_log(double x, const MathTables& T) {
   const int j = (int)((hi >> 13) & 127u);
   const double m = __hiloint2double((int)((hi & 0x000fffffu) | 0x3ff00000u), (int)lo);
   const double r = fma(m, T.c[j], -1.0);
-  // log1p(r) = r + r^2 q(r),  q = -1/2 + r (1/3 + r q2),  q2 = -1/4 + r/5 - r^2/6 + r^3/7 in FP32
-  const float rf = tail_arg_f(r);
-  const float q2 = fmaf(fmaf(fmaf(1.0f / 7.0f, rf, -1.0f / 6.0f), rf, 0.2f), rf, -0.25f);
-  const double q = fma(fma(tail_val_d(q2), r, 1.0 / 3.0), r, -0.5);
-  // k as a double: 2^52 + 2^31 + k read from its bit pattern, minus 2^52 + 2^31
-  const double kd = __hiloint2double(0x43300000, (int)((unsigned int)k + 0x80000000u)) - 4503601774854144.0;
-  const double t1 = fma(kd, NSFR_LN2_HI, T.lhi[j]);
-  const double t2 = fma(kd, NSFR_LN2_LO, T.llo[j]);
-  return t1 + (fma(r * r, q, r) + t2);
+  // q = -1/2 + r w, w = 1/3 + r q2, q2 = -1/4 + r/5 - r^2/6 + r^3/7: w and q in
+  // float-float (r/3 and r w need more than FP32's 24 bits), q2 in FP32
+  const ff rf = ff_split_i(r);
+  const float q2 = fmaf(fmaf(fmaf(1.0f / 7.0f, rf.hi, -1.0f / 6.0f), rf.hi, 0.2f), rf.hi, -0.25f);
+  const ff w = ff_add_small(ff{0x1.555556p-2f, -0x1.555556p-27f}, __fmul_rn(rf.hi, q2));
+  const ff q = ff_add_nn(ff{-0.5f, 0.0f}, ff_mul_nn(rf, w));
+  // c = r^2 q + (k ln2_lo + llo_j), renormalised for the join
+  const ff t2 = ff_add_nn(ff_mul_nn(ff{(float)k, 0.0f}, ff{0x1.ef357ap-45f, -0x1.87131ap-70f}),
+                          ff{d2f_i(T.llo[j]), 0.0f});
+  const ff c = ff_add(ff_mul_nn(ff_mul_nn(rf, rf), q), t2);
+  const double t1 = fma(i2d_i(k), NSFR_LN2_HI, T.lhi[j]);
+  return t1 + (r + ff_join_i(c));
 }
 
 __device__ __forceinline__ double nsfr_exp(double x, const MathTables& T) {
   const unsigned int ahi = (unsigned int)__double2hiint(x) & 0x7fffffffu;
   if (ahi >= 0x4085e000u) return exp(x);  // |x| >= 700, infinity, NaN
-  // n = round(32 x / ln 2) in the low word of t (1.5 2^52 fixes the exponent)
-  const double t = fma(x, NSFR_EXP_INV_L, 6755399441055744.0);
-  const int n = __double2loint(t);
-  const double nd = t - 6755399441055744.0;
+  // n = round(32 x / ln 2) in FP32: 1.5 2^23 fixes the binade, so n is the
+  // difference of the bit patterns
+  const float tn = __fmaf_rn(d2f_i(x), 0x1.715476p+5f, 12582912.0f);
+  const int n = (int)__float_as_uint(tn) - 0x4b400000;
+  const double nd = i2d_i(n);
   const double r = fma(-nd, NSFR_EXP_L2, fma(-nd, NSFR_EXP_L1, x));
   const int j = n & 31, k = n >> 5;
-  // expm1(r) = r + r^2 (1/2 + r/6 + r^2/24 + r^3 q3),  q3 = 1/120 + r/720 in FP32
-  const float q3 = fmaf(1.0f / 720.0f, tail_arg_f(r), 1.0f / 120.0f);
-  const double q = fma(fma(fma(tail_val_d(q3), r, 1.0 / 24.0), r, 1.0 / 6.0), r, 0.5);
-  const double p = fma(r * r, q, r);
+  // q = 1/2 + r w, w = 1/6 + r z, z = 1/24 + r (1/120 + r/720): z, w and q in
+  // float-float (their leading terms need more than FP32's 24 bits)
+  const ff rf = ff_split_i(r);
+  const ff z = ff_add_small(ff{0x1.555556p-5f, -0x1.555556p-30f},
+                            __fmul_rn(rf.hi, fmaf(1.0f / 720.0f, rf.hi, 1.0f / 120.0f)));
+  const ff w = ff_add_nn(ff{0x1.555556p-3f, -0x1.555556p-28f}, ff_mul_nn(rf, z));
+  const ff q = ff_add_nn(ff{0.5f, 0.0f}, ff_mul_nn(rf, w));
   const double sh = T.shi[j];
-  const double y = sh + fma(sh, p, T.slo[j]);
+  // c = s_hi r^2 q + s_lo, renormalised for the join
+  const ff c = ff_add(ff_mul_nn(ff_split_i(sh), ff_mul_nn(ff_mul_nn(rf, rf), q)), ff{d2f_i(T.slo[j]), 0.0f});
+  const double y = sh + fma(sh, r, ff_join_i(c));
   return __hiloint2double(__double2hiint(y) + (int)((unsigned int)k << 20), __double2loint(y));
 }
 

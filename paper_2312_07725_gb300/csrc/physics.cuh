@@ -136,15 +136,6 @@ __device__ __forceinline__ ff ff_div_nn(ff a, ff b, float r) {
   return ff{q1, __fmul_rn(rem, r)};
 }
 
-// a b without the final renormalisation (operands of further products only)
-__device__ __forceinline__ ff ff_mul_nn(ff a, ff b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  return ff{p, e};
-}
-
 // 1/x for an FP64 x > 0 from a float-float approximation xf of it and r, the
 // FP32 reciprocal of xf.hi: the float-float seed r + r (1 - xf r) (~2^-45),
 // joined on the integer pipe, and one FP64 Newton step -- two FP64
@@ -154,6 +145,13 @@ __device__ __forceinline__ double rcp_from_ff(double x, ff xf, float r) {
   const float e = __fmaf_rn(-xf.lo, r, __fmaf_rn(-xf.hi, r, 1.0f));
   const double r0 = ff_join_i(ff{r, __fmul_rn(r, e)});
   return fma(r0, fma(-x, r0, 1.0), r0);
+}
+
+// 1/x for an FP64 x > 0 in two FP64 operations: rcp_from_ff of x's
+// integer-pipe split (rcp_full outside the FP32 range).
+__device__ __forceinline__ double rcp_ff(double x) {
+  const ff xf = ff_split_i(x);
+  return rcp_from_ff(x, xf, rcp32(xf.hi));
 }
 
 // The series branch of a logarithmic mean on the FP32 pipe.  With

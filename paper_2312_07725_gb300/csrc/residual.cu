@@ -53,12 +53,12 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
     if (e >= ne) continue;
     const double* ue = u + (size_t)e * 5 * NV + node;
     const double r = ue[0], m0 = ue[NV], m1 = ue[2 * NV], m2 = ue[3 * NV], E = ue[4 * NV];
-    const double ir = rcp_full(r);
+    const double ir = rcp_ff(r);
     const double u0 = m0 * ir, u1 = m1 * ir, u2 = m2 * ir;
     const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
     const double p = gm1 * fma(-0.5 * r, q2, E);
     if (!(r > 0.0) || !(p > 0.0)) atomicOr(flag, 1);
-    const double b2 = r * rcp_full(p);  // 2 beta = rho / p
+    const double b2 = r * rcp_ff(p);  // 2 beta = rho / p
     const double lr = nsfr_log(r, T), lp = nsfr_log(p, T);
     const double s = lp - g * lr;
     double* v = sm + (size_t)le * 5 * NV + node;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
     const double* w = s ? vp : vm;
     if (!(w[4] < 0.0)) atomicOr(flag, 1);
     const double b2 = -w[4];                  // 2 beta
-    const double iv5 = rcp_full(w[4]);
+    const double iv5 = -rcp_ff(b2);
     const double u0 = -w[1] * iv5, u1 = -w[2] * iv5, u2 = -w[3] * iv5;
     const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
     const double sent = g - gm1 * fma(mul_pow2<-1>(b2), q2, w[0]);

@@ -83,12 +83,6 @@ __device__ __forceinline__ ff ff_rcp(ff x) {
 // a - b for close float-float values (|a - b| << |a|): the hi difference is exact
 __device__ __forceinline__ float ff_diff(ff a, ff b) { return (a.hi - b.hi) + (a.lo - b.lo); }
 
-// c + x for a float-float constant c and a correction |x| << |c|
-__device__ __forceinline__ ff ff_add_small(ff c, float x) {
-  ff r;
-  fast_two_sum(c.hi, __fadd_rn(x, c.lo), r.hi, r.lo);
-  return r;
-}
 
 // series branch of the log means in float-float: u = f^2 below this
 #define NSFR_LM_EPS32 1.0e-3f
