@@ -30,14 +30,13 @@ constexpr int vol_ctas(int n) {
 }
 constexpr int vol_threads(int n) { return vol_epb(n) * 3 * n * n; }
 // The FP32-bulk volume kernels: 7 n^3 doubles + 43 n^3 floats of shared memory
-// per element, the same thread layout.  The FP32-bulk form (FP64 log means) is
-// bound by the FP64 pipe like the FP64 kernel and takes its shapes; the
-// float-float variant runs on the FP32 pipe and is bound by latency at the
-// 128-register cap, where 16 warps per SM is the most the register file holds:
-// at n = 5, 3 elements x 2 CTAs (16 warps) measured 2% faster than 2 x 3 (15
-// warps) and 9% faster than 2 x 2.
-constexpr int bulk_epb(int n, bool ff) { return (ff && n == 5) ? 3 : vol_epb(n); }
-constexpr int bulk_ctas(int n, bool ff) { return (ff && n == 5) ? 2 : vol_ctas(n); }
+// per element, the same thread layout.  Both forms run their flux arithmetic
+// on the FP32 pipe and are bound by latency at the 128-register cap, where 16
+// warps per SM is the most the register file holds: at n = 5, 3 elements x 2
+// CTAs (16 warps) measured 2% faster than 2 x 3 (15 warps) and 9% faster than
+// 2 x 2 for the float-float variant.
+constexpr int bulk_epb(int n, bool ff) { return n == 5 ? 3 : vol_epb(n); }
+constexpr int bulk_ctas(int n, bool ff) { return n == 5 ? 2 : vol_ctas(n); }
 constexpr int bulk_threads(int n, bool ff) { return bulk_epb(n, ff) * 3 * n * n; }
 
 // neighbour of element e across face (d, side): side 0 is xi_d = -1 (periodic)

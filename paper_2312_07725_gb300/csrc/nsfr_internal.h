@@ -48,10 +48,13 @@ struct OpsGL {
   float lma[3];
   float lmb[3];
   float cab_hi, cab_lo;
-  // the FP64 kernels' series branch in float-float: {c1 hi, c1 lo, c2 hi, c2 lo,
-  // c3} of G(u) - 1 = u (c1 + u (c2 + u c3)) and of F4g(u) - F4g(0)
+  // the series branch in float-float: {c1 hi, c1 lo, c2 hi, c2 lo, c3} of
+  // G(u) - 1 = u (c1 + u (c2 + u c3)), of F4g(u) - F4g(0) and of
+  // 2 atanh(f)/f - 2 (the FP32-bulk form's H); cab = 2 + 2/(gamma-1) in FP64
   float lmg_ff[5];
   float lmb_ff[5];
+  float lma_ff[5];
+  double cab;
   // Uncollocated scheme (solution on ns Lobatto nodes, the n points above are
   // GL quadrature points, n >= ns): chi (n x ns) the solution basis at the
   // points, Pi = (chi^T W chi)^{-1} chi^T W (ns x n), ls_m / ls_p the solution

@@ -201,6 +201,10 @@ void nsfr_build_ops(int p, int p_geo, double c, double gamma, int nodes, OpsGL* 
     split(gl->f4g[1], gl->lmb_ff);
     split(gl->f4g[2], gl->lmb_ff + 2);
     gl->lmb_ff[4] = (float)gl->f4g[3];
+    split(gl->fr2[1], gl->lma_ff);
+    split(gl->fr2[2], gl->lma_ff + 2);
+    gl->lma_ff[4] = (float)gl->fr2[3];
+    gl->cab = gl->fr2[0] + gl->f4g[0];
   }
   {
     const double cab = 2.0 + 2.0 / (gamma - 1.0);

@@ -157,28 +157,39 @@ __device__ __forceinline__ double rcp_ff(double x) {
 // The series branch of a logarithmic mean on the FP32 pipe.  With
 // f = d / s = (a - b)/(a + b) and u = f^2 formed in float-float from the
 // float-float difference and sum of a, b (rs the FP32 reciprocal of s.hi),
-// it returns false when u >= NSFR_LM_EPS (the caller takes the log branch in
-// FP64); otherwise it sets eps = u (c1 + u (c2 + u c3)) -- the series' part
-// beyond its constant term, c = {c1 hi, c1 lo, c2 hi, c2 lo, c3} -- as a
-// double.  |eps| <= 1e-4 |c1|, and eps is good to about 2^-40 of itself, so
-// c0 + eps in FP64 matches the FP64 Horner form to its rounding: the series
-// costs no FP64 operation (eps's two floats are joined on the integer pipe)
-// instead of the FP64 ratio, square and Horner chain.  f, u and the tail keep
-// ~44 bits: the float-float inputs (2^-48) and the sum and difference (2^-47
-// of the larger operand) put ~2^-49 into f, i.e. below 2^-55 into c0 + eps
-// when u < 1e-4.
-// A sum outside the FP32 range (and a NaN) takes the log branch.
-__device__ __forceinline__ bool lm_series_ff(ff d, ff s, float rs, const float* c, double& eps) {
+// lm_u_ff returns false when u >= NSFR_LM_EPS (the caller takes the log
+// branch in FP64); otherwise lm_tail_ff(u, c) gives the series' part beyond
+// its constant term, eps = u (c1 + u (c2 + u c3)), c = {c1 hi, c1 lo, c2 hi,
+// c2 lo, c3}, as a double.  |eps| <= 1e-4 |c1|, and eps is good to about
+// 2^-40 of itself, so c0 + eps in FP64 matches the FP64 Horner form to its
+// rounding: the series costs no FP64 operation (eps's two floats are joined
+// on the integer pipe) instead of the FP64 ratio, square and Horner chain.
+// f, u and the tail keep ~44 bits: the float-float inputs (2^-48) and the sum
+// and difference (2^-47 of the larger operand) put ~2^-49 into f, i.e. below
+// 2^-55 into c0 + eps when u < 1e-4.  A sum outside the FP32 range (and a
+// NaN) takes the log branch.
+__device__ __forceinline__ bool lm_u_ff(ff d, ff s, float rs, ff& u) {
   if (!(s.hi > 1.0e-37f && s.hi < 1.0e37f)) return false;
   const ff f = ff_div_nn(d, s, rs);
   const float uh = __fmul_rn(f.hi, f.hi);
-  const ff u{uh, __fmaf_rn(__fmul_rn(2.0f, f.hi), f.lo, __fmaf_rn(f.hi, f.hi, -uh))};
-  if (!(uh < (float)NSFR_LM_EPS)) return false;
+  u = ff{uh, __fmaf_rn(__fmul_rn(2.0f, f.hi), f.lo, __fmaf_rn(f.hi, f.hi, -uh))};
+  return uh < (float)NSFR_LM_EPS;
+}
+
+// the tail as float-float (not renormalised), and joined to a double
+__device__ __forceinline__ ff lm_tail_ffv(ff u, const float* c) {
   float ts, te;
-  two_sum(c[2], __fmul_rn(uh, c[4]), ts, te);
-  const ff t{ts, __fadd_rn(te, c[3])};                 // c2 + u c3
+  two_sum(c[2], __fmul_rn(u.hi, c[4]), ts, te);
+  const ff t{ts, __fadd_rn(te, c[3])};                      // c2 + u c3
   const ff q = ff_add_nn(ff{c[0], c[1]}, ff_mul_nn(u, t));  // c1 + u (c2 + u c3)
-  eps = ff_join_i(ff_mul_nn(u, q));
+  return ff_mul_nn(u, q);
+}
+__device__ __forceinline__ double lm_tail_ff(ff u, const float* c) { return ff_join_i(lm_tail_ffv(u, c)); }
+
+__device__ __forceinline__ bool lm_series_ff(ff d, ff s, float rs, const float* c, double& eps) {
+  ff u;
+  if (!lm_u_ff(d, s, rs, u)) return false;
+  eps = lm_tail_ff(u, c);
   return true;
 }
 
@@ -216,12 +227,17 @@ struct RecLogs {
   const Rec& a;
   __device__ __forceinline__ double lr() const { return a.lr; }
   __device__ __forceinline__ double lb() const { return a.lb; }
+  __device__ __forceinline__ double r() const { return a.r; }
+  __device__ __forceinline__ double b2() const { return a.b2; }
 };
 struct PtrLogs {
-  const double* p;  // ln rho at p[0], ln beta at p[off]
+  const double* p;  // ln rho at p[0], ln beta at p[off]: fields of a record with field stride off
   int off;
   __device__ __forceinline__ double lr() const { return p[0]; }
   __device__ __forceinline__ double lb() const { return p[off]; }
+  // the record's FP64 rho and 2 beta (for kernels that stage them in float-float only)
+  __device__ __forceinline__ double r() const { return p[(P_RHO - P_LRHO) * off]; }
+  __device__ __forceinline__ double b2() const { return p[(P_B2 - P_LRHO) * off]; }
 };
 
 // F = f_s(A, B) . n, n the averaged metric row (n0, n1, n2).

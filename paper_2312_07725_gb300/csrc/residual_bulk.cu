@@ -36,11 +36,13 @@
 namespace {
 using namespace nsfr_k;
 
-// log-mean inputs rho, 2 beta: FP64 in the FP32-bulk form, float-float in its
-// float-float variant (the logs are read when a log mean needs them)
+// a node of the bulk kernels: rho, 2 beta, u/2 as float-float (split from the
+// FP64 records in the FP32-bulk form, the float-float records in its variant);
+// the FP64 values and the logs are read from the records when a log mean
+// leaves its series branch
 template <bool FF>
 struct BNode {
-  typename std::conditional<FF, ff, double>::type r, b2;
+  ff r, b2;
   ff u0, u1, u2;  // u/2
   float qq;       // |u|^2/4
 };
@@ -48,16 +50,11 @@ struct BNode {
 template <bool FF>
 __device__ __forceinline__ BNode<FF> bnode_from_rec(const Rec& a) {
   BNode<FF> b;
-  if constexpr (FF) {
-    b.r = ff_from_double(a.r);
-    b.b2 = ff_from_double(a.b2);
-  } else {
-    b.r = a.r;
-    b.b2 = a.b2;
-  }
-  b.u0 = ff_from_double(a.u0);
-  b.u1 = ff_from_double(a.u1);
-  b.u2 = ff_from_double(a.u2);
+  b.r = ff_split_i(a.r);
+  b.b2 = ff_split_i(a.b2);
+  b.u0 = ff_split_i(a.u0);
+  b.u1 = ff_split_i(a.u1);
+  b.u2 = ff_split_i(a.u2);
   b.qq = d2f_i(a.qq);
   return b;
 }
@@ -69,16 +66,16 @@ struct BRef {
   float kin;         // |u_ref|^2 / 2
 };
 
-// 1/x as float-float for x > 0 (normal): the FP32 seed r0 and one correction
-// r0 (1 - x r0), with 1 - x r0 formed by FMAs (error ~2^-46 relative)
-__device__ __forceinline__ ff ff_rcp(ff x) {
-  float r0;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(x.hi));
+// 1/x as float-float for x > 0 (normal): the FP32 seed r0 (rcp32(x.hi)) and
+// one correction r0 (1 - x r0), with 1 - x r0 formed by FMAs (error ~2^-46
+// relative)
+__device__ __forceinline__ ff ff_rcp(ff x, float r0) {
   const float e = __fmaf_rn(-x.lo, r0, __fmaf_rn(-x.hi, r0, 1.0f));
   ff r;
   fast_two_sum(r0, __fmul_rn(r0, e), r.hi, r.lo);
   return r;
 }
+__device__ __forceinline__ ff ff_rcp(ff x) { return ff_rcp(x, rcp32(x.hi)); }
 
 // a - b for close float-float values (|a - b| << |a|): the hi difference is exact
 __device__ __forceinline__ float ff_diff(ff a, ff b) { return (a.hi - b.hi) + (a.lo - b.lo); }
@@ -94,33 +91,41 @@ __device__ __forceinline__ float ff_diff(ff a, ff b) { return (a.hi - b.hi) + (a
 //   H s2 = p_hat s2 / rho_ln + s2 / (2 (gamma-1) beta_ln) = 2 atanh(f_r)/f_r + F4g(u_b)
 //        = (2 + 2/(gamma-1)) + u_r P_a(u_r) + u_b P_b(u_b)
 // (s2 = 2 beta_a + 2 beta_b), truncated where the next term is below 1e-13 (u < 1e-3).
-// The FP32-bulk form: the log means and the scalars made from them in FP64,
-// with H s2 = 2 atanh(f_r)/f_r + F4g(u_b) on the series branches as below.
+// The FP32-bulk form: the log means to FP64 accuracy as the FP64 path forms
+// them -- the series branch (u < 1e-4) from the nodes' float-float rho and
+// 2 beta with float-float tails good to ~2^-40 of themselves (lm_u_ff,
+// lm_tail_ffv), the FP64 records and logs off it -- and the scalars made from
+// them in float-float: rho_ln = (s/2)(1 + eps_G(u_r)), H s2 = (2 + F4g(0)) +
+// eps_a(u_r) + eps_b(u_b), eps_a the series of 2 atanh(f_r)/f_r - 2.
 template <class LA, class LB>
 __device__ __forceinline__ void bulk_flux(const BNode<false>& A, const BNode<false>& B, ff n0, ff n1, ff n2,
                                           const BRef& ref, const OpsGL& K, const LA& la, const LB& lb, ff& Fr,
                                           float Fm[3], float& FE) {
-  const double sr = A.r + B.r, dr = A.r - B.r;
-  const double s2 = A.b2 + B.b2, d2 = A.b2 - B.b2;
-  const double rb2 = rcp_newton1(s2), rr = rcp_newton1(sr);
-  const double fr = dr * rr, fb = d2 * rb2;
-  const double ur = fr * fr, ub = fb * fb;
-  double rln, a, b;  // rho_ln and the two parts of H s2
-  if (lm_small(ur)) {
-    rln = sr * horner4(K.gh, ur);
-    a = horner4(K.fr2, ur);
-  } else {
-    const double dl = la.lr() - lb.lr();
-    rln = dr / dl;
-    a = sr * dl / dr;
+  const ff sr = ff_add_nn(A.r, B.r), s2 = ff_add_nn(A.b2, B.b2);
+  const float rs2 = rcp32(s2.hi);
+  const ff rb2 = ff_rcp(s2, rs2);
+  ff ur, ub, rln, cx;  // cx = H s2 - (2 + 2/(gamma-1))
+  if (lm_u_ff(ff_add_nn(A.r, ff_neg(B.r)), sr, rcp32(sr.hi), ur)) {
+    const ff sh{0.5f * sr.hi, 0.5f * sr.lo};
+    rln = ff_add(sh, ff_mul_nn(sh, lm_tail_ffv(ur, K.lmg_ff)));
+    cx = lm_tail_ffv(ur, K.lma_ff);
+  } else {  // FP64 from the records and the logs of the face-state pass
+    const double dr = la.r() - lb.r(), dl = la.lr() - lb.lr();
+    rln = ff_split_i(dr / dl);
+    cx = ff_split_i(fma(la.r() + lb.r(), dl / dr, -K.fr2[0]));
   }
-  if (lm_small(ub)) b = horner4(K.f4g, ub);
-  else b = K.inv_gm1 * (la.lb() - lb.lb()) * s2 / d2;
-  const float dp = d2f_i(fma(sr, rb2, -ref.p));
-  const float dH = d2f_i(fma(a + b, rb2, -ref.H));
+  if (lm_u_ff(ff_add_nn(A.b2, ff_neg(B.b2)), s2, rs2, ub)) {
+    cx = ff_add(cx, lm_tail_ffv(ub, K.lmb_ff));
+  } else {
+    const double sb = la.b2() + lb.b2(), db = la.b2() - lb.b2();
+    cx = ff_add(cx, ff_split_i(fma(K.inv_gm1 * (la.lb() - lb.lb()), sb / db, -K.f4g[0])));
+  }
+  const ff H = ff_mul(ff_add(ff{K.cab_hi, K.cab_lo}, cx), rb2);
+  const float dp = ff_diff(ff_mul(sr, rb2), ref.pf);
+  const float dH = ff_diff(H, ref.Hf);
   const ff v0 = ff_add_nn(A.u0, B.u0), v1 = ff_add_nn(A.u1, B.u1), v2 = ff_add_nn(A.u2, B.u2);
   const ff un = ff_add_nn(ff_add_nn(ff_mul(v0, n0), ff_mul(v1, n1)), ff_mul(v2, n2));
-  Fr = ff_mul(ff_from_double(rln), un);
+  Fr = ff_mul(rln, un);
   const float f = Fr.hi;
   const float w0 = ff_diff(v0, ref.u0), w1 = ff_diff(v1, ref.u1), w2 = ff_diff(v2, ref.u2);
   Fm[0] = fmaf(f, w0, dp * n0.hi);
@@ -413,7 +418,7 @@ __device__ void uncol_epilogue_f(const double* Rd, float* X, float* Y, int nel, 
 }
 
 // shared-memory layout per element (SoA over the NV nodes)
-//   floats : r, 2 beta as float-float (the bytes of 2 doubles) 4 NV
+//   floats : r, 2 beta as float-float                          4 NV
 //   doubles: R (combined), epilogue                            5 NV
 //   floats : u/2 hi(3) lo(3), |u|^2/4, metric hi(9) lo(9)     25 NV
 //   floats : line sums R_rho hi, lo, R_m(3), R_E', one slab
@@ -434,10 +439,8 @@ __global__ void __launch_bounds__(bulk_threads(N, FF), bulk_ctas(N, FF))
   const int epb = blockDim.x / NL;
   const int e0 = e_beg + blockIdx.x * epb;
   BRef* Refs = (BRef*)sm;                          // [epb]
-  // [epb][2][NV] doubles (FP32-bulk) or [epb][4][NV] floats (float-float): rho, 2 beta
-  double* Pdd = (double*)(Refs + epb);
-  float* Pdf = (float*)Pdd;
-  double* Rd = Pdd + (size_t)epb * 2 * NV;         // [epb][5][NV]
+  float* Pdf = (float*)(Refs + epb);               // [epb][4][NV] rho, 2 beta as float-float
+  double* Rd = (double*)(Pdf + (size_t)epb * 4 * NV);  // [epb][5][NV]
   float* Pf = (float*)(Rd + (size_t)epb * 5 * NV); // [epb][25][NV]
   float* Ra = Pf + (size_t)epb * 25 * NV;          // [epb][3][6][NV]
   float* Xf = Pf;                                  // epilogue (aliases Pf)
@@ -466,12 +469,15 @@ __global__ void __launch_bounds__(bulk_threads(N, FF), bulk_ctas(N, FF))
       // the FP64 node record (face_state_kernel)
       const Rec a = load_rec6(nrec + (size_t)e * NSFR_NFIELD * NV + node, NV);
       if (node == 0) Refs[le] = make_ref(a, ops);
-      double* pd = Pdd + (size_t)le * 2 * NV + node;
-      pd[0] = a.r;
-      pd[NV] = a.b2;
-      u0 = ff_from_double(a.u0);
-      u1 = ff_from_double(a.u1);
-      u2 = ff_from_double(a.u2);
+      const ff r = ff_split_i(a.r), b2 = ff_split_i(a.b2);
+      float* pd = Pdf + (size_t)le * 4 * NV + node;
+      pd[0] = r.hi;
+      pd[NV] = r.lo;
+      pd[2 * NV] = b2.hi;
+      pd[3 * NV] = b2.lo;
+      u0 = ff_split_i(a.u0);
+      u1 = ff_split_i(a.u1);
+      u2 = ff_split_i(a.u2);
       qq = d2f_i(a.qq);
     }
     float* pf = Pf + (size_t)le * 25 * NV + node;
@@ -500,20 +506,14 @@ __global__ void __launch_bounds__(bulk_threads(N, FF), bulk_ctas(N, FF))
   line_geometry<N>(d, l0, l1, base, stride);
   if (le < epb && e < ne) {
     const float* pdf = Pdf + (size_t)le * 4 * NV + base;
-    const double* pdd = Pdd + (size_t)le * 2 * NV + base;
     const float* pf = Pf + (size_t)le * 25 * NV + base;
     const double* Le = nrec + ((size_t)e * NSFR_NFIELD + P_LRHO) * NV + base;  // ln rho, ln beta (read only off the series path)
     float* Rl = Ra + ((size_t)le * 18 + 6 * d) * NV + base;
     const BRef ref = Refs[le];
     auto node_at = [&](int a) {
       BNode<FF> b;
-      if constexpr (FF) {
-        b.r = ff{pdf[a * stride], pdf[NV + a * stride]};
-        b.b2 = ff{pdf[2 * NV + a * stride], pdf[3 * NV + a * stride]};
-      } else {
-        b.r = pdd[a * stride];
-        b.b2 = pdd[NV + a * stride];
-      }
+      b.r = ff{pdf[a * stride], pdf[NV + a * stride]};
+      b.b2 = ff{pdf[2 * NV + a * stride], pdf[3 * NV + a * stride]};
       b.u0 = ff{pf[a * stride], pf[3 * NV + a * stride]};
       b.u1 = ff{pf[NV + a * stride], pf[4 * NV + a * stride]};
       b.u2 = ff{pf[2 * NV + a * stride], pf[5 * NV + a * stride]};
