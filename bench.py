@@ -47,10 +47,11 @@ import workloads as wl  # noqa: E402
 # two log means) and per accumulation of one flux into two residual entries
 FLOPS_PER_FLUX = 55
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one volume_kernel<5>
-# launch per element, from an ncu --set full capture at 24^3 elements (813.2 + 125.4 MB
-# for 13,824 elements, the pair-table form: profiles/volume_kernel_p4_tgv24.md; every
-# buffer the kernel touches scales with the element count)
-VOLUME_DRAM_BYTES_PER_ELEMENT = {4: (813.17248e6 + 125.372416e6) / 13824}
+# launch per element, from an ncu --set full capture at 24^3 elements (814.1 + 125.6 MB
+# for 13,824 elements, the kernel with the float-float series branch:
+# profiles/volume_kernel_p4_tgv24.md; every buffer the kernel touches scales with the
+# element count)
+VOLUME_DRAM_BYTES_PER_ELEMENT = {4: (814.130176e6 + 125.56544e6) / 13824}
 FLOPS_PER_ACC = 20
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -717,11 +718,6 @@ def stage_kernel_models(p, ne, precision, has_k=True):
             "volume": ("flops", vol), "max_wavespeed": ("bytes", 40 * n ** 3 * ne)}
 
 
-# FP64 flops per two-point flux that the fp32_bulk form keeps in FP64: the two log
-# means (sums, the reciprocal and f^2, the series) and the scalars p_hat and H made of them
-BULK_FP64_FLOPS_PER_FLUX = 28
-
-
 def roofline_kernels(kern, p, ne, precision, clk, peaks, has_k=True):
     """Per-kernel rooflines of one precision mode's timed step: algorithmic work per launch
     (stage_kernel_models) over the kernel's mean launch time from the library's CUDA events,
@@ -733,7 +729,6 @@ def roofline_kernels(kern, p, ne, precision, clk, peaks, has_k=True):
     fp32_nom = 152 * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
     hbm, hbm_src = hbm_peak()
     models = stage_kernel_models(p, ne, precision, has_k)
-    n = p + 1
     out = {}
     for name, (kind, work) in models.items():
         if name not in kern:
@@ -745,14 +740,14 @@ def roofline_kernels(kern, p, ne, precision, clk, peaks, has_k=True):
                          "achieved": ach, "unit": "GB/s", "peak": hbm, "frac": ach / hbm, "peak_source": hbm_src}
             continue
         ach = work / t / 1e12
-        fp64_part = work
         pipe = "fp64"
+        # the bulk volume kernels run their flux arithmetic on the FP32 pipe (the log
+        # means' series branch included, in float-float); FP64 is left on the rare log
+        # branch and the epilogue's conversions
         if precision != "fp64" and name == "volume":
-            fluxes = 3 * n ** 3 * (n - 1) // 2 + 6 * n ** 3
-            fp64_part = BULK_FP64_FLOPS_PER_FLUX * fluxes * ne if precision == "fp32_bulk" else 0
             pipe = "fp32"
         if precision == "fp32_bulk_ff" and name == "face_states":
-            fp64_part, pipe = 0, "fp32"
+            pipe = "fp32"
         e = {"bound": "alu", "work_per_launch": work, "work_unit": "flops", "ms_avg": t * 1e3, "achieved": ach,
              "unit": "TFLOP/s"}
         if pipe == "fp64":
@@ -761,11 +756,6 @@ def roofline_kernels(kern, p, ne, precision, clk, peaks, has_k=True):
         else:
             e.update({"pipe": "fp32 (the flux arithmetic; float-float where the form says so)", "peak": fp32_nom,
                       "frac": ach / fp32_nom, "peak_source": f"152 SMs x 128 FP32 FMA/clk/SM x 2 x {mhz:.0f} MHz"})
-            if fp64_part:
-                a64 = fp64_part / t / 1e12
-                e["fp64_part"] = {"flops_per_launch": fp64_part, "achieved": a64, "peak": fp64_nom,
-                                  "frac": a64 / fp64_nom,
-                                  "model": f"{BULK_FP64_FLOPS_PER_FLUX} FP64 flops per flux (log means, p_hat, H)"}
         if peaks and pipe == "fp64" and "fp64" in peaks:
             e["frac_of_measured_probe"] = ach / peaks["fp64"]["tflops"]
         out[name] = e
