@@ -339,6 +339,41 @@ __device__ __forceinline__ double ec_flux_over_sr_ff(const Rec& A, const Rec& B,
   return sr;
 }
 
+// ec_flux_l with the log means' series branch on the FP32 pipe (the flux
+// itself, not divided by s): rho_ln = (s/2)(1 + eps_r).
+template <class LA, class LB>
+__device__ __forceinline__ void ec_flux_ff(const Rec& A, const Rec& B, const RecF& Af, const RecF& Bf, double n0,
+                                           double n1, double n2, const OpsGL& K, const LA& la, const LB& lb,
+                                           double F[5]) {
+  const double sr = A.r + B.r, s2 = A.b2 + B.b2;
+  const ff s2f = ff_add_nn(Af.b2, Bf.b2);
+  const float rs2 = rcp32(s2f.hi);
+  const double rb2 = rcp_from_ff(s2, s2f, rs2);
+  const double qs = A.qq + B.qq;
+  double er, eb, rln, h;
+  if (lm_series_ff(Af.r, Bf.r, K.lmg_ff, er)) {
+    const double sh = mul_pow2<-1>(sr);
+    rln = fma(sh, er, sh);
+  } else {
+    rln = (A.r - B.r) / (la.lr() - lb.lr());
+  }
+  if (lm_series_ff(ff_add_nn(Af.b2, ff_neg(Bf.b2)), s2f, rs2, K.lmb_ff, eb))
+    h = fma(eb, rb2, fma(K.f4g[0], rb2, -qs));
+  else
+    h = K.inv_gm1 * (la.lb() - lb.lb()) / (A.b2 - B.b2) - qs;
+  const double ph = sr * rb2;
+  const double v0 = A.u0 + B.u0, v1 = A.u1 + B.u1, v2 = A.u2 + B.u2;  // u_bar
+  const double un = fma(v0, n0, fma(v1, n1, v2 * n2));
+  const double Fr = rln * un;
+  F[0] = Fr;
+  F[1] = fma(Fr, v0, ph * n0);
+  F[2] = fma(Fr, v1, ph * n1);
+  F[3] = fma(Fr, v2, ph * n2);
+  F[4] = fma(v2, F[3], fma(v1, F[2], fma(v0, F[1], Fr * h)));
+}
+
+__device__ __forceinline__ RecF recf_split(const Rec& a) { return RecF{ff_split_i(a.r), ff_split_i(a.b2)}; }
+
 __device__ __forceinline__ void ec_flux(const Rec& A, const Rec& B, double n0, double n1, double n2,
                                         const OpsGL& K, double F[5]) {
   ec_flux_l(A, B, n0, n1, n2, K, RecLogs{A}, RecLogs{B}, F);
@@ -504,10 +539,11 @@ __device__ __forceinline__ void es_dissipation(const Rec& L, const Rec& R, doubl
 // (1/2) R |Lambda| T R^T [[v]] (entropy-variable matrix dissipation).
 __device__ __forceinline__ void face_flux(const Rec& L, const Rec& R, double n0, double n1, double n2,
                                           const OpsGL& K, int kind, int vf, double F[5]) {
+  const RecF Lf = recf_split(L), Rf = recf_split(R);
   if (vf == NSFR_FLUX_RANOCHA)
-    ranocha_flux_l(L, R, pressure_of(L), pressure_of(R), n0, n1, n2, K, RecLogs{L}, RecLogs{R}, F);
+    ranocha_flux_ff(L, R, Lf, Rf, pressure_of(L), pressure_of(R), n0, n1, n2, K, RecLogs{L}, RecLogs{R}, F);
   else
-    ec_flux(L, R, n0, n1, n2, K, F);
+    ec_flux_ff(L, R, Lf, Rf, n0, n1, n2, K, RecLogs{L}, RecLogs{R}, F);
   if (kind == NSFR_FACE_EC_ROE || kind == NSFR_FACE_EC_ES) {
     double D[5];
     if (kind == NSFR_FACE_EC_ROE) roe_dissipation(L, R, n0, n1, n2, K.gamma, D);
