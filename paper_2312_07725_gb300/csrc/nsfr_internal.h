@@ -54,6 +54,7 @@ struct OpsGL {
   float lmg_ff[5];
   float lmb_ff[5];
   float lma_ff[5];
+  float lmgd_ff[5];  // G'(u) = c1 + u (c2 + u c3) (the adjoint's log-mean derivatives)
   double cab;
   // Uncollocated scheme (solution on ns Lobatto nodes, the n points above are
   // GL quadrature points, n >= ns): chi (n x ns) the solution basis at the

@@ -205,6 +205,9 @@ void nsfr_build_ops(int p, int p_geo, double c, double gamma, int nodes, OpsGL* 
     split(gl->fr2[2], gl->lma_ff + 2);
     gl->lma_ff[4] = (float)gl->fr2[3];
     gl->cab = gl->fr2[0] + gl->f4g[0];
+    split(G[1], gl->lmgd_ff);
+    split(2.0 * G[2], gl->lmgd_ff + 2);
+    gl->lmgd_ff[4] = (float)(3.0 * G[3]);
   }
   {
     const double cab = 2.0 + 2.0 / (gamma - 1.0);

@@ -168,22 +168,27 @@ __device__ __forceinline__ double rcp_ff(double x) {
 // and difference (2^-47 of the larger operand) put ~2^-49 into f, i.e. below
 // 2^-55 into c0 + eps when u < 1e-4.  A sum outside the FP32 range (and a
 // NaN) takes the log branch.
-__device__ __forceinline__ bool lm_u_ff(ff d, ff s, float rs, ff& u) {
+__device__ __forceinline__ bool lm_uf_ff(ff d, ff s, float rs, ff& f, ff& u) {
   if (!(s.hi > 1.0e-37f && s.hi < 1.0e37f)) return false;
-  const ff f = ff_div_nn(d, s, rs);
+  f = ff_div_nn(d, s, rs);
   const float uh = __fmul_rn(f.hi, f.hi);
   u = ff{uh, __fmaf_rn(__fmul_rn(2.0f, f.hi), f.lo, __fmaf_rn(f.hi, f.hi, -uh))};
   return uh < (float)NSFR_LM_EPS;
 }
+__device__ __forceinline__ bool lm_u_ff(ff d, ff s, float rs, ff& u) {
+  ff f;
+  return lm_uf_ff(d, s, rs, f, u);
+}
 
-// the tail as float-float (not renormalised), and joined to a double
-__device__ __forceinline__ ff lm_tail_ffv(ff u, const float* c) {
+// c1 + u (c2 + u c3) in float-float (not renormalised), the tail u (c1 + ...)
+// as float-float, and the tail joined to a double
+__device__ __forceinline__ ff lm_poly_ffv(ff u, const float* c) {
   float ts, te;
   two_sum(c[2], __fmul_rn(u.hi, c[4]), ts, te);
-  const ff t{ts, __fadd_rn(te, c[3])};                      // c2 + u c3
-  const ff q = ff_add_nn(ff{c[0], c[1]}, ff_mul_nn(u, t));  // c1 + u (c2 + u c3)
-  return ff_mul_nn(u, q);
+  const ff t{ts, __fadd_rn(te, c[3])};                   // c2 + u c3
+  return ff_add_nn(ff{c[0], c[1]}, ff_mul_nn(u, t));     // c1 + u (c2 + u c3)
 }
+__device__ __forceinline__ ff lm_tail_ffv(ff u, const float* c) { return ff_mul_nn(u, lm_poly_ffv(u, c)); }
 __device__ __forceinline__ double lm_tail_ff(ff u, const float* c) { return ff_join_i(lm_tail_ffv(u, c)); }
 
 __device__ __forceinline__ bool lm_series_ff(ff d, ff s, float rs, const float* c, double& eps) {

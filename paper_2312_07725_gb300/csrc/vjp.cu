@@ -27,29 +27,46 @@ struct PR {
   double r, u0, u1, u2, b;  // rho, velocity, beta = rho / (2p)
 };
 
-// log mean L(a, b) and its partial derivatives; also 1/(a + b).  Series
-// branch: L = s G(u)/2 with s = a + b, f = (a - b)/s, u = f^2 and
-// G = f/atanh f = 1 - u/3 - 4u^2/45 - 44u^3/945 (next term below 1e-16 for
-// u < NSFR_LM_EPS), so that dL/da = G/2 + 2 G'(u) f b/s and
-// dL/db = G/2 - 2 G'(u) f a/s; otherwise L = (a - b)/(ln a - ln b).
-// (reciprocals by an FP32 seed and a third-order step, rcp_full: a division
-// costs several times as many FP64-pipe operations)
-__device__ __forceinline__ void logmean_grad(double a, double b, double& L, double& La, double& Lb, double& is) {
-  const double s = a + b, d = a - b;
-  is = rcp_full(s);
-  const double f = d * is, u = f * f;
-  if (u < NSFR_LM_EPS) {
-    const double h = fma(fma(fma(-22.0 / 945.0, u, -2.0 / 45.0), u, -1.0 / 6.0), u, 0.5);    // G/2
-    const double g2 = fma(fma(-264.0 / 945.0, u, -16.0 / 45.0), u, -2.0 / 3.0) * (f * is);  // 2 G' f/s
-    L = s * h;
-    La = fma(g2, b, h);
-    Lb = fma(-g2, a, h);
-  } else {
-    const double iD = rcp_full(nsfr_log(a) - nsfr_log(b));
-    L = d * iD;
-    La = (1.0 - L * rcp_full(a)) * iD;
-    Lb = (L * rcp_full(b) - 1.0) * iD;
+// Node splits for the reverse fluxes: rho and beta as float-float.
+struct PRF {
+  ff r, b;
+};
+
+// log mean L(a, b) and its partial derivatives.  Series branch, as the
+// forward kernels form the log means: L = s G(u)/2 with s = a + b,
+// f = (a - b)/s, u = f^2 < NSFR_LM_EPS and G = f/atanh f = 1 - u/3 - 4u^2/45
+// - 44u^3/945 (next term below 1e-16), so that dL/da = G/2 + 2 G'(u) f b/s and
+// dL/db = G/2 - 2 G'(u) f a/s:
+//   L = (s/2)(1 + eps_G),  dL/da = 1/2 + (eps_G/2 + 2 G'(u) f b/s),
+//   dL/db = 1/2 + (eps_G/2 - 2 G'(u) f a/s),
+// eps_G = G - 1, with f, u and the parenthesised corrections (below 7e-3)
+// in float-float from float-float a, b (sf their sum, rs the FP32 reciprocal
+// of sf.hi), joined on the integer pipe: 4 FP64 operations instead of about
+// 17.  Returns whether the series branch was taken (u set); otherwise
+// L = (a - b)/(ln a - ln b) and its derivatives in FP64 (reciprocals by an
+// FP32 seed and a third-order step, rcp_full: a division costs several times
+// as many FP64-pipe operations).
+__device__ __forceinline__ bool logmean_grad_ff(double a, double b, ff af, ff bf, ff sf, float rs, const OpsGL& K,
+                                                double& L, double& La, double& Lb, ff& u) {
+  ff f;
+  if (lm_uf_ff(ff_add_nn(af, ff_neg(bf)), sf, rs, f, u)) {
+    const ff eg = lm_tail_ffv(u, K.lmg_ff);
+    // 2 G'(u) f / s, 1/s from rs and one float-float correction
+    const float e = __fmaf_rn(-sf.lo, rs, __fmaf_rn(-sf.hi, rs, 1.0f));
+    const ff t = ff_mul_nn(ff_mul_nn(lm_poly_ffv(u, K.lmgd_ff), f), ff{rs, __fmul_rn(rs, e)});
+    const ff t2{2.0f * t.hi, 2.0f * t.lo};
+    const ff eh{0.5f * eg.hi, 0.5f * eg.lo};
+    const double sh = mul_pow2<-1>(a + b);
+    L = fma(sh, ff_join_i(eg), sh);
+    La = 0.5 + ff_join_i(ff_add(eh, ff_mul_nn(t2, bf)));
+    Lb = 0.5 + ff_join_i(ff_add(eh, ff_neg(ff_mul_nn(t2, af))));
+    return true;
   }
+  const double iD = rcp_full(nsfr_log(a) - nsfr_log(b));
+  L = (a - b) * iD;
+  La = (1.0 - L * rcp_full(a)) * iD;
+  Lb = (L * rcp_full(b) - 1.0) * iD;
+  return false;
 }
 
 // reverse of F = f_s(A, B) . n (Chandrashekar): accumulates into Ab, Bb, nb.
@@ -59,28 +76,39 @@ __device__ __forceinline__ void logmean_grad(double a, double b, double& L, doub
 //   F_E = F_rho (h - |u|^2_bar/2) + u_bar . F_m = F_rho (h + u_A . u_B/2) + p_hat (u_bar . n)
 // (|u_bar|^2 - |u|^2_bar/2 = u_A . u_B/2), reversed term by term.  F is
 // linear in n, so a caller may pass a multiple of n with Fb divided by it.
-__device__ __forceinline__ void ec_flux_vjp(const PR& A, const PR& B, double n0, double n1, double n2, double igm1,
-                                            const double Fb[5], PR& Ab, PR& Bb, double nb[3]) {
-  double rl, rla, rlb, isr, bl, bla, blb, isb;
-  logmean_grad(A.r, B.r, rl, rla, rlb, isr);
-  logmean_grad(A.b, B.b, bl, bla, blb, isb);
-  const double v0 = 0.5 * (A.u0 + B.u0), v1 = 0.5 * (A.u1 + B.u1), v2 = 0.5 * (A.u2 + B.u2);
+// Af, Bf: the float-float rho and beta of A and B (the log means' series
+// branch, logmean_grad_ff); 1/s_b from a float-float seed and one Newton step,
+// and on the series branch 1/beta_ln = (1/s_b)(2 atanh(f)/f) = (1/s_b)(2 + eps_a).
+__device__ __forceinline__ void ec_flux_vjp(const PR& A, const PR& B, const PRF& Af, const PRF& Bf, double n0,
+                                            double n1, double n2, const OpsGL& K, const double Fb[5], PR& Ab,
+                                            PR& Bb, double nb[3]) {
+  double rl, rla, rlb, bl, bla, blb;
+  ff ur, ub;
+  const ff sr = ff_add_nn(Af.r, Bf.r), sb = ff_add_nn(Af.b, Bf.b);
+  const float rsb = rcp32(sb.hi);
+  logmean_grad_ff(A.r, B.r, Af.r, Bf.r, sr, rcp32(sr.hi), K, rl, rla, rlb, ur);
+  const double isb = rcp_from_ff(A.b + B.b, sb, rsb);
+  double ibl;
+  if (logmean_grad_ff(A.b, B.b, Af.b, Bf.b, sb, rsb, K, bl, bla, blb, ub))
+    ibl = fma(isb, ff_join_i(lm_tail_ffv(ub, K.lma_ff)), mul_pow2<1>(isb));
+  else
+    ibl = rcp_full(bl);
+  const double v0 = mul_pow2<-1>(A.u0 + B.u0), v1 = mul_pow2<-1>(A.u1 + B.u1), v2 = mul_pow2<-1>(A.u2 + B.u2);
   const double un = fma(v0, n0, fma(v1, n1, v2 * n2));
   const double F0 = rl * un;
-  const double hs = 0.5 * isb;  // dp_hat/drho_A = dp_hat/drho_B
+  const double hs = mul_pow2<-1>(isb);  // dp_hat/drho_A = dp_hat/drho_B
   const double ph = (A.r + B.r) * hs;
-  const double ibl = rcp_full(bl);
-  const double h = 0.5 * igm1 * ibl;
+  const double h = mul_pow2<-1>(K.inv_gm1 * ibl);
   const double uab = fma(A.u0, B.u0, fma(A.u1, B.u1, A.u2 * B.u2));
   // reverse
   const double t4 = Fb[4];
   const double F0b = fma(t4, fma(0.5, uab, h), fma(Fb[1], v0, fma(Fb[2], v1, fma(Fb[3], v2, Fb[0]))));
   const double phb = fma(t4, un, fma(Fb[1], n0, fma(Fb[2], n1, Fb[3] * n2)));
   const double hb = t4 * F0;
-  const double uabb = 0.5 * hb;
+  const double uabb = mul_pow2<-1>(hb);
   const double unb = fma(F0b, rl, t4 * ph);  // u_bar . n: through F_rho and F_E
   // u_bar cotangent (F_rho Fb_m + unb n) shared by both sides, halved, plus the u_A . u_B term
-  const double F0h = 0.5 * F0, unbh = 0.5 * unb;
+  const double F0h = mul_pow2<-1>(F0), unbh = mul_pow2<-1>(unb);
   const double g0 = fma(unbh, n0, F0h * Fb[1]), g1 = fma(unbh, n1, F0h * Fb[2]), g2 = fma(unbh, n2, F0h * Fb[3]);
   Ab.u0 += fma(uabb, B.u0, g0);
   Ab.u1 += fma(uabb, B.u1, g1);
@@ -245,6 +273,7 @@ __global__ void __launch_bounds__(threads_for(N), 1)
   double* Rb = P + (size_t)epb * 5 * NV;   // [epb][5][NV] Rbar
   double* Pb = Rb + (size_t)epb * 5 * NV;  // [epb][5][NV] record cotangents
   double* Y = Pb + (size_t)epb * 5 * NV;   // [epb][5][NV] Pi~^T R (for Jbar)
+  PRF* Pf = reinterpret_cast<PRF*>(Y + (size_t)epb * 5 * NV);  // [epb][NV] rho, beta as float-float
   const double g = ops.gamma;
   const int nel = min(epb, ne - e0);
   const int total = nel * 5 * NV;
@@ -341,6 +370,12 @@ __global__ void __launch_bounds__(threads_for(N), 1)
     }
   }
   }  // collocated
+  for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
+    const int le = t / NV, node = t % NV;
+    const double* p = P + (size_t)le * 5 * NV + node;
+    Pf[t] = PRF{ff_split_i(p[0]), ff_split_i(p[4 * NV])};
+  }
+  __syncthreads();
 
   // line phase
   const int le = threadIdx.x / NL, l = threadIdx.x % NL, e = e0 + le;
@@ -356,6 +391,7 @@ __global__ void __launch_bounds__(threads_for(N), 1)
   }
   if (valid) {
     const double* Pe = P + (size_t)le * 5 * NV + base;
+    const PRF* Pfe = Pf + (size_t)le * NV + base;
     const double* Re = Rb + (size_t)le * 5 * NV + base;
     const double* Me = metric + ((size_t)e * 9 + 3 * d) * NV + base;
     const double wperp = ops.w[l0] * ops.w[l1];
@@ -370,8 +406,9 @@ __global__ void __launch_bounds__(threads_for(N), 1)
         double Fb[5];
         for (int k = 0; k < 5; ++k) Fb[k] = c * (Re[k * NV + a * stride] - Re[k * NV + b * stride]);
         double nb[3] = {0.0, 0.0, 0.0};
-        ec_flux_vjp(A, B, Me[a * stride] + Me[b * stride], Me[NV + a * stride] + Me[NV + b * stride],
-                    Me[2 * NV + a * stride] + Me[2 * NV + b * stride], ops.inv_gm1, Fb, ab[a], ab[b], nb);
+        ec_flux_vjp(A, B, Pfe[a * stride], Pfe[b * stride], Me[a * stride] + Me[b * stride],
+                    Me[NV + a * stride] + Me[NV + b * stride], Me[2 * NV + a * stride] + Me[2 * NV + b * stride], ops,
+                    Fb, ab[a], ab[b], nb);
         for (int c2 = 0; c2 < 3; ++c2) {
           mb[a][c2] += nb[c2];
           mb[b][c2] += nb[c2];
@@ -383,6 +420,7 @@ __global__ void __launch_bounds__(threads_for(N), 1)
       const int enb = nbr_index(e, d, s, nx, ny, nz);
       const PR Fo = pr_from_face(face + (((size_t)e * 6 + f) * NSFR_NFIELD) * NFP + line, NFP);
       const PR Fn = pr_from_face(face + (((size_t)enb * 6 + 2 * d + 1 - s) * NSFR_NFIELD) * NFP + line, NFP);
+      const PRF Fof{ff_split_i(Fo.r), ff_split_i(Fo.b)}, Fnf{ff_split_i(Fn.r), ff_split_i(Fn.b)};
       const double* nf = nf_plus + (((size_t)(s ? e : enb) * 3 + d) * 3) * NFP + line;
       const double f0 = nf[0], f1 = nf[NFP], f2 = nf[2 * NFP];
       const double* t = s ? ops.tp : ops.tm;
@@ -395,8 +433,8 @@ __global__ void __launch_bounds__(threads_for(N), 1)
       PR fob{0, 0, 0, 0, 0}, fnb{0, 0, 0, 0, 0};
       double nfb[3] = {0.0, 0.0, 0.0};
       // face flux f* = F(L, R; n_f)
-      if (s) ec_flux_vjp(Fo, Fn, f0, f1, f2, ops.inv_gm1, rho, fob, fnb, nfb);
-      else ec_flux_vjp(Fn, Fo, f0, f1, f2, ops.inv_gm1, rho, fnb, fob, nfb);
+      if (s) ec_flux_vjp(Fo, Fn, Fof, Fnf, f0, f1, f2, ops, rho, fob, fnb, nfb);
+      else ec_flux_vjp(Fn, Fo, Fnf, Fof, f0, f1, f2, ops, rho, fnb, fob, nfb);
       // hybrid terms (metric-row sums with halved cotangents, as above)
       for (int a = 0; a < N; ++a) {
         const PR A = pr_load(Pe + a * stride, NV);
@@ -404,8 +442,8 @@ __global__ void __launch_bounds__(threads_for(N), 1)
         double Fb[5];
         for (int k = 0; k < 5; ++k) Fb[k] = th * fma(sw, Re[k * NV + a * stride], -rho[k]);
         double nb[3] = {0.0, 0.0, 0.0};
-        ec_flux_vjp(A, Fo, Me[a * stride] + f0, Me[NV + a * stride] + f1, Me[2 * NV + a * stride] + f2,
-                    ops.inv_gm1, Fb, ab[a], fob, nb);
+        ec_flux_vjp(A, Fo, Pfe[a * stride], Fof, Me[a * stride] + f0, Me[NV + a * stride] + f1,
+                    Me[2 * NV + a * stride] + f2, ops, Fb, ab[a], fob, nb);
         for (int c2 = 0; c2 < 3; ++c2) {
           mb[a][c2] += nb[c2];
           nfb[c2] += nb[c2];
@@ -925,7 +963,8 @@ cudaError_t launch_vjp_n(nsfr_ctx* ctx, const double* u, const double* dbar, dou
   constexpr int NV = N * N * N;
   constexpr int epb = epb_for(N);
   const int grid = (ctx->ne + epb - 1) / epb;
-  size_t smem = (size_t)epb * 20 * NV * sizeof(double);
+  // per element: P, Rbar, record cotangents, Y (5 NV doubles each), then the node splits (NV PRF)
+  size_t smem = (size_t)epb * NV * (20 * sizeof(double) + sizeof(PRF));
   cudaError_t err =
       cudaFuncSetAttribute(vjp_volume_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
