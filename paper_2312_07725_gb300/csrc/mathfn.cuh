@@ -87,8 +87,8 @@ __device__ __forceinline__ double nsfr_exp(double x, const MathTables& T) {
   // difference of the bit patterns
   const float tn = __fmaf_rn(d2f_i(x), 0x1.715476p+5f, 12582912.0f);
   const int n = (int)__float_as_uint(tn) - 0x4b400000;
-  const double nd = i2d_i(n);
-  const double r = fma(-nd, NSFR_EXP_L2, fma(-nd, NSFR_EXP_L1, x));
+  const double ndn = i2d_i(-n);  // -n as a double, so that no FP64 negation is needed
+  const double r = fma(ndn, NSFR_EXP_L2, fma(ndn, NSFR_EXP_L1, x));
   const int j = n & 31, k = n >> 5;
   // q = 1/2 + r w, w = 1/6 + r z, z = 1/24 + r (1/120 + r/720): z, w and q in
   // float-float (their leading terms need more than FP32's 24 bits)

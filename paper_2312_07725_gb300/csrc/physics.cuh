@@ -96,11 +96,32 @@ __device__ __forceinline__ double rcp_full(double x) {
 
 // x 2^k (k small) by moving the exponent field: exact, and off the FP64 pipe.
 // Zero stays zero; a subnormal x (never a state quantity) takes the multiply.
+// (The rare path is a call, not inlined: inlined, the compiler evaluates its
+// multiply on every call and selects, which costs the FP64 operation this
+// avoids.)
+static __device__ __noinline__ double mul_pow2_slow(double x, double scale) { return x * scale; }
 template <int K>
 __device__ __forceinline__ double mul_pow2(double x) {
   const int hi = __double2hiint(x);
-  if ((hi & 0x7ff00000) == 0) return x * (K >= 0 ? (double)(1LL << K) : 1.0 / (double)(1LL << -K));
+  if ((hi & 0x7ff00000) == 0) {
+    if ((hi & 0x7fffffff) == 0 && __double2loint(x) == 0) return x;  // +-0
+    return mul_pow2_slow(x, K >= 0 ? (double)(1LL << K) : 1.0 / (double)(1LL << -K));
+  }
   return __hiloint2double(hi + K * (1 << 20), __double2loint(x));
+}
+
+// -x, and x with its sign flipped when neg, on the integer pipe (an FP64
+// negation that no FMA absorbs costs an FP64 addition)
+__device__ __forceinline__ double neg_i(double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+__device__ __forceinline__ double neg_if(double x, bool neg) {
+  return __hiloint2double(__double2hiint(x) ^ (neg ? (int)0x80000000 : 0), __double2loint(x));
+}
+// x > 0 (false for zero, negative and NaN), decided on the bit pattern
+__device__ __forceinline__ bool pos_i(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b <= 0x7ff0000000000000LL;
 }
 
 // u < NSFR_LM_EPS for u = f^2 >= 0, decided on the integer bit pattern

@@ -42,8 +42,10 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
   extern __shared__ double sm[];
   const int epb = blockDim.x / NL;
   const int e0 = blockIdx.x * epb;
-  const double g = ops.gamma, gm1 = g - 1.0;
+  const double g = ops.gamma, gm1 = g - 1.0, igm1 = ops.inv_gm1;
   const double ln2 = 0.69314718055994530942;
+  // constants of v_1 and of ln rho~ (below): (gamma + ln 2)/(gamma-1), -gamma/(gamma-1), -1/(gamma-1)
+  const double cv0 = (g + ln2) * igm1, ngig = -g * igm1, nigm1 = -igm1;
   const MathTables T = nsfr_stage_tables(sm + (size_t)epb * 5 * NV);
   __syncthreads();
   // v(u) at every node of the block's elements; the node records (rho, 2 beta,
@@ -53,20 +55,21 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
     if (e >= ne) continue;
     const double* ue = u + (size_t)e * 5 * NV + node;
     const double r = ue[0], m0 = ue[NV], m1 = ue[2 * NV], m2 = ue[3 * NV], E = ue[4 * NV];
+    // (negations by neg_i and the sign tests by pos_i run on the integer pipe)
     const double ir = rcp_ff(r);
     const double u0 = m0 * ir, u1 = m1 * ir, u2 = m2 * ir;
     const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
-    const double p = gm1 * fma(-0.5 * r, q2, E);
-    if (!(r > 0.0) || !(p > 0.0)) atomicOr(flag, 1);
+    const double p = gm1 * fma(neg_i(mul_pow2<-1>(r)), q2, E);
+    if (!pos_i(r) || !pos_i(p)) atomicOr(flag, 1);
     const double b2 = r * rcp_ff(p);  // 2 beta = rho / p
-    const double lr = nsfr_log(r, T), lp = nsfr_log(p, T);
-    const double s = lp - g * lr;
+    const double lr = nsfr_log(r, T), l2p = nsfr_log(mul_pow2<1>(p), T);
+    // v_1 = (gamma - s)/(gamma-1) - beta |u|^2 with s = ln p - gamma ln rho = ln 2p - ln 2 - gamma ln rho
     double* v = sm + (size_t)le * 5 * NV + node;
-    v[0] = fma(-mul_pow2<-1>(b2), q2, (g - s) * ops.inv_gm1);
+    v[0] = fma(neg_i(mul_pow2<-1>(b2)), q2, fma(igm1, fma(g, lr, neg_i(l2p)), cv0));
     v[NV] = b2 * u0;
     v[2 * NV] = b2 * u1;
     v[3 * NV] = b2 * u2;
-    v[4 * NV] = -b2;
+    v[4 * NV] = neg_i(b2);
     Rec a;
     a.r = r;
     a.b2 = b2;
@@ -75,7 +78,7 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
     a.u2 = mul_pow2<-1>(u2);
     a.qq = mul_pow2<-2>(q2);
     a.lr = lr;
-    a.lb = lr - lp - ln2;  // ln beta = ln rho - ln 2p
+    a.lb = lr - l2p;  // ln beta = ln rho - ln 2p
     store_rec(nrec + (size_t)e * NSFR_NFIELD * NV + node, NV, a);
   }
   __syncthreads();
@@ -101,14 +104,15 @@ __global__ void __launch_bounds__(threads_for(N)) face_state_kernel(const double
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const double* w = s ? vp : vm;
-    if (!(w[4] < 0.0)) atomicOr(flag, 1);
-    const double b2 = -w[4];                  // 2 beta
-    const double iv5 = -rcp_ff(b2);
-    const double u0 = -w[1] * iv5, u1 = -w[2] * iv5, u2 = -w[3] * iv5;
+    const double b2 = neg_i(w[4]);            // 2 beta = -v_5
+    if (!pos_i(b2)) atomicOr(flag, 1);
+    const double iv = rcp_ff(b2);
+    const double u0 = w[1] * iv, u1 = w[2] * iv, u2 = w[3] * iv;  // u = -v_{2..4} / v_5
     const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
-    const double sent = g - gm1 * fma(mul_pow2<-1>(b2), q2, w[0]);
     const double L5 = nsfr_log(b2, T);        // ln(2 beta)
-    const double lr = -(sent + L5) * ops.inv_gm1;  // s = (1-gamma) ln rho - ln(2 beta)
+    // s = gamma - (gamma-1)(v_1 + beta |u|^2) = (1-gamma) ln rho - ln(2 beta), so
+    // ln rho = (v_1 + beta |u|^2) - (gamma + ln(2 beta))/(gamma-1)
+    const double lr = fma(nigm1, L5, fma(mul_pow2<-1>(b2), q2, w[0] + ngig));
     Rec P;
     P.r = nsfr_exp(lr, T);
     P.b2 = b2;
@@ -348,7 +352,7 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
                                        Ph[(3 * a + 2) * NFP], ops,
                                        PtrLogs{Le + a * stride, NV}, PtrLogs{fo + P_LRHO * NFP, NFP}, F);
         const double ta = VF == NSFR_FLUX_RANOCHA ? t[a] : t[a] * fs;
-        const double swt = s ? ta : -ta;  // s t_a, the sign without a multiply
+        const double swt = neg_if(ta, !s);  // s t_a, the sign flipped on the integer pipe
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
           tphi[k] = fma(ta, F[k], tphi[k]);
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
       for (int k = 0; k < 5; ++k) tphi[k] = fsp[k * NFP] - tphi[k];
 #pragma unroll
       for (int a = 0; a < N; ++a) {
-        const double swt = s ? t[a] : -t[a];
+        const double swt = neg_if(t[a], !s);
 #pragma unroll
         for (int k = 0; k < 5; ++k) Rl[k * NV + a * stride] = fma(swt, tphi[k], Rl[k * NV + a * stride]);
       }
