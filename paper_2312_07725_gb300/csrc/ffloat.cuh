@@ -52,6 +52,20 @@ __device__ __forceinline__ ff ff_from_double(double x) {
 
 __device__ __forceinline__ double ff_to_double(ff a) { return f2d_i(a.hi) + f2d_i(a.lo); }
 
+// -x, and x with its sign flipped when neg, on the integer pipe (an FP64
+// negation that no FMA absorbs costs an FP64 addition)
+__device__ __forceinline__ double neg_i(double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+__device__ __forceinline__ double neg_if(double x, bool neg) {
+  return __hiloint2double(__double2hiint(x) ^ (neg ? (int)0x80000000 : 0), __double2loint(x));
+}
+// x > 0 (false for zero, negative and NaN), decided on the bit pattern
+__device__ __forceinline__ bool pos_i(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b <= 0x7ff0000000000000LL;
+}
+
 // x as hi + lo on the integer pipe (ff_from_double without its FP64
 // subtraction): hi the nearest float (d2f_i, ties away from zero), lo the
 // leading 24 bits of the remainder x - hi (truncated: x - hi - lo is below

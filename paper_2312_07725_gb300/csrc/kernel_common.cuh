@@ -1,6 +1,7 @@
 // Index helpers shared by the residual kernels.
 #pragma once
 
+#include "ffloat.cuh"
 #include "nsfr_internal.h"
 
 namespace nsfr_k {
@@ -149,9 +150,9 @@ __device__ void uncol_epilogue(double* X, double* Y, int nel, int e0, const OpsG
     if (epi == EPI_RAW) {
       out[off + t] = r;
     } else if (epi == EPI_DUDT) {
-      out[off + t] = -r;
+      out[off + t] = neg_i(r);
     } else {
-      const double k = -r;
+      const double k = neg_i(r);
       if (rk.last) {
         rk.unext[off + t] = fma(rk.b * rk.dt, k, rk.acc[off + t]);
       } else {

@@ -59,9 +59,14 @@ __device__ __forceinline__ MathTables nsfr_stage_tables(double* sm) {
   return MathTables{sm, sm + 128, sm + 256, sm + 384, sm + 416};
 }
 
+// the out-of-range arguments' path, a call rather than inlined code (inlined,
+// the compiler evaluates parts of it on every call and selects)
+static __device__ __noinline__ double nsfr_log_slow(double x) { return log(x); }
+static __device__ __noinline__ double nsfr_exp_slow(double x) { return exp(x); }
+
 __device__ __forceinline__ double nsfr_log(double x, const MathTables& T) {
   const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
-  if (hi - 0x00100000u >= 0x7fe00000u) return log(x);
+  if (hi - 0x00100000u >= 0x7fe00000u) return nsfr_log_slow(x);
   const int k = (int)(hi >> 20) - 1023;
   const int j = (int)((hi >> 13) & 127u);
   const double m = __hiloint2double((int)((hi & 0x000fffffu) | 0x3ff00000u), (int)lo);
@@ -82,7 +87,7 @@ __device__ __forceinline__ double nsfr_log(double x, const MathTables& T) {
 
 __device__ __forceinline__ double nsfr_exp(double x, const MathTables& T) {
   const unsigned int ahi = (unsigned int)__double2hiint(x) & 0x7fffffffu;
-  if (ahi >= 0x4085e000u) return exp(x);  // |x| >= 700, infinity, NaN
+  if (ahi >= 0x4085e000u) return nsfr_exp_slow(x);  // |x| >= 700, infinity, NaN
   // n = round(32 x / ln 2) in FP32: 1.5 2^23 fixes the binade, so n is the
   // difference of the bit patterns
   const float tn = __fmaf_rn(d2f_i(x), 0x1.715476p+5f, 12582912.0f);

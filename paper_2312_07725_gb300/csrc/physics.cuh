@@ -110,20 +110,6 @@ __device__ __forceinline__ double mul_pow2(double x) {
   return __hiloint2double(hi + K * (1 << 20), __double2loint(x));
 }
 
-// -x, and x with its sign flipped when neg, on the integer pipe (an FP64
-// negation that no FMA absorbs costs an FP64 addition)
-__device__ __forceinline__ double neg_i(double x) {
-  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
-}
-__device__ __forceinline__ double neg_if(double x, bool neg) {
-  return __hiloint2double(__double2hiint(x) ^ (neg ? (int)0x80000000 : 0), __double2loint(x));
-}
-// x > 0 (false for zero, negative and NaN), decided on the bit pattern
-__device__ __forceinline__ bool pos_i(double x) {
-  const long long b = __double_as_longlong(x);
-  return b > 0 && b <= 0x7ff0000000000000LL;
-}
-
 // u < NSFR_LM_EPS for u = f^2 >= 0, decided on the integer bit pattern
 __device__ __forceinline__ bool lm_small(double u) {
   return __double_as_longlong(u) < __double_as_longlong(NSFR_LM_EPS);
@@ -138,7 +124,7 @@ __device__ __forceinline__ double horner4(const double* c, double u) {
 struct RecF {
   ff r, b2;
 };
-__device__ __forceinline__ RecF recf_of(const Rec& a) { return RecF{ff_from_double(a.r), ff_from_double(a.b2)}; }
+__device__ __forceinline__ RecF recf_of(const Rec& a) { return RecF{ff_split_i(a.r), ff_split_i(a.b2)}; }
 
 __device__ __forceinline__ float rcp32(float x) {
   float r;
@@ -161,8 +147,9 @@ __device__ __forceinline__ ff ff_div_nn(ff a, ff b, float r) {
 // FP32 reciprocal of xf.hi: the float-float seed r + r (1 - xf r) (~2^-45),
 // joined on the integer pipe, and one FP64 Newton step -- two FP64
 // operations, to the accuracy of rcp_full's three.
+static __device__ __noinline__ double rcp_full_slow(double x) { return rcp_full(x); }
 __device__ __forceinline__ double rcp_from_ff(double x, ff xf, float r) {
-  if (!(xf.hi > 1.0e-37f && xf.hi < 1.0e37f)) return rcp_full(x);  // outside the FP32 seed's range
+  if (!(xf.hi > 1.0e-37f && xf.hi < 1.0e37f)) return rcp_full_slow(x);  // outside the FP32 seed's range (a call)
   const float e = __fmaf_rn(-xf.lo, r, __fmaf_rn(-xf.hi, r, 1.0f));
   const double r0 = ff_join_i(ff{r, __fmul_rn(r, e)});
   return fma(r0, fma(-x, r0, 1.0), r0);

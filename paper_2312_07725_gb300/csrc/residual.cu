@@ -267,8 +267,8 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
     const int le = t / NV, node = t % NV;
     double* pe = P + (size_t)le * 6 * NV + node;
     const double r = pe[P_RHO * NV], b2 = pe[P_B2 * NV];
-    Pf[(size_t)le * 2 * NV + node] = ff_from_double(r);
-    Pf[((size_t)le * 2 + 1) * NV + node] = ff_from_double(b2);
+    Pf[(size_t)le * 2 * NV + node] = ff_split_i(r);
+    Pf[((size_t)le * 2 + 1) * NV + node] = ff_split_i(b2);
     if (VF == NSFR_FLUX_RANOCHA) pe[P_QQ * NV] = r * rcp_full(b2);
   }
   __syncthreads();
@@ -411,11 +411,11 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
   if (epi == EPI_RAW) {
     for (int t = threadIdx.x; t < total; t += blockDim.x) out[off + t] = Rs[t];
   } else if (epi == EPI_DUDT) {
-    for (int t = threadIdx.x; t < total; t += blockDim.x) out[off + t] = -Rs[t];
+    for (int t = threadIdx.x; t < total; t += blockDim.x) out[off + t] = neg_i(Rs[t]);
   } else {
     const double bdt = rk.b * rk.dt, adt = rk.a_next * rk.dt;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const double k = -Rs[t];
+      const double k = neg_i(Rs[t]);  // (the negations on the integer pipe)
       if (rk.last) {
         rk.unext[off + t] = fma(bdt, k, rk.acc[off + t]);
       } else {

@@ -403,9 +403,9 @@ __device__ void uncol_epilogue_f(const double* Rd, float* X, float* Y, int nel, 
     if (epi == EPI_RAW) {
       out[off + t] = r;
     } else if (epi == EPI_DUDT) {
-      out[off + t] = -r;
+      out[off + t] = neg_i(r);
     } else {
-      const double k = -r;
+      const double k = neg_i(r);
       if (rk.last) {
         rk.unext[off + t] = fma(bdt, k, rk.acc[off + t]);
       } else {
@@ -688,11 +688,11 @@ __global__ void __launch_bounds__(bulk_threads(N, FF), bulk_ctas(N, FF))
     }
   }
   if (epi == EPI_DUDT) {
-    for (int t = threadIdx.x; t < total; t += blockDim.x) out[off + t] = -f2d_i(Xf[t]);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) out[off + t] = neg_i(f2d_i(Xf[t]));
   } else {
     const double bdt = rk.b * rk.dt, adt = rk.a_next * rk.dt;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const double k = -f2d_i(Xf[t]);
+      const double k = neg_i(f2d_i(Xf[t]));
       if (rk.last) {
         rk.unext[off + t] = fma(bdt, k, rk.acc[off + t]);
       } else {

@@ -247,10 +247,10 @@ __device__ __forceinline__ PR pr_from_face(const double* f, int nfp) {
   const Rec R = load_rec(f, nfp);
   PR a;
   a.r = R.r;
-  a.u0 = 2.0 * R.u0;
-  a.u1 = 2.0 * R.u1;
-  a.u2 = 2.0 * R.u2;
-  a.b = 0.5 * R.b2;
+  a.u0 = mul_pow2<1>(R.u0);
+  a.u1 = mul_pow2<1>(R.u1);
+  a.u2 = mul_pow2<1>(R.u2);
+  a.b = mul_pow2<-1>(R.b2);
   return a;
 }
 
@@ -293,10 +293,10 @@ __global__ void __launch_bounds__(threads_for(N), 1)
       const double* rec = nrec + (size_t)(e0 + le) * NSFR_NFIELD * NV + node;
       double* p = P + (size_t)le * 5 * NV + node;
       p[0] = rec[P_RHO * NV];
-      p[NV] = 2.0 * rec[P_UH * NV];
-      p[2 * NV] = 2.0 * rec[(P_UH + 1) * NV];
-      p[3 * NV] = 2.0 * rec[(P_UH + 2) * NV];
-      p[4 * NV] = 0.5 * rec[P_B2 * NV];
+      p[NV] = mul_pow2<1>(rec[P_UH * NV]);
+      p[2 * NV] = mul_pow2<1>(rec[(P_UH + 1) * NV]);
+      p[3 * NV] = mul_pow2<1>(rec[(P_UH + 2) * NV]);
+      p[4 * NV] = mul_pow2<-1>(rec[P_B2 * NV]);
     }
     for (int t = threadIdx.x; t < nel * 5 * nsv; t += blockDim.x)
       Y[(size_t)(t / nsv) * NV + t % nsv] = -rbar[(size_t)e0 * 5 * nsv + t];
