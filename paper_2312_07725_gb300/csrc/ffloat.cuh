@@ -26,7 +26,10 @@ __device__ __forceinline__ float d2f_i(double x) {
   unsigned int f = (unsigned int)(r >> 29) + 0x40000000u;
   f = ahi < (897u << 20) ? 0u : f;
   f = ahi >= (1151u << 20) ? 0x7f800000u : f;
-  f = (b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull ? 0x7fc00000u : f;
+  // NaN, tested on the two 32-bit words (the compiler turns the same test on the
+  // 64-bit pattern into an FP64 instruction)
+  const unsigned int bh = (unsigned int)(b >> 32) & 0x7fffffffu, bl = (unsigned int)b;
+  f = (bh > 0x7ff00000u) | ((bh == 0x7ff00000u) & (bl != 0u)) ? 0x7fc00000u : f;
   return __uint_as_float(f | sign);
 }
 
