@@ -258,7 +258,7 @@ __device__ __forceinline__ PR pr_from_face(const double* f, int nfp) {
 // volume reverse: one thread per line, like volume_kernel
 // --------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(threads_for(N), 1)
+__global__ void __launch_bounds__(threads_for(N), 2)
     vjp_volume_kernel(const double* __restrict__ u, const double* __restrict__ rbar, const double* __restrict__ Rfwd,
                       const double* __restrict__ metric, const double* __restrict__ nf_plus,
                       const double* __restrict__ face, const double* __restrict__ wj, OpsGL ops, int nx, int ny,
