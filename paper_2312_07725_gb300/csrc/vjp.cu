@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(threads_for(N), 2)
 // face reverse: face-state cotangents -> volume state cotangents
 // --------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(threads_for(N), 1)
+__global__ void __launch_bounds__(threads_for(N), 2)
     vjp_face_kernel(const double* __restrict__ u, const double* __restrict__ fbar_own,
                     const double* __restrict__ fbar_nbr, OpsGL ops, int nx, int ny, int nz, int ne,
                     double* __restrict__ ubar) {
