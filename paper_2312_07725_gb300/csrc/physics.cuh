@@ -253,75 +253,22 @@ struct PtrLogs {
   __device__ __forceinline__ double b2() const { return p[(P_B2 - P_LRHO) * off]; }
 };
 
-// F = f_s(A, B) . n, n the averaged metric row (n0, n1, n2).
-//   rho_ln = (rho_a + rho_b) Gh(u_r),        1/(2(gamma-1) beta_ln) = F4g(u_b) / (2 beta_a + 2 beta_b)
-//   p_hat  = (rho_a + rho_b) / (2 beta_a + 2 beta_b)
-//   F_rho = rho_ln u.n,  F_m = F_rho u + p_hat n,  F_E = F_rho (1/(2(gamma-1) beta_ln) - |u|^2_bar/2) + u.F_m
-template <class LA, class LB>
-__device__ __forceinline__ void ec_flux_l(const Rec& A, const Rec& B, double n0, double n1, double n2,
-                                          const OpsGL& K, const LA& la, const LB& lb, double F[5]) {
-  const double sr = A.r + B.r, dr = A.r - B.r;
-  const double s2 = A.b2 + B.b2, d2 = A.b2 - B.b2;
-  const double rb2 = rcp_full(s2);
-  const double rr = rcp_newton1(sr);  // only enters f^2, a correction below 1e-4
-  const double fr = dr * rr, fb = d2 * rb2;
-  const double ur = fr * fr, ub = fb * fb;
-  // h = 1/(2(gamma-1) beta_ln) - |u|^2_bar/2; on the series branch one FMA forms it
-  const double qs = A.qq + B.qq;
-  double rln, h;
-  if (lm_small(ur)) rln = sr * horner4(K.gh, ur);
-  else rln = dr / (la.lr() - lb.lr());
-  if (lm_small(ub)) h = fma(horner4(K.f4g, ub), rb2, -qs);
-  else h = K.inv_gm1 * (la.lb() - lb.lb()) / d2 - qs;
-  const double ph = sr * rb2;
-  const double v0 = A.u0 + B.u0, v1 = A.u1 + B.u1, v2 = A.u2 + B.u2;  // u_bar
-  const double un = fma(v0, n0, fma(v1, n1, v2 * n2));
-  const double Fr = rln * un;
-  F[0] = Fr;
-  F[1] = fma(Fr, v0, ph * n0);
-  F[2] = fma(Fr, v1, ph * n1);
-  F[3] = fma(Fr, v2, ph * n2);
-  F[4] = fma(v2, F[3], fma(v1, F[2], fma(v0, F[1], Fr * h)));
-}
-
-// The same flux divided by s = rho_a + rho_b, returned with s: every component
-// carries that factor (rho_ln = s G(u_r), p_hat = s / (2 beta_a + 2 beta_b), and
-// F_E is linear in both), so a caller that accumulates w F folds s into the
-// weight and saves the two products by s.  Off the series branch rho_ln / s
-// is dr / ((ln rho_a - ln rho_b) s).
-template <class LA, class LB>
-__device__ __forceinline__ double ec_flux_over_sr(const Rec& A, const Rec& B, double n0, double n1, double n2,
-                                                  const OpsGL& K, const LA& la, const LB& lb, double F[5]) {
-  const double sr = A.r + B.r, dr = A.r - B.r;
-  const double s2 = A.b2 + B.b2, d2 = A.b2 - B.b2;
-  const double rb2 = rcp_full(s2);
-  const double rr = rcp_newton1(sr);  // only enters f^2, a correction below 1e-4
-  const double fr = dr * rr, fb = d2 * rb2;
-  const double ur = fr * fr, ub = fb * fb;
-  const double qs = A.qq + B.qq;
-  double gr, h;
-  if (lm_small(ur)) gr = horner4(K.gh, ur);
-  else gr = dr / ((la.lr() - lb.lr()) * sr);
-  if (lm_small(ub)) h = fma(horner4(K.f4g, ub), rb2, -qs);
-  else h = K.inv_gm1 * (la.lb() - lb.lb()) / d2 - qs;
-  const double v0 = A.u0 + B.u0, v1 = A.u1 + B.u1, v2 = A.u2 + B.u2;  // u_bar
-  const double un = fma(v0, n0, fma(v1, n1, v2 * n2));
-  const double Fr = gr * un;
-  F[0] = Fr;
-  F[1] = fma(Fr, v0, rb2 * n0);
-  F[2] = fma(Fr, v1, rb2 * n1);
-  F[3] = fma(Fr, v2, rb2 * n2);
-  F[4] = fma(v2, F[3], fma(v1, F[2], fma(v0, F[1], Fr * h)));
-  return sr;
-}
-
-// ec_flux_over_sr with the log means' series branch on the FP32 pipe
-// (lm_series_ff, from the float-float rho and 2 beta of the two nodes): there
+// Chandrashekar's flux, F = f_s(A, B) . n, n the averaged metric row (n0, n1, n2):
+//   rho_ln = (rho_a + rho_b) Gh(u_r),   1/(2(gamma-1) beta_ln) = F4g(u_b) / (2 beta_a + 2 beta_b),
+//   p_hat  = (rho_a + rho_b) / (2 beta_a + 2 beta_b),
+//   F_rho = rho_ln u.n,  F_m = F_rho u + p_hat n,  F_E = F_rho (1/(2(gamma-1) beta_ln) - |u|^2_bar/2) + u.F_m,
+// with the log means' series branch on the FP32 pipe (lm_series_ff, from the
+// float-float rho and 2 beta of the two nodes).  ec_flux_over_sr_ff returns
+// the flux divided by s = rho_a + rho_b, and s: every component carries that
+// factor (rho_ln = s G(u_r), p_hat = s / (2 beta_a + 2 beta_b), and F_E is
+// linear in both), so a caller that accumulates w F folds s into the weight
+// and saves the two products by s.  On the series branch
 //   F_rho / s = Gh(u_r) u.n = (u.n / 2) (1 + eps_r),
 //   h = F4g(u_b) / s2 - qs = (F4g(0) + eps_b) / s2 - qs,
-// and the FP64 work left is the sums, 1/s2, the two joins of eps and the flux.
-// The differences rho_a - rho_b and 2 beta_a - 2 beta_b are formed in FP64 on
-// the log branch only.
+// and the FP64 work left is the sums, 1/s2, the FMAs that add the eps and the
+// flux; off it rho_ln / s = (rho_a - rho_b) / ((ln rho_a - ln rho_b) s), and
+// the differences rho_a - rho_b and 2 beta_a - 2 beta_b are formed in FP64 on
+// that branch only.
 template <class LA, class LB>
 __device__ __forceinline__ double ec_flux_over_sr_ff(const Rec& A, const Rec& B, const RecF& Af, const RecF& Bf,
                                                      double n0, double n1, double n2, const OpsGL& K, const LA& la,
@@ -352,8 +299,7 @@ __device__ __forceinline__ double ec_flux_over_sr_ff(const Rec& A, const Rec& B,
   return sr;
 }
 
-// ec_flux_l with the log means' series branch on the FP32 pipe (the flux
-// itself, not divided by s): rho_ln = (s/2)(1 + eps_r).
+// The same flux itself, not divided by s: rho_ln = (s/2)(1 + eps_r).
 template <class LA, class LB>
 __device__ __forceinline__ void ec_flux_ff(const Rec& A, const Rec& B, const RecF& Af, const RecF& Bf, double n0,
                                            double n1, double n2, const OpsGL& K, const LA& la, const LB& lb,
@@ -387,11 +333,6 @@ __device__ __forceinline__ void ec_flux_ff(const Rec& A, const Rec& B, const Rec
 
 __device__ __forceinline__ RecF recf_split(const Rec& a) { return RecF{ff_split_i(a.r), ff_split_i(a.b2)}; }
 
-__device__ __forceinline__ void ec_flux(const Rec& A, const Rec& B, double n0, double n1, double n2,
-                                        const OpsGL& K, double F[5]) {
-  ec_flux_l(A, B, n0, n1, n2, K, RecLogs{A}, RecLogs{B}, F);
-}
-
 // Chandrashekar's flux with Ranocha's pressure terms (Sec. "Results": the EC
 // runs use Chandrashekar's flux with Ranocha's pressure fix), F = f_s(A, B) . n:
 // the same mass flux and internal-energy term, the arithmetic pressure mean in
@@ -400,37 +341,8 @@ __device__ __forceinline__ void ec_flux(const Rec& A, const Rec& B, double n0, d
 //   F_E = F_rho (1/(2(gamma-1) beta_ln) + u_a . u_b / 2) + (p_a u_b.n + p_b u_a.n)/2.
 // pa, pb are the two pressures (rho / (2 beta)); with the half velocities h of
 // the records u_a . u_b / 2 = 2 h_a . h_b and u_b . n / 2 = u_bar . n - h_a . n.
-template <class LA, class LB>
-__device__ __forceinline__ void ranocha_flux_l(const Rec& A, const Rec& B, double pa, double pb, double n0,
-                                               double n1, double n2, const OpsGL& K, const LA& la, const LB& lb,
-                                               double F[5]) {
-  const double sr = A.r + B.r, dr = A.r - B.r;
-  const double s2 = A.b2 + B.b2, d2 = A.b2 - B.b2;
-  const double rb2 = rcp_full(s2);
-  const double rr = rcp_newton1(sr);
-  const double fr = dr * rr, fb = d2 * rb2;
-  const double ur = fr * fr, ub = fb * fb;
-  double rln, ibg;
-  if (lm_small(ur)) rln = sr * horner4(K.gh, ur);
-  else rln = dr / (la.lr() - lb.lr());
-  if (lm_small(ub)) ibg = horner4(K.f4g, ub) * rb2;
-  else ibg = K.inv_gm1 * (la.lb() - lb.lb()) / d2;
-  const double v0 = A.u0 + B.u0, v1 = A.u1 + B.u1, v2 = A.u2 + B.u2;  // u_bar
-  const double un = fma(v0, n0, fma(v1, n1, v2 * n2));
-  const double an = fma(A.u0, n0, fma(A.u1, n1, A.u2 * n2));     // u_a . n / 2
-  const double hab = fma(A.u0, B.u0, fma(A.u1, B.u1, A.u2 * B.u2));  // u_a . u_b / 4
-  const double Fr = rln * un;
-  const double pm = 0.5 * (pa + pb);
-  F[0] = Fr;
-  F[1] = fma(Fr, v0, pm * n0);
-  F[2] = fma(Fr, v1, pm * n1);
-  F[3] = fma(Fr, v2, pm * n2);
-  F[4] = fma(Fr, fma(2.0, hab, ibg), fma(pa, un - an, pb * an));
-}
-
-// ranocha_flux_l with the log means' series branch on the FP32 pipe, as in
-// ec_flux_over_sr_ff: rho_ln = (s/2)(1 + eps_r), 1/(2(gamma-1) beta_ln) =
-// (F4g(0) + eps_b) / s2.
+// The log means' series branch runs on the FP32 pipe, as in ec_flux_over_sr_ff:
+// rho_ln = (s/2)(1 + eps_r), 1/(2(gamma-1) beta_ln) = (F4g(0) + eps_b) / s2.
 template <class LA, class LB>
 __device__ __forceinline__ void ranocha_flux_ff(const Rec& A, const Rec& B, const RecF& Af, const RecF& Bf,
                                                 double pa, double pb, double n0, double n1, double n2,
