@@ -21,18 +21,20 @@
 namespace {
 using namespace nsfr_k;
 
-// the record of u(w), w entropy variables (the face-state conversion); flags
-// 2 beta <= 0 or NaN
-__device__ __forceinline__ Rec rec_from_entropy(const double w[5], const OpsGL& ops, const MathTables& T, int* flag) {
-  const double g = ops.gamma, gm1 = g - 1.0, ln2 = 0.69314718055994530942;
-  if (!(w[4] < 0.0)) atomicOr(flag, 1);
-  const double b2 = -w[4];
-  const double iv5 = rcp_full(w[4]);
-  const double u0 = -w[1] * iv5, u1 = -w[2] * iv5, u2 = -w[3] * iv5;
+// the record of u(w), w entropy variables (the face-state conversion, with its
+// constants ngig = -gamma/(gamma-1), nigm1 = -1/(gamma-1)); flags 2 beta <= 0 or
+// NaN.  As in the face-state kernel: ln rho = (w_1 + beta |u|^2) - (gamma +
+// ln(2 beta))/(gamma-1), the negations and the sign test on the integer pipe.
+__device__ __forceinline__ Rec rec_from_entropy(const double w[5], double ngig, double nigm1, const MathTables& T,
+                                                int* flag) {
+  const double ln2 = 0.69314718055994530942;
+  const double b2 = neg_i(w[4]);
+  if (!pos_i(b2)) atomicOr(flag, 1);
+  const double iv = rcp_ff(b2);
+  const double u0 = w[1] * iv, u1 = w[2] * iv, u2 = w[3] * iv;  // u = -w_{2..4} / w_5
   const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
-  const double sent = g - gm1 * fma(mul_pow2<-1>(b2), q2, w[0]);
   const double L5 = nsfr_log(b2, T);
-  const double lr = -(sent + L5) * ops.inv_gm1;
+  const double lr = fma(nigm1, L5, fma(mul_pow2<-1>(b2), q2, w[0] + ngig));
   Rec P;
   P.r = nsfr_exp(lr, T);
   P.b2 = b2;
@@ -61,7 +63,8 @@ __global__ void __launch_bounds__(256) projection_kernel(const double* __restric
   double* T1 = Vq + EPB * SL;
   double* T2 = T1 + EPB * SL;
   const MathTables T = nsfr_stage_tables(T2 + EPB * SL);
-  const double g = ops.gamma, gm1 = g - 1.0;
+  const double g = ops.gamma, gm1 = g - 1.0, igm1 = ops.inv_gm1, ln2 = 0.69314718055994530942;
+  const double cv0 = (g + ln2) * igm1, ngig = -g * igm1, nigm1 = -igm1;
   for (int t = threadIdx.x; t < nsl * nsv; t += blockDim.x)
     Us[(size_t)(t / nsv) * NV + t % nsv] = u[(size_t)e0 * 5 * nsv + t];
   __syncthreads();
@@ -73,18 +76,19 @@ __global__ void __launch_bounds__(256) projection_kernel(const double* __restric
   for (int t = threadIdx.x; t < nel * NV; t += blockDim.x) {
     double* v = Vq + (size_t)(t / NV) * SL + t % NV;
     const double r = v[0], m0 = v[NV], m1 = v[2 * NV], m2 = v[3 * NV], E = v[4 * NV];
-    const double ir = rcp_full(r);
+    const double ir = rcp_ff(r);
     const double u0 = m0 * ir, u1 = m1 * ir, u2 = m2 * ir;
     const double q2 = fma(u0, u0, fma(u1, u1, u2 * u2));
-    const double p = gm1 * fma(-0.5 * r, q2, E);
-    if (!(r > 0.0) || !(p > 0.0)) atomicOr(flag, 1);
-    const double b2 = r * rcp_full(p);  // 2 beta
-    const double s = nsfr_log(p, T) - g * nsfr_log(r, T);
-    v[0] = fma(-mul_pow2<-1>(b2), q2, (g - s) * ops.inv_gm1);
+    const double p = gm1 * fma(neg_i(mul_pow2<-1>(r)), q2, E);
+    if (!pos_i(r) || !pos_i(p)) atomicOr(flag, 1);
+    const double b2 = r * rcp_ff(p);  // 2 beta
+    // v_1 = (gamma - s)/(gamma-1) - beta |u|^2, s = ln 2p - ln 2 - gamma ln rho
+    v[0] = fma(neg_i(mul_pow2<-1>(b2)), q2,
+               fma(igm1, fma(g, nsfr_log(r, T), neg_i(nsfr_log(mul_pow2<1>(p), T))), cv0));
     v[NV] = b2 * u0;
     v[2 * NV] = b2 * u1;
     v[3 * NV] = b2 * u2;
-    v[4 * NV] = -b2;
+    v[4 * NV] = neg_i(b2);
   }
   __syncthreads();
   // v~^ = Pi v(u_q), into Us
@@ -99,7 +103,7 @@ __global__ void __launch_bounds__(256) projection_kernel(const double* __restric
     const int le = t / NV, node = t % NV;
     const double* v = Vq + (size_t)le * SL + node;
     const double w[5] = {v[0], v[NV], v[2 * NV], v[3 * NV], v[4 * NV]};
-    store_rec(nrec + (size_t)(e0 + le) * NSFR_NFIELD * NV + node, NV, rec_from_entropy(w, ops, T, flag));
+    store_rec(nrec + (size_t)(e0 + le) * NSFR_NFIELD * NV + node, NV, rec_from_entropy(w, ngig, nigm1, T, flag));
   }
   __syncthreads();
   // faces: l_s along d (to extent 1), then chi along the two face directions
@@ -122,7 +126,7 @@ __global__ void __launch_bounds__(256) projection_kernel(const double* __restric
         const double* v = Vq + (size_t)le * SL + fn;
         const double w[5] = {v[0], v[NV], v[2 * NV], v[3 * NV], v[4 * NV]};
         store_rec(face + (((size_t)(e0 + le) * 6 + 2 * d + s) * NSFR_NFIELD) * NFP + fn, NFP,
-                  rec_from_entropy(w, ops, T, flag));
+                  rec_from_entropy(w, ngig, nigm1, T, flag));
       }
       __syncthreads();
     }

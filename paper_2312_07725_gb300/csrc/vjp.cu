@@ -132,13 +132,13 @@ __device__ __forceinline__ void ec_flux_vjp(const PR& A, const PR& B, const PRF&
 __device__ __forceinline__ PR pr_from_conserved(const double* U, int stride, double gamma) {
   PR a;
   a.r = U[0];
-  const double ir = rcp_full(a.r);
+  const double ir = rcp_ff(a.r);
   a.u0 = U[stride] * ir;
   a.u1 = U[2 * stride] * ir;
   a.u2 = U[3 * stride] * ir;
   const double q2 = a.u0 * a.u0 + a.u1 * a.u1 + a.u2 * a.u2;
-  const double p = (gamma - 1.0) * (U[4 * stride] - 0.5 * a.r * q2);
-  a.b = 0.5 * a.r * rcp_full(p);
+  const double p = (gamma - 1.0) * (U[4 * stride] - mul_pow2<-1>(a.r) * q2);
+  a.b = mul_pow2<-1>(a.r) * rcp_ff(p);
   return a;
 }
 
@@ -147,7 +147,7 @@ __device__ __forceinline__ void conserved_bar(const PR& a, double gamma, const P
                                               double Ub[5]) {
   // p = rho / (2 beta): 1/(2p) = beta/rho, beta/p = 2 beta^2/rho
   const double q2 = a.u0 * a.u0 + a.u1 * a.u1 + a.u2 * a.u2;
-  const double ir = rcp_full(a.r);
+  const double ir = rcp_ff(a.r);
   double rb = pb.r + pb.b * a.b * ir;
   const double pbar = pbar_direct - 2.0 * pb.b * a.b * a.b * ir;
   // p = (gamma-1)(E - |m|^2/(2 rho))
@@ -167,22 +167,24 @@ __device__ __forceinline__ void conserved_bar(const PR& a, double gamma, const P
   Ub[4] = Eb;
 }
 
-__device__ __forceinline__ void entropy_vars(const PR& a, double gamma, double v[5]) {
+// (igm1 = 1/(gamma-1); the exact doublings and halvings are exponent adds)
+__device__ __forceinline__ void entropy_vars(const PR& a, double gamma, double igm1, double v[5]) {
   const double q2 = a.u0 * a.u0 + a.u1 * a.u1 + a.u2 * a.u2;
-  const double p = 0.5 * a.r * rcp_full(a.b);
+  const double p = mul_pow2<-1>(a.r) * rcp_ff(a.b);
   const double s = nsfr_log(p) - gamma * nsfr_log(a.r);
-  v[0] = (gamma - s) * rcp_full(gamma - 1.0) - a.b * q2;
-  v[1] = 2.0 * a.b * a.u0;
-  v[2] = 2.0 * a.b * a.u1;
-  v[3] = 2.0 * a.b * a.u2;
-  v[4] = -2.0 * a.b;
+  const double b2 = mul_pow2<1>(a.b);
+  v[0] = (gamma - s) * igm1 - a.b * q2;
+  v[1] = b2 * a.u0;
+  v[2] = b2 * a.u1;
+  v[3] = b2 * a.u2;
+  v[4] = neg_i(b2);
 }
 
 // face state from entropy variables (forward) as a primitive record
-__device__ __forceinline__ PR pr_from_entropy(const double v[5], double gamma) {
+__device__ __forceinline__ PR pr_from_entropy(const double v[5], double gamma, double igm1) {
   PR a;
-  const double v5 = v[4], iv5 = rcp_full(v5), igm1 = rcp_full(gamma - 1.0);
-  a.b = -0.5 * v5;
+  const double v5 = v[4], iv5 = rcp_full(v5);
+  a.b = neg_i(mul_pow2<-1>(v5));
   a.u0 = -v[1] * iv5;
   a.u1 = -v[2] * iv5;
   a.u2 = -v[3] * iv5;
@@ -193,9 +195,9 @@ __device__ __forceinline__ PR pr_from_entropy(const double v[5], double gamma) {
 }
 
 // reverse of pr_from_entropy: (rho, u, beta) cotangent -> v cotangent
-__device__ __forceinline__ void entropy_bar_from_pr(const double v[5], const PR& a, double gamma, const PR& pb,
-                                                    double vb[5]) {
-  const double v5 = v[4], iv5 = rcp_full(v5), iv52 = iv5 * iv5, igm1 = rcp_full(gamma - 1.0);
+__device__ __forceinline__ void entropy_bar_from_pr(const double v[5], const PR& a, double gamma, double igm1,
+                                                    const PR& pb, double vb[5]) {
+  const double v5 = v[4], iv5 = rcp_full(v5), iv52 = iv5 * iv5;
   const double vm2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
   vb[0] = 0.0;
   vb[1] = vb[2] = vb[3] = 0.0;
@@ -212,10 +214,10 @@ __device__ __forceinline__ void entropy_bar_from_pr(const double v[5], const PR&
 }
 
 // reverse of entropy_vars: v cotangent -> (rho, u, beta) cotangent and direct p cotangent
-__device__ __forceinline__ void pr_bar_from_entropy_bar(const PR& a, double gamma, const double vb[5], PR& pb,
-                                                        double& pbar) {
+__device__ __forceinline__ void pr_bar_from_entropy_bar(const PR& a, double gamma, double igm1, const double vb[5],
+                                                        PR& pb, double& pbar) {
   const double q2 = a.u0 * a.u0 + a.u1 * a.u1 + a.u2 * a.u2;
-  const double ir = rcp_full(a.r);  // 1/p = 2 beta / rho
+  const double ir = rcp_ff(a.r);  // 1/p = 2 beta / rho
   const double u[3] = {a.u0, a.u1, a.u2};
   double bb = -2.0 * vb[4] - vb[0] * q2;
   double ubv[3];
@@ -223,7 +225,7 @@ __device__ __forceinline__ void pr_bar_from_entropy_bar(const PR& a, double gamm
     bb += 2.0 * vb[1 + c] * u[c];
     ubv[c] = 2.0 * a.b * vb[1 + c] - 2.0 * a.b * u[c] * vb[0];
   }
-  const double sb = -vb[0] * rcp_full(gamma - 1.0);
+  const double sb = -vb[0] * igm1;
   pbar = 2.0 * sb * a.b * ir;
   pb.r = -gamma * sb * ir;
   pb.u0 = ubv[0];
@@ -524,7 +526,7 @@ __global__ void __launch_bounds__(threads_for(N), 2)
     const int le = t / NV, node = t % NV;
     const PR a = pr_from_conserved(u + (size_t)(e0 + le) * 5 * NV + node, NV, g);
     double v[5];
-    entropy_vars(a, g, v);
+    entropy_vars(a, g, ops.inv_gm1, v);
     for (int k = 0; k < 5; ++k) V[(size_t)(le * 5 + k) * NV + node] = v[k];
   }
   __syncthreads();
@@ -548,13 +550,13 @@ __global__ void __launch_bounds__(threads_for(N), 2)
         for (int a = 0; a < N; ++a) x += t[a] * Ve[k * NV + a * stride];
         vf[k] = x;
       }
-      const PR fa = pr_from_entropy(vf, g);
+      const PR fa = pr_from_entropy(vf, g, ops.inv_gm1);
       const double* o = fbar_own + (((size_t)e * 6 + f) * 5) * NFP + line;
       const double* q = fbar_nbr + (((size_t)enb * 6 + 2 * d + 1 - s) * 5) * NFP + line;
       const PR pb{o[0] + q[0], o[NFP] + q[NFP], o[2 * NFP] + q[2 * NFP], o[3 * NFP] + q[3 * NFP],
                   o[4 * NFP] + q[4 * NFP]};
       double vfb[5];
-      entropy_bar_from_pr(vf, fa, g, pb, vfb);
+      entropy_bar_from_pr(vf, fa, g, ops.inv_gm1, pb, vfb);
       for (int a = 0; a < N; ++a)
         for (int k = 0; k < 5; ++k) vbl[a][k] += t[a] * vfb[k];
     }
@@ -577,7 +579,7 @@ __global__ void __launch_bounds__(threads_for(N), 2)
     for (int k = 0; k < 5; ++k) vb[k] = Vb[(size_t)(lq * 5 + k) * NV + node];
     PR pb;
     double pbar;
-    pr_bar_from_entropy_bar(a, g, vb, pb, pbar);
+    pr_bar_from_entropy_bar(a, g, ops.inv_gm1, vb, pb, pbar);
     double Ub[5];
     conserved_bar(a, g, pb, pbar, Ub);
     double* ub = ubar + (size_t)(e0 + lq) * 5 * NV + node;
@@ -630,7 +632,7 @@ __global__ void __launch_bounds__(256) vjp_projection_kernel(const double* __res
     for (int t = threadIdx.x; t < NV; t += blockDim.x) {
       const PR a = pr_from_conserved(B1 + t, NV, g);
       double v[5];
-      entropy_vars(a, g, v);
+      entropy_vars(a, g, ops.inv_gm1, v);
       for (int k = 0; k < 5; ++k) B2[k * NV + t] = v[k];
     }
     __syncthreads();
@@ -644,10 +646,10 @@ __global__ void __launch_bounds__(256) vjp_projection_kernel(const double* __res
     for (int t = threadIdx.x; t < NV; t += blockDim.x) {
       double w[5], wb[5];
       for (int k = 0; k < 5; ++k) w[k] = B4[k * NV + t];
-      const PR a = pr_from_entropy(w, g);
+      const PR a = pr_from_entropy(w, g, ops.inv_gm1);
       const double* q = pbq + (size_t)e * 5 * NV + t;
       const PR pb{q[0], q[NV], q[2 * NV], q[3 * NV], q[4 * NV]};
-      entropy_bar_from_pr(w, a, g, pb, wb);
+      entropy_bar_from_pr(w, a, g, ops.inv_gm1, pb, wb);
       for (int k = 0; k < 5; ++k) B5[k * NV + t] = wb[k];
     }
     __syncthreads();
@@ -693,12 +695,12 @@ __global__ void __launch_bounds__(256) vjp_projection_kernel(const double* __res
           for (int c = 0; c < ns; ++c) acc = fma(ops.chi[j * ns + c], mid[(k * N + i) * ns + c], acc);
           w[k] = acc;
         }
-        const PR a = pr_from_entropy(w, g);
+        const PR a = pr_from_entropy(w, g, ops.inv_gm1);
         const double* o = fbar_own + (((size_t)e * 6 + f) * 5) * NFP + t;
         const double* q = fbar_nbr + (((size_t)enb * 6 + 2 * d + 1 - side) * 5) * NFP + t;
         const PR pb{o[0] + q[0], o[NFP] + q[NFP], o[2 * NFP] + q[2 * NFP], o[3 * NFP] + q[3 * NFP],
                     o[4 * NFP] + q[4 * NFP]};
-        entropy_bar_from_pr(w, a, g, pb, wb);
+        entropy_bar_from_pr(w, a, g, ops.inv_gm1, pb, wb);
         for (int k = 0; k < 5; ++k) B2[k * NFP + t] = wb[k];
       }
       __syncthreads();
@@ -735,7 +737,7 @@ __global__ void __launch_bounds__(256) vjp_projection_kernel(const double* __res
       for (int k = 0; k < 5; ++k) vb[k] = B2[k * NV + t];
       PR pb;
       double pbar;
-      pr_bar_from_entropy_bar(a, g, vb, pb, pbar);
+      pr_bar_from_entropy_bar(a, g, ops.inv_gm1, vb, pb, pbar);
       conserved_bar(a, g, pb, pbar, Ub);
       for (int k = 0; k < 5; ++k) B4[k * NV + t] = Ub[k];
     }
