@@ -404,6 +404,13 @@ nsfr_status nsfr_residual_static(const double* u, const double* C, const double*
  *                u = ((x-1)/(x+1))^2 < 1e-4 the series of f/atanh(f) in u,
  *                its terms beyond the constant in float-float, plus one FP64
  *                FMA (about one ulp); else (x - 1) / ln x in FP64
+ *   NSFR_FN_SPLIT the integer-pipe split of x into two floats: hi the
+ *                nearest float (ties away from zero), lo the leading 24 bits
+ *                of x - hi (truncated), returned packed as NSFR_FN_JOIN
+ *                takes them (hi in the high 32 bits); for normal x with
+ *                2^-100 < |x| < 2^100
+ *   NSFR_FN_I2D  the integer-pipe conversion of the int in the low 32 bits of
+ *                x to a double (exact)
  * The kernels compute the entropy variables, face states and two-point
  * fluxes with these.  x and y are device buffers of n doubles (n >= 0; they
  * may alias); asynchronous on the stream.  NSFR_ERR_ARG for an unknown fn, a
@@ -417,7 +424,9 @@ typedef enum {
   NSFR_FN_LOG_FF = 4,
   NSFR_FN_EXP_FF = 5,
   NSFR_FN_JOIN = 6,
-  NSFR_FN_LOGMEAN1 = 7
+  NSFR_FN_LOGMEAN1 = 7,
+  NSFR_FN_SPLIT = 8,
+  NSFR_FN_I2D = 9
 } nsfr_fn;
 nsfr_status nsfr_math_eval(int fn, const double* x, double* y, long long n, void* stream);
 

@@ -708,7 +708,7 @@ nsfr_status nsfr_profile_read(nsfr_ctx* ctx, double* ms, long long* count) {
 }
 
 nsfr_status nsfr_math_eval(int fn, const double* x, double* y, long long n, void* stream) {
-  if (fn < NSFR_FN_LOG || fn > NSFR_FN_LOGMEAN1 || n < 0) return NSFR_ERR_ARG;
+  if (fn < NSFR_FN_LOG || fn > NSFR_FN_I2D || n < 0) return NSFR_ERR_ARG;
   if (n == 0) return NSFR_OK;
   if (!x || !y || !is_device_ptr(x) || !is_device_ptr(y)) return NSFR_ERR_ARG;
   return nsfr_launch_math_eval(fn, x, y, n, (cudaStream_t)stream) == cudaSuccess ? NSFR_OK : NSFR_ERR_CUDA;

@@ -1,8 +1,8 @@
 // Elementwise evaluation of the library's own device elementary functions
 // (nsfr_math_eval): the FP64 log and exp of mathfn.cuh, the float-float ones
-// of mathfn_ff.cuh, the reciprocals of physics.cuh, the integer-pipe join of
-// float-float pairs and the volume kernels' logarithmic mean, so that they can
-// be checked against reference values.
+// of mathfn_ff.cuh, the reciprocals of physics.cuh, the integer-pipe split,
+// join and int-to-double conversion of ffloat.cuh and the volume kernels'
+// logarithmic mean, so that they can be checked against reference values.
 #include "mathfn.cuh"
 #include "mathfn_ff.cuh"
 #include "physics.cuh"
@@ -24,6 +24,12 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
         r = ff_join_i(ff{__uint_as_float((unsigned int)(b >> 32)), __uint_as_float((unsigned int)b)});
         break;
       }
+      case NSFR_FN_SPLIT: {  // the integer-pipe split of v, hi in the high 32 bits, lo in the low
+        const ff q = ff_split_i(v);
+        r = __hiloint2double((int)__float_as_uint(q.hi), (int)__float_as_uint(q.lo));
+        break;
+      }
+      case NSFR_FN_I2D: r = i2d_i(__double2loint(v)); break;  // the low 32 bits of v as an int
       case NSFR_FN_LOGMEAN1: {  // logarithmic mean of v and 1 as the volume kernels form it
         // G(u) - 1 = u (c1 + u (c2 + u c3)): c1 = -1/3, c2 = -4/45 (hi, lo), c3 = -44/945
         const double c1 = -1.0 / 3.0, c2 = -4.0 / 45.0;

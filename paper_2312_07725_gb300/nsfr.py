@@ -170,7 +170,8 @@ def fma_probe(fp32, iters, blocks, sink, stream=None):
     return n.value
 
 
-MATH_FN = {"log": 0, "exp": 1, "rcp": 2, "rcp1": 3, "log_ff": 4, "exp_ff": 5, "join": 6, "logmean1": 7}
+MATH_FN = {"log": 0, "exp": 1, "rcp": 2, "rcp1": 3, "log_ff": 4, "exp_ff": 5, "join": 6, "logmean1": 7,
+           "split": 8, "i2d": 9}
 
 
 def math_eval(fn, x, y=None, stream=None):
@@ -178,8 +179,10 @@ def math_eval(fn, x, y=None, stream=None):
     ``rcp``: full-precision reciprocal, ``rcp1``: one Newton step, ``log_ff``,
     ``exp_ff``: the float-float functions of the FP32-bulk kernels, ``join``:
     the integer-pipe join of the float pair packed in each element's 64 bits,
-    ``logmean1``: the volume kernels' logarithmic mean of x and 1), for
-    checking them; x, y contiguous float64 CUDA tensors.  Returns y."""
+    ``logmean1``: the volume kernels' logarithmic mean of x and 1, ``split``:
+    the integer-pipe split of x into two floats, packed as ``join`` takes them,
+    ``i2d``: the int in the low 32 bits of x as a double), for checking them;
+    x, y contiguous float64 CUDA tensors.  Returns y."""
     import torch
     if y is None:
         y = torch.empty_like(x)

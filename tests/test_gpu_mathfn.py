@@ -199,3 +199,59 @@ def test_logmean_series_branch_within_two_ulp():
     ulps = np.abs(y - ref) / np.spacing(np.abs(ref))
     assert np.max(ulps[series]) <= 2.0, np.max(ulps[series])
     assert np.max(np.abs(y - ref)[logb] / ref[logb]) <= 1e-14
+
+
+def _unpack_pairs(y):
+    bits = y.view(np.uint64)
+    hi = (bits >> np.uint64(32)).astype(np.uint32).view(np.float32)
+    lo = (bits & np.uint64(0xffffffff)).astype(np.uint32).view(np.float32)
+    return hi, lo
+
+
+def test_split_into_nearest_float_and_truncated_remainder():
+    """ff_split_i (integer-pipe split of a double, used by the log, exp and all float-float
+    paths): hi is the float nearest x (ties away from zero), lo the leading 24 bits of the
+    exact remainder x - hi (truncated toward zero), so |x - hi - lo| < 2^-48 |x|; a remainder
+    below the FP32 normal range gives lo = 0."""
+    from fractions import Fraction
+    import math
+    n = 4000
+    x = np.ldexp(RNG.uniform(1.0, 2.0, n), RNG.integers(-90, 90, n)) * RNG.choice([-1.0, 1.0], n)
+    f = np.float32(RNG.uniform(1.0, 2.0, 200)).astype(np.float64)
+    half_ulp = np.ldexp(1.0, np.frexp(f)[1] - 25)     # exact ties between two floats
+    x = np.concatenate([x, f, -f, f + half_ulp, -(f + half_ulp), np.array([1.0, -3.0, 1e-30, 7e29])])
+    y, _ = _eval("split", x)
+    hi, lo = _unpack_pairs(y)
+    for xv, h, l in zip(x, hi.astype(np.float64), lo.astype(np.float64)):
+        X = Fraction(xv)
+        f0 = np.float32(xv)                      # nearest float, ties to even
+        want = Fraction(float(f0))
+        if want != X:                            # the float on X's other side
+            f1 = np.nextafter(f0, np.float32(-np.inf) if want > X else np.float32(np.inf))
+            other = Fraction(float(f1))
+            if abs(X - other) == abs(X - want) and abs(other) > abs(want):
+                want = other                     # a tie goes away from zero
+        assert Fraction(h) == want, (xv, h)
+        R = X - want
+        if R == 0:
+            assert l == 0.0
+        else:
+            e = math.floor(math.log2(abs(float(R))))
+            if Fraction(2) ** e > abs(R):
+                e -= 1
+            q = math.floor(abs(R) * Fraction(2) ** (23 - e))
+            if e < -126:                         # below the FP32 normal range: flushed
+                assert l == 0.0, (xv, l)
+                continue
+            assert Fraction(l) == (1 if R > 0 else -1) * Fraction(q) / Fraction(2) ** (23 - e), (xv, l)
+        assert abs(X - Fraction(h) - Fraction(l)) < abs(X) * Fraction(1, 2 ** 48)
+
+
+def test_int_to_double_is_exact():
+    """i2d_i (integer-pipe int-to-double conversion, used by the log's and exp's
+    reductions): exact for every 32-bit int."""
+    ints = np.concatenate([RNG.integers(-2 ** 31, 2 ** 31, 20000), np.array([0, 1, -1, 2 ** 31 - 1, -2 ** 31, 1023,
+                                                                            -1022, 32316, -32316])])
+    bits = (np.uint64(0x3ff00000) << np.uint64(32)) | (ints.astype(np.int64) & 0xffffffff).astype(np.uint64)
+    y, _ = _eval("i2d", bits.view(np.float64))
+    assert np.array_equal(y, ints.astype(np.float64))
