@@ -47,10 +47,10 @@ import workloads as wl  # noqa: E402
 # two log means) and per accumulation of one flux into two residual entries
 FLOPS_PER_FLUX = 55
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one volume_kernel<5>
-# launch per element, from an ncu --set full capture at 24^3 elements (813.1 + 125.6 MB
+# launch per element, from an ncu --set full capture at 24^3 elements (813.1 + 125.2 MB
 # for 13,824 elements, the kernel as it stands: profiles/volume_kernel_p4_tgv24.md; every
 # buffer the kernel touches scales with the element count)
-VOLUME_DRAM_BYTES_PER_ELEMENT = {4: (813.127936e6 + 125.575168e6) / 13824}
+VOLUME_DRAM_BYTES_PER_ELEMENT = {4: (813.061120e6 + 125.166336e6) / 13824}
 FLOPS_PER_ACC = 20
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 

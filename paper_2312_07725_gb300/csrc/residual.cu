@@ -277,9 +277,11 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
   // slab of Ra (only this thread touches them), node a's in registers while
   // a is the outer pair index -- the additions keep the order of a plain
   // per-line accumulation.  The averaged metric row of each pair comes from
-  // the pair table (rows scaled by w_perp / 2: w_perp is constant along a line
-  // and the fluxes are linear in the metric row, so the pair weights reduce to
-  // S1); the next row is loaded while the current flux is evaluated.
+  // the pair table, scaled by w_perp / 2 (constant along a line) and, for
+  // Chandrashekar's flux, by the pair's weight S1_ab (t_s,a for a hybrid row):
+  // the fluxes are linear in the metric row, so only that flux's own factor
+  // s = rho_a + rho_b remains; Ranocha's takes S1_ab and t_s,a here.  The next
+  // row is loaded while the current flux is evaluated.
   const int le = threadIdx.x / NL, l = threadIdx.x % NL, e = e0 + le;
   const int d = l / NFP, line = l % NFP, l0 = line % N, l1 = line / N;
   int base, stride;
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
         double F[5];
         const double fs = vol_flux<VF>(A, B, Af, recf_at(b), n0, n1, n2, ops, PtrLogs{Le + a * stride, NV},
                                        PtrLogs{Le + b * stride, NV}, F);
-        const double c = VF == NSFR_FLUX_RANOCHA ? ops.S1[a * N + b] : ops.S1[a * N + b] * fs;
+        const double c = VF == NSFR_FLUX_RANOCHA ? ops.S1[a * N + b] : fs;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
           Racc[k] = fma(c, F[k], Racc[k]);
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(vol_threads(N), vol_ctas(N)) volume_kernel(con
         const double fs = vol_flux<VF>(A, Fo, recf_at(a), Fof, Ph[3 * a * NFP], Ph[(3 * a + 1) * NFP],
                                        Ph[(3 * a + 2) * NFP], ops,
                                        PtrLogs{Le + a * stride, NV}, PtrLogs{fo + P_LRHO * NFP, NFP}, F);
-        const double ta = VF == NSFR_FLUX_RANOCHA ? t[a] : t[a] * fs;
+        const double ta = VF == NSFR_FLUX_RANOCHA ? t[a] : fs;
         const double swt = neg_if(ta, !s);  // s t_a, the sign flipped on the integer pipe
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -516,12 +518,17 @@ __global__ void scaled_rows_kernel(const double* __restrict__ metric, const doub
 namespace {
 // The pair table of the volume kernel, from the scaled rows (geometry only): for
 // element e, direction d, line l, component c, row q < n(n-1)/2 holds
-// M_a + M_b for the q-th pair a < b of the line (the volume kernel's loop
-// order), row n(n-1)/2 + s n + a holds M_a + (w_perp C_f)/2 for node a and
-// the face of side s (C_f the face's shared row), M = w_perp C / 2 the scaled
-// metric row of the node: the same sums the line phase would form per pair.
-__global__ void pair_rows_kernel(const double* __restrict__ metric_s, const double* __restrict__ nf_s, int n, int nx,
-                                 int ny, int nz, double* __restrict__ pm) {
+// w_ab (M_a + M_b) for the q-th pair a < b of the line (the volume kernel's
+// loop order), row n(n-1)/2 + s n + a holds w_sa (M_a + (w_perp C_f)/2) for
+// node a and the face of side s (C_f the face's shared row), M = w_perp C / 2
+// the scaled metric row of the node.  With fold the weights are the pairs'
+// weights in the Hadamard sum (Eq. NSFR), w_ab = S1_ab and w_sa = t_s,a (the
+// extrapolation to that face): the two-point fluxes are linear in the metric
+// row, so a pair's flux on this row is its flux on the averaged row times its
+// weight, which then costs the line phase nothing per step.  Without fold
+// they are 1, and the line phase applies them.
+__global__ void pair_rows_kernel(const double* __restrict__ metric_s, const double* __restrict__ nf_s, OpsGL ops,
+                                 bool fold, int n, int nx, int ny, int nz, double* __restrict__ pm) {
   const int nv = n * n * n, nfp = n * n, np = n * (n - 1) / 2, npp = pair_rows(n);
   const size_t ne = (size_t)nx * ny * nz, total = ne * 3 * npp * 3 * nfp;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
@@ -538,12 +545,15 @@ __global__ void pair_rows_kernel(const double* __restrict__ metric_s, const doub
         r -= n - 1 - a;
         ++a;
       }
-      pm[t] = M[a * stride] + M[(a + 1 + r) * stride];
+      const int b = a + 1 + r;
+      const double m = M[a * stride] + M[b * stride];
+      pm[t] = fold ? ops.S1[a * n + b] * m : m;
     } else {
       const int side = (q - np) / n, a = (q - np) % n;
       const int en = nsfr_k::nbr_index((int)e, d, side, nx, ny, nz);
       const size_t fe = (size_t)(side ? e : en) * 3 + d;
-      pm[t] = M[a * stride] + 0.5 * nf_s[(fe * 3 + c) * nfp + line];
+      const double m = M[a * stride] + 0.5 * nf_s[(fe * 3 + c) * nfp + line];
+      pm[t] = fold ? (side ? ops.tp[a] : ops.tm[a]) * m : m;
     }
   }
 }
@@ -556,7 +566,13 @@ cudaError_t nsfr_launch_scaled_rows(nsfr_ctx* ctx, cudaStream_t s) {
   ctx->launches++;
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess || !ctx->pair_rows) return err;
-  pair_rows_kernel<<<152 * 8, 256, 0, s>>>(ctx->metric_s, ctx->nf_s, ctx->n, ctx->nx, ctx->ny, ctx->nz, ctx->pair_rows);
+  // the weights go into the rows for Chandrashekar's flux, whose line phase
+  // would otherwise multiply them into its factor s per pair; Ranocha's flux
+  // takes them as plain FMA operands in its accumulation (folded, that kernel
+  // measured 2% slower)
+  const bool fold = ctx->vol_flux != NSFR_FLUX_RANOCHA;  // the kernel choice of nsfr_launch_volume
+  pair_rows_kernel<<<152 * 8, 256, 0, s>>>(ctx->metric_s, ctx->nf_s, ctx->ops, fold, ctx->n, ctx->nx, ctx->ny,
+                                           ctx->nz, ctx->pair_rows);
   ctx->launches++;
   return cudaGetLastError();
 }
