@@ -365,11 +365,9 @@ nsfr_status nsfr_profile_read(nsfr_ctx* ctx, double* ms, long long* count);
  * GPU that loads the library keeps until the process exits.  A problem
  * needing more than that, 256 + N_e (36 n^4 + 260 n^3 + 576 n^2) bytes
  * (about 470 elements at p = 3, 240 at p = 4), is rejected with
- * NSFR_ERR_ARG before anything runs.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) with that device
- * current and keeps it for the process; make that first call before any
- * stream capture, and make no call after cudaDeviceReset on that device (the
- * kept address belongs to the context the reset destroyed).  All calls share
+ * NSFR_ERR_ARG before anything runs.  Every call looks up the array's
+ * address in the current device's context (cudaGetSymbolAddress, which
+ * allocates nothing).  All calls share
  * the one array and the last call's contents stay in it; the error word is
  * cleared at the start of every call.  Calls that overlap on the GPU (other
  * streams, other threads) race on the array: serialise them.  The call

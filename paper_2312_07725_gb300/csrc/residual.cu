@@ -644,14 +644,9 @@ cudaError_t nsfr_launch_volume(nsfr_ctx* ctx, const double* u, double* out, int 
 // nsfr_residual_static: the same kernels on caller buffers, with the working
 // memory in a fixed device array of this file instead of allocations.
 // ---------------------------------------------------------------------------
-#include <mutex>
-
 static __device__ __align__(256) unsigned char g_static_scratch[NSFR_STATIC_SCRATCH_BYTES];
 
 namespace {
-std::mutex g_static_mu;
-void* g_static_addr[256] = {nullptr};  // device address of g_static_scratch, per device ordinal
-
 // p is device (or managed) memory of device dev; host memory, memory of another
 // device and unknown pointers are refused before anything is launched
 bool static_dev_ptr(const void* p, int dev) {
@@ -681,20 +676,15 @@ extern "C" nsfr_status nsfr_residual_static(const double* u, const double* C, co
   const size_t need = 256 + face_bytes + fstar_bytes + (2 + NSFR_NFIELD) * jac_bytes + ms_bytes + nfs_bytes + pm_bytes;
   if (need > NSFR_STATIC_SCRATCH_BYTES || ne > (size_t)0x7fffffff) return NSFR_ERR_ARG;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return NSFR_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NSFR_ERR_CUDA;
   if (!static_dev_ptr(u, dev) || !static_dev_ptr(C, dev) || !static_dev_ptr(J, dev) || !static_dev_ptr(Cf, dev) ||
       !static_dev_ptr(dudt, dev))
     return NSFR_ERR_ARG;
-  unsigned char* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
-      void* addr = nullptr;
-      if (cudaGetSymbolAddress(&addr, g_static_scratch) != cudaSuccess || !addr) return NSFR_ERR_CUDA;
-      g_static_addr[dev] = addr;
-    }
-    base = (unsigned char*)g_static_addr[dev];
-  }
+  // the array's address in the current device's context, looked up on every
+  // call (no allocation: the array is part of the loaded module)
+  void* addr = nullptr;
+  if (cudaGetSymbolAddress(&addr, g_static_scratch) != cudaSuccess || !addr) return NSFR_ERR_CUDA;
+  unsigned char* base = (unsigned char*)addr;
   cudaStream_t s = (cudaStream_t)stream;
   nsfr_ctx ctx;  // a view of caller buffers and the fixed array; owns nothing
   ctx.nx = nx;
