@@ -52,6 +52,10 @@ FLOPS_PER_FLUX = 55
 # buffer the kernel touches scales with the element count)
 VOLUME_DRAM_BYTES_PER_ELEMENT = {4: (813.061120e6 + 125.166336e6) / 13824}
 FLOPS_PER_ACC = 20
+# the same with Ranocha's pressure terms: the two log means (22), u_bar (3), u_bar.n,
+# u_a.n / 2 and u_a.u_b / 4 (15), F_rho (1), p_bar (2), 1/(2 (gamma-1) beta_ln) (2), the
+# momentum flux (9) and the energy flux (8)
+FLOPS_PER_FLUX_RANOCHA = 62
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -330,10 +334,22 @@ def run_reference(args, rank, ws, dist):
 # --------------------------------------------------------------------------
 # our implementation
 # --------------------------------------------------------------------------
-def volume_kernel_flops(n_el, p, has_k=True, nq=None):
+def volume_kernel_flops(n_el, p, has_k=True, nq=None, vol_flux="chandrashekar"):
     """Algorithmic FP64 flops of one volume-kernel launch over n_el elements (for the
     uncollocated scheme the lines have nq points and the epilogue is the dense
-    (chi Pi~1)^T, 1/(wJ), Pi~1 sweeps back to the p+1 solution nodes)."""
+    (chi Pi~1)^T, 1/(wJ), Pi~1 sweeps back to the p+1 solution nodes).  With Ranocha's
+    pressure terms every flux counts FLOPS_PER_FLUX_RANOCHA, and the node pressures
+    rho / (2 beta) 2 flops per node."""
+    if vol_flux == "ranocha":
+        if nq is not None:
+            raise ValueError("the Ranocha model is for the collocated scheme")
+        n = p + 1
+        fluxes_vol, fluxes_hyb = 3 * n * n * n * (n - 1) // 2, 6 * n ** 3
+        per_el = (fluxes_vol + fluxes_hyb) * (FLOPS_PER_FLUX_RANOCHA + FLOPS_PER_ACC)
+        per_el += 6 * n * n * (5 + 10 * n) + 5 * n ** 3 + 2 * n ** 3
+        if has_k:
+            per_el += 6 * 5 * n * n * 4 * n
+        return per_el * n_el, {"volume_pairs": fluxes_vol, "hybrid": fluxes_hyb, "flops_per_element": per_el}
     if nq is not None:
         n, ns = nq, p + 1
         per_el = (3 * n * n * n * (n - 1) // 2 + 6 * n ** 3) * (FLOPS_PER_FLUX + FLOPS_PER_ACC)
@@ -591,6 +607,9 @@ def run_ours(args, rank, ws, dist):
         for nm, m in (("fp32_bulk", m32), ("fp32_bulk_ff", mff)):
             if m is not None:
                 rk[nm] = roofline_kernels(m["kernels"], p, ne_launch, nm, m["clocks"], peaks, cfg["c"] != 0.0)
+        if mra is not None:
+            rk["ranocha"] = roofline_kernels(mra["kernels"], p, ne_launch, "fp64", mra["clocks"], peaks,
+                                             cfg["c"] != 0.0, vol_flux="ranocha")
     if adj is not None and rk is not None:
         fp64_nom = peak
         rk["adjoint"] = {}
@@ -700,25 +719,27 @@ def measure_fma_peaks():
     return out
 
 
-def stage_kernel_models(p, ne, precision, has_k=True):
+def stage_kernel_models(p, ne, precision, has_k=True, vol_flux="chandrashekar"):
     """Algorithmic work of one launch of each kernel of an RK stage over ne elements
     (n = p+1; an FMA counts 2 flops; a division, reciprocal, square root, log or exp 1):
       face_states  v(u) at n^3 nodes (32 each: u, |u|^2, p, beta, ln rho, ln p, s, v,
                    the record fields), t_s . v to the six faces (30 n^3 multiply-adds),
                    u(v~) at 6 n^2 face nodes (22 each: u, |u|^2, s~, ln 2 beta~, rho~ by
                    exp, the record fields)
-      face_flux    3 n^2 face fluxes of 55 flops (the EC flux of the bench's faces)
+      face_flux    3 n^2 face fluxes of 55 flops (the EC flux of the bench's faces; with
+                   Ranocha's pressure terms 62, plus 4 for the two states' pressures)
       volume       volume_kernel_flops
       max_wavespeed  40 bytes (the state) read per node and launch
     Returns {kernel: (kind, work, unit)}."""
     n = p + 1
     fs = (32 * n ** 3 + 60 * n ** 3 + 6 * n * n * 22) * ne
-    vol, _ = volume_kernel_flops(ne, p, has_k)
-    return {"face_states": ("flops", fs), "face_flux": ("flops", 3 * n * n * FLOPS_PER_FLUX * ne),
+    vol, _ = volume_kernel_flops(ne, p, has_k, vol_flux=vol_flux)
+    ff = FLOPS_PER_FLUX_RANOCHA + 4 if vol_flux == "ranocha" else FLOPS_PER_FLUX
+    return {"face_states": ("flops", fs), "face_flux": ("flops", 3 * n * n * ff * ne),
             "volume": ("flops", vol), "max_wavespeed": ("bytes", 40 * n ** 3 * ne)}
 
 
-def roofline_kernels(kern, p, ne, precision, clk, peaks, has_k=True):
+def roofline_kernels(kern, p, ne, precision, clk, peaks, has_k=True, vol_flux="chandrashekar"):
     """Per-kernel rooflines of one precision mode's timed step: algorithmic work per launch
     (stage_kernel_models) over the kernel's mean launch time from the library's CUDA events,
     against the bounding resource: the FP64 FMA pipe (nominal from 152 SMs x 2 lanes x the
@@ -728,7 +749,7 @@ def roofline_kernels(kern, p, ne, precision, clk, peaks, has_k=True):
     fp64_nom = 152 * FP64_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
     fp32_nom = 152 * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
     hbm, hbm_src = hbm_peak()
-    models = stage_kernel_models(p, ne, precision, has_k)
+    models = stage_kernel_models(p, ne, precision, has_k, vol_flux)
     out = {}
     for name, (kind, work) in models.items():
         if name not in kern:

@@ -26,6 +26,17 @@ def test_volume_flops_at_p4():
     assert c0["flops_per_element"] == 136375 - 120 * 125
 
 
+def test_ranocha_flops_at_p4():
+    # Ranocha's pressure terms: 1,500 fluxes x (62 + 20), the same face combination, 1/(w J)
+    # and sweeps, and 2 flops per node for the pressures; its face fluxes 75 x (62 + 4)
+    _, counts = bench.volume_kernel_flops(1, 4, vol_flux="ranocha")
+    assert counts["flops_per_element"] == 1500 * 82 + 150 * 55 + 625 + 120 * 125 + 2 * 125 == 147125
+    models = bench.stage_kernel_models(4, 1, "fp64", vol_flux="ranocha")
+    assert models["volume"] == ("flops", 147125)
+    assert models["face_flux"] == ("flops", 75 * 66)
+    assert bench.stage_kernel_models(4, 1, "fp64")["face_flux"] == ("flops", 75 * 55)
+
+
 class _FakeProc:
     def terminate(self):
         pass
