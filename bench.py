@@ -494,12 +494,32 @@ def measure(args, ctrl, u0, precision, dist, rank, ws, steps, vol_flux="chandras
     torch.cuda.synchronize()
     rms = max_over_ranks(dist, e0.elapsed_time(e1)) / (4 * steps)
     residual_only = nodes * ws / (rms / 1e3) / 1e9
+    wa = None
+    if precision == "fp64" and vol_flux == "chandrashekar" and args.nq is None:
+        # the weight-adjusted inverse is the volume kernel's epilogue: its cost is the
+        # kernel storing du/dt (sweeps, 1/(W J)) less the same kernel storing R
+        # (nsfr_residual_raw), both from the library's events on the launch stream
+        # (into a buffer of its own: D keeps the du/dt the precision modes are compared on)
+        vol, Dw = {}, torch.empty_like(uin)
+        for name, fn in (("dudt", S.residual), ("raw", S.residual_raw)):
+            fn(uin, Dw)
+            torch.cuda.synchronize()
+            S.profile(True)
+            for _ in range(2 * steps):
+                fn(uin, Dw)
+            torch.cuda.synchronize()
+            S.profile(False)
+            t_ms, n_l = S.profile_read()["volume"]
+            vol[name] = t_ms / n_l
+        wa = {"volume_ms_dudt": vol["dudt"], "volume_ms_raw": vol["raw"], "ms": vol["dudt"] - vol["raw"]}
+        del Dw
     del uin
     kern = {k: {"ms_total": v[0], "launches": v[1], "ms_avg": v[0] / v[1]} for k, v in prof.items()}
     res = {"value": value, "ms_per_step": ms / steps, "e2e": e2e, "e2e_bytes": e2e_bytes,
            "gpu_launches": launches, "kernels": kern, "clocks": clk,
            "dudt": run.interior(D).cpu().numpy(), "n_el_computed": S.n_el,
-           "residual_only": {"value": residual_only, "unit": "GDOF/s", "ms_per_evaluation": rms}}
+           "residual_only": {"value": residual_only, "unit": "GDOF/s", "ms_per_evaluation": rms},
+           "wa_inverse": wa}
     S.close()
     del u, D, run
     torch.cuda.empty_cache()
@@ -604,6 +624,9 @@ def run_ours(args, rank, ws, dist):
     rk = None
     if args.nq is None:  # the stage models are those of the collocated scheme
         rk = {"fp64": roofline_kernels(m64["kernels"], p, ne_launch, "fp64", clk, peaks, cfg["c"] != 0.0)}
+        if m64.get("wa_inverse"):
+            rk["fp64"]["mass_inverse"] = wa_inverse_roofline(m64["wa_inverse"], p, ne_launch, clk, peaks,
+                                                             cfg["c"] != 0.0)
         for nm, m in (("fp32_bulk", m32), ("fp32_bulk_ff", mff)):
             if m is not None:
                 rk[nm] = roofline_kernels(m["kernels"], p, ne_launch, nm, m["clocks"], peaks, cfg["c"] != 0.0)
@@ -781,6 +804,28 @@ def roofline_kernels(kern, p, ne, precision, clk, peaks, has_k=True, vol_flux="c
             e["frac_of_measured_probe"] = ach / peaks["fp64"]["tflops"]
         out[name] = e
     return out
+
+
+def wa_inverse_roofline(wa, p, ne, clk, peaks, has_k=True):
+    """The weight-adjusted mass inverse, fused into the volume kernel's epilogue: its
+    algorithmic flops (the six rank-one sweeps, 120 n^3 per element, and the 1/(W J)
+    scaling, 5 n^3) over its marginal time, the volume kernel storing du/dt less the
+    same kernel storing R."""
+    n = p + 1
+    work = (5 * n ** 3 + (120 * n ** 3 if has_k else 0)) * ne
+    mhz = clk.get("sm_mhz") or 2070.0
+    fp64_nom = 152 * FP64_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    t = wa["ms"] / 1e3
+    e = {"bound": "alu", "pipe": "fp64", "work_per_launch": work, "work_unit": "flops", "ms_avg": wa["ms"],
+         "how": "marginal: volume kernel with the du/dt epilogue "
+                f"({wa['volume_ms_dudt']:.3f} ms) less the same kernel storing R ({wa['volume_ms_raw']:.3f} ms)"}
+    if t > 0:
+        ach = work / t / 1e12
+        e.update({"achieved": ach, "unit": "TFLOP/s", "peak": fp64_nom, "frac": ach / fp64_nom,
+                  "peak_source": f"152 SMs x 2 FP64 FMA/clk/SM x 2 x {mhz:.0f} MHz"})
+        if peaks and "fp64" in peaks:
+            e["frac_of_measured_probe"] = ach / peaks["fp64"]["tflops"]
+    return e
 
 
 def adjoint_kernel_models(p, ne, has_k=True):

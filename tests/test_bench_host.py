@@ -37,6 +37,18 @@ def test_ranocha_flops_at_p4():
     assert bench.stage_kernel_models(4, 1, "fp64")["face_flux"] == ("flops", 75 * 55)
 
 
+def test_wa_inverse_flops_at_p4():
+    # six rank-one sweeps of 2 n multiply-adds per line (120 n^3 flops per element) and the
+    # 1/(W J) scaling (5 n^3), n = 5; without K only the scaling
+    e = bench.wa_inverse_roofline({"volume_ms_dudt": 3.0, "volume_ms_raw": 2.0, "ms": 1.0}, 4, 10,
+                                  {"sm_mhz": 2000.0}, None)
+    assert e["work_per_launch"] == 15625 * 10
+    assert abs(e["achieved"] - 15625 * 10 / 1e-3 / 1e12) < 1e-15
+    e0 = bench.wa_inverse_roofline({"volume_ms_dudt": 3.0, "volume_ms_raw": 2.0, "ms": 1.0}, 4, 10,
+                                   {"sm_mhz": 2000.0}, None, has_k=False)
+    assert e0["work_per_launch"] == 625 * 10
+
+
 class _FakeProc:
     def terminate(self):
         pass
