@@ -77,6 +77,23 @@ def test_chandrashekar_consistency_and_symmetry():
                        rtol=1e-14, atol=1e-14)
 
 
+@pytest.mark.parametrize("flux", ["chandrashekar", "ranocha"])
+def test_two_point_fluxes_are_linear_in_the_metric_row(flux):
+    """F(u_a, u_b; l n1 + m n2) = l F(n1) + m F(n2): the volume kernels rely on it to average
+    the two nodes' metric rows once per pair and to fold the pair's weight in the Hadamard sum
+    (S1_ab, or t_s,a for a hybrid pair; Eq. NSFR) into that row, signs included."""
+    F = getattr(physics, flux)
+    U, U2 = random_states(1000, 21), random_states(1000, 22)
+    rng = np.random.default_rng(23)
+    n1, n2 = rng.standard_normal((3, 1000)), rng.standard_normal((3, 1000))
+    lam, mu = rng.uniform(-3, 3, 1000), rng.uniform(-3, 3, 1000)
+    lhs = F(U, U2, lam * n1 + mu * n2, G)
+    rhs = lam * F(U, U2, n1, G) + mu * F(U, U2, n2, G)
+    scale = np.abs(lam * F(U, U2, n1, G)).max(axis=1, keepdims=True) + np.abs(mu * F(U, U2, n2, G)).max(
+        axis=1, keepdims=True)
+    assert np.all(np.abs(lhs - rhs) <= 1e-14 * scale)
+
+
 @pytest.mark.parametrize("spread", [1e-3, 0.05, 0.8])
 def test_tadmor_shuffle(spread):
     """[[v]] . f_s . n = [[psi . n]] for every pair (Eq. Tadmor shuffle quad node)."""
