@@ -77,12 +77,8 @@ def test_chandrashekar_consistency_and_symmetry():
                        rtol=1e-14, atol=1e-14)
 
 
-@pytest.mark.parametrize("flux", ["chandrashekar", "ranocha"])
-def test_two_point_fluxes_are_linear_in_the_metric_row(flux):
-    """F(u_a, u_b; l n1 + m n2) = l F(n1) + m F(n2): the volume kernels rely on it to average
-    the two nodes' metric rows once per pair and to fold the pair's weight in the Hadamard sum
-    (S1_ab, or t_s,a for a hybrid pair; Eq. NSFR) into that row, signs included."""
-    F = getattr(physics, flux)
+def _linearity_defect(F):
+    """max over variables of |F(l n1 + m n2) - l F(n1) - m F(n2)| / scale on random pairs."""
     U, U2 = random_states(1000, 21), random_states(1000, 22)
     rng = np.random.default_rng(23)
     n1, n2 = rng.standard_normal((3, 1000)), rng.standard_normal((3, 1000))
@@ -91,7 +87,32 @@ def test_two_point_fluxes_are_linear_in_the_metric_row(flux):
     rhs = lam * F(U, U2, n1, G) + mu * F(U, U2, n2, G)
     scale = np.abs(lam * F(U, U2, n1, G)).max(axis=1, keepdims=True) + np.abs(mu * F(U, U2, n2, G)).max(
         axis=1, keepdims=True)
-    assert np.all(np.abs(lhs - rhs) <= 1e-14 * scale)
+    return float((np.abs(lhs - rhs) / scale).max())
+
+
+@pytest.mark.parametrize("flux", ["chandrashekar", "ranocha"])
+def test_two_point_fluxes_are_linear_in_the_metric_row(flux):
+    """F(u_a, u_b; l n1 + m n2) = l F(n1) + m F(n2): the volume kernels rely on it to average
+    the two nodes' metric rows once per pair and to fold the pair's weight in the Hadamard sum
+    (S1_ab, or t_s,a for a hybrid pair; Eq. NSFR) into that row, signs included."""
+    assert _linearity_defect(getattr(physics, flux)) <= 1e-14
+
+
+def test_linearity_pin_catches_a_unit_normal_pressure_term():
+    """A pressure term taken along the unit normal (p_hat n/|n| in place of p_hat n) keeps the
+    flux consistent for unit rows but breaks linearity, and the pin above sees it."""
+    def planted(UL, UR, nvec, gamma):
+        F = physics.chandrashekar(UL, UR, nvec, gamma)
+        nn = np.sqrt(np.sum(nvec * nvec, axis=0))
+        p_hat = physics.chandrashekar(UL, UR, np.array([[1.0], [0.0], [0.0]]) * np.ones_like(nvec[:1]), gamma)
+        # p_hat from the x-momentum flux along e_x minus its convective part
+        rl, ul, _ = physics.primitive(UL, gamma)
+        rr, ur, _ = physics.primitive(UR, gamma)
+        ubar = 0.5 * (ul + ur)
+        p_hat = p_hat[1] - p_hat[0] * ubar[0]
+        F[1:4] += p_hat * nvec * (1.0 / nn - 1.0)
+        return F
+    assert _linearity_defect(planted) > 1e-3
 
 
 @pytest.mark.parametrize("spread", [1e-3, 0.05, 0.8])
